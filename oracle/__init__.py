@@ -1,0 +1,169 @@
+"""ctypes front end of the FP64 CPU oracle (test infrastructure only).
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` import this package.  The product path never does: it shares no code
+with the oracle, and the oracle shares none with it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "lb3e_oracle.c"
+_LIB = _HERE / "liblb3e_oracle.so"
+
+FIELDS = dict(phi1=0, phi2=1, phi3=2, ux=3, uy=4, p=5, q=6, psi=7, ex=8, ey=9,
+              mu1=10, mu2=11, mu3=12, phinow1=13, phinow2=14, phinow3=15, qtilde=16)
+SETS = dict(g=0, f1=1, f2=2, f3=3, l=4, h=5)
+POP_BASE = 100
+OBS_KEYS = ("mass1", "mass2", "mass3", "charge", "F_phi", "F_E", "F_u", "F_q",
+            "max_sum_dev", "D_inner", "D_outer", "nonfinite", "step", "poisson_iters",
+            "poisson_residual")
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("bc_y", C.c_int32), ("electric", C.c_int32),
+        ("rho", C.c_double * 3), ("visc", C.c_double * 3), ("tau_g", C.c_double),
+        ("gamma12", C.c_double), ("gamma13", C.c_double), ("gamma23", C.c_double),
+        ("width_D", C.c_double), ("tau_f", C.c_double),
+        ("eps", C.c_double * 3), ("sigma", C.c_double * 3), ("eps_ref", C.c_double),
+        ("alpha", C.c_double), ("V_bottom", C.c_double), ("V_top", C.c_double),
+        ("E_ext", C.c_double * 2), ("u_wall_bottom", C.c_double), ("u_wall_top", C.c_double),
+        ("charge_convection", C.c_int32), ("inner_phase", C.c_int32), ("matrix_phase", C.c_int32),
+        ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int32),
+        ("poisson_check_every", C.c_int32), ("poisson_fixed_iter", C.c_int32),
+    ]
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (-O2, no FMA contraction, OpenMP over cells)."""
+    if _LIB.exists() and not force and _LIB.stat().st_mtime >= _SRC.stat().st_mtime:
+        return _LIB
+    tmp = _LIB.with_suffix(f".{os.getpid()}.tmp")
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+           "-shared", "-o", str(tmp), str(_SRC), "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(str(build()))
+        dp = C.POINTER(C.c_double)
+        L.orc_create.restype = C.c_void_p
+        L.orc_create.argtypes = [C.POINTER(_Params), dp, dp, dp, dp, C.POINTER(C.c_int)]
+        L.orc_step.argtypes = [C.c_void_p, C.c_int]
+        L.orc_get_field.argtypes = [C.c_void_p, C.c_int, dp]
+        L.orc_observables.argtypes = [C.c_void_p, dp]
+        L.orc_destroy.argtypes = [C.c_void_p]
+        L.orc_solve_potential.argtypes = [C.c_void_p, dp, C.c_double, C.c_int, C.c_int, C.c_int, dp,
+                                          C.POINTER(C.c_int)]
+        L.orc_last_poisson.argtypes = [C.c_void_p, C.POINTER(C.c_int), dp, C.POINTER(C.c_int)]
+        L.orc_stencil.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, dp]
+        L.orc_lattice.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), dp, C.POINTER(C.c_int)]
+        L.orc_step_count.restype = C.c_int64
+        L.orc_step_count.argtypes = [C.c_void_p]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _c64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_params(p: dict) -> _Params:
+    s = _Params()
+    for name, ctype in _Params._fields_:
+        v = p[name if name != "width_D" else "width_D"]
+        if hasattr(ctype, "_length_"):
+            getattr(s, name)[:] = list(v)
+        else:
+            setattr(s, name, v)
+    return s
+
+
+class Oracle:
+    """FP64 reference simulation (one state per instance)."""
+
+    def __init__(self, params: dict, phi, u=None, q=None, noise=None):
+        self.params = dict(params)
+        self.nx, self.ny = int(params["nx"]), int(params["ny"])
+        self._keep = [_c64(phi), _c64(u), _c64(q), _c64(noise)]
+        st = C.c_int(0)
+        self._p = make_params(params)
+        h = lib().orc_create(C.byref(self._p), *(_ptr(a) for a in self._keep), C.byref(st))
+        if not h:
+            raise ValueError(f"oracle rejected parameters (status {st.value})")
+        self._h = C.c_void_p(h)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().orc_destroy(self._h)
+            self._h = None
+
+    def step(self, n: int = 1):
+        lib().orc_step(self._h, int(n))
+        return self
+
+    @property
+    def steps_done(self) -> int:
+        return int(lib().orc_step_count(self._h))
+
+    def field(self, name: str) -> np.ndarray:
+        out = np.empty((self.ny, self.nx))
+        if lib().orc_get_field(self._h, FIELDS[name], _ptr(out)) != 0:
+            raise KeyError(name)
+        return out
+
+    def pop(self, set_name: str, j: int) -> np.ndarray:
+        out = np.empty((self.ny, self.nx))
+        lib().orc_get_field(self._h, POP_BASE + 9 * SETS[set_name] + j, _ptr(out))
+        return out
+
+    def observables(self) -> dict:
+        out = np.zeros(16)
+        lib().orc_observables(self._h, _ptr(out))
+        return dict(zip(OBS_KEYS, out.tolist()))
+
+    def solve_potential(self, q=None, tol=1e-8, max_iter=100000, fixed=0, check=10):
+        qa = _c64(q)
+        res = C.c_double(0)
+        conv = C.c_int(0)
+        it = lib().orc_solve_potential(self._h, _ptr(qa), tol, max_iter, fixed, check, C.byref(res),
+                                       C.byref(conv))
+        return it, res.value, bool(conv.value)
+
+    def last_poisson(self):
+        it, res, conv = C.c_int(0), C.c_double(0), C.c_int(0)
+        lib().orc_last_poisson(self._h, C.byref(it), C.byref(res), C.byref(conv))
+        return it.value, res.value, bool(conv.value)
+
+
+def stencil(chi: np.ndarray, bc_y: int):
+    chi = _c64(chi)
+    ny, nx = chi.shape
+    gx, gy, lap = np.empty_like(chi), np.empty_like(chi), np.empty_like(chi)
+    lib().orc_stencil(nx, ny, bc_y, _ptr(chi), _ptr(gx), _ptr(gy), _ptr(lap))
+    return gx, gy, lap
+
+
+def lattice():
+    cx, cy, opp = (C.c_int * 9)(), (C.c_int * 9)(), (C.c_int * 9)()
+    w = (C.c_double * 9)()
+    lib().orc_lattice(cx, cy, w, opp)
+    return np.array(cx[:]), np.array(cy[:]), np.array(w[:]), np.array(opp[:])

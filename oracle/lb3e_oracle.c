@@ -1,0 +1,732 @@
+/*
+ * lb3e_oracle.c -- plain FP64 CPU oracle of the three-phase EHD lattice Boltzmann
+ * step (Liu, Qian, Xiong, Wang: Onsager-variational LB model for three-phase
+ * dielectric fluid flows).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct statement of
+ * what the GPU path computes.  Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark load it.  It shares no code, header or constant
+ * generator with the CUDA library.
+ *
+ * Everything is double precision, one cell at a time, in the order of the paper's
+ * Section 3: moments, property interpolation (Eq. 29-30), isotropic stencils
+ * (Eq. 33), the potential solve (Eq. 42-45), the chemical potential (Eq. 20), the
+ * capillary + Coulomb force (Eq. 26/27b), flow moments (Eq. 41), then collision of
+ * the phase (Eq. 34-36), flow (Eq. 37-40) and charge (Eq. 46-50) populations and
+ * streaming.  Build with -ffp-contract=off so no multiply-add is fused.
+ *
+ * Readings where the paper is silent or garbled (each is listed in the design
+ * notes):  chemical potential from Eq. 20, not the energy density printed in
+ * Eq. 27c;  source F_j^i of Eq. 36 read as w_j c_j . [...] (the mobility part is a
+ * flux, so it carries c_j);  the implicit charge q = sum l + R/2 solved in closed
+ * form with the previous step's field;  d/dt terms as first-order backward
+ * differences;  half-way walls at y = -1/2 and ny - 1/2 with mirrored stencil
+ * ghosts;  electrodes applied by anti-bounce-back of the potential populations;
+ * potential iterations stopped on the relative increments of the potential and
+ * of the first moment of h (which carries the field).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------- D2Q9 lattice, Eq. 31 ---------------- */
+static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double W[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                            1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#define CS2 (1.0 / 3.0) /* lattice sound speed squared, Section 3.1 */
+
+/* parameter block; field meanings follow the paper's notation */
+typedef struct orc_params {
+    int32_t nx, ny;
+    int32_t bc_y;              /* 0 periodic, 1 walls, 2 walls + electrodes */
+    int32_t electric;          /* 1: potential solved each step */
+    double rho[3], visc[3];    /* Eq. 29 */
+    double tau_g;              /* used when every visc <= 0 */
+    double gamma12, gamma13, gamma23; /* Eq. 9 */
+    double width_D;            /* interface width D, Eq. 7 */
+    double tau_f;              /* m0 = cs2 (tau_f - 1/2), Section 3.2 */
+    double eps[3], sigma[3];   /* Eq. 29-30 */
+    double eps_ref;            /* the constant part of the permittivity split, Eq. 42 */
+    double alpha;              /* charge diffusivity, tau_l = 1/2 + alpha/cs2 */
+    double V_bottom, V_top;    /* electrode potentials at y = -1/2 and ny - 1/2 */
+    double E_ext[2];           /* uniform external field added to -grad psi */
+    double u_wall_bottom, u_wall_top;
+    int32_t charge_convection; /* 1: u-terms in l_eq and T_j (Eq. 49-50) */
+    int32_t inner_phase, matrix_phase; /* 1-based, for the deformation factor */
+    double poisson_tol;
+    int32_t poisson_max_iter, poisson_check_every, poisson_fixed_iter;
+} orc_params;
+
+enum { F_PHI1 = 0, F_PHI2, F_PHI3, F_UX, F_UY, F_P, F_Q, F_PSI, F_EX, F_EY,
+       F_MU1, F_MU2, F_MU3, F_PHINOW1, F_PHINOW2, F_PHINOW3, F_QTILDE, F_NFIELDS };
+enum { POP_BASE = 100 }; /* POP_BASE + 9*set + j, sets: g, f1, f2, f3, l, h */
+
+typedef struct orc_state {
+    orc_params p;
+    int N;
+    double lam[3], m0, tau_h, tau_l;
+    /* populations at the start of a step (post-stream), and post-collision scratch */
+    double *g, *f, *l, *h;       /* g[9N], f[27N] (set-major), l[9N], h[9N] */
+    double *gs, *fs, *ls, *hs;
+    /* fields of the last completed step */
+    double *phi, *qt, *q, *rho, *sig, *eps, *lap, *geps, *gsig, *grho;
+    double *E, *psi, *mu, *gmu, *F, *u, *pr, *R;
+    double *prev_phiu, *prev_qu;  /* (phi_i u)^{n-1}, (q u)^{n-1} */
+    double *psi_prev, *J_prev;    /* psi and J at the previous pseudo-iteration */
+    int64_t step;
+    int last_iters;
+    double last_res;
+    int last_converged;
+} orc_state;
+
+static double* alloc0(size_t n) { return (double*)calloc(n ? n : 1, sizeof(double)); }
+
+/* ---------------- grid helpers ---------------- */
+static int wrap(int a, int n) { a %= n; return a < 0 ? a + n : a; }
+
+/* Stencil ghost rows: periodic in y, or the mirror image about a half-way wall
+ * (zero normal gradient of every stencilled field). */
+static int ghost_y(const orc_state* s, int y) {
+    int ny = s->p.ny;
+    if (s->p.bc_y == 0) return wrap(y, ny);
+    if (y < 0) return -1 - y;
+    if (y >= ny) return 2 * ny - 1 - y;
+    return y;
+}
+static double at(const orc_state* s, const double* fld, int x, int y) {
+    return fld[ghost_y(s, y) * s->p.nx + wrap(x, s->p.nx)];
+}
+
+/* Eq. 33: grad chi = sum_j w_j c_j chi(x + c_j) / cs2 */
+static void grad_at(const orc_state* s, const double* fld, int x, int y, double* gx, double* gy) {
+    double ax = 0.0, ay = 0.0;
+    for (int j = 0; j < 9; ++j) {
+        double v = at(s, fld, x + CX[j], y + CY[j]);
+        ax += W[j] * CX[j] * v;
+        ay += W[j] * CY[j] * v;
+    }
+    *gx = ax / CS2;
+    *gy = ay / CS2;
+}
+/* Eq. 33: lap chi = sum_j 2 w_j [chi(x + c_j) - chi(x)] / cs2 */
+static double lap_at(const orc_state* s, const double* fld, int x, int y) {
+    double c = at(s, fld, x, y), a = 0.0;
+    for (int j = 0; j < 9; ++j) a += 2.0 * W[j] * (at(s, fld, x + CX[j], y + CY[j]) - c);
+    return a / CS2;
+}
+
+/* ---------------- closures ---------------- */
+/* Eq. 30: eps = sum eps_i H(phi_i), H = phi^2 (3 - 2 phi) */
+static double perm(const orc_params* p, const double* ph) {
+    double e = 0.0;
+    for (int i = 0; i < 3; ++i) e += p->eps[i] * ph[i] * ph[i] * (3.0 - 2.0 * ph[i]);
+    return e;
+}
+static int use_visc(const orc_params* p) { return p->visc[0] > 0 && p->visc[1] > 0 && p->visc[2] > 0; }
+
+/* gather phi_i(x) of the last moments into a small array */
+static void phis(const orc_state* s, int c, double* ph) {
+    for (int i = 0; i < 3; ++i) ph[i] = s->phi[i * s->N + c];
+}
+
+/* ---------------- potential solve, Eq. 42-45 ---------------- */
+static double psi_moment(const orc_state* s, const double* h, int c) {
+    double a = 0.0;
+    for (int j = 1; j < 9; ++j) a += h[j * s->N + c];
+    return a / (1.0 - W[0]);                       /* Eq. 45 */
+}
+static void gradpsi_moment(const orc_state* s, const double* h, int c, double epshat,
+                           double* gx, double* gy) {
+    double ax = 0.0, ay = 0.0;
+    for (int j = 0; j < 9; ++j) {
+        ax += CX[j] * h[j * s->N + c];
+        ay += CY[j] * h[j * s->N + c];
+    }
+    double den = epshat + CS2 * s->tau_h;          /* Eq. 45 (Delta t = 1) */
+    *gx = -ax / den;
+    *gy = -ay / den;
+}
+
+/* stream post-collision populations `src` into `dst` (Section 3, streaming step),
+ * periodic in x; in y periodic or half-way bounce-back.  kind: 0 plain
+ * bounce-back, 1 flow (moving wall, needs rho), 2 potential (anti-bounce-back to the
+ * electrode potential when bc_y == 2, plain bounce-back otherwise). */
+static void stream(const orc_state* s, const double* src, double* dst, int kind) {
+    const int nx = s->p.nx, ny = s->p.ny, N = s->N;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            int c = y * nx + x;
+            for (int j = 0; j < 9; ++j) {
+                double v = src[j * N + c];
+                int yt = y + CY[j];
+                if (s->p.bc_y != 0 && (yt < 0 || yt >= ny)) {
+                    int top = yt >= ny;
+                    double out = v;
+                    if (kind == 1) {
+                        double uw = top ? s->p.u_wall_top : s->p.u_wall_bottom;
+                        out = v - 2.0 * W[j] * s->rho[c] * (CX[j] * uw) / CS2;
+                    } else if (kind == 2 && s->p.bc_y == 2) {
+                        double vw = top ? s->p.V_top : s->p.V_bottom;
+                        out = -v + 2.0 * W[j] * vw;
+                    }
+                    dst[OPP[j] * N + c] = out;
+                } else {
+                    int xt = wrap(x + CX[j], nx);
+                    dst[j * N + wrap(yt, ny) * nx + xt] = v;
+                }
+            }
+        }
+}
+
+/* One pseudo-time iteration of Eq. 43: collide every cell, then stream. */
+static void poisson_iteration(orc_state* s) {
+    const int N = s->N;
+    const double th = s->tau_h;
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < N; ++c) {
+        double epshat = s->eps[c] - s->p.eps_ref;
+        double psi = psi_moment(s, s->h, c);
+        double gx, gy;
+        gradpsi_moment(s, s->h, c, epshat, &gx, &gy);
+        double qc = s->q[c];
+        for (int j = 0; j < 9; ++j) {
+            double heq = (j == 0) ? (W[0] - 1.0) * psi : W[j] * psi;      /* Eq. 44 */
+            double varpi = (j == 0) ? 0.0 : 1.0 / 8.0;
+            double hj = s->h[j * N + c];
+            double cg = CX[j] * gx + CY[j] * gy;
+            s->hs[j * N + c] = hj - (hj - heq) / th - (epshat / CS2) * W[j] * cg / th + varpi * qc;
+        }
+    }
+    stream(s, s->hs, s->h, 2);
+}
+
+/* first moment J = sum_j c_j h_j (E = J / (epshat + cs2 tau_h), Eq. 45) */
+static void first_moment(const orc_state* s, const double* h, int c, double* jx, double* jy) {
+    double ax = 0.0, ay = 0.0;
+    for (int j = 0; j < 9; ++j) {
+        ax += CX[j] * h[j * s->N + c];
+        ay += CY[j] * h[j * s->N + c];
+    }
+    *jx = ax;
+    *jy = ay;
+}
+
+/* Iterate until the relative increments of psi and of the first moment J between
+ * consecutive pseudo-iterations are both <= tol (checked every check_every
+ * iterations, before the collision of that iteration), or a fixed number of
+ * iterations.  Returns the number of collide+stream iterations applied. */
+static int poisson_solve(orc_state* s, double tol, int max_iter, int fixed, int check,
+                         double* res, int* converged) {
+    const int N = s->N;
+    int n = fixed > 0 ? fixed : max_iter;
+    if (check < 1) check = 1;
+    *res = -1.0;
+    *converged = fixed > 0;
+    for (int k = 1; k <= n; ++k) {
+        if (fixed <= 0 && k >= 2 && k % check == 0) {
+            double dp = 0.0, pp = 0.0, dj = 0.0, jj = 0.0;
+            for (int c = 0; c < N; ++c) {
+                double pk = psi_moment(s, s->h, c), jx, jy;
+                first_moment(s, s->h, c, &jx, &jy);
+                double d = pk - s->psi_prev[c];
+                double ex = jx - s->J_prev[c], ey = jy - s->J_prev[N + c];
+                dp += d * d;
+                pp += pk * pk;
+                dj += ex * ex + ey * ey;
+                jj += jx * jx + jy * jy;
+            }
+            double r1 = pp > 0.0 ? sqrt(dp) / sqrt(pp) : (dp > 0.0 ? INFINITY : 0.0);
+            double r2 = jj > 0.0 ? sqrt(dj) / sqrt(jj) : (dj > 0.0 ? INFINITY : 0.0);
+            double r = r1 > r2 ? r1 : r2;
+            *res = r;
+            if (r <= tol) { *converged = 1; return k - 1; }
+        }
+        if (fixed <= 0 && (k + 1) % check == 0)
+            for (int c = 0; c < N; ++c) {
+                s->psi_prev[c] = psi_moment(s, s->h, c);
+                first_moment(s, s->h, c, &s->J_prev[c], &s->J_prev[N + c]);
+            }
+        poisson_iteration(s);
+    }
+    return n;
+}
+
+/* psi and E = -grad psi (+ external field) from the current potential populations */
+static void potential_fields(orc_state* s) {
+    for (int c = 0; c < s->N; ++c) {
+        double gx, gy;
+        s->psi[c] = psi_moment(s, s->h, c);
+        gradpsi_moment(s, s->h, c, s->eps[c] - s->p.eps_ref, &gx, &gy);
+        s->E[c] = -gx + s->p.E_ext[0];
+        s->E[s->N + c] = -gy + s->p.E_ext[1];
+    }
+}
+
+/* ---------------- step pieces ---------------- */
+/* S2 + S3: properties and their stencils from the phi fields */
+static void properties_and_stencils(orc_state* s) {
+    const int nx = s->p.nx, ny = s->p.ny, N = s->N;
+    for (int c = 0; c < N; ++c) {
+        double ph[3];
+        phis(s, c, ph);
+        s->rho[c] = ph[0] * s->p.rho[0] + ph[1] * s->p.rho[1] + ph[2] * s->p.rho[2];   /* Eq. 29 */
+        s->sig[c] = ph[0] * s->p.sigma[0] + ph[1] * s->p.sigma[1] + ph[2] * s->p.sigma[2];
+        s->eps[c] = perm(&s->p, ph);                                                  /* Eq. 30 */
+    }
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            int c = y * nx + x;
+            for (int i = 0; i < 3; ++i) s->lap[i * N + c] = lap_at(s, s->phi + i * N, x, y);
+            grad_at(s, s->eps, x, y, &s->geps[c], &s->geps[N + c]);
+            grad_at(s, s->sig, x, y, &s->gsig[c], &s->gsig[N + c]);
+            grad_at(s, s->rho, x, y, &s->grho[c], &s->grho[N + c]);
+        }
+}
+
+/* S6: chemical potential, Eq. 20 with eps'(phi_i) = 6 eps_i phi_i (1 - phi_i) */
+static void chemical_potential(orc_state* s) {
+    const int N = s->N;
+    const double D = s->p.width_D;
+    for (int c = 0; c < N; ++c) {
+        double e2 = s->E[c] * s->E[c] + s->E[N + c] * s->E[N + c];
+        for (int i = 0; i < 3; ++i) {
+            double ph = s->phi[i * N + c];
+            double bulk = 24.0 / D * s->lam[i] * ph * (ph - 0.5) * (ph - 1.0);
+            double grad = 0.75 * D * s->lam[i] * s->lap[i * N + c];
+            double deps = 6.0 * s->p.eps[i] * ph * (1.0 - ph);
+            s->mu[i * N + c] = bulk - grad - 0.5 * deps * e2;
+        }
+    }
+}
+
+/* S12 ingredients: s_j(u), Eq. 40 */
+static double s_j(int j, double ux, double uy) {
+    double cu = CX[j] * ux + CY[j] * uy;
+    double uu = ux * ux + uy * uy;
+    return W[j] * (cu / CS2 + cu * cu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
+}
+
+static double tau_g_at(const orc_state* s, int c) {
+    if (!use_visc(&s->p)) return s->p.tau_g;
+    double eta = 0.0;
+    for (int i = 0; i < 3; ++i) eta += s->phi[i * s->N + c] * s->p.visc[i];
+    return 0.5 + eta / (s->rho[c] * CS2);           /* mu = rho cs2 (tau_g - 1/2) */
+}
+
+/* S9: u and p from the flow populations, Eq. 41 */
+static void flow_moments(orc_state* s) {
+    const int N = s->N;
+    for (int c = 0; c < N; ++c) {
+        double mx = 0.0, my = 0.0, g1 = 0.0;
+        for (int j = 0; j < 9; ++j) {
+            double gj = s->g[j * N + c];
+            mx += CX[j] * gj;
+            my += CY[j] * gj;
+            if (j) g1 += gj;
+        }
+        double ux = (mx + 0.5 * s->F[c]) / s->rho[c];
+        double uy = (my + 0.5 * s->F[N + c]) / s->rho[c];
+        double ugr = ux * s->grho[c] + uy * s->grho[N + c];
+        s->u[c] = ux;
+        s->u[N + c] = uy;
+        s->pr[c] = CS2 / (1.0 - W[0]) * (g1 + 0.5 * ugr + s->rho[c] * s_j(0, ux, uy));
+    }
+}
+
+/* S11-S13 collisions, then streaming (S14) */
+static void collide_and_stream(orc_state* s, int first) {
+    const int N = s->N;
+    const double tf = s->p.tau_f, tl = s->tau_l, m0 = s->m0;
+    const int cc = s->p.charge_convection;
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < N; ++c) {
+        double ph[3];
+        phis(s, c, ph);
+        double ux = s->u[c], uy = s->u[N + c], qc = s->q[c];
+        /* S10: d/dt(phi_i u) and d/dt(q u), first-order backward differences */
+        double dpu[3][2], dqu[2];
+        for (int i = 0; i < 3; ++i) {
+            dpu[i][0] = first ? 0.0 : ph[i] * ux - s->prev_phiu[(2 * i) * N + c];
+            dpu[i][1] = first ? 0.0 : ph[i] * uy - s->prev_phiu[(2 * i + 1) * N + c];
+        }
+        dqu[0] = first ? 0.0 : qc * ux - s->prev_qu[c];
+        dqu[1] = first ? 0.0 : qc * uy - s->prev_qu[N + c];
+
+        /* phase populations, Eq. 34-36, mobility Eq. 28 */
+        for (int i = 0; i < 3; ++i) {
+            double Yx = 0.0, Yy = 0.0;
+            double Mii = 0.0;
+            for (int k = 0; k < 3; ++k)
+                if (k != i) Mii += m0 * ph[i] * ph[k];
+            for (int k = 0; k < 3; ++k) {
+                double Mik = (k == i) ? (Mii - m0) : -m0 * ph[i] * ph[k];
+                Yx += Mik * s->gmu[(2 * k) * N + c];
+                Yy += Mik * s->gmu[(2 * k + 1) * N + c];
+            }
+            double Ax = dpu[i][0] / CS2 - Yx / m0;
+            double Ay = dpu[i][1] / CS2 - Yy / m0;
+            double mui = s->mu[i * N + c];
+            for (int j = 0; j < 9; ++j) {
+                double feq = (j == 0) ? ph[i] - (1.0 - W[0]) * mui
+                                      : W[j] * mui + W[j] * (CX[j] * ph[i] * ux + CY[j] * ph[i] * uy) / CS2;
+                double Fj = W[j] * (CX[j] * Ax + CY[j] * Ay);
+                double fj = s->f[(9 * i + j) * N + c];
+                s->fs[(9 * i + j) * N + c] = fj - (fj - feq) / tf + (1.0 - 1.0 / (2.0 * tf)) * Fj;
+            }
+        }
+
+        /* flow populations, Eq. 37-40 */
+        {
+            double tg = tau_g_at(s, c);
+            double rho = s->rho[c], p = s->pr[c];
+            double Fx = s->F[c], Fy = s->F[N + c];
+            double grx = s->grho[c], gry = s->grho[N + c];
+            double ugr = ux * grx + uy * gry;
+            for (int j = 0; j < 9; ++j) {
+                double geq = (j == 0) ? (W[0] - 1.0) * p / CS2 + rho * s_j(0, ux, uy)
+                                      : W[j] * p / CS2 + rho * s_j(j, ux, uy);
+                double cu = CX[j] * ux + CY[j] * uy;
+                double cgr = CX[j] * grx + CY[j] * gry;
+                double cF = CX[j] * Fx + CY[j] * Fy;
+                double G = W[j] * (ugr + cF / CS2 + (cu * cgr - CS2 * ugr) / CS2);
+                double gj = s->g[j * N + c];
+                s->gs[j * N + c] = gj - (gj - geq) / tg + (1.0 - 1.0 / (2.0 * tg)) * G;
+            }
+        }
+
+        /* charge populations, Eq. 48-50 */
+        {
+            double Rc = s->R[c];
+            for (int j = 0; j < 9; ++j) {
+                double cu = CX[j] * ux + CY[j] * uy;
+                double leq = cc ? W[j] * qc * (1.0 + cu / CS2) : W[j] * qc;
+                double Sj = (1.0 - 1.0 / (2.0 * tl)) * W[j] * Rc;
+                double Tj = cc ? (1.0 - 1.0 / (2.0 * tl)) * W[j] * (CX[j] * dqu[0] + CY[j] * dqu[1]) / CS2 : 0.0;
+                double lj = s->l[j * N + c];
+                s->ls[j * N + c] = lj - (lj - leq) / tl + Sj + Tj;
+            }
+        }
+    }
+    for (int i = 0; i < 3; ++i) stream(s, s->fs + 9 * i * N, s->f + 9 * i * N, 0);
+    stream(s, s->gs, s->g, 1);
+    stream(s, s->ls, s->l, 0);
+}
+
+static void one_step(orc_state* s) {
+    const int nx = s->p.nx, ny = s->p.ny, N = s->N;
+    const int first = s->step == 0;
+    /* S1: zeroth moments of the current populations */
+    for (int c = 0; c < N; ++c) {
+        for (int i = 0; i < 3; ++i) {
+            double a = 0.0;
+            for (int j = 0; j < 9; ++j) a += s->f[(9 * i + j) * N + c];
+            s->phi[i * N + c] = a;
+        }
+        double a = 0.0;
+        for (int j = 0; j < 9; ++j) a += s->l[j * N + c];
+        s->qt[c] = a;
+    }
+    /* S2, S3 */
+    properties_and_stencils(s);
+    /* S4: q = sum l + R/2 with R linear in q, field of the previous step */
+    for (int c = 0; c < N; ++c) {
+        double r = s->sig[c] / s->eps[c];
+        double Ex = s->E[c], Ey = s->E[N + c];
+        double src = r * (s->geps[c] * Ex + s->geps[N + c] * Ey) - (s->gsig[c] * Ex + s->gsig[N + c] * Ey);
+        s->q[c] = (s->qt[c] + 0.5 * src) / (1.0 + 0.5 * r);
+    }
+    /* S5: potential solve (warm-started from the current h) */
+    if (s->p.electric) {
+        int conv;
+        s->last_iters = poisson_solve(s, s->p.poisson_tol, s->p.poisson_max_iter, s->p.poisson_fixed_iter,
+                                      s->p.poisson_check_every, &s->last_res, &conv);
+        s->last_converged = conv;
+        potential_fields(s);
+    } else {
+        for (int c = 0; c < N; ++c) {
+            s->E[c] = s->p.E_ext[0];
+            s->E[N + c] = s->p.E_ext[1];
+            s->psi[c] = 0.0;
+        }
+    }
+    /* R^n of Eq. 47 with q^n and E^n */
+    for (int c = 0; c < N; ++c) {
+        double r = s->sig[c] / s->eps[c];
+        double Ex = s->E[c], Ey = s->E[N + c];
+        s->R[c] = -r * s->q[c] + r * (s->geps[c] * Ex + s->geps[N + c] * Ey) - (s->gsig[c] * Ex + s->gsig[N + c] * Ey);
+    }
+    /* S6, S7 */
+    chemical_potential(s);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            int c = y * nx + x;
+            for (int i = 0; i < 3; ++i) grad_at(s, s->mu + i * N, x, y, &s->gmu[(2 * i) * N + c], &s->gmu[(2 * i + 1) * N + c]);
+        }
+    /* S8: F = -sum phi_i grad mu_i + q E  (Eq. 27b) */
+    for (int c = 0; c < N; ++c) {
+        double Fx = 0.0, Fy = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            Fx -= s->phi[i * N + c] * s->gmu[(2 * i) * N + c];
+            Fy -= s->phi[i * N + c] * s->gmu[(2 * i + 1) * N + c];
+        }
+        s->F[c] = Fx + s->q[c] * s->E[c];
+        s->F[N + c] = Fy + s->q[c] * s->E[N + c];
+    }
+    /* S9 */
+    flow_moments(s);
+    /* S10-S14 */
+    collide_and_stream(s, first);
+    for (int c = 0; c < N; ++c) {
+        for (int i = 0; i < 3; ++i) {
+            s->prev_phiu[(2 * i) * N + c] = s->phi[i * N + c] * s->u[c];
+            s->prev_phiu[(2 * i + 1) * N + c] = s->phi[i * N + c] * s->u[N + c];
+        }
+        s->prev_qu[c] = s->q[c] * s->u[c];
+        s->prev_qu[N + c] = s->q[c] * s->u[N + c];
+    }
+    s->step += 1;
+}
+
+/* ---------------- public (test-only) API ---------------- */
+void orc_destroy(orc_state* s) {
+    if (!s) return;
+    double* bufs[] = {s->g, s->f, s->l, s->h, s->gs, s->fs, s->ls, s->hs, s->phi, s->qt, s->q, s->rho,
+                      s->sig, s->eps, s->lap, s->geps, s->gsig, s->grho, s->E, s->psi, s->mu, s->gmu,
+                      s->F, s->u, s->pr, s->R, s->prev_phiu, s->prev_qu, s->psi_prev, s->J_prev};
+    for (size_t k = 0; k < sizeof(bufs) / sizeof(bufs[0]); ++k) free(bufs[k]);
+    free(s);
+}
+
+/* status: 0 ok, -1 bad parameters, -2 out of memory */
+orc_state* orc_create(const orc_params* p, const double* phi_init, const double* u_init,
+                      const double* q_init, const double* noise, int* status) {
+    *status = -1;
+    if (p->nx < 2 || p->ny < 2 || p->bc_y < 0 || p->bc_y > 2) return NULL;
+    if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5) || !(p->width_D > 0) || !(p->eps_ref > 0) || !(p->alpha > 0))
+        return NULL;
+    for (int i = 0; i < 3; ++i)
+        if (!(p->rho[i] > 0) || !(p->eps[i] > 0) || p->sigma[i] < 0) return NULL;
+    double lam[3] = {p->gamma12 + p->gamma13 - p->gamma23,   /* Eq. 9 */
+                     p->gamma12 + p->gamma23 - p->gamma13,
+                     p->gamma13 + p->gamma23 - p->gamma12};
+    for (int i = 0; i < 3; ++i)
+        if (!(lam[i] > 0)) return NULL;
+    orc_state* s = (orc_state*)calloc(1, sizeof(orc_state));
+    *status = -2;
+    if (!s) return NULL;
+    s->p = *p;
+    const int N = p->nx * p->ny;
+    s->N = N;
+    for (int i = 0; i < 3; ++i) s->lam[i] = lam[i];
+    s->m0 = CS2 * (p->tau_f - 0.5);
+    s->tau_h = 0.5 + p->eps_ref / CS2;
+    s->tau_l = 0.5 + p->alpha / CS2;
+    s->g = alloc0(9 * (size_t)N); s->f = alloc0(27 * (size_t)N); s->l = alloc0(9 * (size_t)N); s->h = alloc0(9 * (size_t)N);
+    s->gs = alloc0(9 * (size_t)N); s->fs = alloc0(27 * (size_t)N); s->ls = alloc0(9 * (size_t)N); s->hs = alloc0(9 * (size_t)N);
+    s->phi = alloc0(3 * (size_t)N); s->qt = alloc0(N); s->q = alloc0(N); s->rho = alloc0(N); s->sig = alloc0(N);
+    s->eps = alloc0(N); s->lap = alloc0(3 * (size_t)N); s->geps = alloc0(2 * (size_t)N); s->gsig = alloc0(2 * (size_t)N);
+    s->grho = alloc0(2 * (size_t)N); s->E = alloc0(2 * (size_t)N); s->psi = alloc0(N); s->mu = alloc0(3 * (size_t)N);
+    s->gmu = alloc0(6 * (size_t)N); s->F = alloc0(2 * (size_t)N); s->u = alloc0(2 * (size_t)N); s->pr = alloc0(N);
+    s->R = alloc0(N); s->prev_phiu = alloc0(6 * (size_t)N); s->prev_qu = alloc0(2 * (size_t)N); s->psi_prev = alloc0(N);
+    s->J_prev = alloc0(2 * (size_t)N);
+    if (!s->J_prev) { orc_destroy(s); return NULL; }
+
+    memcpy(s->phi, phi_init, 3 * (size_t)N * sizeof(double));
+    if (u_init) memcpy(s->u, u_init, 2 * (size_t)N * sizeof(double));
+    if (q_init) memcpy(s->q, q_init, (size_t)N * sizeof(double));
+    properties_and_stencils(s);
+
+    /* potential populations start at equilibrium with the linear electrode profile */
+    for (int y = 0; y < p->ny; ++y)
+        for (int x = 0; x < p->nx; ++x) {
+            int c = y * p->nx + x;
+            double psi0 = p->bc_y == 2 ? p->V_bottom + (p->V_top - p->V_bottom) * (y + 0.5) / p->ny : 0.0;
+            for (int j = 0; j < 9; ++j) s->h[j * N + c] = (j == 0) ? (W[0] - 1.0) * psi0 : W[j] * psi0;
+        }
+    if (p->electric) {
+        int conv;
+        s->last_iters = poisson_solve(s, p->poisson_tol, p->poisson_max_iter, p->poisson_fixed_iter,
+                                      p->poisson_check_every, &s->last_res, &conv);
+        s->last_converged = conv;
+        potential_fields(s);
+    } else {
+        for (int c = 0; c < N; ++c) {
+            s->E[c] = p->E_ext[0];
+            s->E[N + c] = p->E_ext[1];
+        }
+    }
+    chemical_potential(s);
+    const int cc = p->charge_convection;
+    for (int c = 0; c < N; ++c) {
+        double ux = s->u[c], uy = s->u[N + c];
+        for (int i = 0; i < 3; ++i) {
+            double ph = s->phi[i * N + c], mui = s->mu[i * N + c];
+            for (int j = 0; j < 9; ++j)
+                s->f[(9 * i + j) * N + c] = (j == 0) ? ph - (1.0 - W[0]) * mui
+                                                     : W[j] * mui + W[j] * (CX[j] * ph * ux + CY[j] * ph * uy) / CS2;
+        }
+        for (int j = 0; j < 9; ++j) {
+            /* g_eq with p = 0 (Eq. 39) */
+            s->g[j * N + c] = s->rho[c] * s_j(j, ux, uy);
+            double cu = CX[j] * ux + CY[j] * uy;
+            s->l[j * N + c] = cc ? W[j] * s->q[c] * (1.0 + cu / CS2) : W[j] * s->q[c];
+        }
+    }
+    if (noise) {
+        for (size_t k = 0; k < 9 * (size_t)N; ++k) s->g[k] += noise[k];
+        for (size_t k = 0; k < 27 * (size_t)N; ++k) s->f[k] += noise[9 * (size_t)N + k];
+        for (size_t k = 0; k < 9 * (size_t)N; ++k) s->l[k] += noise[36 * (size_t)N + k];
+    }
+    s->step = 0;
+    *status = 0;
+    return s;
+}
+
+int orc_step(orc_state* s, int nsteps) {
+    for (int k = 0; k < nsteps; ++k) one_step(s);
+    return 0;
+}
+
+/* Solve the potential for the stored eps and a given charge field (or the stored
+ * q), updating h, psi and E.  Returns the iteration count. */
+int orc_solve_potential(orc_state* s, const double* q, double tol, int max_iter, int fixed, int check,
+                        double* res, int* converged) {
+    if (q) memcpy(s->q, q, (size_t)s->N * sizeof(double));
+    int it = poisson_solve(s, tol, max_iter, fixed, check, res, converged);
+    potential_fields(s);
+    return it;
+}
+
+int orc_get_field(const orc_state* s, int id, double* out) {
+    const int N = s->N;
+    const double* src = NULL;
+    switch (id) {
+        case F_PHI1: case F_PHI2: case F_PHI3: src = s->phi + (id - F_PHI1) * N; break;
+        case F_UX: src = s->u; break;
+        case F_UY: src = s->u + N; break;
+        case F_P: src = s->pr; break;
+        case F_Q: src = s->q; break;
+        case F_PSI:
+            for (int c = 0; c < N; ++c) out[c] = psi_moment(s, s->h, c);
+            return 0;
+        case F_EX: src = s->E; break;
+        case F_EY: src = s->E + N; break;
+        case F_MU1: case F_MU2: case F_MU3: src = s->mu + (id - F_MU1) * N; break;
+        case F_PHINOW1: case F_PHINOW2: case F_PHINOW3: {
+            int i = id - F_PHINOW1;
+            for (int c = 0; c < N; ++c) {
+                double a = 0.0;
+                for (int j = 0; j < 9; ++j) a += s->f[(9 * i + j) * N + c];
+                out[c] = a;
+            }
+            return 0;
+        }
+        case F_QTILDE:
+            for (int c = 0; c < N; ++c) {
+                double a = 0.0;
+                for (int j = 0; j < 9; ++j) a += s->l[j * N + c];
+                out[c] = a;
+            }
+            return 0;
+        default: break;
+    }
+    if (!src && id >= POP_BASE && id < POP_BASE + 54) {
+        int set = (id - POP_BASE) / 9, j = (id - POP_BASE) % 9;
+        const double* base = set == 0 ? s->g : set <= 3 ? s->f + 9 * (set - 1) * (size_t)N : set == 4 ? s->l : s->h;
+        src = base + j * N;
+    }
+    if (!src) return -1;
+    memcpy(out, src, (size_t)N * sizeof(double));
+    return 0;
+}
+
+/* Observables of the last completed step (Eq. 18 energy parts, per-phase mass,
+ * deformation factors).  out[0..2] mass, [3] charge, [4..7] F_phi F_E F_u F_q,
+ * [8] max|sum phi - 1|, [9] D_inner, [10] D_outer, [11] nonfinite count,
+ * [12] step, [13] last potential iterations, [14] last residual. */
+int orc_observables(const orc_state* s, double* out) {
+    const int nx = s->p.nx, ny = s->p.ny, N = s->N;
+    const double D = s->p.width_D;
+    double mass[3] = {0, 0, 0}, charge = 0, Fphi = 0, FE = 0, Fu = 0, Fq = 0, dev = 0, nonfin = 0;
+    double m[2][5] = {{0}}; /* sum chi, chi x, chi y, chi x^2, chi y^2 */
+    int ii = s->p.inner_phase - 1, im = s->p.matrix_phase - 1;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            int c = y * nx + x;
+            double ph[3], sum = 0.0;
+            phis(s, c, ph);
+            for (int i = 0; i < 3; ++i) {
+                double gx, gy;
+                mass[i] += ph[i];
+                sum += ph[i];
+                grad_at(s, s->phi + i * N, x, y, &gx, &gy);
+                Fphi += 6.0 / D * s->lam[i] * ph[i] * ph[i] * (1.0 - ph[i]) * (1.0 - ph[i])
+                      + 0.375 * D * s->lam[i] * (gx * gx + gy * gy);
+            }
+            dev = fmax(dev, fabs(sum - 1.0));
+            double eps = perm(&s->p, ph);
+            double Ex = s->E[c], Ey = s->E[N + c];
+            FE += 0.5 * eps * (Ex * Ex + Ey * Ey);                 /* |D|^2 / (2 eps) */
+            double rho = ph[0] * s->p.rho[0] + ph[1] * s->p.rho[1] + ph[2] * s->p.rho[2];
+            double ux = s->u[c], uy = s->u[N + c];
+            Fu += 0.5 * rho * (ux * ux + uy * uy);
+            double sg = ph[0] * s->p.sigma[0] + ph[1] * s->p.sigma[1] + ph[2] * s->p.sigma[2];
+            if (sg > 0) Fq += 0.5 * (s->p.alpha / sg) * s->q[c] * s->q[c];
+            charge += s->q[c];
+            double chis[2] = {ph[ii], 1.0 - ph[im]};
+            for (int k = 0; k < 2; ++k) {
+                m[k][0] += chis[k];
+                m[k][1] += chis[k] * x;
+                m[k][2] += chis[k] * y;
+                m[k][3] += chis[k] * x * x;
+                m[k][4] += chis[k] * y * y;
+            }
+            double vals[6] = {ph[0], ph[1], ph[2], ux, uy, s->q[c]};
+            for (int k = 0; k < 6; ++k)
+                if (!isfinite(vals[k])) nonfin += 1;
+        }
+    double Dk[2];
+    for (int k = 0; k < 2; ++k) {
+        double A = m[k][0];
+        if (!(A > 0)) { Dk[k] = 0.0; continue; }
+        double xc = m[k][1] / A, yc = m[k][2] / A;
+        double Ixx = m[k][3] / A - xc * xc, Iyy = m[k][4] / A - yc * yc;
+        double a = 2.0 * sqrt(fmax(Iyy, 0.0)), b = 2.0 * sqrt(fmax(Ixx, 0.0));
+        Dk[k] = (a + b) > 0 ? (a - b) / (a + b) : 0.0;   /* D = (r_par - r_perp)/(r_par + r_perp) */
+    }
+    out[0] = mass[0]; out[1] = mass[1]; out[2] = mass[2]; out[3] = charge;
+    out[4] = Fphi; out[5] = FE; out[6] = Fu; out[7] = Fq; out[8] = dev;
+    out[9] = Dk[0]; out[10] = Dk[1]; out[11] = nonfin; out[12] = (double)s->step;
+    out[13] = s->last_iters; out[14] = s->last_res;
+    return 0;
+}
+
+/* lattice constants (for the pins that check Eq. 31) */
+void orc_lattice(int* cx, int* cy, double* w, int* opp) {
+    for (int j = 0; j < 9; ++j) { cx[j] = CX[j]; cy[j] = CY[j]; w[j] = W[j]; opp[j] = OPP[j]; }
+}
+
+/* Eq. 33 stencils of a field on an nx*ny grid with the oracle's ghost rule */
+int orc_stencil(int nx, int ny, int bc_y, const double* chi, double* gx, double* gy, double* lap) {
+    orc_state t;
+    memset(&t, 0, sizeof t);
+    t.p.nx = nx; t.p.ny = ny; t.p.bc_y = bc_y; t.N = nx * ny;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            int c = y * nx + x;
+            grad_at(&t, chi, x, y, &gx[c], &gy[c]);
+            lap[c] = lap_at(&t, chi, x, y);
+        }
+    return 0;
+}
+
+int orc_last_poisson(const orc_state* s, int* iters, double* res, int* converged) {
+    *iters = s->last_iters; *res = s->last_res; *converged = s->last_converged;
+    return 0;
+}
+
+int64_t orc_step_count(const orc_state* s) { return s->step; }

@@ -1,0 +1,361 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a lattice
+identity, a closed-form solution, an exact discrete invariant, or a value the paper
+prints.  They are chosen so that a plausible slip anywhere in the oracle (a dropped
+term, a flipped sign, a wrong index or coefficient) fails at least one of them; the
+docstrings say which part of the scheme each one pins.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+CS2 = 1.0 / 3.0
+
+
+# --------------------------------------------------------------------------- lattice
+def test_d2q9_lattice_identities():
+    """Eq. 31: weights sum to 1, first moment vanishes, second moment is cs^2 I,
+    fourth moment is isotropic, opposite directions are exact negatives."""
+    cx, cy, w, opp = oracle.lattice()
+    assert np.isclose(w.sum(), 1.0, rtol=0, atol=1e-15)
+    assert abs((w * cx).sum()) < 1e-16 and abs((w * cy).sum()) < 1e-16
+    assert np.isclose((w * cx * cx).sum(), CS2, atol=1e-15)
+    assert np.isclose((w * cy * cy).sum(), CS2, atol=1e-15)
+    assert abs((w * cx * cy).sum()) < 1e-16
+    assert np.isclose((w * cx ** 4).sum(), 3 * CS2 ** 2, atol=1e-15)
+    assert np.isclose((w * cx ** 2 * cy ** 2).sum(), CS2 ** 2, atol=1e-15)
+    assert (cx[opp] == -cx).all() and (cy[opp] == -cy).all()
+    assert list(cx) == [0, 1, 0, -1, 0, 1, -1, -1, 1] and list(cy) == [0, 0, 1, 0, -1, 1, 1, -1, -1]
+
+
+# --------------------------------------------------------------------------- stencils
+def test_isotropic_stencils_exact_on_polynomials():
+    """Eq. 33: the gradient is exact for quadratics and the Laplacian for cubics
+    (interior cells, away from the periodic seam)."""
+    ny, nx = 24, 20
+    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    a = [0.3, -1.1, 0.7, 0.05, -0.02, 0.03, 0.004, -0.003, 0.002, 0.001]
+    quad = a[0] + a[1] * x + a[2] * y + a[3] * x * x + a[4] * x * y + a[5] * y * y
+    gx, gy, lap = oracle.stencil(quad, bc_y=0)
+    sl = (slice(2, -2), slice(2, -2))
+    assert np.allclose(gx[sl], (a[1] + 2 * a[3] * x + a[4] * y)[sl], rtol=0, atol=1e-12)
+    assert np.allclose(gy[sl], (a[2] + a[4] * x + 2 * a[5] * y)[sl], rtol=0, atol=1e-12)
+    cub = quad + a[6] * x ** 3 + a[7] * x * x * y + a[8] * x * y * y + a[9] * y ** 3
+    _, _, lap = oracle.stencil(cub, bc_y=0)
+    exact = 2 * a[3] + 2 * a[5] + 6 * a[6] * x + 2 * a[7] * y + 2 * a[8] * x + 6 * a[9] * y
+    assert np.allclose(lap[sl], exact[sl], rtol=0, atol=1e-11)
+
+
+def test_wall_ghosts_are_mirror_images():
+    """Half-way walls: a field mirrored about y = -1/2 has zero normal gradient
+    at the wall, so a field that is even about the wall reproduces the periodic
+    stencil of its even extension."""
+    ny, nx = 8, 6
+    rng = np.random.default_rng(1)
+    f = rng.standard_normal((ny, nx))
+    ext = np.concatenate([f[::-1], f], axis=0)          # rows -ny..ny-1, mirror about -1/2
+    ext = np.concatenate([ext, ext[::-1]], axis=0)      # periodic even extension, period 4 ny
+    gx_e, gy_e, lap_e = oracle.stencil(ext, bc_y=0)
+    gx, gy, lap = oracle.stencil(f, bc_y=1)
+    assert np.allclose(gx, gx_e[ny:2 * ny], atol=1e-14)
+    assert np.allclose(gy, gy_e[ny:2 * ny], atol=1e-14)
+    assert np.allclose(lap, lap_e[ny:2 * ny], atol=1e-14)
+
+
+# --------------------------------------------------------------------------- free energy
+TENS = {(1, 2): 1e-3, (1, 3): 8e-4, (2, 3): 6e-4}
+
+
+@pytest.mark.parametrize("pair", list(TENS))
+def test_flat_interface_energy_equals_surface_tension(pair):
+    """Eq. 7-9, 18: a flat i|j tanh interface of width D stores (lambda_i +
+    lambda_j)/2 = gamma_ij per unit length; the discrete value converges to it at
+    second order in 1/D.  Distinct tensions make a swapped lambda visible."""
+    i, j = pair
+    errs = []
+    for D in (4.0, 8.0):
+        p = W.params(nx=4, ny=96, bc_y=1, electric=0, gamma12=1e-3, gamma13=8e-4, gamma23=6e-4, width_D=D)
+        o = oracle.Oracle(p, W.flat_interface(4, 96, D, i, j))
+        errs.append(o.observables()["F_phi"] / 4 / TENS[pair] - 1.0)
+    assert abs(errs[0]) < 0.035 and abs(errs[1]) < 0.01
+    assert 3.0 < errs[0] / errs[1] < 5.0          # second-order convergence
+
+
+@pytest.mark.parametrize("pair", list(TENS))
+def test_chemical_potential_vanishes_on_equilibrium_profile(pair):
+    """Eq. 20: for the tanh profile (the 1-D minimiser) the bulk term
+    24/D lambda phi(phi-1/2)(phi-1) and -3/4 D lambda lap(phi) cancel; the
+    residual is the O(1/D^2) stencil error.  The absent phase has mu = 0."""
+    i, j = pair
+    lam = {1: 1.2e-3, 2: 8e-4, 3: 4e-4}
+    rel = []
+    for D in (4.0, 8.0):
+        p = W.params(nx=4, ny=96, bc_y=1, electric=0, gamma12=1e-3, gamma13=8e-4, gamma23=6e-4, width_D=D)
+        o = oracle.Oracle(p, W.flat_interface(4, 96, D, i, j))
+        scale = {k: lam[k] * 24.0 / D * (math.sqrt(3) / 18) for k in (1, 2, 3)}   # max |phi(phi-1/2)(phi-1)|
+        r = [np.abs(o.field(f"mu{k}")).max() / scale[k] for k in (1, 2, 3)]
+        k_absent = ({1, 2, 3} - {i, j}).pop()
+        assert r[k_absent - 1] == 0.0
+        rel.append(max(r))
+    assert rel[0] < 0.05 and rel[1] < 0.017
+    assert rel[0] / rel[1] > 2.5
+
+
+# --------------------------------------------------------------------------- phase field
+def test_reduction_consistency_absent_phase_stays_zero():
+    """Eq. 28 + the source of Eq. 36: with phase 3 absent, M_3k = 0 and mu_3 = 0,
+    so f^3 stays identically zero, with the field on."""
+    n = 32
+    p = W.params(nx=n, ny=n, bc_y=2, electric=1, V_top=0.01, poisson_check_every=5)
+    phi = W.compound_droplet(n, n, 0.0, 8.0, 4.0)  # r_in = 0: core absent
+    phi[1] += phi[2]
+    phi[2] = 0.0
+    o = oracle.Oracle(p, phi)
+    o.step(40)
+    assert np.abs(o.field("phinow3")).max() == 0.0
+    assert np.abs(o.field("phinow2")).max() > 0.9
+
+
+@pytest.mark.parametrize("bc_y", [0, 1, 2])
+def test_per_phase_mass_conserved_to_roundoff(bc_y):
+    """Sum_j F_j^i = 0, sum_j f^eq = phi_i, and bounce-back/periodic streaming move
+    populations without loss: every phase's total is conserved to round-off."""
+    cfg = W.config_static_compound(n=32)
+    p = dict(cfg["params"], bc_y=bc_y, electric=1 if bc_y == 2 else 0)
+    o = oracle.Oracle(p, cfg["phi"], noise=W.noise(32, 32, 1e-8))
+    o.step(1)
+    m0 = o.observables()
+    o.step(60)
+    m1 = o.observables()
+    for k in ("mass1", "mass2", "mass3"):
+        assert abs(m1[k] - m0[k]) < 1e-11 * 32 * 32
+
+
+# --------------------------------------------------------------------------- flow
+def test_couette_profile_exact():
+    """Eq. 37-41 with moving half-way walls: steady plane Couette flow is linear,
+    u(y) = U_b + (U_t - U_b)(y + 1/2)/ny.  The linear scheme reproduces it exactly;
+    the only deviation is the O(Ma^2) relative error of the quadratic equilibrium
+    (it falls 100x when the wall speeds fall 10x)."""
+    nx, ny = 4, 12
+    errs = []
+    for s in (1.0, 0.1):
+        Ub, Ut = -1e-3 * s, 2e-3 * s
+        p = W.params(nx=nx, ny=ny, bc_y=1, electric=0, u_wall_bottom=Ub, u_wall_top=Ut)
+        o = oracle.Oracle(p, W.single_phase(nx, ny, 1))
+        o.step(6000)
+        u = o.field("ux")[:, 0]
+        y = np.arange(ny)
+        exact = Ub + (Ut - Ub) * (y + 0.5) / ny
+        errs.append(np.abs(u - exact).max() / Ut)
+        assert np.abs(o.field("uy")).max() < 1e-8 * Ut
+    assert errs[0] < 1e-6
+    assert 90 < errs[0] / errs[1] < 110
+
+
+@pytest.mark.parametrize("visc", [None, 0.05])
+def test_shear_wave_decays_at_viscous_rate(visc):
+    """Eq. 37-41: a shear wave u_x = U sin(k y) decays as exp(-nu k^2 t) with
+    nu = cs^2 (tau_g - 1/2), or nu = mu/rho with the viscosity of Eq. 29."""
+    nx, ny, U = 4, 64, 1e-4
+    kw = dict(visc=(visc, visc, visc)) if visc else dict(tau_g=0.9)
+    nu = visc if visc else CS2 * (0.9 - 0.5)
+    p = W.params(nx=nx, ny=ny, bc_y=0, electric=0, **kw)
+    k = 2 * math.pi / ny
+    y = np.arange(ny, dtype=float)
+    u = np.zeros((2, ny, nx))
+    u[0] = (U * np.sin(k * y))[:, None]
+    o = oracle.Oracle(p, W.single_phase(nx, ny, 1), u=u)
+    amp = []
+    for t in (100, 600):
+        o.step(t - o.steps_done)
+        ux = o.field("ux")[:, 0]
+        amp.append((ux * np.sin(k * y)).sum() * 2 / ny)
+    rate = -math.log(amp[1] / amp[0]) / 500.0
+    assert abs(rate / (nu * k * k) - 1.0) < 2e-3
+
+
+# --------------------------------------------------------------------------- potential
+def _potential(p, phi, q=None, tol=1e-13, max_iter=200000):
+    o = oracle.Oracle(dict(p, poisson_tol=1e-30, poisson_max_iter=1, poisson_fixed_iter=1), phi)
+    it, res, conv = o.solve_potential(q=q, tol=tol, max_iter=max_iter, check=10)
+    assert conv
+    return o
+
+
+def test_potential_linear_between_electrodes():
+    """Eq. 42-45 with uniform permittivity and no charge: the potential between
+    electrodes at y = -1/2 (0) and ny - 1/2 (V) is linear, and E = -V/ny."""
+    nx, ny, V = 4, 16, 1.0
+    p = W.params(nx=nx, ny=ny, bc_y=2, electric=1, V_bottom=0.0, V_top=V, eps=(2.0, 2.0, 2.0), eps_ref=2.0)
+    o = _potential(p, W.single_phase(nx, ny, 1))
+    y = np.arange(ny)
+    assert np.allclose(o.field("psi")[:, 0], V * (y + 0.5) / ny, atol=1e-9)
+    assert np.allclose(o.field("ey"), -V / ny, atol=1e-9)
+
+
+def test_potential_uniform_charge_slab():
+    """Eq. 43 source term: a uniform charge q between grounded electrodes gives
+    E_y = -q (ny - 1 - 2y) / (2 eps) exactly (sign and scale of varpi_j q and of
+    Eq. 45), and psi = q (y + 1/2)(ny - 1/2 - y) / (2 eps) up to a uniform offset
+    left by the anti-bounce-back walls, which is O(dx^2): it falls 4x per refinement."""
+    rel = []
+    for ny in (24, 48):
+        nx, q0, e = 4, 1e-4, 2.0
+        p = W.params(nx=nx, ny=ny, bc_y=2, electric=1, eps=(e, e, e), eps_ref=e)
+        o = _potential(p, W.single_phase(nx, ny, 1), q=np.full((ny, nx), q0), tol=1e-12, max_iter=400000)
+        y = np.arange(ny)
+        exact = q0 * (y + 0.5) * (ny - 0.5 - y) / (2 * e)
+        ey_exact = -q0 * (ny - 1 - 2 * y) / (2 * e)
+        assert np.abs(o.field("ey")[:, 0] - ey_exact).max() < 1e-8 * np.abs(ey_exact).max()
+        d = o.field("psi")[:, 0] - exact
+        assert d.max() - d.min() < 1e-7 * exact.max()
+        rel.append(d.mean() / exact.max())
+    assert 3.9 < rel[0] / rel[1] < 4.1
+
+
+@pytest.mark.parametrize("eps_ref", [1.0, 4.0])
+def test_potential_layered_dielectric(eps_ref):
+    """Eq. 42-45 with a permittivity contrast 1:4 across a flat interface: the
+    steady flux eps dpsi/dy is uniform, so psi = V int dy/eps / int dy/eps.  Both
+    choices of the split constant converge to the same solution."""
+    nx, ny, D, V = 4, 64, 6.0, 1.0
+    p = W.params(nx=nx, ny=ny, bc_y=2, electric=1, V_top=V, eps=(1.0, 2.0, 4.0), eps_ref=eps_ref, width_D=D)
+    phi = W.flat_interface(nx, ny, D, 1, 3)
+    o = _potential(p, phi)
+    eps = (phi[0] ** 2 * (3 - 2 * phi[0]) * 1.0 + phi[2] ** 2 * (3 - 2 * phi[2]) * 4.0)[:, 0]
+    # fine quadrature of 1/eps with eps linearly interpolated between cell centres
+    yy = np.linspace(-0.5, ny - 0.5, 64 * ny + 1)
+    ef = np.interp(yy, np.arange(ny), eps)
+    inv = np.concatenate([[0.0], np.cumsum(0.5 * (1 / ef[1:] + 1 / ef[:-1]) * np.diff(yy))])
+    exact = np.interp(np.arange(ny), yy, V * inv / inv[-1])
+    psi = o.field("psi")[:, 0]
+    assert np.abs(psi - exact).max() < 3e-3 * V
+    flux = -o.field("ey")[:, 0] * eps
+    assert np.abs(flux / flux.mean() - 1).max() < 1e-2
+
+
+# --------------------------------------------------------------------------- charge
+def test_uniform_charge_relaxation_factor():
+    """Eq. 46-50 with the closed-form q = sum l + R/2: in a uniform medium
+    q^{n+1} = q^n (1 - k/2)/(1 + k/2) with k = sigma/eps, exactly."""
+    nx, ny = 4, 4
+    s, e = 0.3, 2.0
+    p = W.params(nx=nx, ny=ny, bc_y=0, electric=0, sigma=(s, s, s), eps=(e, e, e))
+    o = oracle.Oracle(p, W.single_phase(nx, ny, 1), q=np.full((ny, nx), 1e-3))
+    qs = []
+    for _ in range(6):
+        o.step(1)
+        qs.append(o.field("q")[0, 0])
+    k = s / e
+    ratio = np.array(qs[1:]) / np.array(qs[:-1])
+    assert np.allclose(ratio, (1 - k / 2) / (1 + k / 2), rtol=1e-13, atol=0)
+    assert np.isclose(qs[0], 1e-3 / (1 + k / 2), rtol=1e-14)
+
+
+def test_charge_diffusion_gaussian():
+    """Eq. 48 with R = 0 (no conductivity): a Gaussian charge blob keeps its total
+    and its variance grows by exactly 2 alpha per step (closed form, tau_l =
+    1/2 + alpha/cs^2)."""
+    nx = ny = 64
+    alpha, s0 = 0.1, 3.0
+    p = W.params(nx=nx, ny=ny, bc_y=0, electric=0, sigma=(0, 0, 0), alpha=alpha)
+    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    r2 = (x - 32) ** 2 + (y - 32) ** 2
+    q0 = 1e-3 * np.exp(-r2 / (2 * s0 * s0))
+    o = oracle.Oracle(p, W.single_phase(nx, ny, 1), q=q0)
+    var = []
+    for t in (20, 120):
+        o.step(t - o.steps_done)
+        q = o.field("q")
+        var.append((q * r2).sum() / q.sum() / 2)
+        assert abs(q.sum() - q0.sum()) < 1e-12
+    assert abs((var[1] - var[0]) / (2 * alpha * 100) - 1) < 2e-3
+
+
+# --------------------------------------------------------------------------- coupled
+def _laplace_jump(phi, p, steps, r_probe_in, r_probe_out):
+    o = oracle.Oracle(p, phi)
+    o.step(steps)
+    pr = o.field("p")
+    ny, nx = pr.shape
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    r = np.hypot(x - nx / 2, y - ny / 2)
+    return pr[r < r_probe_in].mean() - pr[r > r_probe_out].mean(), o
+
+
+def test_laplace_pressure_two_phase_drop():
+    """Capillary force of Eq. 27b through the pressure of Eq. 41: a 2-D drop of
+    radius R at rest carries the jump p_in - p_out = gamma/R (within 10% at R = 16,
+    D = 4)."""
+    n, R = 64, 16.0
+    p = W.params(nx=n, ny=n, bc_y=0, electric=0)
+    phi = W.compound_droplet(n, n, 0.0, R, 4.0)
+    phi[1] += phi[2]
+    phi[2] = 0.0
+    dp, o = _laplace_jump(phi, p, 3000, R - 6, R + 8)
+    assert abs(dp / (1e-3 / R) - 1) < 0.10
+    # parasitic currents stay far below the capillary velocity gamma / mu
+    umax = np.hypot(o.field("ux"), o.field("uy")).max()
+    assert umax < 1e-3 * 1e-3 / (1.0 * CS2 * 0.3)
+
+
+def test_laplace_pressure_compound_drop():
+    """Compound drop (core radius 8 in shell radius 16): the two jumps are
+    gamma_23/R_in and gamma_12/R_out, here 1.6e-4 and 6.25e-5 with distinct
+    tensions (within 12%)."""
+    n = 64
+    p = W.params(nx=n, ny=n, bc_y=0, electric=0, gamma12=1e-3, gamma13=1e-3, gamma23=1.28e-3)
+    phi = W.compound_droplet(n, n, 8.0, 16.0, 4.0)
+    o = oracle.Oracle(p, phi)
+    o.step(3000)
+    pr = o.field("p")
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    r = np.hypot(x - n / 2, y - n / 2)
+    p_in, p_shell, p_out = pr[r < 4].mean(), pr[(r > 11.5) & (r < 12.5)].mean(), pr[r > 24].mean()
+    assert abs((p_in - p_shell) / (1.28e-3 / 8) - 1) < 0.12
+    assert abs((p_shell - p_out) / (1e-3 / 16) - 1) < 0.12
+
+
+def test_free_energy_non_increasing_without_field():
+    """Eq. 18-25 (continuum dissipation): with no field, F_phi + F_u of a relaxing
+    elliptical drop does not increase (sampled every 50 steps after 200)."""
+    n = 48
+    y, x = np.meshgrid(np.arange(n, dtype=float), np.arange(n, dtype=float), indexing="ij")
+    r = np.sqrt(((x - 24) / 1.3) ** 2 + ((y - 24) / 0.8) ** 2)
+    drop = 0.5 + 0.5 * np.tanh(2 * (10 - r) / 4)
+    phi = np.stack([1 - drop, drop, 0 * drop])
+    o = oracle.Oracle(W.params(nx=n, ny=n, bc_y=0, electric=0), phi)
+    o.step(200)
+    vals = []
+    for _ in range(12):
+        ob = o.observables()
+        vals.append(ob["F_phi"] + ob["F_u"])
+        o.step(50)
+    d = np.diff(vals)
+    assert (d <= 1e-12 * vals[0]).all()
+    assert vals[-1] < vals[0]
+
+
+@pytest.mark.parametrize("eps_in", [4.0, 0.25])
+def test_perfect_dielectric_drop_elongates_along_field(eps_in):
+    """The electric term -1/2 eps'(phi)|E|^2 of Eq. 20 (no conductivity, no
+    charge): a perfect-dielectric drop stretches along the field whatever the
+    permittivity ratio (classical electrostriction result), so D > 0."""
+    n, R = 48, 10.0
+    E0 = 0.02
+    p = W.params(nx=n, ny=n, bc_y=2, electric=1, V_top=E0 * n, sigma=(0, 0, 0),
+                 eps=(1.0, eps_in, 1.0), eps_ref=max(1.0, eps_in), inner_phase=2,
+                 poisson_check_every=5, poisson_tol=1e-10)
+    phi = W.compound_droplet(n, n, 0.0, R, 4.0)
+    phi[1] += phi[2]
+    phi[2] = 0.0
+    o = oracle.Oracle(p, phi)
+    o.step(400)
+    D = o.observables()["D_inner"]
+    assert D > 1e-4

@@ -1,0 +1,188 @@
+"""Seeded synthetic workloads for the three-phase EHD lattice Boltzmann step.
+
+This module holds the inputs both implementations are fed with: parameter sets,
+initial phase fields and population noise.  It contains none of the method's
+update arithmetic -- only the initial conditions the paper prescribes for its
+benchmarks (the tanh profiles of Eq. 54 and Eq. 56) and seeded random numbers.
+
+Phase labels follow the workload definitions, not the paper's figures:
+  * compound droplet: phase 1 = matrix, phase 2 = shell, phase 3 = inner core;
+  * liquid lens:      phase 1 = upper fluid, phase 2 = lower fluid, phase 3 = lens.
+Arrays are C-ordered ``[..., ny, nx]`` float64, x fastest.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED = 20261202
+
+#: ordered parameter keys shared by both implementations (plain numbers only)
+PARAM_DEFAULTS = dict(
+    nx=64, ny=64,
+    bc_y=2,                      # 0 periodic, 1 walls, 2 walls carrying electrodes
+    electric=1,                  # 1: solve the potential every step; 0: E = E_ext
+    precision=0,                 # GPU only: 0 fp64, 1 fp32, 2 fp32 compute + fp16 store
+    rho=(1.0, 1.0, 1.0),
+    visc=(0.0, 0.0, 0.0),        # dynamic viscosity per phase; all <= 0 -> constant tau_g
+    tau_g=0.8,
+    gamma12=1e-3, gamma13=1e-3, gamma23=1e-3,
+    width_D=4.0,
+    tau_f=0.8,
+    eps=(1.0, 2.0, 4.0),
+    sigma=(1.0, 0.5, 0.25),
+    eps_ref=4.0,
+    alpha=0.1,
+    V_bottom=0.0, V_top=0.0,
+    E_ext=(0.0, 0.0),
+    u_wall_bottom=0.0, u_wall_top=0.0,
+    charge_convection=1,
+    inner_phase=3, matrix_phase=1,
+    poisson_tol=1e-8,
+    poisson_max_iter=20000,
+    poisson_check_every=10,
+    poisson_fixed_iter=0,
+)
+
+
+def params(**kw) -> dict:
+    p = dict(PARAM_DEFAULTS)
+    for k, v in kw.items():
+        if k not in p:
+            raise KeyError(f"unknown parameter {k!r}")
+        p[k] = v
+    return p
+
+
+def _grid(nx: int, ny: int):
+    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64),
+                       indexing="ij")
+    return x, y
+
+
+def compound_droplet(nx: int, ny: int, r_in: float, r_out: float, W: float,
+                     xc: float | None = None, yc: float | None = None) -> np.ndarray:
+    """Concentric compound drop, Eq. 54 with the workload labels:
+    phase 3 (core) radius r_in inside phase 2 (shell) radius r_out inside phase 1."""
+    x, y = _grid(nx, ny)
+    xc = nx / 2 if xc is None else xc
+    yc = ny / 2 if yc is None else yc
+    r = np.sqrt((x - xc) ** 2 + (y - yc) ** 2)
+    p3 = 0.5 + 0.5 * np.tanh(2.0 * (r_in - r) / W)
+    p2 = (1.0 - p3) * (0.5 + 0.5 * np.tanh(2.0 * (r_out - r) / W))
+    p1 = 1.0 - p2 - p3
+    return np.ascontiguousarray(np.stack([p1, p2, p3]))
+
+
+def liquid_lens(nx: int, ny: int, R: float, D: float, xc: float, yc: float) -> np.ndarray:
+    """Lens between two layers, Eq. 56 with the workload labels: phase 3 is the
+    circular lens, phase 1 the upper layer (clipped at 0), phase 2 the rest."""
+    x, y = _grid(nx, ny)
+    r = np.sqrt((x - xc) ** 2 + (y - yc) ** 2)
+    p3 = 0.5 + 0.5 * np.tanh(2.0 * (R - r) / D)
+    p1 = np.maximum(0.5 + 0.5 * np.tanh(2.0 * (y - yc) / D) - p3, 0.0)
+    p2 = 1.0 - p1 - p3
+    return np.ascontiguousarray(np.stack([p1, p2, p3]))
+
+
+def single_phase(nx: int, ny: int, phase: int = 1) -> np.ndarray:
+    phi = np.zeros((3, ny, nx))
+    phi[phase - 1] = 1.0
+    return phi
+
+
+def flat_interface(nx: int, ny: int, D: float, i: int, j: int, y0: float | None = None) -> np.ndarray:
+    """Phase i below, phase j above a flat tanh interface at height y0."""
+    _, y = _grid(nx, ny)
+    y0 = ny / 2 - 0.5 if y0 is None else y0
+    top = 0.5 + 0.5 * np.tanh(2.0 * (y - y0) / D)
+    phi = np.zeros((3, ny, nx))
+    phi[j - 1] = top
+    phi[i - 1] = 1.0 - top
+    return phi
+
+
+def noise(nx: int, ny: int, amp: float, seed: int = SEED) -> np.ndarray:
+    """Uniform population noise U(-amp, amp) for the sets (g, f1, f2, f3, l),
+    drawn in order set, direction, y, x; never added to the potential set."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-amp, amp, size=(5, 9, ny, nx))
+
+
+# ---------------------------------------------------------------------------
+# The five workloads.  Sizes and parameters are the stated ones; where a value is
+# left open, the reading used is the one listed in the design notes.
+# ---------------------------------------------------------------------------
+
+def config_static_compound(precision: int = 0, n: int = 64, field: bool = True, **kw):
+    """64x64 static compound drop (core radius 8, shell radius 16), electrodes at
+    the y walls with potential difference 0.01, noise 1e-8; 2000 steps."""
+    r_out = 16.0 * n / 64
+    r_in = 8.0 * n / 64
+    p = params(nx=n, ny=n, bc_y=2 if field else 1, electric=1 if field else 0,
+               precision=precision, V_bottom=0.0, V_top=0.01 if field else 0.0, **kw)
+    phi = compound_droplet(n, n, r_in, r_out, 4.0)
+    return dict(name=f"static_compound_{n}x{n}", params=p, phi=phi,
+                noise=noise(n, n, 1e-8), steps=2000)
+
+
+def config_lens(tensions=(1e-3, 1e-3, 1e-3), nx: int = 512, ny: int = 256, R: float = 40.0,
+                precision: int = 1, **kw):
+    """Liquid lens spreading on a flat interface between walls, no field; 20000 steps."""
+    g12, g13, g23 = tensions
+    p = params(nx=nx, ny=ny, bc_y=1, electric=0, precision=precision,
+               gamma12=g12, gamma13=g13, gamma23=g23, V_top=0.0, **kw)
+    phi = liquid_lens(nx, ny, R, 4.0, nx / 2, ny / 2)
+    return dict(name=f"lens_{nx}x{ny}", params=p, phi=phi, noise=None, steps=20000)
+
+
+def field_for_capillary(ca_e: float, gamma: float, eps_matrix: float, radius: float) -> float:
+    """Field magnitude from the electric capillary number of Eq. 51."""
+    return math.sqrt(ca_e * gamma / (eps_matrix * radius))
+
+
+def config_deformation(n: int = 4096, r_out: float = 600.0, r_in: float = 300.0,
+                       ca_e: float = 0.5, precision: int = 1, **kw):
+    """Compound drop deforming in a uniform field between electrodes (4096^2)."""
+    eps = (1.0, 2.0, 4.0)
+    E0 = field_for_capillary(ca_e, 1e-3, eps[0], r_out)
+    p = params(nx=n, ny=n, bc_y=2, electric=1, precision=precision, eps=eps,
+               sigma=(1.0, 0.5, 0.25), eps_ref=eps[2], V_bottom=0.0, V_top=E0 * n,
+               charge_convection=1, **kw)
+    phi = compound_droplet(n, n, r_in, r_out, 4.0)
+    return dict(name=f"deformation_{n}x{n}", params=p, phi=phi, noise=None, steps=5000, E0=E0)
+
+
+def config_batched_sweep(count: int = 256, seed: int = SEED):
+    """Parameter-sweep instances: side from {128,192,256,384,512}, Ca_E ~ U[0.1,1],
+    permittivity ratio inner/outer ~ U[0.5,4], conductivity ratio ~ U[0.25,2]."""
+    rng = np.random.default_rng(seed)
+    sides = rng.choice(np.array([128, 192, 256, 384, 512]), size=count)
+    ca = rng.uniform(0.1, 1.0, size=count)
+    s_ratio = rng.uniform(0.5, 4.0, size=count)
+    r_ratio = rng.uniform(0.25, 2.0, size=count)
+    out = []
+    for k in range(count):
+        n = int(sides[k])
+        e1, e3 = 1.0, float(s_ratio[k])
+        s1, s3 = 1.0, float(r_ratio[k])
+        e2, s2 = math.sqrt(e1 * e3), math.sqrt(s1 * s3)
+        r_out = 0.25 * n
+        E0 = field_for_capillary(float(ca[k]), 1e-3, e1, r_out)
+        p = params(nx=n, ny=n, bc_y=2, electric=1, precision=1, eps=(e1, e2, e3),
+                   sigma=(s1, s2, s3), eps_ref=max(e1, e2, e3), V_top=E0 * n)
+        out.append(dict(name=f"sweep_{k}", params=p,
+                        phi=None, shape=(n, n), r_out=r_out, r_in=0.5 * r_out, steps=3000))
+    return out
+
+
+def config_adjoint(n: int = 256, precision: int = 1, **kw):
+    """Compound drop under field plus shear (walls at -/+1e-3)."""
+    eps = (1.0, 2.0, 4.0)
+    E0 = field_for_capillary(0.5, 1e-3, eps[0], 64.0)
+    p = params(nx=n, ny=n, bc_y=2, electric=1, precision=precision, eps=eps,
+               sigma=(1.0, 0.5, 0.25), eps_ref=eps[2], V_top=E0 * n,
+               u_wall_bottom=-1e-3, u_wall_top=1e-3, **kw)
+    phi = compound_droplet(n, n, 32.0, 64.0, 4.0)
+    return dict(name=f"adjoint_{n}x{n}", params=p, phi=phi, noise=None, steps=4000, E0=E0)
