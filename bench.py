@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Throughput of the three-phase EHD lattice Boltzmann step on one B300.
+
+Workload: compound drop deforming under a uniform field on a 4096 x 4096
+lattice (outer radius 600, inner 300, electric capillary number 0.5,
+permittivity 1:2:4, conductivity 1:0.5:0.25, surface-charge convection on), the
+potential solved to a relative residual of 1e-8 every step.  A "step" is one full
+time step: moments, stencils and charge closure, the potential iterations until
+the residual test passes, and the fused chemical-potential/force/collide/stream
+pass.  Metric: MLUPS = cells x steps / second (all population sets updated per
+cell per step).  Inputs are synthetic (the stated initial condition, no dataset).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lb3e|reference]
+Under torchrun (N > 1) every rank steps its own replica (no data exchange: a
+single lattice does not shard without a halo exchange); value = all ranks' cell
+updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "MLUPS"
+# algorithmic bytes per cell (compulsory traffic, see the design notes)
+FUSED_BYTES = {0: 8 * 112, 1: 4 * 112, 2: 2 * 90 + 4 * 22}   # k_fused: 45 pops r+w, phi, q, E, d/dt state
+POISSON_BYTES = {0: 8 * 20, 1: 4 * 20, 2: 4 * 20}           # one pseudo-iteration: h 9 r + 9 w, eps, q
+STEP_BYTES = {0: 960, 1: 480, 2: 300}                        # whole step without the potential loop
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lb3e", choices=["lb3e", "reference"])
+    ap.add_argument("--precision", type=int, default=1, help="0 fp64, 1 fp32, 2 fp32 + fp16-stored populations")
+    ap.add_argument("--n", type=int, default=4096, help="lattice side (the stated workload is 4096)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
+    ap.add_argument("--cpu-sample", type=int, default=1024, help="side of the oracle's CPU sample lattice")
+    ap.add_argument("--cpu-iters", type=int, default=0, help="potential iterations per step in the CPU sample")
+    return ap.parse_args()
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted((ROOT / "paper_2608_05787_b300" / "csrc").glob("*")):
+        h.update(f.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, precision: int):
+    """DRAM bytes per cell from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    f = ROOT / "profiles" / "traffic.json"
+    if not f.exists():
+        return None
+    d = json.loads(f.read_text())
+    e = d.get(f"{kernel}:{precision}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return float(e["bytes_per_cell"])
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self):
+        self.f.flush()
+        rows = [r.split(",") for r in Path(self.f.name).read_text().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if len(r) > 5 + k and "Active" in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _oracle_sample(n: int, iters: int):
+    import oracle
+    import workloads as W
+    scale = n / 4096.0
+    cfg = W.config_deformation(n=n, r_out=600.0 * scale, r_in=300.0 * scale)
+    return oracle.Oracle(dict(cfg["params"], poisson_fixed_iter=iters), cfg["phi"])
+
+
+def cpu_baseline(args, iters_per_step: float):
+    """The oracle, as it stands, on the host cores: one time step of a bounded
+    sample of the workload (a cpu_sample^2 lattice with the geometry scaled, and
+    the potential iterations per step the GPU needed), after an untimed init."""
+    n = args.cpu_sample
+    it = args.cpu_iters or max(1, int(round(iters_per_step)))
+    o = _oracle_sample(n, it)
+    t0 = time.perf_counter()
+    o.step(1)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n * n / dt / 1e6, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"1 step of a {n}x{n} lattice of the same workload (radii scaled), "
+                      f"{it} potential iterations per step (the GPU's mean), init untimed",
+            "seconds": dt}
+
+
+def run_reference(args):
+    """The oracle timed on the host cores, each step a bounded sample of the
+    workload (see cpu_baseline); rank 0 only."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    n = min(args.cpu_sample, args.n)
+    iters = args.cpu_iters or 30
+    o = _oracle_sample(n, iters)
+    o.step(args.warmup)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.step(1)
+        times.append(time.perf_counter() - t0)
+    per_step = statistics.mean(times)
+    value = n * n / per_step / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (stated initial condition of the workload)",
+            "config": {"workload": f"compound drop deformation under field, {args.n}x{args.n}",
+                       "sample_side": n, "potential_iters_per_step": iters, "poisson": "fixed iterations"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} timed steps of a {n}x{n} lattice of the same workload "
+                                       f"(radii scaled), {iters} potential iterations per step"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_lb3e(args):
+    import torch
+    import paper_2608_05787_b300 as L
+    import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    prec = args.precision
+    cfg = W.config_deformation(n=args.n, r_out=600.0 * args.n / 4096, r_in=300.0 * args.n / 4096, precision=prec)
+    params = cfg["params"]
+    N = args.n * args.n
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        phi_dev = torch.from_numpy(cfg["phi"]).cuda()
+        t_init0 = time.perf_counter()
+        sim = L.Sim(params, phi_dev, stream=stream)
+        t_init = time.perf_counter() - t_init0
+        init_obs = sim.observables()
+        sim.step(args.warmup)
+        torch.cuda.synchronize()
+        sim.set_timing(True)
+        l0 = sim.launches
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(local) as clk:
+            ev0.record(stream)
+            sim.step(args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        launches = sim.launches - l0
+        kt = sim.kernel_times()
+        sim.set_timing(False)
+        obs = sim.observables()
+
+    t = ms / 1e3
+    if dist:
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    total_cells = N * args.steps * ws
+    value = total_cells / t / 1e6
+
+    hbm, peak_kind = peaks()
+    poisson_ms, poisson_n = kt["poisson"]
+    fused_ms, fused_n = kt["fused"]
+    iters_per_step = poisson_n / args.steps
+    kernels = {}
+    for name, (kms, kn) in kt.items():
+        if kn:
+            kernels[name] = {"launches": kn, "ms_total": kms, "share": kms / max(1e-12, sum(v[0] for v in kt.values()))}
+    k_gbs = {}
+    if fused_n:
+        k_gbs["fused"] = FUSED_BYTES[prec] * N / (fused_ms / fused_n / 1e3) / 1e9
+    if poisson_n:
+        k_gbs["poisson"] = POISSON_BYTES[prec] * N / (poisson_ms / poisson_n / 1e3) / 1e9
+    dominant = max(("fused", "poisson"), key=lambda k: kt[k][0])
+    per_cell = FUSED_BYTES[prec] if dominant == "fused" else POISSON_BYTES[prec]
+    traffic = profiled_traffic(dominant, prec)
+    roofline = {"bound": "hbm", "achieved": k_gbs.get(dominant), "peak": hbm, "unit": "GB/s",
+                "frac": (k_gbs.get(dominant) or 0) / hbm, "traffic": traffic * N if traffic else None,
+                "kernel": f"k_{dominant}", "peak_kind": f"{peak_kind} copy bandwidth",
+                "algorithmic_bytes_per_launch": per_cell * N,
+                "other_kernel_gbs": {k: v for k, v in k_gbs.items() if k != dominant}}
+
+    # end to end through the public API: pinned host initial fields, init (with its
+    # potential solve), K steps each followed by an observables read-back
+    e2e = None
+    if not args.no_e2e:
+        del sim
+        torch.cuda.empty_cache()
+        host_phi = torch.from_numpy(cfg["phi"]).pin_memory()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            s2 = L.Sim(params, host_phi, stream=stream)
+            for _ in range(args.steps):
+                s2.step(1)
+                s2.observables()
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        barrier()
+        if dist:
+            tt = torch.tensor([t_e2e], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+        e2e = {"value": total_cells / t_e2e / 1e6, "unit": METRIC,
+               "h2d_bytes_per_step": int(3 * N * 8 / args.steps),
+               "d2h_bytes_per_step": int(20 * 8 + 32 * math.ceil(iters_per_step / max(1, params["poisson_check_every"]))),
+               "includes": "init from pinned host fields (with its potential solve) + per-step observables read-back",
+               "seconds": t_e2e}
+        del s2
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        try:
+            cpu = cpu_baseline(args, iters_per_step)
+        except Exception as exc:  # a failed baseline must not hide the GPU line
+            cpu = {"value": None, "error": repr(exc)}
+
+    if rank == 0:
+        dtype = {0: "f64", 1: "f32", 2: "f32 (f16-stored populations)"}[prec]
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic (stated initial condition of the workload)",
+            "config": {"workload": f"compound drop deformation under field, {args.n}x{args.n}",
+                       "poisson_tol": params["poisson_tol"], "potential_iters_per_step": iters_per_step,
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single lattice",
+                       "l2": "working set (%.1f GB) exceeds the 126 MB L2; no flush needed" % (L.workspace_bytes(params) / 1e9),
+                       "init_seconds": t_init, "init_potential_iters": init_obs["poisson_iters"]},
+            "roofline": roofline,
+            "kernels": kernels,
+            "fused_mlups": N / (fused_ms / fused_n / 1e3) / 1e6 if fused_n else None,
+            "step_bytes_per_cell_no_potential": STEP_BYTES[prec],
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "observables": {k: obs[k] for k in ("D_inner", "D_outer", "max_sum_dev", "poisson_residual",
+                                                 "poisson_iters", "nonfinite")},
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_lb3e(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * lb3e.h -- C ABI of the B300 (sm_103a) three-phase electrohydrodynamic lattice
+ * Boltzmann step: Onsager-variational phase-field model of Liu, Qian, Xiong and
+ * Wang (three-phase dielectric fluid flows), D2Q9 discretisation of its Section 3.
+ *
+ * One time step (lb3e_step) is, in order:
+ *   zeroth moments of the phase and charge populations (phi_i, sum l);
+ *   property interpolation rho, sigma (Eq. 29) and eps (Eq. 30);
+ *   isotropic stencils of Eq. 33 and the closed-form charge q = sum l + R/2;
+ *   the pseudo-time LB potential solve of Eq. 42-45 (warm-started, to a residual);
+ *   the chemical potential of Eq. 20, the force -sum phi_i grad mu_i + q E (Eq. 27b);
+ *   flow moments (Eq. 41);
+ *   collision + streaming of the phase (Eq. 34-36), flow (Eq. 37-40) and
+ *   charge (Eq. 46-50) populations, with half-way walls and electrodes.
+ *
+ * Conventions for every entry point:
+ *   - Device memory is owned by the caller.  lb3e_workspace_bytes() says how much;
+ *     the caller allocates it (e.g. a torch tensor) and passes the pointer to
+ *     lb3e_init(); it must stay alive and untouched until lb3e_destroy().
+ *     The handle itself owns only host memory (and a small pinned host buffer).
+ *   - All work is issued on the stream given to lb3e_init() (a cudaStream_t passed
+ *     as void*; NULL = the legacy default stream).  Functions that return host
+ *     results synchronise that stream.
+ *   - Arrays are C-ordered [..][ny][nx] (x fastest), double precision, in lattice
+ *     units (dx = dt = 1).  Pointer arguments may be host or device memory
+ *     (unified addressing decides); they are read or written before return.
+ *   - Every function returns LB3E_OK (0) or a negative LB3E_ERR_* code; none
+ *     aborts or prints.  lb3e_status_string() describes a code.
+ */
+#ifndef LB3E_H
+#define LB3E_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LB3E_OK = 0,
+    LB3E_ERR_PARAM = -1,          /* invalid parameter (sizes, tau <= 1/2, lambda_i <= 0, ...) */
+    LB3E_ERR_WORKSPACE = -2,      /* workspace NULL, misaligned (256 B) or too small */
+    LB3E_ERR_CUDA = -3,           /* a CUDA call failed; the handle may be unusable */
+    LB3E_ERR_NOT_CONVERGED = -4,  /* potential solve hit max_iter above tol */
+    LB3E_ERR_FIELD = -5,          /* unknown field id */
+    LB3E_ERR_NULL = -6            /* NULL handle or output pointer */
+};
+
+/* Field ids for lb3e_get_field.  "Last step" fields hold the values computed
+ * during the most recent time step (after lb3e_init: the initial values). */
+enum {
+    LB3E_FIELD_PHI1 = 0,  /* phi_i used in the last step (moments at its start) */
+    LB3E_FIELD_PHI2 = 1,
+    LB3E_FIELD_PHI3 = 2,
+    LB3E_FIELD_UX = 3,    /* velocity of the last step, Eq. 41 */
+    LB3E_FIELD_UY = 4,
+    LB3E_FIELD_P = 5,     /* pressure of the last step, Eq. 41 */
+    LB3E_FIELD_Q = 6,     /* charge q = sum l + R/2 of the last step */
+    LB3E_FIELD_PSI = 7,   /* potential, Eq. 45, of the current h */
+    LB3E_FIELD_EX = 8,    /* E = -grad psi (+ E_ext) used in the last step */
+    LB3E_FIELD_EY = 9,
+    LB3E_FIELD_MU1 = 10,  /* chemical potentials (Eq. 20) of the last step */
+    LB3E_FIELD_MU2 = 11,
+    LB3E_FIELD_MU3 = 12,
+    LB3E_FIELD_PHINOW1 = 13, /* phi_i = sum_j f^i_j of the current populations */
+    LB3E_FIELD_PHINOW2 = 14,
+    LB3E_FIELD_PHINOW3 = 15,
+    LB3E_FIELD_QTILDE = 16,  /* sum_j l_j of the current populations */
+    LB3E_FIELD_POP = 100     /* + 9*set + j; sets 0 g, 1-3 f^1..f^3, 4 l, 5 h */
+};
+
+/* Model and run parameters.  Index i of the per-phase arrays is phase i+1. */
+typedef struct lb3e_params {
+    int32_t nx, ny;               /* lattice, cells; both >= 2; periodic in x */
+    int32_t bc_y;                 /* 0 periodic, 1 half-way walls, 2 walls with electrodes */
+    int32_t electric;             /* 1: solve the potential every step; 0: E = E_ext */
+    int32_t precision;            /* 0 fp64; 1 fp32; 2 fp32 compute, fp16-stored populations */
+    int32_t _pad0;
+    double rho[3];                /* phase densities, Eq. 29 */
+    double visc[3];               /* phase dynamic viscosities, Eq. 29; all <= 0: use tau_g */
+    double tau_g;                 /* flow relaxation time when visc is not given */
+    double gamma12, gamma13, gamma23; /* surface tensions; lambda_i from Eq. 9 must be > 0 */
+    double width_D;               /* interface width D, Eq. 7 */
+    double tau_f;                 /* phase relaxation time; m0 = cs^2 (tau_f - 1/2) */
+    double eps[3];                /* phase permittivities, Eq. 30 */
+    double sigma[3];              /* phase conductivities, Eq. 29 (>= 0) */
+    double eps_ref;               /* constant part of the permittivity split (Eq. 42); tau_h = 1/2 + eps_ref/cs^2 */
+    double alpha;                 /* charge diffusivity; tau_l = 1/2 + alpha/cs^2 (Eq. 49) */
+    double V_bottom, V_top;       /* electrode potentials at y = -1/2 and y = ny - 1/2 (bc_y = 2) */
+    double E_ext[2];              /* uniform field added to -grad psi */
+    double u_wall_bottom, u_wall_top; /* tangential wall speeds (bc_y >= 1) */
+    int32_t charge_convection;    /* 1: velocity terms of Eq. 49-50 on */
+    int32_t inner_phase;          /* 1-based phase whose indicator gives D_inner */
+    int32_t matrix_phase;         /* 1-based phase; indicator 1 - phi gives D_outer */
+    int32_t _pad1;
+    double poisson_tol;           /* stop when the relative increments of psi and of
+                                     sum_j c_j h_j between pseudo-iterations are <= tol */
+    int32_t poisson_max_iter;     /* iteration cap per solve */
+    int32_t poisson_check_every;  /* residual evaluated every this many iterations */
+    int32_t poisson_fixed_iter;   /* > 0: exactly this many iterations, no residual */
+    int32_t _pad2;
+} lb3e_params;
+
+typedef struct lb3e_observables_t {
+    double mass[3];          /* sum phi_i of the last step */
+    double charge;           /* sum q of the last step */
+    double free_energy[4];   /* Eq. 18 parts: phase (bulk + gradient), electric, kinetic, charge */
+    double max_sum_dev;      /* max |phi_1 + phi_2 + phi_3 - 1| */
+    double D_inner, D_outer; /* deformation factors from second moments of the indicators */
+    double poisson_residual; /* residual at the last check of the last solve (-1: none) */
+    int64_t nonfinite;       /* non-finite phi, u or q values */
+    int64_t step;            /* completed time steps */
+    int32_t poisson_iters;   /* iterations of the last solve */
+    int32_t poisson_converged;
+} lb3e_observables_t;
+
+typedef struct lb3e_handle lb3e_handle;
+
+/* Device bytes lb3e_init() needs for these parameters.  Errors: PARAM, NULL. */
+int lb3e_workspace_bytes(const lb3e_params* params, size_t* bytes);
+
+/* Validate params, lay out the workspace (256-byte aligned, >= the size above),
+ * build the initial state and solve the initial potential (with the initial
+ * charge).  Initial state: phi_i = phi_init ([3][ny][nx], required), u = u_init
+ * ([2][ny][nx] or NULL = 0), q = q_init ([ny][nx] or NULL = 0), p = 0; phase
+ * populations at equilibrium with mu_i of Eq. 20, flow at g_eq(p = 0, u), charge
+ * at l_eq(q, u); then pop_noise ([5][9][ny][nx] for sets g, f1, f2, f3, l, or
+ * NULL) is added.  Errors: PARAM, WORKSPACE, NULL, CUDA (a non-converged initial
+ * solve is not an error; see lb3e_observables). */
+int lb3e_init(const lb3e_params* params, void* workspace, size_t workspace_bytes,
+              const double* phi_init, const double* u_init, const double* q_init,
+              const double* pop_noise, void* stream, lb3e_handle** out);
+
+/* Advance nsteps time steps.  A potential solve that reaches poisson_max_iter
+ * does not stop the run; lb3e_observables() reports its iterations and
+ * residual.  Errors: NULL, PARAM (nsteps < 0), CUDA. */
+int lb3e_step(lb3e_handle* h, int32_t nsteps);
+
+/* Run the potential solve alone (Eq. 42-45) for the permittivity of the last
+ * step and the charge q (device or host [ny][nx], or NULL for the stored q),
+ * updating h, psi and E.  Returns NOT_CONVERGED if max_iter was reached.
+ * *iters and *residual (may be NULL) receive the iteration count and the last
+ * residual. */
+int lb3e_solve_potential(lb3e_handle* h, const double* q, double tol, int32_t max_iter,
+                         int32_t check_every, int32_t* iters, double* residual);
+
+/* Reductions (FP64) over the last step's fields.  Synchronises the stream. */
+int lb3e_observables(lb3e_handle* h, lb3e_observables_t* out);
+
+/* Copy one field (see the LB3E_FIELD_* ids) as doubles into dst ([ny][nx],
+ * host or device).  Synchronises the stream.  Errors: NULL, FIELD, CUDA. */
+int lb3e_get_field(lb3e_handle* h, int32_t field_id, double* dst);
+
+/* Size of a full state snapshot (populations, potential populations, fields,
+ * d/dt history, step counter) and save/load to caller memory (host or device). */
+int lb3e_state_bytes(const lb3e_handle* h, size_t* bytes);
+int lb3e_save_state(lb3e_handle* h, void* dst);
+int lb3e_load_state(lb3e_handle* h, const void* src);
+
+/* Number of kernel launches issued since lb3e_init (for launch accounting). */
+int64_t lb3e_launch_count(const lb3e_handle* h);
+
+/* Kernel timing with CUDA events recorded on the simulation's stream around each
+ * launch (off by default; costs two event records per launch).  Enabling or
+ * disabling clears the totals. */
+int lb3e_set_timing(lb3e_handle* h, int32_t enable);
+
+/* Kernel classes reported by lb3e_kernel_times. */
+enum {
+    LB3E_KC_MOMENTS = 0,   /* zeroth moments of the phase and charge populations */
+    LB3E_KC_PROLOGUE = 1,  /* properties, stencils, closed-form charge */
+    LB3E_KC_POISSON = 2,   /* one pseudo-iteration of the potential populations */
+    LB3E_KC_REDUCE = 3,    /* FP64 reductions (residual, observables) */
+    LB3E_KC_FIELDS = 4,    /* psi and E from the potential populations */
+    LB3E_KC_FUSED = 5,     /* fused chemical potential, force, collide and stream */
+    LB3E_KC_OTHER = 6,     /* initialisation and conversions */
+    LB3E_KC_COUNT = 7
+};
+
+/* Synchronise the stream and return, per kernel class, the summed event time in
+ * milliseconds (ms[LB3E_KC_COUNT]) and the number of timed launches
+ * (launches[LB3E_KC_COUNT]) since the last call; the totals are then cleared. */
+int lb3e_kernel_times(lb3e_handle* h, double* ms, int64_t* launches);
+
+/* Release the host-side handle (the workspace stays the caller's). */
+void lb3e_destroy(lb3e_handle* h);
+
+/* Static description of a status code. */
+const char* lb3e_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LB3E_H */

@@ -1,0 +1,240 @@
+"""Python binding of liblb3e: the B300 three-phase EHD lattice Boltzmann step.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+``csrc/`` behind the C ABI of ``include/lb3e.h``.  PyTorch supplies the device
+workspace and the stream.  There is no CPU fallback: if the library or a CUDA
+device is missing, constructing a simulation raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+LIB_PATH = _HERE / "liblb3e.so"
+
+FIELDS = dict(phi1=0, phi2=1, phi3=2, ux=3, uy=4, p=5, q=6, psi=7, ex=8, ey=9,
+              mu1=10, mu2=11, mu3=12, phinow1=13, phinow2=14, phinow3=15, qtilde=16)
+SETS = dict(g=0, f1=1, f2=2, f3=3, l=4, h=5)
+POP_BASE = 100
+PRECISIONS = {0: "f64", 1: "f32", 2: "f32-compute/f16-store"}
+
+KERNEL_CLASSES = ("moments", "prologue", "poisson", "reduce", "fields", "fused", "other")
+
+
+class Params(C.Structure):
+    """Mirror of ``lb3e_params`` (include/lb3e.h)."""
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("bc_y", C.c_int32), ("electric", C.c_int32),
+        ("precision", C.c_int32), ("_pad0", C.c_int32),
+        ("rho", C.c_double * 3), ("visc", C.c_double * 3), ("tau_g", C.c_double),
+        ("gamma12", C.c_double), ("gamma13", C.c_double), ("gamma23", C.c_double),
+        ("width_D", C.c_double), ("tau_f", C.c_double),
+        ("eps", C.c_double * 3), ("sigma", C.c_double * 3), ("eps_ref", C.c_double),
+        ("alpha", C.c_double), ("V_bottom", C.c_double), ("V_top", C.c_double),
+        ("E_ext", C.c_double * 2), ("u_wall_bottom", C.c_double), ("u_wall_top", C.c_double),
+        ("charge_convection", C.c_int32), ("inner_phase", C.c_int32), ("matrix_phase", C.c_int32),
+        ("_pad1", C.c_int32),
+        ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int32),
+        ("poisson_check_every", C.c_int32), ("poisson_fixed_iter", C.c_int32), ("_pad2", C.c_int32),
+    ]
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "Params":
+        s = cls()
+        for name, ctype in cls._fields_:
+            if name.startswith("_pad"):
+                continue
+            v = d[name]
+            if hasattr(ctype, "_length_"):
+                getattr(s, name)[:] = [float(a) for a in v]
+            else:
+                setattr(s, name, v)
+        return s
+
+
+class Observables(C.Structure):
+    """Mirror of ``lb3e_observables_t``."""
+    _fields_ = [
+        ("mass", C.c_double * 3), ("charge", C.c_double), ("free_energy", C.c_double * 4),
+        ("max_sum_dev", C.c_double), ("D_inner", C.c_double), ("D_outer", C.c_double),
+        ("poisson_residual", C.c_double), ("nonfinite", C.c_int64), ("step", C.c_int64),
+        ("poisson_iters", C.c_int32), ("poisson_converged", C.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        fe = list(self.free_energy)
+        return dict(mass1=self.mass[0], mass2=self.mass[1], mass3=self.mass[2], charge=self.charge,
+                    F_phi=fe[0], F_E=fe[1], F_u=fe[2], F_q=fe[3], max_sum_dev=self.max_sum_dev,
+                    D_inner=self.D_inner, D_outer=self.D_outer, nonfinite=self.nonfinite,
+                    step=self.step, poisson_iters=self.poisson_iters,
+                    poisson_residual=self.poisson_residual,
+                    poisson_converged=bool(self.poisson_converged))
+
+
+class LB3EError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn} failed: {status_string(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load liblb3e.so (built in-tree by ``build.py``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"{LIB_PATH} is missing: run `python -m paper_2608_05787_b300.build`")
+        L = C.CDLL(str(LIB_PATH))
+        vp, dp = C.c_void_p, C.POINTER(C.c_double)
+        L.lb3e_workspace_bytes.argtypes = [C.POINTER(Params), C.POINTER(C.c_size_t)]
+        L.lb3e_init.argtypes = [C.POINTER(Params), vp, C.c_size_t, vp, vp, vp, vp, vp, C.POINTER(vp)]
+        L.lb3e_step.argtypes = [vp, C.c_int32]
+        L.lb3e_solve_potential.argtypes = [vp, vp, C.c_double, C.c_int32, C.c_int32,
+                                           C.POINTER(C.c_int32), dp]
+        L.lb3e_observables.argtypes = [vp, C.POINTER(Observables)]
+        L.lb3e_get_field.argtypes = [vp, C.c_int32, vp]
+        L.lb3e_state_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.lb3e_save_state.argtypes = [vp, vp]
+        L.lb3e_load_state.argtypes = [vp, vp]
+        L.lb3e_launch_count.restype = C.c_int64
+        L.lb3e_launch_count.argtypes = [vp]
+        L.lb3e_set_timing.argtypes = [vp, C.c_int32]
+        L.lb3e_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64)]
+        L.lb3e_destroy.argtypes = [vp]
+        L.lb3e_destroy.restype = None
+        L.lb3e_status_string.restype = C.c_char_p
+        L.lb3e_status_string.argtypes = [C.c_int]
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().lb3e_status_string(code).decode()
+
+
+def _check(fn: str, code: int):
+    if code != 0:
+        raise LB3EError(fn, code)
+
+
+def workspace_bytes(params: dict) -> int:
+    n = C.c_size_t(0)
+    _check("lb3e_workspace_bytes", lib().lb3e_workspace_bytes(C.byref(Params.from_dict(params)), C.byref(n)))
+    return n.value
+
+
+def _addr(a):
+    """Address of a host numpy array or a CUDA torch tensor (float64, contiguous)."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        return a.ctypes.data, a
+    import torch
+    if isinstance(a, torch.Tensor):
+        a = a.contiguous().to(torch.float64)
+        return a.data_ptr(), a
+    raise TypeError(type(a))
+
+
+class Sim:
+    """One lattice, stepped on the GPU through the C ABI.
+
+    ``params`` is a plain dict with the keys of ``lb3e_params``; initial arrays
+    may be host numpy arrays or CUDA tensors (float64, ``[.., ny, nx]``).
+    """
+
+    def __init__(self, params: dict, phi, u=None, q=None, noise=None, stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("lb3e needs a CUDA device (there is no CPU fallback)")
+        self.params = dict(params)
+        self.nx, self.ny = int(params["nx"]), int(params["ny"])
+        self.device = torch.device(device or "cuda")
+        self._p = Params.from_dict(self.params)
+        nbytes = workspace_bytes(self.params)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        keep = [_addr(a) for a in (phi, u, q, noise)]
+        h = C.c_void_p(None)
+        _check("lb3e_init", lib().lb3e_init(C.byref(self._p), self.workspace.data_ptr(), nbytes,
+                                            *(k[0] for k in keep), self.stream.cuda_stream, C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().lb3e_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1) -> "Sim":
+        _check("lb3e_step", lib().lb3e_step(self._h, int(n)))
+        return self
+
+    def observables(self) -> dict:
+        o = Observables()
+        _check("lb3e_observables", lib().lb3e_observables(self._h, C.byref(o)))
+        return o.as_dict()
+
+    def field(self, name: str, out=None):
+        """Field as a host float64 array (or written into ``out``, a CUDA tensor)."""
+        fid = FIELDS[name]
+        return self._get(fid, out)
+
+    def pop(self, set_name: str, j: int, out=None):
+        return self._get(POP_BASE + 9 * SETS[set_name] + j, out)
+
+    def _get(self, fid: int, out):
+        if out is None:
+            arr = np.empty((self.ny, self.nx))
+            _check("lb3e_get_field", lib().lb3e_get_field(self._h, fid, arr.ctypes.data))
+            return arr
+        _check("lb3e_get_field", lib().lb3e_get_field(self._h, fid, out.data_ptr()))
+        return out
+
+    def solve_potential(self, q=None, tol=1e-8, max_iter=100000, check=10):
+        addr, _keep = _addr(q)
+        it, res = C.c_int32(0), C.c_double(0)
+        rc = lib().lb3e_solve_potential(self._h, addr, tol, max_iter, check, C.byref(it), C.byref(res))
+        if rc not in (0, -4):
+            _check("lb3e_solve_potential", rc)
+        return it.value, res.value, rc == 0
+
+    def state_bytes(self) -> int:
+        n = C.c_size_t(0)
+        _check("lb3e_state_bytes", lib().lb3e_state_bytes(self._h, C.byref(n)))
+        return n.value
+
+    def save_state(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.device)
+        _check("lb3e_save_state", lib().lb3e_save_state(self._h, out.data_ptr()))
+        return out
+
+    def load_state(self, src):
+        _check("lb3e_load_state", lib().lb3e_load_state(self._h, src.data_ptr()))
+
+    def set_timing(self, enable: bool):
+        _check("lb3e_set_timing", lib().lb3e_set_timing(self._h, int(bool(enable))))
+
+    def kernel_times(self) -> dict:
+        """{class: (total ms, launches)} since the last call (synchronises)."""
+        ms = (C.c_double * len(KERNEL_CLASSES))()
+        n = (C.c_int64 * len(KERNEL_CLASSES))()
+        _check("lb3e_kernel_times", lib().lb3e_kernel_times(self._h, ms, n))
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    @property
+    def launches(self) -> int:
+        return int(lib().lb3e_launch_count(self._h))

@@ -1,0 +1,166 @@
+// lb3e_api.cpp -- the extern "C" entry points declared in include/lb3e.h.
+// Parameter validation, precision dispatch and status mapping; no kernels here.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <new>
+
+#include "lb3e_internal.h"
+
+struct lb3e_handle {
+    lb3e::SimBase* sim;
+    lb3e_params params;
+};
+
+namespace {
+
+int validate(const lb3e_params* p) {
+    if (!p) return LB3E_ERR_NULL;
+    if (p->nx < 2 || p->ny < 2) return LB3E_ERR_PARAM;
+    if ((int64_t)p->nx * p->ny > (int64_t)1 << 30) return LB3E_ERR_PARAM;
+    if (p->bc_y < 0 || p->bc_y > 2 || p->precision < 0 || p->precision > 2) return LB3E_ERR_PARAM;
+    if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5) || !(p->width_D > 0) || !(p->eps_ref > 0) || !(p->alpha > 0))
+        return LB3E_ERR_PARAM;
+    for (int i = 0; i < 3; ++i)
+        if (!(p->rho[i] > 0) || !(p->eps[i] > 0) || !(p->sigma[i] >= 0) || !std::isfinite(p->visc[i]))
+            return LB3E_ERR_PARAM;
+    const double lam[3] = {p->gamma12 + p->gamma13 - p->gamma23, p->gamma12 + p->gamma23 - p->gamma13,
+                           p->gamma13 + p->gamma23 - p->gamma12};
+    for (double l : lam)
+        if (!(l > 0)) return LB3E_ERR_PARAM;
+    if (p->inner_phase < 1 || p->inner_phase > 3 || p->matrix_phase < 1 || p->matrix_phase > 3) return LB3E_ERR_PARAM;
+    if (p->poisson_max_iter < 0 || p->poisson_fixed_iter < 0) return LB3E_ERR_PARAM;
+    const double vals[] = {p->V_bottom, p->V_top, p->E_ext[0], p->E_ext[1], p->u_wall_bottom, p->u_wall_top,
+                           p->poisson_tol};
+    for (double v : vals)
+        if (!std::isfinite(v)) return LB3E_ERR_PARAM;
+    return LB3E_OK;
+}
+
+size_t ws_bytes(const lb3e_params& p) {
+    switch (p.precision) {
+        case 0: return lb3e::workspace_bytes_f64(p);
+        case 1: return lb3e::workspace_bytes_f32(p);
+        default: return lb3e::workspace_bytes_f16s(p);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb3e_workspace_bytes(const lb3e_params* params, size_t* bytes) {
+    if (!bytes) return LB3E_ERR_NULL;
+    TRY(validate(params));
+    *bytes = ws_bytes(*params);
+    return LB3E_OK;
+}
+
+int lb3e_init(const lb3e_params* params, void* workspace, size_t workspace_bytes, const double* phi_init,
+              const double* u_init, const double* q_init, const double* pop_noise, void* stream,
+              lb3e_handle** out) {
+    if (!out || !phi_init) return LB3E_ERR_NULL;
+    *out = nullptr;
+    TRY(validate(params));
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0 || workspace_bytes < ws_bytes(*params))
+        return LB3E_ERR_WORKSPACE;
+    lb3e::SimBase* sim = nullptr;
+    switch (params->precision) {
+        case 0: sim = lb3e::make_sim_f64(*params, workspace, stream); break;
+        case 1: sim = lb3e::make_sim_f32(*params, workspace, stream); break;
+        default: sim = lb3e::make_sim_f16s(*params, workspace, stream); break;
+    }
+    if (!sim) return LB3E_ERR_CUDA;
+    const int rc = sim->init(phi_init, u_init, q_init, pop_noise);
+    if (rc != LB3E_OK) {
+        delete sim;
+        return rc;
+    }
+    lb3e_handle* h = new (std::nothrow) lb3e_handle{sim, *params};
+    if (!h) {
+        delete sim;
+        return LB3E_ERR_CUDA;
+    }
+    *out = h;
+    return LB3E_OK;
+}
+
+int lb3e_step(lb3e_handle* h, int32_t nsteps) {
+    if (!h) return LB3E_ERR_NULL;
+    if (nsteps < 0) return LB3E_ERR_PARAM;
+    return h->sim->step(nsteps);
+}
+
+int lb3e_solve_potential(lb3e_handle* h, const double* q, double tol, int32_t max_iter, int32_t check_every,
+                         int32_t* iters, double* residual) {
+    if (!h) return LB3E_ERR_NULL;
+    if (max_iter < 0 || !std::isfinite(tol)) return LB3E_ERR_PARAM;
+    int it = 0;
+    double res = -1.0;
+    const int rc = h->sim->solve_potential(q, tol, max_iter, check_every, &it, &res);
+    if (iters) *iters = it;
+    if (residual) *residual = res;
+    return rc;
+}
+
+int lb3e_observables(lb3e_handle* h, lb3e_observables_t* out) {
+    if (!h || !out) return LB3E_ERR_NULL;
+    return h->sim->observables(out);
+}
+
+int lb3e_get_field(lb3e_handle* h, int32_t field_id, double* dst) {
+    if (!h || !dst) return LB3E_ERR_NULL;
+    return h->sim->get_field(field_id, dst);
+}
+
+int lb3e_state_bytes(const lb3e_handle* h, size_t* bytes) {
+    if (!h || !bytes) return LB3E_ERR_NULL;
+    *bytes = h->sim->state_bytes();
+    return LB3E_OK;
+}
+
+int lb3e_save_state(lb3e_handle* h, void* dst) {
+    if (!h || !dst) return LB3E_ERR_NULL;
+    return h->sim->save(dst);
+}
+
+int lb3e_load_state(lb3e_handle* h, const void* src) {
+    if (!h || !src) return LB3E_ERR_NULL;
+    return h->sim->load(src);
+}
+
+int64_t lb3e_launch_count(const lb3e_handle* h) { return h ? h->sim->launches : 0; }
+
+int lb3e_set_timing(lb3e_handle* h, int32_t enable) {
+    if (!h) return LB3E_ERR_NULL;
+    TRY(h->sim->kernel_times(nullptr, nullptr));
+    h->sim->timer.enabled = enable != 0;
+    return LB3E_OK;
+}
+
+int lb3e_kernel_times(lb3e_handle* h, double* ms, int64_t* launches) {
+    if (!h || !ms || !launches) return LB3E_ERR_NULL;
+    return h->sim->kernel_times(ms, launches);
+}
+
+void lb3e_destroy(lb3e_handle* h) {
+    if (!h) return;
+    delete h->sim;
+    delete h;
+}
+
+const char* lb3e_status_string(int status) {
+    switch (status) {
+        case LB3E_OK: return "ok";
+        case LB3E_ERR_PARAM: return "invalid parameter";
+        case LB3E_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case LB3E_ERR_CUDA: return "CUDA error";
+        case LB3E_ERR_NOT_CONVERGED: return "potential solve did not reach the tolerance";
+        case LB3E_ERR_FIELD: return "unknown field id";
+        case LB3E_ERR_NULL: return "NULL handle or pointer";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// lb3e_internal.h -- pieces shared by the precision-specific translation units
+// and the C ABI layer (host side only).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/lb3e.h"
+
+#define TRY(expr)                         \
+    do {                                  \
+        int _rc = (expr);                 \
+        if (_rc != LB3E_OK) return _rc;   \
+    } while (0)
+
+namespace lb3e {
+
+struct DevParams;
+
+// kernel classes for the timing facility (lb3e_kernel_times)
+enum KernelClass { KC_MOMENTS = 0, KC_PROLOGUE, KC_POISSON, KC_REDUCE, KC_FIELDS, KC_FUSED, KC_OTHER, KC_COUNT };
+
+// CUDA-event timing of kernel launches on the simulation's stream (off by default)
+struct LaunchTimer {
+    bool enabled = false;
+    struct Rec { int cls; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    double ms[KC_COUNT] = {0};
+    int64_t n[KC_COUNT] = {0};
+    cudaEvent_t take() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void begin(cudaStream_t s, int cls) {
+        if (!enabled) return;
+        Rec r{cls, take(), take()};
+        cudaEventRecord(r.a, s);
+        recs.push_back(r);
+    }
+    void end(cudaStream_t s) {
+        if (!enabled || recs.empty()) return;
+        cudaEventRecord(recs.back().b, s);
+    }
+    // fold recorded pairs into the totals (the stream must be synchronised)
+    void collect() {
+        for (auto& r : recs) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) { ms[r.cls] += t; n[r.cls] += 1; }
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        recs.clear();
+    }
+    ~LaunchTimer() {
+        for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+// one simulation, whatever its precision
+struct SimBase {
+    virtual ~SimBase() = default;
+    virtual int init(const double* phi, const double* u, const double* q, const double* noise) = 0;
+    virtual int step(int nsteps) = 0;
+    virtual int solve_potential(const double* q, double tol, int max_iter, int check, int* iters, double* res) = 0;
+    virtual int observables(lb3e_observables_t* out) = 0;
+    virtual int get_field(int id, double* dst) = 0;
+    virtual size_t state_bytes() const = 0;
+    virtual int save(void* dst) = 0;
+    virtual int load(const void* src) = 0;
+    virtual int kernel_times(double* ms, int64_t* counts) = 0;
+    int64_t launches = 0;
+    LaunchTimer timer;
+};
+
+// factories, one per translation unit (precision)
+size_t workspace_bytes_f64(const lb3e_params& p);
+SimBase* make_sim_f64(const lb3e_params& p, void* ws, void* stream);
+size_t workspace_bytes_f32(const lb3e_params& p);
+SimBase* make_sim_f32(const lb3e_params& p, void* ws, void* stream);
+size_t workspace_bytes_f16s(const lb3e_params& p);
+SimBase* make_sim_f16s(const lb3e_params& p, void* ws, void* stream);
+
+}  // namespace lb3e

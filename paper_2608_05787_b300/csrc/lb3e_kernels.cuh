@@ -1,0 +1,747 @@
+// lb3e_kernels.cuh -- sm_103a kernels of the three-phase EHD lattice Boltzmann step.
+//
+// Templated on the arithmetic type R (double or float) and the population storage
+// type S (double, float or __half).  lb3e_f64.cu instantiates <double,double> with
+// --fmad=false so its arithmetic rounds exactly like a plain C evaluation of the
+// same formulas; lb3e_f32.cu instantiates <float,float> and <float,__half>.
+//
+// Layout in HBM (structure of arrays, x fastest): population plane (set, j) of a
+// buffer is the contiguous [ny][nx] array at offset (9*set + j) * N, sets 0 = g
+// (flow), 1..3 = f^1..f^3 (phase), 4 = l (charge).  The potential populations h
+// live in their own 9-plane buffers.  Populations are stored post-streaming (the
+// state at the start of a step); collision kernels read their own cell and push
+// each post-collision value to the neighbour it streams to (x periodic, half-way
+// bounce-back at y walls).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lb3e {
+
+// ---------------------------------------------------------------- parameters
+struct DevParams {
+    int nx, ny, N, bc_y, electric, charge_convection, use_visc;
+    int inner, matrix;  // 0-based phase indices for the deformation moments
+    double rho[3], visc[3], tau_g, lam[3], D, tau_f, m0, eps[3], sigma[3];
+    double eps_ref, tau_h, alpha, tau_l;
+    double V_bottom, V_top, E_ext[2], u_wall_bottom, u_wall_top;
+};
+
+// Device-side buffers of one simulation (pointers into the caller's workspace).
+template <class R, class S>
+struct DevState {
+    S* pop[2];       // 45 planes each; pop[cur] holds the current state
+    R* h[2];         // 9 planes each
+    R* phi;          // 3 planes: phi_i of the last step
+    R* qt;           // sum l of the last step
+    R* q;            // corrected charge of the last step
+    R* eps;          // permittivity of the last step
+    R* E;            // 2 planes: field used in the last step
+    R* prev;         // 8 planes: (phi_i u)_x, (phi_i u)_y for i = 1..3, then (q u)_x, (q u)_y
+    R* diag;         // 6 planes: u_x, u_y, p, mu_1, mu_2, mu_3 of the last output step
+    R* psi_prev;     // 3 planes: psi, J_x, J_y at the previous pseudo-iteration
+    double* partial; // FP64 per-block partial sums
+    double* result;  // FP64 reduction results
+    double* stage;   // FP64 staging (9 planes)
+};
+
+// ---------------------------------------------------------------- lattice (Eq. 31)
+__host__ __device__ constexpr int cx(int j) { return (j == 1 || j == 5 || j == 8) ? 1 : (j == 3 || j == 6 || j == 7) ? -1 : 0; }
+__host__ __device__ constexpr int cy(int j) { return (j == 2 || j == 5 || j == 6) ? 1 : (j == 4 || j == 7 || j == 8) ? -1 : 0; }
+__host__ __device__ constexpr int opp(int j) { return j == 0 ? 0 : (j <= 4 ? ((j + 1) & 3) + 1 : ((j - 3) & 3) + 5); }
+template <class R>
+__host__ __device__ constexpr R wgt(int j) { return j == 0 ? R(4.0 / 9.0) : (j <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0)); }
+template <class R>
+__host__ __device__ constexpr R cs2() { return R(1.0 / 3.0); }
+
+// ---------------------------------------------------------------- storage conversion
+// Storage types.  With fp16 storage the rest population f^i_0 of each phase set
+// (which is close to phi_i, an O(1) number) is stored as its deviation from the
+// phi_i of the step that wrote it -- the "anchor", held in the phi field until the
+// next moments pass reads it.  The deviation is O(mu) ~ 1e-3, so fp16 keeps ~1e-6
+// absolute accuracy on it; every other plane is small already and stored as is.
+template <class S> struct Store;
+template <> struct Store<double> {
+    static __device__ __forceinline__ double ld(const double* p, size_t i) { return p[i]; }
+    static __device__ __forceinline__ void st(double* p, size_t i, double v) { p[i] = v; }
+};
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(const float* p, size_t i) { return p[i]; }
+    static __device__ __forceinline__ void st(float* p, size_t i, float v) { p[i] = v; }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half* p, size_t i) { return __half2float(p[i]); }
+    static __device__ __forceinline__ void st(__half* p, size_t i, float v) { p[i] = __float2half_rn(v); }
+};
+template <class S>
+__host__ __device__ constexpr bool anchored() { return sizeof(S) == 2; }
+
+// ---------------------------------------------------------------- grid helpers
+__device__ __forceinline__ int wrapi(int a, int n) { a %= n; return a < 0 ? a + n : a; }
+// stencil ghost rows: periodic, or mirror about the half-way wall
+__device__ __forceinline__ int ghost_row(int y, int ny, int bc_y) {
+    if (bc_y == 0) return wrapi(y, ny);
+    if (y < 0) return -1 - y;
+    if (y >= ny) return 2 * ny - 1 - y;
+    return y;
+}
+// the same, clamped into the grid: tile loaders may touch rows beyond the ghost
+// ring on small or ragged grids, whose values are never used
+__device__ __forceinline__ int tile_row(int y, int ny, int bc_y) {
+    const int r = ghost_row(y, ny, bc_y);
+    return r < 0 ? 0 : (r >= ny ? ny - 1 : r);
+}
+
+// Eq. 30
+template <class R>
+__device__ __forceinline__ R perm(const DevParams& P, R p0, R p1, R p2) {
+    R e = R(0);
+    e += R(P.eps[0]) * p0 * p0 * (R(3) - R(2) * p0);
+    e += R(P.eps[1]) * p1 * p1 * (R(3) - R(2) * p1);
+    e += R(P.eps[2]) * p2 * p2 * (R(3) - R(2) * p2);
+    return e;
+}
+template <class R>
+__device__ __forceinline__ R cond(const DevParams& P, R p0, R p1, R p2) {
+    return p0 * R(P.sigma[0]) + p1 * R(P.sigma[1]) + p2 * R(P.sigma[2]);
+}
+template <class R>
+__device__ __forceinline__ R dens(const DevParams& P, R p0, R p1, R p2) {
+    return p0 * R(P.rho[0]) + p1 * R(P.rho[1]) + p2 * R(P.rho[2]);
+}
+// Eq. 40
+template <class R>
+__device__ __forceinline__ R s_eq(int j, R ux, R uy) {
+    R cu = R(cx(j)) * ux + R(cy(j)) * uy;
+    R uu = ux * ux + uy * uy;
+    return wgt<R>(j) * (cu / cs2<R>() + cu * cu / (R(2) * cs2<R>() * cs2<R>()) - uu / (R(2) * cs2<R>()));
+}
+
+// ---------------------------------------------------------------- block reduction (FP64)
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* out) {
+    __shared__ double red[32][NV];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double a = lane < nwarps ? red[lane][k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) out[k] = a;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- S1: moments
+template <class R, class S>
+__global__ void __launch_bounds__(256) k_moments(DevParams P, const S* __restrict__ pop, const R* phi_anchor,
+                                                 R* phi, R* __restrict__ qt) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const size_t N = P.N, c = (size_t)y * P.nx + x;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        R a = R(0);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            R v = Store<S>::ld(pop, (9 * (i + 1) + j) * N + c);
+            if (anchored<S>() && j == 0) v += phi_anchor[i * N + c];
+            a += v;
+        }
+        phi[i * N + c] = a;  // may alias phi_anchor: read above, written here
+    }
+    R a = R(0);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) a += Store<S>::ld(pop, (36 + j) * N + c);
+    qt[c] = a;
+}
+
+// ---------------------------------------------------------------- S2-S4: properties, stencils, charge
+// Reads phi on the 1-ring (L1-cached), writes eps and the closed-form charge
+// q = [q~ + (sigma/eps grad eps . E - grad sigma . E)/2] / (1 + sigma/(2 eps)),
+// with E of the previous step.
+template <class R>
+__global__ void __launch_bounds__(256) k_prologue(DevParams P, const R* __restrict__ phi, const R* __restrict__ qt,
+                                                  const R* __restrict__ E, R* __restrict__ q, R* __restrict__ eps_out,
+                                                  int use_qt) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const size_t N = P.N, c = (size_t)y * P.nx + x;
+    R gex = R(0), gey = R(0), gsx = R(0), gsy = R(0), e0 = R(0), s0 = R(0);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const size_t n = (size_t)ghost_row(y + cy(j), P.ny, P.bc_y) * P.nx + wrapi(x + cx(j), P.nx);
+        const R p0 = phi[n], p1 = phi[N + n], p2 = phi[2 * N + n];
+        const R e = perm<R>(P, p0, p1, p2), s = cond<R>(P, p0, p1, p2);
+        gex += wgt<R>(j) * R(cx(j)) * e;
+        gey += wgt<R>(j) * R(cy(j)) * e;
+        gsx += wgt<R>(j) * R(cx(j)) * s;
+        gsy += wgt<R>(j) * R(cy(j)) * s;
+        if (j == 0) { e0 = e; s0 = s; }
+    }
+    gex = gex / cs2<R>(); gey = gey / cs2<R>(); gsx = gsx / cs2<R>(); gsy = gsy / cs2<R>();
+    eps_out[c] = e0;
+    if (!use_qt) return;
+    const R r = s0 / e0;
+    const R Ex = E[c], Ey = E[N + c];
+    const R src = r * (gex * Ex + gey * Ey) - (gsx * Ex + gsy * Ey);
+    q[c] = (qt[c] + R(0.5) * src) / (R(1) + R(0.5) * r);
+}
+
+// ---------------------------------------------------------------- S5: potential iteration (Eq. 43-45)
+// One pseudo-time collide + push-stream of h.  On iterations before a check it
+// saves psi and J = sum c_j h_j; on a check it accumulates (FP64, per block)
+// |d psi|^2, |psi|^2, |d J|^2, |J|^2.
+template <class R>
+__global__ void __launch_bounds__(256) k_poisson(DevParams P, const R* __restrict__ hin, R* __restrict__ hout,
+                                                 const R* __restrict__ eps, const R* __restrict__ q,
+                                                 R* __restrict__ prev, double* __restrict__ partial,
+                                                 int save_prev, int check) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool in = x < P.nx && y < P.ny;
+    const size_t N = P.N, c = in ? (size_t)y * P.nx + x : 0;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (in) {
+        R hj[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) hj[j] = hin[j * N + c];
+        R ps = R(0), jx = R(0), jy = R(0);
+#pragma unroll
+        for (int j = 1; j < 9; ++j) ps += hj[j];
+        ps = ps / (R(1) - wgt<R>(0));
+#pragma unroll
+        for (int j = 0; j < 9; ++j) { jx += R(cx(j)) * hj[j]; jy += R(cy(j)) * hj[j]; }
+        if (check) {
+            const double d = (double)ps - (double)prev[c];
+            const double ex = (double)jx - (double)prev[N + c], ey = (double)jy - (double)prev[2 * N + c];
+            acc[0] = d * d;
+            acc[1] = (double)ps * (double)ps;
+            acc[2] = ex * ex + ey * ey;
+            acc[3] = (double)jx * (double)jx + (double)jy * (double)jy;
+        }
+        if (save_prev) { prev[c] = ps; prev[N + c] = jx; prev[2 * N + c] = jy; }
+        const R th = R(P.tau_h);
+        const R epshat = eps[c] - R(P.eps_ref);
+        const R den = epshat + cs2<R>() * th;
+        const R gx = -jx / den, gy = -jy / den;
+        const R qc = q[c];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const R heq = (j == 0) ? (wgt<R>(0) - R(1)) * ps : wgt<R>(j) * ps;
+            const R varpi = (j == 0) ? R(0) : R(1.0 / 8.0);
+            const R cg = R(cx(j)) * gx + R(cy(j)) * gy;
+            const R v = hj[j] - (hj[j] - heq) / th - (epshat / cs2<R>()) * wgt<R>(j) * cg / th + varpi * qc;
+            const int yt = y + cy(j);
+            if (P.bc_y != 0 && (yt < 0 || yt >= P.ny)) {
+                R out = v;
+                if (P.bc_y == 2) out = -v + R(2) * wgt<R>(j) * R(yt >= P.ny ? P.V_top : P.V_bottom);
+                hout[opp(j) * N + c] = out;
+            } else {
+                hout[j * N + (size_t)wrapi(yt, P.ny) * P.nx + wrapi(x + cx(j), P.nx)] = v;
+            }
+        }
+    }
+    if (check) {
+        const int b = blockIdx.x + gridDim.x * blockIdx.y;
+        block_reduce_store<4>(acc, partial + 4 * (size_t)b);
+    }
+}
+
+// final reduction of nblk x NV partials in a fixed order (one block of 256 threads)
+template <int NV>
+__global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ partial, int nblk,
+                                                         double* __restrict__ out) {
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += partial[(size_t)b * NV + k];
+    block_reduce_store<NV>(v, out);
+}
+
+// psi and E = sum c_j h_j / (eps - eps_ref + cs2 tau_h) + E_ext from the current h
+template <class R>
+__global__ void __launch_bounds__(256) k_potential_fields(DevParams P, const R* __restrict__ h,
+                                                          const R* __restrict__ eps, R* __restrict__ E,
+                                                          double* __restrict__ psi_out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const size_t N = P.N, c = (size_t)y * P.nx + x;
+    R ps = R(0), jx = R(0), jy = R(0);
+#pragma unroll
+    for (int j = 1; j < 9; ++j) ps += h[j * N + c];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) { jx += R(cx(j)) * h[j * N + c]; jy += R(cy(j)) * h[j * N + c]; }
+    if (psi_out) { psi_out[c] = (double)(ps / (R(1) - wgt<R>(0))); return; }
+    const R den = (eps[c] - R(P.eps_ref)) + cs2<R>() * R(P.tau_h);
+    const R gx = -jx / den, gy = -jy / den;
+    E[c] = -gx + R(P.E_ext[0]);
+    E[N + c] = -gy + R(P.E_ext[1]);
+}
+
+// h at equilibrium with the linear electrode profile (or zero)
+template <class R>
+__global__ void k_init_h(DevParams P, R* __restrict__ h) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const size_t N = P.N, c = (size_t)y * P.nx + x;
+    const double ps = P.bc_y == 2 ? P.V_bottom + (P.V_top - P.V_bottom) * (y + 0.5) / P.ny : 0.0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) h[j * N + c] = (j == 0) ? (wgt<R>(0) - R(1)) * R(ps) : wgt<R>(j) * R(ps);
+}
+
+template <class R>
+__global__ void k_fill_E(DevParams P, R* __restrict__ E) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= (size_t)P.N) return;
+    E[i] = R(P.E_ext[0]);
+    E[P.N + i] = R(P.E_ext[1]);
+}
+
+// ---------------------------------------------------------------- Eq. 20 at one cell from a phi tile
+template <class R>
+__device__ __forceinline__ R lap_tile(const R* t, int pitch, int ty, int tx) {
+    const R c = t[ty * pitch + tx];
+    R a = R(0);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) a += R(2) * wgt<R>(j) * (t[(ty + cy(j)) * pitch + tx + cx(j)] - c);
+    return a / cs2<R>();
+}
+template <class R>
+__device__ __forceinline__ R chem_pot(const DevParams& P, int i, R ph, R lap, R e2) {
+    const R D = R(P.D), lam = R(P.lam[i]);
+    const R bulk = R(24) / D * lam * ph * (ph - R(0.5)) * (ph - R(1));
+    const R grad = R(0.75) * D * lam * lap;
+    const R deps = R(6) * R(P.eps[i]) * ph * (R(1) - ph);
+    return bulk - grad - R(0.5) * deps * e2;
+}
+
+// ---------------------------------------------------------------- S6-S14: fused collide + stream
+// One thread per cell of a TX x TY tile.  phi (2-ring halo) and E (1-ring) are
+// staged in shared memory; mu is evaluated on the 1-ring there (mirrored at walls);
+// then each thread forms grad mu, the force, u and p, and collides and pushes its
+// 45 populations.  write_diag stores u, p, mu for field output.
+constexpr int TX = 32, TY = 8;
+
+template <class R, class S>
+__global__ void __launch_bounds__(TX * TY) k_fused(DevParams P, const S* __restrict__ pin, S* __restrict__ pout,
+                                                   const R* __restrict__ phi, const R* __restrict__ qf,
+                                                   const R* __restrict__ E, R* __restrict__ prev,
+                                                   R* __restrict__ diag, int first, int write_diag) {
+    constexpr int PX = TX + 4, PY = TY + 4;  // phi tile, 2-ring
+    constexpr int MX = TX + 2, MY = TY + 2;  // mu / E tile, 1-ring
+    __shared__ R sphi[3][PY * PX];
+    __shared__ R sE[2][MY * MX];
+    __shared__ R smu[3][MY * MX];
+    const int nx = P.nx, ny = P.ny;
+    const size_t N = P.N;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.x + TX * threadIdx.y;
+
+    for (int k = tid; k < PY * PX; k += TX * TY) {
+        const int ly = k / PX, lx = k % PX;
+        const size_t n = (size_t)tile_row(y0 + ly - 2, ny, P.bc_y) * nx + wrapi(x0 + lx - 2, nx);
+        sphi[0][k] = phi[n];
+        sphi[1][k] = phi[N + n];
+        sphi[2][k] = phi[2 * N + n];
+    }
+    for (int k = tid; k < MY * MX; k += TX * TY) {
+        const int ly = k / MX, lx = k % MX;
+        const size_t n = (size_t)tile_row(y0 + ly - 1, ny, P.bc_y) * nx + wrapi(x0 + lx - 1, nx);
+        sE[0][k] = E[n];
+        sE[1][k] = E[N + n];
+    }
+    __syncthreads();
+    // mu on the 1-ring at in-domain rows
+    for (int k = tid; k < MY * MX; k += TX * TY) {
+        const int ly = k / MX, lx = k % MX;
+        const int gy = y0 + ly - 1;
+        if (P.bc_y != 0 && (gy < 0 || gy >= ny)) continue;
+        const R ex = sE[0][k], ey = sE[1][k];
+        const R e2 = ex * ex + ey * ey;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const R ph = sphi[i][(ly + 1) * PX + lx + 1];
+            smu[i][k] = chem_pot<R>(P, i, ph, lap_tile<R>(sphi[i], PX, ly + 1, lx + 1), e2);
+        }
+    }
+    __syncthreads();
+    // ghost rows of mu mirror the in-domain row they face
+    if (P.bc_y != 0) {
+        for (int k = tid; k < MY * MX; k += TX * TY) {
+            const int ly = k / MX, lx = k % MX;
+            const int gy = y0 + ly - 1;
+            if (gy >= 0 && gy < ny) continue;
+            const int src = ghost_row(gy, ny, P.bc_y) - (y0 - 1);
+            if (src >= 0 && src < MY)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) smu[i][k] = smu[i][src * MX + lx];
+        }
+        __syncthreads();
+    }
+
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const size_t c = (size_t)y * nx + x;
+    const int py = threadIdx.y + 2, px = threadIdx.x + 2;
+    const int my = threadIdx.y + 1, mx = threadIdx.x + 1;
+
+    R ph[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ph[i] = sphi[i][py * PX + px];
+    // stencils (Eq. 33) of mu_i, rho, eps, sigma
+    R gmu[3][2], grx = R(0), gry = R(0), gex = R(0), gey = R(0), gsx = R(0), gsy = R(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        R ax = R(0), ay = R(0);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const R v = smu[i][(my + cy(j)) * MX + mx + cx(j)];
+            ax += wgt<R>(j) * R(cx(j)) * v;
+            ay += wgt<R>(j) * R(cy(j)) * v;
+        }
+        gmu[i][0] = ax / cs2<R>();
+        gmu[i][1] = ay / cs2<R>();
+    }
+    R rho = R(0), sg = R(0), ep = R(0);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const int k = (py + cy(j)) * PX + px + cx(j);
+        const R p0 = sphi[0][k], p1 = sphi[1][k], p2 = sphi[2][k];
+        const R r = dens<R>(P, p0, p1, p2), e = perm<R>(P, p0, p1, p2), s = cond<R>(P, p0, p1, p2);
+        grx += wgt<R>(j) * R(cx(j)) * r;
+        gry += wgt<R>(j) * R(cy(j)) * r;
+        gex += wgt<R>(j) * R(cx(j)) * e;
+        gey += wgt<R>(j) * R(cy(j)) * e;
+        gsx += wgt<R>(j) * R(cx(j)) * s;
+        gsy += wgt<R>(j) * R(cy(j)) * s;
+        if (j == 0) { rho = r; ep = e; sg = s; }
+    }
+    grx = grx / cs2<R>(); gry = gry / cs2<R>();
+    gex = gex / cs2<R>(); gey = gey / cs2<R>();
+    gsx = gsx / cs2<R>(); gsy = gsy / cs2<R>();
+
+    const R Ex = sE[0][my * MX + mx], Ey = sE[1][my * MX + mx];
+    const R qc = qf[c];
+    // R of Eq. 47 with q^n and E^n
+    const R rr = sg / ep;
+    const R Rc = -rr * qc + rr * (gex * Ex + gey * Ey) - (gsx * Ex + gsy * Ey);
+    // force, Eq. 27b
+    R Fx = R(0), Fy = R(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { Fx -= ph[i] * gmu[i][0]; Fy -= ph[i] * gmu[i][1]; }
+    Fx = Fx + qc * Ex;
+    Fy = Fy + qc * Ey;
+
+    // flow moments, Eq. 41
+    const S* gin = pin;
+    R g[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) g[j] = Store<S>::ld(gin, j * N + c);
+    R mxm = R(0), mym = R(0), g1 = R(0);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        mxm += R(cx(j)) * g[j];
+        mym += R(cy(j)) * g[j];
+        if (j) g1 += g[j];
+    }
+    const R ux = (mxm + R(0.5) * Fx) / rho;
+    const R uy = (mym + R(0.5) * Fy) / rho;
+    const R ugr = ux * grx + uy * gry;
+    const R pr = cs2<R>() / (R(1) - wgt<R>(0)) * (g1 + R(0.5) * ugr + rho * s_eq<R>(0, ux, uy));
+
+    // d/dt terms (first-order backward differences)
+    R dpu[3][2], dqu[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        dpu[i][0] = first ? R(0) : ph[i] * ux - prev[(2 * i) * N + c];
+        dpu[i][1] = first ? R(0) : ph[i] * uy - prev[(2 * i + 1) * N + c];
+    }
+    dqu[0] = first ? R(0) : qc * ux - prev[6 * N + c];
+    dqu[1] = first ? R(0) : qc * uy - prev[7 * N + c];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        prev[(2 * i) * N + c] = ph[i] * ux;
+        prev[(2 * i + 1) * N + c] = ph[i] * uy;
+    }
+    prev[6 * N + c] = qc * ux;
+    prev[7 * N + c] = qc * uy;
+
+    if (write_diag) {
+        diag[c] = ux;
+        diag[N + c] = uy;
+        diag[2 * N + c] = pr;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) diag[(3 + i) * N + c] = smu[i][my * MX + mx];
+    }
+
+    const bool walls = P.bc_y != 0;
+    // push helper: post-collision value v of plane (set, j) leaving cell (x, y)
+    auto push = [&](int set, int j, R v) {
+        const int yt = y + cy(j);
+        if (walls && (yt < 0 || yt >= ny)) {
+            Store<S>::st(pout, (9 * set + opp(j)) * N + c, v);
+        } else {
+            Store<S>::st(pout, (9 * set + j) * N + (size_t)wrapi(yt, ny) * nx + wrapi(x + cx(j), nx), v);
+        }
+    };
+
+    // phase populations, Eq. 34-36 with the mobility of Eq. 28
+    const R tf = R(P.tau_f), m0 = R(P.m0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        R Mii = R(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (k != i) Mii += m0 * ph[i] * ph[k];
+        R Yx = R(0), Yy = R(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const R Mik = (k == i) ? (Mii - m0) : -m0 * ph[i] * ph[k];
+            Yx += Mik * gmu[k][0];
+            Yy += Mik * gmu[k][1];
+        }
+        const R Ax = dpu[i][0] / cs2<R>() - Yx / m0;
+        const R Ay = dpu[i][1] / cs2<R>() - Yy / m0;
+        const R mui = smu[i][my * MX + mx];
+        R fv[9];
+#pragma unroll
+        for (int j = anchored<S>() ? 1 : 0; j < 9; ++j) fv[j] = Store<S>::ld(pin, (9 * (i + 1) + j) * N + c);
+        if (anchored<S>()) {  // f_0 = phi_i - sum of the moving populations
+            R a = R(0);
+#pragma unroll
+            for (int j = 1; j < 9; ++j) a += fv[j];
+            fv[0] = ph[i] - a;
+        }
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const R feq = (j == 0) ? ph[i] - (R(1) - wgt<R>(0)) * mui
+                                   : wgt<R>(j) * mui + wgt<R>(j) * (R(cx(j)) * ph[i] * ux + R(cy(j)) * ph[i] * uy) / cs2<R>();
+            const R Fj = wgt<R>(j) * (R(cx(j)) * Ax + R(cy(j)) * Ay);
+            const R v = fv[j] - (fv[j] - feq) / tf + (R(1) - R(1) / (R(2) * tf)) * Fj;
+            push(i + 1, j, (anchored<S>() && j == 0) ? v - ph[i] : v);
+        }
+    }
+
+    // flow populations, Eq. 37-40
+    {
+        R tg = R(P.tau_g);
+        if (P.use_visc) {
+            R eta = R(0);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) eta += ph[i] * R(P.visc[i]);
+            tg = R(0.5) + eta / (rho * cs2<R>());
+        }
+        const R uw = y == 0 ? R(P.u_wall_bottom) : R(P.u_wall_top);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const R geq = (j == 0) ? (wgt<R>(0) - R(1)) * pr / cs2<R>() + rho * s_eq<R>(0, ux, uy)
+                                   : wgt<R>(j) * pr / cs2<R>() + rho * s_eq<R>(j, ux, uy);
+            const R cu = R(cx(j)) * ux + R(cy(j)) * uy;
+            const R cgr = R(cx(j)) * grx + R(cy(j)) * gry;
+            const R cF = R(cx(j)) * Fx + R(cy(j)) * Fy;
+            const R G = wgt<R>(j) * (ugr + cF / cs2<R>() + (cu * cgr - cs2<R>() * ugr) / cs2<R>());
+            const R v = g[j] - (g[j] - geq) / tg + (R(1) - R(1) / (R(2) * tg)) * G;
+            const int yt = y + cy(j);
+            if (walls && (yt < 0 || yt >= ny))  // g_opp = g* - 2 w rho (c . u_w) / cs2
+                push(0, j, v - R(2) * wgt<R>(j) * rho * (R(cx(j)) * uw) / cs2<R>());
+            else
+                push(0, j, v);
+        }
+    }
+
+    // charge populations, Eq. 48-50
+    {
+        const R tl = R(P.tau_l);
+        const bool cc = P.charge_convection != 0;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const R cu = R(cx(j)) * ux + R(cy(j)) * uy;
+            const R leq = cc ? wgt<R>(j) * qc * (R(1) + cu / cs2<R>()) : wgt<R>(j) * qc;
+            const R Sj = (R(1) - R(1) / (R(2) * tl)) * wgt<R>(j) * Rc;
+            const R Tj = cc ? (R(1) - R(1) / (R(2) * tl)) * wgt<R>(j) * (R(cx(j)) * dqu[0] + R(cy(j)) * dqu[1]) / cs2<R>()
+                            : R(0);
+            const R lj = Store<S>::ld(pin, (36 + j) * N + c);
+            push(4, j, lj - (lj - leq) / tl + Sj + Tj);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- initial populations
+// f^i = f^eq(phi, mu, u), g = g_eq(p = 0, u), l = l_eq(q, u); mu from Eq. 20 with
+// the initial field (global-memory stencil; init only).
+template <class R, class S>
+__global__ void k_init_pops(DevParams P, S* __restrict__ pop, const R* __restrict__ phi, const R* __restrict__ q,
+                            const R* __restrict__ E, R* __restrict__ diag) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const size_t N = P.N, c = (size_t)y * P.nx + x;
+    const R ux = diag[c], uy = diag[N + c];
+    const R Ex = E[c], Ey = E[N + c];
+    const R e2 = Ex * Ex + Ey * Ey;
+    R ph[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const R* f = phi + i * N;
+        const R cc = f[c];
+        R a = R(0);
+#pragma unroll
+        for (int j = 0; j < 9; ++j)
+            a += R(2) * wgt<R>(j) * (f[(size_t)ghost_row(y + cy(j), P.ny, P.bc_y) * P.nx + wrapi(x + cx(j), P.nx)] - cc);
+        const R lap = a / cs2<R>();
+        ph[i] = cc;
+        const R mui = chem_pot<R>(P, i, cc, lap, e2);
+        diag[(3 + i) * N + c] = mui;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const R feq = (j == 0) ? cc - (R(1) - wgt<R>(0)) * mui
+                                   : wgt<R>(j) * mui + wgt<R>(j) * (R(cx(j)) * cc * ux + R(cy(j)) * cc * uy) / cs2<R>();
+            Store<S>::st(pop, (9 * (i + 1) + j) * N + c, (anchored<S>() && j == 0) ? feq - cc : feq);
+        }
+    }
+    const R rho = dens<R>(P, ph[0], ph[1], ph[2]);
+    const R qc = q[c];
+    const bool cc = P.charge_convection != 0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        Store<S>::st(pop, j * N + c, rho * s_eq<R>(j, ux, uy));
+        const R cu = R(cx(j)) * ux + R(cy(j)) * uy;
+        Store<S>::st(pop, (36 + j) * N + c, cc ? wgt<R>(j) * qc * (R(1) + cu / cs2<R>()) : wgt<R>(j) * qc);
+    }
+    diag[2 * N + c] = R(0);
+}
+
+// add caller noise (FP64 staging, 9 planes of one set) to set `set`; an anchored
+// rest population is a deviation, so the noise adds to it unchanged
+template <class R, class S>
+__global__ void k_add_noise(DevParams P, S* __restrict__ pop, const double* __restrict__ nz, int set) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x, N = P.N;
+    if (i >= 9 * N) return;
+    const size_t idx = (size_t)(9 * set) * N + i;
+    Store<S>::st(pop, idx, Store<S>::ld(pop, idx) + R(nz[i]));
+}
+
+// ---------------------------------------------------------------- conversions
+template <class R>
+__global__ void k_from_f64(R* __restrict__ dst, const double* __restrict__ src, size_t n) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = R(src[i]);
+}
+template <class T>
+__global__ void k_to_f64(double* __restrict__ dst, const T* __restrict__ src, size_t n) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (double)src[i];
+}
+template <class R, class S>
+__global__ void k_pop_to_f64(double* __restrict__ dst, const S* __restrict__ pop, const R* __restrict__ phi,
+                             int set, int j, size_t N) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double v = (double)Store<S>::ld(pop, (size_t)(9 * set + j) * N + i);
+    if (anchored<S>() && set >= 1 && set <= 3 && j == 0) v += (double)phi[(size_t)(set - 1) * N + i];
+    dst[i] = v;
+}
+
+// ---------------------------------------------------------------- observables (FP64 reductions)
+// Per block: mass[3], charge, F_phi, F_E, F_u, F_q, nonfinite, then the indicator
+// moments (sum chi, chi x, chi y, chi x^2, chi y^2) for inner and outer; max
+// deviation is reduced separately (as a sum of nothing: see k_maxdev).
+constexpr int NOBS = 19;
+template <class R>
+__global__ void __launch_bounds__(256) k_observables(DevParams P, const R* __restrict__ phi, const R* __restrict__ q,
+                                                     const R* __restrict__ E, const R* __restrict__ diag,
+                                                     double* __restrict__ partial) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    double v[NOBS];
+#pragma unroll
+    for (int k = 0; k < NOBS; ++k) v[k] = 0.0;
+    if (x < P.nx && y < P.ny) {
+        const size_t N = P.N, c = (size_t)y * P.nx + x;
+        const double D = P.D;
+        double ph[3];
+        for (int i = 0; i < 3; ++i) {
+            const R* f = phi + i * N;
+            double ax = 0.0, ay = 0.0;
+            for (int j = 0; j < 9; ++j) {
+                const double w = (double)f[(size_t)ghost_row(y + cy(j), P.ny, P.bc_y) * P.nx + wrapi(x + cx(j), P.nx)];
+                ax += wgt<double>(j) * cx(j) * w;
+                ay += wgt<double>(j) * cy(j) * w;
+            }
+            ax = ax / cs2<double>();
+            ay = ay / cs2<double>();
+            ph[i] = (double)f[c];
+            v[i] = ph[i];
+            v[4] += 6.0 / D * P.lam[i] * ph[i] * ph[i] * (1.0 - ph[i]) * (1.0 - ph[i]) + 0.375 * D * P.lam[i] * (ax * ax + ay * ay);
+        }
+        double eps = 0.0;
+        for (int i = 0; i < 3; ++i) eps += P.eps[i] * ph[i] * ph[i] * (3.0 - 2.0 * ph[i]);
+        const double Ex = E[c], Ey = E[N + c];
+        v[5] = 0.5 * eps * (Ex * Ex + Ey * Ey);
+        const double rho = ph[0] * P.rho[0] + ph[1] * P.rho[1] + ph[2] * P.rho[2];
+        const double ux = diag[c], uy = diag[N + c];
+        v[6] = 0.5 * rho * (ux * ux + uy * uy);
+        const double sg = ph[0] * P.sigma[0] + ph[1] * P.sigma[1] + ph[2] * P.sigma[2];
+        const double qc = q[c];
+        if (sg > 0) v[7] = 0.5 * (P.alpha / sg) * qc * qc;
+        v[3] = qc;
+        const double vals[6] = {ph[0], ph[1], ph[2], ux, uy, qc};
+        for (int k = 0; k < 6; ++k)
+            if (!isfinite(vals[k])) v[8] += 1.0;
+        const double chis[2] = {ph[P.inner], 1.0 - ph[P.matrix]};
+        for (int k = 0; k < 2; ++k) {
+            v[9 + 5 * k] = chis[k];
+            v[10 + 5 * k] = chis[k] * x;
+            v[11 + 5 * k] = chis[k] * y;
+            v[12 + 5 * k] = chis[k] * x * x;
+            v[13 + 5 * k] = chis[k] * y * y;
+        }
+    }
+    block_reduce_store<NOBS>(v, partial + (size_t)NOBS * (blockIdx.x + gridDim.x * blockIdx.y));
+}
+
+// max |sum phi - 1| as a per-block max, then a fixed-order max
+template <class R>
+__global__ void __launch_bounds__(256) k_maxdev(DevParams P, const R* __restrict__ phi, double* __restrict__ partial) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    double m = 0.0;
+    if (x < P.nx && y < P.ny) {
+        const size_t N = P.N, c = (size_t)y * P.nx + x;
+        m = fabs((double)phi[c] + (double)phi[N + c] + (double)phi[2 * N + c] - 1.0);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    __shared__ double red[32];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if ((tid & 31) == 0) red[tid >> 5] = m;
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0;
+        for (int k = 0; k < (int)((blockDim.x * blockDim.y + 31) >> 5); ++k) a = fmax(a, red[k]);
+        partial[blockIdx.x + gridDim.x * blockIdx.y] = a;
+    }
+}
+static __global__ void k_max_partials(const double* __restrict__ partial, int n, double* __restrict__ out) {
+    double m = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) m = fmax(m, partial[b]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) a = fmax(a, red[k]);
+        *out = a;
+    }
+}
+
+}  // namespace lb3e

@@ -1,0 +1,387 @@
+// lb3e_sim.cuh -- host-side sequencing of the kernels for one precision.
+//
+// Sim<R,S> owns no device memory: it carves the caller's workspace into the
+// buffers listed in DevState and issues every kernel on the caller's stream.
+// The potential solve is a host loop of pseudo-iterations; every
+// poisson_check_every iterations one FP64 residual is read back to pinned host
+// memory (the only device->host traffic of a time step).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "lb3e_internal.h"
+#include "lb3e_kernels.cuh"
+
+namespace lb3e {
+
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+template <class R, class S>
+class Sim final : public SimBase {
+  public:
+    // workspace layout (byte offsets), computed identically by bytes() and the constructor
+    struct Layout {
+        size_t pop[2], h[2], phi, qt, q, eps, E, prev, diag, psi_prev, partial, result, stage, total;
+    };
+    static Layout layout(const lb3e_params& p) {
+        const size_t N = (size_t)p.nx * p.ny;
+        const size_t nblk = (size_t)((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY);
+        Layout L{};
+        size_t o = 0;
+        auto take = [&](size_t bytes) { size_t a = o; o += align256(bytes); return a; };
+        L.pop[0] = take(45 * N * sizeof(S));
+        L.pop[1] = take(45 * N * sizeof(S));
+        L.h[0] = take(9 * N * sizeof(R));
+        L.h[1] = take(9 * N * sizeof(R));
+        L.phi = take(3 * N * sizeof(R));
+        L.qt = take(N * sizeof(R));
+        L.q = take(N * sizeof(R));
+        L.eps = take(N * sizeof(R));
+        L.E = take(2 * N * sizeof(R));
+        L.prev = take(8 * N * sizeof(R));
+        L.diag = take(6 * N * sizeof(R));
+        L.psi_prev = take(3 * N * sizeof(R));
+        L.partial = take(nblk * NOBS * sizeof(double));
+        L.result = take(64 * sizeof(double));
+        L.stage = take(9 * N * sizeof(double));
+        L.total = o;
+        return L;
+    }
+
+    Sim(const lb3e_params& prm, void* ws, cudaStream_t st) : p_(prm), stream_(st) {
+        L_ = layout(prm);
+        char* b = static_cast<char*>(ws);
+        d_.pop[0] = reinterpret_cast<S*>(b + L_.pop[0]);
+        d_.pop[1] = reinterpret_cast<S*>(b + L_.pop[1]);
+        d_.h[0] = reinterpret_cast<R*>(b + L_.h[0]);
+        d_.h[1] = reinterpret_cast<R*>(b + L_.h[1]);
+        d_.phi = reinterpret_cast<R*>(b + L_.phi);
+        d_.qt = reinterpret_cast<R*>(b + L_.qt);
+        d_.q = reinterpret_cast<R*>(b + L_.q);
+        d_.eps = reinterpret_cast<R*>(b + L_.eps);
+        d_.E = reinterpret_cast<R*>(b + L_.E);
+        d_.prev = reinterpret_cast<R*>(b + L_.prev);
+        d_.diag = reinterpret_cast<R*>(b + L_.diag);
+        d_.psi_prev = reinterpret_cast<R*>(b + L_.psi_prev);
+        d_.partial = reinterpret_cast<double*>(b + L_.partial);
+        d_.result = reinterpret_cast<double*>(b + L_.result);
+        d_.stage = reinterpret_cast<double*>(b + L_.stage);
+        base_ = b;
+        N_ = (size_t)prm.nx * prm.ny;
+        dp_ = make_dev_params(prm);
+        grid2_ = dim3((prm.nx + TX - 1) / TX, (prm.ny + TY - 1) / TY);
+        nblk_ = (int)(grid2_.x * grid2_.y);
+    }
+    ~Sim() override {
+        if (pinned_) cudaFreeHost(pinned_);
+    }
+
+    int init(const double* phi, const double* u, const double* q, const double* noise) override {
+        if (cudaHostAlloc(reinterpret_cast<void**>(&pinned_), 64 * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
+            return LB3E_ERR_CUDA;
+        // phi, u, q -> device fields (through the FP64 staging area)
+        TRY(upload(phi, 3 * N_, d_.phi));
+        if (u) {
+            TRY(upload(u, 2 * N_, d_.diag));
+        } else {
+            TRY(memset_async(d_.diag, 2 * N_ * sizeof(R)));
+        }
+        if (q) {
+            TRY(upload(q, N_, d_.q));
+        } else {
+            TRY(memset_async(d_.q, N_ * sizeof(R)));
+        }
+        TRY(memset_async(d_.prev, 8 * N_ * sizeof(R)));
+        TRY(memset_async(d_.psi_prev, 3 * N_ * sizeof(R)));
+        cur_ = 0;
+        hcur_ = 0;
+        // permittivity of the initial phase field
+        timer.begin(stream_, KC_PROLOGUE);
+        k_prologue<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.phi, d_.qt, d_.E, d_.q, d_.eps, 0);
+        TRY(launched());
+        timer.begin(stream_, KC_OTHER);
+        k_init_h<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[0]);
+        TRY(launched());
+        if (p_.electric) {
+            TRY(poisson(p_.poisson_tol, p_.poisson_max_iter, p_.poisson_fixed_iter, p_.poisson_check_every));
+        } else {
+            timer.begin(stream_, KC_OTHER);
+            k_fill_E<R><<<blocks1(N_), 256, 0, stream_>>>(dp_, d_.E);
+            TRY(launched());
+        }
+        timer.begin(stream_, KC_OTHER);
+        k_init_pops<R, S><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.pop[0], d_.phi, d_.q, d_.E, d_.diag);
+        TRY(launched());
+        if (noise) {
+            for (int set = 0; set < 5; ++set) {
+                if (cudaMemcpyAsync(d_.stage, noise + (size_t)set * 9 * N_, 9 * N_ * sizeof(double),
+                                    cudaMemcpyDefault, stream_) != cudaSuccess)
+                    return LB3E_ERR_CUDA;
+                timer.begin(stream_, KC_OTHER);
+                k_add_noise<R, S><<<blocks1(9 * N_), 256, 0, stream_>>>(dp_, d_.pop[0], d_.stage, set);
+                TRY(launched());
+            }
+        }
+        step_ = 0;
+        return sync();
+    }
+
+    int step(int nsteps) override {
+        for (int s = 0; s < nsteps; ++s) {
+            const int last = (s == nsteps - 1);
+            timer.begin(stream_, KC_MOMENTS);
+            k_moments<R, S><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.pop[cur_], d_.phi, d_.phi, d_.qt);
+            TRY(launched());
+            timer.begin(stream_, KC_PROLOGUE);
+            k_prologue<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.phi, d_.qt, d_.E, d_.q, d_.eps, 1);
+            TRY(launched());
+            if (p_.electric) {
+                TRY(poisson(p_.poisson_tol, p_.poisson_max_iter, p_.poisson_fixed_iter, p_.poisson_check_every));
+            }
+            timer.begin(stream_, KC_FUSED);
+            k_fused<R, S><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q,
+                                                                 d_.E, d_.prev, d_.diag, step_ == 0 ? 1 : 0, last);
+            TRY(launched());
+            cur_ ^= 1;
+            ++step_;
+        }
+        return LB3E_OK;
+    }
+
+    int solve_potential(const double* q, double tol, int max_iter, int check, int* iters, double* res) override {
+        if (q) TRY(upload(q, N_, d_.q));
+        TRY(poisson(tol, max_iter, 0, check));
+        if (iters) *iters = last_iters_;
+        if (res) *res = last_res_;
+        TRY(sync());
+        return last_conv_ ? LB3E_OK : LB3E_ERR_NOT_CONVERGED;
+    }
+
+    int observables(lb3e_observables_t* o) override {
+        timer.begin(stream_, KC_REDUCE);
+        k_observables<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.phi, d_.q, d_.E, d_.diag, d_.partial);
+        TRY(launched());
+        timer.begin(stream_, KC_REDUCE);
+        k_reduce_partials<NOBS><<<1, 256, 0, stream_>>>(d_.partial, nblk_, d_.result);
+        TRY(launched());
+        timer.begin(stream_, KC_REDUCE);
+        k_maxdev<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.phi, d_.partial);
+        TRY(launched());
+        timer.begin(stream_, KC_REDUCE);
+        k_max_partials<<<1, 256, 0, stream_>>>(d_.partial, nblk_, d_.result + NOBS);
+        TRY(launched());
+        if (cudaMemcpyAsync(pinned_, d_.result, (NOBS + 1) * sizeof(double), cudaMemcpyDeviceToHost, stream_) !=
+            cudaSuccess)
+            return LB3E_ERR_CUDA;
+        TRY(sync());
+        const double* v = pinned_;
+        std::memset(o, 0, sizeof(*o));
+        for (int i = 0; i < 3; ++i) o->mass[i] = v[i];
+        o->charge = v[3];
+        for (int k = 0; k < 4; ++k) o->free_energy[k] = v[4 + k];
+        o->nonfinite = (int64_t)v[8];
+        double Dk[2];
+        for (int k = 0; k < 2; ++k) {
+            const double* m = v + 9 + 5 * k;
+            const double A = m[0];
+            if (!(A > 0)) { Dk[k] = 0.0; continue; }
+            const double xc = m[1] / A, yc = m[2] / A;
+            const double Ixx = m[3] / A - xc * xc, Iyy = m[4] / A - yc * yc;
+            const double a = 2.0 * std::sqrt(Iyy > 0 ? Iyy : 0.0), b = 2.0 * std::sqrt(Ixx > 0 ? Ixx : 0.0);
+            Dk[k] = (a + b) > 0 ? (a - b) / (a + b) : 0.0;
+        }
+        o->D_inner = Dk[0];
+        o->D_outer = Dk[1];
+        o->max_sum_dev = v[NOBS];
+        o->poisson_residual = last_res_;
+        o->poisson_iters = last_iters_;
+        o->poisson_converged = last_conv_;
+        o->step = step_;
+        return LB3E_OK;
+    }
+
+    int get_field(int id, double* dst) override {
+        const R* src = nullptr;
+        switch (id) {
+            case LB3E_FIELD_PHI1: case LB3E_FIELD_PHI2: case LB3E_FIELD_PHI3: src = d_.phi + (id - LB3E_FIELD_PHI1) * N_; break;
+            case LB3E_FIELD_UX: src = d_.diag; break;
+            case LB3E_FIELD_UY: src = d_.diag + N_; break;
+            case LB3E_FIELD_P: src = d_.diag + 2 * N_; break;
+            case LB3E_FIELD_Q: src = d_.q; break;
+            case LB3E_FIELD_EX: src = d_.E; break;
+            case LB3E_FIELD_EY: src = d_.E + N_; break;
+            case LB3E_FIELD_MU1: case LB3E_FIELD_MU2: case LB3E_FIELD_MU3: src = d_.diag + (3 + id - LB3E_FIELD_MU1) * N_; break;
+            case LB3E_FIELD_PSI:
+                timer.begin(stream_, KC_FIELDS);
+                k_potential_fields<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[hcur_], d_.eps, d_.E, d_.stage);
+                TRY(launched());
+                return copy_out(dst, d_.stage);
+            case LB3E_FIELD_PHINOW1: case LB3E_FIELD_PHINOW2: case LB3E_FIELD_PHINOW3: case LB3E_FIELD_QTILDE: {
+                // moments of the current populations into scratch planes of the other buffer's view
+                R* tmp = reinterpret_cast<R*>(d_.stage + 5 * N_);  // 4 N R-values fit in 4 N doubles
+                timer.begin(stream_, KC_MOMENTS);
+                k_moments<R, S><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.pop[cur_], d_.phi, tmp, tmp + 3 * N_);
+                TRY(launched());
+                const R* t = id == LB3E_FIELD_QTILDE ? tmp + 3 * N_ : tmp + (id - LB3E_FIELD_PHINOW1) * N_;
+                timer.begin(stream_, KC_OTHER);
+                k_to_f64<R><<<blocks1(N_), 256, 0, stream_>>>(d_.stage, t, N_);
+                TRY(launched());
+                return copy_out(dst, d_.stage);
+            }
+            default: break;
+        }
+        if (!src && id >= LB3E_FIELD_POP && id < LB3E_FIELD_POP + 54) {
+            const int set = (id - LB3E_FIELD_POP) / 9, j = (id - LB3E_FIELD_POP) % 9;
+            if (set < 5) {
+                timer.begin(stream_, KC_OTHER);
+                k_pop_to_f64<R, S><<<blocks1(N_), 256, 0, stream_>>>(d_.stage, d_.pop[cur_], d_.phi, set, j, N_);
+            } else {
+                timer.begin(stream_, KC_OTHER);
+                k_to_f64<R><<<blocks1(N_), 256, 0, stream_>>>(d_.stage, d_.h[hcur_] + j * N_, N_);
+            }
+            TRY(launched());
+            return copy_out(dst, d_.stage);
+        }
+        if (!src) return LB3E_ERR_FIELD;
+        timer.begin(stream_, KC_OTHER);
+        k_to_f64<R><<<blocks1(N_), 256, 0, stream_>>>(d_.stage, src, N_);
+        TRY(launched());
+        return copy_out(dst, d_.stage);
+    }
+
+    // snapshot: current pops, current h, then phi..psi_prev fields, then a trailer
+    size_t state_bytes() const override {
+        return 45 * N_ * sizeof(S) + 9 * N_ * sizeof(R) + fields_bytes() + 4 * sizeof(int64_t);
+    }
+    int save(void* dst) override {
+        char* o = static_cast<char*>(dst);
+        TRY(copy(o, d_.pop[cur_], 45 * N_ * sizeof(S)));
+        o += 45 * N_ * sizeof(S);
+        TRY(copy(o, d_.h[hcur_], 9 * N_ * sizeof(R)));
+        o += 9 * N_ * sizeof(R);
+        TRY(copy(o, base_ + L_.phi, fields_bytes()));
+        o += fields_bytes();
+        int64_t trailer[4] = {step_, last_iters_, last_conv_, 0};
+        std::memcpy(&trailer[3], &last_res_, sizeof(double));
+        TRY(copy(o, trailer, sizeof trailer));
+        return sync();
+    }
+    int load(const void* src) override {
+        const char* s = static_cast<const char*>(src);
+        cur_ = 0;
+        hcur_ = 0;
+        TRY(copy(d_.pop[0], s, 45 * N_ * sizeof(S)));
+        s += 45 * N_ * sizeof(S);
+        TRY(copy(d_.h[0], s, 9 * N_ * sizeof(R)));
+        s += 9 * N_ * sizeof(R);
+        TRY(copy(base_ + L_.phi, s, fields_bytes()));
+        s += fields_bytes();
+        int64_t trailer[4];
+        TRY(copy(trailer, s, sizeof trailer));
+        TRY(sync());
+        step_ = trailer[0];
+        last_iters_ = (int)trailer[1];
+        last_conv_ = (int)trailer[2];
+        std::memcpy(&last_res_, &trailer[3], sizeof(double));
+        return LB3E_OK;
+    }
+
+    int kernel_times(double* ms, int64_t* counts) override {
+        TRY(sync());
+        timer.collect();
+        for (int k = 0; k < KC_COUNT; ++k) {
+            if (ms) ms[k] = timer.ms[k];
+            if (counts) counts[k] = timer.n[k];
+            timer.ms[k] = 0.0;
+            timer.n[k] = 0;
+        }
+        return LB3E_OK;
+    }
+
+  private:
+    size_t fields_bytes() const { return L_.psi_prev + align256(3 * N_ * sizeof(R)) - L_.phi; }
+    static unsigned blocks1(size_t n) { return (unsigned)((n + 255) / 256); }
+    int launched() {
+        ++launches;
+        timer.end(stream_);
+        return cudaGetLastError() == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
+    }
+    int sync() { return cudaStreamSynchronize(stream_) == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA; }
+    int memset_async(void* p, size_t b) { return cudaMemsetAsync(p, 0, b, stream_) == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA; }
+    int copy(void* d, const void* s, size_t b) {
+        return cudaMemcpyAsync(d, s, b, cudaMemcpyDefault, stream_) == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
+    }
+    // host-or-device doubles -> R field, through the staging area (chunks of 9 N)
+    int upload(const double* src, size_t n, R* dst) {
+        for (size_t off = 0; off < n; off += 9 * N_) {
+            const size_t m = (n - off) < 9 * N_ ? (n - off) : 9 * N_;
+            TRY(copy(d_.stage, src + off, m * sizeof(double)));
+            timer.begin(stream_, KC_OTHER);
+            k_from_f64<R><<<blocks1(m), 256, 0, stream_>>>(dst + off, d_.stage, m);
+            TRY(launched());
+        }
+        return LB3E_OK;
+    }
+    int copy_out(double* dst, const double* dsrc) {
+        TRY(copy(dst, dsrc, N_ * sizeof(double)));
+        return sync();
+    }
+
+    // the pseudo-time potential solve (Eq. 43) from the current h
+    int poisson(double tol, int max_iter, int fixed, int check) {
+        const int n = fixed > 0 ? fixed : max_iter;
+        if (check < 1) check = 1;
+        last_res_ = -1.0;
+        last_conv_ = fixed > 0;
+        last_iters_ = n;
+        for (int k = 1; k <= n; ++k) {
+            const int do_check = fixed <= 0 && k >= 2 && k % check == 0;
+            const int save = fixed <= 0 && (k + 1) % check == 0;
+            timer.begin(stream_, KC_POISSON);
+            k_poisson<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q,
+                                                               d_.psi_prev, d_.partial, save, do_check);
+            TRY(launched());
+            if (do_check) {
+                timer.begin(stream_, KC_REDUCE);
+                k_reduce_partials<4><<<1, 256, 0, stream_>>>(d_.partial, nblk_, d_.result);
+                TRY(launched());
+                if (cudaMemcpyAsync(pinned_, d_.result, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream_) !=
+                    cudaSuccess)
+                    return LB3E_ERR_CUDA;
+                TRY(sync());
+                const double dp = pinned_[0], pp = pinned_[1], dj = pinned_[2], jj = pinned_[3];
+                const double r1 = pp > 0.0 ? std::sqrt(dp) / std::sqrt(pp) : (dp > 0.0 ? INFINITY : 0.0);
+                const double r2 = jj > 0.0 ? std::sqrt(dj) / std::sqrt(jj) : (dj > 0.0 ? INFINITY : 0.0);
+                last_res_ = r1 > r2 ? r1 : r2;
+                if (last_res_ <= tol) {  // the state before this iteration's collision is the answer
+                    last_conv_ = 1;
+                    last_iters_ = k - 1;
+                    break;
+                }
+            }
+            hcur_ ^= 1;
+        }
+        timer.begin(stream_, KC_FIELDS);
+        k_potential_fields<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[hcur_], d_.eps, d_.E, nullptr);
+        return launched();
+    }
+
+    lb3e_params p_;
+    cudaStream_t stream_;
+    Layout L_;
+    DevState<R, S> d_{};
+    DevParams dp_{};
+    char* base_ = nullptr;
+    size_t N_ = 0;
+    dim3 grid2_;
+    int nblk_ = 0;
+    int cur_ = 0, hcur_ = 0;
+    int64_t step_ = 0;
+    int last_iters_ = 0, last_conv_ = 0;
+    double last_res_ = -1.0;
+    double* pinned_ = nullptr;
+};
+
+}  // namespace lb3e

@@ -1,0 +1,73 @@
+"""The C ABI library loads and exports every entry point include/lb3e.h declares,
+and its host-side validation works without a GPU (no compute calls here)."""
+import ctypes as C
+import re
+from pathlib import Path
+
+import pytest
+
+import paper_2608_05787_b300 as L
+import workloads as W
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+def declared_functions():
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        names |= set(re.findall(r"\b(lb3e_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for fn in ("lb3e_init", "lb3e_step", "lb3e_solve_potential", "lb3e_observables", "lb3e_get_field"):
+        assert fn in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2608_05787_b300 import build
+    build.build()
+    lib = C.CDLL(str(L.LIB_PATH))
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """ctypes mirrors of lb3e_params / lb3e_observables_t have the C compiler's
+    size and every field offset."""
+    import subprocess
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "lb3e.h"', "int main(void) {"]
+    for cname, py in (("lb3e_params", L.Params), ("lb3e_observables_t", L.Observables)):
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", str(ROOT / "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = []
+    for py in (L.Params, L.Observables):
+        want.append(C.sizeof(py))
+        want += [getattr(py, f).offset for f, _ in py._fields_]
+    assert got == want
+
+
+@pytest.mark.parametrize("bad", [dict(tau_f=0.5), dict(nx=1), dict(bc_y=3), dict(precision=7),
+                                 dict(gamma23=3e-3), dict(eps=(1.0, 0.0, 2.0)), dict(sigma=(-1, 0, 0)),
+                                 dict(inner_phase=0), dict(V_top=float("nan"))])
+def test_invalid_parameters_rejected(bad):
+    with pytest.raises(L.LB3EError) as e:
+        L.workspace_bytes(W.params(**bad))
+    assert e.value.code == -1
+
+
+def test_workspace_scales_with_precision():
+    p = W.params(nx=256, ny=128)
+    b64 = L.workspace_bytes(dict(p, precision=0))
+    b32 = L.workspace_bytes(dict(p, precision=1))
+    b16 = L.workspace_bytes(dict(p, precision=2))
+    assert b64 > b32 > b16 > 256 * 128 * 45 * 2 * 2

@@ -1,0 +1,152 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+FP64 GPU: <= 1e-12 relative L-infinity per field.  FP32: <= 1e-5.  FP16-stored
+populations: <= 1e-3.  Relative L-infinity = max |gpu - oracle| / max |oracle|
+(fields that vanish identically in the oracle are compared absolutely).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ["phi1", "phi2", "phi3", "ux", "uy", "p", "q", "psi", "ex", "ey", "mu1", "mu2", "mu3",
+          "phinow1", "phinow2", "phinow3", "qtilde"]
+
+
+def _lb():
+    import paper_2608_05787_b300 as L
+    return L
+
+
+def rel_linf(a, b, floor=1e-300):
+    scale = np.abs(b).max()
+    if scale < floor:
+        return np.abs(a - b).max()
+    return np.abs(a - b).max() / scale
+
+
+def field_errors(sim, orc, fields=FIELDS):
+    return {f: rel_linf(sim.field(f), orc.field(f)) for f in fields}
+
+
+def run_pair(params, phi, steps, u=None, q=None, noise=None):
+    L = _lb()
+    sim = L.Sim(params, phi, u=u, q=q, noise=noise)
+    orc = oracle.Oracle(params, phi, u=u, q=q, noise=noise)
+    if steps:
+        sim.step(steps)
+        orc.step(steps)
+    return sim, orc
+
+
+def assert_fields(sim, orc, tol, fields=FIELDS):
+    errs = field_errors(sim, orc, fields)
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, f"fields above {tol}: {bad}"
+    return errs
+
+
+# ------------------------------------------------------------------ FP64 parity
+def test_fp64_static_compound_short_fixed_iterations():
+    """64x64 compound drop with electrodes, fixed potential iteration counts,
+    every field after 25 steps."""
+    cfg = W.config_static_compound(precision=0)
+    p = dict(cfg["params"], poisson_fixed_iter=40)
+    sim, orc = run_pair(p, cfg["phi"], 25, noise=cfg["noise"])
+    assert_fields(sim, orc, 1e-12)
+
+
+@pytest.mark.parametrize("bc_y", [0, 1, 2])
+def test_fp64_ragged_grid_all_terms(bc_y):
+    """Grid that is not a multiple of the tile (53 x 37), every optional term on:
+    per-phase viscosity, unequal densities, moving walls, external field, initial
+    velocity and charge, charge convection, noise; 30 steps, residual-based solve."""
+    nx, ny = 53, 37
+    rng = np.random.default_rng(7)
+    p = W.params(nx=nx, ny=ny, bc_y=bc_y, electric=1, precision=0, rho=(1.0, 1.4, 0.7),
+                 visc=(0.1, 0.05, 0.2), gamma12=1e-3, gamma13=8e-4, gamma23=6e-4,
+                 eps=(1.0, 3.0, 2.0), sigma=(0.5, 0.1, 1.0), eps_ref=2.0, V_bottom=0.02, V_top=-0.01,
+                 E_ext=(1e-3, 0.0), u_wall_bottom=-2e-4 if bc_y else 0.0, u_wall_top=3e-4 if bc_y else 0.0,
+                 poisson_tol=1e-10, poisson_check_every=3, inner_phase=3, matrix_phase=1)
+    phi = W.compound_droplet(nx, ny, 6.0, 12.0, 4.0, xc=25.3, yc=17.6)
+    u = rng.uniform(-1e-4, 1e-4, size=(2, ny, nx))
+    q = rng.uniform(-1e-4, 1e-4, size=(ny, nx))
+    sim, orc = run_pair(p, phi, 30, u=u, q=q, noise=W.noise(nx, ny, 1e-7, seed=3))
+    assert_fields(sim, orc, 1e-12)
+    assert sim.observables()["poisson_iters"] == orc.observables()["poisson_iters"]
+
+
+def test_fp64_populations_match():
+    """Raw populations of every set (including h) after 10 steps."""
+    n = 40
+    p = W.params(nx=n, ny=24, bc_y=2, V_top=0.05, poisson_fixed_iter=15, precision=0)
+    phi = W.compound_droplet(n, 24, 5.0, 9.0, 4.0)
+    sim, orc = run_pair(p, phi, 10, noise=W.noise(n, 24, 1e-8))
+    for s in ("g", "f1", "f2", "f3", "l", "h"):
+        for j in range(9):
+            assert rel_linf(sim.pop(s, j), orc.pop(s, j)) <= 1e-12, (s, j)
+
+
+def test_fp64_tiny_and_field_off():
+    """Degenerate sizes (3 x 2, 2 x 5) and the field switched off."""
+    for nx, ny, bc in ((3, 2, 1), (2, 5, 0), (4, 2, 2)):
+        p = W.params(nx=nx, ny=ny, bc_y=bc, electric=1 if bc == 2 else 0, V_top=0.01, precision=0,
+                     poisson_fixed_iter=5)
+        rng = np.random.default_rng(nx * 10 + ny)
+        phi = rng.dirichlet([1, 1, 1], size=(ny, nx)).transpose(2, 0, 1).copy()
+        sim, orc = run_pair(p, phi, 6)
+        assert_fields(sim, orc, 1e-12)
+
+
+def test_fp64_observables_match():
+    cfg = W.config_static_compound(precision=0, n=48)
+    p = dict(cfg["params"], poisson_fixed_iter=30)
+    sim, orc = run_pair(p, cfg["phi"], 15)
+    a, b = sim.observables(), orc.observables()
+    for k in ("mass1", "mass2", "mass3", "F_phi", "F_E", "F_u", "F_q", "max_sum_dev"):
+        assert abs(a[k] - b[k]) <= 1e-11 * max(abs(b[k]), 1e-30), (k, a[k], b[k])
+    # D = (a - b)/(a + b) of two nearly equal radii: compared absolutely (it is O(1)-scaled)
+    for k in ("D_inner", "D_outer"):
+        assert abs(a[k] - b[k]) <= 1e-12, (k, a[k], b[k])
+    assert abs(a["charge"] - b["charge"]) <= 1e-11 * np.abs(orc.field("q")).sum()
+    assert a["step"] == b["step"] == 15 and a["nonfinite"] == 0
+
+
+@pytest.mark.slow
+def test_fp64_static_compound_full_run():
+    """The stated 64x64 run: 2000 steps, residual-controlled solve to 1e-8."""
+    cfg = W.config_static_compound(precision=0)
+    sim, orc = run_pair(cfg["params"], cfg["phi"], cfg["steps"], noise=cfg["noise"])
+    errs = assert_fields(sim, orc, 1e-12)
+    assert sim.observables()["poisson_iters"] == orc.observables()["poisson_iters"]
+    print("fp64 2000-step errors", errs)
+
+
+# ------------------------------------------------------------------ reduced precision
+@pytest.mark.parametrize("precision,tol", [(1, 1e-5), (2, 1e-3)])
+def test_reduced_precision_static_compound(precision, tol):
+    """FP32 and FP16-stored populations against the FP64 oracle, 200 steps of the
+    64x64 compound drop (fixed iteration counts so both do the same work)."""
+    cfg = W.config_static_compound(precision=precision)
+    p = dict(cfg["params"], poisson_fixed_iter=60)
+    sim, orc = run_pair(p, cfg["phi"], 200, noise=cfg["noise"])
+    errs = field_errors(sim, orc, ["phi1", "phi2", "phi3", "phinow1", "phinow2", "phinow3"])
+    assert max(errs.values()) <= tol, errs
+
+
+def test_state_save_load_roundtrip():
+    L = _lb()
+    cfg = W.config_static_compound(precision=1, n=32)
+    p = dict(cfg["params"], poisson_fixed_iter=10)
+    sim = L.Sim(p, cfg["phi"], noise=cfg["noise"])
+    sim.step(5)
+    snap = sim.save_state()
+    sim.step(7)
+    a = sim.field("phinow1")
+    sim.load_state(snap)
+    sim.step(7)
+    assert np.array_equal(a, sim.field("phinow1"))
+    assert sim.observables()["step"] == 12

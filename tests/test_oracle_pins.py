@@ -121,6 +121,51 @@ def test_reduction_consistency_absent_phase_stays_zero():
     assert np.abs(o.field("phinow2")).max() > 0.9
 
 
+def test_wide_interface_relaxes_toward_equilibrium_profile():
+    """Eq. 27c-28 through Eq. 34-36: a flat binary interface started twice as wide
+    as D relaxes, by mobility-driven diffusion, toward the tanh(2 y/D) profile that
+    minimises Eq. 18: the central slope rises monotonically from 1/(2D) toward the
+    discrete equilibrium slope and never overshoots it.  With lambda_1 = lambda_2
+    the off-diagonal M_12 carries half the flux, so a sign slip in it (the two
+    fluxes cancelling) leaves the profile wide."""
+    nx, ny, D = 4, 48, 4.0
+    p = W.params(nx=nx, ny=ny, bc_y=1, electric=0, gamma12=1e-2, gamma13=1e-2, gamma23=1e-2,
+                 width_D=D, tau_f=1.0)
+    o = oracle.Oracle(p, W.flat_interface(nx, ny, 2 * D, 1, 2))
+    eq = np.diff(W.flat_interface(nx, ny, D, 1, 2)[1][:, 0]).max()
+    slopes = []
+    for T in (0, 500, 1000, 2000):
+        o.step(T - o.steps_done)
+        slopes.append(np.diff(o.field("phinow2")[:, 0]).max())
+    assert abs(slopes[0] * D - 0.5) < 0.01
+    assert all(b > a for a, b in zip(slopes, slopes[1:]))
+    assert 0.72 * eq < slopes[-1] < eq
+
+
+def test_drop_carried_by_uniformly_accelerating_fluid():
+    """Coulomb force qE of Eq. 27b and the d/dt(phi u) source of Eq. 36: a uniform
+    charge in a uniform field accelerates the whole (equal-density) fluid at
+    a = qE/rho, and a drop is carried along: its centroid moves by the time
+    integral of u (the trapezoid rule is exact for u linear in t), to 1e-3."""
+    n, q0, E, T = 64, 1e-3, 1e-3, 300
+    p = W.params(nx=n, ny=n, bc_y=0, electric=0, sigma=(0, 0, 0), E_ext=(E, 0.0), alpha=0.02)
+    phi = W.compound_droplet(n, n, 0.0, 10.0, 4.0)
+    phi[1] += phi[2]
+    phi[2] = 0.0
+    o = oracle.Oracle(p, phi, q=np.full((n, n), q0))
+    x = np.arange(n, dtype=float)[None, :]
+    cen = lambda f: (f * x).sum() / f.sum()
+    c0 = cen(o.field("phinow2"))
+    us = []
+    for _ in range(T):
+        o.step(1)
+        us.append(o.field("ux").mean())
+    assert abs(us[-1] - us[-2] - q0 * E) < 1e-3 * q0 * E          # uniform acceleration a = qE/rho
+    us.append(2 * us[-1] - us[-2])
+    travel = sum(0.5 * (us[k] + us[k + 1]) for k in range(T))
+    assert abs((cen(o.field("phinow2")) - c0) / travel - 1) < 1e-3
+
+
 @pytest.mark.parametrize("bc_y", [0, 1, 2])
 def test_per_phase_mass_conserved_to_roundoff(bc_y):
     """Sum_j F_j^i = 0, sum_j f^eq = phi_i, and bounce-back/periodic streaming move
