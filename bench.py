@@ -117,7 +117,7 @@ class Clocks:
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if len(r) > 5 + k and "Active" in r[5 + k]})
+        reasons = sorted({names[k] for r in rows for k in range(4) if len(r) > 5 + k and r[5 + k].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
 
@@ -137,21 +137,31 @@ def _oracle_sample(n: int, iters: int):
     return oracle.Oracle(dict(cfg["params"], poisson_fixed_iter=iters), cfg["phi"])
 
 
-def cpu_baseline(args, iters_per_step: float):
-    """The oracle, as it stands, on the host cores: one time step of a bounded
-    sample of the workload (a cpu_sample^2 lattice with the geometry scaled, and
-    the potential iterations per step the GPU needed), after an untimed init."""
-    n = args.cpu_sample
-    it = args.cpu_iters or max(1, int(round(iters_per_step)))
-    o = _oracle_sample(n, it)
+def _timed_oracle_step(n: int, iters: int) -> float:
+    o = _oracle_sample(n, iters)
     t0 = time.perf_counter()
     o.step(1)
-    dt = time.perf_counter() - t0
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(args, iters_per_step: float):
+    """The oracle, as it stands, on the host cores, on a bounded sample of the
+    workload: a cpu_sample^2 lattice with the geometry scaled.  One step is timed
+    with 2 and with 6 potential iterations (init untimed); the difference gives the
+    cost of one iteration, and the step time is projected to the potential
+    iterations per step that the GPU needed."""
+    n = args.cpu_sample
+    t2 = _timed_oracle_step(n, 2)
+    t6 = _timed_oracle_step(n, 6)
+    per_iter = max(0.0, (t6 - t2) / 4.0)
+    base = max(1e-9, t2 - 2 * per_iter)
+    it = args.cpu_iters or iters_per_step
+    dt = base + it * per_iter
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": n * n / dt / 1e6, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": f"1 step of a {n}x{n} lattice of the same workload (radii scaled), "
-                      f"{it} potential iterations per step (the GPU's mean), init untimed",
-            "seconds": dt}
+            "sample": f"{n}x{n} lattice of the same workload (radii scaled): one step timed with 2 and 6 "
+                      f"potential iterations, projected to {it:.1f} iterations per step (the GPU's mean); init untimed",
+            "seconds_per_step": dt, "seconds_per_potential_iteration": per_iter, "seconds_rest_of_step": base}
 
 
 def run_reference(args):
