@@ -44,7 +44,8 @@ enum {
     LB3E_ERR_CUDA = -3,           /* a CUDA call failed; the handle may be unusable */
     LB3E_ERR_NOT_CONVERGED = -4,  /* potential solve hit max_iter above tol */
     LB3E_ERR_FIELD = -5,          /* unknown field id */
-    LB3E_ERR_NULL = -6            /* NULL handle or output pointer */
+    LB3E_ERR_NULL = -6,           /* NULL handle or output pointer */
+    LB3E_ERR_TOO_LARGE = -7       /* lattice larger than lb3e_observables_noalloc's fixed scratch */
 };
 
 /* Field ids for lb3e_get_field.  "Last step" fields hold the values computed
@@ -182,6 +183,33 @@ enum {
  * milliseconds (ms[LB3E_KC_COUNT]) and the number of timed launches
  * (launches[LB3E_KC_COUNT]) since the last call; the totals are then cleared. */
 int lb3e_kernel_times(lb3e_handle* h, double* ms, int64_t* launches);
+
+/* Largest lattice (nx * ny cells) lb3e_observables_noalloc accepts. */
+#define LB3E_NOALLOC_MAX_CELLS (2048 * 2048)
+
+/* The reductions of lb3e_observables for callers that cannot allocate device
+ * memory -- for instance code running under a memory pool that must not grow,
+ * inside an allocator owned by another framework, or in a monitoring hook that
+ * must leave the caller's memory untouched.  The paper has no counterpart: this is
+ * a deployment convenience around the same FP64 reductions.
+ *
+ * Inputs are the caller's FP64 device fields of one lattice: phi [3][ny][nx],
+ * q [ny][nx], E [2][ny][nx], u [2][ny][nx]; params gives nx, ny, bc_y, the
+ * phase properties, width_D and inner/matrix_phase.  No handle or workspace is
+ * used and nothing is allocated: the scratch is a fixed array of the library
+ * (about 2.5 MB per GPU that loads the library, held until the process exits).
+ * Results are written to *out (host); poisson_* and step are left at -1 / 0.
+ *
+ * The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current); make that first call before
+ * any stream capture.  All calls share the one array, so calls that overlap on
+ * the GPU (different streams or threads, same device) race; serialise them.
+ * Each call overwrites what the previous one left there.
+ * Errors: NULL, PARAM, TOO_LARGE (nx * ny > LB3E_NOALLOC_MAX_CELLS), CUDA.
+ * Synchronises `stream`. */
+int lb3e_observables_noalloc(const lb3e_params* params, const double* phi, const double* q,
+                             const double* E, const double* u, void* stream,
+                             lb3e_observables_t* out);
 
 /* Release the host-side handle (the workspace stays the caller's). */
 void lb3e_destroy(lb3e_handle* h);

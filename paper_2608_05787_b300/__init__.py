@@ -105,6 +105,7 @@ def lib() -> C.CDLL:
         L.lb3e_launch_count.argtypes = [vp]
         L.lb3e_set_timing.argtypes = [vp, C.c_int32]
         L.lb3e_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64)]
+        L.lb3e_observables_noalloc.argtypes = [C.POINTER(Params), vp, vp, vp, vp, vp, C.POINTER(Observables)]
         L.lb3e_destroy.argtypes = [vp]
         L.lb3e_destroy.restype = None
         L.lb3e_status_string.restype = C.c_char_p
@@ -140,6 +141,23 @@ def _addr(a):
         a = a.contiguous().to(torch.float64)
         return a.data_ptr(), a
     raise TypeError(type(a))
+
+
+def observables_noalloc(params: dict, phi, q, E, u, stream=None) -> dict:
+    """The observables reductions on caller-provided FP64 CUDA tensors, for callers
+    that cannot allocate device memory: the scratch is a fixed array inside the
+    library (lattices up to 2048 x 2048).  phi [3,ny,nx], q [ny,nx], E and u
+    [2,ny,nx], all contiguous float64 on the current device."""
+    import torch
+    for t in (phi, q, E, u):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError("lb3e_observables_noalloc takes contiguous float64 CUDA tensors")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    o = Observables()
+    _check("lb3e_observables_noalloc",
+           lib().lb3e_observables_noalloc(C.byref(Params.from_dict(params)), phi.data_ptr(), q.data_ptr(),
+                                          E.data_ptr(), u.data_ptr(), st.cuda_stream, C.byref(o)))
+    return o.as_dict()
 
 
 class Sim:

@@ -159,6 +159,7 @@ const char* lb3e_status_string(int status) {
         case LB3E_ERR_NOT_CONVERGED: return "potential solve did not reach the tolerance";
         case LB3E_ERR_FIELD: return "unknown field id";
         case LB3E_ERR_NULL: return "NULL handle or pointer";
+        case LB3E_ERR_TOO_LARGE: return "lattice larger than the fixed scratch of lb3e_observables_noalloc";
         default: return "unknown status";
     }
 }
