@@ -71,12 +71,17 @@ enum {
     LB3E_FIELD_POP = 100     /* + 9*set + j; sets 0 g, 1-3 f^1..f^3, 4 l, 5 h */
 };
 
+/* Largest lattice lb3e_init accepts (45 population planes are addressed with
+ * 32-bit offsets). */
+#define LB3E_MAX_CELLS 40000000
+
 /* Model and run parameters.  Index i of the per-phase arrays is phase i+1. */
 typedef struct lb3e_params {
-    int32_t nx, ny;               /* lattice, cells; both >= 2; periodic in x */
+    int32_t nx, ny;               /* lattice, cells; both >= 2, nx * ny <= LB3E_MAX_CELLS; periodic in x */
     int32_t bc_y;                 /* 0 periodic, 1 half-way walls, 2 walls with electrodes */
     int32_t electric;             /* 1: solve the potential every step; 0: E = E_ext */
-    int32_t precision;            /* 0 fp64; 1 fp32; 2 fp32 compute, fp16-stored populations */
+    int32_t precision;            /* 0 fp64; 1 fp32; 2 fp32 compute, fp16-stored populations;
+                                     3 fp32 with 3 tangent directions; 4 fp64 with 1 tangent */
     int32_t _pad0;
     double rho[3];                /* phase densities, Eq. 29 */
     double visc[3];               /* phase dynamic viscosities, Eq. 29; all <= 0: use tau_g */
@@ -101,7 +106,17 @@ typedef struct lb3e_params {
     int32_t poisson_check_every;  /* residual evaluated every this many iterations */
     int32_t poisson_fixed_iter;   /* > 0: exactly this many iterations, no residual */
     int32_t _pad2;
+    /* precision 3 and 4 only: the parameter each tangent direction (3, or the
+     * first only for precision 4) differentiates (-1 none; 0 V_top; 1, 2, 3 eps[0..2]; 4, 5, 6 gamma12,
+     * gamma13, gamma23).  Fields are then available per direction (see
+     * LB3E_TANGENT). */
+    int32_t tangent_param[3];
+    int32_t _pad3;
 } lb3e_params;
+
+/* Field id offset of tangent k (1..3) of a field in the tangent builds: field
+ * f's derivative along direction k is field f + k * LB3E_TANGENT. */
+#define LB3E_TANGENT 1000
 
 typedef struct lb3e_observables_t {
     double mass[3];          /* sum phi_i of the last step */
@@ -162,6 +177,10 @@ int lb3e_load_state(lb3e_handle* h, const void* src);
 /* Number of kernel launches issued since lb3e_init (for launch accounting). */
 int64_t lb3e_launch_count(const lb3e_handle* h);
 
+/* Pseudo-iterations of the potential solve (Eq. 43) executed since lb3e_init,
+ * over all solves (a launch may run several). */
+int64_t lb3e_potential_iterations(const lb3e_handle* h);
+
 /* Kernel timing with CUDA events recorded on the simulation's stream around each
  * launch (off by default; costs two event records per launch).  Enabling or
  * disabling clears the totals. */
@@ -183,6 +202,44 @@ enum {
  * milliseconds (ms[LB3E_KC_COUNT]) and the number of timed launches
  * (launches[LB3E_KC_COUNT]) since the last call; the totals are then cleared. */
 int lb3e_kernel_times(lb3e_handle* h, double* ms, int64_t* launches);
+
+/* ---- Batches: many lattices stepped together (parameter sweeps) ----
+ * Instances of one precision, each with its own size and parameters, are
+ * advanced in lockstep: every kernel of a time step is one launch over the tiles
+ * of all instances, and pairs of steps are replayed as one CUDA graph.  Every
+ * instance with electric = 1 must use the same poisson_fixed_iter (> 0): the
+ * potential is iterated a fixed number of times per step, so all instances do
+ * the same work and the graph is fixed.  Each instance starts as lb3e_init would
+ * start it with u = q = 0 and no noise.  The device workspace is the caller's. */
+typedef struct lb3e_batch lb3e_batch;
+
+/* Device bytes for n instances (params[n]).  Errors: NULL, PARAM. */
+int lb3e_batch_workspace_bytes(const lb3e_params* params, int32_t n, size_t* bytes);
+
+/* Create and initialise n instances; phi_init[i] is instance i's [3][ny][nx]
+ * phase field (host or device).  Errors: NULL, PARAM, WORKSPACE, CUDA. */
+int lb3e_batch_create(const lb3e_params* params, int32_t n, const double* const* phi_init, void* workspace,
+                      size_t workspace_bytes, void* stream, lb3e_batch** out);
+
+/* Advance every instance nsteps time steps (synchronises the stream). */
+int lb3e_batch_run(lb3e_batch* b, int32_t nsteps);
+
+/* Observables of every instance into out[n] (D_inner, D_outer, ...). */
+int lb3e_batch_observables(lb3e_batch* b, lb3e_observables_t* out);
+
+/* One field of one instance, as lb3e_get_field. */
+int lb3e_batch_get_field(lb3e_batch* b, int32_t instance, int32_t field_id, double* dst);
+
+/* Pseudo-iterations of the potential per launch for this batch: 1 (one launch
+ * per iteration) up to 8 (temporally blocked: several iterations on a tile held
+ * in shared memory).  The result does not depend on it; the speed does.
+ * Errors: NULL, PARAM (out of range), CUDA. */
+int lb3e_batch_set_potential_chunk(lb3e_batch* b, int32_t iterations_per_launch);
+
+/* Kernel launches issued for this batch (graph nodes counted per replay). */
+int64_t lb3e_batch_launch_count(const lb3e_batch* b);
+
+void lb3e_batch_destroy(lb3e_batch* b);
 
 /* Largest lattice (nx * ny cells) lb3e_observables_noalloc accepts. */
 #define LB3E_NOALLOC_MAX_CELLS (2048 * 2048)

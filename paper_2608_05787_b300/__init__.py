@@ -19,7 +19,9 @@ FIELDS = dict(phi1=0, phi2=1, phi3=2, ux=3, uy=4, p=5, q=6, psi=7, ex=8, ey=9,
               mu1=10, mu2=11, mu3=12, phinow1=13, phinow2=14, phinow3=15, qtilde=16)
 SETS = dict(g=0, f1=1, f2=2, f3=3, l=4, h=5)
 POP_BASE = 100
-PRECISIONS = {0: "f64", 1: "f32", 2: "f32-compute/f16-store"}
+PRECISIONS = {0: "f64", 1: "f32", 2: "f32-compute/f16-store", 3: "f32 + 3 tangents", 4: "f64 + 1 tangent"}
+TANGENT = 1000
+TANGENT_PARAMS = dict(V_top=0, eps1=1, eps2=2, eps3=3, gamma12=4, gamma13=5, gamma23=6)
 
 KERNEL_CLASSES = ("moments", "prologue", "poisson", "reduce", "fields", "fused", "other")
 
@@ -39,6 +41,7 @@ class Params(C.Structure):
         ("_pad1", C.c_int32),
         ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int32),
         ("poisson_check_every", C.c_int32), ("poisson_fixed_iter", C.c_int32), ("_pad2", C.c_int32),
+        ("tangent_param", C.c_int32 * 3), ("_pad3", C.c_int32),
     ]
 
     @classmethod
@@ -49,7 +52,8 @@ class Params(C.Structure):
                 continue
             v = d[name]
             if hasattr(ctype, "_length_"):
-                getattr(s, name)[:] = [float(a) for a in v]
+                conv = int if ctype._type_ is C.c_int32 else float
+                getattr(s, name)[:] = [conv(a) for a in v]
             else:
                 setattr(s, name, v)
         return s
@@ -103,9 +107,22 @@ def lib() -> C.CDLL:
         L.lb3e_load_state.argtypes = [vp, vp]
         L.lb3e_launch_count.restype = C.c_int64
         L.lb3e_launch_count.argtypes = [vp]
+        L.lb3e_potential_iterations.restype = C.c_int64
+        L.lb3e_potential_iterations.argtypes = [vp]
         L.lb3e_set_timing.argtypes = [vp, C.c_int32]
         L.lb3e_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64)]
         L.lb3e_observables_noalloc.argtypes = [C.POINTER(Params), vp, vp, vp, vp, vp, C.POINTER(Observables)]
+        L.lb3e_batch_workspace_bytes.argtypes = [C.POINTER(Params), C.c_int32, C.POINTER(C.c_size_t)]
+        L.lb3e_batch_create.argtypes = [C.POINTER(Params), C.c_int32, C.POINTER(vp), vp, C.c_size_t, vp,
+                                        C.POINTER(vp)]
+        L.lb3e_batch_run.argtypes = [vp, C.c_int32]
+        L.lb3e_batch_observables.argtypes = [vp, C.POINTER(Observables)]
+        L.lb3e_batch_get_field.argtypes = [vp, C.c_int32, C.c_int32, vp]
+        L.lb3e_batch_set_potential_chunk.argtypes = [vp, C.c_int32]
+        L.lb3e_batch_launch_count.restype = C.c_int64
+        L.lb3e_batch_launch_count.argtypes = [vp]
+        L.lb3e_batch_destroy.argtypes = [vp]
+        L.lb3e_batch_destroy.restype = None
         L.lb3e_destroy.argtypes = [vp]
         L.lb3e_destroy.restype = None
         L.lb3e_status_string.restype = C.c_char_p
@@ -204,9 +221,11 @@ class Sim:
         _check("lb3e_observables", lib().lb3e_observables(self._h, C.byref(o)))
         return o.as_dict()
 
-    def field(self, name: str, out=None):
-        """Field as a host float64 array (or written into ``out``, a CUDA tensor)."""
-        fid = FIELDS[name]
+    def field(self, name: str, out=None, tangent: int = 0):
+        """Field as a host float64 array (or written into ``out``, a CUDA tensor).
+        In the tangent builds, ``tangent=k`` (1..3) gives its derivative along
+        direction k."""
+        fid = FIELDS[name] + TANGENT * int(tangent)
         return self._get(fid, out)
 
     def pop(self, set_name: str, j: int, out=None):
@@ -256,3 +275,73 @@ class Sim:
     @property
     def launches(self) -> int:
         return int(lib().lb3e_launch_count(self._h))
+
+    @property
+    def potential_iterations(self) -> int:
+        return int(lib().lb3e_potential_iterations(self._h))
+
+
+class Batch:
+    """Many lattices (one precision, any sizes) stepped together through the C ABI.
+
+    ``params_list[i]`` is instance i's parameter dict; ``phis[i]`` its initial
+    [3, ny, nx] phase field (host numpy or CUDA float64).  Electric instances must
+    share one ``poisson_fixed_iter``.
+    """
+
+    def __init__(self, params_list, phis, stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("lb3e needs a CUDA device (there is no CPU fallback)")
+        n = len(params_list)
+        self.params = [dict(p) for p in params_list]
+        self.shapes = [(int(p["ny"]), int(p["nx"])) for p in params_list]
+        self._p = (Params * n)(*[Params.from_dict(p) for p in params_list])
+        nb = C.c_size_t(0)
+        _check("lb3e_batch_workspace_bytes", lib().lb3e_batch_workspace_bytes(self._p, n, C.byref(nb)))
+        self.device = torch.device(device or "cuda")
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        keep = [_addr(a) for a in phis]
+        ptrs = (C.c_void_p * n)(*[k[0] for k in keep])
+        h = C.c_void_p(None)
+        _check("lb3e_batch_create", lib().lb3e_batch_create(self._p, n, ptrs, self.workspace.data_ptr(), nb.value,
+                                                            self.stream.cuda_stream, C.byref(h)))
+        self._h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().lb3e_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, nsteps: int) -> "Batch":
+        _check("lb3e_batch_run", lib().lb3e_batch_run(self._h, int(nsteps)))
+        return self
+
+    def set_chunk(self, k: int) -> "Batch":
+        """Potential pseudo-iterations per launch (1..8); see autotune.py."""
+        _check("lb3e_batch_set_potential_chunk", lib().lb3e_batch_set_potential_chunk(self._h, int(k)))
+        self.chunk = int(k)
+        return self
+
+    def observables(self) -> list:
+        out = (Observables * self.n)()
+        _check("lb3e_batch_observables", lib().lb3e_batch_observables(self._h, out))
+        return [o.as_dict() for o in out]
+
+    def field(self, instance: int, name: str):
+        ny, nx = self.shapes[instance]
+        arr = np.empty((ny, nx))
+        _check("lb3e_batch_get_field", lib().lb3e_batch_get_field(self._h, instance, FIELDS[name], arr.ctypes.data))
+        return arr
+
+    @property
+    def launches(self) -> int:
+        return int(lib().lb3e_batch_launch_count(self._h))

@@ -21,6 +21,8 @@ UNITS = {
     # FP64: no contraction into FMA, so the arithmetic rounds like plain C
     "lb3e_f64.cu": ["--fmad=false"],
     "lb3e_f32.cu": [],
+    # dual-number (tangent) builds
+    "lb3e_tangent.cu": [],
     # fixed-scratch observables for callers that cannot allocate (FP64 like lb3e_f64.cu)
     "lb3e_noalloc.cu": ["--fmad=false"],
     "lb3e_api.cpp": [],

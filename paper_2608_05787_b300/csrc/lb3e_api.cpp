@@ -18,8 +18,10 @@ namespace {
 int validate(const lb3e_params* p) {
     if (!p) return LB3E_ERR_NULL;
     if (p->nx < 2 || p->ny < 2) return LB3E_ERR_PARAM;
-    if ((int64_t)p->nx * p->ny > (int64_t)1 << 30) return LB3E_ERR_PARAM;
-    if (p->bc_y < 0 || p->bc_y > 2 || p->precision < 0 || p->precision > 2) return LB3E_ERR_PARAM;
+    if ((int64_t)p->nx * p->ny > LB3E_MAX_CELLS) return LB3E_ERR_PARAM;  // 32-bit plane offsets
+    if (p->bc_y < 0 || p->bc_y > 2 || p->precision < 0 || p->precision > 4) return LB3E_ERR_PARAM;
+    for (int k = 0; k < 3; ++k)
+        if (p->tangent_param[k] < -1 || p->tangent_param[k] > 6) return LB3E_ERR_PARAM;
     if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5) || !(p->width_D > 0) || !(p->eps_ref > 0) || !(p->alpha > 0))
         return LB3E_ERR_PARAM;
     for (int i = 0; i < 3; ++i)
@@ -42,11 +44,42 @@ size_t ws_bytes(const lb3e_params& p) {
     switch (p.precision) {
         case 0: return lb3e::workspace_bytes_f64(p);
         case 1: return lb3e::workspace_bytes_f32(p);
-        default: return lb3e::workspace_bytes_f16s(p);
+        case 2: return lb3e::workspace_bytes_f16s(p);
+        case 3: return lb3e::workspace_bytes_t32(p);
+        default: return lb3e::workspace_bytes_t64(p);
+    }
+}
+
+// every instance valid, one precision, the same fixed potential iteration count
+int validate_batch(const lb3e_params* ps, int32_t n) {
+    if (!ps) return LB3E_ERR_NULL;
+    if (n < 1) return LB3E_ERR_PARAM;
+    int iters = -1;
+    for (int i = 0; i < n; ++i) {
+        TRY(validate(ps + i));
+        if (ps[i].precision != ps[0].precision || ps[i].precision > 2) return LB3E_ERR_PARAM;
+        if (ps[i].electric) {
+            if (ps[i].poisson_fixed_iter <= 0) return LB3E_ERR_PARAM;
+            if (iters >= 0 && ps[i].poisson_fixed_iter != iters) return LB3E_ERR_PARAM;
+            iters = ps[i].poisson_fixed_iter;
+        }
+    }
+    return LB3E_OK;
+}
+
+size_t batch_ws_bytes(const lb3e_params* ps, int n) {
+    switch (ps[0].precision) {
+        case 0: return lb3e::batch_bytes_f64(ps, n);
+        case 1: return lb3e::batch_bytes_f32(ps, n);
+        default: return lb3e::batch_bytes_f16s(ps, n);
     }
 }
 
 }  // namespace
+
+struct lb3e_batch {
+    lb3e::BatchBase* b;
+};
 
 extern "C" {
 
@@ -69,7 +102,9 @@ int lb3e_init(const lb3e_params* params, void* workspace, size_t workspace_bytes
     switch (params->precision) {
         case 0: sim = lb3e::make_sim_f64(*params, workspace, stream); break;
         case 1: sim = lb3e::make_sim_f32(*params, workspace, stream); break;
-        default: sim = lb3e::make_sim_f16s(*params, workspace, stream); break;
+        case 2: sim = lb3e::make_sim_f16s(*params, workspace, stream); break;
+        case 3: sim = lb3e::make_sim_t32(*params, workspace, stream); break;
+        default: sim = lb3e::make_sim_t64(*params, workspace, stream); break;
     }
     if (!sim) return LB3E_ERR_CUDA;
     const int rc = sim->init(phi_init, u_init, q_init, pop_noise);
@@ -132,6 +167,8 @@ int lb3e_load_state(lb3e_handle* h, const void* src) {
 
 int64_t lb3e_launch_count(const lb3e_handle* h) { return h ? h->sim->launches : 0; }
 
+int64_t lb3e_potential_iterations(const lb3e_handle* h) { return h ? h->sim->potential_iterations() : 0; }
+
 int lb3e_set_timing(lb3e_handle* h, int32_t enable) {
     if (!h) return LB3E_ERR_NULL;
     TRY(h->sim->kernel_times(nullptr, nullptr));
@@ -148,6 +185,72 @@ void lb3e_destroy(lb3e_handle* h) {
     if (!h) return;
     delete h->sim;
     delete h;
+}
+
+int lb3e_batch_workspace_bytes(const lb3e_params* params, int32_t n, size_t* bytes) {
+    if (!bytes) return LB3E_ERR_NULL;
+    TRY(validate_batch(params, n));
+    *bytes = batch_ws_bytes(params, n);
+    return LB3E_OK;
+}
+
+int lb3e_batch_create(const lb3e_params* params, int32_t n, const double* const* phi_init, void* workspace,
+                      size_t workspace_bytes, void* stream, lb3e_batch** out) {
+    if (!out || !phi_init) return LB3E_ERR_NULL;
+    *out = nullptr;
+    TRY(validate_batch(params, n));
+    for (int i = 0; i < n; ++i)
+        if (!phi_init[i]) return LB3E_ERR_NULL;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0 ||
+        workspace_bytes < batch_ws_bytes(params, n))
+        return LB3E_ERR_WORKSPACE;
+    lb3e::BatchBase* b = nullptr;
+    int rc = LB3E_OK;
+    switch (params[0].precision) {
+        case 0: b = lb3e::new_batch_f64(params, n, workspace, stream); rc = b ? lb3e::init_batch_f64(b, phi_init) : LB3E_ERR_CUDA; break;
+        case 1: b = lb3e::new_batch_f32(params, n, workspace, stream); rc = b ? lb3e::init_batch_f32(b, phi_init) : LB3E_ERR_CUDA; break;
+        default: b = lb3e::new_batch_f16s(params, n, workspace, stream); rc = b ? lb3e::init_batch_f16s(b, phi_init) : LB3E_ERR_CUDA; break;
+    }
+    if (rc != LB3E_OK) {
+        delete b;
+        return rc;
+    }
+    lb3e_batch* h = new (std::nothrow) lb3e_batch{b};
+    if (!h) {
+        delete b;
+        return LB3E_ERR_CUDA;
+    }
+    *out = h;
+    return LB3E_OK;
+}
+
+int lb3e_batch_run(lb3e_batch* b, int32_t nsteps) {
+    if (!b) return LB3E_ERR_NULL;
+    if (nsteps < 0) return LB3E_ERR_PARAM;
+    return b->b->run(nsteps);
+}
+
+int lb3e_batch_observables(lb3e_batch* b, lb3e_observables_t* out) {
+    if (!b || !out) return LB3E_ERR_NULL;
+    return b->b->observables(out);
+}
+
+int lb3e_batch_get_field(lb3e_batch* b, int32_t instance, int32_t field_id, double* dst) {
+    if (!b || !dst) return LB3E_ERR_NULL;
+    return b->b->get_field(instance, field_id, dst);
+}
+
+int64_t lb3e_batch_launch_count(const lb3e_batch* b) { return b ? b->b->total_launches() : 0; }
+
+int lb3e_batch_set_potential_chunk(lb3e_batch* b, int32_t iterations_per_launch) {
+    if (!b) return LB3E_ERR_NULL;
+    return b->b->set_chunk(iterations_per_launch);
+}
+
+void lb3e_batch_destroy(lb3e_batch* b) {
+    if (!b) return;
+    delete b->b;
+    delete b;
 }
 
 const char* lb3e_status_string(int status) {

@@ -12,4 +12,14 @@ size_t workspace_bytes_f16s(const lb3e_params& p) { return Sim<float, __half>::l
 SimBase* make_sim_f16s(const lb3e_params& p, void* ws, void* stream) {
     return new Sim<float, __half>(p, ws, static_cast<cudaStream_t>(stream));
 }
+size_t batch_bytes_f32(const lb3e_params* ps, int n) { return Batch<float, float>::bytes(ps, n); }
+BatchBase* new_batch_f32(const lb3e_params* ps, int n, void* ws, void* stream) {
+    return new Batch<float, float>(ps, n, ws, static_cast<cudaStream_t>(stream));
+}
+int init_batch_f32(BatchBase* b, const double* const* phis) { return static_cast<Batch<float, float>*>(b)->init(phis); }
+size_t batch_bytes_f16s(const lb3e_params* ps, int n) { return Batch<float, __half>::bytes(ps, n); }
+BatchBase* new_batch_f16s(const lb3e_params* ps, int n, void* ws, void* stream) {
+    return new Batch<float, __half>(ps, n, ws, static_cast<cudaStream_t>(stream));
+}
+int init_batch_f16s(BatchBase* b, const double* const* phis) { return static_cast<Batch<float, __half>*>(b)->init(phis); }
 }  // namespace lb3e

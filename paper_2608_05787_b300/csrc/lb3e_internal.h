@@ -76,8 +76,21 @@ struct SimBase {
     virtual int save(void* dst) = 0;
     virtual int load(const void* src) = 0;
     virtual int kernel_times(double* ms, int64_t* counts) = 0;
+    virtual int64_t potential_iterations() const = 0;
     int64_t launches = 0;
     LaunchTimer timer;
+};
+
+// a batch of lattices of one precision, stepped together
+struct BatchBase {
+    virtual ~BatchBase() = default;
+    virtual int run(int nsteps) = 0;
+    virtual int observables(lb3e_observables_t* out) = 0;
+    virtual int get_field(int inst, int id, double* dst) = 0;
+    virtual int count() const = 0;
+    virtual int64_t total_launches() const = 0;
+    virtual int set_chunk(int k) = 0;
+    int64_t launches = 0;
 };
 
 // factories, one per translation unit (precision)
@@ -87,5 +100,18 @@ size_t workspace_bytes_f32(const lb3e_params& p);
 SimBase* make_sim_f32(const lb3e_params& p, void* ws, void* stream);
 size_t workspace_bytes_f16s(const lb3e_params& p);
 SimBase* make_sim_f16s(const lb3e_params& p, void* ws, void* stream);
+size_t workspace_bytes_t32(const lb3e_params& p);
+SimBase* make_sim_t32(const lb3e_params& p, void* ws, void* stream);
+size_t workspace_bytes_t64(const lb3e_params& p);
+SimBase* make_sim_t64(const lb3e_params& p, void* ws, void* stream);
+size_t batch_bytes_f64(const lb3e_params* ps, int n);
+BatchBase* new_batch_f64(const lb3e_params* ps, int n, void* ws, void* stream);
+int init_batch_f64(BatchBase* b, const double* const* phis);
+size_t batch_bytes_f32(const lb3e_params* ps, int n);
+BatchBase* new_batch_f32(const lb3e_params* ps, int n, void* ws, void* stream);
+int init_batch_f32(BatchBase* b, const double* const* phis);
+size_t batch_bytes_f16s(const lb3e_params* ps, int n);
+BatchBase* new_batch_f16s(const lb3e_params* ps, int n, void* ws, void* stream);
+int init_batch_f16s(BatchBase* b, const double* const* phis);
 
 }  // namespace lb3e

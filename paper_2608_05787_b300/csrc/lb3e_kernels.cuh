@@ -17,6 +17,10 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
+#include "lb3e_dual.cuh"
+
 namespace lb3e {
 
 // ---------------------------------------------------------------- parameters
@@ -26,6 +30,8 @@ struct DevParams {
     double rho[3], visc[3], tau_g, lam[3], D, tau_f, m0, eps[3], sigma[3];
     double eps_ref, tau_h, alpha, tau_l;
     double V_bottom, V_top, E_ext[2], u_wall_bottom, u_wall_top;
+    // tangent seeds (dual-number builds only): d(param)/d(theta_k), k < 4
+    double t_eps[3][4], t_lam[3][4], t_Vb[4], t_Vt[4];
 };
 
 // Device-side buffers of one simulation (pointers into the caller's workspace).
@@ -55,6 +61,48 @@ __host__ __device__ constexpr R wgt(int j) { return j == 0 ? R(4.0 / 9.0) : (j <
 template <class R>
 __host__ __device__ constexpr R cs2() { return R(1.0 / 3.0); }
 
+template <class R>
+__host__ __device__ constexpr bool exact_arith() { return std::is_same<R, double>::value; }
+// blocks per SM the register budget is sized for
+template <class R>
+__host__ __device__ constexpr int fused_min_blocks() { return std::is_same<R, float>::value ? 3 : 1; }
+template <class R>
+__host__ __device__ constexpr int pb_min_blocks() { return std::is_same<R, float>::value ? 2 : 1; }
+
+// A model parameter as an R: plain builds take the value; dual builds also carry
+// its seeded tangents (one per differentiated parameter direction).
+template <class R>
+__device__ __forceinline__ R prm(double v, const double* t) {
+    if constexpr (is_dual<R>::value) {
+        R r(v);
+#pragma unroll
+        for (int k = 0; k < (int)(sizeof(r.d) / sizeof(r.d[0])); ++k) r.d[k] = decltype(r.v)(t[k]);
+        return r;
+    } else {
+        return R(v);
+    }
+}
+
+// Divisions.  The FP64 build divides exactly where a plain C evaluation of the
+// same formula divides (it is compared with the oracle to 1e-12 after thousands of
+// steps); the FP32 builds multiply by a reciprocal formed once per thread, which
+// removes most of their instruction count.
+template <class R>
+__device__ __forceinline__ R dv(R a, R b, R inv_b) {
+    if constexpr (exact_arith<R>()) return a / b;
+    else return a * inv_b;
+}
+template <class R>
+__device__ __forceinline__ R rcp(R b) {
+    if constexpr (std::is_same<R, float>::value) return __frcp_rn(b);
+    else return R(1) / b;
+}
+template <class R>
+__device__ __forceinline__ R oc2(R a) {  // a / cs^2
+    if constexpr (exact_arith<R>()) return a / cs2<R>();
+    else return a * R(3);
+}
+
 // ---------------------------------------------------------------- storage conversion
 // Storage types.  With fp16 storage the rest population f^i_0 of each phase set
 // (which is close to phi_i, an O(1) number) is stored as its deviation from the
@@ -74,11 +122,23 @@ template <> struct Store<__half> {
     static __device__ __forceinline__ float ld(const __half* p, size_t i) { return __half2float(p[i]); }
     static __device__ __forceinline__ void st(__half* p, size_t i, float v) { p[i] = __float2half_rn(v); }
 };
+template <class T, int M> struct Store<Dual<T, M>> {
+    static __device__ __forceinline__ Dual<T, M> ld(const Dual<T, M>* p, size_t i) { return p[i]; }
+    static __device__ __forceinline__ void st(Dual<T, M>* p, size_t i, Dual<T, M> v) { p[i] = v; }
+};
 template <class S>
 __host__ __device__ constexpr bool anchored() { return sizeof(S) == 2; }
 
 // ---------------------------------------------------------------- grid helpers
-__device__ __forceinline__ int wrapi(int a, int n) { a %= n; return a < 0 ? a + n : a; }
+__device__ __forceinline__ int wrapi(int a, int n) {
+    if (a < 0) a += n;
+    else if (a >= n) a -= n;
+    if ((unsigned)a >= (unsigned)n) {  // only on grids smaller than the offset
+        a %= n;
+        if (a < 0) a += n;
+    }
+    return a;
+}
 // stencil ghost rows: periodic, or mirror about the half-way wall
 __device__ __forceinline__ int ghost_row(int y, int ny, int bc_y) {
     if (bc_y == 0) return wrapi(y, ny);
@@ -97,9 +157,9 @@ __device__ __forceinline__ int tile_row(int y, int ny, int bc_y) {
 template <class R>
 __device__ __forceinline__ R perm(const DevParams& P, R p0, R p1, R p2) {
     R e = R(0);
-    e += R(P.eps[0]) * p0 * p0 * (R(3) - R(2) * p0);
-    e += R(P.eps[1]) * p1 * p1 * (R(3) - R(2) * p1);
-    e += R(P.eps[2]) * p2 * p2 * (R(3) - R(2) * p2);
+    e += prm<R>(P.eps[0], P.t_eps[0]) * p0 * p0 * (R(3) - R(2) * p0);
+    e += prm<R>(P.eps[1], P.t_eps[1]) * p1 * p1 * (R(3) - R(2) * p1);
+    e += prm<R>(P.eps[2], P.t_eps[2]) * p2 * p2 * (R(3) - R(2) * p2);
     return e;
 }
 template <class R>
@@ -115,7 +175,10 @@ template <class R>
 __device__ __forceinline__ R s_eq(int j, R ux, R uy) {
     R cu = R(cx(j)) * ux + R(cy(j)) * uy;
     R uu = ux * ux + uy * uy;
-    return wgt<R>(j) * (cu / cs2<R>() + cu * cu / (R(2) * cs2<R>() * cs2<R>()) - uu / (R(2) * cs2<R>()));
+    if constexpr (exact_arith<R>())
+        return wgt<R>(j) * (cu / cs2<R>() + cu * cu / (R(2) * cs2<R>() * cs2<R>()) - uu / (R(2) * cs2<R>()));
+    else
+        return wgt<R>(j) * (cu * R(3) + cu * cu * R(4.5) - uu * R(1.5));
 }
 
 // ---------------------------------------------------------------- block reduction (FP64)
@@ -144,11 +207,11 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* out)
 
 // ---------------------------------------------------------------- S1: moments
 template <class R, class S>
-__global__ void __launch_bounds__(256) k_moments(DevParams P, const S* __restrict__ pop, const R* phi_anchor,
-                                                 R* phi, R* __restrict__ qt) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void body_moments(const DevParams P, const S* __restrict__ pop, const R* phi_anchor,
+                                                 R* phi, R* __restrict__ qt, int bx, int by, int gdx) {
+    const int x = bx * blockDim.x + threadIdx.x, y = by * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
-    const size_t N = P.N, c = (size_t)y * P.nx + x;
+    const unsigned N = P.N, c = (unsigned)y * P.nx + x;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         R a = R(0);
@@ -165,22 +228,27 @@ __global__ void __launch_bounds__(256) k_moments(DevParams P, const S* __restric
     for (int j = 0; j < 9; ++j) a += Store<S>::ld(pop, (36 + j) * N + c);
     qt[c] = a;
 }
+template <class R, class S>
+__global__ void __launch_bounds__(256) k_moments(DevParams P, const S* __restrict__ pop, const R* phi_anchor,
+                                                 R* phi, R* __restrict__ qt) {
+    body_moments<R, S>(P, pop, phi_anchor, phi, qt, blockIdx.x, blockIdx.y, gridDim.x);
+}
 
 // ---------------------------------------------------------------- S2-S4: properties, stencils, charge
 // Reads phi on the 1-ring (L1-cached), writes eps and the closed-form charge
 // q = [q~ + (sigma/eps grad eps . E - grad sigma . E)/2] / (1 + sigma/(2 eps)),
 // with E of the previous step.
 template <class R>
-__global__ void __launch_bounds__(256) k_prologue(DevParams P, const R* __restrict__ phi, const R* __restrict__ qt,
+__device__ __forceinline__ void body_prologue(const DevParams P, const R* __restrict__ phi, const R* __restrict__ qt,
                                                   const R* __restrict__ E, R* __restrict__ q, R* __restrict__ eps_out,
-                                                  int use_qt) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+                                                  int use_qt, int bx, int by, int gdx) {
+    const int x = bx * blockDim.x + threadIdx.x, y = by * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
-    const size_t N = P.N, c = (size_t)y * P.nx + x;
+    const unsigned N = P.N, c = (unsigned)y * P.nx + x;
     R gex = R(0), gey = R(0), gsx = R(0), gsy = R(0), e0 = R(0), s0 = R(0);
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
-        const size_t n = (size_t)ghost_row(y + cy(j), P.ny, P.bc_y) * P.nx + wrapi(x + cx(j), P.nx);
+        const unsigned n = (unsigned)ghost_row(y + cy(j), P.ny, P.bc_y) * P.nx + wrapi(x + cx(j), P.nx);
         const R p0 = phi[n], p1 = phi[N + n], p2 = phi[2 * N + n];
         const R e = perm<R>(P, p0, p1, p2), s = cond<R>(P, p0, p1, p2);
         gex += wgt<R>(j) * R(cx(j)) * e;
@@ -189,13 +257,20 @@ __global__ void __launch_bounds__(256) k_prologue(DevParams P, const R* __restri
         gsy += wgt<R>(j) * R(cy(j)) * s;
         if (j == 0) { e0 = e; s0 = s; }
     }
-    gex = gex / cs2<R>(); gey = gey / cs2<R>(); gsx = gsx / cs2<R>(); gsy = gsy / cs2<R>();
+    gex = oc2(gex); gey = oc2(gey); gsx = oc2(gsx); gsy = oc2(gsy);
     eps_out[c] = e0;
     if (!use_qt) return;
-    const R r = s0 / e0;
+    const R r = dv(s0, e0, rcp(e0));
     const R Ex = E[c], Ey = E[N + c];
     const R src = r * (gex * Ex + gey * Ey) - (gsx * Ex + gsy * Ey);
-    q[c] = (qt[c] + R(0.5) * src) / (R(1) + R(0.5) * r);
+    const R den = R(1) + R(0.5) * r;
+    q[c] = dv(qt[c] + R(0.5) * src, den, rcp(den));
+}
+template <class R>
+__global__ void __launch_bounds__(256) k_prologue(DevParams P, const R* __restrict__ phi, const R* __restrict__ qt,
+                                                  const R* __restrict__ E, R* __restrict__ q, R* __restrict__ eps_out,
+                                                  int use_qt) {
+    body_prologue<R>(P, phi, qt, E, q, eps_out, use_qt, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 // ---------------------------------------------------------------- S5: potential iteration (Eq. 43-45)
@@ -203,13 +278,13 @@ __global__ void __launch_bounds__(256) k_prologue(DevParams P, const R* __restri
 // saves psi and J = sum c_j h_j; on a check it accumulates (FP64, per block)
 // |d psi|^2, |psi|^2, |d J|^2, |J|^2.
 template <class R>
-__global__ void __launch_bounds__(256) k_poisson(DevParams P, const R* __restrict__ hin, R* __restrict__ hout,
+__device__ __forceinline__ void body_poisson(const DevParams P, const R* __restrict__ hin, R* __restrict__ hout,
                                                  const R* __restrict__ eps, const R* __restrict__ q,
                                                  R* __restrict__ prev, double* __restrict__ partial,
-                                                 int save_prev, int check) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+                                                 int save_prev, int check, int bx, int by, int gdx) {
+    const int x = bx * blockDim.x + threadIdx.x, y = by * blockDim.y + threadIdx.y;
     const bool in = x < P.nx && y < P.ny;
-    const size_t N = P.N, c = in ? (size_t)y * P.nx + x : 0;
+    const unsigned N = P.N, c = in ? (unsigned)y * P.nx + x : 0;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     if (in) {
         R hj[9];
@@ -218,7 +293,7 @@ __global__ void __launch_bounds__(256) k_poisson(DevParams P, const R* __restric
         R ps = R(0), jx = R(0), jy = R(0);
 #pragma unroll
         for (int j = 1; j < 9; ++j) ps += hj[j];
-        ps = ps / (R(1) - wgt<R>(0));
+        ps = dv(ps, R(1) - wgt<R>(0), R(1.8));
 #pragma unroll
         for (int j = 0; j < 9; ++j) { jx += R(cx(j)) * hj[j]; jy += R(cy(j)) * hj[j]; }
         if (check) {
@@ -230,31 +305,191 @@ __global__ void __launch_bounds__(256) k_poisson(DevParams P, const R* __restric
             acc[3] = (double)jx * (double)jx + (double)jy * (double)jy;
         }
         if (save_prev) { prev[c] = ps; prev[N + c] = jx; prev[2 * N + c] = jy; }
-        const R th = R(P.tau_h);
+        const R th = R(P.tau_h), ith = rcp(th);
         const R epshat = eps[c] - R(P.eps_ref);
-        const R den = epshat + cs2<R>() * th;
-        const R gx = -jx / den, gy = -jy / den;
+        const R den = epshat + cs2<R>() * th, iden = rcp(den);
+        const R gx = dv(-jx, den, iden), gy = dv(-jy, den, iden);
         const R qc = q[c];
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
             const R heq = (j == 0) ? (wgt<R>(0) - R(1)) * ps : wgt<R>(j) * ps;
             const R varpi = (j == 0) ? R(0) : R(1.0 / 8.0);
             const R cg = R(cx(j)) * gx + R(cy(j)) * gy;
-            const R v = hj[j] - (hj[j] - heq) / th - (epshat / cs2<R>()) * wgt<R>(j) * cg / th + varpi * qc;
+            const R v = hj[j] - dv(hj[j] - heq, th, ith) - dv(oc2(epshat) * wgt<R>(j) * cg, th, ith) + varpi * qc;
             const int yt = y + cy(j);
             if (P.bc_y != 0 && (yt < 0 || yt >= P.ny)) {
                 R out = v;
-                if (P.bc_y == 2) out = -v + R(2) * wgt<R>(j) * R(yt >= P.ny ? P.V_top : P.V_bottom);
+                if (P.bc_y == 2)
+                    out = -v + R(2) * wgt<R>(j) * (yt >= P.ny ? prm<R>(P.V_top, P.t_Vt) : prm<R>(P.V_bottom, P.t_Vb));
                 hout[opp(j) * N + c] = out;
             } else {
-                hout[j * N + (size_t)wrapi(yt, P.ny) * P.nx + wrapi(x + cx(j), P.nx)] = v;
+                hout[j * N + (unsigned)wrapi(yt, P.ny) * P.nx + wrapi(x + cx(j), P.nx)] = v;
             }
         }
     }
     if (check) {
-        const int b = blockIdx.x + gridDim.x * blockIdx.y;
+        const int b = bx + gdx * by;
         block_reduce_store<4>(acc, partial + 4 * (size_t)b);
     }
+}
+template <class R>
+__global__ void __launch_bounds__(256) k_poisson(DevParams P, const R* __restrict__ hin, R* __restrict__ hout,
+                                                 const R* __restrict__ eps, const R* __restrict__ q,
+                                                 R* __restrict__ prev, double* __restrict__ partial,
+                                                 int save_prev, int check) {
+    body_poisson<R>(P, hin, hout, eps, q, prev, partial, save_prev, check, blockIdx.x, blockIdx.y, gridDim.x);
+}
+
+// ---------------------------------------------------------------- S5, temporally blocked
+// K (<= PB_HALO) pseudo-iterations of Eq. 43 per launch.  A block loads the h
+// populations of its PB_TX x PB_TY tile plus a PB_HALO-cell halo into registers
+// (PB_CPT cells per thread), and eps, q into shared memory.  Each iteration
+// collides in registers, writes the post-collision values to shared memory, and
+// pulls each cell's incoming populations back (bounce-back at walls); the region
+// of correct cells shrinks by one per iteration, so after K <= PB_HALO iterations
+// the tile itself is exact and is written out.  Per cell the arithmetic is that of
+// body_poisson.  Residual partials (check) are taken before the first collision,
+// the residual state (save_prev) before the last one.
+constexpr int PB_TX = 32, PB_TY = 16, PB_HALO = 8;
+constexpr int PB_RX = PB_TX + 2 * PB_HALO, PB_RY = PB_TY + 2 * PB_HALO;
+constexpr int PB_CELLS = PB_RX * PB_RY, PB_THREADS = 512;
+constexpr int PB_CPT = (PB_CELLS + PB_THREADS - 1) / PB_THREADS;
+template <class R>
+constexpr size_t pb_smem_bytes() { return (size_t)11 * PB_CELLS * sizeof(R); }
+
+template <class R>
+__device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __restrict__ hin,
+                                                           R* __restrict__ hout, const R* __restrict__ eps,
+                                                           const R* __restrict__ q, R* __restrict__ prev,
+                                                           double* __restrict__ partial, int K, int save_prev,
+                                                           int check, int bx, int by, int gdx) {
+    extern __shared__ __align__(16) unsigned char pb_raw[];
+    R* hs = reinterpret_cast<R*>(pb_raw);           // [9][PB_CELLS] post-collision values
+    R* se = hs + 9 * PB_CELLS;                      // eps
+    R* sq = se + PB_CELLS;                          // q
+    const int nx = P.nx, ny = P.ny;
+    const unsigned N = P.N;
+    const int x0 = bx * PB_TX - PB_HALO, y0 = by * PB_TY - PB_HALO;
+    const int tid = threadIdx.x;
+    const bool walls = P.bc_y != 0;
+
+    R h[PB_CPT][9];
+    int gyv[PB_CPT];  // global row of each owned cell (unwrapped)
+#pragma unroll
+    for (int m = 0; m < PB_CPT; ++m) {
+        const int k = tid + m * PB_THREADS;
+        const int ly = k / PB_RX, lx = k % PB_RX;
+        const int gy = y0 + ly, gx = x0 + lx;
+        gyv[m] = gy;
+        const bool real = k < PB_CELLS && (!walls || (gy >= 0 && gy < ny));
+        if (real) {
+            const unsigned c = (unsigned)wrapi(gy, ny) * nx + wrapi(gx, nx);
+#pragma unroll
+            for (int j = 0; j < 9; ++j) h[m][j] = hin[j * N + c];
+            se[k] = eps[c];
+            sq[k] = q[c];
+        } else {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) h[m][j] = R(0);
+            if (k < PB_CELLS) { se[k] = R(P.eps_ref); sq[k] = R(0); }
+        }
+    }
+    __syncthreads();
+
+    const R th = R(P.tau_h), ith = rcp(th);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int t = 0; t < K; ++t) {
+#pragma unroll
+        for (int m = 0; m < PB_CPT; ++m) {
+            const int k = tid + m * PB_THREADS;
+            if (k >= PB_CELLS) continue;
+            const int ly = k / PB_RX, lx = k % PB_RX;
+            const int gy = gyv[m];
+            if (walls && (gy < 0 || gy >= ny)) continue;
+            R ps = R(0), jx = R(0), jy = R(0);
+#pragma unroll
+            for (int j = 1; j < 9; ++j) ps += h[m][j];
+            ps = dv(ps, R(1) - wgt<R>(0), R(1.8));
+#pragma unroll
+            for (int j = 0; j < 9; ++j) { jx += R(cx(j)) * h[m][j]; jy += R(cy(j)) * h[m][j]; }
+            const bool tile = ly >= PB_HALO && ly < PB_HALO + PB_TY && lx >= PB_HALO && lx < PB_HALO + PB_TX &&
+                              x0 + lx < nx && gy < ny;
+            if (tile && (check && t == 0 || save_prev && t == K - 1)) {
+                const unsigned c = (unsigned)gy * nx + (x0 + lx);
+                if (check && t == 0) {
+                    const double d = (double)ps - (double)prev[c];
+                    const double ex = (double)jx - (double)prev[N + c], ey = (double)jy - (double)prev[2 * N + c];
+                    acc[0] += d * d;
+                    acc[1] += (double)ps * (double)ps;
+                    acc[2] += ex * ex + ey * ey;
+                    acc[3] += (double)jx * (double)jx + (double)jy * (double)jy;
+                }
+                if (save_prev && t == K - 1) { prev[c] = ps; prev[N + c] = jx; prev[2 * N + c] = jy; }
+            }
+            const R epshat = se[k] - R(P.eps_ref);
+            const R den = epshat + cs2<R>() * th, iden = rcp(den);
+            const R gx = dv(-jx, den, iden), gy2 = dv(-jy, den, iden);
+            const R qc = sq[k];
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const R heq = (j == 0) ? (wgt<R>(0) - R(1)) * ps : wgt<R>(j) * ps;
+                const R varpi = (j == 0) ? R(0) : R(1.0 / 8.0);
+                const R cg = R(cx(j)) * gx + R(cy(j)) * gy2;
+                hs[j * PB_CELLS + k] =
+                    h[m][j] - dv(h[m][j] - heq, th, ith) - dv(oc2(epshat) * wgt<R>(j) * cg, th, ith) + varpi * qc;
+            }
+        }
+        __syncthreads();
+        // pull streaming inside the region
+#pragma unroll
+        for (int m = 0; m < PB_CPT; ++m) {
+            const int k = tid + m * PB_THREADS;
+            if (k >= PB_CELLS) continue;
+            const int ly = k / PB_RX, lx = k % PB_RX;
+            const int gy = gyv[m];
+            if (walls && (gy < 0 || gy >= ny)) continue;
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const int sy = gy - cy(j);
+                if (walls && (sy < 0 || sy >= ny)) {
+                    // the population that left this cell toward the wall, reflected
+                    const int jo = opp(j);
+                    const R v = hs[jo * PB_CELLS + k];
+                    h[m][j] = P.bc_y == 2 ? -v + R(2) * wgt<R>(jo) * (sy >= ny ? prm<R>(P.V_top, P.t_Vt)
+                                                                                : prm<R>(P.V_bottom, P.t_Vb))
+                                          : v;
+                } else {
+                    int syl = ly - cy(j), sxl = lx - cx(j);
+                    // sources outside the region only feed cells outside the exact cone
+                    syl = syl < 0 ? 0 : (syl >= PB_RY ? PB_RY - 1 : syl);
+                    sxl = sxl < 0 ? 0 : (sxl >= PB_RX ? PB_RX - 1 : sxl);
+                    h[m][j] = hs[j * PB_CELLS + syl * PB_RX + sxl];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // write the tile
+#pragma unroll
+    for (int m = 0; m < PB_CPT; ++m) {
+        const int k = tid + m * PB_THREADS;
+        if (k >= PB_CELLS) continue;
+        const int ly = k / PB_RX, lx = k % PB_RX;
+        const int gy = gyv[m], gx = x0 + lx;
+        if (ly < PB_HALO || ly >= PB_HALO + PB_TY || lx < PB_HALO || lx >= PB_HALO + PB_TX || gx >= nx || gy >= ny)
+            continue;
+        const unsigned c = (unsigned)gy * nx + gx;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) hout[j * N + c] = h[m][j];
+    }
+    if (check) block_reduce_store<4>(acc, partial + 4 * (size_t)(bx + gdx * by));
+}
+template <class R>
+__global__ void __launch_bounds__(PB_THREADS, pb_min_blocks<R>())
+    k_poisson_tb(DevParams P, const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ eps,
+                 const R* __restrict__ q, R* __restrict__ prev, double* __restrict__ partial, int K, int save_prev,
+                 int check) {
+    body_poisson_tb<R>(P, hin, hout, eps, q, prev, partial, K, save_prev, check, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 // final reduction of nblk x NV partials in a fixed order (one block of 256 threads)
@@ -270,14 +505,30 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const double* __restric
     block_reduce_store<NV>(v, out);
 }
 
+// first stage of a two-stage reduction: block b sums partial rows
+// [b*chunk, (b+1)*chunk) into out[b]; k_reduce_partials then sums the gridDim.x rows.
+// Both stages run in a fixed order, so the result does not depend on timing.
+template <int NV>
+__global__ void __launch_bounds__(256) k_reduce_stage1(const double* __restrict__ partial, int nblk, int chunk,
+                                                       double* __restrict__ out) {
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+    const int b0 = blockIdx.x * chunk, b1 = min(nblk, b0 + chunk);
+    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += partial[(size_t)b * NV + k];
+    block_reduce_store<NV>(v, out + (size_t)NV * blockIdx.x);
+}
+
 // psi and E = sum c_j h_j / (eps - eps_ref + cs2 tau_h) + E_ext from the current h
 template <class R>
-__global__ void __launch_bounds__(256) k_potential_fields(DevParams P, const R* __restrict__ h,
+__device__ __forceinline__ void body_potential_fields(const DevParams P, const R* __restrict__ h,
                                                           const R* __restrict__ eps, R* __restrict__ E,
-                                                          double* __restrict__ psi_out) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+                                                          double* __restrict__ psi_out, int bx, int by, int gdx) {
+    const int x = bx * blockDim.x + threadIdx.x, y = by * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
-    const size_t N = P.N, c = (size_t)y * P.nx + x;
+    const unsigned N = P.N, c = (unsigned)y * P.nx + x;
     R ps = R(0), jx = R(0), jy = R(0);
 #pragma unroll
     for (int j = 1; j < 9; ++j) ps += h[j * N + c];
@@ -289,16 +540,28 @@ __global__ void __launch_bounds__(256) k_potential_fields(DevParams P, const R* 
     E[c] = -gx + R(P.E_ext[0]);
     E[N + c] = -gy + R(P.E_ext[1]);
 }
+template <class R>
+__global__ void __launch_bounds__(256) k_potential_fields(DevParams P, const R* __restrict__ h,
+                                                          const R* __restrict__ eps, R* __restrict__ E,
+                                                          double* __restrict__ psi_out) {
+    body_potential_fields<R>(P, h, eps, E, psi_out, blockIdx.x, blockIdx.y, gridDim.x);
+}
 
 // h at equilibrium with the linear electrode profile (or zero)
 template <class R>
 __global__ void k_init_h(DevParams P, R* __restrict__ h) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
-    const size_t N = P.N, c = (size_t)y * P.nx + x;
-    const double ps = P.bc_y == 2 ? P.V_bottom + (P.V_top - P.V_bottom) * (y + 0.5) / P.ny : 0.0;
+    const unsigned N = P.N, c = (unsigned)y * P.nx + x;
+    R ps;
+    if constexpr (is_dual<R>::value) {
+        const R vb = prm<R>(P.V_bottom, P.t_Vb), vt = prm<R>(P.V_top, P.t_Vt);
+        ps = P.bc_y == 2 ? vb + (vt - vb) * R((y + 0.5) / P.ny) : R(0);
+    } else {
+        ps = R(P.bc_y == 2 ? P.V_bottom + (P.V_top - P.V_bottom) * (y + 0.5) / P.ny : 0.0);
+    }
 #pragma unroll
-    for (int j = 0; j < 9; ++j) h[j * N + c] = (j == 0) ? (wgt<R>(0) - R(1)) * R(ps) : wgt<R>(j) * R(ps);
+    for (int j = 0; j < 9; ++j) h[j * N + c] = (j == 0) ? (wgt<R>(0) - R(1)) * ps : wgt<R>(j) * ps;
 }
 
 template <class R>
@@ -316,14 +579,15 @@ __device__ __forceinline__ R lap_tile(const R* t, int pitch, int ty, int tx) {
     R a = R(0);
 #pragma unroll
     for (int j = 0; j < 9; ++j) a += R(2) * wgt<R>(j) * (t[(ty + cy(j)) * pitch + tx + cx(j)] - c);
-    return a / cs2<R>();
+    return oc2(a);
 }
 template <class R>
-__device__ __forceinline__ R chem_pot(const DevParams& P, int i, R ph, R lap, R e2) {
-    const R D = R(P.D), lam = R(P.lam[i]);
-    const R bulk = R(24) / D * lam * ph * (ph - R(0.5)) * (ph - R(1));
+__device__ __forceinline__ R chem_pot(const DevParams& P, int i, R ph, R lap, R e2, R c24) {
+    // c24 = 24 / D, formed once by the caller
+    const R D = R(P.D), lam = prm<R>(P.lam[i], P.t_lam[i]);
+    const R bulk = c24 * lam * ph * (ph - R(0.5)) * (ph - R(1));
     const R grad = R(0.75) * D * lam * lap;
-    const R deps = R(6) * R(P.eps[i]) * ph * (R(1) - ph);
+    const R deps = R(6) * prm<R>(P.eps[i], P.t_eps[i]) * ph * (R(1) - ph);
     return bulk - grad - R(0.5) * deps * e2;
 }
 
@@ -335,35 +599,36 @@ __device__ __forceinline__ R chem_pot(const DevParams& P, int i, R ph, R lap, R 
 constexpr int TX = 32, TY = 8;
 
 template <class R, class S>
-__global__ void __launch_bounds__(TX * TY) k_fused(DevParams P, const S* __restrict__ pin, S* __restrict__ pout,
+__device__ __forceinline__ void body_fused(const DevParams P, const S* __restrict__ pin, S* __restrict__ pout,
                                                    const R* __restrict__ phi, const R* __restrict__ qf,
                                                    const R* __restrict__ E, R* __restrict__ prev,
-                                                   R* __restrict__ diag, int first, int write_diag) {
+                                                   R* __restrict__ diag, int first, int write_diag, int bx, int by, int gdx) {
     constexpr int PX = TX + 4, PY = TY + 4;  // phi tile, 2-ring
     constexpr int MX = TX + 2, MY = TY + 2;  // mu / E tile, 1-ring
     __shared__ R sphi[3][PY * PX];
     __shared__ R sE[2][MY * MX];
     __shared__ R smu[3][MY * MX];
     const int nx = P.nx, ny = P.ny;
-    const size_t N = P.N;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const unsigned N = P.N;
+    const int x0 = bx * TX, y0 = by * TY;
     const int tid = threadIdx.x + TX * threadIdx.y;
 
     for (int k = tid; k < PY * PX; k += TX * TY) {
         const int ly = k / PX, lx = k % PX;
-        const size_t n = (size_t)tile_row(y0 + ly - 2, ny, P.bc_y) * nx + wrapi(x0 + lx - 2, nx);
+        const unsigned n = (unsigned)tile_row(y0 + ly - 2, ny, P.bc_y) * nx + wrapi(x0 + lx - 2, nx);
         sphi[0][k] = phi[n];
         sphi[1][k] = phi[N + n];
         sphi[2][k] = phi[2 * N + n];
     }
     for (int k = tid; k < MY * MX; k += TX * TY) {
         const int ly = k / MX, lx = k % MX;
-        const size_t n = (size_t)tile_row(y0 + ly - 1, ny, P.bc_y) * nx + wrapi(x0 + lx - 1, nx);
+        const unsigned n = (unsigned)tile_row(y0 + ly - 1, ny, P.bc_y) * nx + wrapi(x0 + lx - 1, nx);
         sE[0][k] = E[n];
         sE[1][k] = E[N + n];
     }
     __syncthreads();
     // mu on the 1-ring at in-domain rows
+    const R c24 = R(24) / R(P.D);
     for (int k = tid; k < MY * MX; k += TX * TY) {
         const int ly = k / MX, lx = k % MX;
         const int gy = y0 + ly - 1;
@@ -373,7 +638,7 @@ __global__ void __launch_bounds__(TX * TY) k_fused(DevParams P, const S* __restr
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const R ph = sphi[i][(ly + 1) * PX + lx + 1];
-            smu[i][k] = chem_pot<R>(P, i, ph, lap_tile<R>(sphi[i], PX, ly + 1, lx + 1), e2);
+            smu[i][k] = chem_pot<R>(P, i, ph, lap_tile<R>(sphi[i], PX, ly + 1, lx + 1), e2, c24);
         }
     }
     __syncthreads();
@@ -393,7 +658,7 @@ __global__ void __launch_bounds__(TX * TY) k_fused(DevParams P, const S* __restr
 
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     if (x >= nx || y >= ny) return;
-    const size_t c = (size_t)y * nx + x;
+    const unsigned c = (unsigned)y * nx + x;
     const int py = threadIdx.y + 2, px = threadIdx.x + 2;
     const int my = threadIdx.y + 1, mx = threadIdx.x + 1;
 
@@ -411,8 +676,8 @@ __global__ void __launch_bounds__(TX * TY) k_fused(DevParams P, const S* __restr
             ax += wgt<R>(j) * R(cx(j)) * v;
             ay += wgt<R>(j) * R(cy(j)) * v;
         }
-        gmu[i][0] = ax / cs2<R>();
-        gmu[i][1] = ay / cs2<R>();
+        gmu[i][0] = oc2(ax);
+        gmu[i][1] = oc2(ay);
     }
     R rho = R(0), sg = R(0), ep = R(0);
 #pragma unroll
@@ -428,14 +693,14 @@ __global__ void __launch_bounds__(TX * TY) k_fused(DevParams P, const S* __restr
         gsy += wgt<R>(j) * R(cy(j)) * s;
         if (j == 0) { rho = r; ep = e; sg = s; }
     }
-    grx = grx / cs2<R>(); gry = gry / cs2<R>();
-    gex = gex / cs2<R>(); gey = gey / cs2<R>();
-    gsx = gsx / cs2<R>(); gsy = gsy / cs2<R>();
+    grx = oc2(grx); gry = oc2(gry);
+    gex = oc2(gex); gey = oc2(gey);
+    gsx = oc2(gsx); gsy = oc2(gsy);
 
     const R Ex = sE[0][my * MX + mx], Ey = sE[1][my * MX + mx];
     const R qc = qf[c];
     // R of Eq. 47 with q^n and E^n
-    const R rr = sg / ep;
+    const R rr = dv(sg, ep, rcp(ep));
     const R Rc = -rr * qc + rr * (gex * Ex + gey * Ey) - (gsx * Ex + gsy * Ey);
     // force, Eq. 27b
     R Fx = R(0), Fy = R(0);
@@ -456,8 +721,9 @@ __global__ void __launch_bounds__(TX * TY) k_fused(DevParams P, const S* __restr
         mym += R(cy(j)) * g[j];
         if (j) g1 += g[j];
     }
-    const R ux = (mxm + R(0.5) * Fx) / rho;
-    const R uy = (mym + R(0.5) * Fy) / rho;
+    const R irho = rcp(rho);
+    const R ux = dv(mxm + R(0.5) * Fx, rho, irho);
+    const R uy = dv(mym + R(0.5) * Fy, rho, irho);
     const R ugr = ux * grx + uy * gry;
     const R pr = cs2<R>() / (R(1) - wgt<R>(0)) * (g1 + R(0.5) * ugr + rho * s_eq<R>(0, ux, uy));
 
@@ -493,12 +759,13 @@ __global__ void __launch_bounds__(TX * TY) k_fused(DevParams P, const S* __restr
         if (walls && (yt < 0 || yt >= ny)) {
             Store<S>::st(pout, (9 * set + opp(j)) * N + c, v);
         } else {
-            Store<S>::st(pout, (9 * set + j) * N + (size_t)wrapi(yt, ny) * nx + wrapi(x + cx(j), nx), v);
+            Store<S>::st(pout, (9 * set + j) * N + (unsigned)wrapi(yt, ny) * nx + wrapi(x + cx(j), nx), v);
         }
     };
 
     // phase populations, Eq. 34-36 with the mobility of Eq. 28
-    const R tf = R(P.tau_f), m0 = R(P.m0);
+    const R tf = R(P.tau_f), m0 = R(P.m0), itf = rcp(tf), im0 = rcp(m0);
+    const R pf = R(1) - R(1) / (R(2) * tf);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         R Mii = R(0);
@@ -512,8 +779,8 @@ __global__ void __launch_bounds__(TX * TY) k_fused(DevParams P, const S* __restr
             Yx += Mik * gmu[k][0];
             Yy += Mik * gmu[k][1];
         }
-        const R Ax = dpu[i][0] / cs2<R>() - Yx / m0;
-        const R Ay = dpu[i][1] / cs2<R>() - Yy / m0;
+        const R Ax = oc2(dpu[i][0]) - dv(Yx, m0, im0);
+        const R Ay = oc2(dpu[i][1]) - dv(Yy, m0, im0);
         const R mui = smu[i][my * MX + mx];
         R fv[9];
 #pragma unroll
@@ -527,9 +794,9 @@ __global__ void __launch_bounds__(TX * TY) k_fused(DevParams P, const S* __restr
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
             const R feq = (j == 0) ? ph[i] - (R(1) - wgt<R>(0)) * mui
-                                   : wgt<R>(j) * mui + wgt<R>(j) * (R(cx(j)) * ph[i] * ux + R(cy(j)) * ph[i] * uy) / cs2<R>();
+                                   : wgt<R>(j) * mui + oc2(wgt<R>(j) * (R(cx(j)) * ph[i] * ux + R(cy(j)) * ph[i] * uy));
             const R Fj = wgt<R>(j) * (R(cx(j)) * Ax + R(cy(j)) * Ay);
-            const R v = fv[j] - (fv[j] - feq) / tf + (R(1) - R(1) / (R(2) * tf)) * Fj;
+            const R v = fv[j] - dv(fv[j] - feq, tf, itf) + pf * Fj;
             push(i + 1, j, (anchored<S>() && j == 0) ? v - ph[i] : v);
         }
     }
@@ -544,18 +811,19 @@ __global__ void __launch_bounds__(TX * TY) k_fused(DevParams P, const S* __restr
             tg = R(0.5) + eta / (rho * cs2<R>());
         }
         const R uw = y == 0 ? R(P.u_wall_bottom) : R(P.u_wall_top);
+        const R itg = rcp(tg), pg = R(1) - R(1) / (R(2) * tg);
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
-            const R geq = (j == 0) ? (wgt<R>(0) - R(1)) * pr / cs2<R>() + rho * s_eq<R>(0, ux, uy)
-                                   : wgt<R>(j) * pr / cs2<R>() + rho * s_eq<R>(j, ux, uy);
+            const R geq = (j == 0) ? oc2((wgt<R>(0) - R(1)) * pr) + rho * s_eq<R>(0, ux, uy)
+                                   : oc2(wgt<R>(j) * pr) + rho * s_eq<R>(j, ux, uy);
             const R cu = R(cx(j)) * ux + R(cy(j)) * uy;
             const R cgr = R(cx(j)) * grx + R(cy(j)) * gry;
             const R cF = R(cx(j)) * Fx + R(cy(j)) * Fy;
-            const R G = wgt<R>(j) * (ugr + cF / cs2<R>() + (cu * cgr - cs2<R>() * ugr) / cs2<R>());
-            const R v = g[j] - (g[j] - geq) / tg + (R(1) - R(1) / (R(2) * tg)) * G;
+            const R G = wgt<R>(j) * (ugr + oc2(cF) + oc2(cu * cgr - cs2<R>() * ugr));
+            const R v = g[j] - dv(g[j] - geq, tg, itg) + pg * G;
             const int yt = y + cy(j);
             if (walls && (yt < 0 || yt >= ny))  // g_opp = g* - 2 w rho (c . u_w) / cs2
-                push(0, j, v - R(2) * wgt<R>(j) * rho * (R(cx(j)) * uw) / cs2<R>());
+                push(0, j, v - oc2(R(2) * wgt<R>(j) * rho * (R(cx(j)) * uw)));
             else
                 push(0, j, v);
         }
@@ -563,19 +831,25 @@ __global__ void __launch_bounds__(TX * TY) k_fused(DevParams P, const S* __restr
 
     // charge populations, Eq. 48-50
     {
-        const R tl = R(P.tau_l);
+        const R tl = R(P.tau_l), itl = rcp(tl), pl = R(1) - R(1) / (R(2) * tl);
         const bool cc = P.charge_convection != 0;
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
             const R cu = R(cx(j)) * ux + R(cy(j)) * uy;
-            const R leq = cc ? wgt<R>(j) * qc * (R(1) + cu / cs2<R>()) : wgt<R>(j) * qc;
-            const R Sj = (R(1) - R(1) / (R(2) * tl)) * wgt<R>(j) * Rc;
-            const R Tj = cc ? (R(1) - R(1) / (R(2) * tl)) * wgt<R>(j) * (R(cx(j)) * dqu[0] + R(cy(j)) * dqu[1]) / cs2<R>()
-                            : R(0);
+            const R leq = cc ? wgt<R>(j) * qc * (R(1) + oc2(cu)) : wgt<R>(j) * qc;
+            const R Sj = pl * wgt<R>(j) * Rc;
+            const R Tj = cc ? oc2(pl * wgt<R>(j) * (R(cx(j)) * dqu[0] + R(cy(j)) * dqu[1])) : R(0);
             const R lj = Store<S>::ld(pin, (36 + j) * N + c);
-            push(4, j, lj - (lj - leq) / tl + Sj + Tj);
+            push(4, j, lj - dv(lj - leq, tl, itl) + Sj + Tj);
         }
     }
+}
+template <class R, class S>
+__global__ void __launch_bounds__(TX * TY, fused_min_blocks<R>()) k_fused(DevParams P, const S* __restrict__ pin, S* __restrict__ pout,
+                                                   const R* __restrict__ phi, const R* __restrict__ qf,
+                                                   const R* __restrict__ E, R* __restrict__ prev,
+                                                   R* __restrict__ diag, int first, int write_diag) {
+    body_fused<R, S>(P, pin, pout, phi, qf, E, prev, diag, first, write_diag, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 // ---------------------------------------------------------------- initial populations
@@ -586,7 +860,7 @@ __global__ void k_init_pops(DevParams P, S* __restrict__ pop, const R* __restric
                             const R* __restrict__ E, R* __restrict__ diag) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
-    const size_t N = P.N, c = (size_t)y * P.nx + x;
+    const unsigned N = P.N, c = (unsigned)y * P.nx + x;
     const R ux = diag[c], uy = diag[N + c];
     const R Ex = E[c], Ey = E[N + c];
     const R e2 = Ex * Ex + Ey * Ey;
@@ -601,7 +875,7 @@ __global__ void k_init_pops(DevParams P, S* __restrict__ pop, const R* __restric
             a += R(2) * wgt<R>(j) * (f[(size_t)ghost_row(y + cy(j), P.ny, P.bc_y) * P.nx + wrapi(x + cx(j), P.nx)] - cc);
         const R lap = a / cs2<R>();
         ph[i] = cc;
-        const R mui = chem_pot<R>(P, i, cc, lap, e2);
+        const R mui = chem_pot<R>(P, i, cc, lap, e2, R(24) / R(P.D));
         diag[(3 + i) * N + c] = mui;
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
@@ -643,6 +917,16 @@ __global__ void k_to_f64(double* __restrict__ dst, const T* __restrict__ src, si
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i < n) dst[i] = (double)src[i];
 }
+// component `comp` of a dual field (0 value, k >= 1 tangent k-1) as doubles
+template <class R>
+__global__ void k_comp_to_f64(double* __restrict__ dst, const R* __restrict__ src, size_t n, int comp) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if constexpr (is_dual<R>::value)
+        dst[i] = comp == 0 ? (double)src[i].v : (double)src[i].d[comp - 1];
+    else
+        dst[i] = (double)src[i];
+}
 template <class R, class S>
 __global__ void k_pop_to_f64(double* __restrict__ dst, const S* __restrict__ pop, const R* __restrict__ phi,
                              int set, int j, size_t N) {
@@ -667,7 +951,7 @@ __global__ void __launch_bounds__(256) k_observables(DevParams P, const R* __res
 #pragma unroll
     for (int k = 0; k < NOBS; ++k) v[k] = 0.0;
     if (x < P.nx && y < P.ny) {
-        const size_t N = P.N, c = (size_t)y * P.nx + x;
+        const unsigned N = P.N, c = (unsigned)y * P.nx + x;
         const double D = P.D;
         double ph[3];
         for (int i = 0; i < 3; ++i) {
@@ -686,13 +970,13 @@ __global__ void __launch_bounds__(256) k_observables(DevParams P, const R* __res
         }
         double eps = 0.0;
         for (int i = 0; i < 3; ++i) eps += P.eps[i] * ph[i] * ph[i] * (3.0 - 2.0 * ph[i]);
-        const double Ex = E[c], Ey = E[N + c];
+        const double Ex = (double)E[c], Ey = (double)E[N + c];
         v[5] = 0.5 * eps * (Ex * Ex + Ey * Ey);
         const double rho = ph[0] * P.rho[0] + ph[1] * P.rho[1] + ph[2] * P.rho[2];
-        const double ux = diag[c], uy = diag[N + c];
+        const double ux = (double)diag[c], uy = (double)diag[N + c];
         v[6] = 0.5 * rho * (ux * ux + uy * uy);
         const double sg = ph[0] * P.sigma[0] + ph[1] * P.sigma[1] + ph[2] * P.sigma[2];
-        const double qc = q[c];
+        const double qc = (double)q[c];
         if (sg > 0) v[7] = 0.5 * (P.alpha / sg) * qc * qc;
         v[3] = qc;
         const double vals[6] = {ph[0], ph[1], ph[2], ux, uy, qc};
@@ -716,7 +1000,7 @@ __global__ void __launch_bounds__(256) k_maxdev(DevParams P, const R* __restrict
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     double m = 0.0;
     if (x < P.nx && y < P.ny) {
-        const size_t N = P.N, c = (size_t)y * P.nx + x;
+        const unsigned N = P.N, c = (unsigned)y * P.nx + x;
         m = fabs((double)phi[c] + (double)phi[N + c] + (double)phi[2 * N + c] - 1.0);
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
@@ -742,6 +1026,68 @@ static __global__ void k_max_partials(const double* __restrict__ partial, int n,
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) a = fmax(a, red[k]);
         *out = a;
     }
+}
+
+}  // namespace lb3e
+
+namespace lb3e {
+
+// ---------------------------------------------------------------- batched launches
+// Many lattices of different sizes stepped together: each block takes one tile
+// from a work list (instance, tile x, tile y) and runs the same tile body as the
+// single-lattice kernels on that instance's parameters and buffers.
+template <class R, class S>
+struct InstState {
+    DevParams P;
+    S* pop[2];
+    R* h[2];
+    R *phi, *qt, *q, *eps, *E, *prev, *diag;
+};
+
+template <class R, class S>
+__global__ void __launch_bounds__(256) kb_moments(const InstState<R, S>* __restrict__ st, const int4* __restrict__ tiles,
+                                                  int cur) {
+    const int4 t = tiles[blockIdx.x];
+    const InstState<R, S>& e = st[t.x];
+    body_moments<R, S>(e.P, e.pop[cur], e.phi, e.phi, e.qt, t.y, t.z, 0);
+}
+template <class R, class S>
+__global__ void __launch_bounds__(256) kb_prologue(const InstState<R, S>* __restrict__ st, const int4* __restrict__ tiles) {
+    const int4 t = tiles[blockIdx.x];
+    const InstState<R, S>& e = st[t.x];
+    body_prologue<R>(e.P, e.phi, e.qt, e.E, e.q, e.eps, 1, t.y, t.z, 0);
+}
+template <class R, class S>
+__global__ void __launch_bounds__(256) kb_poisson(const InstState<R, S>* __restrict__ st, const int4* __restrict__ tiles,
+                                                  int hcur) {
+    const int4 t = tiles[blockIdx.x];
+    const InstState<R, S>& e = st[t.x];
+    if (!e.P.electric) return;
+    body_poisson<R>(e.P, e.h[hcur], e.h[hcur ^ 1], e.eps, e.q, nullptr, nullptr, 0, 0, t.y, t.z, 0);
+}
+// K pseudo-iterations per launch over the 32 x 16 tiles of all instances
+template <class R, class S>
+__global__ void __launch_bounds__(PB_THREADS, pb_min_blocks<R>())
+    kb_poisson_tb(const InstState<R, S>* __restrict__ st, const int4* __restrict__ tiles, int hcur, int K) {
+    const int4 t = tiles[blockIdx.x];
+    const InstState<R, S>& e = st[t.x];
+    if (!e.P.electric) return;
+    body_poisson_tb<R>(e.P, e.h[hcur], e.h[hcur ^ 1], e.eps, e.q, nullptr, nullptr, K, 0, 0, t.y, t.z, 0);
+}
+template <class R, class S>
+__global__ void __launch_bounds__(256) kb_potential_fields(const InstState<R, S>* __restrict__ st,
+                                                           const int4* __restrict__ tiles, int hcur) {
+    const int4 t = tiles[blockIdx.x];
+    const InstState<R, S>& e = st[t.x];
+    if (!e.P.electric) return;
+    body_potential_fields<R>(e.P, e.h[hcur], e.eps, e.E, nullptr, t.y, t.z, 0);
+}
+template <class R, class S>
+__global__ void __launch_bounds__(TX * TY, fused_min_blocks<R>())
+    kb_fused(const InstState<R, S>* __restrict__ st, const int4* __restrict__ tiles, int cur, int first, int write_diag) {
+    const int4 t = tiles[blockIdx.x];
+    const InstState<R, S>& e = st[t.x];
+    body_fused<R, S>(e.P, e.pop[cur], e.pop[cur ^ 1], e.phi, e.q, e.E, e.prev, e.diag, first, write_diag, t.y, t.z, 0);
 }
 
 }  // namespace lb3e

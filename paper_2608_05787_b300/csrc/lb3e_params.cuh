@@ -42,6 +42,15 @@ inline DevParams make_dev_params(const lb3e_params& p) {
     d.E_ext[1] = p.E_ext[1];
     d.u_wall_bottom = p.u_wall_bottom;
     d.u_wall_top = p.u_wall_top;
+    // tangent seeds: d lambda_i / d gamma_jk from Eq. 9
+    static const double dlam[3][3] = {{1, 1, -1}, {1, -1, 1}, {-1, 1, 1}};
+    for (int k = 0; k < 3; ++k) {
+        const int id = p.tangent_param[k];
+        if (id == 0) d.t_Vt[k] = 1.0;
+        if (id >= 1 && id <= 3) d.t_eps[id - 1][k] = 1.0;
+        if (id >= 4 && id <= 6)
+            for (int i = 0; i < 3; ++i) d.t_lam[i][k] = dlam[i][id - 4];
+    }
     return d;
 }
 

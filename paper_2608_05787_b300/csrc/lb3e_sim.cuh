@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <vector>
 
 #include "lb3e_internal.h"
 #include "lb3e_kernels.cuh"
@@ -45,7 +46,10 @@ class Sim final : public SimBase {
         L.psi_prev = take(3 * N * sizeof(R));
         L.partial = take(nblk * NOBS * sizeof(double));
         L.result = take(64 * sizeof(double));
-        L.stage = take(9 * N * sizeof(double));
+        // FP64 staging: 9 planes, or room for 4 planes of R after the first plane
+        L.stage = take(9 * N * sizeof(double) > N * sizeof(double) + 4 * N * sizeof(R)
+                           ? 9 * N * sizeof(double)
+                           : N * sizeof(double) + 4 * N * sizeof(R));
         L.total = o;
         return L;
     }
@@ -204,6 +208,16 @@ class Sim final : public SimBase {
 
     int get_field(int id, double* dst) override {
         const R* src = nullptr;
+        int comp = 0;  // tangent builds: component 0 value, k >= 1 tangent k-1
+        if (id >= LB3E_TANGENT) {
+            comp = id / LB3E_TANGENT;
+            id %= LB3E_TANGENT;
+            if constexpr (is_dual<R>::value) {
+                if (comp > (int)(sizeof(R().d) / sizeof(R().d[0]))) return LB3E_ERR_FIELD;
+            } else {
+                return LB3E_ERR_FIELD;
+            }
+        }
         switch (id) {
             case LB3E_FIELD_PHI1: case LB3E_FIELD_PHI2: case LB3E_FIELD_PHI3: src = d_.phi + (id - LB3E_FIELD_PHI1) * N_; break;
             case LB3E_FIELD_UX: src = d_.diag; break;
@@ -214,25 +228,27 @@ class Sim final : public SimBase {
             case LB3E_FIELD_EY: src = d_.E + N_; break;
             case LB3E_FIELD_MU1: case LB3E_FIELD_MU2: case LB3E_FIELD_MU3: src = d_.diag + (3 + id - LB3E_FIELD_MU1) * N_; break;
             case LB3E_FIELD_PSI:
+                if (comp) return LB3E_ERR_FIELD;
                 timer.begin(stream_, KC_FIELDS);
                 k_potential_fields<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[hcur_], d_.eps, d_.E, d_.stage);
                 TRY(launched());
                 return copy_out(dst, d_.stage);
             case LB3E_FIELD_PHINOW1: case LB3E_FIELD_PHINOW2: case LB3E_FIELD_PHINOW3: case LB3E_FIELD_QTILDE: {
                 // moments of the current populations into scratch planes of the other buffer's view
-                R* tmp = reinterpret_cast<R*>(d_.stage + 5 * N_);  // 4 N R-values fit in 4 N doubles
+                R* tmp = reinterpret_cast<R*>(d_.stage + N_);  // 4 N R-values after the output plane
                 timer.begin(stream_, KC_MOMENTS);
                 k_moments<R, S><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.pop[cur_], d_.phi, tmp, tmp + 3 * N_);
                 TRY(launched());
                 const R* t = id == LB3E_FIELD_QTILDE ? tmp + 3 * N_ : tmp + (id - LB3E_FIELD_PHINOW1) * N_;
                 timer.begin(stream_, KC_OTHER);
-                k_to_f64<R><<<blocks1(N_), 256, 0, stream_>>>(d_.stage, t, N_);
+                k_comp_to_f64<R><<<blocks1(N_), 256, 0, stream_>>>(d_.stage, t, N_, comp);
                 TRY(launched());
                 return copy_out(dst, d_.stage);
             }
             default: break;
         }
         if (!src && id >= LB3E_FIELD_POP && id < LB3E_FIELD_POP + 54) {
+            if (comp) return LB3E_ERR_FIELD;
             const int set = (id - LB3E_FIELD_POP) / 9, j = (id - LB3E_FIELD_POP) % 9;
             if (set < 5) {
                 timer.begin(stream_, KC_OTHER);
@@ -246,7 +262,7 @@ class Sim final : public SimBase {
         }
         if (!src) return LB3E_ERR_FIELD;
         timer.begin(stream_, KC_OTHER);
-        k_to_f64<R><<<blocks1(N_), 256, 0, stream_>>>(d_.stage, src, N_);
+        k_comp_to_f64<R><<<blocks1(N_), 256, 0, stream_>>>(d_.stage, src, N_, comp);
         TRY(launched());
         return copy_out(dst, d_.stage);
     }
@@ -288,6 +304,7 @@ class Sim final : public SimBase {
         return LB3E_OK;
     }
 
+    int64_t potential_iterations() const override { return poisson_iters_run_; }
     int kernel_times(double* ms, int64_t* counts) override {
         TRY(sync());
         timer.collect();
@@ -298,6 +315,24 @@ class Sim final : public SimBase {
             timer.n[k] = 0;
         }
         return LB3E_OK;
+    }
+
+    // --- used by Batch: device buffers, and bookkeeping after steps run elsewhere
+    const DevState<R, S>& dev() const { return d_; }
+    const DevParams& dev_params() const { return dp_; }
+    int cur() const { return cur_; }
+    int hcur() const { return hcur_; }
+    int64_t steps_done() const { return step_; }
+    void stepped_externally(int nsteps, int iters_per_step, int swaps_per_step) {
+        if (p_.electric) {
+            hcur_ ^= (int)(((int64_t)nsteps * swaps_per_step) & 1);
+            poisson_iters_run_ += (int64_t)nsteps * iters_per_step;
+            last_iters_ = iters_per_step;
+            last_conv_ = 1;
+            last_res_ = -1.0;
+        }
+        cur_ ^= nsteps & 1;
+        step_ += nsteps;
     }
 
   private:
@@ -324,29 +359,77 @@ class Sim final : public SimBase {
         }
         return LB3E_OK;
     }
+    // sum nb x 4 block partials into result[0..3]: 148 first-stage blocks write
+    // their sums after the partial rows (the partial area holds nblk x NOBS
+    // doubles, and 4 * nb + 4 * 148 fits for every grid), then one block adds those
+    int reduce4(int nb) {
+        const int s1 = nb < 148 ? 1 : 148;
+        const int chunk = (nb + s1 - 1) / s1;
+        double* mid = d_.partial + 4 * (size_t)nb;
+        timer.begin(stream_, KC_REDUCE);
+        k_reduce_stage1<4><<<s1, 256, 0, stream_>>>(d_.partial, nb, chunk, mid);
+        TRY(launched());
+        timer.begin(stream_, KC_REDUCE);
+        k_reduce_partials<4><<<1, 256, 0, stream_>>>(mid, s1, d_.result);
+        return launched();
+    }
     int copy_out(double* dst, const double* dsrc) {
         TRY(copy(dst, dsrc, N_ * sizeof(double)));
         return sync();
     }
 
-    // the pseudo-time potential solve (Eq. 43) from the current h
+    // the pseudo-time potential solve (Eq. 43) from the current h.  Iterations
+    // run in chunks of up to PB_HALO per launch (k_poisson_tb); a chunk never
+    // straddles a residual check, which is taken before the first collision of a
+    // chunk, and the state for the next check is saved before the last one.
     int poisson(double tol, int max_iter, int fixed, int check) {
         const int n = fixed > 0 ? fixed : max_iter;
         if (check < 1) check = 1;
         last_res_ = -1.0;
         last_conv_ = fixed > 0;
         last_iters_ = n;
-        for (int k = 1; k <= n; ++k) {
+        if constexpr (!is_dual<R>::value) {
+            if (!pb_ready_) {
+                if (cudaFuncSetAttribute(k_poisson_tb<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pb_smem_bytes<R>()) != cudaSuccess)
+                    return LB3E_ERR_CUDA;
+                pb_ready_ = true;
+            }
+        }
+        const dim3 pgrid((p_.nx + PB_TX - 1) / PB_TX, (p_.ny + PB_TY - 1) / PB_TY);
+        const int pblk = (int)(pgrid.x * pgrid.y);
+        int k = 1;
+        while (k <= n) {
+            int c = n - k + 1 < PB_HALO ? n - k + 1 : PB_HALO;
+            if (fixed <= 0) {
+                int next = (k / check + 1) * check;  // next check iteration after k
+                if (next < 2) next = 2;
+                if (next - k < c) c = next - k;
+            }
             const int do_check = fixed <= 0 && k >= 2 && k % check == 0;
-            const int save = fixed <= 0 && (k + 1) % check == 0;
-            timer.begin(stream_, KC_POISSON);
-            k_poisson<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q,
-                                                               d_.psi_prev, d_.partial, save, do_check);
-            TRY(launched());
-            if (do_check) {
-                timer.begin(stream_, KC_REDUCE);
-                k_reduce_partials<4><<<1, 256, 0, stream_>>>(d_.partial, nblk_, d_.result);
+            const int save = fixed <= 0 && (k + c) % check == 0;
+            bool blocked = false;
+            if constexpr (!is_dual<R>::value) {  // dual tiles would not fit in shared memory
+                if (c >= 2) {
+                    timer.begin(stream_, KC_POISSON);
+                    k_poisson_tb<R><<<pgrid, PB_THREADS, pb_smem_bytes<R>(), stream_>>>(
+                        dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q, d_.psi_prev, d_.partial, c, save, do_check);
+                    TRY(launched());
+                    poisson_iters_run_ += c;
+                    blocked = true;
+                }
+            }
+            if (!blocked) {
+                c = 1;
+                timer.begin(stream_, KC_POISSON);
+                k_poisson<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q,
+                                                                   d_.psi_prev, d_.partial, (k + 1) % check == 0 && fixed <= 0,
+                                                                   do_check);
                 TRY(launched());
+                poisson_iters_run_ += 1;
+            }
+            if (do_check) {
+                TRY(reduce4(blocked ? pblk : nblk_));
                 if (cudaMemcpyAsync(pinned_, d_.result, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream_) !=
                     cudaSuccess)
                     return LB3E_ERR_CUDA;
@@ -355,13 +438,14 @@ class Sim final : public SimBase {
                 const double r1 = pp > 0.0 ? std::sqrt(dp) / std::sqrt(pp) : (dp > 0.0 ? INFINITY : 0.0);
                 const double r2 = jj > 0.0 ? std::sqrt(dj) / std::sqrt(jj) : (dj > 0.0 ? INFINITY : 0.0);
                 last_res_ = r1 > r2 ? r1 : r2;
-                if (last_res_ <= tol) {  // the state before this iteration's collision is the answer
+                if (last_res_ <= tol) {  // the state before this chunk's first collision is the answer
                     last_conv_ = 1;
                     last_iters_ = k - 1;
                     break;
                 }
             }
             hcur_ ^= 1;
+            k += c;
         }
         timer.begin(stream_, KC_FIELDS);
         k_potential_fields<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[hcur_], d_.eps, d_.E, nullptr);
@@ -382,6 +466,222 @@ class Sim final : public SimBase {
     int last_iters_ = 0, last_conv_ = 0;
     double last_res_ = -1.0;
     double* pinned_ = nullptr;
+    bool pb_ready_ = false;
+
+  public:
+    int64_t poisson_iters_run_ = 0;  // pseudo-iterations executed (all solves)
+};
+
+// ---------------------------------------------------------------- batches
+// Instances of one precision stepped together.  Each instance is a Sim laid out
+// in its own slice of the caller's workspace; the batch adds a device table of
+// instance parameters/pointers and the tile work list, and replays each pair of
+// steps as one CUDA graph (potential iterations per step are fixed, so the
+// ping-pong parities return to where they started after two steps).
+template <class R, class S>
+class Batch final : public BatchBase {
+  public:
+    static size_t tiles_of(const lb3e_params& p) {
+        return (size_t)((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY);
+    }
+    static size_t ptiles_of(const lb3e_params& p) {
+        return (size_t)((p.nx + PB_TX - 1) / PB_TX) * ((p.ny + PB_TY - 1) / PB_TY);
+    }
+    static size_t bytes(const lb3e_params* ps, int n) {
+        size_t ntiles = 0, nptiles = 0, b = 0;
+        for (int i = 0; i < n; ++i) {
+            ntiles += tiles_of(ps[i]);
+            nptiles += ptiles_of(ps[i]);
+            b += align256(Sim<R, S>::layout(ps[i]).total);
+        }
+        return b + align256(n * sizeof(InstState<R, S>)) + align256(ntiles * sizeof(int4)) +
+               align256(nptiles * sizeof(int4));
+    }
+
+    Batch(const lb3e_params* ps, int n, void* ws, cudaStream_t st) : stream_(st), n_(n) {
+        char* b = static_cast<char*>(ws);
+        size_t ntiles = 0, nptiles = 0;
+        for (int i = 0; i < n; ++i) {
+            ntiles += tiles_of(ps[i]);
+            nptiles += ptiles_of(ps[i]);
+        }
+        table_ = reinterpret_cast<InstState<R, S>*>(b);
+        b += align256(n * sizeof(InstState<R, S>));
+        tiles_ = reinterpret_cast<int4*>(b);
+        b += align256(ntiles * sizeof(int4));
+        ptiles_ = reinterpret_cast<int4*>(b);
+        b += align256(nptiles * sizeof(int4));
+        ntiles_ = (int)ntiles;
+        nptiles_ = (int)nptiles;
+        iters_ = 0;
+        for (int i = 0; i < n; ++i) {
+            sims_.push_back(new Sim<R, S>(ps[i], b, st));
+            b += align256(Sim<R, S>::layout(ps[i]).total);
+            if (ps[i].electric) iters_ = ps[i].poisson_fixed_iter;
+        }
+    }
+    ~Batch() override {
+        for (auto& g : graphs_)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        for (auto* s : sims_) delete s;
+    }
+
+    int init(const double* const* phis) {
+        for (int i = 0; i < n_; ++i) TRY(sims_[i]->init(phis[i], nullptr, nullptr, nullptr));
+        std::vector<InstState<R, S>> tab(n_);
+        std::vector<int4> tl, ptl;
+        tl.reserve(ntiles_);
+        ptl.reserve(nptiles_);
+        for (int i = 0; i < n_; ++i) {
+            const auto& d = sims_[i]->dev();
+            InstState<R, S>& e = tab[i];
+            e.P = sims_[i]->dev_params();
+            e.pop[0] = d.pop[0];
+            e.pop[1] = d.pop[1];
+            e.h[0] = d.h[0];
+            e.h[1] = d.h[1];
+            e.phi = d.phi;
+            e.qt = d.qt;
+            e.q = d.q;
+            e.eps = d.eps;
+            e.E = d.E;
+            e.prev = d.prev;
+            e.diag = d.diag;
+            const int gx = (e.P.nx + TX - 1) / TX, gy = (e.P.ny + TY - 1) / TY;
+            for (int by = 0; by < gy; ++by)
+                for (int bx = 0; bx < gx; ++bx) tl.push_back(make_int4(i, bx, by, 0));
+            const int px = (e.P.nx + PB_TX - 1) / PB_TX, py = (e.P.ny + PB_TY - 1) / PB_TY;
+            for (int by = 0; by < py; ++by)
+                for (int bx = 0; bx < px; ++bx) ptl.push_back(make_int4(i, bx, by, 0));
+        }
+        // ping-pong parities shared by all instances (every electric instance ran
+        // the same fixed number of initial potential iterations)
+        cur_ = 0;
+        hcur_ = 0;
+        for (auto* s : sims_)
+            if (s->dev_params().electric) { hcur_ = s->hcur(); break; }
+        steps_ = 0;
+        if (cudaMemcpyAsync(table_, tab.data(), n_ * sizeof(InstState<R, S>), cudaMemcpyHostToDevice, stream_) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(tiles_, tl.data(), tl.size() * sizeof(int4), cudaMemcpyHostToDevice, stream_) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(ptiles_, ptl.data(), ptl.size() * sizeof(int4), cudaMemcpyHostToDevice, stream_) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(stream_) != cudaSuccess)
+            return LB3E_ERR_CUDA;
+        return LB3E_OK;
+    }
+
+    int run(int nsteps) override {
+        int done = 0;
+        while (done < nsteps) {
+            const int left = nsteps - done;
+            int k = 1;
+            if (steps_ > 0 && left > 2) {  // pairs of steps by graph; the last step stays a plain launch
+                cudaGraphExec_t g = nullptr;
+                TRY(graph_for(cur_, hcur_, &g));
+                if (cudaGraphLaunch(g, stream_) != cudaSuccess) return LB3E_ERR_CUDA;
+                launches += 2 * (3 + swaps() + (iters_ > 0));
+                k = 2;
+            } else {
+                TRY(issue_step(cur_, hcur_, steps_ == 0, left == 1));
+            }
+            for (auto* s : sims_) s->stepped_externally(k, iters_, swaps());
+            cur_ ^= k & 1;
+            hcur_ ^= (k * swaps()) & 1;
+            steps_ += k;
+            done += k;
+        }
+        return cudaStreamSynchronize(stream_) == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
+    }
+
+    int observables(lb3e_observables_t* out) override {
+        for (int i = 0; i < n_; ++i) TRY(sims_[i]->observables(out + i));
+        return LB3E_OK;
+    }
+    int get_field(int inst, int id, double* dst) override {
+        if (inst < 0 || inst >= n_) return LB3E_ERR_PARAM;
+        return sims_[inst]->get_field(id, dst);
+    }
+    int count() const override { return n_; }
+    int64_t total_launches() const override {
+        int64_t l = launches;
+        for (auto* s : sims_) l += s->launches;
+        return l;
+    }
+
+    // pseudo-iterations per potential launch (1: one iteration per launch; up to
+    // PB_HALO: temporally blocked); chosen by the caller's autotuner
+    int set_chunk(int k) override {
+        if (k < 1 || k > PB_HALO) return LB3E_ERR_PARAM;
+        if constexpr (is_dual<R>::value) return k == 1 ? LB3E_OK : LB3E_ERR_PARAM;
+        if (k > 1 && !pb_ready_) {
+            if (cudaFuncSetAttribute(kb_poisson_tb<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pb_smem_bytes<R>()) != cudaSuccess)
+                return LB3E_ERR_CUDA;
+            pb_ready_ = true;
+        }
+        chunk_ = k;
+        return LB3E_OK;
+    }
+
+  private:
+    struct Graph {
+        int cur, hcur, chunk;
+        cudaGraphExec_t exec;
+    };
+    // potential launches per step (each swaps the h buffers once)
+    int swaps() const { return iters_ == 0 ? 0 : (chunk_ <= 1 ? iters_ : (iters_ + chunk_ - 1) / chunk_); }
+    int issue_step(int cur, int hcur, bool first, bool diag) {
+        const dim3 blk(TX, TY);
+        kb_moments<R, S><<<ntiles_, blk, 0, stream_>>>(table_, tiles_, cur);
+        kb_prologue<R, S><<<ntiles_, blk, 0, stream_>>>(table_, tiles_);
+        int h = hcur;
+        if (chunk_ <= 1) {
+            for (int k = 0; k < iters_; ++k, h ^= 1) kb_poisson<R, S><<<ntiles_, blk, 0, stream_>>>(table_, tiles_, h);
+        } else {
+            for (int k = 0; k < iters_; k += chunk_, h ^= 1) {
+                const int c = iters_ - k < chunk_ ? iters_ - k : chunk_;
+                kb_poisson_tb<R, S><<<nptiles_, PB_THREADS, pb_smem_bytes<R>(), stream_>>>(table_, ptiles_, h, c);
+            }
+        }
+        if (iters_ > 0) kb_potential_fields<R, S><<<ntiles_, blk, 0, stream_>>>(table_, tiles_, h);
+        kb_fused<R, S><<<ntiles_, blk, 0, stream_>>>(table_, tiles_, cur, first ? 1 : 0, diag ? 1 : 0);
+        launches += 3 + swaps() + (iters_ > 0);
+        return cudaGetLastError() == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
+    }
+    int graph_for(int cur, int hcur, cudaGraphExec_t* out) {
+        for (auto& g : graphs_)
+            if (g.cur == cur && g.hcur == hcur && g.chunk == chunk_) { *out = g.exec; return LB3E_OK; }
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LB3E_ERR_CUDA;
+        const int64_t l0 = launches;
+        int rc = issue_step(cur, hcur, false, false);
+        if (rc == LB3E_OK) rc = issue_step(cur ^ 1, hcur ^ (swaps() & 1), false, false);
+        launches = l0;  // counted when the graph is launched
+        if (cudaStreamEndCapture(stream_, &graph) != cudaSuccess || rc != LB3E_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return LB3E_ERR_CUDA;
+        }
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return LB3E_ERR_CUDA;
+        graphs_.push_back({cur, hcur, chunk_, exec});
+        *out = exec;
+        return LB3E_OK;
+    }
+
+    cudaStream_t stream_;
+    int n_ = 0, ntiles_ = 0, nptiles_ = 0, iters_ = 0, chunk_ = 1;
+    bool pb_ready_ = false;
+    int cur_ = 0, hcur_ = 0;
+    int64_t steps_ = 0;
+    InstState<R, S>* table_ = nullptr;
+    int4* tiles_ = nullptr;
+    int4* ptiles_ = nullptr;
+    std::vector<Sim<R, S>*> sims_;
+    std::vector<Graph> graphs_;
 };
 
 }  // namespace lb3e

@@ -1,0 +1,89 @@
+"""Batched stepping (many lattices of uneven sizes in one set of launches, pairs
+of steps replayed as a CUDA graph) against single-lattice runs and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _instances(precision, iters=6):
+    specs = [(48, 40, 1.0, 2.0), (64, 64, 4.0, 0.5), (37, 29, 0.7, 1.3), (32, 24, 2.0, 2.0)]
+    out = []
+    for k, (nx, ny, s_ratio, r_ratio) in enumerate(specs):
+        r_out = 0.25 * min(nx, ny)
+        p = W.params(nx=nx, ny=ny, bc_y=2, electric=1, precision=precision, eps=(1.0, (s_ratio) ** 0.5, s_ratio),
+                     sigma=(1.0, r_ratio ** 0.5, r_ratio), eps_ref=max(1.0, s_ratio), V_top=0.02 * (k + 1),
+                     poisson_fixed_iter=iters)
+        out.append((p, W.compound_droplet(nx, ny, 0.5 * r_out, r_out, 4.0)))
+    return out
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_batch_equals_single_lattice_runs(precision):
+    """Every instance of a batch is bitwise the lattice stepped alone (the same
+    tile bodies run on the same data), over 9 steps: plain, graph pairs, plain."""
+    import paper_2608_05787_b300 as L
+    inst = _instances(precision)
+    b = L.Batch([p for p, _ in inst], [phi for _, phi in inst])
+    b.run(4)
+    b.run(5)
+    obs = b.observables()
+    for i, (p, phi) in enumerate(inst):
+        s = L.Sim(p, phi)
+        s.step(4)
+        s.step(5)
+        for f in ("phinow1", "phinow2", "phinow3", "psi", "ex", "ey", "ux", "p", "q"):
+            assert np.array_equal(b.field(i, f), s.field(f)), (i, f)
+        so = s.observables()
+        assert obs[i]["D_outer"] == so["D_outer"] and obs[i]["step"] == 9
+
+
+def test_batch_fp64_matches_oracle():
+    import paper_2608_05787_b300 as L
+    inst = _instances(0, iters=5)
+    b = L.Batch([p for p, _ in inst], [phi for _, phi in inst])
+    b.run(12)
+    for i in (0, 2):
+        p, phi = inst[i]
+        o = oracle.Oracle(p, phi)
+        o.step(12)
+        for f in ("phinow1", "phinow2", "phinow3", "psi", "ex", "ey", "q", "ux"):
+            ref = o.field(f)
+            err = np.abs(b.field(i, f) - ref).max() / max(np.abs(ref).max(), 1e-300)
+            assert err <= 1e-12, (i, f, err)
+
+
+@pytest.mark.parametrize("chunk", [2, 3, 8])
+def test_blocked_potential_chunks_give_the_same_state(chunk):
+    """Temporal blocking depth changes the launches, not the result: FP64 batches
+    with 1 and `chunk` iterations per launch agree bitwise."""
+    import paper_2608_05787_b300 as L
+    inst = _instances(0, iters=7)
+    a = L.Batch([p for p, _ in inst], [phi for _, phi in inst])
+    b = L.Batch([p for p, _ in inst], [phi for _, phi in inst]).set_chunk(chunk)
+    a.run(6)
+    b.run(6)
+    for i in range(len(inst)):
+        for f in ("phinow1", "phinow3", "psi", "ex", "ux"):
+            assert np.array_equal(a.field(i, f), b.field(i, f)), (chunk, i, f)
+
+
+def test_autotuner_picks_a_candidate_and_caches(tmp_path, monkeypatch):
+    from paper_2608_05787_b300 import autotune
+    monkeypatch.setenv("LB3E_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    inst = _instances(1, iters=8)
+    k = autotune.tune_batch_chunk([p for p, _ in inst], steps=2)
+    assert k in autotune.CANDIDATES
+    assert autotune.tune_batch_chunk([p for p, _ in inst]) == k     # served from the cache
+    assert (tmp_path / "tune.json").exists()
+
+
+def test_batch_rejects_mixed_iteration_counts():
+    import paper_2608_05787_b300 as L
+    inst = _instances(1)
+    inst[1][0]["poisson_fixed_iter"] = 7
+    with pytest.raises(L.LB3EError):
+        L.Batch([p for p, _ in inst], [phi for _, phi in inst])

@@ -1,0 +1,68 @@
+"""Spreading liquid lens (512 x 256, walls, no field): Neumann-triangle angles and
+chord (Eq. 57-58), FP32 against FP64 after the stated 20 000 steps, and FP64
+parity with the oracle at full size over a shorter horizon.
+
+Labels: phase 1 upper layer, phase 2 lower layer, phase 3 lens (radius 40).
+Angles are measured from the flat upper|lower interface: the upper cap meets it
+at theta_up, with cos theta_up = (g12^2 + g13^2 - g23^2) / (2 g12 g13), and the
+lower cap at theta_low likewise with 13 <-> 23.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from lens_geometry import measure_lens, neumann
+
+pytestmark = pytest.mark.gpu
+
+TRIPLES = [(1e-3, 1e-3, 1e-3), (1e-3, 8e-4, 6e-4)]
+
+
+def _run(precision, tens, steps):
+    import paper_2608_05787_b300 as L
+    cfg = W.config_lens(tensions=tens, precision=precision)
+    sim = L.Sim(cfg["params"], cfg["phi"])
+    sim.step(steps)
+    return sim
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("tens", TRIPLES)
+def test_lens_neumann_angles_and_chord(tens):
+    sim = _run(1, tens, 20000)
+    p1, p2, p3 = (sim.field(f"phinow{i}") for i in (1, 2, 3))
+    th_up, th_lo, d = measure_lens(p1, p2, p3)
+    a_up, a_lo, a_d = neumann(*tens, area=float(p3.sum()))
+    print(f"lens {tens}: theta_up {th_up:.2f} (Neumann {a_up:.2f}), theta_low {th_lo:.2f} "
+          f"({a_lo:.2f}), d {d:.2f} ({a_d:.2f})")
+    assert abs(th_up / a_up - 1) < 0.08
+    assert abs(th_lo / a_lo - 1) < 0.08
+    assert abs(d / a_d - 1) < 0.05
+
+
+@pytest.mark.slow
+def test_lens_fp32_against_fp64_after_20000_steps():
+    tens = TRIPLES[1]
+    s64 = _run(0, tens, 20000)
+    s32 = _run(1, tens, 20000)
+    errs = {}
+    for f in ("phinow1", "phinow2", "phinow3"):
+        a, b = s32.field(f), s64.field(f)
+        errs[f] = float(np.abs(a - b).max() / np.abs(b).max())
+    print("lens fp32 vs fp64 rel Linf after 20000 steps:", errs)
+    assert max(errs.values()) <= 1e-5
+
+
+@pytest.mark.slow
+def test_lens_fp64_full_size_parity_with_oracle():
+    tens = TRIPLES[1]
+    cfg = W.config_lens(tensions=tens, precision=0)
+    import paper_2608_05787_b300 as L
+    sim = L.Sim(cfg["params"], cfg["phi"])
+    orc = oracle.Oracle(cfg["params"], cfg["phi"])
+    sim.step(150)
+    orc.step(150)
+    for f in ("phinow1", "phinow2", "phinow3", "ux", "uy", "p", "mu1", "mu3"):
+        ref = orc.field(f)
+        assert np.abs(sim.field(f) - ref).max() <= 1e-12 * np.abs(ref).max(), f
