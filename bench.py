@@ -45,8 +45,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lb3e", choices=["lb3e", "reference"])
-    ap.add_argument("--workload", default="deformation", choices=["deformation", "sweep"],
-                    help="deformation: the 4096^2 lattice (default); sweep: 256 lattices in one batch")
+    ap.add_argument("--workload", default="deformation", choices=["deformation", "sweep", "adjoint"],
+                    help="deformation: the 4096^2 lattice (default); sweep: 256 lattices in one batch; "
+                         "adjoint: cost of the three parameter derivatives relative to a forward step")
     ap.add_argument("--precision", type=int, default=1, help="0 fp64, 1 fp32, 2 fp32 + fp16-stored populations")
     ap.add_argument("--n", type=int, default=4096, help="lattice side (the stated workload is 4096)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -139,30 +140,28 @@ def _oracle_sample(n: int, iters: int):
     return oracle.Oracle(dict(cfg["params"], poisson_fixed_iter=iters), cfg["phi"])
 
 
-def _timed_oracle_step(n: int, iters: int) -> float:
-    o = _oracle_sample(n, iters)
-    t0 = time.perf_counter()
-    o.step(1)
-    return time.perf_counter() - t0
-
-
 def cpu_baseline(args, iters_per_step: float):
     """The oracle, as it stands, on the host cores, on a bounded sample of the
-    workload: a cpu_sample^2 lattice with the geometry scaled.  One step is timed
-    with 2 and with 6 potential iterations (init untimed); the difference gives the
-    cost of one iteration, and the step time is projected to the potential
+    workload: a cpu_sample^2 lattice with the geometry scaled.  Timed (init
+    excluded): one time step with a single potential iteration, and 40 potential
+    iterations on their own; the step time is projected to the potential
     iterations per step that the GPU needed."""
     n = args.cpu_sample
-    t2 = _timed_oracle_step(n, 2)
-    t6 = _timed_oracle_step(n, 6)
-    per_iter = max(0.0, (t6 - t2) / 4.0)
-    base = max(1e-9, t2 - 2 * per_iter)
+    o = _oracle_sample(n, 1)
+    t0 = time.perf_counter()
+    o.step(1)
+    t_step1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.solve_potential(fixed=40, max_iter=40)
+    per_iter = (time.perf_counter() - t0) / 40
+    base = max(1e-9, t_step1 - per_iter)
     it = args.cpu_iters or iters_per_step
     dt = base + it * per_iter
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": n * n / dt / 1e6, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": f"{n}x{n} lattice of the same workload (radii scaled): one step timed with 2 and 6 "
-                      f"potential iterations, projected to {it:.1f} iterations per step (the GPU's mean); init untimed",
+            "sample": f"{n}x{n} lattice of the same workload (radii scaled): one step with 1 potential iteration "
+                      f"and 40 potential iterations timed separately, projected to {it:.1f} iterations per step "
+                      "(the GPU's mean); init untimed",
             "seconds_per_step": dt, "seconds_per_potential_iteration": per_iter, "seconds_rest_of_step": base}
 
 
@@ -361,9 +360,12 @@ def run_sweep(args):
     insts = W.config_batched_sweep(precision=args.precision)
     cells = [i["shape"][0] * i["shape"][1] for i in insts]
     mine = shard(cells, ws)[rank]
+    from paper_2608_05787_b300.autotune import tune_batch_chunk
+    chunk = tune_batch_chunk([insts[i]["params"] for i in mine])
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         b = L.Batch([insts[i]["params"] for i in mine], [W.sweep_phi(insts[i]) for i in mine], stream=stream)
+        b.set_chunk(chunk)
         b.run(args.warmup)
         torch.cuda.synchronize()
         if dist:
@@ -392,7 +394,7 @@ def run_sweep(args):
                 "dtype": {0: "f64", 1: "f32", 2: "f32 (f16-stored populations)"}[args.precision],
                 "data": "synthetic (seeded sweep of the stated parameter ranges)",
                 "config": {"workload": "batched sweep: 256 compound drops, sides {128,192,256,384,512}",
-                           "cells": sum(cells), "potential_iters_per_step": 16,
+                           "cells": sum(cells), "potential_iters_per_step": 16, "autotuned_chunk": chunk,
                            "parallelism": f"instances sharded over {ws} ranks" if ws > 1 else "one batch"},
                 "roofline": {"bound": "hbm", "achieved": per_cell * total / t / 1e9, "peak": hbm, "unit": "GB/s",
                              "frac": per_cell * total / t / 1e9 / hbm, "traffic": None,
@@ -405,12 +407,50 @@ def run_sweep(args):
         dist.destroy_process_group()
 
 
+def run_adjoint(args):
+    """Derivative cost on the 256^2 drop under field plus shear: time per step of
+    the FP32 tangent build (three parameter directions: E0, eps3, gamma23) over the
+    time per step of the plain FP32 build, potential iterated 16 times per step."""
+    import torch
+    import paper_2608_05787_b300 as L
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    cfg = W.config_adjoint()
+    p = dict(cfg["params"], poisson_fixed_iter=16)
+    res = {}
+    for name, prec, extra in (("forward", 1, {}), ("tangent3", 3, {"tangent_param": (0, 3, 6)})):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            sim = L.Sim(dict(p, precision=prec, **extra), cfg["phi"], stream=stream)
+            sim.step(args.warmup)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[name] = e0.elapsed_time(e1) / args.steps
+            sim.close()
+    N = p["nx"] * p["ny"]
+    line = {"metric": "derivative/forward time per step", "value": res["tangent3"] / res["forward"],
+            "unit": "ratio", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["tangent3"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (dual numbers, 3 directions)", "data": "synthetic (stated initial condition)",
+            "config": {"workload": "compound drop under field + shear, 256x256", "potential_iters_per_step": 16,
+                       "forward_ms_per_step": res["forward"], "forward_mlups": N / res["forward"] / 1e3,
+                       "derivatives": ["dD/dE0", "dD/d(eps3/eps1)", "dD/dgamma23"], "mode": "tangent (forward)"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_lb3e(args)
 

@@ -209,7 +209,9 @@ int lb3e_kernel_times(lb3e_handle* h, double* ms, int64_t* launches);
  * of all instances, and pairs of steps are replayed as one CUDA graph.  Every
  * instance with electric = 1 must use the same poisson_fixed_iter (> 0): the
  * potential is iterated a fixed number of times per step, so all instances do
- * the same work and the graph is fixed.  Each instance starts as lb3e_init would
+ * the same work and the graph is fixed (graphs are used only on a created stream:
+ * the legacy default stream cannot be captured, and there every step is plain
+ * launches).  Each instance starts as lb3e_init would
  * start it with u = q = 0 and no noise.  The device workspace is the caller's. */
 typedef struct lb3e_batch lb3e_batch;
 

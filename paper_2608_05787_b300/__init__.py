@@ -8,12 +8,14 @@ device is missing, constructing a simulation raises.
 from __future__ import annotations
 
 import ctypes as C
+import os
 from pathlib import Path
 
 import numpy as np
 
 _HERE = Path(__file__).resolve().parent
-LIB_PATH = _HERE / "liblb3e.so"
+# the in-tree build; LB3E_LIBRARY may point at another build of the same sources
+LIB_PATH = Path(os.environ.get("LB3E_LIBRARY", _HERE / "liblb3e.so"))
 
 FIELDS = dict(phi1=0, phi2=1, phi3=2, ux=3, uy=4, p=5, q=6, psi=7, ex=8, ey=9,
               mu1=10, mu2=11, mu3=12, phinow1=13, phinow2=14, phinow3=15, qtilde=16)

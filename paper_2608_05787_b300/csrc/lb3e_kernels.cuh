@@ -356,13 +356,19 @@ constexpr int PB_CELLS = PB_RX * PB_RY, PB_THREADS = 512;
 constexpr int PB_CPT = (PB_CELLS + PB_THREADS - 1) / PB_THREADS;
 template <class R>
 constexpr size_t pb_smem_bytes() { return (size_t)11 * PB_CELLS * sizeof(R); }
+// distance of a region cell from the region border
+__device__ __forceinline__ int ring_dist(int ly, int lx) {
+    const int a = ly < PB_RY - 1 - ly ? ly : PB_RY - 1 - ly;
+    const int b = lx < PB_RX - 1 - lx ? lx : PB_RX - 1 - lx;
+    return a < b ? a : b;
+}
 
 template <class R>
 __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __restrict__ hin,
-                                                           R* __restrict__ hout, const R* __restrict__ eps,
-                                                           const R* __restrict__ q, R* __restrict__ prev,
-                                                           double* __restrict__ partial, int K, int save_prev,
-                                                           int check, int bx, int by, int gdx) {
+                                                R* __restrict__ hout, const R* __restrict__ eps,
+                                                const R* __restrict__ q, R* __restrict__ prev,
+                                                double* __restrict__ partial, int K, int save_prev, int check,
+                                                int bx, int by, int gdx) {
     extern __shared__ __align__(16) unsigned char pb_raw[];
     R* hs = reinterpret_cast<R*>(pb_raw);           // [9][PB_CELLS] post-collision values
     R* se = hs + 9 * PB_CELLS;                      // eps
@@ -373,15 +379,24 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
     const int tid = threadIdx.x;
     const bool walls = P.bc_y != 0;
 
+    // per owned cell, fixed over the iterations: region index, ring distance
+    // (-1: not a fluid cell), wall contact (bit 0 bottom row, bit 1 top row), tile
+    // membership, and the global cell index (tile cells only)
     R h[PB_CPT][9];
-    int gyv[PB_CPT];  // global row of each owned cell (unwrapped)
+    int kk[PB_CPT], ring[PB_CPT], wall[PB_CPT];
+    unsigned gc[PB_CPT];
+    bool tile[PB_CPT];
 #pragma unroll
     for (int m = 0; m < PB_CPT; ++m) {
         const int k = tid + m * PB_THREADS;
+        kk[m] = k;
         const int ly = k / PB_RX, lx = k % PB_RX;
         const int gy = y0 + ly, gx = x0 + lx;
-        gyv[m] = gy;
         const bool real = k < PB_CELLS && (!walls || (gy >= 0 && gy < ny));
+        ring[m] = real ? ring_dist(ly, lx) : -1;
+        wall[m] = walls ? ((gy == 0 ? 1 : 0) | (gy == ny - 1 ? 2 : 0)) : 0;
+        tile[m] = real && ring[m] >= PB_HALO && gx < nx && gy < ny;
+        gc[m] = tile[m] ? (unsigned)gy * nx + gx : 0u;
         if (real) {
             const unsigned c = (unsigned)wrapi(gy, ny) * nx + wrapi(gx, nx);
 #pragma unroll
@@ -397,25 +412,22 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
     __syncthreads();
 
     const R th = R(P.tau_h), ith = rcp(th);
+    const R vb = prm<R>(P.V_bottom, P.t_Vb), vt = prm<R>(P.V_top, P.t_Vt);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int t = 0; t < K; ++t) {
 #pragma unroll
         for (int m = 0; m < PB_CPT; ++m) {
-            const int k = tid + m * PB_THREADS;
-            if (k >= PB_CELLS) continue;
-            const int ly = k / PB_RX, lx = k % PB_RX;
-            const int gy = gyv[m];
-            if (walls && (gy < 0 || gy >= ny)) continue;
+            // cells closer than t to the region border can no longer feed the tile
+            if (ring[m] < t) continue;
+            const int k = kk[m];
             R ps = R(0), jx = R(0), jy = R(0);
 #pragma unroll
             for (int j = 1; j < 9; ++j) ps += h[m][j];
             ps = dv(ps, R(1) - wgt<R>(0), R(1.8));
 #pragma unroll
             for (int j = 0; j < 9; ++j) { jx += R(cx(j)) * h[m][j]; jy += R(cy(j)) * h[m][j]; }
-            const bool tile = ly >= PB_HALO && ly < PB_HALO + PB_TY && lx >= PB_HALO && lx < PB_HALO + PB_TX &&
-                              x0 + lx < nx && gy < ny;
-            if (tile && (check && t == 0 || save_prev && t == K - 1)) {
-                const unsigned c = (unsigned)gy * nx + (x0 + lx);
+            if (tile[m] && (check && t == 0 || save_prev && t == K - 1)) {
+                const unsigned c = gc[m];
                 if (check && t == 0) {
                     const double d = (double)ps - (double)prev[c];
                     const double ex = (double)jx - (double)prev[N + c], ey = (double)jy - (double)prev[2 * N + c];
@@ -440,30 +452,21 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
             }
         }
         __syncthreads();
-        // pull streaming inside the region
+        // pull streaming inside the region (cells whose sources were all updated)
 #pragma unroll
         for (int m = 0; m < PB_CPT; ++m) {
-            const int k = tid + m * PB_THREADS;
-            if (k >= PB_CELLS) continue;
-            const int ly = k / PB_RX, lx = k % PB_RX;
-            const int gy = gyv[m];
-            if (walls && (gy < 0 || gy >= ny)) continue;
+            if (ring[m] < t + 1) continue;
+            const int k = kk[m];
 #pragma unroll
             for (int j = 0; j < 9; ++j) {
-                const int sy = gy - cy(j);
-                if (walls && (sy < 0 || sy >= ny)) {
+                const int from_wall = cy(j) > 0 ? (wall[m] & 1) : (cy(j) < 0 ? (wall[m] & 2) : 0);
+                if (from_wall) {
                     // the population that left this cell toward the wall, reflected
                     const int jo = opp(j);
                     const R v = hs[jo * PB_CELLS + k];
-                    h[m][j] = P.bc_y == 2 ? -v + R(2) * wgt<R>(jo) * (sy >= ny ? prm<R>(P.V_top, P.t_Vt)
-                                                                                : prm<R>(P.V_bottom, P.t_Vb))
-                                          : v;
+                    h[m][j] = P.bc_y == 2 ? -v + R(2) * wgt<R>(jo) * (cy(j) < 0 ? vt : vb) : v;
                 } else {
-                    int syl = ly - cy(j), sxl = lx - cx(j);
-                    // sources outside the region only feed cells outside the exact cone
-                    syl = syl < 0 ? 0 : (syl >= PB_RY ? PB_RY - 1 : syl);
-                    sxl = sxl < 0 ? 0 : (sxl >= PB_RX ? PB_RX - 1 : sxl);
-                    h[m][j] = hs[j * PB_CELLS + syl * PB_RX + sxl];
+                    h[m][j] = hs[j * PB_CELLS + k - cy(j) * PB_RX - cx(j)];
                 }
             }
         }
@@ -472,13 +475,8 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
     // write the tile
 #pragma unroll
     for (int m = 0; m < PB_CPT; ++m) {
-        const int k = tid + m * PB_THREADS;
-        if (k >= PB_CELLS) continue;
-        const int ly = k / PB_RX, lx = k % PB_RX;
-        const int gy = gyv[m], gx = x0 + lx;
-        if (ly < PB_HALO || ly >= PB_HALO + PB_TY || lx < PB_HALO || lx >= PB_HALO + PB_TX || gx >= nx || gy >= ny)
-            continue;
-        const unsigned c = (unsigned)gy * nx + gx;
+        if (!tile[m]) continue;
+        const unsigned c = gc[m];
 #pragma unroll
         for (int j = 0; j < 9; ++j) hout[j * N + c] = h[m][j];
     }

@@ -577,7 +577,9 @@ class Batch final : public BatchBase {
         while (done < nsteps) {
             const int left = nsteps - done;
             int k = 1;
-            if (steps_ > 0 && left > 2) {  // pairs of steps by graph; the last step stays a plain launch
+            // pairs of steps by graph (not on the legacy default stream, which cannot be
+            // captured); the last step stays a plain launch
+            if (stream_ != nullptr && steps_ > 0 && left > 2) {
                 cudaGraphExec_t g = nullptr;
                 TRY(graph_for(cur_, hcur_, &g));
                 if (cudaGraphLaunch(g, stream_) != cudaSuccess) return LB3E_ERR_CUDA;

@@ -137,6 +137,22 @@ def test_reduced_precision_static_compound(precision, tol):
     assert max(errs.values()) <= tol, errs
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("precision,tol", [(1, 1e-5), (2, 1e-3)])
+def test_reduced_precision_static_compound_full_run(precision, tol):
+    """The stated 64x64 run (2000 steps) in FP32 and with FP16-stored populations,
+    against the FP64 oracle, phase fields.  The potential is solved to 1e-6 here:
+    the FP32 potential populations cannot resolve relative increments of 1e-8 (the
+    iteration would run to its cap every step), so both sides use the tolerance
+    FP32 can meet."""
+    cfg = W.config_static_compound(precision=precision)
+    p = dict(cfg["params"], poisson_tol=1e-6)
+    sim, orc = run_pair(p, cfg["phi"], cfg["steps"], noise=cfg["noise"])
+    errs = field_errors(sim, orc, ["phi1", "phi2", "phi3", "phinow1", "phinow2", "phinow3"])
+    print(f"precision {precision}: 2000-step errors", errs)
+    assert max(errs.values()) <= tol, errs
+
+
 def test_state_save_load_roundtrip():
     L = _lb()
     cfg = W.config_static_compound(precision=1, n=32)
