@@ -37,6 +37,10 @@ METRIC = "MLUPS"
 FUSED_BYTES = {0: 8 * 112, 1: 4 * 112, 2: 2 * 90 + 4 * 22}   # k_fused: 45 pops r+w, phi, q, E, d/dt state
 POISSON_BYTES = {0: 8 * 20, 1: 4 * 20, 2: 4 * 20}           # one pseudo-iteration: h 9 r + 9 w, eps, q
 STEP_BYTES = {0: 960, 1: 480, 2: 300}                        # whole step without the potential loop
+# multigrid V-cycle, FP64, per fine cell: 4 red-black sweeps over psi, eps, rhs
+# (4 x 32 B), the fine residual (40 B) and the prolongation (16 B), times 4/3 for
+# the coarser levels
+MG_VCYCLE_BYTES = 245
 
 
 def parse():
@@ -54,6 +58,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
     ap.add_argument("--cpu-sample", type=int, default=1024, help="side of the oracle's CPU sample lattice")
     ap.add_argument("--cpu-iters", type=int, default=0, help="potential iterations per step in the CPU sample")
+    ap.add_argument("--potential", default="lb", choices=["lb", "mg"],
+                    help="lb: the paper's pseudo-time LB solve (default); mg: multigrid on its FD form")
+    ap.add_argument("--check-every", type=int, default=0,
+                    help="potential residual cadence (default: the workload's; 1 runs one iteration per launch)")
     return ap.parse_args()
 
 
@@ -215,6 +223,10 @@ def run_lb3e(args):
     prec = args.precision
     cfg = W.config_deformation(n=args.n, r_out=600.0 * args.n / 4096, r_in=300.0 * args.n / 4096, precision=prec)
     params = cfg["params"]
+    if args.check_every:
+        params = dict(params, poisson_check_every=args.check_every)
+    if args.potential == "mg":
+        params = dict(params, potential_solver=1, poisson_max_iter=50)
     N = args.n * args.n
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -263,15 +275,18 @@ def run_lb3e(args):
     k_gbs = {}
     if fused_n:
         k_gbs["fused"] = FUSED_BYTES[prec] * N / (fused_ms / fused_n / 1e3) / 1e9
+    mg = bool(params.get("potential_solver"))
+    pot_bytes = MG_VCYCLE_BYTES if mg else POISSON_BYTES[prec]
     if poisson_n:
         # per pseudo-iteration (the unit of the algorithmic figure); a blocked launch runs several
-        k_gbs["poisson"] = POISSON_BYTES[prec] * N * pot_iters / (poisson_ms / 1e3) / 1e9
+        k_gbs["poisson"] = pot_bytes * N * pot_iters / (poisson_ms / 1e3) / 1e9
     dominant = max(("fused", "poisson"), key=lambda k: kt[k][0])
-    per_cell = FUSED_BYTES[prec] if dominant == "fused" else POISSON_BYTES[prec]
+    per_cell = FUSED_BYTES[prec] if dominant == "fused" else pot_bytes
     traffic = profiled_traffic(dominant, prec)
     roofline = {"bound": "hbm", "achieved": k_gbs.get(dominant), "peak": hbm, "unit": "GB/s",
                 "frac": (k_gbs.get(dominant) or 0) / hbm, "traffic": traffic * N if traffic else None,
-                "kernel": f"k_{dominant}", "peak_kind": f"{peak_kind} copy bandwidth",
+                "kernel": f"k_{dominant}" if not (mg and dominant == "poisson") else "multigrid V-cycle kernels",
+                "peak_kind": f"{peak_kind} copy bandwidth",
                 "algorithmic_bytes_per_launch": per_cell * N * (pot_iters / max(1, poisson_n) if dominant == "poisson" else 1),
                 "units_per_launch": (f"{N} cells x {pot_iters / max(1, poisson_n):.2f} pseudo-iterations"
                                      if dominant == "poisson" else f"{N} cells"),
@@ -322,6 +337,8 @@ def run_lb3e(args):
             "data": "synthetic (stated initial condition of the workload)",
             "config": {"workload": f"compound drop deformation under field, {args.n}x{args.n}",
                        "poisson_tol": params["poisson_tol"], "potential_iters_per_step": iters_per_step,
+                       "potential_solver": ("multigrid V-cycles on the FD form" if params.get("potential_solver")
+                                            else "LB pseudo-time iterations (Eq. 43)"),
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single lattice",
                        "l2": "working set (%.1f GB) exceeds the 126 MB L2; no flush needed" % (L.workspace_bytes(params) / 1e9),
                        "init_seconds": t_init, "init_potential_iters": init_obs["poisson_iters"]},

@@ -111,7 +111,12 @@ typedef struct lb3e_params {
      * gamma13, gamma23).  Fields are then available per direction (see
      * LB3E_TANGENT). */
     int32_t tangent_param[3];
-    int32_t _pad3;
+    /* 0: the paper's pseudo-time LB potential solve (Eq. 42-45); 1: geometric
+     * multigrid on the finite-difference form of Eq. 27d (5-point, harmonic-mean
+     * faces, half-cell Dirichlet electrodes; bc_y = 2, even nx, precision <= 2), FP64, V-cycles until
+     * the relative residual is <= poisson_tol (at most poisson_max_iter cycles);
+     * E is then the Eq. 33 gradient of psi */
+    int32_t potential_solver;
 } lb3e_params;
 
 /* Field id offset of tangent k (1..3) of a field in the tangent builds: field

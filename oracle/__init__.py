@@ -38,6 +38,7 @@ class _Params(C.Structure):
         ("charge_convection", C.c_int32), ("inner_phase", C.c_int32), ("matrix_phase", C.c_int32),
         ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int32),
         ("poisson_check_every", C.c_int32), ("poisson_fixed_iter", C.c_int32),
+        ("potential_solver", C.c_int32),
     ]
 
 

@@ -58,6 +58,8 @@ typedef struct orc_params {
     int32_t inner_phase, matrix_phase; /* 1-based, for the deformation factor */
     double poisson_tol;
     int32_t poisson_max_iter, poisson_check_every, poisson_fixed_iter;
+    int32_t potential_solver;  /* 0: the LB pseudo-time solve (Eq. 42-45); 1: the
+                                  finite-difference form of Eq. 27d solved directly */
 } orc_params;
 
 enum { F_PHI1 = 0, F_PHI2, F_PHI3, F_UX, F_UY, F_P, F_Q, F_PSI, F_EX, F_EY,
@@ -266,6 +268,111 @@ static void potential_fields(orc_state* s) {
     }
 }
 
+/* ---------------- finite-difference potential (alternative solver) ----------------
+ * The same equation, div(eps grad psi) + q = 0 (Eq. 27d), discretised with the
+ * 5-point stencil: face permittivity = harmonic mean of the two cells; a wall
+ * carrying an electrode is a Dirichlet face at distance 1/2 (flux 2 eps_C (V - psi_C));
+ * an insulating wall carries no flux; x (and y when bc_y = 0) is periodic.  The
+ * symmetric system A psi = b is solved by conjugate gradients to a relative
+ * residual of 1e-13 (with no Dirichlet face the mean of q is removed and psi has
+ * zero mean).  E is the isotropic gradient of Eq. 33, with ghost cells 2V - psi at
+ * electrodes and mirrors at insulating walls. */
+static double hmean(double a, double b) { return 2.0 * a * b / (a + b); }
+
+static void fd_apply(const orc_state* s, const double* x, double* Ax) {
+    const int nx = s->p.nx, ny = s->p.ny;
+    for (int y = 0; y < ny; ++y)
+        for (int xx = 0; xx < nx; ++xx) {
+            int c = y * nx + xx;
+            double ec = s->eps[c], acc = 0.0;
+            int nb[4][2] = {{xx + 1, y}, {xx - 1, y}, {xx, y + 1}, {xx, y - 1}};
+            for (int k = 0; k < 4; ++k) {
+                int yy = nb[k][1];
+                if (s->p.bc_y != 0 && (yy < 0 || yy >= ny)) {
+                    if (s->p.bc_y == 2) acc += 2.0 * ec * x[c];
+                    continue;
+                }
+                int n = wrap(yy, ny) * nx + wrap(nb[k][0], nx);
+                acc += hmean(ec, s->eps[n]) * (x[c] - x[n]);
+            }
+            Ax[c] = acc;
+        }
+}
+
+static double dot(const double* a, const double* b, int n) {
+    double r = 0.0;
+    for (int i = 0; i < n; ++i) r += a[i] * b[i];
+    return r;
+}
+
+static int fd_solve(orc_state* s, double* res_out) {
+    const int nx = s->p.nx, ny = s->p.ny, N = s->N;
+    double* b = alloc0(N);
+    double* r = alloc0(N);
+    double* d = alloc0(N);
+    double* Ad = alloc0(N);
+    for (int c = 0; c < N; ++c) b[c] = s->q[c];
+    if (s->p.bc_y == 2)
+        for (int x = 0; x < nx; ++x) {
+            b[x] += 2.0 * s->eps[x] * s->p.V_bottom;
+            b[(ny - 1) * nx + x] += 2.0 * s->eps[(ny - 1) * nx + x] * s->p.V_top;
+        }
+    else {
+        double m = 0.0;
+        for (int c = 0; c < N; ++c) m += b[c];
+        for (int c = 0; c < N; ++c) b[c] -= m / N;
+    }
+    double* x = s->psi;
+    fd_apply(s, x, Ad);
+    for (int c = 0; c < N; ++c) { r[c] = b[c] - Ad[c]; d[c] = r[c]; }
+    double bb = dot(b, b, N), rr = dot(r, r, N);
+    int it = 0;
+    const double tol2 = 1e-26 * (bb > 0 ? bb : 1.0);
+    while (rr > tol2 && it < 100000) {
+        fd_apply(s, d, Ad);
+        double alpha = rr / dot(d, Ad, N);
+        for (int c = 0; c < N; ++c) { x[c] += alpha * d[c]; r[c] -= alpha * Ad[c]; }
+        double rr2 = dot(r, r, N);
+        for (int c = 0; c < N; ++c) d[c] = r[c] + (rr2 / rr) * d[c];
+        rr = rr2;
+        ++it;
+    }
+    if (s->p.bc_y != 2) {
+        double m = 0.0;
+        for (int c = 0; c < N; ++c) m += x[c];
+        for (int c = 0; c < N; ++c) x[c] -= m / N;
+    }
+    *res_out = bb > 0 ? sqrt(rr / bb) : 0.0;
+    free(b); free(r); free(d); free(Ad);
+    return it;
+}
+
+/* psi at a stencil ghost position: periodic, 2V - psi at electrodes, mirror at walls */
+static double psi_at(const orc_state* s, int x, int y) {
+    const int nx = s->p.nx, ny = s->p.ny;
+    if (s->p.bc_y == 0 || (y >= 0 && y < ny)) return s->psi[wrap(y, ny) * nx + wrap(x, nx)];
+    int ym = y < 0 ? -1 - y : 2 * ny - 1 - y;
+    double v = s->psi[ym * nx + wrap(x, nx)];
+    if (s->p.bc_y == 2) return 2.0 * (y < 0 ? s->p.V_bottom : s->p.V_top) - v;
+    return v;
+}
+
+static void fd_fields(orc_state* s) {
+    const int nx = s->p.nx, ny = s->p.ny, N = s->N;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double ax = 0.0, ay = 0.0;
+            for (int j = 0; j < 9; ++j) {
+                double v = psi_at(s, x + CX[j], y + CY[j]);
+                ax += W[j] * CX[j] * v;
+                ay += W[j] * CY[j] * v;
+            }
+            int c = y * nx + x;
+            s->E[c] = -(ax / CS2) + s->p.E_ext[0];
+            s->E[N + c] = -(ay / CS2) + s->p.E_ext[1];
+        }
+}
+
 /* ---------------- step pieces ---------------- */
 /* S2 + S3: properties and their stencils from the phi fields */
 static void properties_and_stencils(orc_state* s) {
@@ -439,8 +546,12 @@ static void one_step(orc_state* s) {
         double src = r * (s->geps[c] * Ex + s->geps[N + c] * Ey) - (s->gsig[c] * Ex + s->gsig[N + c] * Ey);
         s->q[c] = (s->qt[c] + 0.5 * src) / (1.0 + 0.5 * r);
     }
-    /* S5: potential solve (warm-started from the current h) */
-    if (s->p.electric) {
+    /* S5: potential solve (warm-started from the current h, or the FD form) */
+    if (s->p.electric && s->p.potential_solver == 1) {
+        s->last_iters = fd_solve(s, &s->last_res);
+        s->last_converged = 1;
+        fd_fields(s);
+    } else if (s->p.electric) {
         int conv;
         s->last_iters = poisson_solve(s, s->p.poisson_tol, s->p.poisson_max_iter, s->p.poisson_fixed_iter,
                                       s->p.poisson_check_every, &s->last_res, &conv);
@@ -505,7 +616,8 @@ void orc_destroy(orc_state* s) {
 orc_state* orc_create(const orc_params* p, const double* phi_init, const double* u_init,
                       const double* q_init, const double* noise, int* status) {
     *status = -1;
-    if (p->nx < 2 || p->ny < 2 || p->bc_y < 0 || p->bc_y > 2) return NULL;
+    if (p->nx < 2 || p->ny < 2 || p->bc_y < 0 || p->bc_y > 2 || p->potential_solver < 0 || p->potential_solver > 1)
+        return NULL;
     if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5) || !(p->width_D > 0) || !(p->eps_ref > 0) || !(p->alpha > 0))
         return NULL;
     for (int i = 0; i < 3; ++i)
@@ -547,7 +659,14 @@ orc_state* orc_create(const orc_params* p, const double* phi_init, const double*
             double psi0 = p->bc_y == 2 ? p->V_bottom + (p->V_top - p->V_bottom) * (y + 0.5) / p->ny : 0.0;
             for (int j = 0; j < 9; ++j) s->h[j * N + c] = (j == 0) ? (W[0] - 1.0) * psi0 : W[j] * psi0;
         }
-    if (p->electric) {
+    if (p->electric && p->potential_solver == 1) {
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x)
+                s->psi[y * p->nx + x] = p->bc_y == 2 ? p->V_bottom + (p->V_top - p->V_bottom) * (y + 0.5) / p->ny : 0.0;
+        s->last_iters = fd_solve(s, &s->last_res);
+        s->last_converged = 1;
+        fd_fields(s);
+    } else if (p->electric) {
         int conv;
         s->last_iters = poisson_solve(s, p->poisson_tol, p->poisson_max_iter, p->poisson_fixed_iter,
                                       p->poisson_check_every, &s->last_res, &conv);
@@ -596,6 +715,12 @@ int orc_step(orc_state* s, int nsteps) {
 int orc_solve_potential(orc_state* s, const double* q, double tol, int max_iter, int fixed, int check,
                         double* res, int* converged) {
     if (q) memcpy(s->q, q, (size_t)s->N * sizeof(double));
+    if (s->p.potential_solver == 1) {
+        int it = fd_solve(s, res);
+        *converged = 1;
+        fd_fields(s);
+        return it;
+    }
     int it = poisson_solve(s, tol, max_iter, fixed, check, res, converged);
     potential_fields(s);
     return it;
@@ -611,6 +736,7 @@ int orc_get_field(const orc_state* s, int id, double* out) {
         case F_P: src = s->pr; break;
         case F_Q: src = s->q; break;
         case F_PSI:
+            if (s->p.potential_solver == 1) { src = s->psi; break; }
             for (int c = 0; c < N; ++c) out[c] = psi_moment(s, s->h, c);
             return 0;
         case F_EX: src = s->E; break;

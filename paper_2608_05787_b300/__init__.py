@@ -43,7 +43,7 @@ class Params(C.Structure):
         ("_pad1", C.c_int32),
         ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int32),
         ("poisson_check_every", C.c_int32), ("poisson_fixed_iter", C.c_int32), ("_pad2", C.c_int32),
-        ("tangent_param", C.c_int32 * 3), ("_pad3", C.c_int32),
+        ("tangent_param", C.c_int32 * 3), ("potential_solver", C.c_int32),
     ]
 
     @classmethod

@@ -22,6 +22,9 @@ int validate(const lb3e_params* p) {
     if (p->bc_y < 0 || p->bc_y > 2 || p->precision < 0 || p->precision > 4) return LB3E_ERR_PARAM;
     for (int k = 0; k < 3; ++k)
         if (p->tangent_param[k] < -1 || p->tangent_param[k] > 6) return LB3E_ERR_PARAM;
+    if (p->potential_solver < 0 || p->potential_solver > 1) return LB3E_ERR_PARAM;
+    if (p->potential_solver == 1 && p->electric && (p->bc_y != 2 || p->precision > 2 || (p->nx & 1)))
+        return LB3E_ERR_PARAM;  // multigrid: electrodes, plain precisions, even nx (red-black across the seam)
     if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5) || !(p->width_D > 0) || !(p->eps_ref > 0) || !(p->alpha > 0))
         return LB3E_ERR_PARAM;
     for (int i = 0; i < 3; ++i)
@@ -57,7 +60,8 @@ int validate_batch(const lb3e_params* ps, int32_t n) {
     int iters = -1;
     for (int i = 0; i < n; ++i) {
         TRY(validate(ps + i));
-        if (ps[i].precision != ps[0].precision || ps[i].precision > 2) return LB3E_ERR_PARAM;
+        if (ps[i].precision != ps[0].precision || ps[i].precision > 2 || ps[i].potential_solver != 0)
+            return LB3E_ERR_PARAM;
         if (ps[i].electric) {
             if (ps[i].poisson_fixed_iter <= 0) return LB3E_ERR_PARAM;
             if (iters >= 0 && ps[i].poisson_fixed_iter != iters) return LB3E_ERR_PARAM;

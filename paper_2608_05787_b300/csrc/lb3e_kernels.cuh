@@ -32,6 +32,10 @@ struct DevParams {
     double V_bottom, V_top, E_ext[2], u_wall_bottom, u_wall_top;
     // tangent seeds (dual-number builds only): d(param)/d(theta_k), k < 4
     double t_eps[3][4], t_lam[3][4], t_Vb[4], t_Vt[4];
+    // single-precision copies used by the FP32 kernels (FP64 arithmetic, including
+    // conversions, is slow on this part)
+    float frho[3], fvisc[3], feps[3], fsig[3], flam[3];
+    float fD, ftau_f, fm0, ftau_g, ftau_l, ftau_h, feps_ref, fVb, fVt, fuwb, fuwt;
 };
 
 // Device-side buffers of one simulation (pointers into the caller's workspace).
@@ -69,11 +73,20 @@ __host__ __device__ constexpr int fused_min_blocks() { return std::is_same<R, fl
 template <class R>
 __host__ __device__ constexpr int pb_min_blocks() { return std::is_same<R, float>::value ? 2 : 1; }
 
+// A parameter as an R: the FP32 build reads its single-precision copy.
+template <class R>
+__device__ __forceinline__ R pv(double v, float vf) {
+    if constexpr (std::is_same<R, float>::value) return vf;
+    else return R(v);
+}
+
 // A model parameter as an R: plain builds take the value; dual builds also carry
 // its seeded tangents (one per differentiated parameter direction).
 template <class R>
-__device__ __forceinline__ R prm(double v, const double* t) {
-    if constexpr (is_dual<R>::value) {
+__device__ __forceinline__ R prm(double v, const double* t, float vf = 0.f) {
+    if constexpr (std::is_same<R, float>::value) {
+        return vf;
+    } else if constexpr (is_dual<R>::value) {
         R r(v);
 #pragma unroll
         for (int k = 0; k < (int)(sizeof(r.d) / sizeof(r.d[0])); ++k) r.d[k] = decltype(r.v)(t[k]);
@@ -104,11 +117,13 @@ __device__ __forceinline__ R oc2(R a) {  // a / cs^2
 }
 
 // ---------------------------------------------------------------- storage conversion
-// Storage types.  With fp16 storage the rest population f^i_0 of each phase set
-// (which is close to phi_i, an O(1) number) is stored as its deviation from the
+// Storage types.  With fp32 or fp16 storage the rest population f^i_0 of each
+// phase set (close to phi_i, an O(1) number) is stored as its deviation from the
 // phi_i of the step that wrote it -- the "anchor", held in the phi field until the
-// next moments pass reads it.  The deviation is O(mu) ~ 1e-3, so fp16 keeps ~1e-6
-// absolute accuracy on it; every other plane is small already and stored as is.
+// next moments pass reads it -- and its collision is carried out in deviation form,
+// so no O(1) terms cancel: f_0 - f_0^eq = (1 - w_0) mu - sum_{j>0} f_j.  The
+// deviation is O(mu), resolved to ~1e-10 (fp32) or ~1e-6 (fp16) absolute; every
+// other plane is small already and stored as is.  The fp64 build stores plainly.
 template <class S> struct Store;
 template <> struct Store<double> {
     static __device__ __forceinline__ double ld(const double* p, size_t i) { return p[i]; }
@@ -127,7 +142,9 @@ template <class T, int M> struct Store<Dual<T, M>> {
     static __device__ __forceinline__ void st(Dual<T, M>* p, size_t i, Dual<T, M> v) { p[i] = v; }
 };
 template <class S>
-__host__ __device__ constexpr bool anchored() { return sizeof(S) == 2; }
+__host__ __device__ constexpr bool anchored() {
+    return std::is_same<S, float>::value || std::is_same<S, __half>::value;
+}
 
 // ---------------------------------------------------------------- grid helpers
 __device__ __forceinline__ int wrapi(int a, int n) {
@@ -157,18 +174,18 @@ __device__ __forceinline__ int tile_row(int y, int ny, int bc_y) {
 template <class R>
 __device__ __forceinline__ R perm(const DevParams& P, R p0, R p1, R p2) {
     R e = R(0);
-    e += prm<R>(P.eps[0], P.t_eps[0]) * p0 * p0 * (R(3) - R(2) * p0);
-    e += prm<R>(P.eps[1], P.t_eps[1]) * p1 * p1 * (R(3) - R(2) * p1);
-    e += prm<R>(P.eps[2], P.t_eps[2]) * p2 * p2 * (R(3) - R(2) * p2);
+    e += prm<R>(P.eps[0], P.t_eps[0], P.feps[0]) * p0 * p0 * (R(3) - R(2) * p0);
+    e += prm<R>(P.eps[1], P.t_eps[1], P.feps[1]) * p1 * p1 * (R(3) - R(2) * p1);
+    e += prm<R>(P.eps[2], P.t_eps[2], P.feps[2]) * p2 * p2 * (R(3) - R(2) * p2);
     return e;
 }
 template <class R>
 __device__ __forceinline__ R cond(const DevParams& P, R p0, R p1, R p2) {
-    return p0 * R(P.sigma[0]) + p1 * R(P.sigma[1]) + p2 * R(P.sigma[2]);
+    return p0 * pv<R>(P.sigma[0], P.fsig[0]) + p1 * pv<R>(P.sigma[1], P.fsig[1]) + p2 * pv<R>(P.sigma[2], P.fsig[2]);
 }
 template <class R>
 __device__ __forceinline__ R dens(const DevParams& P, R p0, R p1, R p2) {
-    return p0 * R(P.rho[0]) + p1 * R(P.rho[1]) + p2 * R(P.rho[2]);
+    return p0 * pv<R>(P.rho[0], P.frho[0]) + p1 * pv<R>(P.rho[1], P.frho[1]) + p2 * pv<R>(P.rho[2], P.frho[2]);
 }
 // Eq. 40
 template <class R>
@@ -216,11 +233,8 @@ __device__ __forceinline__ void body_moments(const DevParams P, const S* __restr
     for (int i = 0; i < 3; ++i) {
         R a = R(0);
 #pragma unroll
-        for (int j = 0; j < 9; ++j) {
-            R v = Store<S>::ld(pop, (9 * (i + 1) + j) * N + c);
-            if (anchored<S>() && j == 0) v += phi_anchor[i * N + c];
-            a += v;
-        }
+        for (int j = 0; j < 9; ++j) a += Store<S>::ld(pop, (9 * (i + 1) + j) * N + c);
+        if (anchored<S>()) a = phi_anchor[i * N + c] + a;  // anchor + (deviation + moving populations)
         phi[i * N + c] = a;  // may alias phi_anchor: read above, written here
     }
     R a = R(0);
@@ -305,8 +319,8 @@ __device__ __forceinline__ void body_poisson(const DevParams P, const R* __restr
             acc[3] = (double)jx * (double)jx + (double)jy * (double)jy;
         }
         if (save_prev) { prev[c] = ps; prev[N + c] = jx; prev[2 * N + c] = jy; }
-        const R th = R(P.tau_h), ith = rcp(th);
-        const R epshat = eps[c] - R(P.eps_ref);
+        const R th = pv<R>(P.tau_h, P.ftau_h), ith = rcp(th);
+        const R epshat = eps[c] - pv<R>(P.eps_ref, P.feps_ref);
         const R den = epshat + cs2<R>() * th, iden = rcp(den);
         const R gx = dv(-jx, den, iden), gy = dv(-jy, den, iden);
         const R qc = q[c];
@@ -320,7 +334,8 @@ __device__ __forceinline__ void body_poisson(const DevParams P, const R* __restr
             if (P.bc_y != 0 && (yt < 0 || yt >= P.ny)) {
                 R out = v;
                 if (P.bc_y == 2)
-                    out = -v + R(2) * wgt<R>(j) * (yt >= P.ny ? prm<R>(P.V_top, P.t_Vt) : prm<R>(P.V_bottom, P.t_Vb));
+                    out = -v + R(2) * wgt<R>(j) * (yt >= P.ny ? prm<R>(P.V_top, P.t_Vt, P.fVt)
+                                                              : prm<R>(P.V_bottom, P.t_Vb, P.fVb));
                 hout[opp(j) * N + c] = out;
             } else {
                 hout[j * N + (unsigned)wrapi(yt, P.ny) * P.nx + wrapi(x + cx(j), P.nx)] = v;
@@ -406,13 +421,14 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
         } else {
 #pragma unroll
             for (int j = 0; j < 9; ++j) h[m][j] = R(0);
-            if (k < PB_CELLS) { se[k] = R(P.eps_ref); sq[k] = R(0); }
+            if (k < PB_CELLS) { se[k] = pv<R>(P.eps_ref, P.feps_ref); sq[k] = R(0); }
         }
     }
     __syncthreads();
 
-    const R th = R(P.tau_h), ith = rcp(th);
-    const R vb = prm<R>(P.V_bottom, P.t_Vb), vt = prm<R>(P.V_top, P.t_Vt);
+    const R th = pv<R>(P.tau_h, P.ftau_h), ith = rcp(th);
+    const R vb = prm<R>(P.V_bottom, P.t_Vb, P.fVb), vt = prm<R>(P.V_top, P.t_Vt, P.fVt);
+    const R eref = pv<R>(P.eps_ref, P.feps_ref);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int t = 0; t < K; ++t) {
 #pragma unroll
@@ -438,7 +454,7 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
                 }
                 if (save_prev && t == K - 1) { prev[c] = ps; prev[N + c] = jx; prev[2 * N + c] = jy; }
             }
-            const R epshat = se[k] - R(P.eps_ref);
+            const R epshat = se[k] - eref;
             const R den = epshat + cs2<R>() * th, iden = rcp(den);
             const R gx = dv(-jx, den, iden), gy2 = dv(-jy, den, iden);
             const R qc = sq[k];
@@ -582,10 +598,10 @@ __device__ __forceinline__ R lap_tile(const R* t, int pitch, int ty, int tx) {
 template <class R>
 __device__ __forceinline__ R chem_pot(const DevParams& P, int i, R ph, R lap, R e2, R c24) {
     // c24 = 24 / D, formed once by the caller
-    const R D = R(P.D), lam = prm<R>(P.lam[i], P.t_lam[i]);
+    const R D = pv<R>(P.D, P.fD), lam = prm<R>(P.lam[i], P.t_lam[i], P.flam[i]);
     const R bulk = c24 * lam * ph * (ph - R(0.5)) * (ph - R(1));
     const R grad = R(0.75) * D * lam * lap;
-    const R deps = R(6) * prm<R>(P.eps[i], P.t_eps[i]) * ph * (R(1) - ph);
+    const R deps = R(6) * prm<R>(P.eps[i], P.t_eps[i], P.feps[i]) * ph * (R(1) - ph);
     return bulk - grad - R(0.5) * deps * e2;
 }
 
@@ -626,7 +642,7 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     }
     __syncthreads();
     // mu on the 1-ring at in-domain rows
-    const R c24 = R(24) / R(P.D);
+    const R c24 = R(24) / pv<R>(P.D, P.fD);
     for (int k = tid; k < MY * MX; k += TX * TY) {
         const int ly = k / MX, lx = k % MX;
         const int gy = y0 + ly - 1;
@@ -762,7 +778,7 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     };
 
     // phase populations, Eq. 34-36 with the mobility of Eq. 28
-    const R tf = R(P.tau_f), m0 = R(P.m0), itf = rcp(tf), im0 = rcp(m0);
+    const R tf = pv<R>(P.tau_f, P.ftau_f), m0 = pv<R>(P.m0, P.fm0), itf = rcp(tf), im0 = rcp(m0);
     const R pf = R(1) - R(1) / (R(2) * tf);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -783,32 +799,34 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
         R fv[9];
 #pragma unroll
         for (int j = anchored<S>() ? 1 : 0; j < 9; ++j) fv[j] = Store<S>::ld(pin, (9 * (i + 1) + j) * N + c);
-        if (anchored<S>()) {  // f_0 = phi_i - sum of the moving populations
+        if constexpr (anchored<S>()) {
+            // rest population in deviation form about phi_i: f_0 - phi_i = -sum_{j>0} f_j,
+            // f_0 - f_0^eq = (1 - w_0) mu_i - sum_{j>0} f_j; the source term of j = 0 is zero
             R a = R(0);
 #pragma unroll
             for (int j = 1; j < 9; ++j) a += fv[j];
-            fv[0] = ph[i] - a;
+            const R neq0 = (R(1) - wgt<R>(0)) * mui - a;
+            push(i + 1, 0, -a - dv(neq0, tf, itf));
         }
 #pragma unroll
-        for (int j = 0; j < 9; ++j) {
+        for (int j = anchored<S>() ? 1 : 0; j < 9; ++j) {
             const R feq = (j == 0) ? ph[i] - (R(1) - wgt<R>(0)) * mui
                                    : wgt<R>(j) * mui + oc2(wgt<R>(j) * (R(cx(j)) * ph[i] * ux + R(cy(j)) * ph[i] * uy));
             const R Fj = wgt<R>(j) * (R(cx(j)) * Ax + R(cy(j)) * Ay);
-            const R v = fv[j] - dv(fv[j] - feq, tf, itf) + pf * Fj;
-            push(i + 1, j, (anchored<S>() && j == 0) ? v - ph[i] : v);
+            push(i + 1, j, fv[j] - dv(fv[j] - feq, tf, itf) + pf * Fj);
         }
     }
 
     // flow populations, Eq. 37-40
     {
-        R tg = R(P.tau_g);
+        R tg = pv<R>(P.tau_g, P.ftau_g);
         if (P.use_visc) {
             R eta = R(0);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) eta += ph[i] * R(P.visc[i]);
+            for (int i = 0; i < 3; ++i) eta += ph[i] * pv<R>(P.visc[i], P.fvisc[i]);
             tg = R(0.5) + eta / (rho * cs2<R>());
         }
-        const R uw = y == 0 ? R(P.u_wall_bottom) : R(P.u_wall_top);
+        const R uw = y == 0 ? pv<R>(P.u_wall_bottom, P.fuwb) : pv<R>(P.u_wall_top, P.fuwt);
         const R itg = rcp(tg), pg = R(1) - R(1) / (R(2) * tg);
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
@@ -829,7 +847,7 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
 
     // charge populations, Eq. 48-50
     {
-        const R tl = R(P.tau_l), itl = rcp(tl), pl = R(1) - R(1) / (R(2) * tl);
+        const R tl = pv<R>(P.tau_l, P.ftau_l), itl = rcp(tl), pl = R(1) - R(1) / (R(2) * tl);
         const bool cc = P.charge_convection != 0;
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
@@ -879,7 +897,9 @@ __global__ void k_init_pops(DevParams P, S* __restrict__ pop, const R* __restric
         for (int j = 0; j < 9; ++j) {
             const R feq = (j == 0) ? cc - (R(1) - wgt<R>(0)) * mui
                                    : wgt<R>(j) * mui + wgt<R>(j) * (R(cx(j)) * cc * ux + R(cy(j)) * cc * uy) / cs2<R>();
-            Store<S>::st(pop, (9 * (i + 1) + j) * N + c, (anchored<S>() && j == 0) ? feq - cc : feq);
+            // anchored storage keeps f_0 - phi = -(1 - w_0) mu without forming phi - ... - phi
+            Store<S>::st(pop, (9 * (i + 1) + j) * N + c,
+                         (anchored<S>() && j == 0) ? -((R(1) - wgt<R>(0)) * mui) : feq);
         }
     }
     const R rho = dens<R>(P, ph[0], ph[1], ph[2]);

@@ -42,6 +42,24 @@ inline DevParams make_dev_params(const lb3e_params& p) {
     d.E_ext[1] = p.E_ext[1];
     d.u_wall_bottom = p.u_wall_bottom;
     d.u_wall_top = p.u_wall_top;
+    for (int i = 0; i < 3; ++i) {
+        d.frho[i] = (float)d.rho[i];
+        d.fvisc[i] = (float)d.visc[i];
+        d.feps[i] = (float)d.eps[i];
+        d.fsig[i] = (float)d.sigma[i];
+        d.flam[i] = (float)d.lam[i];
+    }
+    d.fD = (float)d.D;
+    d.ftau_f = (float)d.tau_f;
+    d.fm0 = (float)d.m0;
+    d.ftau_g = (float)d.tau_g;
+    d.ftau_l = (float)d.tau_l;
+    d.ftau_h = (float)d.tau_h;
+    d.feps_ref = (float)d.eps_ref;
+    d.fVb = (float)d.V_bottom;
+    d.fVt = (float)d.V_top;
+    d.fuwb = (float)d.u_wall_bottom;
+    d.fuwt = (float)d.u_wall_top;
     // tangent seeds: d lambda_i / d gamma_jk from Eq. 9
     static const double dlam[3][3] = {{1, 1, -1}, {1, -1, 1}, {-1, 1, 1}};
     for (int k = 0; k < 3; ++k) {

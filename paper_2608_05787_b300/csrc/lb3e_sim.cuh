@@ -14,6 +14,7 @@
 
 #include "lb3e_internal.h"
 #include "lb3e_kernels.cuh"
+#include "lb3e_mg.cuh"
 
 namespace lb3e {
 
@@ -24,7 +25,7 @@ class Sim final : public SimBase {
   public:
     // workspace layout (byte offsets), computed identically by bytes() and the constructor
     struct Layout {
-        size_t pop[2], h[2], phi, qt, q, eps, E, prev, diag, psi_prev, partial, result, stage, total;
+        size_t pop[2], h[2], phi, qt, q, eps, E, prev, diag, psi_prev, partial, result, stage, mg, total;
     };
     static Layout layout(const lb3e_params& p) {
         const size_t N = (size_t)p.nx * p.ny;
@@ -50,6 +51,13 @@ class Sim final : public SimBase {
         L.stage = take(9 * N * sizeof(double) > N * sizeof(double) + 4 * N * sizeof(R)
                            ? 9 * N * sizeof(double)
                            : N * sizeof(double) + 4 * N * sizeof(R));
+        // multigrid levels (finite-difference potential only): psi, rhs, res, eps
+        size_t mg = 0;
+        if (p.potential_solver == 1 && p.electric) {
+            const int nl = mg_levels(p.nx, p.ny);
+            for (int l = 0; l < nl; ++l) mg += 8 * align256((size_t)(p.nx >> l) * (p.ny >> l) * sizeof(double));
+        }
+        L.mg = take(mg);
         L.total = o;
         return L;
     }
@@ -77,6 +85,26 @@ class Sim final : public SimBase {
         dp_ = make_dev_params(prm);
         grid2_ = dim3((prm.nx + TX - 1) / TX, (prm.ny + TY - 1) / TY);
         nblk_ = (int)(grid2_.x * grid2_.y);
+        if (prm.potential_solver == 1 && prm.electric) {
+            const int nl = mg_levels(prm.nx, prm.ny);
+            char* m = b + L_.mg;
+            for (int l = 0; l < nl; ++l) {
+                MGLevel v;
+                v.nx = prm.nx >> l;
+                v.ny = prm.ny >> l;
+                const size_t sz = align256((size_t)v.nx * v.ny * sizeof(double));
+                v.psi = reinterpret_cast<double*>(m);
+                v.rhs = reinterpret_cast<double*>(m + sz);
+                v.res = reinterpret_cast<double*>(m + 2 * sz);
+                v.eps = reinterpret_cast<double*>(m + 3 * sz);
+                v.ae = reinterpret_cast<double*>(m + 4 * sz);
+                v.an = reinterpret_cast<double*>(m + 5 * sz);
+                v.dg = reinterpret_cast<double*>(m + 6 * sz);
+                v.idg = reinterpret_cast<double*>(m + 7 * sz);
+                m += 8 * sz;
+                mg_.push_back(v);
+            }
+        }
     }
     ~Sim() override {
         if (pinned_) cudaFreeHost(pinned_);
@@ -108,7 +136,12 @@ class Sim final : public SimBase {
         timer.begin(stream_, KC_OTHER);
         k_init_h<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[0]);
         TRY(launched());
-        if (p_.electric) {
+        if (p_.electric && !mg_.empty()) {
+            timer.begin(stream_, KC_OTHER);
+            k_mg_init<<<mg_grid(0), dim3(TX, TY), 0, stream_>>>(mg_[0], p_.V_bottom, p_.V_top);
+            TRY(launched());
+            TRY(mg_solve(p_.poisson_tol, p_.poisson_max_iter));
+        } else if (p_.electric) {
             TRY(poisson(p_.poisson_tol, p_.poisson_max_iter, p_.poisson_fixed_iter, p_.poisson_check_every));
         } else {
             timer.begin(stream_, KC_OTHER);
@@ -141,7 +174,9 @@ class Sim final : public SimBase {
             timer.begin(stream_, KC_PROLOGUE);
             k_prologue<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.phi, d_.qt, d_.E, d_.q, d_.eps, 1);
             TRY(launched());
-            if (p_.electric) {
+            if (p_.electric && !mg_.empty()) {
+                TRY(mg_solve(p_.poisson_tol, p_.poisson_max_iter));
+            } else if (p_.electric) {
                 TRY(poisson(p_.poisson_tol, p_.poisson_max_iter, p_.poisson_fixed_iter, p_.poisson_check_every));
             }
             timer.begin(stream_, KC_FUSED);
@@ -156,7 +191,10 @@ class Sim final : public SimBase {
 
     int solve_potential(const double* q, double tol, int max_iter, int check, int* iters, double* res) override {
         if (q) TRY(upload(q, N_, d_.q));
-        TRY(poisson(tol, max_iter, 0, check));
+        if (!mg_.empty())
+            TRY(mg_solve(tol, max_iter));
+        else
+            TRY(poisson(tol, max_iter, 0, check));
         if (iters) *iters = last_iters_;
         if (res) *res = last_res_;
         TRY(sync());
@@ -229,6 +267,7 @@ class Sim final : public SimBase {
             case LB3E_FIELD_MU1: case LB3E_FIELD_MU2: case LB3E_FIELD_MU3: src = d_.diag + (3 + id - LB3E_FIELD_MU1) * N_; break;
             case LB3E_FIELD_PSI:
                 if (comp) return LB3E_ERR_FIELD;
+                if (!mg_.empty()) return copy_out(dst, mg_[0].psi);
                 timer.begin(stream_, KC_FIELDS);
                 k_potential_fields<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[hcur_], d_.eps, d_.E, d_.stage);
                 TRY(launched());
@@ -378,6 +417,80 @@ class Sim final : public SimBase {
         return sync();
     }
 
+    dim3 mg_grid(int l) const { return dim3((mg_[l].nx + TX - 1) / TX, (mg_[l].ny + TY - 1) / TY); }
+    // FD potential by multigrid V-cycles (warm-started from the last psi)
+    int mg_solve(double tol, int max_cycles) {
+        const int nl = (int)mg_.size();
+        const dim3 blk(TX, TY);
+        const double vb = p_.V_bottom, vt = p_.V_top;
+        timer.begin(stream_, KC_POISSON);
+        k_mg_load<R><<<mg_grid(0), blk, 0, stream_>>>(mg_[0], d_.eps, d_.q, vb, vt);
+        TRY(launched());
+        for (int l = 0; l < nl; ++l) {
+            if (l > 0) {
+                timer.begin(stream_, KC_POISSON);
+                k_mg_coarsen_eps<<<mg_grid(l), blk, 0, stream_>>>(mg_[l - 1], mg_[l]);
+                TRY(launched());
+            }
+            timer.begin(stream_, KC_POISSON);
+            k_mg_coeffs<<<mg_grid(l), blk, 0, stream_>>>(mg_[l]);
+            TRY(launched());
+        }
+        auto smooth = [&](int l, int sweeps) -> int {
+            for (int s = 0; s < sweeps; ++s)
+                for (int color = 0; color < 2; ++color) {
+                    timer.begin(stream_, KC_POISSON);
+                    k_mg_smooth<<<mg_grid(l), blk, 0, stream_>>>(mg_[l], color);
+                    TRY(launched());
+                }
+            return LB3E_OK;
+        };
+        last_res_ = -1.0;
+        last_conv_ = 0;
+        int cycles = 0;
+        for (;;) {
+            timer.begin(stream_, KC_REDUCE);
+            k_mg_residual<<<mg_grid(0), blk, 0, stream_>>>(mg_[0], d_.partial);
+            TRY(launched());
+            const int nb = (int)(mg_grid(0).x * mg_grid(0).y);
+            timer.begin(stream_, KC_REDUCE);
+            k_reduce_partials<2><<<1, 256, 0, stream_>>>(d_.partial, nb, d_.result);
+            TRY(launched());
+            if (cudaMemcpyAsync(pinned_, d_.result, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_) !=
+                cudaSuccess)
+                return LB3E_ERR_CUDA;
+            TRY(sync());
+            last_res_ = pinned_[1] > 0 ? std::sqrt(pinned_[0] / pinned_[1]) : 0.0;
+            if (last_res_ <= tol) { last_conv_ = 1; break; }
+            if (cycles >= max_cycles) break;
+            // V-cycle (the fine residual is in mg_[0].res)
+            for (int l = 0; l + 1 < nl; ++l) {
+                TRY(smooth(l, 2));
+                timer.begin(stream_, KC_POISSON);
+                k_mg_residual<<<mg_grid(l), blk, 0, stream_>>>(mg_[l], nullptr);
+                TRY(launched());
+                timer.begin(stream_, KC_POISSON);
+                k_mg_restrict<<<mg_grid(l + 1), blk, 0, stream_>>>(mg_[l], mg_[l + 1]);
+                TRY(launched());
+            }
+            timer.begin(stream_, KC_POISSON);
+            k_mg_coarse_solve<<<1, 256, 0, stream_>>>(mg_[nl - 1], nl == 1 ? 2 : 200);
+            TRY(launched());
+            for (int l = nl - 2; l >= 0; --l) {
+                timer.begin(stream_, KC_POISSON);
+                k_mg_prolong<<<mg_grid(l), blk, 0, stream_>>>(mg_[l], mg_[l + 1]);
+                TRY(launched());
+                TRY(smooth(l, 2));
+            }
+            ++cycles;
+            poisson_iters_run_ += 1;
+        }
+        last_iters_ = cycles;
+        timer.begin(stream_, KC_FIELDS);
+        k_mg_fields<R><<<mg_grid(0), blk, 0, stream_>>>(mg_[0], vb, vt, p_.E_ext[0], p_.E_ext[1], d_.E);
+        return launched();
+    }
+
     // the pseudo-time potential solve (Eq. 43) from the current h.  Iterations
     // run in chunks of up to PB_HALO per launch (k_poisson_tb); a chunk never
     // straddles a residual check, which is taken before the first collision of a
@@ -467,6 +580,7 @@ class Sim final : public SimBase {
     double last_res_ = -1.0;
     double* pinned_ = nullptr;
     bool pb_ready_ = false;
+    std::vector<MGLevel> mg_;
 
   public:
     int64_t poisson_iters_run_ = 0;  // pseudo-iterations executed (all solves)

@@ -21,10 +21,10 @@ def _instances(precision, iters=6):
     return out
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 0.0), (1, 1e-6), (2, 1e-4)])
+@pytest.mark.parametrize("precision,tol", [(0, 0.0), (1, 1e-5), (2, 1e-4)])
 def test_batch_equals_single_lattice_runs(precision, tol):
     """Every instance of a batch matches the lattice stepped alone over 9 steps
-    (plain, graph pairs, plain): bitwise in FP64 (no contraction), to 1e-6 in FP32
+    (plain, graph pairs, plain): bitwise in FP64 (no contraction), to 1e-5 in FP32
     (the batched and single kernels are compiled separately and may fuse different
     multiply-adds), to 1e-4 with FP16 storage (an ulp of FP32 may flip an FP16
     rounding)."""

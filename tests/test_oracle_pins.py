@@ -404,3 +404,67 @@ def test_perfect_dielectric_drop_elongates_along_field(eps_in):
     o.step(400)
     D = o.observables()["D_inner"]
     assert D > 1e-4
+
+
+# --------------------------------------------------------------------------- FD potential
+def _fd(p, phi, q=None):
+    o = oracle.Oracle(dict(p, potential_solver=1), phi)
+    it, res, conv = o.solve_potential(q=q)
+    assert conv and res < 1e-12
+    return o
+
+
+def test_fd_potential_linear_between_electrodes_exact():
+    """Eq. 27d in 5-point form, uniform eps, no charge: psi = V (y + 1/2)/ny and
+    E = -V/ny exactly (the half-cell Dirichlet face and the Eq. 33 gradient are
+    exact on linear fields)."""
+    nx, ny, V = 8, 20, 0.7
+    p = W.params(nx=nx, ny=ny, bc_y=2, V_top=V, eps=(3.0, 3.0, 3.0))
+    o = _fd(p, W.single_phase(nx, ny, 1))
+    y = np.arange(ny)
+    assert np.allclose(o.field("psi")[:, 0], V * (y + 0.5) / ny, atol=1e-12)
+    assert np.allclose(o.field("ey"), -V / ny, atol=1e-12)
+    assert np.abs(o.field("ex")).max() < 1e-13
+
+
+def test_fd_potential_periodic_mode_is_the_discrete_eigenfunction():
+    """Periodic, uniform eps, q = sin(2 pi k x / nx): the 5-point operator's
+    eigenvalue is eps (2 - 2 cos(2 pi k / nx)), so psi = q / that, exactly."""
+    nx, ny, e, k = 32, 6, 2.0, 3
+    p = W.params(nx=nx, ny=ny, bc_y=0, eps=(e, e, e))
+    x = np.arange(nx)
+    q = np.tile(1e-3 * np.sin(2 * np.pi * k * x / nx), (ny, 1))
+    o = _fd(p, W.single_phase(nx, ny, 1), q=q)
+    lam = e * (2 - 2 * np.cos(2 * np.pi * k / nx))
+    assert np.allclose(o.field("psi"), q / lam, rtol=0, atol=1e-12 * np.abs(q / lam).max())
+
+
+def test_fd_potential_layered_dielectric_discrete_series():
+    """eps varying in y only, no charge, electrodes: the discrete flux through
+    every face is the same, so psi follows the series of face resistances
+    (harmonic-mean faces, half-cell Dirichlet faces at the walls) exactly."""
+    nx, ny, D, V = 4, 40, 6.0, 1.0
+    p = W.params(nx=nx, ny=ny, bc_y=2, V_top=V, eps=(1.0, 2.0, 4.0), width_D=D)
+    phi = W.flat_interface(nx, ny, D, 1, 3)
+    o = _fd(p, phi)
+    eps = (phi[0] ** 2 * (3 - 2 * phi[0]) * 1.0 + phi[2] ** 2 * (3 - 2 * phi[2]) * 4.0)[:, 0]
+    r = [1 / (2 * eps[0])] + [1 / (2 * eps[i] * eps[i + 1] / (eps[i] + eps[i + 1])) for i in range(ny - 1)] \
+        + [1 / (2 * eps[-1])]
+    cum = np.cumsum(r)
+    exact = V * cum[:-1] / cum[-1]
+    assert np.allclose(o.field("psi")[:, 0], exact, atol=1e-12)
+
+
+def test_fd_potential_charge_slab_second_order():
+    """Uniform charge between grounded electrodes: the FD potential converges to
+    q (y + 1/2)(ny - 1/2 - y) / (2 eps) at second order."""
+    errs = []
+    for ny in (16, 32, 64):
+        nx, q0, e = 4, 1e-3, 2.0
+        p = W.params(nx=nx, ny=ny, bc_y=2, eps=(e, e, e))
+        o = _fd(p, W.single_phase(nx, ny, 1), q=np.full((ny, nx), q0))
+        y = np.arange(ny)
+        exact = q0 * (y + 0.5) * (ny - 0.5 - y) / (2 * e)
+        errs.append(np.abs(o.field("psi")[:, 0] - exact).max() / exact.max())
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5
+    assert errs[2] < 2e-3

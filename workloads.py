@@ -43,6 +43,7 @@ PARAM_DEFAULTS = dict(
     poisson_max_iter=20000,
     poisson_check_every=8,
     poisson_fixed_iter=0,
+    potential_solver=0,          # 0 the LB pseudo-time solve of the paper; 1 multigrid on its FD form
     tangent_param=(-1, -1, -1),  # GPU tangent builds: parameter per tangent direction
 )
 
