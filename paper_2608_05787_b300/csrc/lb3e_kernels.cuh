@@ -612,6 +612,31 @@ __device__ __forceinline__ R chem_pot(const DevParams& P, int i, R ph, R lap, R 
 // 45 populations.  write_diag stores u, p, mu for field output.
 constexpr int TX = 32, TY = 8;
 
+// Asynchronous global->shared copies (cp.async): a thread's populations, d/dt
+// state and charge are requested at kernel entry and stream in while the phi/E
+// tiles load and mu is evaluated, so many loads are in flight per warp without
+// holding registers.  Used when the storage type is float or double.
+template <class S>
+__host__ __device__ constexpr bool fused_prefetch() {
+    return std::is_same<S, float>::value || std::is_same<S, double>::value;
+}
+constexpr int FZ_SLOTS = 54;  // 45 population planes, 8 d/dt planes, q
+template <class S>
+__host__ __device__ constexpr size_t fused_dyn_smem() {
+    return fused_prefetch<S>() ? (size_t)FZ_SLOTS * TX * TY * sizeof(S) : 0;
+}
+template <class T>
+__device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async of 4 or 8 bytes");
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <class R, class S>
 __device__ __forceinline__ void body_fused(const DevParams P, const S* __restrict__ pin, S* __restrict__ pout,
                                                    const R* __restrict__ phi, const R* __restrict__ qf,
@@ -626,6 +651,30 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     const unsigned N = P.N;
     const int x0 = bx * TX, y0 = by * TY;
     const int tid = threadIdx.x + TX * threadIdx.y;
+
+    // request this thread's populations, d/dt state and charge (own cell) first
+    extern __shared__ __align__(16) unsigned char fz_raw[];
+    S* sp = reinterpret_cast<S*>(fz_raw);  // [FZ_SLOTS][TX * TY]
+    if constexpr (fused_prefetch<S>()) {
+        const int xs = x0 + threadIdx.x, ys = y0 + threadIdx.y;
+        if (xs < nx && ys < ny) {
+            const unsigned cs = (unsigned)ys * nx + xs;
+#pragma unroll
+            for (int k = 0; k < 45; ++k) {
+                if (anchored<S>() && (k == 9 || k == 18 || k == 27)) continue;  // rest populations rebuilt
+                cp_async(sp + k * (TX * TY) + tid, pin + k * N + cs);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) cp_async(sp + (45 + k) * (TX * TY) + tid, reinterpret_cast<const S*>(prev) + k * N + cs);
+            cp_async(sp + 53 * (TX * TY) + tid, reinterpret_cast<const S*>(qf) + cs);
+        }
+        cp_async_commit();
+    }
+    // population k (plane k of the set-major layout), d/dt plane k, charge of this cell
+    auto popk = [&](int k, unsigned cc) -> R {
+        if constexpr (fused_prefetch<S>()) return (R)sp[k * (TX * TY) + tid];
+        else return Store<S>::ld(pin, k * N + cc);
+    };
 
     for (int k = tid; k < PY * PX; k += TX * TY) {
         const int ly = k / PX, lx = k % PX;
@@ -673,6 +722,7 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     if (x >= nx || y >= ny) return;
     const unsigned c = (unsigned)y * nx + x;
+    if constexpr (fused_prefetch<S>()) cp_async_wait_all();  // this thread's own slots are in
     const int py = threadIdx.y + 2, px = threadIdx.x + 2;
     const int my = threadIdx.y + 1, mx = threadIdx.x + 1;
 
@@ -712,7 +762,9 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     gsx = oc2(gsx); gsy = oc2(gsy);
 
     const R Ex = sE[0][my * MX + mx], Ey = sE[1][my * MX + mx];
-    const R qc = qf[c];
+    R qc;
+    if constexpr (fused_prefetch<S>()) qc = (R)sp[53 * (TX * TY) + tid];
+    else qc = qf[c];
     // R of Eq. 47 with q^n and E^n
     const R rr = dv(sg, ep, rcp(ep));
     const R Rc = -rr * qc + rr * (gex * Ex + gey * Ey) - (gsx * Ex + gsy * Ey);
@@ -724,10 +776,9 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     Fy = Fy + qc * Ey;
 
     // flow moments, Eq. 41
-    const S* gin = pin;
     R g[9];
 #pragma unroll
-    for (int j = 0; j < 9; ++j) g[j] = Store<S>::ld(gin, j * N + c);
+    for (int j = 0; j < 9; ++j) g[j] = popk(j, c);
     R mxm = R(0), mym = R(0), g1 = R(0);
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
@@ -742,14 +793,18 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     const R pr = cs2<R>() / (R(1) - wgt<R>(0)) * (g1 + R(0.5) * ugr + rho * s_eq<R>(0, ux, uy));
 
     // d/dt terms (first-order backward differences)
+    auto prevk = [&](int k) -> R {
+        if constexpr (fused_prefetch<S>()) return (R)sp[(45 + k) * (TX * TY) + tid];
+        else return prev[k * N + c];
+    };
     R dpu[3][2], dqu[2];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        dpu[i][0] = first ? R(0) : ph[i] * ux - prev[(2 * i) * N + c];
-        dpu[i][1] = first ? R(0) : ph[i] * uy - prev[(2 * i + 1) * N + c];
+        dpu[i][0] = first ? R(0) : ph[i] * ux - prevk(2 * i);
+        dpu[i][1] = first ? R(0) : ph[i] * uy - prevk(2 * i + 1);
     }
-    dqu[0] = first ? R(0) : qc * ux - prev[6 * N + c];
-    dqu[1] = first ? R(0) : qc * uy - prev[7 * N + c];
+    dqu[0] = first ? R(0) : qc * ux - prevk(6);
+    dqu[1] = first ? R(0) : qc * uy - prevk(7);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         prev[(2 * i) * N + c] = ph[i] * ux;
@@ -798,7 +853,7 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
         const R mui = smu[i][my * MX + mx];
         R fv[9];
 #pragma unroll
-        for (int j = anchored<S>() ? 1 : 0; j < 9; ++j) fv[j] = Store<S>::ld(pin, (9 * (i + 1) + j) * N + c);
+        for (int j = anchored<S>() ? 1 : 0; j < 9; ++j) fv[j] = popk(9 * (i + 1) + j, c);
         if constexpr (anchored<S>()) {
             // rest population in deviation form about phi_i: f_0 - phi_i = -sum_{j>0} f_j,
             // f_0 - f_0^eq = (1 - w_0) mu_i - sum_{j>0} f_j; the source term of j = 0 is zero
@@ -855,7 +910,7 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
             const R leq = cc ? wgt<R>(j) * qc * (R(1) + oc2(cu)) : wgt<R>(j) * qc;
             const R Sj = pl * wgt<R>(j) * Rc;
             const R Tj = cc ? oc2(pl * wgt<R>(j) * (R(cx(j)) * dqu[0] + R(cy(j)) * dqu[1])) : R(0);
-            const R lj = Store<S>::ld(pin, (36 + j) * N + c);
+            const R lj = popk(36 + j, c);
             push(4, j, lj - dv(lj - leq, tl, itl) + Sj + Tj);
         }
     }

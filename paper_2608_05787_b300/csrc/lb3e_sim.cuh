@@ -111,6 +111,11 @@ class Sim final : public SimBase {
     }
 
     int init(const double* phi, const double* u, const double* q, const double* noise) override {
+        if constexpr (fused_dyn_smem<S>() > 0) {
+            if (cudaFuncSetAttribute(k_fused<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)fused_dyn_smem<S>()) != cudaSuccess)
+                return LB3E_ERR_CUDA;
+        }
         if (cudaHostAlloc(reinterpret_cast<void**>(&pinned_), 64 * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
             return LB3E_ERR_CUDA;
         // phi, u, q -> device fields (through the FP64 staging area)
@@ -180,7 +185,7 @@ class Sim final : public SimBase {
                 TRY(poisson(p_.poisson_tol, p_.poisson_max_iter, p_.poisson_fixed_iter, p_.poisson_check_every));
             }
             timer.begin(stream_, KC_FUSED);
-            k_fused<R, S><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q,
+            k_fused<R, S><<<grid2_, dim3(TX, TY), fused_dyn_smem<S>(), stream_>>>(dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q,
                                                                  d_.E, d_.prev, d_.diag, step_ == 0 ? 1 : 0, last);
             TRY(launched());
             cur_ ^= 1;
@@ -401,15 +406,17 @@ class Sim final : public SimBase {
     // sum nb x 4 block partials into result[0..3]: 148 first-stage blocks write
     // their sums after the partial rows (the partial area holds nblk x NOBS
     // doubles, and 4 * nb + 4 * 148 fits for every grid), then one block adds those
-    int reduce4(int nb) {
+    int reduce4(int nb) { return reduce_nv<4>(nb); }
+    template <int NV>
+    int reduce_nv(int nb) {
         const int s1 = nb < 148 ? 1 : 148;
         const int chunk = (nb + s1 - 1) / s1;
-        double* mid = d_.partial + 4 * (size_t)nb;
+        double* mid = d_.partial + NV * (size_t)nb;
         timer.begin(stream_, KC_REDUCE);
-        k_reduce_stage1<4><<<s1, 256, 0, stream_>>>(d_.partial, nb, chunk, mid);
+        k_reduce_stage1<NV><<<s1, 256, 0, stream_>>>(d_.partial, nb, chunk, mid);
         TRY(launched());
         timer.begin(stream_, KC_REDUCE);
-        k_reduce_partials<4><<<1, 256, 0, stream_>>>(mid, s1, d_.result);
+        k_reduce_partials<NV><<<1, 256, 0, stream_>>>(mid, s1, d_.result);
         return launched();
     }
     int copy_out(double* dst, const double* dsrc) {
@@ -452,10 +459,7 @@ class Sim final : public SimBase {
             timer.begin(stream_, KC_REDUCE);
             k_mg_residual<<<mg_grid(0), blk, 0, stream_>>>(mg_[0], d_.partial);
             TRY(launched());
-            const int nb = (int)(mg_grid(0).x * mg_grid(0).y);
-            timer.begin(stream_, KC_REDUCE);
-            k_reduce_partials<2><<<1, 256, 0, stream_>>>(d_.partial, nb, d_.result);
-            TRY(launched());
+            TRY(reduce_nv<2>((int)(mg_grid(0).x * mg_grid(0).y)));
             if (cudaMemcpyAsync(pinned_, d_.result, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_) !=
                 cudaSuccess)
                 return LB3E_ERR_CUDA;
@@ -474,7 +478,7 @@ class Sim final : public SimBase {
                 TRY(launched());
             }
             timer.begin(stream_, KC_POISSON);
-            k_mg_coarse_solve<<<1, 256, 0, stream_>>>(mg_[nl - 1], nl == 1 ? 2 : 200);
+            k_mg_coarse_solve<<<1, 256, 0, stream_>>>(mg_[nl - 1], nl == 1 ? 2 : 50);
             TRY(launched());
             for (int l = nl - 2; l >= 0; --l) {
                 timer.begin(stream_, KC_POISSON);
@@ -641,6 +645,11 @@ class Batch final : public BatchBase {
     }
 
     int init(const double* const* phis) {
+        if constexpr (fused_dyn_smem<S>() > 0) {
+            if (cudaFuncSetAttribute(kb_fused<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)fused_dyn_smem<S>()) != cudaSuccess)
+                return LB3E_ERR_CUDA;
+        }
         for (int i = 0; i < n_; ++i) TRY(sims_[i]->init(phis[i], nullptr, nullptr, nullptr));
         std::vector<InstState<R, S>> tab(n_);
         std::vector<int4> tl, ptl;
@@ -762,7 +771,7 @@ class Batch final : public BatchBase {
             }
         }
         if (iters_ > 0) kb_potential_fields<R, S><<<ntiles_, blk, 0, stream_>>>(table_, tiles_, h);
-        kb_fused<R, S><<<ntiles_, blk, 0, stream_>>>(table_, tiles_, cur, first ? 1 : 0, diag ? 1 : 0);
+        kb_fused<R, S><<<ntiles_, blk, fused_dyn_smem<S>(), stream_>>>(table_, tiles_, cur, first ? 1 : 0, diag ? 1 : 0);
         launches += 3 + swaps() + (iters_ > 0);
         return cudaGetLastError() == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
     }
