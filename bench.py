@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=0, help="potential iterations per step in the CPU sample")
     ap.add_argument("--potential", default="lb", choices=["lb", "mg"],
                     help="lb: the paper's pseudo-time LB solve (default); mg: multigrid on its FD form")
+    ap.add_argument("--max-iter", type=int, default=0,
+                    help="cap on LB potential iterations per step (default: the workload's 20000); profiling "
+                         "runs use a small cap to keep ncu captures short, and config records it")
     ap.add_argument("--check-every", type=int, default=0,
                     help="potential residual cadence (default: the workload's; 1 runs one iteration per launch)")
     return ap.parse_args()
@@ -237,6 +240,8 @@ def run_lb3e(args):
     params = cfg["params"]
     if args.check_every:
         params = dict(params, poisson_check_every=args.check_every)
+    if args.max_iter:
+        params = dict(params, poisson_max_iter=args.max_iter)
     if args.potential == "mg":
         params = dict(params, potential_solver=1, poisson_max_iter=50)
     N = args.n * args.n
@@ -348,7 +353,7 @@ def run_lb3e(args):
             "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic (stated initial condition of the workload)",
             "config": {"workload": f"compound drop deformation under field, {args.n}x{args.n}",
-                       "poisson_tol": params["poisson_tol"], "potential_iters_per_step": iters_per_step,
+                       "poisson_tol": params["poisson_tol"], "poisson_max_iter": params["poisson_max_iter"], "potential_iters_per_step": iters_per_step,
                        "potential_solver": ("multigrid V-cycles on the FD form" if params.get("potential_solver")
                                             else "LB pseudo-time iterations (Eq. 43)"),
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single lattice",

@@ -36,6 +36,9 @@ struct DevParams {
     // conversions, is slow on this part)
     float frho[3], fvisc[3], feps[3], fsig[3], flam[3];
     float fD, ftau_f, fm0, ftau_g, ftau_l, ftau_h, feps_ref, fVb, fVt, fuwb, fuwt;
+    // launch-wide constants of the FP32 collisions, formed once on the host:
+    // 1/tau, the source prefactor 1 - 1/(2 tau), 1/m0 and 24/D
+    float fitau_f, fpf, fim0, fitau_g, fpg, fitau_l, fpl, fitau_h, fc24;
 };
 
 // Device-side buffers of one simulation (pointers into the caller's workspace).
@@ -64,6 +67,33 @@ template <class R>
 __host__ __device__ constexpr R wgt(int j) { return j == 0 ? R(4.0 / 9.0) : (j <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0)); }
 template <class R>
 __host__ __device__ constexpr R cs2() { return R(1.0 / 3.0); }
+// c_j . (ax, ay) with the zero components left out and the unit ones as adds: the
+// same value as cx*ax + cy*ay (x * 0 is not folded away without fast-math, so the
+// literal form costs a multiply per zero component)
+template <class R>
+__device__ __forceinline__ R cdot(int j, R ax, R ay) {
+    if (cx(j) == 0 && cy(j) == 0) return R(0);
+    if (cy(j) == 0) return cx(j) > 0 ? ax : -ax;
+    if (cx(j) == 0) return cy(j) > 0 ? ay : -ay;
+    const R a = cx(j) > 0 ? ax : -ax;
+    return cy(j) > 0 ? a + ay : a - ay;
+}
+// acc += c_j,x * v (or c_j,y * v) in j order, skipping zero components
+template <class R>
+__device__ __forceinline__ void cacc(R& acc, int c, R v) {
+    if (c > 0) acc += v;
+    else if (c < 0) acc -= v;
+}
+// a * b + c rounded once.  The factored FP32 collisions spell out every FMA, so
+// their rounding does not depend on how the compiler contracts one kernel or
+// another (a batched and a single-lattice kernel then give the same bits).
+__device__ __forceinline__ float fmaf_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// acc += c * w * v for a lattice component c in {-1, 0, 1} (one FMA, or nothing)
+template <class R>
+__device__ __forceinline__ void cacc(R& acc, int c, R w, R v) {
+    if (c > 0) acc += w * v;
+    else if (c < 0) acc -= w * v;
+}
 
 template <class R>
 __host__ __device__ constexpr bool exact_arith() { return std::is_same<R, double>::value; }
@@ -107,8 +137,15 @@ __device__ __forceinline__ R dv(R a, R b, R inv_b) {
 }
 template <class R>
 __device__ __forceinline__ R rcp(R b) {
-    if constexpr (std::is_same<R, float>::value) return __frcp_rn(b);
+    if constexpr (std::is_same<R, float>::value) return __fdividef(1.0f, b);  // approximate, ~2 ulp
     else return R(1) / b;
+}
+// A launch-wide constant: the FP32 build reads the host-formed copy, the others
+// evaluate the expression (exactly, in the FP64 build)
+template <class R, class F>
+__device__ __forceinline__ R kconst(float host_value, F expr) {
+    if constexpr (std::is_same<R, float>::value) return host_value;
+    else return expr();
 }
 template <class R>
 __device__ __forceinline__ R oc2(R a) {  // a / cs^2
@@ -147,6 +184,8 @@ __host__ __device__ constexpr bool anchored() {
 }
 
 // ---------------------------------------------------------------- grid helpers
+// periodic index for a in [-n, 2n) (one lattice link from a cell), without branches
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 __device__ __forceinline__ int wrapi(int a, int n) {
     if (a < 0) a += n;
     else if (a >= n) a -= n;
@@ -288,6 +327,28 @@ __global__ void __launch_bounds__(256) k_prologue(DevParams P, const R* __restri
 }
 
 // ---------------------------------------------------------------- S5: potential iteration (Eq. 43-45)
+// Post-collision h_j of one cell (Eq. 43) with heq_0 = (w_0 - 1) psi, heq_j = w_j psi,
+// source varpi_j q (varpi_0 = 0, varpi_j = 1/8) and grad psi = -J / den,
+// den = eps_hat + cs2 tau_h.  The FP64 and dual builds evaluate Eq. 43 as written;
+// the FP32 build uses the equal factored form
+//   h_j* = (1 - 1/tau_h) h_j + w_j (psi/tau_h + Kc c_j.J) + q/8,
+//   h_0* = (1 - 1/tau_h) h_0 + (w_0 - 1) psi/tau_h,   Kc = 3 eps_hat / (tau_h den),
+// which takes a third of the instructions.
+template <class R>
+__device__ __forceinline__ R h_collide(int j, R hj, R ps, R gx, R gy, R jx, R jy, R th, R ith, R epshat, R Kc, R qc,
+                                       R q8) {
+    if constexpr (std::is_same<R, float>::value) {
+        const R A = ith * ps, om = R(1) - ith;
+        if (j == 0) return fmaf_(om, hj, (wgt<R>(0) - R(1)) * A);
+        return fmaf_(om, hj, fmaf_(wgt<R>(j), fmaf_(Kc, cdot<R>(j, jx, jy), A), q8));
+    } else {
+        const R heq = (j == 0) ? (wgt<R>(0) - R(1)) * ps : wgt<R>(j) * ps;
+        const R varpi = (j == 0) ? R(0) : R(1.0 / 8.0);
+        const R cg = cdot<R>(j, gx, gy);
+        return hj - dv(hj - heq, th, ith) - dv(oc2(epshat) * wgt<R>(j) * cg, th, ith) + varpi * qc;
+    }
+}
+
 // One pseudo-time collide + push-stream of h.  On iterations before a check it
 // saves psi and J = sum c_j h_j; on a check it accumulates (FP64, per block)
 // |d psi|^2, |psi|^2, |d J|^2, |J|^2.
@@ -309,7 +370,7 @@ __device__ __forceinline__ void body_poisson(const DevParams P, const R* __restr
         for (int j = 1; j < 9; ++j) ps += hj[j];
         ps = dv(ps, R(1) - wgt<R>(0), R(1.8));
 #pragma unroll
-        for (int j = 0; j < 9; ++j) { jx += R(cx(j)) * hj[j]; jy += R(cy(j)) * hj[j]; }
+        for (int j = 0; j < 9; ++j) { cacc(jx, cx(j), hj[j]); cacc(jy, cy(j), hj[j]); }
         if (check) {
             const double d = (double)ps - (double)prev[c];
             const double ex = (double)jx - (double)prev[N + c], ey = (double)jy - (double)prev[2 * N + c];
@@ -319,17 +380,15 @@ __device__ __forceinline__ void body_poisson(const DevParams P, const R* __restr
             acc[3] = (double)jx * (double)jx + (double)jy * (double)jy;
         }
         if (save_prev) { prev[c] = ps; prev[N + c] = jx; prev[2 * N + c] = jy; }
-        const R th = pv<R>(P.tau_h, P.ftau_h), ith = rcp(th);
+        const R th = pv<R>(P.tau_h, P.ftau_h), ith = kconst<R>(P.fitau_h, [&] { return rcp(th); });
         const R epshat = eps[c] - pv<R>(P.eps_ref, P.feps_ref);
         const R den = epshat + cs2<R>() * th, iden = rcp(den);
         const R gx = dv(-jx, den, iden), gy = dv(-jy, den, iden);
         const R qc = q[c];
+        const R Kc = R(3) * ith * epshat * iden;
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
-            const R heq = (j == 0) ? (wgt<R>(0) - R(1)) * ps : wgt<R>(j) * ps;
-            const R varpi = (j == 0) ? R(0) : R(1.0 / 8.0);
-            const R cg = R(cx(j)) * gx + R(cy(j)) * gy;
-            const R v = hj[j] - dv(hj[j] - heq, th, ith) - dv(oc2(epshat) * wgt<R>(j) * cg, th, ith) + varpi * qc;
+            const R v = h_collide<R>(j, hj[j], ps, gx, gy, jx, jy, th, ith, epshat, Kc, qc, R(0.125) * qc);
             const int yt = y + cy(j);
             if (P.bc_y != 0 && (yt < 0 || yt >= P.ny)) {
                 R out = v;
@@ -386,8 +445,11 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
                                                 int bx, int by, int gdx) {
     extern __shared__ __align__(16) unsigned char pb_raw[];
     R* hs = reinterpret_cast<R*>(pb_raw);           // [9][PB_CELLS] post-collision values
-    R* se = hs + 9 * PB_CELLS;                      // eps
-    R* sq = se + PB_CELLS;                          // q
+    // per cell, fixed over the iterations: eps and q, or, in the factored FP32
+    // form, Kc = 3 eps_hat / (tau_h den) and q / 8
+    constexpr bool kFact = std::is_same<R, float>::value;
+    R* se = hs + 9 * PB_CELLS;                      // eps (Kc)
+    R* sq = se + PB_CELLS;                          // q (q / 8)
     const int nx = P.nx, ny = P.ny;
     const unsigned N = P.N;
     const int x0 = bx * PB_TX - PB_HALO, y0 = by * PB_TY - PB_HALO;
@@ -416,17 +478,23 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
             const unsigned c = (unsigned)wrapi(gy, ny) * nx + wrapi(gx, nx);
 #pragma unroll
             for (int j = 0; j < 9; ++j) h[m][j] = hin[j * N + c];
-            se[k] = eps[c];
-            sq[k] = q[c];
+            if constexpr (kFact) {
+                const R eh = eps[c] - P.feps_ref;
+                se[k] = R(3) * P.fitau_h * eh * rcp(eh + cs2<R>() * P.ftau_h);
+                sq[k] = R(0.125) * q[c];
+            } else {
+                se[k] = eps[c];
+                sq[k] = q[c];
+            }
         } else {
 #pragma unroll
             for (int j = 0; j < 9; ++j) h[m][j] = R(0);
-            if (k < PB_CELLS) { se[k] = pv<R>(P.eps_ref, P.feps_ref); sq[k] = R(0); }
+            if (k < PB_CELLS) { se[k] = kFact ? R(0) : pv<R>(P.eps_ref, P.feps_ref); sq[k] = R(0); }
         }
     }
     __syncthreads();
 
-    const R th = pv<R>(P.tau_h, P.ftau_h), ith = rcp(th);
+    const R th = pv<R>(P.tau_h, P.ftau_h), ith = kconst<R>(P.fitau_h, [&] { return rcp(th); });
     const R vb = prm<R>(P.V_bottom, P.t_Vb, P.fVb), vt = prm<R>(P.V_top, P.t_Vt, P.fVt);
     const R eref = pv<R>(P.eps_ref, P.feps_ref);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -441,7 +509,7 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
             for (int j = 1; j < 9; ++j) ps += h[m][j];
             ps = dv(ps, R(1) - wgt<R>(0), R(1.8));
 #pragma unroll
-            for (int j = 0; j < 9; ++j) { jx += R(cx(j)) * h[m][j]; jy += R(cy(j)) * h[m][j]; }
+            for (int j = 0; j < 9; ++j) { cacc(jx, cx(j), h[m][j]); cacc(jy, cy(j), h[m][j]); }
             if (tile[m] && (check && t == 0 || save_prev && t == K - 1)) {
                 const unsigned c = gc[m];
                 if (check && t == 0) {
@@ -454,17 +522,19 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
                 }
                 if (save_prev && t == K - 1) { prev[c] = ps; prev[N + c] = jx; prev[2 * N + c] = jy; }
             }
-            const R epshat = se[k] - eref;
-            const R den = epshat + cs2<R>() * th, iden = rcp(den);
-            const R gx = dv(-jx, den, iden), gy2 = dv(-jy, den, iden);
-            const R qc = sq[k];
+            if constexpr (kFact) {
+                const R Kc = se[k], q8 = sq[k];
 #pragma unroll
-            for (int j = 0; j < 9; ++j) {
-                const R heq = (j == 0) ? (wgt<R>(0) - R(1)) * ps : wgt<R>(j) * ps;
-                const R varpi = (j == 0) ? R(0) : R(1.0 / 8.0);
-                const R cg = R(cx(j)) * gx + R(cy(j)) * gy2;
-                hs[j * PB_CELLS + k] =
-                    h[m][j] - dv(h[m][j] - heq, th, ith) - dv(oc2(epshat) * wgt<R>(j) * cg, th, ith) + varpi * qc;
+                for (int j = 0; j < 9; ++j)
+                    hs[j * PB_CELLS + k] = h_collide<R>(j, h[m][j], ps, R(0), R(0), jx, jy, th, ith, R(0), Kc, R(0), q8);
+            } else {
+                const R epshat = se[k] - eref;
+                const R den = epshat + cs2<R>() * th, iden = rcp(den);
+                const R gx = dv(-jx, den, iden), gy2 = dv(-jy, den, iden);
+                const R qc = sq[k];
+#pragma unroll
+                for (int j = 0; j < 9; ++j)
+                    hs[j * PB_CELLS + k] = h_collide<R>(j, h[m][j], ps, gx, gy2, jx, jy, th, ith, epshat, R(0), qc, R(0));
             }
         }
         __syncthreads();
@@ -590,9 +660,9 @@ __global__ void k_fill_E(DevParams P, R* __restrict__ E) {
 template <class R>
 __device__ __forceinline__ R lap_tile(const R* t, int pitch, int ty, int tx) {
     const R c = t[ty * pitch + tx];
-    R a = R(0);
+    R a = R(0);  // the j = 0 term, 2 w_0 (c - c), is exactly zero
 #pragma unroll
-    for (int j = 0; j < 9; ++j) a += R(2) * wgt<R>(j) * (t[(ty + cy(j)) * pitch + tx + cx(j)] - c);
+    for (int j = 1; j < 9; ++j) a += R(2) * wgt<R>(j) * (t[(ty + cy(j)) * pitch + tx + cx(j)] - c);
     return oc2(a);
 }
 template <class R>
@@ -634,6 +704,11 @@ __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+template <class T>
+__device__ __forceinline__ void cp_async16(T* smem, const T* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
@@ -647,26 +722,47 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     __shared__ R sphi[3][PY * PX];
     __shared__ R sE[2][MY * MX];
     __shared__ R smu[3][MY * MX];
+    // rho, eps, sigma of the 1-ring cells (formed once per tile; dual types, whose
+    // tiles would exceed the static shared-memory limit, evaluate them per stencil)
+    constexpr bool kProps = !is_dual<R>::value;
+    // FP32 collisions in factored form (same expressions up to rounding, fewer
+    // instructions); the FP64 and dual builds evaluate Eq. 34-50 as written
+    constexpr bool kFact = std::is_same<R, float>::value;
+    __shared__ R sprop[kProps ? 3 : 1][kProps ? MY * MX : 1];
     const int nx = P.nx, ny = P.ny;
     const unsigned N = P.N;
     const int x0 = bx * TX, y0 = by * TY;
     const int tid = threadIdx.x + TX * threadIdx.y;
 
-    // request this thread's populations, d/dt state and charge (own cell) first
+    // request the tile's populations, d/dt state and charge first: 16-byte copies
+    // of row segments when rows are 16-byte aligned (nx a multiple of 16/sizeof(S)),
+    // else one element per copy; slot layout [plane][ty * TX + tx]
     extern __shared__ __align__(16) unsigned char fz_raw[];
     S* sp = reinterpret_cast<S*>(fz_raw);  // [FZ_SLOTS][TX * TY]
     if constexpr (fused_prefetch<S>()) {
-        const int xs = x0 + threadIdx.x, ys = y0 + threadIdx.y;
-        if (xs < nx && ys < ny) {
-            const unsigned cs = (unsigned)ys * nx + xs;
-#pragma unroll
-            for (int k = 0; k < 45; ++k) {
+        static_assert(std::is_same<R, S>::value, "prefetch stores R-typed d/dt state and charge in S slots");
+        auto plane = [&](int k) -> const S* {
+            return k < 45 ? pin + (size_t)k * N : (k < 53 ? prev + (size_t)(k - 45) * N : qf);
+        };
+        constexpr int V = 16 / (int)sizeof(S);      // cells per 16-byte segment
+        constexpr int SEG = TX / V;                  // segments per tile row
+        if (nx % V == 0) {
+            for (int t = tid; t < FZ_SLOTS * TY * SEG; t += TX * TY) {
+                const int k = t / (TY * SEG), r = (t / SEG) % TY, m = t % SEG;
                 if (anchored<S>() && (k == 9 || k == 18 || k == 27)) continue;  // rest populations rebuilt
-                cp_async(sp + k * (TX * TY) + tid, pin + k * N + cs);
+                const int ys = y0 + r, xs = x0 + m * V;
+                if (ys >= ny || xs >= nx) continue;   // nx % V == 0: a segment is all in or all out
+                cp_async16(sp + k * (TX * TY) + r * TX + m * V, plane(k) + (unsigned)ys * nx + xs);
             }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) cp_async(sp + (45 + k) * (TX * TY) + tid, reinterpret_cast<const S*>(prev) + k * N + cs);
-            cp_async(sp + 53 * (TX * TY) + tid, reinterpret_cast<const S*>(qf) + cs);
+        } else {
+            const int xs = x0 + threadIdx.x, ys = y0 + threadIdx.y;
+            if (xs < nx && ys < ny) {
+                const unsigned cs = (unsigned)ys * nx + xs;
+                for (int k = 0; k < FZ_SLOTS; ++k) {
+                    if (anchored<S>() && (k == 9 || k == 18 || k == 27)) continue;
+                    cp_async(sp + k * (TX * TY) + tid, plane(k) + cs);
+                }
+            }
         }
         cp_async_commit();
     }
@@ -691,10 +787,18 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     }
     __syncthreads();
     // mu on the 1-ring at in-domain rows
-    const R c24 = R(24) / pv<R>(P.D, P.fD);
+    const R c24 = kconst<R>(P.fc24, [&] { return R(24) / pv<R>(P.D, P.fD); });
     for (int k = tid; k < MY * MX; k += TX * TY) {
         const int ly = k / MX, lx = k % MX;
         const int gy = y0 + ly - 1;
+        if constexpr (kProps) {
+            // ghost rows hold the mirrored phi, as the stencil expects
+            const int kp = (ly + 1) * PX + lx + 1;
+            const R p0 = sphi[0][kp], p1 = sphi[1][kp], p2 = sphi[2][kp];
+            sprop[0][k] = dens<R>(P, p0, p1, p2);
+            sprop[1][k] = perm<R>(P, p0, p1, p2);
+            sprop[2][k] = cond<R>(P, p0, p1, p2);
+        }
         if (P.bc_y != 0 && (gy < 0 || gy >= ny)) continue;
         const R ex = sE[0][k], ey = sE[1][k];
         const R e2 = ex * ex + ey * ey;
@@ -704,6 +808,7 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
             smu[i][k] = chem_pot<R>(P, i, ph, lap_tile<R>(sphi[i], PX, ly + 1, lx + 1), e2, c24);
         }
     }
+    if constexpr (fused_prefetch<S>()) cp_async_wait_all();  // slots are published by the barrier
     __syncthreads();
     // ghost rows of mu mirror the in-domain row they face
     if (P.bc_y != 0) {
@@ -722,7 +827,6 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     if (x >= nx || y >= ny) return;
     const unsigned c = (unsigned)y * nx + x;
-    if constexpr (fused_prefetch<S>()) cp_async_wait_all();  // this thread's own slots are in
     const int py = threadIdx.y + 2, px = threadIdx.x + 2;
     const int my = threadIdx.y + 1, mx = threadIdx.x + 1;
 
@@ -735,10 +839,10 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     for (int i = 0; i < 3; ++i) {
         R ax = R(0), ay = R(0);
 #pragma unroll
-        for (int j = 0; j < 9; ++j) {
+        for (int j = 1; j < 9; ++j) {
             const R v = smu[i][(my + cy(j)) * MX + mx + cx(j)];
-            ax += wgt<R>(j) * R(cx(j)) * v;
-            ay += wgt<R>(j) * R(cy(j)) * v;
+            cacc(ax, cx(j), wgt<R>(j), v);
+            cacc(ay, cy(j), wgt<R>(j), v);
         }
         gmu[i][0] = oc2(ax);
         gmu[i][1] = oc2(ay);
@@ -746,16 +850,26 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     R rho = R(0), sg = R(0), ep = R(0);
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
-        const int k = (py + cy(j)) * PX + px + cx(j);
-        const R p0 = sphi[0][k], p1 = sphi[1][k], p2 = sphi[2][k];
-        const R r = dens<R>(P, p0, p1, p2), e = perm<R>(P, p0, p1, p2), s = cond<R>(P, p0, p1, p2);
-        grx += wgt<R>(j) * R(cx(j)) * r;
-        gry += wgt<R>(j) * R(cy(j)) * r;
-        gex += wgt<R>(j) * R(cx(j)) * e;
-        gey += wgt<R>(j) * R(cy(j)) * e;
-        gsx += wgt<R>(j) * R(cx(j)) * s;
-        gsy += wgt<R>(j) * R(cy(j)) * s;
-        if (j == 0) { rho = r; ep = e; sg = s; }
+        R r, e, s;
+        if constexpr (kProps) {
+            const int k = (my + cy(j)) * MX + mx + cx(j);
+            r = sprop[0][k];
+            e = sprop[1][k];
+            s = sprop[2][k];
+        } else {
+            const int k = (py + cy(j)) * PX + px + cx(j);
+            const R p0 = sphi[0][k], p1 = sphi[1][k], p2 = sphi[2][k];
+            r = dens<R>(P, p0, p1, p2);
+            e = perm<R>(P, p0, p1, p2);
+            s = cond<R>(P, p0, p1, p2);
+        }
+        if (j == 0) { rho = r; ep = e; sg = s; continue; }
+        cacc(grx, cx(j), wgt<R>(j), r);
+        cacc(gry, cy(j), wgt<R>(j), r);
+        cacc(gex, cx(j), wgt<R>(j), e);
+        cacc(gey, cy(j), wgt<R>(j), e);
+        cacc(gsx, cx(j), wgt<R>(j), s);
+        cacc(gsy, cy(j), wgt<R>(j), s);
     }
     grx = oc2(grx); gry = oc2(gry);
     gex = oc2(gex); gey = oc2(gey);
@@ -782,8 +896,8 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     R mxm = R(0), mym = R(0), g1 = R(0);
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
-        mxm += R(cx(j)) * g[j];
-        mym += R(cy(j)) * g[j];
+        cacc(mxm, cx(j), g[j]);
+        cacc(mym, cy(j), g[j]);
         if (j) g1 += g[j];
     }
     const R irho = rcp(rho);
@@ -822,19 +936,22 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     }
 
     const bool walls = P.bc_y != 0;
-    // push helper: post-collision value v of plane (set, j) leaving cell (x, y)
+    // link j of this cell crosses a wall (half-way bounce-back) instead of reaching a neighbour
+    auto to_wall = [&](int j) { return cy(j) != 0 && walls && (y + cy(j) < 0 || y + cy(j) >= ny); };
+    // push helper: post-collision value v of plane (set, j) leaving cell (x, y); a
+    // link into a wall returns to this cell in the opposite direction.  Selects, not
+    // branches: the target is an index computed for every cell.
     auto push = [&](int set, int j, R v) {
-        const int yt = y + cy(j);
-        if (walls && (yt < 0 || yt >= ny)) {
-            Store<S>::st(pout, (9 * set + opp(j)) * N + c, v);
-        } else {
-            Store<S>::st(pout, (9 * set + j) * N + (unsigned)wrapi(yt, ny) * nx + wrapi(x + cx(j), nx), v);
-        }
+        const unsigned to = to_wall(j) ? (unsigned)opp(j) * N + c
+                                       : (unsigned)j * N + (unsigned)wrap1(y + cy(j), ny) * nx + wrap1(x + cx(j), nx);
+        Store<S>::st(pout, (size_t)(9 * set) * N + to, v);
     };
 
     // phase populations, Eq. 34-36 with the mobility of Eq. 28
-    const R tf = pv<R>(P.tau_f, P.ftau_f), m0 = pv<R>(P.m0, P.fm0), itf = rcp(tf), im0 = rcp(m0);
-    const R pf = R(1) - R(1) / (R(2) * tf);
+    const R tf = pv<R>(P.tau_f, P.ftau_f), m0 = pv<R>(P.m0, P.fm0);
+    const R itf = kconst<R>(P.fitau_f, [&] { return rcp(tf); });
+    const R im0 = kconst<R>(P.fim0, [&] { return rcp(m0); });
+    const R pf = kconst<R>(P.fpf, [&] { return R(1) - R(1) / (R(2) * tf); });
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         R Mii = R(0);
@@ -863,55 +980,94 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
             const R neq0 = (R(1) - wgt<R>(0)) * mui - a;
             push(i + 1, 0, -a - dv(neq0, tf, itf));
         }
+        if constexpr (kFact) {
+            // f_j* = (1 - 1/tau_f) f_j + w_j (mu/tau_f + c_j.Q), Q = 3 phi u / tau_f + pf A
+            const R om = R(1) - itf, b = itf * mui, c3 = R(3) * itf;
+            const R Qx = fmaf_(pf, Ax, c3 * (ph[i] * ux)), Qy = fmaf_(pf, Ay, c3 * (ph[i] * uy));
 #pragma unroll
-        for (int j = anchored<S>() ? 1 : 0; j < 9; ++j) {
-            const R feq = (j == 0) ? ph[i] - (R(1) - wgt<R>(0)) * mui
-                                   : wgt<R>(j) * mui + oc2(wgt<R>(j) * (R(cx(j)) * ph[i] * ux + R(cy(j)) * ph[i] * uy));
-            const R Fj = wgt<R>(j) * (R(cx(j)) * Ax + R(cy(j)) * Ay);
-            push(i + 1, j, fv[j] - dv(fv[j] - feq, tf, itf) + pf * Fj);
+            for (int j = 1; j < 9; ++j) push(i + 1, j, fmaf_(om, fv[j], wgt<R>(j) * (b + cdot<R>(j, Qx, Qy))));
+        } else {
+#pragma unroll
+            for (int j = anchored<S>() ? 1 : 0; j < 9; ++j) {
+                const R feq = (j == 0) ? ph[i] - (R(1) - wgt<R>(0)) * mui
+                                       : wgt<R>(j) * mui + oc2(wgt<R>(j) * cdot<R>(j, ph[i] * ux, ph[i] * uy));
+                const R Fj = wgt<R>(j) * cdot<R>(j, Ax, Ay);
+                push(i + 1, j, fv[j] - dv(fv[j] - feq, tf, itf) + pf * Fj);
+            }
         }
     }
 
     // flow populations, Eq. 37-40
     {
         R tg = pv<R>(P.tau_g, P.ftau_g);
+        R itg = kconst<R>(P.fitau_g, [&] { return rcp(tg); });
+        R pg = kconst<R>(P.fpg, [&] { return R(1) - R(1) / (R(2) * tg); });
         if (P.use_visc) {
             R eta = R(0);
 #pragma unroll
             for (int i = 0; i < 3; ++i) eta += ph[i] * pv<R>(P.visc[i], P.fvisc[i]);
-            tg = R(0.5) + eta / (rho * cs2<R>());
+            tg = R(0.5) + dv(eta, rho * cs2<R>(), oc2(irho));
+            itg = rcp(tg);
+            pg = R(1) - dv(R(1), R(2) * tg, R(0.5) * itg);
         }
         const R uw = y == 0 ? pv<R>(P.u_wall_bottom, P.fuwb) : pv<R>(P.u_wall_top, P.fuwt);
-        const R itg = rcp(tg), pg = R(1) - R(1) / (R(2) * tg);
+        // into a moving wall: g_opp = g* - 2 w rho (c . u_w) / cs2
+        auto wall_term = [&](int j) { return oc2(R(2) * wgt<R>(j) * rho * (R(cx(j)) * uw)); };
+        if constexpr (kFact) {
+            // g_j* = (1 - 1/tau_g) g_j + w_j [B + rho/tau_g c.u (3 + 4.5 c.u) + 3 pg (c.F + c.u c.grad rho)],
+            // B = (3 pr - 1.5 rho |u|^2)/tau_g; j = 0: (1 - 1/tau_g) g_0 + w_0 B - 3 pr/tau_g
+            // (G_0 = 0: the u.grad rho terms of Eq. 38 cancel for the rest direction)
+            const R om = R(1) - itg, uu = fmaf_(ux, ux, uy * uy);
+            const R B = itg * fmaf_(R(-1.5) * rho, uu, R(3) * pr);
+            const R c3 = R(3) * itg * rho, c45 = R(4.5) * itg * rho, p3 = R(3) * pg;
+            push(0, 0, fmaf_(om, g[0], fmaf_(wgt<R>(0), B, R(-3) * itg * pr)));
 #pragma unroll
-        for (int j = 0; j < 9; ++j) {
-            const R geq = (j == 0) ? oc2((wgt<R>(0) - R(1)) * pr) + rho * s_eq<R>(0, ux, uy)
-                                   : oc2(wgt<R>(j) * pr) + rho * s_eq<R>(j, ux, uy);
-            const R cu = R(cx(j)) * ux + R(cy(j)) * uy;
-            const R cgr = R(cx(j)) * grx + R(cy(j)) * gry;
-            const R cF = R(cx(j)) * Fx + R(cy(j)) * Fy;
-            const R G = wgt<R>(j) * (ugr + oc2(cF) + oc2(cu * cgr - cs2<R>() * ugr));
-            const R v = g[j] - dv(g[j] - geq, tg, itg) + pg * G;
-            const int yt = y + cy(j);
-            if (walls && (yt < 0 || yt >= ny))  // g_opp = g* - 2 w rho (c . u_w) / cs2
-                push(0, j, v - oc2(R(2) * wgt<R>(j) * rho * (R(cx(j)) * uw)));
-            else
-                push(0, j, v);
+            for (int j = 1; j < 9; ++j) {
+                const R cu = cdot<R>(j, ux, uy);
+                const R t = fmaf_(p3, fmaf_(cu, cdot<R>(j, grx, gry), cdot<R>(j, Fx, Fy)), fmaf_(cu, fmaf_(c45, cu, c3), B));
+                const R v = fmaf_(om, g[j], wgt<R>(j) * t);
+                push(0, j, to_wall(j) ? v - wall_term(j) : v);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const R geq = (j == 0) ? oc2((wgt<R>(0) - R(1)) * pr) + rho * s_eq<R>(0, ux, uy)
+                                       : oc2(wgt<R>(j) * pr) + rho * s_eq<R>(j, ux, uy);
+                const R cu = cdot<R>(j, ux, uy);
+                const R cgr = cdot<R>(j, grx, gry);
+                const R cF = cdot<R>(j, Fx, Fy);
+                const R G = wgt<R>(j) * (ugr + oc2(cF) + oc2(cu * cgr - cs2<R>() * ugr));
+                const R v = g[j] - dv(g[j] - geq, tg, itg) + pg * G;
+                push(0, j, to_wall(j) ? v - wall_term(j) : v);
+            }
         }
     }
 
     // charge populations, Eq. 48-50
     {
-        const R tl = pv<R>(P.tau_l, P.ftau_l), itl = rcp(tl), pl = R(1) - R(1) / (R(2) * tl);
+        const R tl = pv<R>(P.tau_l, P.ftau_l);
+        const R itl = kconst<R>(P.fitau_l, [&] { return rcp(tl); });
+        const R pl = kconst<R>(P.fpl, [&] { return R(1) - R(1) / (R(2) * tl); });
         const bool cc = P.charge_convection != 0;
+        if constexpr (kFact) {
+            // l_j* = (1 - 1/tau_l) l_j + w_j (q/tau_l + pl R + c_j.K),
+            // K = 3 (q u / tau_l + pl d(qu)/dt) with convection, else 0
+            const R om = R(1) - itl, iq = itl * qc, a0 = fmaf_(pl, Rc, iq);
+            const R Kx = cc ? R(3) * fmaf_(pl, dqu[0], iq * ux) : R(0);
+            const R Ky = cc ? R(3) * fmaf_(pl, dqu[1], iq * uy) : R(0);
+            push(4, 0, fmaf_(om, popk(36, c), wgt<R>(0) * a0));
 #pragma unroll
-        for (int j = 0; j < 9; ++j) {
-            const R cu = R(cx(j)) * ux + R(cy(j)) * uy;
-            const R leq = cc ? wgt<R>(j) * qc * (R(1) + oc2(cu)) : wgt<R>(j) * qc;
-            const R Sj = pl * wgt<R>(j) * Rc;
-            const R Tj = cc ? oc2(pl * wgt<R>(j) * (R(cx(j)) * dqu[0] + R(cy(j)) * dqu[1])) : R(0);
-            const R lj = popk(36 + j, c);
-            push(4, j, lj - dv(lj - leq, tl, itl) + Sj + Tj);
+            for (int j = 1; j < 9; ++j) push(4, j, fmaf_(om, popk(36 + j, c), wgt<R>(j) * (a0 + cdot<R>(j, Kx, Ky))));
+        } else {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const R cu = cdot<R>(j, ux, uy);
+                const R leq = cc ? wgt<R>(j) * qc * (R(1) + oc2(cu)) : wgt<R>(j) * qc;
+                const R Sj = pl * wgt<R>(j) * Rc;
+                const R Tj = cc ? oc2(pl * wgt<R>(j) * cdot<R>(j, dqu[0], dqu[1])) : R(0);
+                const R lj = popk(36 + j, c);
+                push(4, j, lj - dv(lj - leq, tl, itl) + Sj + Tj);
+            }
         }
     }
 }

@@ -60,6 +60,15 @@ inline DevParams make_dev_params(const lb3e_params& p) {
     d.fVt = (float)d.V_top;
     d.fuwb = (float)d.u_wall_bottom;
     d.fuwt = (float)d.u_wall_top;
+    d.fitau_f = (float)(1.0 / d.tau_f);
+    d.fpf = (float)(1.0 - 1.0 / (2.0 * d.tau_f));
+    d.fim0 = (float)(1.0 / d.m0);
+    d.fitau_g = (float)(1.0 / d.tau_g);
+    d.fpg = (float)(1.0 - 1.0 / (2.0 * d.tau_g));
+    d.fitau_l = (float)(1.0 / d.tau_l);
+    d.fpl = (float)(1.0 - 1.0 / (2.0 * d.tau_l));
+    d.fitau_h = (float)(1.0 / d.tau_h);
+    d.fc24 = (float)(24.0 / d.D);
     // tangent seeds: d lambda_i / d gamma_jk from Eq. 9
     static const double dlam[3][3] = {{1, 1, -1}, {1, -1, 1}, {-1, 1, 1}};
     for (int k = 0; k < 3; ++k) {
