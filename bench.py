@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=0,
                     help="cap on LB potential iterations per step (default: the workload's 20000); profiling "
                          "runs use a small cap to keep ncu captures short, and config records it")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="LB potential iterations per launch, 1..8 (default: the library's)")
     ap.add_argument("--check-every", type=int, default=0,
                     help="potential residual cadence (default: the workload's; 1 runs one iteration per launch)")
     return ap.parse_args()
@@ -83,14 +85,15 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, precision: int):
-    """DRAM bytes per cell from the committed ncu summary, if it was taken on the
-    current kernel sources (else None)."""
+def profiled_traffic(key: str):
+    """DRAM bytes per cell and launch from the committed ncu summary
+    (profiles/traffic.json, keyed "<kernel>:<precision>[:<iterations per launch>]"),
+    if it was taken on the current kernel sources (else None)."""
     f = ROOT / "profiles" / "traffic.json"
     if not f.exists():
         return None
     d = json.loads(f.read_text())
-    e = d.get(f"{kernel}:{precision}")
+    e = d.get(key)
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
     return float(e["bytes_per_cell"])
@@ -250,6 +253,8 @@ def run_lb3e(args):
         phi_dev = torch.from_numpy(cfg["phi"]).cuda()
         t_init0 = time.perf_counter()
         sim = L.Sim(params, phi_dev, stream=stream)
+        if args.chunk:
+            sim.set_chunk(args.chunk)
         t_init = time.perf_counter() - t_init0
         init_obs = sim.observables()
         sim.step(args.warmup)
@@ -299,10 +304,18 @@ def run_lb3e(args):
         k_gbs["poisson"] = pot_bytes * N * pot_iters / (poisson_ms / 1e3) / 1e9
     dominant = max(("fused", "poisson"), key=lambda k: kt[k][0])
     per_cell = FUSED_BYTES[prec] if dominant == "fused" else pot_bytes
-    traffic = profiled_traffic(dominant, prec)
+    chunk = args.chunk or 4
+    if dominant == "fused":
+        kname = "k_fused"
+    elif mg:
+        kname = "multigrid V-cycle kernels"
+    else:
+        kname = "k_poisson_tb" if chunk > 1 else "k_poisson"
+    traffic = None if mg and dominant == "poisson" else profiled_traffic(
+        f"{kname}:{prec}" + (f":{chunk}" if kname == "k_poisson_tb" else ""))
     roofline = {"bound": "hbm", "achieved": k_gbs.get(dominant), "peak": hbm, "unit": "GB/s",
                 "frac": (k_gbs.get(dominant) or 0) / hbm, "traffic": traffic * N if traffic else None,
-                "kernel": f"k_{dominant}" if not (mg and dominant == "poisson") else "multigrid V-cycle kernels",
+                "kernel": kname,
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "algorithmic_bytes_per_launch": per_cell * N * (pot_iters / max(1, poisson_n) if dominant == "poisson" else 1),
                 "units_per_launch": (f"{N} cells x {pot_iters / max(1, poisson_n):.2f} pseudo-iterations"
@@ -321,6 +334,8 @@ def run_lb3e(args):
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             s2 = L.Sim(params, host_phi, stream=stream)
+            if args.chunk:
+                s2.set_chunk(args.chunk)
             for _ in range(args.steps):
                 s2.step(1)
                 s2.observables()
@@ -353,7 +368,7 @@ def run_lb3e(args):
             "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic (stated initial condition of the workload)",
             "config": {"workload": f"compound drop deformation under field, {args.n}x{args.n}",
-                       "poisson_tol": params["poisson_tol"], "poisson_max_iter": params["poisson_max_iter"], "potential_iters_per_step": iters_per_step,
+                       "poisson_tol": params["poisson_tol"], "poisson_max_iter": params["poisson_max_iter"], "potential_chunk": args.chunk or 4, "potential_iters_per_step": iters_per_step,
                        "potential_solver": ("multigrid V-cycles on the FD form" if params.get("potential_solver")
                                             else "LB pseudo-time iterations (Eq. 43)"),
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single lattice",

@@ -74,10 +74,11 @@ enum {
 /* Largest lattice lb3e_init accepts (45 population planes are addressed with
  * 32-bit offsets). */
 #define LB3E_MAX_CELLS 40000000
+#define LB3E_MAX_NY (65535 * 8)   /* tiles of 8 rows, at most 65535 of them along y */
 
 /* Model and run parameters.  Index i of the per-phase arrays is phase i+1. */
 typedef struct lb3e_params {
-    int32_t nx, ny;               /* lattice, cells; both >= 2, nx * ny <= LB3E_MAX_CELLS; periodic in x */
+    int32_t nx, ny;               /* lattice, cells; both >= 2, nx * ny <= LB3E_MAX_CELLS, ny <= LB3E_MAX_NY; periodic in x */
     int32_t bc_y;                 /* 0 periodic, 1 half-way walls, 2 walls with electrodes */
     int32_t electric;             /* 1: solve the potential every step; 0: E = E_ext */
     int32_t precision;            /* 0 fp64; 1 fp32; 2 fp32 compute, fp16-stored populations;
@@ -185,6 +186,13 @@ int64_t lb3e_launch_count(const lb3e_handle* h);
 /* Pseudo-iterations of the potential solve (Eq. 43) executed since lb3e_init,
  * over all solves (a launch may run several). */
 int64_t lb3e_potential_iterations(const lb3e_handle* h);
+
+/* Pseudo-iterations of the LB potential solve (Eq. 43) per kernel launch: 1
+ * (one launch per iteration), 2 (temporally blocked on a tile with a 2-cell
+ * halo), 3..4 (4-cell halo; the default is 4) or 5..8 (8-cell halo).  The result does not depend on
+ * it up to rounding order; the speed does.  Dual-number precisions accept only 1.
+ * Errors: NULL, PARAM (out of range). */
+int lb3e_set_potential_chunk(lb3e_handle* h, int32_t iterations_per_launch);
 
 /* Kernel timing with CUDA events recorded on the simulation's stream around each
  * launch (off by default; costs two event records per launch).  Enabling or

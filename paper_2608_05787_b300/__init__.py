@@ -112,6 +112,7 @@ def lib() -> C.CDLL:
         L.lb3e_potential_iterations.restype = C.c_int64
         L.lb3e_potential_iterations.argtypes = [vp]
         L.lb3e_set_timing.argtypes = [vp, C.c_int32]
+        L.lb3e_set_potential_chunk.argtypes = [vp, C.c_int32]
         L.lb3e_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64)]
         L.lb3e_observables_noalloc.argtypes = [C.POINTER(Params), vp, vp, vp, vp, vp, C.POINTER(Observables)]
         L.lb3e_batch_workspace_bytes.argtypes = [C.POINTER(Params), C.c_int32, C.POINTER(C.c_size_t)]
@@ -266,6 +267,11 @@ class Sim:
 
     def set_timing(self, enable: bool):
         _check("lb3e_set_timing", lib().lb3e_set_timing(self._h, int(bool(enable))))
+
+    def set_chunk(self, k: int) -> "Sim":
+        """LB potential iterations per kernel launch (1..8; speed only)."""
+        _check("lb3e_set_potential_chunk", lib().lb3e_set_potential_chunk(self._h, int(k)))
+        return self
 
     def kernel_times(self) -> dict:
         """{class: (total ms, launches)} since the last call (synchronises)."""

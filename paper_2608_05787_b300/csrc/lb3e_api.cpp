@@ -19,6 +19,7 @@ int validate(const lb3e_params* p) {
     if (!p) return LB3E_ERR_NULL;
     if (p->nx < 2 || p->ny < 2) return LB3E_ERR_PARAM;
     if ((int64_t)p->nx * p->ny > LB3E_MAX_CELLS) return LB3E_ERR_PARAM;  // 32-bit plane offsets
+    if (p->ny > LB3E_MAX_NY) return LB3E_ERR_PARAM;  // grid y extent of the 32 x 8 tile launches
     if (p->bc_y < 0 || p->bc_y > 2 || p->precision < 0 || p->precision > 4) return LB3E_ERR_PARAM;
     for (int k = 0; k < 3; ++k)
         if (p->tangent_param[k] < -1 || p->tangent_param[k] > 6) return LB3E_ERR_PARAM;
@@ -172,6 +173,11 @@ int lb3e_load_state(lb3e_handle* h, const void* src) {
 int64_t lb3e_launch_count(const lb3e_handle* h) { return h ? h->sim->launches : 0; }
 
 int64_t lb3e_potential_iterations(const lb3e_handle* h) { return h ? h->sim->potential_iterations() : 0; }
+
+int lb3e_set_potential_chunk(lb3e_handle* h, int32_t iterations_per_launch) {
+    if (!h) return LB3E_ERR_NULL;
+    return h->sim->set_chunk(iterations_per_launch);
+}
 
 int lb3e_set_timing(lb3e_handle* h, int32_t enable) {
     if (!h) return LB3E_ERR_NULL;

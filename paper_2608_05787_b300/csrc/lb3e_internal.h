@@ -77,6 +77,7 @@ struct SimBase {
     virtual int load(const void* src) = 0;
     virtual int kernel_times(double* ms, int64_t* counts) = 0;
     virtual int64_t potential_iterations() const = 0;
+    virtual int set_chunk(int k) = 0;
     int64_t launches = 0;
     LaunchTimer timer;
 };

@@ -100,8 +100,6 @@ __host__ __device__ constexpr bool exact_arith() { return std::is_same<R, double
 // blocks per SM the register budget is sized for
 template <class R>
 __host__ __device__ constexpr int fused_min_blocks() { return std::is_same<R, float>::value ? 3 : 1; }
-template <class R>
-__host__ __device__ constexpr int pb_min_blocks() { return std::is_same<R, float>::value ? 2 : 1; }
 
 // A parameter as an R: the FP32 build reads its single-precision copy.
 template <class R>
@@ -261,6 +259,40 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* out)
     }
 }
 
+// The same for values of type R: FP32 values are summed within a warp in FP32
+// (a residual needs a few digits; FP64 shuffles and adds cost far more on this
+// part), the warp sums across the block and the grid in FP64.  Other types are
+// converted to FP64 first.
+template <int NV, class R>
+__device__ __forceinline__ void block_reduce_store_r(R (&v)[NV], double* out) {
+    if constexpr (std::is_same<R, float>::value) {
+        __shared__ double red[32][NV];
+        const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+        const int lane = tid & 31, warp = tid >> 5;
+        const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) red[warp][k] = (double)v[k];
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                double a = lane < nwarps ? red[lane][k] : 0.0;
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+                if (lane == 0) out[k] = a;
+            }
+        }
+    } else {
+        double d[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) d[k] = (double)v[k];
+        block_reduce_store<NV>(d, out);
+    }
+}
+
 // ---------------------------------------------------------------- S1: moments
 template <class R, class S>
 __device__ __forceinline__ void body_moments(const DevParams P, const S* __restrict__ pop, const R* phi_anchor,
@@ -360,7 +392,7 @@ __device__ __forceinline__ void body_poisson(const DevParams P, const R* __restr
     const int x = bx * blockDim.x + threadIdx.x, y = by * blockDim.y + threadIdx.y;
     const bool in = x < P.nx && y < P.ny;
     const unsigned N = P.N, c = in ? (unsigned)y * P.nx + x : 0;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    R acc[4] = {R(0), R(0), R(0), R(0)};
     if (in) {
         R hj[9];
 #pragma unroll
@@ -372,12 +404,11 @@ __device__ __forceinline__ void body_poisson(const DevParams P, const R* __restr
 #pragma unroll
         for (int j = 0; j < 9; ++j) { cacc(jx, cx(j), hj[j]); cacc(jy, cy(j), hj[j]); }
         if (check) {
-            const double d = (double)ps - (double)prev[c];
-            const double ex = (double)jx - (double)prev[N + c], ey = (double)jy - (double)prev[2 * N + c];
+            const R d = ps - prev[c], ex = jx - prev[N + c], ey = jy - prev[2 * N + c];
             acc[0] = d * d;
-            acc[1] = (double)ps * (double)ps;
+            acc[1] = ps * ps;
             acc[2] = ex * ex + ey * ey;
-            acc[3] = (double)jx * (double)jx + (double)jy * (double)jy;
+            acc[3] = jx * jx + jy * jy;
         }
         if (save_prev) { prev[c] = ps; prev[N + c] = jx; prev[2 * N + c] = jy; }
         const R th = pv<R>(P.tau_h, P.ftau_h), ith = kconst<R>(P.fitau_h, [&] { return rcp(th); });
@@ -403,7 +434,7 @@ __device__ __forceinline__ void body_poisson(const DevParams P, const R* __restr
     }
     if (check) {
         const int b = bx + gdx * by;
-        block_reduce_store<4>(acc, partial + 4 * (size_t)b);
+        block_reduce_store_r<4>(acc, partial + 4 * (size_t)b);
     }
 }
 template <class R>
@@ -415,65 +446,71 @@ __global__ void __launch_bounds__(256) k_poisson(DevParams P, const R* __restric
 }
 
 // ---------------------------------------------------------------- S5, temporally blocked
-// K (<= PB_HALO) pseudo-iterations of Eq. 43 per launch.  A block loads the h
-// populations of its PB_TX x PB_TY tile plus a PB_HALO-cell halo into registers
-// (PB_CPT cells per thread), and eps, q into shared memory.  Each iteration
+// K (<= H) pseudo-iterations of Eq. 43 per launch.  A block loads the h
+// populations of its PB_TX x PB_TY tile plus an H-cell halo into registers (three
+// cells per thread), and per-cell constants into shared memory.  Each iteration
 // collides in registers, writes the post-collision values to shared memory, and
-// pulls each cell's incoming populations back (bounce-back at walls); the region
-// of correct cells shrinks by one per iteration, so after K <= PB_HALO iterations
-// the tile itself is exact and is written out.  Per cell the arithmetic is that of
-// body_poisson.  Residual partials (check) are taken before the first collision,
-// the residual state (save_prev) before the last one.
+// pulls each cell's incoming populations back.  Cells at an electrode (or no-slip)
+// wall also write their reflected populations into the ghost row beyond the wall,
+// so the pull reads one slot per direction with no wall cases.  A cell at distance d
+// outside the tile collides at iteration t only while d <= K - t and pulls while
+// d <= K - 1 - t, so after K iterations the tile is exact and is written out.  The
+// arithmetic per cell is that of body_poisson.  Residual partials (check) are taken
+// before the first collision, the residual state (save_prev) before the last one.
 constexpr int PB_TX = 32, PB_TY = 16, PB_HALO = 8;
-constexpr int PB_RX = PB_TX + 2 * PB_HALO, PB_RY = PB_TY + 2 * PB_HALO;
-constexpr int PB_CELLS = PB_RX * PB_RY, PB_THREADS = 512;
-constexpr int PB_CPT = (PB_CELLS + PB_THREADS - 1) / PB_THREADS;
-template <class R>
-constexpr size_t pb_smem_bytes() { return (size_t)11 * PB_CELLS * sizeof(R); }
-// distance of a region cell from the region border
-__device__ __forceinline__ int ring_dist(int ly, int lx) {
-    const int a = ly < PB_RY - 1 - ly ? ly : PB_RY - 1 - ly;
-    const int b = lx < PB_RX - 1 - lx ? lx : PB_RX - 1 - lx;
-    return a < b ? a : b;
+template <int H>
+struct PBGeom {
+    static constexpr int RX = PB_TX + 2 * H, RY = PB_TY + 2 * H, CELLS = RX * RY;
+    static constexpr int CPT = 3, THREADS = CELLS / CPT;
+    static_assert(CELLS % CPT == 0, "region cells split evenly over the threads");
+};
+// blocks per SM the register budget is sized for (64 registers a thread in FP32)
+template <class R, int H>
+__host__ __device__ constexpr int pb_min_blocks() {
+    return std::is_same<R, float>::value ? (H == 8 ? 2 : (H == 4 ? 3 : 4)) : 1;
 }
+template <class R, int H>
+constexpr size_t pb_smem_bytes() { return (size_t)11 * PBGeom<H>::CELLS * sizeof(R); }
+// halo depth of the region that serves a chunk of K iterations
+__host__ __device__ constexpr int pb_halo_for(int K) { return K <= 2 ? 2 : (K <= 4 ? 4 : 8); }
 
-template <class R>
+template <class R, int H>
 __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __restrict__ hin,
                                                 R* __restrict__ hout, const R* __restrict__ eps,
                                                 const R* __restrict__ q, R* __restrict__ prev,
                                                 double* __restrict__ partial, int K, int save_prev, int check,
                                                 int bx, int by, int gdx) {
+    using G = PBGeom<H>;
+    constexpr int RX = G::RX, RY = G::RY, CELLS = G::CELLS, CPT = G::CPT, NT = G::THREADS;
     extern __shared__ __align__(16) unsigned char pb_raw[];
-    R* hs = reinterpret_cast<R*>(pb_raw);           // [9][PB_CELLS] post-collision values
+    R* hs = reinterpret_cast<R*>(pb_raw);  // [9][CELLS] post-collision values
     // per cell, fixed over the iterations: eps and q, or, in the factored FP32
     // form, Kc = 3 eps_hat / (tau_h den) and q / 8
     constexpr bool kFact = std::is_same<R, float>::value;
-    R* se = hs + 9 * PB_CELLS;                      // eps (Kc)
-    R* sq = se + PB_CELLS;                          // q (q / 8)
+    R* se = hs + 9 * CELLS;  // eps (Kc)
+    R* sq = se + CELLS;      // q (q / 8)
     const int nx = P.nx, ny = P.ny;
     const unsigned N = P.N;
-    const int x0 = bx * PB_TX - PB_HALO, y0 = by * PB_TY - PB_HALO;
+    const int x0 = bx * PB_TX - H, y0 = by * PB_TY - H;
     const int tid = threadIdx.x;
     const bool walls = P.bc_y != 0;
 
-    // per owned cell, fixed over the iterations: region index, ring distance
-    // (-1: not a fluid cell), wall contact (bit 0 bottom row, bit 1 top row), tile
-    // membership, and the global cell index (tile cells only)
-    R h[PB_CPT][9];
-    int kk[PB_CPT], ring[PB_CPT], wall[PB_CPT];
-    unsigned gc[PB_CPT];
-    bool tile[PB_CPT];
+    // per owned cell k = tid + m * NT, fixed over the iterations, packed in one word:
+    // bits 0-7 the distance d outside the tile (0 inside; 255: not a fluid cell),
+    // bit 8 bottom wall row, bit 9 top wall row, bit 10 a tile cell inside the grid
+    R h[CPT][9];
+    int meta[CPT];
 #pragma unroll
-    for (int m = 0; m < PB_CPT; ++m) {
-        const int k = tid + m * PB_THREADS;
-        kk[m] = k;
-        const int ly = k / PB_RX, lx = k % PB_RX;
+    for (int m = 0; m < CPT; ++m) {
+        const int k = tid + m * NT;
+        const int ly = k / RX, lx = k % RX;
         const int gy = y0 + ly, gx = x0 + lx;
-        const bool real = k < PB_CELLS && (!walls || (gy >= 0 && gy < ny));
-        ring[m] = real ? ring_dist(ly, lx) : -1;
-        wall[m] = walls ? ((gy == 0 ? 1 : 0) | (gy == ny - 1 ? 2 : 0)) : 0;
-        tile[m] = real && ring[m] >= PB_HALO && gx < nx && gy < ny;
-        gc[m] = tile[m] ? (unsigned)gy * nx + gx : 0u;
+        const bool real = !walls || (gy >= 0 && gy < ny);
+        const int dx = lx < H ? H - lx : (lx >= H + PB_TX ? lx - (H + PB_TX - 1) : 0);
+        const int dy = ly < H ? H - ly : (ly >= H + PB_TY ? ly - (H + PB_TY - 1) : 0);
+        const int d = dx > dy ? dx : dy;
+        meta[m] = (real ? d : 255) | (walls && gy == 0 ? 256 : 0) | (walls && gy == ny - 1 ? 512 : 0) |
+                  (real && d == 0 && gx < nx && gy < ny ? 1024 : 0);
         if (real) {
             const unsigned c = (unsigned)wrapi(gy, ny) * nx + wrapi(gx, nx);
 #pragma unroll
@@ -489,44 +526,51 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
         } else {
 #pragma unroll
             for (int j = 0; j < 9; ++j) h[m][j] = R(0);
-            if (k < PB_CELLS) { se[k] = kFact ? R(0) : pv<R>(P.eps_ref, P.feps_ref); sq[k] = R(0); }
+            se[k] = kFact ? R(0) : pv<R>(P.eps_ref, P.feps_ref);
+            sq[k] = R(0);
         }
     }
     __syncthreads();
 
+    // the global index of an owned tile cell
+    auto cell = [&](int m) {
+        const int k = tid + m * NT;
+        return (unsigned)(y0 + k / RX) * nx + (unsigned)(x0 + k % RX);
+    };
     const R th = pv<R>(P.tau_h, P.ftau_h), ith = kconst<R>(P.fitau_h, [&] { return rcp(th); });
     const R vb = prm<R>(P.V_bottom, P.t_Vb, P.fVb), vt = prm<R>(P.V_top, P.t_Vt, P.fVt);
     const R eref = pv<R>(P.eps_ref, P.feps_ref);
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const bool electrodes = P.bc_y == 2;
+    // residual sums: a thread's own cells (three at most) in R, the block and grid
+    // sums in FP64
+    R acc[4] = {R(0), R(0), R(0), R(0)};
     for (int t = 0; t < K; ++t) {
 #pragma unroll
-        for (int m = 0; m < PB_CPT; ++m) {
-            // cells closer than t to the region border can no longer feed the tile
-            if (ring[m] < t) continue;
-            const int k = kk[m];
+        for (int m = 0; m < CPT; ++m) {
+            if ((meta[m] & 255) > K - t) continue;  // no longer feeds the tile (or not a fluid cell)
+            const int k = tid + m * NT;
             R ps = R(0), jx = R(0), jy = R(0);
 #pragma unroll
             for (int j = 1; j < 9; ++j) ps += h[m][j];
             ps = dv(ps, R(1) - wgt<R>(0), R(1.8));
 #pragma unroll
             for (int j = 0; j < 9; ++j) { cacc(jx, cx(j), h[m][j]); cacc(jy, cy(j), h[m][j]); }
-            if (tile[m] && (check && t == 0 || save_prev && t == K - 1)) {
-                const unsigned c = gc[m];
+            if ((meta[m] & 1024) && (check && t == 0 || save_prev && t == K - 1)) {
+                const unsigned c = cell(m);
                 if (check && t == 0) {
-                    const double d = (double)ps - (double)prev[c];
-                    const double ex = (double)jx - (double)prev[N + c], ey = (double)jy - (double)prev[2 * N + c];
+                    const R d = ps - prev[c], ex = jx - prev[N + c], ey = jy - prev[2 * N + c];
                     acc[0] += d * d;
-                    acc[1] += (double)ps * (double)ps;
+                    acc[1] += ps * ps;
                     acc[2] += ex * ex + ey * ey;
-                    acc[3] += (double)jx * (double)jx + (double)jy * (double)jy;
+                    acc[3] += jx * jx + jy * jy;
                 }
                 if (save_prev && t == K - 1) { prev[c] = ps; prev[N + c] = jx; prev[2 * N + c] = jy; }
             }
+            R hc[9];
             if constexpr (kFact) {
                 const R Kc = se[k], q8 = sq[k];
 #pragma unroll
-                for (int j = 0; j < 9; ++j)
-                    hs[j * PB_CELLS + k] = h_collide<R>(j, h[m][j], ps, R(0), R(0), jx, jy, th, ith, R(0), Kc, R(0), q8);
+                for (int j = 0; j < 9; ++j) hc[j] = h_collide<R>(j, h[m][j], ps, R(0), R(0), jx, jy, th, ith, R(0), Kc, R(0), q8);
             } else {
                 const R epshat = se[k] - eref;
                 const R den = epshat + cs2<R>() * th, iden = rcp(den);
@@ -534,46 +578,54 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
                 const R qc = sq[k];
 #pragma unroll
                 for (int j = 0; j < 9; ++j)
-                    hs[j * PB_CELLS + k] = h_collide<R>(j, h[m][j], ps, gx, gy2, jx, jy, th, ith, epshat, R(0), qc, R(0));
+                    hc[j] = h_collide<R>(j, h[m][j], ps, gx, gy2, jx, jy, th, ith, epshat, R(0), qc, R(0));
+            }
+#pragma unroll
+            for (int j = 0; j < 9; ++j) hs[j * CELLS + k] = hc[j];
+            // a wall cell whose own pull is still needed (so it is not on the region
+            // border, and its ghost slots lie inside the region): the populations
+            // leaving toward the wall come back in the opposite direction, through
+            // the ghost cell they would be pulled from (anti-bounce-back to the
+            // electrode potential, or plain bounce-back)
+            if ((meta[m] & 768) && (meta[m] & 255) <= K - 1 - t) {
+#pragma unroll
+                for (int j = 1; j < 9; ++j) {
+                    const bool bottom = cy(j) < 0 && (meta[m] & 256), top = cy(j) > 0 && (meta[m] & 512);
+                    if (!bottom && !top) continue;
+                    const int jo = opp(j);  // arriving direction
+                    const R v = electrodes ? -hc[j] + R(2) * wgt<R>(j) * (top ? vt : vb) : hc[j];
+                    hs[jo * CELLS + k - cy(jo) * RX - cx(jo)] = v;
+                }
             }
         }
         __syncthreads();
         // pull streaming inside the region (cells whose sources were all updated)
 #pragma unroll
-        for (int m = 0; m < PB_CPT; ++m) {
-            if (ring[m] < t + 1) continue;
-            const int k = kk[m];
+        for (int m = 0; m < CPT; ++m) {
+            if ((meta[m] & 255) > K - 1 - t) continue;
+            const int k = tid + m * NT;
 #pragma unroll
-            for (int j = 0; j < 9; ++j) {
-                const int from_wall = cy(j) > 0 ? (wall[m] & 1) : (cy(j) < 0 ? (wall[m] & 2) : 0);
-                if (from_wall) {
-                    // the population that left this cell toward the wall, reflected
-                    const int jo = opp(j);
-                    const R v = hs[jo * PB_CELLS + k];
-                    h[m][j] = P.bc_y == 2 ? -v + R(2) * wgt<R>(jo) * (cy(j) < 0 ? vt : vb) : v;
-                } else {
-                    h[m][j] = hs[j * PB_CELLS + k - cy(j) * PB_RX - cx(j)];
-                }
-            }
+            for (int j = 0; j < 9; ++j) h[m][j] = hs[j * CELLS + k - cy(j) * RX - cx(j)];
         }
         __syncthreads();
     }
     // write the tile
 #pragma unroll
-    for (int m = 0; m < PB_CPT; ++m) {
-        if (!tile[m]) continue;
-        const unsigned c = gc[m];
+    for (int m = 0; m < CPT; ++m) {
+        if (!(meta[m] & 1024)) continue;
+        const unsigned c = cell(m);
 #pragma unroll
         for (int j = 0; j < 9; ++j) hout[j * N + c] = h[m][j];
     }
-    if (check) block_reduce_store<4>(acc, partial + 4 * (size_t)(bx + gdx * by));
+    if (check) block_reduce_store_r<4>(acc, partial + 4 * (size_t)(bx + gdx * by));
 }
-template <class R>
-__global__ void __launch_bounds__(PB_THREADS, pb_min_blocks<R>())
+template <class R, int H>
+__global__ void __launch_bounds__(PBGeom<H>::THREADS, pb_min_blocks<R, H>())
     k_poisson_tb(DevParams P, const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ eps,
                  const R* __restrict__ q, R* __restrict__ prev, double* __restrict__ partial, int K, int save_prev,
                  int check) {
-    body_poisson_tb<R>(P, hin, hout, eps, q, prev, partial, K, save_prev, check, blockIdx.x, blockIdx.y, gridDim.x);
+    body_poisson_tb<R, H>(P, hin, hout, eps, q, prev, partial, K, save_prev, check, blockIdx.x, blockIdx.y,
+                          gridDim.x);
 }
 
 // final reduction of nblk x NV partials in a fixed order (one block of 256 threads)
@@ -1168,81 +1220,99 @@ __global__ void k_pop_to_f64(double* __restrict__ dst, const S* __restrict__ pop
 
 // ---------------------------------------------------------------- observables (FP64 reductions)
 // Per block: mass[3], charge, F_phi, F_E, F_u, F_q, nonfinite, then the indicator
-// moments (sum chi, chi x, chi y, chi x^2, chi y^2) for inner and outer; max
-// deviation is reduced separately (as a sum of nothing: see k_maxdev).
+// moments (sum chi, chi x, chi y, chi x^2, chi y^2) for inner and outer; the max
+// deviation |sum phi - 1| is a separate per-block max.
 constexpr int NOBS = 19;
+// OBS_Y cells per thread along y: a 32 x 8 block covers 32 x 64 cells, so the FP64
+// block reduction of the NOBS sums is shared by eight cells per thread.
+constexpr int OBS_Y = 8;
+inline dim3 obs_grid(int nx, int ny) { return dim3((nx + TX - 1) / TX, (ny + TY * OBS_Y - 1) / (TY * OBS_Y)); }
+// Per-block FP64 sums of the NOBS observables (partial[b * NOBS + k]) and the
+// per-block max |sum phi - 1| (maxpart[b]).  The per-cell terms are evaluated in
+// FP32 in the FP32 builds and in FP64 otherwise (FP64 arithmetic runs at a small
+// fraction of the FP32 rate on this part); every sum and the max are FP64.
 template <class R>
 __global__ void __launch_bounds__(256) k_observables(DevParams P, const R* __restrict__ phi, const R* __restrict__ q,
                                                      const R* __restrict__ E, const R* __restrict__ diag,
-                                                     double* __restrict__ partial) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+                                                     double* __restrict__ partial, double* __restrict__ maxpart) {
+    using T = typename std::conditional<std::is_same<R, float>::value, float, double>::type;
     double v[NOBS];
 #pragma unroll
     for (int k = 0; k < NOBS; ++k) v[k] = 0.0;
-    if (x < P.nx && y < P.ny) {
+    double mdev = 0.0;
+    const int x = blockIdx.x * TX + threadIdx.x;
+    for (int r = 0; r < OBS_Y; ++r) {
+        const int y = blockIdx.y * (TY * OBS_Y) + r * TY + threadIdx.y;
+        if (x >= P.nx || y >= P.ny) continue;
         const unsigned N = P.N, c = (unsigned)y * P.nx + x;
-        const double D = P.D;
-        double ph[3];
+        const T D = pv<T>(P.D, P.fD);
+        T ph[3];
+        T fphi = T(0);
+#pragma unroll
         for (int i = 0; i < 3; ++i) {
             const R* f = phi + i * N;
-            double ax = 0.0, ay = 0.0;
-            for (int j = 0; j < 9; ++j) {
-                const double w = (double)f[(size_t)ghost_row(y + cy(j), P.ny, P.bc_y) * P.nx + wrapi(x + cx(j), P.nx)];
-                ax += wgt<double>(j) * cx(j) * w;
-                ay += wgt<double>(j) * cy(j) * w;
+            T ax = T(0), ay = T(0);
+#pragma unroll
+            for (int j = 1; j < 9; ++j) {
+                const T w = (T)f[(size_t)ghost_row(y + cy(j), P.ny, P.bc_y) * P.nx + wrapi(x + cx(j), P.nx)];
+                cacc(ax, cx(j), wgt<T>(j), w);
+                cacc(ay, cy(j), wgt<T>(j), w);
             }
-            ax = ax / cs2<double>();
-            ay = ay / cs2<double>();
-            ph[i] = (double)f[c];
-            v[i] = ph[i];
-            v[4] += 6.0 / D * P.lam[i] * ph[i] * ph[i] * (1.0 - ph[i]) * (1.0 - ph[i]) + 0.375 * D * P.lam[i] * (ax * ax + ay * ay);
+            ax = oc2(ax);
+            ay = oc2(ay);
+            ph[i] = (T)f[c];
+            v[i] += (double)ph[i];
+            const T lam = pv<T>(P.lam[i], P.flam[i]);
+            fphi += T(6) / D * lam * ph[i] * ph[i] * (T(1) - ph[i]) * (T(1) - ph[i]) +
+                    T(0.375) * D * lam * (ax * ax + ay * ay);
         }
-        double eps = 0.0;
-        for (int i = 0; i < 3; ++i) eps += P.eps[i] * ph[i] * ph[i] * (3.0 - 2.0 * ph[i]);
-        const double Ex = (double)E[c], Ey = (double)E[N + c];
-        v[5] = 0.5 * eps * (Ex * Ex + Ey * Ey);
-        const double rho = ph[0] * P.rho[0] + ph[1] * P.rho[1] + ph[2] * P.rho[2];
-        const double ux = (double)diag[c], uy = (double)diag[N + c];
-        v[6] = 0.5 * rho * (ux * ux + uy * uy);
-        const double sg = ph[0] * P.sigma[0] + ph[1] * P.sigma[1] + ph[2] * P.sigma[2];
-        const double qc = (double)q[c];
-        if (sg > 0) v[7] = 0.5 * (P.alpha / sg) * qc * qc;
-        v[3] = qc;
-        const double vals[6] = {ph[0], ph[1], ph[2], ux, uy, qc};
+        v[4] += (double)fphi;
+        T eps = T(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) eps += pv<T>(P.eps[i], P.feps[i]) * ph[i] * ph[i] * (T(3) - T(2) * ph[i]);
+        const T Ex = (T)E[c], Ey = (T)E[N + c];
+        v[5] += (double)(T(0.5) * eps * (Ex * Ex + Ey * Ey));
+        const T rho = ph[0] * pv<T>(P.rho[0], P.frho[0]) + ph[1] * pv<T>(P.rho[1], P.frho[1]) +
+                      ph[2] * pv<T>(P.rho[2], P.frho[2]);
+        const T ux = (T)diag[c], uy = (T)diag[N + c];
+        v[6] += (double)(T(0.5) * rho * (ux * ux + uy * uy));
+        const T sg = ph[0] * pv<T>(P.sigma[0], P.fsig[0]) + ph[1] * pv<T>(P.sigma[1], P.fsig[1]) +
+                     ph[2] * pv<T>(P.sigma[2], P.fsig[2]);
+        const T qc = (T)q[c];
+        if (sg > T(0)) v[7] += (double)(T(0.5) * (T(P.alpha) / sg) * qc * qc);
+        v[3] += (double)qc;
+        const T vals[6] = {ph[0], ph[1], ph[2], ux, uy, qc};
+#pragma unroll
         for (int k = 0; k < 6; ++k)
             if (!isfinite(vals[k])) v[8] += 1.0;
-        const double chis[2] = {ph[P.inner], 1.0 - ph[P.matrix]};
+        const T chis[2] = {ph[P.inner], T(1) - ph[P.matrix]};
+#pragma unroll
         for (int k = 0; k < 2; ++k) {
-            v[9 + 5 * k] = chis[k];
-            v[10 + 5 * k] = chis[k] * x;
-            v[11 + 5 * k] = chis[k] * y;
-            v[12 + 5 * k] = chis[k] * x * x;
-            v[13 + 5 * k] = chis[k] * y * y;
+            v[9 + 5 * k] += (double)chis[k];
+            v[10 + 5 * k] += (double)(chis[k] * T(x));
+            v[11 + 5 * k] += (double)(chis[k] * T(y));
+            v[12 + 5 * k] += (double)(chis[k] * T(x) * T(x));
+            v[13 + 5 * k] += (double)(chis[k] * T(y) * T(y));
         }
+        mdev = fmax(mdev, fabs((double)ph[0] + (double)ph[1] + (double)ph[2] - 1.0));
     }
-    block_reduce_store<NOBS>(v, partial + (size_t)NOBS * (blockIdx.x + gridDim.x * blockIdx.y));
-}
-
-// max |sum phi - 1| as a per-block max, then a fixed-order max
-template <class R>
-__global__ void __launch_bounds__(256) k_maxdev(DevParams P, const R* __restrict__ phi, double* __restrict__ partial) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    double m = 0.0;
-    if (x < P.nx && y < P.ny) {
-        const unsigned N = P.N, c = (unsigned)y * P.nx + x;
-        m = fabs((double)phi[c] + (double)phi[N + c] + (double)phi[2 * N + c] - 1.0);
-    }
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
-    __shared__ double red[32];
-    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    if ((tid & 31) == 0) red[tid >> 5] = m;
+    const int b = blockIdx.x + gridDim.x * blockIdx.y;
+    block_reduce_store<NOBS>(v, partial + (size_t)NOBS * b);
+    // block max of the sum deviation (the reduction above ends with a barrier-free
+    // warp-0 stage, so this uses its own shared array)
+    for (int o = 16; o > 0; o >>= 1) mdev = fmax(mdev, __shfl_down_sync(0xffffffffu, mdev, o));
+    __shared__ double mred[8];
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    if ((tid & 31) == 0) mred[tid >> 5] = mdev;
     __syncthreads();
     if (tid == 0) {
         double a = 0.0;
-        for (int k = 0; k < (int)((blockDim.x * blockDim.y + 31) >> 5); ++k) a = fmax(a, red[k]);
-        partial[blockIdx.x + gridDim.x * blockIdx.y] = a;
+        for (int k = 0; k < (TX * TY) / 32; ++k) a = fmax(a, mred[k]);
+        maxpart[b] = a;
     }
 }
+
+// fixed-order max of n per-block maxima
 static __global__ void k_max_partials(const double* __restrict__ partial, int n, double* __restrict__ out) {
     double m = 0.0;
     for (int b = threadIdx.x; b < n; b += blockDim.x) m = fmax(m, partial[b]);
@@ -1295,13 +1365,13 @@ __global__ void __launch_bounds__(256) kb_poisson(const InstState<R, S>* __restr
     body_poisson<R>(e.P, e.h[hcur], e.h[hcur ^ 1], e.eps, e.q, nullptr, nullptr, 0, 0, t.y, t.z, 0);
 }
 // K pseudo-iterations per launch over the 32 x 16 tiles of all instances
-template <class R, class S>
-__global__ void __launch_bounds__(PB_THREADS, pb_min_blocks<R>())
+template <class R, class S, int H>
+__global__ void __launch_bounds__(PBGeom<H>::THREADS, pb_min_blocks<R, H>())
     kb_poisson_tb(const InstState<R, S>* __restrict__ st, const int4* __restrict__ tiles, int hcur, int K) {
     const int4 t = tiles[blockIdx.x];
     const InstState<R, S>& e = st[t.x];
     if (!e.P.electric) return;
-    body_poisson_tb<R>(e.P, e.h[hcur], e.h[hcur ^ 1], e.eps, e.q, nullptr, nullptr, K, 0, 0, t.y, t.z, 0);
+    body_poisson_tb<R, H>(e.P, e.h[hcur], e.h[hcur ^ 1], e.eps, e.q, nullptr, nullptr, K, 0, 0, t.y, t.z, 0);
 }
 template <class R, class S>
 __global__ void __launch_bounds__(256) kb_potential_fields(const InstState<R, S>* __restrict__ st,

@@ -23,7 +23,9 @@
 
 namespace lb3e {
 
-// 32 x 8 tiles: 16384 blocks cover up to 4 194 304 cells (2048 x 2048).
+// Blocks of 32 x 8 threads: at most 16384 of them for 4 194 304 cells (2048 x 2048).
+// The observables grid (32 x 64 cells a block) needs about an eighth of that; the
+// size check in the entry point makes sure its NOBS sums and block maxima fit.
 constexpr int kNoallocMaxBlocks = LB3E_NOALLOC_MAX_CELLS / (TX * TY);
 constexpr int kNoallocSlots = kNoallocMaxBlocks * NOBS + 64;
 
@@ -81,23 +83,24 @@ extern "C" int lb3e_observables_noalloc(const lb3e_params* params, const double*
         params->matrix_phase < 1 || params->matrix_phase > 3 || !(params->width_D > 0))
         return LB3E_ERR_PARAM;
     if ((int64_t)params->nx * params->ny > LB3E_NOALLOC_MAX_CELLS) return LB3E_ERR_TOO_LARGE;
-    const dim3 grid((params->nx + TX - 1) / TX, (params->ny + TY - 1) / TY);
-    const int nblk = (int)(grid.x * grid.y);
-    if (nblk > kNoallocMaxBlocks) return LB3E_ERR_TOO_LARGE;
+    const dim3 grid = obs_grid(params->nx, params->ny);
+    const int64_t nblk64 = (int64_t)grid.x * grid.y;
+    // NOBS sums and one max per block must fit before the result slots
+    if (nblk64 * (NOBS + 1) > (int64_t)kNoallocMaxBlocks * NOBS) return LB3E_ERR_TOO_LARGE;
+    const int nblk = (int)nblk64;
 
     double* scratch = nullptr;
     TRY(scratch_for_current_device(&scratch));
-    double* partial = scratch;                           // nblk * NOBS slots, each written by its block
+    double* partial = scratch;  // nblk * NOBS sums, then nblk maxima, each written by its block
     double* result = scratch + (size_t)kNoallocMaxBlocks * NOBS;  // NOBS + 1 slots, written by the final kernels
     const DevParams dp = make_dev_params(*params);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     // Every slot read below is written earlier in this same call, so nothing
     // needs clearing; the array keeps the last call's values afterwards.
-    k_observables<double><<<grid, dim3(TX, TY), 0, st>>>(dp, phi, q, E, u, partial);
+    k_observables<double><<<grid, dim3(TX, TY), 0, st>>>(dp, phi, q, E, u, partial, partial + (size_t)nblk * NOBS);
     k_reduce_partials<NOBS><<<1, 256, 0, st>>>(partial, nblk, result);
-    k_maxdev<double><<<grid, dim3(TX, TY), 0, st>>>(dp, phi, partial);
-    k_max_partials<<<1, 256, 0, st>>>(partial, nblk, result + NOBS);
+    k_max_partials<<<1, 256, 0, st>>>(partial + (size_t)nblk * NOBS, nblk, result + NOBS);
     if (cudaGetLastError() != cudaSuccess) return LB3E_ERR_CUDA;
     double v[NOBS + 1];
     if (cudaMemcpyAsync(v, result, sizeof v, cudaMemcpyDeviceToHost, st) != cudaSuccess) return LB3E_ERR_CUDA;

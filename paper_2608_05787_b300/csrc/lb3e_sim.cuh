@@ -45,7 +45,11 @@ class Sim final : public SimBase {
         L.prev = take(8 * N * sizeof(R));
         L.diag = take(6 * N * sizeof(R));
         L.psi_prev = take(3 * N * sizeof(R));
-        L.partial = take(nblk * NOBS * sizeof(double));
+        // per-block partials: NOBS per 32 x 8 tile, or the observables' NOBS sums
+        // and one max per 32 x 64 block, whichever is larger
+        const dim3 og = obs_grid(p.nx, p.ny);
+        const size_t nobs = (size_t)og.x * og.y * (NOBS + 1);
+        L.partial = take((nblk * NOBS > nobs ? nblk * NOBS : nobs) * sizeof(double));
         L.result = take(64 * sizeof(double));
         // FP64 staging: 9 planes, or room for 4 planes of R after the first plane
         L.stage = take(9 * N * sizeof(double) > N * sizeof(double) + 4 * N * sizeof(R)
@@ -208,16 +212,18 @@ class Sim final : public SimBase {
 
     int observables(lb3e_observables_t* o) override {
         timer.begin(stream_, KC_REDUCE);
-        k_observables<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.phi, d_.q, d_.E, d_.diag, d_.partial);
+        // sums in partial[0, nb * NOBS), block maxima after them (the layout sizes
+        // the partial area for both)
+        const dim3 og = obs_grid(p_.nx, p_.ny);
+        const int nb = (int)(og.x * og.y);
+        k_observables<R><<<og, dim3(TX, TY), 0, stream_>>>(dp_, d_.phi, d_.q, d_.E, d_.diag, d_.partial,
+                                                          d_.partial + (size_t)nb * NOBS);
         TRY(launched());
         timer.begin(stream_, KC_REDUCE);
-        k_reduce_partials<NOBS><<<1, 256, 0, stream_>>>(d_.partial, nblk_, d_.result);
+        k_reduce_partials<NOBS><<<1, 256, 0, stream_>>>(d_.partial, nb, d_.result);
         TRY(launched());
         timer.begin(stream_, KC_REDUCE);
-        k_maxdev<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.phi, d_.partial);
-        TRY(launched());
-        timer.begin(stream_, KC_REDUCE);
-        k_max_partials<<<1, 256, 0, stream_>>>(d_.partial, nblk_, d_.result + NOBS);
+        k_max_partials<<<1, 256, 0, stream_>>>(d_.partial + (size_t)nb * NOBS, nb, d_.result + NOBS);
         TRY(launched());
         if (cudaMemcpyAsync(pinned_, d_.result, (NOBS + 1) * sizeof(double), cudaMemcpyDeviceToHost, stream_) !=
             cudaSuccess)
@@ -495,8 +501,52 @@ class Sim final : public SimBase {
         return launched();
     }
 
+    // blocked-iteration kernels need more than the default dynamic shared memory
+    int pb_prepare() {
+        if constexpr (!is_dual<R>::value) {
+            if (!pb_ready_) {
+                if (cudaFuncSetAttribute(k_poisson_tb<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pb_smem_bytes<R, 2>()) != cudaSuccess ||
+                    cudaFuncSetAttribute(k_poisson_tb<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pb_smem_bytes<R, 4>()) != cudaSuccess ||
+                    cudaFuncSetAttribute(k_poisson_tb<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pb_smem_bytes<R, 8>()) != cudaSuccess)
+                    return LB3E_ERR_CUDA;
+                pb_ready_ = true;
+            }
+        }
+        return LB3E_OK;
+    }
+    // one blocked launch of c iterations, on the region sized for c
+    void pb_launch(dim3 pgrid, int c, int save, int check) {
+        if constexpr (!is_dual<R>::value) {
+            if (pb_halo_for(c) == 2)
+                k_poisson_tb<R, 2><<<pgrid, PBGeom<2>::THREADS, pb_smem_bytes<R, 2>(), stream_>>>(
+                    dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q, d_.psi_prev, d_.partial, c, save, check);
+            else if (pb_halo_for(c) == 4)
+                k_poisson_tb<R, 4><<<pgrid, PBGeom<4>::THREADS, pb_smem_bytes<R, 4>(), stream_>>>(
+                    dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q, d_.psi_prev, d_.partial, c, save, check);
+            else
+                k_poisson_tb<R, 8><<<pgrid, PBGeom<8>::THREADS, pb_smem_bytes<R, 8>(), stream_>>>(
+                    dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q, d_.psi_prev, d_.partial, c, save, check);
+        }
+    }
+
+  public:
+    // pseudo-iterations per potential launch: 1 (one per launch), 2 (blocked,
+    // 2-cell halo), 3..4 (4-cell halo) or 5..8 (8-cell halo)
+    int set_chunk(int k) override {
+        if (k < 1 || k > PB_HALO) return LB3E_ERR_PARAM;
+        if constexpr (is_dual<R>::value) {
+            if (k != 1) return LB3E_ERR_PARAM;
+        }
+        chunk_ = k;
+        return LB3E_OK;
+    }
+
+  private:
     // the pseudo-time potential solve (Eq. 43) from the current h.  Iterations
-    // run in chunks of up to PB_HALO per launch (k_poisson_tb); a chunk never
+    // run in chunks of up to chunk_ per launch (k_poisson_tb); a chunk never
     // straddles a residual check, which is taken before the first collision of a
     // chunk, and the state for the next check is saved before the last one.
     int poisson(double tol, int max_iter, int fixed, int check) {
@@ -505,19 +555,12 @@ class Sim final : public SimBase {
         last_res_ = -1.0;
         last_conv_ = fixed > 0;
         last_iters_ = n;
-        if constexpr (!is_dual<R>::value) {
-            if (!pb_ready_) {
-                if (cudaFuncSetAttribute(k_poisson_tb<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)pb_smem_bytes<R>()) != cudaSuccess)
-                    return LB3E_ERR_CUDA;
-                pb_ready_ = true;
-            }
-        }
+        TRY(pb_prepare());
         const dim3 pgrid((p_.nx + PB_TX - 1) / PB_TX, (p_.ny + PB_TY - 1) / PB_TY);
         const int pblk = (int)(pgrid.x * pgrid.y);
         int k = 1;
         while (k <= n) {
-            int c = n - k + 1 < PB_HALO ? n - k + 1 : PB_HALO;
+            int c = n - k + 1 < chunk_ ? n - k + 1 : chunk_;
             if (fixed <= 0) {
                 int next = (k / check + 1) * check;  // next check iteration after k
                 if (next < 2) next = 2;
@@ -529,8 +572,7 @@ class Sim final : public SimBase {
             if constexpr (!is_dual<R>::value) {  // dual tiles would not fit in shared memory
                 if (c >= 2) {
                     timer.begin(stream_, KC_POISSON);
-                    k_poisson_tb<R><<<pgrid, PB_THREADS, pb_smem_bytes<R>(), stream_>>>(
-                        dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q, d_.psi_prev, d_.partial, c, save, do_check);
+                    pb_launch(pgrid, c, save, do_check);
                     TRY(launched());
                     poisson_iters_run_ += c;
                     blocked = true;
@@ -584,6 +626,7 @@ class Sim final : public SimBase {
     double last_res_ = -1.0;
     double* pinned_ = nullptr;
     bool pb_ready_ = false;
+    int chunk_ = 4;  // pseudo-iterations per potential launch (4: fastest measured on a 4096^2 lattice)
     std::vector<MGLevel> mg_;
 
   public:
@@ -735,14 +778,19 @@ class Batch final : public BatchBase {
         return l;
     }
 
-    // pseudo-iterations per potential launch (1: one iteration per launch; up to
-    // PB_HALO: temporally blocked); chosen by the caller's autotuner
+    // pseudo-iterations per potential launch (1: one iteration per launch; 2
+    // blocked on a 2-cell halo, 3..4 on a 4-cell halo, 5..8 on an 8-cell halo);
+    // chosen by the caller's autotuner
     int set_chunk(int k) override {
         if (k < 1 || k > PB_HALO) return LB3E_ERR_PARAM;
         if constexpr (is_dual<R>::value) return k == 1 ? LB3E_OK : LB3E_ERR_PARAM;
         if (k > 1 && !pb_ready_) {
-            if (cudaFuncSetAttribute(kb_poisson_tb<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)pb_smem_bytes<R>()) != cudaSuccess)
+            if (cudaFuncSetAttribute(kb_poisson_tb<R, S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pb_smem_bytes<R, 2>()) != cudaSuccess ||
+                cudaFuncSetAttribute(kb_poisson_tb<R, S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pb_smem_bytes<R, 4>()) != cudaSuccess ||
+                cudaFuncSetAttribute(kb_poisson_tb<R, S, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pb_smem_bytes<R, 8>()) != cudaSuccess)
                 return LB3E_ERR_CUDA;
             pb_ready_ = true;
         }
@@ -767,7 +815,15 @@ class Batch final : public BatchBase {
         } else {
             for (int k = 0; k < iters_; k += chunk_, h ^= 1) {
                 const int c = iters_ - k < chunk_ ? iters_ - k : chunk_;
-                kb_poisson_tb<R, S><<<nptiles_, PB_THREADS, pb_smem_bytes<R>(), stream_>>>(table_, ptiles_, h, c);
+                if (pb_halo_for(c) == 2)
+                    kb_poisson_tb<R, S, 2><<<nptiles_, PBGeom<2>::THREADS, pb_smem_bytes<R, 2>(), stream_>>>(
+                        table_, ptiles_, h, c);
+                else if (pb_halo_for(c) == 4)
+                    kb_poisson_tb<R, S, 4><<<nptiles_, PBGeom<4>::THREADS, pb_smem_bytes<R, 4>(), stream_>>>(
+                        table_, ptiles_, h, c);
+                else
+                    kb_poisson_tb<R, S, 8><<<nptiles_, PBGeom<8>::THREADS, pb_smem_bytes<R, 8>(), stream_>>>(
+                        table_, ptiles_, h, c);
             }
         }
         if (iters_ > 0) kb_potential_fields<R, S><<<ntiles_, blk, 0, stream_>>>(table_, tiles_, h);

@@ -58,7 +58,7 @@ def test_struct_layouts_match_the_header(tmp_path):
 
 @pytest.mark.parametrize("bad", [dict(tau_f=0.5), dict(nx=1), dict(bc_y=3), dict(precision=7),
                                  dict(gamma23=3e-3), dict(eps=(1.0, 0.0, 2.0)), dict(sigma=(-1, 0, 0)),
-                                 dict(inner_phase=0), dict(V_top=float("nan"))])
+                                 dict(inner_phase=0), dict(V_top=float("nan")), dict(nx=2, ny=65535 * 8 + 1)])
 def test_invalid_parameters_rejected(bad):
     with pytest.raises(L.LB3EError) as e:
         L.workspace_bytes(W.params(**bad))

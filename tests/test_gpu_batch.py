@@ -61,7 +61,7 @@ def test_batch_fp64_matches_oracle():
             assert err <= 1e-12, (i, f, err)
 
 
-@pytest.mark.parametrize("chunk", [2, 3, 8])
+@pytest.mark.parametrize("chunk", [2, 3, 4, 5, 8])
 def test_blocked_potential_chunks_give_the_same_state(chunk):
     """Temporal blocking depth changes the launches, not the result: FP64 batches
     with 1 and `chunk` iterations per launch agree bitwise."""
