@@ -480,6 +480,13 @@ def run_adjoint(args):
             e1.record(stream)
             torch.cuda.synchronize()
             res[name] = e0.elapsed_time(e1) / args.steps
+            # per-kernel-class breakdown from a separate event-timed pass
+            sim.set_timing(True)
+            sim.step(args.steps)
+            kt = sim.kernel_times()
+            sim.set_timing(False)
+            res[name + "_kernels"] = {k: {"launches": n, "ms_per_step": ms / args.steps}
+                                      for k, (ms, n) in kt.items() if n}
             sim.close()
     N = p["nx"] * p["ny"]
     line = {"metric": "derivative/forward time per step", "value": res["tangent3"] / res["forward"],
@@ -488,6 +495,7 @@ def run_adjoint(args):
             "dtype": "f32 (dual numbers, 3 directions)", "data": "synthetic (stated initial condition)",
             "config": {"workload": "compound drop under field + shear, 256x256", "potential_iters_per_step": 16,
                        "forward_ms_per_step": res["forward"], "forward_mlups": N / res["forward"] / 1e3,
+                       "forward_kernels": res["forward_kernels"], "tangent_kernels": res["tangent3_kernels"],
                        "derivatives": ["dD/dE0", "dD/d(eps3/eps1)", "dD/dgamma23"], "mode": "tangent (forward)"}}
     print(json.dumps(line), flush=True)
 

@@ -467,7 +467,7 @@ struct PBGeom {
 // blocks per SM the register budget is sized for (64 registers a thread in FP32)
 template <class R, int H>
 __host__ __device__ constexpr int pb_min_blocks() {
-    return std::is_same<R, float>::value ? (H == 8 ? 2 : (H == 4 ? 3 : 4)) : 1;
+    return std::is_same<R, float>::value ? (H == 8 ? 2 : 3) : 1;
 }
 template <class R, int H>
 constexpr size_t pb_smem_bytes() { return (size_t)11 * PBGeom<H>::CELLS * sizeof(R); }
