@@ -88,6 +88,20 @@ __device__ __forceinline__ void cacc(R& acc, int c, R v) {
 // their rounding does not depend on how the compiler contracts one kernel or
 // another (a batched and a single-lattice kernel then give the same bits).
 __device__ __forceinline__ float fmaf_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// the same for FP32 dual numbers: (a b + c)' = a' b + a b' + c', each part rounded once
+template <int M>
+__device__ __forceinline__ Dual<float, M> fmaf_(const Dual<float, M>& a, const Dual<float, M>& b,
+                                                const Dual<float, M>& c) {
+    Dual<float, M> r;
+    r.v = __fmaf_rn(a.v, b.v, c.v);
+#pragma unroll
+    for (int k = 0; k < M; ++k) r.d[k] = __fmaf_rn(a.v, b.d[k], __fmaf_rn(a.d[k], b.v, c.d[k]));
+    return r;
+}
+// FP32 arithmetic, plain or with FP32 tangents: the builds that take the factored
+// collision forms (the FP64 builds evaluate the paper's equations as written)
+template <class R> struct f32_family { static constexpr bool value = std::is_same<R, float>::value; };
+template <int M> struct f32_family<Dual<float, M>> { static constexpr bool value = true; };
 // acc += c * w * v for a lattice component c in {-1, 0, 1} (one FMA, or nothing)
 template <class R>
 __device__ __forceinline__ void cacc(R& acc, int c, R w, R v) {
@@ -97,9 +111,12 @@ __device__ __forceinline__ void cacc(R& acc, int c, R w, R v) {
 
 template <class R>
 __host__ __device__ constexpr bool exact_arith() { return std::is_same<R, double>::value; }
-// blocks per SM the register budget is sized for
+// blocks per SM the register budget is sized for: FP32 80 registers a thread, FP32
+// duals 128 (at 255 they held one block, 8 warps, per SM), FP64 unconstrained
 template <class R>
-__host__ __device__ constexpr int fused_min_blocks() { return std::is_same<R, float>::value ? 3 : 1; }
+__host__ __device__ constexpr int fused_min_blocks() {
+    return std::is_same<R, float>::value ? 3 : (f32_family<R>::value ? 2 : 1);
+}
 
 // A parameter as an R: the FP32 build reads its single-precision copy.
 template <class R>
@@ -362,14 +379,14 @@ __global__ void __launch_bounds__(256) k_prologue(DevParams P, const R* __restri
 // Post-collision h_j of one cell (Eq. 43) with heq_0 = (w_0 - 1) psi, heq_j = w_j psi,
 // source varpi_j q (varpi_0 = 0, varpi_j = 1/8) and grad psi = -J / den,
 // den = eps_hat + cs2 tau_h.  The FP64 and dual builds evaluate Eq. 43 as written;
-// the FP32 build uses the equal factored form
+// the FP32 builds (plain and dual) use the equal factored form
 //   h_j* = (1 - 1/tau_h) h_j + w_j (psi/tau_h + Kc c_j.J) + q/8,
 //   h_0* = (1 - 1/tau_h) h_0 + (w_0 - 1) psi/tau_h,   Kc = 3 eps_hat / (tau_h den),
 // which takes a third of the instructions.
 template <class R>
 __device__ __forceinline__ R h_collide(int j, R hj, R ps, R gx, R gy, R jx, R jy, R th, R ith, R epshat, R Kc, R qc,
                                        R q8) {
-    if constexpr (std::is_same<R, float>::value) {
+    if constexpr (f32_family<R>::value) {
         const R A = ith * ps, om = R(1) - ith;
         if (j == 0) return fmaf_(om, hj, (wgt<R>(0) - R(1)) * A);
         return fmaf_(om, hj, fmaf_(wgt<R>(j), fmaf_(Kc, cdot<R>(j, jx, jy), A), q8));
@@ -777,9 +794,9 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     // rho, eps, sigma of the 1-ring cells (formed once per tile; dual types, whose
     // tiles would exceed the static shared-memory limit, evaluate them per stencil)
     constexpr bool kProps = !is_dual<R>::value;
-    // FP32 collisions in factored form (same expressions up to rounding, fewer
-    // instructions); the FP64 and dual builds evaluate Eq. 34-50 as written
-    constexpr bool kFact = std::is_same<R, float>::value;
+    // FP32 collisions (plain and dual) in factored form (same expressions up to
+    // rounding, fewer instructions); the FP64 builds evaluate Eq. 34-50 as written
+    constexpr bool kFact = f32_family<R>::value;
     __shared__ R sprop[kProps ? 3 : 1][kProps ? MY * MX : 1];
     const int nx = P.nx, ny = P.ny;
     const unsigned N = P.N;
@@ -1036,6 +1053,8 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
             // f_j* = (1 - 1/tau_f) f_j + w_j (mu/tau_f + c_j.Q), Q = 3 phi u / tau_f + pf A
             const R om = R(1) - itf, b = itf * mui, c3 = R(3) * itf;
             const R Qx = fmaf_(pf, Ax, c3 * (ph[i] * ux)), Qy = fmaf_(pf, Ay, c3 * (ph[i] * uy));
+            if constexpr (!anchored<S>())  // plain rest population: f_0^eq = phi - (1 - w_0) mu, F_0 = 0
+                push(i + 1, 0, fmaf_(om, fv[0], itf * (ph[i] - (R(1) - wgt<R>(0)) * mui)));
 #pragma unroll
             for (int j = 1; j < 9; ++j) push(i + 1, j, fmaf_(om, fv[j], wgt<R>(j) * (b + cdot<R>(j, Qx, Qy))));
         } else {
