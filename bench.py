@@ -37,10 +37,12 @@ METRIC = "MLUPS"
 FUSED_BYTES = {0: 8 * 112, 1: 4 * 112, 2: 2 * 90 + 4 * 22}   # k_fused: 45 pops r+w, phi, q, E, d/dt state
 POISSON_BYTES = {0: 8 * 20, 1: 4 * 20, 2: 4 * 20}           # one pseudo-iteration: h 9 r + 9 w, eps, q
 STEP_BYTES = {0: 960, 1: 480, 2: 300}                        # whole step without the potential loop
-# multigrid V-cycle, FP64, per fine cell: 4 red-black sweeps over psi, eps, rhs
-# (4 x 32 B), the fine residual (40 B) and the prolongation (16 B), times 4/3 for
-# the coarser levels
-MG_VCYCLE_BYTES = 245
+# multigrid cycle per fine cell (defect correction): the FP64 fine residual (psi,
+# rhs, 3 coefficients read, residual written: 48 B), then the FP32 V-cycle on the
+# error equation -- defect load (16 B), 4 red-black sweeps (e r/w, rhs, 3
+# coefficients: 4 x 24 B), residual (24 B), restriction (5 B), prolongation (9 B),
+# FP64 correction (20 B) -- times 4/3 for the coarser levels
+MG_VCYCLE_BYTES = 48 + round(170 * 4 / 3)
 
 
 def parse():

@@ -9,28 +9,39 @@
 // electrodes are supported (bc_y = 2).  The operator is applied unscaled
 // (A psi = sum of face fluxes), so a coarse level, with cells 2x larger, takes
 // the sum of its four children's residuals as right-hand side.  Red-black
-// Gauss-Seidel smoothing, bilinear prolongation, FP64 throughout; the V-cycle is
-// repeated until ||b - A psi|| / ||b|| <= tol on the fine level.  Face
-// coefficients and inverse diagonals are formed once per solve, so the sweeps are
-// multiply-adds only (FP64 division is expensive on this part).
+// Gauss-Seidel smoothing, bilinear prolongation.
+//
+// Precision: defect correction.  The fine-level potential, right-hand side and
+// coefficients are FP64, and so is each residual r = b - A psi (formed in FP64,
+// its norm summed in FP64 across warps).  The V-cycle then solves A e = r in FP32
+// on a parallel FP32 hierarchy, and psi += e in FP64.  Each cycle cuts the FP64
+// residual by the V-cycle's factor as long as that factor is well above FP32
+// rounding, so the loop reaches FP64-level tolerances; the V-cycle itself runs on
+// the FP32 pipe (FP64 runs at a small fraction of its rate on this part) and moves
+// half the bytes.  Repeated until ||b - A psi|| / ||b|| <= tol.  Face coefficients
+// and inverse diagonals are formed once per solve (FP64, then rounded to FP32), so
+// the sweeps are multiply-adds only.
 #pragma once
 
 #include "lb3e_kernels.cuh"
 
 namespace lb3e {
 
-struct MGLevel {
+template <class T>
+struct MGLevelT {
     int nx, ny;
-    double *psi, *rhs, *res, *eps;
-    double *ae, *an, *dg, *idg;  // east / north face coefficients, diagonal and its inverse
+    T *psi, *rhs, *res, *eps;  // eps: FP64 levels only
+    T *ae, *an, *dg, *idg;     // east / north face coefficients, diagonal and its inverse
 };
+using MGLevel = MGLevelT<double>;   // the equation itself (coefficients on every level)
+using MGLevelF = MGLevelT<float>;   // the FP32 error equation of the V-cycle
 
 __device__ __forceinline__ double mg_hmean(double a, double b) { return 2.0 * a * b / (a + b); }
 
 // Face coefficients of level L (harmonic means; no face across an electrode wall,
-// which instead adds 2 eps_C to the diagonal).  The only FP64 divisions of a solve
-// happen here, once per level.
-static __global__ void __launch_bounds__(256) k_mg_coeffs(MGLevel L) {
+// which instead adds 2 eps_C to the diagonal), and their FP32 copies in F.  The only
+// FP64 divisions of a solve happen here, once per level.
+static __global__ void __launch_bounds__(256) k_mg_coeffs(MGLevel L, MGLevelF F) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= L.nx || y >= L.ny) return;
     const int c = y * L.nx + x;
@@ -45,47 +56,73 @@ static __global__ void __launch_bounds__(256) k_mg_coeffs(MGLevel L) {
     L.an[c] = an;
     L.dg[c] = d;
     L.idg[c] = 1.0 / d;
+    F.ae[c] = (float)ae;
+    F.an[c] = (float)an;
+    F.dg[c] = (float)d;
+    F.idg[c] = (float)(1.0 / d);
 }
 
 // sum_{faces} a_f psi_neighbour at cell (x, y)
-__device__ __forceinline__ double mg_offdiag(const MGLevel& L, int x, int y, int c) {
+template <class T>
+__device__ __forceinline__ T mg_offdiag(const MGLevelT<T>& L, int x, int y, int c) {
     const int xe = x + 1 == L.nx ? 0 : x + 1, xw = x == 0 ? L.nx - 1 : x - 1;
-    double off = L.ae[c] * L.psi[y * L.nx + xe] + L.ae[y * L.nx + xw] * L.psi[y * L.nx + xw];
+    T off = L.ae[c] * L.psi[y * L.nx + xe] + L.ae[y * L.nx + xw] * L.psi[y * L.nx + xw];
     if (y + 1 < L.ny) off += L.an[c] * L.psi[c + L.nx];
     if (y > 0) off += L.an[c - L.nx] * L.psi[c - L.nx];
     return off;
 }
 
 // one colour of red-black Gauss-Seidel on level L
-static __global__ void __launch_bounds__(256) k_mg_smooth(MGLevel L, int color) {
+template <class T>
+__global__ void __launch_bounds__(256) k_mg_smooth(MGLevelT<T> L, int color) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= L.nx || y >= L.ny || ((x + y) & 1) != color) return;
     const int c = y * L.nx + x;
     L.psi[c] = (L.rhs[c] + mg_offdiag(L, x, y, c)) * L.idg[c];
 }
 
-// res = rhs - A psi; optionally FP64 partial sums of res^2 and rhs^2 per block
-static __global__ void __launch_bounds__(256) k_mg_residual(MGLevel L, double* __restrict__ partial) {
+// res = rhs - A psi (in the level's precision); optionally per-block sums of res^2
+// and rhs^2 (squares in FP32, summed in FP32 within a warp and in FP64 across
+// warps: a norm needs a few digits, the residual itself is formed in full)
+template <class T>
+__global__ void __launch_bounds__(256) k_mg_residual(MGLevelT<T> L, double* __restrict__ partial) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    double acc[2] = {0.0, 0.0};
+    float acc[2] = {0.f, 0.f};
     if (x < L.nx && y < L.ny) {
         const int c = y * L.nx + x;
-        const double b = L.rhs[c];
-        const double r = b - (L.dg[c] * L.psi[c] - mg_offdiag(L, x, y, c));
+        const T b = L.rhs[c];
+        const T r = b - (L.dg[c] * L.psi[c] - mg_offdiag(L, x, y, c));
         L.res[c] = r;
-        acc[0] = r * r;
-        acc[1] = b * b;
+        acc[0] = (float)r * (float)r;
+        acc[1] = (float)b * (float)b;
     }
-    if (partial) block_reduce_store<2>(acc, partial + 2 * (size_t)(blockIdx.x + gridDim.x * blockIdx.y));
+    if (partial) block_reduce_store_r<2>(acc, partial + 2 * (size_t)(blockIdx.x + gridDim.x * blockIdx.y));
+}
+
+// start of a V-cycle on the error equation: F.rhs = the fine FP64 residual, F.psi = 0
+static __global__ void __launch_bounds__(256) k_mg_defect(MGLevel D, MGLevelF F) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= D.nx || y >= D.ny) return;
+    const int c = y * D.nx + x;
+    F.rhs[c] = (float)D.res[c];
+    F.psi[c] = 0.f;
+}
+// end of a V-cycle: psi += e (FP64)
+static __global__ void __launch_bounds__(256) k_mg_correct(MGLevel D, MGLevelF F) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= D.nx || y >= D.ny) return;
+    const int c = y * D.nx + x;
+    D.psi[c] += (double)F.psi[c];
 }
 
 // coarse right-hand side = sum of the four children's residuals; coarse guess 0
-static __global__ void __launch_bounds__(256) k_mg_restrict(MGLevel F, MGLevel C) {
+template <class T>
+__global__ void __launch_bounds__(256) k_mg_restrict(MGLevelT<T> F, MGLevelT<T> C) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= C.nx || y >= C.ny) return;
     const int f = 2 * y * F.nx + 2 * x;
     C.rhs[y * C.nx + x] = F.res[f] + F.res[f + 1] + F.res[f + F.nx] + F.res[f + F.nx + 1];
-    C.psi[y * C.nx + x] = 0.0;
+    C.psi[y * C.nx + x] = T(0);
 }
 
 // coarse permittivity = mean of the four children (re-discretised coarse operator)
@@ -98,24 +135,27 @@ static __global__ void __launch_bounds__(256) k_mg_coarsen_eps(MGLevel F, MGLeve
 
 // psi_fine += bilinear interpolation of the coarse correction (x periodic; the
 // coarse error vanishes on the electrode faces, so its ghost is -value)
-__device__ __forceinline__ double mg_coarse_at(const MGLevel& C, int x, int y) {
+template <class T>
+__device__ __forceinline__ T mg_coarse_at(const MGLevelT<T>& C, int x, int y) {
     x = x < 0 ? x + C.nx : (x >= C.nx ? x - C.nx : x);
     if (y < 0) return -C.psi[x];
     if (y >= C.ny) return -C.psi[(C.ny - 1) * C.nx + x];
     return C.psi[y * C.nx + x];
 }
-static __global__ void __launch_bounds__(256) k_mg_prolong(MGLevel F, MGLevel C) {
+template <class T>
+__global__ void __launch_bounds__(256) k_mg_prolong(MGLevelT<T> F, MGLevelT<T> C) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= F.nx || y >= F.ny) return;
     const int cx0 = x >> 1, cy0 = y >> 1;
     const int sx = (x & 1) ? 1 : -1, sy = (y & 1) ? 1 : -1;
-    const double v = 0.5625 * mg_coarse_at(C, cx0, cy0) + 0.1875 * mg_coarse_at(C, cx0 + sx, cy0) +
-                     0.1875 * mg_coarse_at(C, cx0, cy0 + sy) + 0.0625 * mg_coarse_at(C, cx0 + sx, cy0 + sy);
+    const T v = T(0.5625) * mg_coarse_at(C, cx0, cy0) + T(0.1875) * mg_coarse_at(C, cx0 + sx, cy0) +
+                T(0.1875) * mg_coarse_at(C, cx0, cy0 + sy) + T(0.0625) * mg_coarse_at(C, cx0 + sx, cy0 + sy);
     F.psi[y * F.nx + x] += v;
 }
 
 // the coarsest level, solved by many red-black sweeps inside one block
-static __global__ void __launch_bounds__(256) k_mg_coarse_solve(MGLevel L, int sweeps) {
+template <class T>
+__global__ void __launch_bounds__(256) k_mg_coarse_solve(MGLevelT<T> L, int sweeps) {
     const int n = L.nx * L.ny;
     for (int s = 0; s < sweeps; ++s)
         for (int color = 0; color < 2; ++color) {

@@ -55,11 +55,15 @@ class Sim final : public SimBase {
         L.stage = take(9 * N * sizeof(double) > N * sizeof(double) + 4 * N * sizeof(R)
                            ? 9 * N * sizeof(double)
                            : N * sizeof(double) + 4 * N * sizeof(R));
-        // multigrid levels (finite-difference potential only): psi, rhs, res, eps
+        // multigrid levels (finite-difference potential only): FP64 psi, rhs, res, eps
+        // and coefficients; FP32 error-equation psi, rhs, res and coefficients
         size_t mg = 0;
         if (p.potential_solver == 1 && p.electric) {
             const int nl = mg_levels(p.nx, p.ny);
-            for (int l = 0; l < nl; ++l) mg += 8 * align256((size_t)(p.nx >> l) * (p.ny >> l) * sizeof(double));
+            for (int l = 0; l < nl; ++l) {
+                const size_t n = (size_t)(p.nx >> l) * (p.ny >> l);
+                mg += 8 * align256(n * sizeof(double)) + 7 * align256(n * sizeof(float));
+            }
         }
         L.mg = take(mg);
         L.total = o;
@@ -107,6 +111,20 @@ class Sim final : public SimBase {
                 v.idg = reinterpret_cast<double*>(m + 7 * sz);
                 m += 8 * sz;
                 mg_.push_back(v);
+                MGLevelF f;
+                f.nx = v.nx;
+                f.ny = v.ny;
+                const size_t fz = align256((size_t)v.nx * v.ny * sizeof(float));
+                f.psi = reinterpret_cast<float*>(m);
+                f.rhs = reinterpret_cast<float*>(m + fz);
+                f.res = reinterpret_cast<float*>(m + 2 * fz);
+                f.eps = nullptr;
+                f.ae = reinterpret_cast<float*>(m + 3 * fz);
+                f.an = reinterpret_cast<float*>(m + 4 * fz);
+                f.dg = reinterpret_cast<float*>(m + 5 * fz);
+                f.idg = reinterpret_cast<float*>(m + 6 * fz);
+                m += 7 * fz;
+                mgf_.push_back(f);
             }
         }
     }
@@ -446,14 +464,15 @@ class Sim final : public SimBase {
                 TRY(launched());
             }
             timer.begin(stream_, KC_POISSON);
-            k_mg_coeffs<<<mg_grid(l), blk, 0, stream_>>>(mg_[l]);
+            k_mg_coeffs<<<mg_grid(l), blk, 0, stream_>>>(mg_[l], mgf_[l]);
             TRY(launched());
         }
+        // smoothing of the FP32 error equation on level l
         auto smooth = [&](int l, int sweeps) -> int {
             for (int s = 0; s < sweeps; ++s)
                 for (int color = 0; color < 2; ++color) {
                     timer.begin(stream_, KC_POISSON);
-                    k_mg_smooth<<<mg_grid(l), blk, 0, stream_>>>(mg_[l], color);
+                    k_mg_smooth<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], color);
                     TRY(launched());
                 }
             return LB3E_OK;
@@ -463,7 +482,7 @@ class Sim final : public SimBase {
         int cycles = 0;
         for (;;) {
             timer.begin(stream_, KC_REDUCE);
-            k_mg_residual<<<mg_grid(0), blk, 0, stream_>>>(mg_[0], d_.partial);
+            k_mg_residual<double><<<mg_grid(0), blk, 0, stream_>>>(mg_[0], d_.partial);
             TRY(launched());
             TRY(reduce_nv<2>((int)(mg_grid(0).x * mg_grid(0).y)));
             if (cudaMemcpyAsync(pinned_, d_.result, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_) !=
@@ -473,25 +492,32 @@ class Sim final : public SimBase {
             last_res_ = pinned_[1] > 0 ? std::sqrt(pinned_[0] / pinned_[1]) : 0.0;
             if (last_res_ <= tol) { last_conv_ = 1; break; }
             if (cycles >= max_cycles) break;
-            // V-cycle (the fine residual is in mg_[0].res)
+            // V-cycle on the FP32 error equation A e = r (r: the fine residual in
+            // mg_[0].res), then psi += e in FP64
+            timer.begin(stream_, KC_POISSON);
+            k_mg_defect<<<mg_grid(0), blk, 0, stream_>>>(mg_[0], mgf_[0]);
+            TRY(launched());
             for (int l = 0; l + 1 < nl; ++l) {
                 TRY(smooth(l, 2));
                 timer.begin(stream_, KC_POISSON);
-                k_mg_residual<<<mg_grid(l), blk, 0, stream_>>>(mg_[l], nullptr);
+                k_mg_residual<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], nullptr);
                 TRY(launched());
                 timer.begin(stream_, KC_POISSON);
-                k_mg_restrict<<<mg_grid(l + 1), blk, 0, stream_>>>(mg_[l], mg_[l + 1]);
+                k_mg_restrict<float><<<mg_grid(l + 1), blk, 0, stream_>>>(mgf_[l], mgf_[l + 1]);
                 TRY(launched());
             }
             timer.begin(stream_, KC_POISSON);
-            k_mg_coarse_solve<<<1, 256, 0, stream_>>>(mg_[nl - 1], nl == 1 ? 2 : 50);
+            k_mg_coarse_solve<float><<<1, 256, 0, stream_>>>(mgf_[nl - 1], nl == 1 ? 2 : 50);
             TRY(launched());
             for (int l = nl - 2; l >= 0; --l) {
                 timer.begin(stream_, KC_POISSON);
-                k_mg_prolong<<<mg_grid(l), blk, 0, stream_>>>(mg_[l], mg_[l + 1]);
+                k_mg_prolong<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], mgf_[l + 1]);
                 TRY(launched());
                 TRY(smooth(l, 2));
             }
+            timer.begin(stream_, KC_POISSON);
+            k_mg_correct<<<mg_grid(0), blk, 0, stream_>>>(mg_[0], mgf_[0]);
+            TRY(launched());
             ++cycles;
             poisson_iters_run_ += 1;
         }
@@ -628,6 +654,7 @@ class Sim final : public SimBase {
     bool pb_ready_ = false;
     int chunk_ = 4;  // pseudo-iterations per potential launch (4: fastest measured on a 4096^2 lattice)
     std::vector<MGLevel> mg_;
+    std::vector<MGLevelF> mgf_;
 
   public:
     int64_t poisson_iters_run_ = 0;  // pseudo-iterations executed (all solves)
