@@ -757,12 +757,13 @@ constexpr int TX = 32, TY = 8;
 // holding registers.  Used when the storage type is float or double.
 template <class S>
 __host__ __device__ constexpr bool fused_prefetch() {
-    return std::is_same<S, float>::value || std::is_same<S, double>::value;
+    return std::is_same<S, float>::value || std::is_same<S, double>::value || std::is_same<S, __half>::value;
 }
-constexpr int FZ_SLOTS = 54;  // 45 population planes, 8 d/dt planes, q
-template <class S>
+// staging area: 45 population planes in the storage type, then the 8 d/dt planes
+// and the charge in the arithmetic type, TX * TY cells each
+template <class R, class S>
 __host__ __device__ constexpr size_t fused_dyn_smem() {
-    return fused_prefetch<S>() ? (size_t)FZ_SLOTS * TX * TY * sizeof(S) : 0;
+    return fused_prefetch<S>() ? (size_t)45 * TX * TY * sizeof(S) + (size_t)9 * TX * TY * sizeof(R) : 0;
 }
 template <class T>
 __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
@@ -804,41 +805,51 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     const int tid = threadIdx.x + TX * threadIdx.y;
 
     // request the tile's populations, d/dt state and charge first: 16-byte copies
-    // of row segments when rows are 16-byte aligned (nx a multiple of 16/sizeof(S)),
-    // else one element per copy; slot layout [plane][ty * TX + tx]
+    // of row segments when rows are 16-byte aligned (nx a multiple of 16/sizeof for
+    // both types), else one element per copy (4- or 8-byte types) or, for 2-byte
+    // storage, plain loads later; slot layout [plane][ty * TX + tx]
+    constexpr bool kStage = fused_prefetch<S>();
     extern __shared__ __align__(16) unsigned char fz_raw[];
-    S* sp = reinterpret_cast<S*>(fz_raw);  // [FZ_SLOTS][TX * TY]
-    if constexpr (fused_prefetch<S>()) {
-        static_assert(std::is_same<R, S>::value, "prefetch stores R-typed d/dt state and charge in S slots");
-        auto plane = [&](int k) -> const S* {
-            return k < 45 ? pin + (size_t)k * N : (k < 53 ? prev + (size_t)(k - 45) * N : qf);
-        };
-        constexpr int V = 16 / (int)sizeof(S);      // cells per 16-byte segment
-        constexpr int SEG = TX / V;                  // segments per tile row
-        if (nx % V == 0) {
-            for (int t = tid; t < FZ_SLOTS * TY * SEG; t += TX * TY) {
-                const int k = t / (TY * SEG), r = (t / SEG) % TY, m = t % SEG;
+    S* sp = reinterpret_cast<S*>(fz_raw);                                      // [45][TX * TY]
+    R* sr = reinterpret_cast<R*>(fz_raw + (size_t)45 * TX * TY * sizeof(S));  // [9][TX * TY]
+    bool staged = false;  // the same for the whole block (depends on nx only)
+    if constexpr (kStage) {
+        constexpr int VS = 16 / (int)sizeof(S), VR = 16 / (int)sizeof(R);  // cells per 16-byte segment
+        constexpr int SGS = TX / VS, SGR = TX / VR;                        // segments per tile row
+        auto rplane = [&](int k) -> const R* { return k < 8 ? prev + (size_t)k * N : qf; };
+        if (nx % (VS > VR ? VS : VR) == 0) {
+            staged = true;
+            for (int t = tid; t < 45 * TY * SGS; t += TX * TY) {
+                const int k = t / (TY * SGS), r = (t / SGS) % TY, m = t % SGS;
                 if (anchored<S>() && (k == 9 || k == 18 || k == 27)) continue;  // rest populations rebuilt
-                const int ys = y0 + r, xs = x0 + m * V;
-                if (ys >= ny || xs >= nx) continue;   // nx % V == 0: a segment is all in or all out
-                cp_async16(sp + k * (TX * TY) + r * TX + m * V, plane(k) + (unsigned)ys * nx + xs);
+                const int ys = y0 + r, xs = x0 + m * VS;
+                if (ys >= ny || xs >= nx) continue;  // nx % VS == 0: a segment is all in or all out
+                cp_async16(sp + k * (TX * TY) + r * TX + m * VS, pin + (size_t)k * N + (unsigned)ys * nx + xs);
             }
-        } else {
+            for (int t = tid; t < 9 * TY * SGR; t += TX * TY) {
+                const int k = t / (TY * SGR), r = (t / SGR) % TY, m = t % SGR;
+                const int ys = y0 + r, xs = x0 + m * VR;
+                if (ys >= ny || xs >= nx) continue;
+                cp_async16(sr + k * (TX * TY) + r * TX + m * VR, rplane(k) + (unsigned)ys * nx + xs);
+            }
+        } else if constexpr (sizeof(S) >= 4) {
+            staged = true;
             const int xs = x0 + threadIdx.x, ys = y0 + threadIdx.y;
             if (xs < nx && ys < ny) {
                 const unsigned cs = (unsigned)ys * nx + xs;
-                for (int k = 0; k < FZ_SLOTS; ++k) {
+                for (int k = 0; k < 45; ++k) {
                     if (anchored<S>() && (k == 9 || k == 18 || k == 27)) continue;
-                    cp_async(sp + k * (TX * TY) + tid, plane(k) + cs);
+                    cp_async(sp + k * (TX * TY) + tid, pin + (size_t)k * N + cs);
                 }
+                for (int k = 0; k < 9; ++k) cp_async(sr + k * (TX * TY) + tid, rplane(k) + cs);
             }
         }
         cp_async_commit();
     }
-    // population k (plane k of the set-major layout), d/dt plane k, charge of this cell
+    // population k (plane k of the set-major layout) of this cell
     auto popk = [&](int k, unsigned cc) -> R {
-        if constexpr (fused_prefetch<S>()) return (R)sp[k * (TX * TY) + tid];
-        else return Store<S>::ld(pin, k * N + cc);
+        if (kStage && staged) return (R)sp[k * (TX * TY) + tid];
+        return Store<S>::ld(pin, k * N + cc);
     };
 
     for (int k = tid; k < PY * PX; k += TX * TY) {
@@ -877,7 +888,7 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
             smu[i][k] = chem_pot<R>(P, i, ph, lap_tile<R>(sphi[i], PX, ly + 1, lx + 1), e2, c24);
         }
     }
-    if constexpr (fused_prefetch<S>()) cp_async_wait_all();  // slots are published by the barrier
+    if constexpr (kStage) cp_async_wait_all();  // slots are published by the barrier
     __syncthreads();
     // ghost rows of mu mirror the in-domain row they face
     if (P.bc_y != 0) {
@@ -945,9 +956,7 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     gsx = oc2(gsx); gsy = oc2(gsy);
 
     const R Ex = sE[0][my * MX + mx], Ey = sE[1][my * MX + mx];
-    R qc;
-    if constexpr (fused_prefetch<S>()) qc = (R)sp[53 * (TX * TY) + tid];
-    else qc = qf[c];
+    const R qc = (kStage && staged) ? sr[8 * (TX * TY) + tid] : qf[c];
     // R of Eq. 47 with q^n and E^n
     const R rr = dv(sg, ep, rcp(ep));
     const R Rc = -rr * qc + rr * (gex * Ex + gey * Ey) - (gsx * Ex + gsy * Ey);
@@ -977,8 +986,8 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
 
     // d/dt terms (first-order backward differences)
     auto prevk = [&](int k) -> R {
-        if constexpr (fused_prefetch<S>()) return (R)sp[(45 + k) * (TX * TY) + tid];
-        else return prev[k * N + c];
+        if (kStage && staged) return sr[k * (TX * TY) + tid];
+        return prev[k * N + c];
     };
     R dpu[3][2], dqu[2];
 #pragma unroll

@@ -133,9 +133,9 @@ class Sim final : public SimBase {
     }
 
     int init(const double* phi, const double* u, const double* q, const double* noise) override {
-        if constexpr (fused_dyn_smem<S>() > 0) {
+        if constexpr (fused_dyn_smem<R, S>() > 0) {
             if (cudaFuncSetAttribute(k_fused<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)fused_dyn_smem<S>()) != cudaSuccess)
+                                     (int)fused_dyn_smem<R, S>()) != cudaSuccess)
                 return LB3E_ERR_CUDA;
         }
         if (cudaHostAlloc(reinterpret_cast<void**>(&pinned_), 64 * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
@@ -207,7 +207,7 @@ class Sim final : public SimBase {
                 TRY(poisson(p_.poisson_tol, p_.poisson_max_iter, p_.poisson_fixed_iter, p_.poisson_check_every));
             }
             timer.begin(stream_, KC_FUSED);
-            k_fused<R, S><<<grid2_, dim3(TX, TY), fused_dyn_smem<S>(), stream_>>>(dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q,
+            k_fused<R, S><<<grid2_, dim3(TX, TY), fused_dyn_smem<R, S>(), stream_>>>(dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q,
                                                                  d_.E, d_.prev, d_.diag, step_ == 0 ? 1 : 0, last);
             TRY(launched());
             cur_ ^= 1;
@@ -715,9 +715,9 @@ class Batch final : public BatchBase {
     }
 
     int init(const double* const* phis) {
-        if constexpr (fused_dyn_smem<S>() > 0) {
+        if constexpr (fused_dyn_smem<R, S>() > 0) {
             if (cudaFuncSetAttribute(kb_fused<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)fused_dyn_smem<S>()) != cudaSuccess)
+                                     (int)fused_dyn_smem<R, S>()) != cudaSuccess)
                 return LB3E_ERR_CUDA;
         }
         for (int i = 0; i < n_; ++i) TRY(sims_[i]->init(phis[i], nullptr, nullptr, nullptr));
@@ -854,7 +854,7 @@ class Batch final : public BatchBase {
             }
         }
         if (iters_ > 0) kb_potential_fields<R, S><<<ntiles_, blk, 0, stream_>>>(table_, tiles_, h);
-        kb_fused<R, S><<<ntiles_, blk, fused_dyn_smem<S>(), stream_>>>(table_, tiles_, cur, first ? 1 : 0, diag ? 1 : 0);
+        kb_fused<R, S><<<ntiles_, blk, fused_dyn_smem<R, S>(), stream_>>>(table_, tiles_, cur, first ? 1 : 0, diag ? 1 : 0);
         launches += 3 + swaps() + (iters_ > 0);
         return cudaGetLastError() == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
     }
