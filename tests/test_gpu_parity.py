@@ -148,8 +148,14 @@ def test_reduced_precision_static_compound_full_run(precision, tol):
     cfg = W.config_static_compound(precision=precision)
     p = dict(cfg["params"], poisson_tol=1e-6)
     sim, orc = run_pair(p, cfg["phi"], cfg["steps"], noise=cfg["noise"])
-    errs = field_errors(sim, orc, ["phi1", "phi2", "phi3", "phinow1", "phinow2", "phinow3"])
-    # every field, for the record (the gate is on the phase fields)
+    # gated: the phase fields and the potential (FP32 also charge and field); the
+    # velocity and pressure are reported only: u is a small residual of balanced
+    # capillary, Coulomb and pressure terms (max |u| ~ 1e-5 against p ~ 1e-4), so
+    # FP32 rounding of those terms leaves ~1e-9 absolute, ~1e-4 of max |u|
+    gated = ["phi1", "phi2", "phi3", "phinow1", "phinow2", "phinow3", "psi"]
+    if precision == 1:
+        gated += ["q", "ex", "ey"]
+    errs = field_errors(sim, orc, gated)
     print(f"precision {precision}: 2000-step errors per field", field_errors(sim, orc))
     assert max(errs.values()) <= tol, errs
 
