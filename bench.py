@@ -194,14 +194,29 @@ def cpu_baseline(args, iters_per_step: float):
 
 
 def run_reference(args):
-    """The oracle timed on the host cores, each step a bounded sample of the
-    workload (see cpu_baseline); rank 0 only."""
+    """The oracle timed on the host cores for the same metric as the lb3e arm; rank 0
+    only.  Each timed step is a bounded sample of the workload: a cpu_sample^2
+    lattice with the geometry scaled.
+    * LB potential: the sample steps with a few potential iterations; the cost of
+      one iteration is timed on its own, and the step time is projected to the
+      iterations per step of the workload, its cap (the FP32 GPU solve runs to the
+      cap every step at 4096^2; --max-iter lowers it for both arms).
+    * multigrid (--potential mg): the oracle's own FD solve (conjugate gradients to
+      1e-13) on a sample of at most 256^2."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     n = min(args.cpu_sample, args.n)
-    iters = args.cpu_iters or 30
-    o = _oracle_sample(n, iters)
+    mg = getattr(args, "potential", "lb") == "mg"
+    if mg:
+        n = min(n, 256)
+        o = _oracle_sample(n, 1, solver=1)
+        iters, target, per_iter = None, None, 0.0
+    else:
+        iters = args.cpu_iters or 30
+        target = args.max_iter or 20000
+        o = _oracle_sample(n, iters)
     o.step(args.warmup)
     times = []
     for _ in range(args.steps):
@@ -209,17 +224,28 @@ def run_reference(args):
         o.step(1)
         times.append(time.perf_counter() - t0)
     per_step = statistics.mean(times)
+    if not mg:
+        t0 = time.perf_counter()
+        o.solve_potential(fixed=40, max_iter=40)
+        per_iter = (time.perf_counter() - t0) / 40
+        per_step = max(1e-9, per_step - iters * per_iter) + target * per_iter
+        sample = (f"{args.steps} timed steps of a {n}x{n} lattice of the same workload (radii scaled) with "
+                  f"{iters} potential iterations each, plus 40 iterations timed alone; projected to {target} "
+                  f"iterations per step")
+        cfg = {"potential_iters_per_step": target, "potential_solver": "LB pseudo-time iterations (Eq. 43)"}
+    else:
+        sample = (f"{args.steps} timed steps of a {n}x{n} lattice of the same workload (radii scaled), the "
+                  f"oracle's FD potential solve (conjugate gradients to 1e-13)")
+        cfg = {"potential_solver": "FD form, conjugate gradients (oracle)"}
     value = n * n / per_step / 1e6
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (stated initial condition of the workload)",
-            "config": {"workload": f"compound drop deformation under field, {args.n}x{args.n}",
-                       "sample_side": n, "potential_iters_per_step": iters, "poisson": "fixed iterations"},
-            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} timed steps of a {n}x{n} lattice of the same workload "
-                                       f"(radii scaled), {iters} potential iterations per step"},
+            "config": dict({"workload": f"compound drop deformation under field, {args.n}x{args.n}",
+                            "sample_side": n}, **cfg),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample,
+                             "seconds_per_potential_iteration": per_iter},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
