@@ -196,3 +196,84 @@ def config_adjoint(n: int = 256, precision: int = 1, **kw):
                u_wall_bottom=-1e-3, u_wall_top=1e-3, **kw)
     phi = compound_droplet(n, n, 32.0, 64.0, 4.0)
     return dict(name=f"adjoint_{n}x{n}", params=p, phi=phi, noise=None, steps=4000, E0=E0)
+
+
+# ---------------------------------------------------------------------------
+# Second workload: two compound drops under a field, and a compound drop in a
+# confined shear flow under a field (the paper's Section 5.4-5.5 studies).  Phase
+# labels as above: 1 matrix, 2 shell, 3 core.  The paper writes its ratios
+# S_ij = eps_i / eps_j, R_ij = sigma_i / sigma_j with 1 core, 2 shell, 3 bulk, so
+# its S23, R23 are shell / matrix and S12, R12 core / shell.
+# ---------------------------------------------------------------------------
+
+def _ratios_to_props(S12: float, S23: float, R12: float, R23: float, sigma_matrix: float):
+    """(eps, sigma) per workload phase (matrix, shell, core) from the paper's ratios,
+    matrix permittivity 1."""
+    e_shell = S23
+    e_core = S12 * e_shell
+    s_shell = R23 * sigma_matrix
+    s_core = R12 * s_shell
+    return (1.0, e_shell, e_core), (sigma_matrix, s_shell, s_core)
+
+
+def two_compound_drops(nx: int, ny: int, r_in: float, r_out: float, W: float, gap: float) -> np.ndarray:
+    """Two equal compound drops centred on the vertical line x = nx/2 (along the
+    field), their shells `gap` cells apart; each profile as in Eq. 54."""
+    x, y = _grid(nx, ny)
+    d = r_out + gap / 2
+    p3 = np.zeros((ny, nx))
+    shell = np.zeros((ny, nx))
+    for yc in (ny / 2 - d, ny / 2 + d):
+        r = np.sqrt((x - nx / 2) ** 2 + (y - yc) ** 2)
+        p3 += 0.5 + 0.5 * np.tanh(2.0 * (r_in - r) / W)
+        shell += 0.5 + 0.5 * np.tanh(2.0 * (r_out - r) / W)
+    p3 = np.minimum(p3, 1.0)
+    p2 = (1.0 - p3) * np.minimum(shell, 1.0)
+    p1 = 1.0 - p2 - p3
+    return np.ascontiguousarray(np.stack([p1, p2, p3]))
+
+
+# the paper's two regimes of drop pairs (its Figs. 10, 11)
+TWO_DROP_REGIMES = {
+    "coalescence": dict(S12=1.0 / 8.0, S23=8.0, R12=1.0 / 6.0, R23=6.0),
+    "separation": dict(S12=5.0, S23=0.2, R12=1.0 / 1.04, R23=1.04),
+}
+
+
+def config_two_drops(regime: str, n: int = 256, r_in: float = 12.0, r_out: float = 24.0, gap: float = 8.0,
+                     ca_e: float = 0.2, sigma_matrix: float = 0.1, iters: int = 16, precision: int = 1, **kw):
+    """Two compound drops aligned with the field between electrodes (Ca_E = 0.2,
+    equal densities and viscosities); the potential iterated `iters` times a step."""
+    eps, sigma = _ratios_to_props(sigma_matrix=sigma_matrix, **TWO_DROP_REGIMES[regime])
+    E0 = field_for_capillary(ca_e, 1e-3, eps[0], r_out)
+    p = params(nx=n, ny=n, bc_y=2, electric=1, precision=precision, eps=eps, sigma=sigma,
+               eps_ref=max(eps), V_bottom=0.0, V_top=E0 * n, poisson_fixed_iter=iters, **kw)
+    return dict(name=f"two_drops_{regime}_{n}", params=p, phi=two_compound_drops(n, n, r_in, r_out, 4.0, gap),
+                noise=None, regime=regime, gap=gap, r_out=r_out)
+
+
+def config_shear_regimes(ca_e=(0.2, 0.4, 0.6, 0.8, 1.0), wc=(0.3, 0.5, 0.6, 0.75), r_in: float = 15.0,
+                         r_out: float = 30.0, nx: int = 256, ca: float = 0.5, tau_g: float = 1.5,
+                         re_e: float = 0.01, iters: int = 16, precision: int = 1):
+    """Compound drop in a channel whose walls slide at -/+U and carry electrodes,
+    one instance per (Ca_E, W_c): the paper's regime diagram (its Fig. 15) with its
+    ratios S12 = 0.5, S23 = 2, R12 = 2, R23 = 0.5 and Ca = 0.5.  Readings: W_c =
+    R_b / H with H the half-height (channel height 2 R_b / W_c); Ca = mu gamma_dot
+    R_b / gamma with gamma_dot = 2 U / height; Re_E = eps gamma_dot / sigma fixes the
+    matrix conductivity; tau_g = 1.5 gives Re = rho gamma_dot R_b^2 / mu ~ 0.14."""
+    gamma = 1e-3
+    mu = (tau_g - 0.5) / 3.0  # rho = 1
+    gdot = ca * gamma / (mu * r_out)
+    eps, sigma = _ratios_to_props(S12=0.5, S23=2.0, R12=2.0, R23=0.5, sigma_matrix=gdot / re_e)
+    out = []
+    for w in wc:
+        ny = 2 * int(round(r_out / w))
+        U = 0.5 * gdot * ny
+        for c in ca_e:
+            E0 = field_for_capillary(c, gamma, eps[0], r_out)
+            p = params(nx=nx, ny=ny, bc_y=2, electric=1, precision=precision, eps=eps, sigma=sigma,
+                       eps_ref=max(eps), tau_g=tau_g, V_bottom=0.0, V_top=E0 * ny,
+                       u_wall_bottom=-U, u_wall_top=U, poisson_fixed_iter=iters)
+            out.append(dict(params=p, phi=compound_droplet(nx, ny, r_in, r_out, 4.0), ca_e=c, wc=w,
+                            shear_rate=gdot, capillary_time=mu * r_out / gamma))
+    return out
