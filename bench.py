@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lb3e", choices=["lb3e", "reference"])
-    ap.add_argument("--workload", default="deformation", choices=["deformation", "sweep", "adjoint"],
+    ap.add_argument("--workload", default="deformation", choices=["deformation", "sweep", "adjoint", "regimes"],
                     help="deformation: the 4096^2 lattice (default); sweep: 256 lattices in one batch; "
                          "adjoint: cost of the three parameter derivatives relative to a forward step")
     ap.add_argument("--precision", type=int, default=1, help="0 fp64, 1 fp32, 2 fp32 + fp16-stored populations")
@@ -484,6 +484,61 @@ def run_sweep(args):
         dist.destroy_process_group()
 
 
+def run_regimes(args):
+    """The second workload as one batch: the confined-shear grid (20 compound drops
+    in channels of heights 80..200, Ca_E 0.2..1 x W_c 0.3..0.75, sliding electrode
+    walls) and the two drop pairs (coalescence and separation, 256^2), 16
+    warm-started potential iterations per step.  Reports MLUPS over the timed steps
+    and the outcome measures at their end (a short horizon: the steady states take
+    tens of capillary times, see the GPU tests)."""
+    import torch
+    import paper_2608_05787_b300 as L
+    import workloads as W
+    from paper_2608_05787_b300 import regimes as G
+
+    torch.cuda.set_device(0)
+    shear = W.config_shear_regimes(precision=args.precision)
+    pairs = [W.config_two_drops(r, precision=args.precision) for r in ("coalescence", "separation")]
+    insts = [(c["params"], c["phi"]) for c in shear] + [(c["params"], c["phi"]) for c in pairs]
+    cells = sum(p["nx"] * p["ny"] for p, _ in insts)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = L.Batch([p for p, _ in insts], [phi for _, phi in insts], stream=stream).set_chunk(4)
+        b.run(args.warmup)
+        torch.cuda.synchronize()
+        l0 = b.launches
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(0) as clk:
+            ev0.record(stream)
+            b.run(args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        outcome = {"shear": [dict(wc=c["wc"], ca_e=c["ca_e"], drops=G.count_drops(b.field(i, "phinow1")),
+                                  **{k: round(v, 4) for k, v in G.shape_measures(b.field(i, "phinow1")).items()})
+                             for i, c in enumerate(shear)],
+                   "pairs": [dict(regime=c["regime"], **{k: round(v, 3) for k, v in
+                                                         G.pair_measures(b.field(len(shear) + k, "phinow1")).items()})
+                             for k, c in enumerate(pairs)]}
+    t = ms / 1e3
+    total = cells * args.steps
+    hbm, peak_kind = peaks()
+    per_cell = FUSED_BYTES[args.precision] + 16 * POISSON_BYTES[args.precision]
+    line = {"metric": METRIC, "value": total / t / 1e6, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {0: "f64", 1: "f32", 2: "f32 (f16-stored populations)"}[args.precision],
+            "data": "synthetic (the paper's drop-pair and confined-shear set-ups)",
+            "config": {"workload": "second workload: 20 confined-shear channels + 2 drop pairs, one batch",
+                       "cells": cells, "potential_iters_per_step": 16, "chunk": 4,
+                       "steps_before_outcome": args.warmup + args.steps},
+            "roofline": {"bound": "hbm", "achieved": per_cell * total / t / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": per_cell * total / t / 1e9 / hbm, "traffic": None,
+                         "kernel": "whole step (batched fused + 16 potential iterations)",
+                         "peak_kind": f"{peak_kind} copy bandwidth"},
+            "gpu_launches": b.launches - l0, "clocks": clk.summary(), "outcome": outcome}
+    print(json.dumps(line), flush=True)
+
+
 def run_adjoint(args):
     """Derivative cost on the 256^2 drop under field plus shear: time per step of
     the FP32 tangent build (three parameter directions: E0, eps3, gamma23) over the
@@ -534,6 +589,8 @@ def main():
         run_reference(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "regimes":
+        run_regimes(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
     else:
