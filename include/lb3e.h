@@ -167,7 +167,8 @@ int lb3e_step(lb3e_handle* h, int32_t nsteps);
 int lb3e_solve_potential(lb3e_handle* h, const double* q, double tol, int32_t max_iter,
                          int32_t check_every, int32_t* iters, double* residual);
 
-/* Reductions (FP64) over the last step's fields.  Synchronises the stream. */
+/* Reductions over the last step's fields: per-cell terms in the build's
+ * precision, every sum and the max in FP64.  Synchronises the stream. */
 int lb3e_observables(lb3e_handle* h, lb3e_observables_t* out);
 
 /* Copy one field (see the LB3E_FIELD_* ids) as doubles into dst ([ny][nx],
@@ -189,8 +190,9 @@ int64_t lb3e_potential_iterations(const lb3e_handle* h);
 
 /* Pseudo-iterations of the LB potential solve (Eq. 43) per kernel launch: 1
  * (one launch per iteration), 2 (temporally blocked on a tile with a 2-cell
- * halo), 3..4 (4-cell halo; the default is 4) or 5..8 (8-cell halo).  The result does not depend on
- * it up to rounding order; the speed does.  Dual-number precisions accept only 1.
+ * halo), 3..4 (4-cell halo; the default is 4) or 5..8 (8-cell halo).  The
+ * per-cell arithmetic is the same for every choice (FP64 states agree bitwise);
+ * the speed differs.  Dual-number precisions accept only 1.
  * Errors: NULL, PARAM (out of range). */
 int lb3e_set_potential_chunk(lb3e_handle* h, int32_t iterations_per_launch);
 
@@ -203,7 +205,7 @@ int lb3e_set_timing(lb3e_handle* h, int32_t enable);
 enum {
     LB3E_KC_MOMENTS = 0,   /* zeroth moments of the phase and charge populations */
     LB3E_KC_PROLOGUE = 1,  /* properties, stencils, closed-form charge */
-    LB3E_KC_POISSON = 2,   /* one pseudo-iteration of the potential populations */
+    LB3E_KC_POISSON = 2,   /* potential solve: LB pseudo-iterations (one or several per launch) or multigrid */
     LB3E_KC_REDUCE = 3,    /* FP64 reductions (residual, observables) */
     LB3E_KC_FIELDS = 4,    /* psi and E from the potential populations */
     LB3E_KC_FUSED = 5,     /* fused chemical potential, force, collide and stream */
