@@ -39,6 +39,7 @@ class _Params(C.Structure):
         ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int32),
         ("poisson_check_every", C.c_int32), ("poisson_fixed_iter", C.c_int32),
         ("potential_solver", C.c_int32),
+        ("debye_kappa2", C.c_double),
     ]
 
 

@@ -60,6 +60,10 @@ typedef struct orc_params {
     int32_t poisson_max_iter, poisson_check_every, poisson_fixed_iter;
     int32_t potential_solver;  /* 0: the LB pseudo-time solve (Eq. 42-45); 1: the
                                   finite-difference form of Eq. 27d solved directly */
+    double debye_kappa2;       /* > 0: validation closure for the electro-osmotic channel
+                                  (Section 5.1): the charge is the linearised Boltzmann
+                                  (Debye-Hueckel) response q = -eps kappa^2 psi instead of
+                                  the transported charge; 0: the method as stated */
 } orc_params;
 
 enum { F_PHI1 = 0, F_PHI2, F_PHI3, F_UX, F_UY, F_P, F_Q, F_PSI, F_EX, F_EY,
@@ -194,7 +198,8 @@ static void poisson_iteration(orc_state* s) {
         double psi = psi_moment(s, s->h, c);
         double gx, gy;
         gradpsi_moment(s, s->h, c, epshat, &gx, &gy);
-        double qc = s->q[c];
+        /* the Debye-Hueckel closure follows the current iterate of psi */
+        double qc = s->p.debye_kappa2 > 0.0 ? -s->eps[c] * s->p.debye_kappa2 * psi : s->q[c];
         for (int j = 0; j < 9; ++j) {
             double heq = (j == 0) ? (W[0] - 1.0) * psi : W[j] * psi;      /* Eq. 44 */
             double varpi = (j == 0) ? 0.0 : 1.0 / 8.0;
@@ -564,6 +569,9 @@ static void one_step(orc_state* s) {
             s->psi[c] = 0.0;
         }
     }
+    /* the Debye-Hueckel closure: charge from the solved potential */
+    if (s->p.debye_kappa2 > 0.0)
+        for (int c = 0; c < N; ++c) s->q[c] = -s->eps[c] * s->p.debye_kappa2 * s->psi[c];
     /* R^n of Eq. 47 with q^n and E^n */
     for (int c = 0; c < N; ++c) {
         double r = s->sig[c] / s->eps[c];

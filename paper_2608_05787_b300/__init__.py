@@ -48,6 +48,10 @@ class Params(C.Structure):
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
+        if d.get("debye_kappa2", 0.0):
+            # a validation closure of the test oracle (electro-osmotic channel), not
+            # part of the method this library implements
+            raise ValueError("debye_kappa2 is an oracle-only validation closure; lb3e does not implement it")
         s = cls()
         for name, ctype in cls._fields_:
             if name.startswith("_pad"):

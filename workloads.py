@@ -45,6 +45,7 @@ PARAM_DEFAULTS = dict(
     poisson_fixed_iter=0,
     potential_solver=0,          # 0 the LB pseudo-time solve of the paper; 1 multigrid on its FD form
     tangent_param=(-1, -1, -1),  # GPU tangent builds: parameter per tangent direction
+    debye_kappa2=0.0,            # oracle only: > 0 replaces the charge by -eps kappa^2 psi (EOF check)
 )
 
 
