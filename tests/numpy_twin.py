@@ -1,0 +1,263 @@
+"""A second, independent implementation of the method's step in vectorised NumPy,
+written from the paper's equations and the readings listed in the design notes
+(test infrastructure: it checks the C oracle's transcription on tiny lattices).
+
+Whole-lattice array operations replace the oracle's per-cell loops: neighbours
+come from index arrays (x periodic; y periodic, or mirrored about the half-way
+walls for stencils), streaming shifts whole planes and reflects what crosses a wall.
+Only the fixed-iteration potential solve is implemented (the residual-controlled
+stop is a host decision, covered elsewhere).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])       # Eq. 31
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+OPP = np.array([0, 3, 4, 1, 2, 7, 8, 5, 6])
+CS2 = 1.0 / 3.0
+
+
+class Twin:
+    def __init__(self, p: dict, phi, u=None, q=None, noise=None):
+        self.p = dict(p)
+        self.ny, self.nx = int(p["ny"]), int(p["nx"])
+        ny, nx = self.ny, self.nx
+        g12, g13, g23 = p["gamma12"], p["gamma13"], p["gamma23"]
+        self.lam = np.array([g12 + g13 - g23, g12 + g23 - g13, g13 + g23 - g12])   # Eq. 9
+        self.m0 = CS2 * (p["tau_f"] - 0.5)
+        self.tau_h = 0.5 + p["eps_ref"] / CS2
+        self.tau_l = 0.5 + p["alpha"] / CS2
+        self.phi = np.array(phi, dtype=float).copy()
+        self.u = np.zeros((2, ny, nx)) if u is None else np.array(u, dtype=float).copy()
+        self.q = np.zeros((ny, nx)) if q is None else np.array(q, dtype=float).copy()
+        self.step_count = 0
+        self._properties()
+        # potential populations at equilibrium with the linear electrode profile (or 0)
+        yy = (np.arange(ny) + 0.5)[:, None] * np.ones((1, nx))
+        psi0 = p["V_bottom"] + (p["V_top"] - p["V_bottom"]) * yy / ny if p["bc_y"] == 2 else np.zeros((ny, nx))
+        self.h = self._heq(psi0)
+        self._solve_potential()
+        self._chemical_potential()
+        ux, uy = self.u
+        f = np.empty((3, 9, ny, nx))
+        for i in range(3):
+            f[i] = self._feq(self.phi[i], self.mu[i], ux, uy)
+        self.f = f
+        self.g = self.rho[None] * self._s(ux, uy)                 # g_eq with p = 0
+        self.l = self._leq(self.q, ux, uy)
+        if noise is not None:
+            nz = np.asarray(noise, dtype=float)
+            self.g = self.g + nz[0]
+            self.f = self.f + nz[1:4]
+            self.l = self.l + nz[4]
+        self.prev_phiu = np.zeros((3, 2, ny, nx))
+        self.prev_qu = np.zeros((2, ny, nx))
+
+    # ---------------------------------------------------------------- lattice helpers
+    def _rows(self, dy):
+        y = np.arange(self.ny) + dy
+        if self.p["bc_y"] == 0:
+            return y % self.ny
+        return np.where(y < 0, -1 - y, np.where(y >= self.ny, 2 * self.ny - 1 - y, y))
+
+    def _nb(self, a, dx, dy):
+        """a at (x + dx, y + dy): x periodic; y periodic or mirror ghosts."""
+        return np.roll(a[self._rows(dy)], -dx, axis=1)
+
+    def _grad(self, a):                                              # Eq. 33
+        gx = sum(W[j] * CX[j] * self._nb(a, CX[j], CY[j]) for j in range(9)) / CS2
+        gy = sum(W[j] * CY[j] * self._nb(a, CX[j], CY[j]) for j in range(9)) / CS2
+        return gx, gy
+
+    def _lap(self, a):                                               # Eq. 33
+        return sum(2 * W[j] * (self._nb(a, CX[j], CY[j]) - a) for j in range(9)) / CS2
+
+    def _stream(self, post, kind):
+        """Push streaming of 9 planes; what leaves through a wall comes back to the
+        same cell in the opposite direction: plain (kind 'bb'), with the moving-wall
+        term (kind 'flow'), or anti-bounce-back to the electrode potential ('pot')."""
+        ny = self.ny
+        out = np.empty_like(post)
+        walls = self.p["bc_y"] != 0
+        for j in range(9):
+            v = np.roll(post[j], CX[j], axis=1)
+            if not walls or CY[j] == 0:
+                out[j] = np.roll(v, CY[j], axis=0)
+            elif CY[j] > 0:
+                out[j][1:] = v[:-1]
+            else:
+                out[j][:-1] = v[1:]
+        if walls:
+            for j in range(9):
+                if CY[j] == 0:
+                    continue
+                row = ny - 1 if CY[j] > 0 else 0       # cells whose link j crosses the wall
+                top = CY[j] > 0
+                v = post[j][row]
+                if kind == "flow":
+                    uw = self.p["u_wall_top"] if top else self.p["u_wall_bottom"]
+                    v = v - 2.0 * W[j] * self.rho[row] * (CX[j] * uw) / CS2
+                elif kind == "pot" and self.p["bc_y"] == 2:
+                    vw = self.p["V_top"] if top else self.p["V_bottom"]
+                    v = -v + 2.0 * W[j] * vw
+                out[OPP[j]][row] = v
+        return out
+
+    # ---------------------------------------------------------------- closures
+    def _properties(self):
+        p = self.p
+        ph = self.phi
+        self.rho = sum(ph[i] * p["rho"][i] for i in range(3))                      # Eq. 29
+        self.sig = sum(ph[i] * p["sigma"][i] for i in range(3))
+        self.eps = sum(p["eps"][i] * ph[i] ** 2 * (3 - 2 * ph[i]) for i in range(3))   # Eq. 30
+        self.lap = np.array([self._lap(ph[i]) for i in range(3)])
+        self.geps = np.array(self._grad(self.eps))
+        self.gsig = np.array(self._grad(self.sig))
+        self.grho = np.array(self._grad(self.rho))
+
+    def _heq(self, psi):
+        h = np.empty((9,) + psi.shape)
+        h[0] = (W[0] - 1.0) * psi                                                   # Eq. 44
+        for j in range(1, 9):
+            h[j] = W[j] * psi
+        return h
+
+    def _solve_potential(self):
+        p = self.p
+        if not p["electric"]:
+            self.E = np.array([np.full((self.ny, self.nx), p["E_ext"][0]), np.full((self.ny, self.nx), p["E_ext"][1])])
+            self.psi = np.zeros((self.ny, self.nx))
+            return
+        th = self.tau_h
+        ehat = self.eps - p["eps_ref"]
+        den = ehat + CS2 * th
+        varpi = np.array([0.0] + [1 / 8] * 8)
+        for _ in range(p["poisson_fixed_iter"]):                                    # Eq. 43
+            psi = self.h[1:].sum(0) / (1 - W[0])
+            jx = np.tensordot(CX, self.h, 1)
+            jy = np.tensordot(CY, self.h, 1)
+            gx, gy = -jx / den, -jy / den
+            heq = self._heq(psi)
+            post = np.empty_like(self.h)
+            for j in range(9):
+                post[j] = (self.h[j] - (self.h[j] - heq[j]) / th
+                           - (ehat / CS2) * W[j] * (CX[j] * gx + CY[j] * gy) / th + varpi[j] * self.q)
+            self.h = self._stream(post, "pot")
+        self.psi = self.h[1:].sum(0) / (1 - W[0])                                    # Eq. 45
+        jx = np.tensordot(CX, self.h, 1)
+        jy = np.tensordot(CY, self.h, 1)
+        self.E = np.array([jx / den + p["E_ext"][0], jy / den + p["E_ext"][1]])
+
+    def _chemical_potential(self):                                                  # Eq. 20
+        D = self.p["width_D"]
+        e2 = self.E[0] ** 2 + self.E[1] ** 2
+        self.mu = np.array([24 / D * self.lam[i] * self.phi[i] * (self.phi[i] - 0.5) * (self.phi[i] - 1)
+                            - 0.75 * D * self.lam[i] * self.lap[i]
+                            - 0.5 * 6 * self.p["eps"][i] * self.phi[i] * (1 - self.phi[i]) * e2 for i in range(3)])
+
+    def _s(self, ux, uy):                                                           # Eq. 40
+        out = np.empty((9,) + ux.shape)
+        uu = ux * ux + uy * uy
+        for j in range(9):
+            cu = CX[j] * ux + CY[j] * uy
+            out[j] = W[j] * (cu / CS2 + cu * cu / (2 * CS2 * CS2) - uu / (2 * CS2))
+        return out
+
+    def _feq(self, ph, mu, ux, uy):                                                 # Eq. 35
+        out = np.empty((9,) + ph.shape)
+        out[0] = ph - (1 - W[0]) * mu
+        for j in range(1, 9):
+            out[j] = W[j] * mu + W[j] * (CX[j] * ph * ux + CY[j] * ph * uy) / CS2
+        return out
+
+    def _leq(self, q, ux, uy):                                                      # Eq. 50
+        out = np.empty((9,) + q.shape)
+        for j in range(9):
+            cu = CX[j] * ux + CY[j] * uy
+            out[j] = W[j] * q * (1 + cu / CS2) if self.p["charge_convection"] else W[j] * q
+        return out
+
+    # ---------------------------------------------------------------- one time step
+    def step(self, n: int = 1):
+        for _ in range(n):
+            self._one_step()
+        return self
+
+    def _one_step(self):
+        p = self.p
+        first = self.step_count == 0
+        self.phi = self.f.sum(1)                                                    # S1
+        qt = self.l.sum(0)
+        self._properties()                                                          # S2, S3
+        r = self.sig / self.eps
+        Ex, Ey = self.E                                                             # E of the last step
+        src = r * (self.geps[0] * Ex + self.geps[1] * Ey) - (self.gsig[0] * Ex + self.gsig[1] * Ey)
+        self.q = (qt + 0.5 * src) / (1 + 0.5 * r)                                   # S4 (reading R9)
+        self._solve_potential()                                                     # S5
+        Ex, Ey = self.E
+        R = -r * self.q + r * (self.geps[0] * Ex + self.geps[1] * Ey) - (self.gsig[0] * Ex + self.gsig[1] * Ey)
+        self._chemical_potential()                                                  # S6
+        gmu = np.array([self._grad(self.mu[i]) for i in range(3)])                 # S7
+        Fx = -sum(self.phi[i] * gmu[i][0] for i in range(3)) + self.q * Ex         # S8
+        Fy = -sum(self.phi[i] * gmu[i][1] for i in range(3)) + self.q * Ey
+        g = self.g                                                                  # S9, Eq. 41
+        ux = (np.tensordot(CX, g, 1) + 0.5 * Fx) / self.rho
+        uy = (np.tensordot(CY, g, 1) + 0.5 * Fy) / self.rho
+        ugr = ux * self.grho[0] + uy * self.grho[1]
+        s = self._s(ux, uy)
+        pr = CS2 / (1 - W[0]) * (g[1:].sum(0) + 0.5 * ugr + self.rho * s[0])
+        self.u = np.array([ux, uy])
+        self.pr = pr
+        # S10: backward differences, zero on the first step (reading R10)
+        phiu = np.array([[self.phi[i] * ux, self.phi[i] * uy] for i in range(3)])
+        qu = np.array([self.q * ux, self.q * uy])
+        dpu = np.zeros_like(phiu) if first else phiu - self.prev_phiu
+        dqu = np.zeros_like(qu) if first else qu - self.prev_qu
+        # S11: phase populations, mobility of Eq. 28, source read as R3
+        tf, m0 = p["tau_f"], self.m0
+        fpost = np.empty_like(self.f)
+        for i in range(3):
+            Y = np.zeros((2,) + ux.shape)
+            for k in range(3):
+                if k == i:
+                    Mik = m0 * self.phi[i] * sum(self.phi[kk] for kk in range(3) if kk != i) - m0
+                else:
+                    Mik = -m0 * self.phi[i] * self.phi[k]
+                Y = Y + Mik * gmu[k]
+            A = dpu[i] / CS2 - Y / m0
+            feq = self._feq(self.phi[i], self.mu[i], ux, uy)
+            for j in range(9):
+                Fj = W[j] * (CX[j] * A[0] + CY[j] * A[1])
+                fpost[i, j] = self.f[i, j] - (self.f[i, j] - feq[j]) / tf + (1 - 1 / (2 * tf)) * Fj
+        # S12: flow populations, Eq. 37-40 (local tau_g from the dynamic viscosity)
+        if all(v > 0 for v in p["visc"]):
+            eta = sum(self.phi[i] * p["visc"][i] for i in range(3))
+            tg = 0.5 + eta / (self.rho * CS2)
+        else:
+            tg = p["tau_g"]
+        gpost = np.empty_like(g)
+        for j in range(9):
+            geq = ((W[0] - 1) if j == 0 else W[j]) * pr / CS2 + self.rho * s[j]
+            cu = CX[j] * ux + CY[j] * uy
+            cgr = CX[j] * self.grho[0] + CY[j] * self.grho[1]
+            cF = CX[j] * Fx + CY[j] * Fy
+            G = W[j] * (ugr + cF / CS2 + (cu * cgr - CS2 * ugr) / CS2)
+            gpost[j] = g[j] - (g[j] - geq) / tg + (1 - 1 / (2 * tg)) * G
+        # S13: charge populations, Eq. 48-50
+        tl = self.tau_l
+        leq = self._leq(self.q, ux, uy)
+        lpost = np.empty_like(self.l)
+        for j in range(9):
+            Sj = (1 - 1 / (2 * tl)) * W[j] * R
+            Tj = ((1 - 1 / (2 * tl)) * W[j] * (CX[j] * dqu[0] + CY[j] * dqu[1]) / CS2
+                  if p["charge_convection"] else 0.0)
+            lpost[j] = self.l[j] - (self.l[j] - leq[j]) / tl + Sj + Tj
+        # S14: streaming with the walls
+        self.f = np.array([self._stream(fpost[i], "bb") for i in range(3)])
+        self.g = self._stream(gpost, "flow")
+        self.l = self._stream(lpost, "bb")
+        self.prev_phiu = phiu
+        self.prev_qu = qu
+        self.step_count += 1
