@@ -39,27 +39,56 @@ using MGLevelF = MGLevelT<float>;   // the FP32 error equation of the V-cycle
 __device__ __forceinline__ double mg_hmean(double a, double b) { return 2.0 * a * b / (a + b); }
 
 // Face coefficients of level L (harmonic means; no face across an electrode wall,
-// which instead adds 2 eps_C to the diagonal), and their FP32 copies in F.  The only
-// FP64 divisions of a solve happen here, once per level.
-static __global__ void __launch_bounds__(256) k_mg_coeffs(MGLevel L, MGLevelF F) {
+// which instead adds 2 eps_C to the diagonal).  Fine level, FP64 (the FP64 residual
+// uses them), in two passes so that each face's division happens once: the east and
+// north faces of every cell, then the diagonal from a cell's own faces and its west
+// and south neighbours' (the harmonic mean is symmetric, so these equal the faces
+// seen from this cell bit for bit).  Copies rounded to FP32 feed the V-cycle.
+static __global__ void __launch_bounds__(256) k_mg_faces(MGLevel L) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= L.nx || y >= L.ny) return;
     const int c = y * L.nx + x;
     const double ec = L.eps[c];
-    const int xe = x + 1 == L.nx ? 0 : x + 1, xw = x == 0 ? L.nx - 1 : x - 1;
-    const double ae = mg_hmean(ec, L.eps[y * L.nx + xe]);
-    const double aw = mg_hmean(ec, L.eps[y * L.nx + xw]);
-    const double an = y + 1 < L.ny ? mg_hmean(ec, L.eps[c + L.nx]) : 0.0;
-    const double as = y > 0 ? mg_hmean(ec, L.eps[c - L.nx]) : 0.0;
+    const int xe = x + 1 == L.nx ? 0 : x + 1;
+    L.ae[c] = mg_hmean(ec, L.eps[y * L.nx + xe]);
+    L.an[c] = y + 1 < L.ny ? mg_hmean(ec, L.eps[c + L.nx]) : 0.0;
+}
+static __global__ void __launch_bounds__(256) k_mg_diag(MGLevel L, MGLevelF F) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= L.nx || y >= L.ny) return;
+    const int c = y * L.nx + x;
+    const double ec = L.eps[c];
+    const int xw = x == 0 ? L.nx - 1 : x - 1;
+    const double ae = L.ae[c], an = L.an[c];
+    const double aw = L.ae[y * L.nx + xw];
+    const double as = y > 0 ? L.an[c - L.nx] : 0.0;
     const double d = ae + aw + (y + 1 < L.ny ? an : 2.0 * ec) + (y > 0 ? as : 2.0 * ec);
-    L.ae[c] = ae;
-    L.an[c] = an;
     L.dg[c] = d;
     L.idg[c] = 1.0 / d;
     F.ae[c] = (float)ae;
     F.an[c] = (float)an;
     F.dg[c] = (float)d;
     F.idg[c] = (float)(1.0 / d);
+}
+// Coarse levels: coefficients only set the V-cycle's rate of convergence, not the
+// answer (the FP64 fine residual does), so they are formed in FP32 from the
+// coarsened permittivity, directly into the FP32 level.
+static __global__ void __launch_bounds__(256) k_mg_coeffs_f(MGLevel L, MGLevelF F) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= L.nx || y >= L.ny) return;
+    const int c = y * L.nx + x;
+    auto hm = [](float a, float b) { return 2.0f * a * b / (a + b); };
+    const float ec = (float)L.eps[c];
+    const int xe = x + 1 == L.nx ? 0 : x + 1, xw = x == 0 ? L.nx - 1 : x - 1;
+    const float ae = hm(ec, (float)L.eps[y * L.nx + xe]);
+    const float aw = hm(ec, (float)L.eps[y * L.nx + xw]);
+    const float an = y + 1 < L.ny ? hm(ec, (float)L.eps[c + L.nx]) : 0.0f;
+    const float as = y > 0 ? hm(ec, (float)L.eps[c - L.nx]) : 0.0f;
+    const float d = ae + aw + (y + 1 < L.ny ? an : 2.0f * ec) + (y > 0 ? as : 2.0f * ec);
+    F.ae[c] = ae;
+    F.an[c] = an;
+    F.dg[c] = d;
+    F.idg[c] = 1.0f / d;
 }
 
 // sum_{faces} a_f psi_neighbour at cell (x, y)
@@ -196,17 +225,32 @@ static __global__ void __launch_bounds__(256) k_mg_fields(MGLevel L, double vb, 
                                                           R* __restrict__ E) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= L.nx || y >= L.ny) return;
-    double ax = 0.0, ay = 0.0;
-#pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        const double v = mg_psi_ghost(L, x + cx(j), y + cy(j), vb, vt);
-        ax += wgt<double>(j) * cx(j) * v;
-        ay += wgt<double>(j) * cy(j) * v;
-    }
     const int c = y * L.nx + x;
     const size_t N = (size_t)L.nx * L.ny;
-    E[c] = R(-(ax * 3.0) + ex);  // / cs^2 (a multiply: FP64 division is slow here)
-    E[N + c] = R(-(ay * 3.0) + ey);
+    if constexpr (std::is_same<R, double>::value) {
+        double ax = 0.0, ay = 0.0;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const double v = mg_psi_ghost(L, x + cx(j), y + cy(j), vb, vt);
+            ax += wgt<double>(j) * cx(j) * v;
+            ay += wgt<double>(j) * cy(j) * v;
+        }
+        E[c] = R(-(ax * 3.0) + ex);  // / cs^2 (a multiply: FP64 division is slow here)
+        E[N + c] = R(-(ay * 3.0) + ey);
+    } else {
+        // FP32 output: differences from the centre in FP64 (the electrode profile
+        // makes psi large against its neighbour differences), weighted sums in FP32
+        const double pc = L.psi[c];
+        float ax = 0.f, ay = 0.f;
+#pragma unroll
+        for (int j = 1; j < 9; ++j) {
+            const float d = (float)(mg_psi_ghost(L, x + cx(j), y + cy(j), vb, vt) - pc);
+            cacc(ax, cx(j), wgt<float>(j), d);
+            cacc(ay, cy(j), wgt<float>(j), d);
+        }
+        E[c] = R(-(double)(ax * 3.0f) + ex);  // / cs^2
+        E[N + c] = R(-(double)(ay * 3.0f) + ey);
+    }
 }
 
 // initial guess: the linear electrode profile

@@ -464,7 +464,14 @@ class Sim final : public SimBase {
                 TRY(launched());
             }
             timer.begin(stream_, KC_POISSON);
-            k_mg_coeffs<<<mg_grid(l), blk, 0, stream_>>>(mg_[l], mgf_[l]);
+            if (l == 0) {
+                k_mg_faces<<<mg_grid(0), blk, 0, stream_>>>(mg_[0]);
+                TRY(launched());
+                timer.begin(stream_, KC_POISSON);
+                k_mg_diag<<<mg_grid(0), blk, 0, stream_>>>(mg_[0], mgf_[0]);
+            } else {
+                k_mg_coeffs_f<<<mg_grid(l), blk, 0, stream_>>>(mg_[l], mgf_[l]);
+            }
             TRY(launched());
         }
         // smoothing of the FP32 error equation on level l
