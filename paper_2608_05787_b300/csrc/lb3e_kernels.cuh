@@ -491,14 +491,14 @@ constexpr size_t pb_smem_bytes() { return (size_t)11 * PBGeom<H>::CELLS * sizeof
 // halo depth of the region that serves a chunk of K iterations
 __host__ __device__ constexpr int pb_halo_for(int K) { return K <= 2 ? 2 : (K <= 4 ? 4 : 8); }
 
-template <class R, int H>
+template <class R, int H, int KC = 0>
 __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __restrict__ hin,
                                                 R* __restrict__ hout, const R* __restrict__ eps,
                                                 const R* __restrict__ q, R* __restrict__ prev,
-                                                double* __restrict__ partial, int K, int save_prev, int check,
+                                                double* __restrict__ partial, int Kdyn, int save_prev, int check,
                                                 int bx, int by, int gdx) {
     using G = PBGeom<H>;
-    constexpr int RX = G::RX, RY = G::RY, CELLS = G::CELLS, CPT = G::CPT, NT = G::THREADS;
+    constexpr int RX = G::RX, CELLS = G::CELLS, CPT = G::CPT, NT = G::THREADS;
     extern __shared__ __align__(16) unsigned char pb_raw[];
     R* hs = reinterpret_cast<R*>(pb_raw);  // [9][CELLS] post-collision values
     // per cell, fixed over the iterations: eps and q, or, in the factored FP32
@@ -561,6 +561,11 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
     // residual sums: a thread's own cells (three at most) in R, the block and grid
     // sums in FP64
     R acc[4] = {R(0), R(0), R(0), R(0)};
+    // K = 4 (the default chunk) is a compile-time constant in its own instantiation:
+    // the iteration loop unrolls and its cone and check conditions resolve per t
+    const int K = KC > 0 ? KC : Kdyn;
+    constexpr int kUnroll = KC > 0 ? KC : 1;
+#pragma unroll kUnroll
     for (int t = 0; t < K; ++t) {
 #pragma unroll
         for (int m = 0; m < CPT; ++m) {
@@ -636,12 +641,12 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
     }
     if (check) block_reduce_store_r<4>(acc, partial + 4 * (size_t)(bx + gdx * by));
 }
-template <class R, int H>
+template <class R, int H, int KC = 0>
 __global__ void __launch_bounds__(PBGeom<H>::THREADS, pb_min_blocks<R, H>())
     k_poisson_tb(DevParams P, const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ eps,
                  const R* __restrict__ q, R* __restrict__ prev, double* __restrict__ partial, int K, int save_prev,
                  int check) {
-    body_poisson_tb<R, H>(P, hin, hout, eps, q, prev, partial, K, save_prev, check, blockIdx.x, blockIdx.y,
+    body_poisson_tb<R, H, KC>(P, hin, hout, eps, q, prev, partial, K, save_prev, check, blockIdx.x, blockIdx.y,
                           gridDim.x);
 }
 
@@ -1393,13 +1398,13 @@ __global__ void __launch_bounds__(256) kb_poisson(const InstState<R, S>* __restr
     body_poisson<R>(e.P, e.h[hcur], e.h[hcur ^ 1], e.eps, e.q, nullptr, nullptr, 0, 0, t.y, t.z, 0);
 }
 // K pseudo-iterations per launch over the 32 x 16 tiles of all instances
-template <class R, class S, int H>
+template <class R, class S, int H, int KC = 0>
 __global__ void __launch_bounds__(PBGeom<H>::THREADS, pb_min_blocks<R, H>())
     kb_poisson_tb(const InstState<R, S>* __restrict__ st, const int4* __restrict__ tiles, int hcur, int K) {
     const int4 t = tiles[blockIdx.x];
     const InstState<R, S>& e = st[t.x];
     if (!e.P.electric) return;
-    body_poisson_tb<R, H>(e.P, e.h[hcur], e.h[hcur ^ 1], e.eps, e.q, nullptr, nullptr, K, 0, 0, t.y, t.z, 0);
+    body_poisson_tb<R, H, KC>(e.P, e.h[hcur], e.h[hcur ^ 1], e.eps, e.q, nullptr, nullptr, K, 0, 0, t.y, t.z, 0);
 }
 template <class R, class S>
 __global__ void __launch_bounds__(256) kb_potential_fields(const InstState<R, S>* __restrict__ st,

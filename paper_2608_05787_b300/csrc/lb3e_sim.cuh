@@ -542,6 +542,8 @@ class Sim final : public SimBase {
                                          (int)pb_smem_bytes<R, 2>()) != cudaSuccess ||
                     cudaFuncSetAttribute(k_poisson_tb<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)pb_smem_bytes<R, 4>()) != cudaSuccess ||
+                    cudaFuncSetAttribute(k_poisson_tb<R, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pb_smem_bytes<R, 4>()) != cudaSuccess ||
                     cudaFuncSetAttribute(k_poisson_tb<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)pb_smem_bytes<R, 8>()) != cudaSuccess)
                     return LB3E_ERR_CUDA;
@@ -555,6 +557,9 @@ class Sim final : public SimBase {
         if constexpr (!is_dual<R>::value) {
             if (pb_halo_for(c) == 2)
                 k_poisson_tb<R, 2><<<pgrid, PBGeom<2>::THREADS, pb_smem_bytes<R, 2>(), stream_>>>(
+                    dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q, d_.psi_prev, d_.partial, c, save, check);
+            else if (c == 4)
+                k_poisson_tb<R, 4, 4><<<pgrid, PBGeom<4>::THREADS, pb_smem_bytes<R, 4>(), stream_>>>(
                     dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q, d_.psi_prev, d_.partial, c, save, check);
             else if (pb_halo_for(c) == 4)
                 k_poisson_tb<R, 4><<<pgrid, PBGeom<4>::THREADS, pb_smem_bytes<R, 4>(), stream_>>>(
@@ -823,6 +828,8 @@ class Batch final : public BatchBase {
                                      (int)pb_smem_bytes<R, 2>()) != cudaSuccess ||
                 cudaFuncSetAttribute(kb_poisson_tb<R, S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)pb_smem_bytes<R, 4>()) != cudaSuccess ||
+                cudaFuncSetAttribute(kb_poisson_tb<R, S, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pb_smem_bytes<R, 4>()) != cudaSuccess ||
                 cudaFuncSetAttribute(kb_poisson_tb<R, S, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)pb_smem_bytes<R, 8>()) != cudaSuccess)
                 return LB3E_ERR_CUDA;
@@ -851,6 +858,9 @@ class Batch final : public BatchBase {
                 const int c = iters_ - k < chunk_ ? iters_ - k : chunk_;
                 if (pb_halo_for(c) == 2)
                     kb_poisson_tb<R, S, 2><<<nptiles_, PBGeom<2>::THREADS, pb_smem_bytes<R, 2>(), stream_>>>(
+                        table_, ptiles_, h, c);
+                else if (c == 4)
+                    kb_poisson_tb<R, S, 4, 4><<<nptiles_, PBGeom<4>::THREADS, pb_smem_bytes<R, 4>(), stream_>>>(
                         table_, ptiles_, h, c);
                 else if (pb_halo_for(c) == 4)
                     kb_poisson_tb<R, S, 4><<<nptiles_, PBGeom<4>::THREADS, pb_smem_bytes<R, 4>(), stream_>>>(
