@@ -203,6 +203,40 @@ def test_couette_profile_exact():
     assert 90 < errs[0] / errs[1] < 110
 
 
+@pytest.mark.parametrize("tau_g", [0.5 + math.sqrt(3.0 / 16.0), 1.2])
+def test_poiseuille_profile_matches_bounce_back_closed_form(tau_g):
+    """Eq. 37-41 driven by the Coulomb force qE of Eq. 27b between resting half-way
+    walls (electrodes at zero potential, sigma = 0 so q stays uniform): the steady
+    flow is the parabola u(y) = F/(2 mu) [(y + 1/2)(ny - y - 1/2) + s] with F = q E_x.
+    For BGK with half-way bounce-back and a second-order force term the discrete
+    solution is known in closed form (He, Zou, Luo & Dembo 1997; Ginzburg &
+    d'Humieres 2003): the wall slip is s = (4/3)((tau - 1/2)^2 - 3/16), which vanishes
+    at tau = 1/2 + sqrt(3/16).  A missing half-force in u, a wrong force weight or
+    a wall off by half a cell each change s or the amplitude at order one.
+    E_y from the charge's own potential gives a wall-normal force F_y = (q^2/eps)
+    (y - (ny-1)/2), balanced by the pressure; it perturbs u_x at order q^2, kept below
+    the checked bound by q << E_x.  It also drives the scheme's staggered momentum
+    invariant: streaming and half-way bounce-back carry (-1)^(y+t) c_y f unchanged and
+    collision conserves momentum, so sum_y (-1)^(y+t) j_y moves only by the force's
+    alternating row sum each step.  With u = (j + F/2)/rho that leaves the two-cell
+    oscillation u_y = +-q^2/(4 eps), flipping sign every step, independent of tau."""
+    nx, ny, q0, Ex = 4, 16, 1e-5, 1e-2
+    mu = CS2 * (tau_g - 0.5)
+    p = W.params(nx=nx, ny=ny, bc_y=2, electric=1, eps=(1.0, 1.0, 1.0), sigma=(0.0, 0.0, 0.0), eps_ref=1.0,
+                 V_bottom=0.0, V_top=0.0, E_ext=(Ex, 0.0), tau_g=tau_g, poisson_tol=1e-13,
+                 poisson_max_iter=100000, poisson_check_every=10)
+    o = oracle.Oracle(p, W.single_phase(nx, ny, 1), q=np.full((ny, nx), q0))
+    o.step(3500)
+    y = np.arange(ny, dtype=float)
+    s = 4.0 / 3.0 * ((tau_g - 0.5) ** 2 - 3.0 / 16.0)
+    exact = q0 * Ex / (2 * mu) * ((y + 0.5) * (ny - y - 0.5) + s)
+    ux = o.field("ux")
+    assert np.abs(ux - exact[:, None]).max() < 1e-6 * exact.max()
+    uy = o.field("uy")
+    stag = q0 * q0 / 4.0 * (-1.0) ** (y + o.steps_done)
+    assert np.abs(uy * stag[:, None] / abs(stag[0]) ** 2 - 1.0).max() < 1e-3
+
+
 @pytest.mark.parametrize("visc", [None, 0.05])
 def test_shear_wave_decays_at_viscous_rate(visc):
     """Eq. 37-41: a shear wave u_x = U sin(k y) decays as exp(-nu k^2 t) with
