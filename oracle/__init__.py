@@ -18,8 +18,8 @@ _SRC = _HERE / "lb3e_oracle.c"
 _LIB = _HERE / "liblb3e_oracle.so"
 
 FIELDS = dict(phi1=0, phi2=1, phi3=2, ux=3, uy=4, p=5, q=6, psi=7, ex=8, ey=9,
-              mu1=10, mu2=11, mu3=12, phinow1=13, phinow2=14, phinow3=15, qtilde=16)
-SETS = dict(g=0, f1=1, f2=2, f3=3, l=4, h=5)
+              mu1=10, mu2=11, mu3=12, phinow1=13, phinow2=14, phinow3=15, qtilde=16, n1=17, n2=18)
+SETS = dict(g=0, f1=1, f2=2, f3=3, l=4, h=5, n1=6, n2=7)
 POP_BASE = 100
 OBS_KEYS = ("mass1", "mass2", "mass3", "charge", "F_phi", "F_E", "F_u", "F_q",
             "max_sum_dev", "D_inner", "D_outer", "nonfinite", "step", "poisson_iters",
@@ -40,6 +40,8 @@ class _Params(C.Structure):
         ("poisson_check_every", C.c_int32), ("poisson_fixed_iter", C.c_int32),
         ("potential_solver", C.c_int32),
         ("debye_kappa2", C.c_double),
+        ("ions", C.c_int32), ("ion_D", C.c_double * 2), ("ion_z", C.c_double * 2),
+        ("ion_beta", C.c_double), ("ion_charge", C.c_double),
     ]
 
 
@@ -74,6 +76,7 @@ def lib():
         L.orc_last_poisson.argtypes = [C.c_void_p, C.POINTER(C.c_int), dp, C.POINTER(C.c_int)]
         L.orc_stencil.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, dp]
         L.orc_lattice.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), dp, C.POINTER(C.c_int)]
+        L.orc_set_ions.argtypes = [C.c_void_p, dp]
         L.orc_step_count.restype = C.c_int64
         L.orc_step_count.argtypes = [C.c_void_p]
         _lib = L
@@ -102,7 +105,9 @@ def make_params(p: dict) -> _Params:
 class Oracle:
     """FP64 reference simulation (one state per instance)."""
 
-    def __init__(self, params: dict, phi, u=None, q=None, noise=None):
+    def __init__(self, params: dict, phi, u=None, q=None, noise=None, ions=None):
+        """`ions`: initial concentrations (2, ny, nx) of the Nernst-Planck species, for
+        parameters with `ions` = 1."""
         self.params = dict(params)
         self.nx, self.ny = int(params["nx"]), int(params["ny"])
         self._keep = [_c64(phi), _c64(u), _c64(q), _c64(noise)]
@@ -112,6 +117,10 @@ class Oracle:
         if not h:
             raise ValueError(f"oracle rejected parameters (status {st.value})")
         self._h = C.c_void_p(h)
+        if ions is not None:
+            n = _c64(ions)
+            if lib().orc_set_ions(self._h, _ptr(n)) != 0:
+                raise ValueError("ion concentrations need parameters with ions = 1")
 
     def __del__(self):
         if getattr(self, "_h", None):

@@ -24,6 +24,15 @@
  * ghosts;  electrodes applied by anti-bounce-back of the potential populations;
  * potential iterations stopped on the relative increments of the potential and
  * of the first moment of h (which carries the field).
+ *
+ * Optional ion transport (Eq. 52, the electro-osmotic validation of Section 5.1):
+ * two species with concentrations n_i obey the Nernst-Planck equation.  Each is
+ * carried by its own D2Q9 population set with the structure of the charge scheme of
+ * Eq. 48-50: equilibrium w_j n_i (1 + c_j . v_i / cs2) with the drift velocity
+ * v_i = u + z_i beta D_i E (advection plus migration along E), the same first-order
+ * d/dt(n_i v_i) correction T_j, relaxation tau_i = 1/2 + D_i/cs2, and plain
+ * bounce-back (no flux) at walls.  The charge is then q = e_q sum_i z_i n_i and
+ * replaces the transported charge of Eq. 46-50.
  */
 #include <math.h>
 #include <stdint.h>
@@ -64,11 +73,16 @@ typedef struct orc_params {
                                   (Section 5.1): the charge is the linearised Boltzmann
                                   (Debye-Hueckel) response q = -eps kappa^2 psi instead of
                                   the transported charge; 0: the method as stated */
+    int32_t ions;              /* 1: two Nernst-Planck ion species carry the charge (Eq. 52) */
+    double ion_D[2];           /* diffusivities D_i (lattice units) */
+    double ion_z[2];           /* valences z_i */
+    double ion_beta;           /* e / (k_B T) in lattice units: the inverse thermal voltage */
+    double ion_charge;         /* charge per unit concentration: q = ion_charge sum_i z_i n_i */
 } orc_params;
 
 enum { F_PHI1 = 0, F_PHI2, F_PHI3, F_UX, F_UY, F_P, F_Q, F_PSI, F_EX, F_EY,
-       F_MU1, F_MU2, F_MU3, F_PHINOW1, F_PHINOW2, F_PHINOW3, F_QTILDE, F_NFIELDS };
-enum { POP_BASE = 100 }; /* POP_BASE + 9*set + j, sets: g, f1, f2, f3, l, h */
+       F_MU1, F_MU2, F_MU3, F_PHINOW1, F_PHINOW2, F_PHINOW3, F_QTILDE, F_N1, F_N2, F_NFIELDS };
+enum { POP_BASE = 100 }; /* POP_BASE + 9*set + j, sets: g, f1, f2, f3, l, h, n1, n2 */
 
 typedef struct orc_state {
     orc_params p;
@@ -81,6 +95,9 @@ typedef struct orc_state {
     double *phi, *qt, *q, *rho, *sig, *eps, *lap, *geps, *gsig, *grho;
     double *E, *psi, *mu, *gmu, *F, *u, *pr, *R;
     double *prev_phiu, *prev_qu;  /* (phi_i u)^{n-1}, (q u)^{n-1} */
+    double *ion, *ions_s;         /* ion populations n^i_j [18N] and post-collision scratch */
+    double *nion, *prev_nv;       /* n_i [2N] of the step, (n_i v_i)^{n-1} [4N] */
+    double tau_ion[2];
     double *psi_prev, *J_prev;    /* psi and J at the previous pseudo-iteration */
     int64_t step;
     int last_iters;
@@ -528,6 +545,53 @@ static void collide_and_stream(orc_state* s, int first) {
     stream(s, s->ls, s->l, 0);
 }
 
+/* Ion moments n_i = sum_j n^i_j and the charge they carry, q = e_q sum_i z_i n_i. */
+static void ion_charge_from_populations(orc_state* s) {
+    const int N = s->N;
+    for (int c = 0; c < N; ++c) {
+        double q = 0.0;
+        for (int i = 0; i < 2; ++i) {
+            double a = 0.0;
+            for (int j = 0; j < 9; ++j) a += s->ion[(9 * i + j) * N + c];
+            s->nion[i * N + c] = a;
+            q += s->p.ion_z[i] * a;
+        }
+        s->q[c] = s->p.ion_charge * q;
+    }
+}
+
+/* drift velocity of species i at cell c: v_i = u + z_i beta D_i E */
+static void ion_velocity(const orc_state* s, int i, int c, double* vx, double* vy) {
+    double m = s->p.ion_z[i] * s->p.ion_beta * s->p.ion_D[i];
+    *vx = s->u[c] + m * s->E[c];
+    *vy = s->u[s->N + c] + m * s->E[s->N + c];
+}
+
+/* Nernst-Planck populations (Eq. 52): collide with the u^n and E^n of this step,
+ * then stream with bounce-back at walls. */
+static void ions_collide_and_stream(orc_state* s, int first) {
+    const int N = s->N;
+    for (int i = 0; i < 2; ++i) {
+        const double ti = s->tau_ion[i];
+        for (int c = 0; c < N; ++c) {
+            double n = s->nion[i * N + c], vx, vy;
+            ion_velocity(s, i, c, &vx, &vy);
+            double dx = first ? 0.0 : n * vx - s->prev_nv[(2 * i) * N + c];
+            double dy = first ? 0.0 : n * vy - s->prev_nv[(2 * i + 1) * N + c];
+            for (int j = 0; j < 9; ++j) {
+                double cv = CX[j] * vx + CY[j] * vy;
+                double neq = W[j] * n * (1.0 + cv / CS2);
+                double Tj = (1.0 - 1.0 / (2.0 * ti)) * W[j] * (CX[j] * dx + CY[j] * dy) / CS2;
+                double nj = s->ion[(9 * i + j) * N + c];
+                s->ions_s[(9 * i + j) * N + c] = nj - (nj - neq) / ti + Tj;
+            }
+            s->prev_nv[(2 * i) * N + c] = n * vx;
+            s->prev_nv[(2 * i + 1) * N + c] = n * vy;
+        }
+        stream(s, s->ions_s + 9 * i * N, s->ion + 9 * i * N, 0);
+    }
+}
+
 static void one_step(orc_state* s) {
     const int nx = s->p.nx, ny = s->p.ny, N = s->N;
     const int first = s->step == 0;
@@ -544,8 +608,9 @@ static void one_step(orc_state* s) {
     }
     /* S2, S3 */
     properties_and_stencils(s);
+    if (s->p.ions) ion_charge_from_populations(s);
     /* S4: q = sum l + R/2 with R linear in q, field of the previous step */
-    for (int c = 0; c < N; ++c) {
+    for (int c = 0; c < N && !s->p.ions; ++c) {
         double r = s->sig[c] / s->eps[c];
         double Ex = s->E[c], Ey = s->E[N + c];
         double src = r * (s->geps[c] * Ex + s->geps[N + c] * Ey) - (s->gsig[c] * Ex + s->gsig[N + c] * Ey);
@@ -599,6 +664,7 @@ static void one_step(orc_state* s) {
     flow_moments(s);
     /* S10-S14 */
     collide_and_stream(s, first);
+    if (s->p.ions) ions_collide_and_stream(s, first);
     for (int c = 0; c < N; ++c) {
         for (int i = 0; i < 3; ++i) {
             s->prev_phiu[(2 * i) * N + c] = s->phi[i * N + c] * s->u[c];
@@ -615,7 +681,8 @@ void orc_destroy(orc_state* s) {
     if (!s) return;
     double* bufs[] = {s->g, s->f, s->l, s->h, s->gs, s->fs, s->ls, s->hs, s->phi, s->qt, s->q, s->rho,
                       s->sig, s->eps, s->lap, s->geps, s->gsig, s->grho, s->E, s->psi, s->mu, s->gmu,
-                      s->F, s->u, s->pr, s->R, s->prev_phiu, s->prev_qu, s->psi_prev, s->J_prev};
+                      s->F, s->u, s->pr, s->R, s->prev_phiu, s->prev_qu, s->psi_prev, s->J_prev,
+                      s->ion, s->ions_s, s->nion, s->prev_nv};
     for (size_t k = 0; k < sizeof(bufs) / sizeof(bufs[0]); ++k) free(bufs[k]);
     free(s);
 }
@@ -630,6 +697,8 @@ orc_state* orc_create(const orc_params* p, const double* phi_init, const double*
         return NULL;
     for (int i = 0; i < 3; ++i)
         if (!(p->rho[i] > 0) || !(p->eps[i] > 0) || p->sigma[i] < 0) return NULL;
+    if (p->ions != 0 && (p->ions != 1 || !(p->ion_D[0] > 0) || !(p->ion_D[1] > 0) || p->debye_kappa2 > 0.0))
+        return NULL;
     double lam[3] = {p->gamma12 + p->gamma13 - p->gamma23,   /* Eq. 9 */
                      p->gamma12 + p->gamma23 - p->gamma13,
                      p->gamma13 + p->gamma23 - p->gamma12};
@@ -653,7 +722,10 @@ orc_state* orc_create(const orc_params* p, const double* phi_init, const double*
     s->gmu = alloc0(6 * (size_t)N); s->F = alloc0(2 * (size_t)N); s->u = alloc0(2 * (size_t)N); s->pr = alloc0(N);
     s->R = alloc0(N); s->prev_phiu = alloc0(6 * (size_t)N); s->prev_qu = alloc0(2 * (size_t)N); s->psi_prev = alloc0(N);
     s->J_prev = alloc0(2 * (size_t)N);
-    if (!s->J_prev) { orc_destroy(s); return NULL; }
+    s->ion = alloc0(18 * (size_t)N); s->ions_s = alloc0(18 * (size_t)N); s->nion = alloc0(2 * (size_t)N);
+    s->prev_nv = alloc0(4 * (size_t)N);
+    if (!s->J_prev || !s->prev_nv) { orc_destroy(s); return NULL; }
+    for (int i = 0; i < 2; ++i) s->tau_ion[i] = 0.5 + p->ion_D[i] / CS2;
 
     memcpy(s->phi, phi_init, 3 * (size_t)N * sizeof(double));
     if (u_init) memcpy(s->u, u_init, 2 * (size_t)N * sizeof(double));
@@ -713,6 +785,38 @@ orc_state* orc_create(const orc_params* p, const double* phi_init, const double*
     return s;
 }
 
+/* Start the ion species from the concentrations n_init[2N] (species-major): the
+ * charge they carry is set, the potential solved for it (as at creation) and each
+ * ion set put at its equilibrium with the stored u and that field.  Returns -1
+ * when the state has no ion transport, -2 after the first step. */
+int orc_set_ions(orc_state* s, const double* n_init) {
+    const int N = s->N;
+    if (!s->p.ions) return -1;
+    if (s->step != 0) return -2;
+    memcpy(s->nion, n_init, 2 * (size_t)N * sizeof(double));
+    for (int c = 0; c < N; ++c)
+        s->q[c] = s->p.ion_charge * (s->p.ion_z[0] * s->nion[c] + s->p.ion_z[1] * s->nion[N + c]);
+    if (s->p.electric && s->p.potential_solver == 1) {
+        s->last_iters = fd_solve(s, &s->last_res);
+        s->last_converged = 1;
+        fd_fields(s);
+    } else if (s->p.electric) {
+        int conv;
+        s->last_iters = poisson_solve(s, s->p.poisson_tol, s->p.poisson_max_iter, s->p.poisson_fixed_iter,
+                                      s->p.poisson_check_every, &s->last_res, &conv);
+        s->last_converged = conv;
+        potential_fields(s);
+    }
+    for (int i = 0; i < 2; ++i)
+        for (int c = 0; c < N; ++c) {
+            double n = s->nion[i * N + c], vx, vy;
+            ion_velocity(s, i, c, &vx, &vy);
+            for (int j = 0; j < 9; ++j)
+                s->ion[(9 * i + j) * N + c] = W[j] * n * (1.0 + (CX[j] * vx + CY[j] * vy) / CS2);
+        }
+    return 0;
+}
+
 int orc_step(orc_state* s, int nsteps) {
     for (int k = 0; k < nsteps; ++k) one_step(s);
     return 0;
@@ -759,6 +863,15 @@ int orc_get_field(const orc_state* s, int id, double* out) {
             }
             return 0;
         }
+        case F_N1: case F_N2: {
+            int i = id - F_N1;
+            for (int c = 0; c < N; ++c) {
+                double a = 0.0;
+                for (int j = 0; j < 9; ++j) a += s->ion[(9 * i + j) * N + c];
+                out[c] = a;
+            }
+            return 0;
+        }
         case F_QTILDE:
             for (int c = 0; c < N; ++c) {
                 double a = 0.0;
@@ -768,9 +881,10 @@ int orc_get_field(const orc_state* s, int id, double* out) {
             return 0;
         default: break;
     }
-    if (!src && id >= POP_BASE && id < POP_BASE + 54) {
+    if (!src && id >= POP_BASE && id < POP_BASE + 72) {
         int set = (id - POP_BASE) / 9, j = (id - POP_BASE) % 9;
-        const double* base = set == 0 ? s->g : set <= 3 ? s->f + 9 * (set - 1) * (size_t)N : set == 4 ? s->l : s->h;
+        const double* base = set == 0 ? s->g : set <= 3 ? s->f + 9 * (set - 1) * (size_t)N : set == 4 ? s->l
+                           : set == 5 ? s->h : s->ion + 9 * (set - 6) * (size_t)N;
         src = base + j * N;
     }
     if (!src) return -1;

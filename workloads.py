@@ -46,6 +46,11 @@ PARAM_DEFAULTS = dict(
     potential_solver=0,          # 0 the LB pseudo-time solve of the paper; 1 multigrid on its FD form
     tangent_param=(-1, -1, -1),  # GPU tangent builds: parameter per tangent direction
     debye_kappa2=0.0,            # oracle only: > 0 replaces the charge by -eps kappa^2 psi (EOF check)
+    ions=0,                      # 1: two Nernst-Planck ion species carry the charge (Eq. 52)
+    ion_D=(0.05, 0.05),          # ion diffusivities (lattice units)
+    ion_z=(1.0, -1.0),           # valences
+    ion_beta=1.0,                # e / (k_B T): inverse thermal voltage
+    ion_charge=1.0,              # charge per unit concentration
 )
 
 
