@@ -43,6 +43,12 @@ STEP_BYTES = {0: 960, 1: 480, 2: 300}                        # whole step withou
 # coefficients: 4 x 24 B), residual (24 B), restriction (5 B), prolongation (9 B),
 # FP64 correction (20 B) -- times 4/3 for the coarser levels
 MG_VCYCLE_BYTES = 48 + round(170 * 4 / 3)
+# Nernst-Planck ions per cell and step, in units of the compute type: k_ion_moments
+# reads 18 populations and writes n_1, n_2, q (21); k_ions reads 18 populations,
+# n_i, u, E and (n_i v_i)^{n-1} (28) and writes 18 populations and (n_i v_i)^n (22)
+ION_WORDS = {"k_ion_moments": 21, "k_ions": 50}
+# with ions on, k_fused also writes u, p and mu (6 planes) every step
+FUSED_DIAG_WORDS = 6
 
 
 def parse():
@@ -51,7 +57,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lb3e", choices=["lb3e", "reference"])
-    ap.add_argument("--workload", default="deformation", choices=["deformation", "sweep", "adjoint", "regimes"],
+    ap.add_argument("--workload", default="deformation",
+                    choices=["deformation", "sweep", "adjoint", "regimes", "eof"],
                     help="deformation: the 4096^2 lattice (default); sweep: 256 lattices in one batch; "
                          "adjoint: cost of the three parameter derivatives relative to a forward step")
     ap.add_argument("--precision", type=int, default=1, help="0 fp64, 1 fp32, 2 fp32 + fp16-stored populations")
@@ -80,10 +87,18 @@ def peaks():
     return 6400.0, "fallback"
 
 
+# the files the profiled kernels' device code is compiled from (host sequencing and
+# the ABI layer do not enter it), hashed with the build's flags
+KERNEL_SOURCES = ("lb3e_kernels.cuh", "lb3e_params.cuh", "lb3e_dual.cuh", "lb3e_f32.cu", "lb3e_f64.cu")
+
+
 def kernel_source_hash() -> str:
+    from paper_2608_05787_b300 import build as B
     h = hashlib.sha256()
-    for f in sorted((ROOT / "paper_2608_05787_b300" / "csrc").glob("*")):
-        h.update(f.read_bytes())
+    for name in KERNEL_SOURCES:
+        h.update((ROOT / "paper_2608_05787_b300" / "csrc" / name).read_bytes())
+    common = [a for i, a in enumerate(B.COMMON) if a != "-I" and (i == 0 or B.COMMON[i - 1] != "-I")]
+    h.update(repr((B.ARCH, common, sorted(B.UNITS.items()))).encode())
     return h.hexdigest()[:16]
 
 
@@ -539,6 +554,125 @@ def run_regimes(args):
     print(json.dumps(line), flush=True)
 
 
+def run_eof(args):
+    """The electro-osmotic channel with Nernst-Planck ions (Eq. 52-53; 10240 x 2048,
+    5:1 like the paper's channel): one phase, two ion species started in their
+    double layers, the multigrid potential with the ions' charge every step, the
+    fused flow/phase/charge pass and the ion pass.  MLUPS over the timed steps, the
+    roofline of the dominant kernel class, the ion pass's own bandwidth, an end-to-end
+    run from pinned host fields, and the oracle on a bounded sample."""
+    import torch
+    import paper_2608_05787_b300 as L
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    prec = args.precision
+    cfg = W.config_eof_channel(precision=prec)
+    params = cfg["params"]
+    N = params["nx"] * params["ny"]
+    word = 8 if prec == 0 else 4
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = L.Sim(params, torch.from_numpy(cfg["phi"]).cuda(), ions=torch.from_numpy(cfg["ions"]).cuda(),
+                    stream=stream)
+        sim.step(args.warmup)
+        torch.cuda.synchronize()
+        sim.set_timing(True)
+        l0 = sim.launches
+        it0 = sim.potential_iterations
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(0) as clk:
+            ev0.record(stream)
+            sim.step(args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        launches = sim.launches - l0
+        cycles = sim.potential_iterations - it0
+        kt = sim.kernel_times()
+        sim.set_timing(False)
+        obs = sim.observables()
+        mass = [float(sim.field(k).sum()) for k in ("n1", "n2")]
+    t = ms / 1e3
+    total = N * args.steps
+    hbm, peak_kind = peaks()
+    per_cell = {"fused": FUSED_BYTES[prec] + FUSED_DIAG_WORDS * word, "ions": sum(ION_WORDS.values()) * word,
+                "poisson": MG_VCYCLE_BYTES}
+    gbs = {}
+    for k in ("fused", "ions"):
+        kms, kn = kt[k]
+        if kn:
+            gbs[k] = per_cell[k] * N * args.steps / (kms / 1e3) / 1e9
+    pms, pn = kt["poisson"]
+    if pn and cycles:
+        # per V-cycle and fine cell (the unit of the multigrid figure), over the V-cycle kernels' time
+        gbs["poisson"] = MG_VCYCLE_BYTES * N * cycles / (pms / 1e3) / 1e9
+    dominant = max(("fused", "ions", "poisson"), key=lambda k: kt[k][0])
+    kname = {"fused": "k_fused", "ions": "k_ion_moments + k_ions", "poisson": "multigrid V-cycle kernels"}[dominant]
+    achieved = gbs.get(dominant)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved or 0) / hbm if achieved else None, "traffic": None, "kernel": kname,
+                "peak_kind": f"{peak_kind} copy bandwidth",
+                "algorithmic_bytes_per_cell": per_cell[dominant],
+                "units": ("fine cells x V-cycles" if dominant == "poisson" else "cells x steps"),
+                "other_kernel_gbs": {k: v for k, v in gbs.items() if k != dominant}}
+    kernels = {k: {"launches": kn, "ms_total": kms, "share": kms / max(1e-12, sum(v[0] for v in kt.values()))}
+               for k, (kms, kn) in kt.items() if kn}
+
+    e2e = None
+    if not args.no_e2e:
+        del sim
+        torch.cuda.empty_cache()
+        host_phi = torch.from_numpy(cfg["phi"]).pin_memory()
+        host_ions = torch.from_numpy(cfg["ions"]).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            s2 = L.Sim(params, host_phi, ions=host_ions, stream=stream)
+            for _ in range(args.steps):
+                s2.step(1)
+                s2.observables()
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": total / t_e2e / 1e6, "unit": METRIC,
+               "h2d_bytes_per_step": int(5 * N * 8 / args.steps), "d2h_bytes_per_step": 20 * 8,
+               "includes": "init from pinned host phase and ion fields (with its potential solves) + per-step "
+                           "observables read-back", "seconds": t_e2e}
+        del s2
+
+    cpu = None
+    if not args.no_cpu:
+        try:
+            import oracle
+            cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+            nx, ny, k = 1280, 256, 4
+            c = W.config_eof_channel(nx=nx, ny=ny, precision=0)
+            o = oracle.Oracle(c["params"], c["phi"], ions=c["ions"])
+            t0 = time.perf_counter()
+            o.step(k)
+            dt = (time.perf_counter() - t0) / k
+            cpu = {"value": nx * ny / dt / 1e6, "unit": METRIC, "cores": cores, "kind": "oracle",
+                   "sample": f"{k} steps of the same channel at {nx}x{ny} (kappa h scaled alike) with the oracle's FD "
+                             "potential solve (conjugate gradients); init untimed", "seconds_per_step": dt}
+        except Exception as exc:
+            cpu = {"value": None, "error": repr(exc)}
+
+    line = {"metric": METRIC, "value": total / t / 1e6, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {0: "f64", 1: "f32", 2: "f32 (f16-stored populations)"}[prec],
+            "data": "synthetic (the paper's electro-osmotic channel in lattice units, ions in their double layers)",
+            "config": {"workload": f"electro-osmotic channel with Nernst-Planck ions, {params['nx']}x{params['ny']}",
+                       "kappa_h": 20.0, "potential_solver": "multigrid V-cycles on the FD form",
+                       "poisson_tol": params["poisson_tol"],
+                       "l2": "working set (%.1f GB) exceeds the 126 MB L2; no flush needed" % (
+                           L.workspace_bytes(params) / 1e9), "v_cycles_per_step": cycles / args.steps},
+            "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "observables": {"nonfinite": obs["nonfinite"], "poisson_iters": obs["poisson_iters"],
+                            "poisson_residual": obs["poisson_residual"], "ion_totals": mass}}
+    print(json.dumps(line), flush=True)
+
+
 def run_adjoint(args):
     """Derivative cost on the 256^2 drop under field plus shear: time per step of
     the FP32 tangent build (three parameter directions: E0, eps3, gamma23) over the
@@ -593,6 +727,8 @@ def main():
         run_regimes(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
+    elif args.workload == "eof":
+        run_eof(args)
     else:
         run_lb3e(args)
 

@@ -68,7 +68,10 @@ enum {
     LB3E_FIELD_PHINOW2 = 14,
     LB3E_FIELD_PHINOW3 = 15,
     LB3E_FIELD_QTILDE = 16,  /* sum_j l_j of the current populations */
-    LB3E_FIELD_POP = 100     /* + 9*set + j; sets 0 g, 1-3 f^1..f^3, 4 l, 5 h */
+    LB3E_FIELD_N1 = 17,      /* ion concentrations n_i = sum_j n^i_j of the current */
+    LB3E_FIELD_N2 = 18,      /* ion populations (ions = 1 only) */
+    LB3E_FIELD_POP = 100     /* + 9*set + j; sets 0 g, 1-3 f^1..f^3, 4 l, 5 h,
+                                6-7 the ion species (ions = 1 only) */
 };
 
 /* Largest lattice lb3e_init accepts (45 population planes are addressed with
@@ -118,6 +121,20 @@ typedef struct lb3e_params {
      * the relative residual is <= poisson_tol (at most poisson_max_iter cycles);
      * E is then the Eq. 33 gradient of psi */
     int32_t potential_solver;
+    /* 1: two Nernst-Planck ion species (Eq. 52; Section 5.1's electro-osmotic
+     * check) carry the charge, q = ion_charge * sum_i ion_z[i] n_i, in place of the
+     * closure charge of Eq. 46-50 (whose populations still evolve, unread).  Each
+     * species is a D2Q9 set of the charge scheme's form: equilibrium w_j n_i (1 +
+     * c_j . v_i / cs^2) with v_i = u + ion_z[i] ion_beta ion_D[i] E, the backward-
+     * difference source T_j of d/dt(n_i v_i), tau_i = 1/2 + ion_D[i]/cs^2, bounce-
+     * back at walls.  Concentrations start at 0; set them with lb3e_set_ions.
+     * Precisions 0-2, single lattices (not batches). */
+    int32_t ions;
+    int32_t _pad3;
+    double ion_D[2];              /* diffusivities (> 0 when ions = 1) */
+    double ion_z[2];              /* valences */
+    double ion_beta;              /* e / (k_B T): inverse thermal voltage, lattice units */
+    double ion_charge;            /* charge per unit concentration */
 } lb3e_params;
 
 /* Field id offset of tangent k (1..3) of a field in the tangent builds: field
@@ -176,10 +193,18 @@ int lb3e_observables(lb3e_handle* h, lb3e_observables_t* out);
 int lb3e_get_field(lb3e_handle* h, int32_t field_id, double* dst);
 
 /* Size of a full state snapshot (populations, potential populations, fields,
- * d/dt history, step counter) and save/load to caller memory (host or device). */
+ * d/dt history, ion state when ions = 1, step counter) and save/load to caller
+ * memory (host or device). */
 int lb3e_state_bytes(const lb3e_handle* h, size_t* bytes);
 int lb3e_save_state(lb3e_handle* h, void* dst);
 int lb3e_load_state(lb3e_handle* h, const void* src);
+
+/* Start the Nernst-Planck ion species (ions = 1) from the concentrations n_init
+ * ([2][ny][nx] doubles, host or device; species-major): their charge replaces q,
+ * the potential is solved for it as lb3e_init solves it, and each ion set starts at
+ * its equilibrium with the initial u and that field.  Only before the first step.
+ * Errors: NULL, PARAM (ions = 0, a step already taken, or a tangent build), CUDA. */
+int lb3e_set_ions(lb3e_handle* h, const double* n_init);
 
 /* Number of kernel launches issued since lb3e_init (for launch accounting). */
 int64_t lb3e_launch_count(const lb3e_handle* h);
@@ -210,7 +235,8 @@ enum {
     LB3E_KC_FIELDS = 4,    /* psi and E from the potential populations */
     LB3E_KC_FUSED = 5,     /* fused chemical potential, force, collide and stream */
     LB3E_KC_OTHER = 6,     /* initialisation and conversions */
-    LB3E_KC_COUNT = 7
+    LB3E_KC_IONS = 7,      /* Nernst-Planck ion moments, collision and streaming */
+    LB3E_KC_COUNT = 8
 };
 
 /* Synchronise the stream and return, per kernel class, the summed event time in

@@ -18,14 +18,14 @@ _HERE = Path(__file__).resolve().parent
 LIB_PATH = Path(os.environ.get("LB3E_LIBRARY", _HERE / "liblb3e.so"))
 
 FIELDS = dict(phi1=0, phi2=1, phi3=2, ux=3, uy=4, p=5, q=6, psi=7, ex=8, ey=9,
-              mu1=10, mu2=11, mu3=12, phinow1=13, phinow2=14, phinow3=15, qtilde=16)
-SETS = dict(g=0, f1=1, f2=2, f3=3, l=4, h=5)
+              mu1=10, mu2=11, mu3=12, phinow1=13, phinow2=14, phinow3=15, qtilde=16, n1=17, n2=18)
+SETS = dict(g=0, f1=1, f2=2, f3=3, l=4, h=5, n1=6, n2=7)
 POP_BASE = 100
 PRECISIONS = {0: "f64", 1: "f32", 2: "f32-compute/f16-store", 3: "f32 + 3 tangents", 4: "f64 + 1 tangent"}
 TANGENT = 1000
 TANGENT_PARAMS = dict(V_top=0, eps1=1, eps2=2, eps3=3, gamma12=4, gamma13=5, gamma23=6)
 
-KERNEL_CLASSES = ("moments", "prologue", "poisson", "reduce", "fields", "fused", "other")
+KERNEL_CLASSES = ("moments", "prologue", "poisson", "reduce", "fields", "fused", "other", "ions")
 
 
 class Params(C.Structure):
@@ -44,7 +44,11 @@ class Params(C.Structure):
         ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int32),
         ("poisson_check_every", C.c_int32), ("poisson_fixed_iter", C.c_int32), ("_pad2", C.c_int32),
         ("tangent_param", C.c_int32 * 3), ("potential_solver", C.c_int32),
+        ("ions", C.c_int32), ("_pad3", C.c_int32), ("ion_D", C.c_double * 2), ("ion_z", C.c_double * 2),
+        ("ion_beta", C.c_double), ("ion_charge", C.c_double),
     ]
+    # Nernst-Planck ion transport is off unless the dict asks for it
+    _ION_DEFAULTS = dict(ions=0, ion_D=(0.0, 0.0), ion_z=(1.0, -1.0), ion_beta=1.0, ion_charge=0.0)
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
@@ -56,7 +60,7 @@ class Params(C.Structure):
         for name, ctype in cls._fields_:
             if name.startswith("_pad"):
                 continue
-            v = d[name]
+            v = d[name] if name in d or name not in cls._ION_DEFAULTS else cls._ION_DEFAULTS[name]
             if hasattr(ctype, "_length_"):
                 conv = int if ctype._type_ is C.c_int32 else float
                 getattr(s, name)[:] = [conv(a) for a in v]
@@ -117,6 +121,7 @@ def lib() -> C.CDLL:
         L.lb3e_potential_iterations.argtypes = [vp]
         L.lb3e_set_timing.argtypes = [vp, C.c_int32]
         L.lb3e_set_potential_chunk.argtypes = [vp, C.c_int32]
+        L.lb3e_set_ions.argtypes = [vp, vp]
         L.lb3e_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64)]
         L.lb3e_observables_noalloc.argtypes = [C.POINTER(Params), vp, vp, vp, vp, vp, C.POINTER(Observables)]
         L.lb3e_batch_workspace_bytes.argtypes = [C.POINTER(Params), C.c_int32, C.POINTER(C.c_size_t)]
@@ -191,7 +196,9 @@ class Sim:
     may be host numpy arrays or CUDA tensors (float64, ``[.., ny, nx]``).
     """
 
-    def __init__(self, params: dict, phi, u=None, q=None, noise=None, stream=None, device=None):
+    def __init__(self, params: dict, phi, u=None, q=None, noise=None, stream=None, device=None, ions=None):
+        """``ions``: initial concentrations [2, ny, nx] of the Nernst-Planck species
+        (parameters with ``ions`` = 1), set through ``lb3e_set_ions``."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("lb3e needs a CUDA device (there is no CPU fallback)")
@@ -207,6 +214,9 @@ class Sim:
         _check("lb3e_init", lib().lb3e_init(C.byref(self._p), self.workspace.data_ptr(), nbytes,
                                             *(k[0] for k in keep), self.stream.cuda_stream, C.byref(h)))
         self._h = h
+        if ions is not None:
+            addr, _keep = _addr(ions)
+            _check("lb3e_set_ions", lib().lb3e_set_ions(self._h, addr))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -41,6 +41,13 @@ int validate(const lb3e_params* p) {
                            p->poisson_tol};
     for (double v : vals)
         if (!std::isfinite(v)) return LB3E_ERR_PARAM;
+    if (p->ions < 0 || p->ions > 1) return LB3E_ERR_PARAM;
+    if (p->ions) {  // Nernst-Planck ions: plain precisions, positive diffusivities
+        if (p->precision > 2 || !(p->ion_D[0] > 0) || !(p->ion_D[1] > 0)) return LB3E_ERR_PARAM;
+        const double iv[] = {p->ion_z[0], p->ion_z[1], p->ion_beta, p->ion_charge};
+        for (double v : iv)
+            if (!std::isfinite(v)) return LB3E_ERR_PARAM;
+    }
     return LB3E_OK;
 }
 
@@ -61,7 +68,7 @@ int validate_batch(const lb3e_params* ps, int32_t n) {
     int iters = -1;
     for (int i = 0; i < n; ++i) {
         TRY(validate(ps + i));
-        if (ps[i].precision != ps[0].precision || ps[i].precision > 2 || ps[i].potential_solver != 0)
+        if (ps[i].precision != ps[0].precision || ps[i].precision > 2 || ps[i].potential_solver != 0 || ps[i].ions)
             return LB3E_ERR_PARAM;
         if (ps[i].electric) {
             if (ps[i].poisson_fixed_iter <= 0) return LB3E_ERR_PARAM;
@@ -177,6 +184,11 @@ int64_t lb3e_potential_iterations(const lb3e_handle* h) { return h ? h->sim->pot
 int lb3e_set_potential_chunk(lb3e_handle* h, int32_t iterations_per_launch) {
     if (!h) return LB3E_ERR_NULL;
     return h->sim->set_chunk(iterations_per_launch);
+}
+
+int lb3e_set_ions(lb3e_handle* h, const double* n_init) {
+    if (!h || !n_init) return LB3E_ERR_NULL;
+    return h->sim->set_ions(n_init);
 }
 
 int lb3e_set_timing(lb3e_handle* h, int32_t enable) {

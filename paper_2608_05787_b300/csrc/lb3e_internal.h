@@ -22,7 +22,8 @@ namespace lb3e {
 struct DevParams;
 
 // kernel classes for the timing facility (lb3e_kernel_times)
-enum KernelClass { KC_MOMENTS = 0, KC_PROLOGUE, KC_POISSON, KC_REDUCE, KC_FIELDS, KC_FUSED, KC_OTHER, KC_COUNT };
+enum KernelClass { KC_MOMENTS = 0, KC_PROLOGUE, KC_POISSON, KC_REDUCE, KC_FIELDS, KC_FUSED, KC_OTHER, KC_IONS,
+                   KC_COUNT };
 
 // CUDA-event timing of kernel launches on the simulation's stream (off by default)
 struct LaunchTimer {
@@ -78,6 +79,7 @@ struct SimBase {
     virtual int kernel_times(double* ms, int64_t* counts) = 0;
     virtual int64_t potential_iterations() const = 0;
     virtual int set_chunk(int k) = 0;
+    virtual int set_ions(const double* n) = 0;
     int64_t launches = 0;
     LaunchTimer timer;
 };

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "lb3e_internal.h"
+#include "lb3e_ions.cuh"
 #include "lb3e_kernels.cuh"
 #include "lb3e_mg.cuh"
 
@@ -25,7 +26,8 @@ class Sim final : public SimBase {
   public:
     // workspace layout (byte offsets), computed identically by bytes() and the constructor
     struct Layout {
-        size_t pop[2], h[2], phi, qt, q, eps, E, prev, diag, psi_prev, partial, result, stage, mg, total;
+        size_t pop[2], h[2], phi, qt, q, eps, E, prev, diag, psi_prev, partial, result, stage, mg, ion[2], ionst,
+            total;
     };
     static Layout layout(const lb3e_params& p) {
         const size_t N = (size_t)p.nx * p.ny;
@@ -66,6 +68,12 @@ class Sim final : public SimBase {
             }
         }
         L.mg = take(mg);
+        // Nernst-Planck ions: 2 x 18 population planes, then n_i (2 planes) and
+        // (n_i v_i)^{n-1} (4 planes) in one block
+        const size_t ni = p.ions ? N : 0;
+        L.ion[0] = take(18 * ni * sizeof(R));
+        L.ion[1] = take(18 * ni * sizeof(R));
+        L.ionst = take(6 * ni * sizeof(R));
         L.total = o;
         return L;
     }
@@ -90,6 +98,13 @@ class Sim final : public SimBase {
         d_.stage = reinterpret_cast<double*>(b + L_.stage);
         base_ = b;
         N_ = (size_t)prm.nx * prm.ny;
+        if (prm.ions) {
+            ion_[0] = reinterpret_cast<R*>(b + L_.ion[0]);
+            ion_[1] = reinterpret_cast<R*>(b + L_.ion[1]);
+            nion_ = reinterpret_cast<R*>(b + L_.ionst);
+            ionprev_ = nion_ + 2 * N_;
+            ip_ = make_ion_params(prm);
+        }
         dp_ = make_dev_params(prm);
         grid2_ = dim3((prm.nx + TX - 1) / TX, (prm.ny + TY - 1) / TY);
         nblk_ = (int)(grid2_.x * grid2_.y);
@@ -199,8 +214,16 @@ class Sim final : public SimBase {
             k_moments<R, S><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.pop[cur_], d_.phi, d_.phi, d_.qt);
             TRY(launched());
             timer.begin(stream_, KC_PROLOGUE);
-            k_prologue<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.phi, d_.qt, d_.E, d_.q, d_.eps, 1);
+            k_prologue<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.phi, d_.qt, d_.E, d_.q, d_.eps,
+                                                                p_.ions ? 0 : 1);
             TRY(launched());
+            if constexpr (!is_dual<R>::value) {
+                if (p_.ions) {  // the charge the ions carry replaces the closure charge
+                    timer.begin(stream_, KC_IONS);
+                    k_ion_moments<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(p_.nx, p_.ny, ion_[icur_], nion_, d_.q, ip_);
+                    TRY(launched());
+                }
+            }
             if (p_.electric && !mg_.empty()) {
                 TRY(mg_solve(p_.poisson_tol, p_.poisson_max_iter));
             } else if (p_.electric) {
@@ -208,8 +231,19 @@ class Sim final : public SimBase {
             }
             timer.begin(stream_, KC_FUSED);
             k_fused<R, S><<<grid2_, dim3(TX, TY), fused_dyn_smem<R, S>(), stream_>>>(dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q,
-                                                                 d_.E, d_.prev, d_.diag, step_ == 0 ? 1 : 0, last);
+                                                                 d_.E, d_.prev, d_.diag, step_ == 0 ? 1 : 0,
+                                                                 (last || p_.ions) ? 1 : 0);
             TRY(launched());
+            if constexpr (!is_dual<R>::value) {
+                if (p_.ions) {  // with the u^n (diag) and E^n of this step
+                    timer.begin(stream_, KC_IONS);
+                    k_ions<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(p_.nx, p_.ny, p_.bc_y, ion_[icur_], ion_[icur_ ^ 1],
+                                                                    nion_, d_.diag, d_.E, ionprev_, ip_,
+                                                                    step_ == 0 ? 1 : 0);
+                    TRY(launched());
+                    icur_ ^= 1;
+                }
+            }
             cur_ ^= 1;
             ++step_;
         }
@@ -226,6 +260,29 @@ class Sim final : public SimBase {
         if (res) *res = last_res_;
         TRY(sync());
         return last_conv_ ? LB3E_OK : LB3E_ERR_NOT_CONVERGED;
+    }
+
+    int set_ions(const double* n) override {
+        if constexpr (is_dual<R>::value) {
+            return LB3E_ERR_PARAM;
+        } else {
+            if (!p_.ions || step_ != 0) return LB3E_ERR_PARAM;
+            TRY(upload(n, 2 * N_, nion_));
+            timer.begin(stream_, KC_OTHER);
+            k_ion_charge<R><<<blocks1(N_), 256, 0, stream_>>>(N_, nion_, d_.q, ip_);
+            TRY(launched());
+            if (p_.electric && !mg_.empty()) {
+                TRY(mg_solve(p_.poisson_tol, p_.poisson_max_iter));
+            } else if (p_.electric) {
+                TRY(poisson(p_.poisson_tol, p_.poisson_max_iter, p_.poisson_fixed_iter, p_.poisson_check_every));
+            }
+            icur_ = 0;
+            timer.begin(stream_, KC_OTHER);
+            k_init_ions<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(p_.nx, p_.ny, ion_[0], nion_, d_.diag, d_.E, ip_);
+            TRY(launched());
+            TRY(memset_async(ionprev_, 4 * N_ * sizeof(R)));
+            return sync();
+        }
     }
 
     int observables(lb3e_observables_t* o) override {
@@ -313,7 +370,29 @@ class Sim final : public SimBase {
                 TRY(launched());
                 return copy_out(dst, d_.stage);
             }
+            case LB3E_FIELD_N1: case LB3E_FIELD_N2:
+                if constexpr (is_dual<R>::value) {
+                    return LB3E_ERR_FIELD;
+                } else {
+                    if (!p_.ions || comp) return LB3E_ERR_FIELD;
+                    // moments of the current ion populations into scratch after the output plane
+                    R* tmp = reinterpret_cast<R*>(d_.stage + N_);
+                    timer.begin(stream_, KC_MOMENTS);
+                    k_ion_moments<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(p_.nx, p_.ny, ion_[icur_], tmp, tmp + 2 * N_, ip_);
+                    TRY(launched());
+                    timer.begin(stream_, KC_OTHER);
+                    k_to_f64<R><<<blocks1(N_), 256, 0, stream_>>>(d_.stage, tmp + (id - LB3E_FIELD_N1) * N_, N_);
+                    TRY(launched());
+                    return copy_out(dst, d_.stage);
+                }
             default: break;
+        }
+        if (!src && id >= LB3E_FIELD_POP + 54 && id < LB3E_FIELD_POP + 72) {
+            if (!p_.ions || comp) return LB3E_ERR_FIELD;
+            timer.begin(stream_, KC_OTHER);
+            k_to_f64<R><<<blocks1(N_), 256, 0, stream_>>>(d_.stage, ion_[icur_] + (size_t)(id - LB3E_FIELD_POP - 54) * N_, N_);
+            TRY(launched());
+            return copy_out(dst, d_.stage);
         }
         if (!src && id >= LB3E_FIELD_POP && id < LB3E_FIELD_POP + 54) {
             if (comp) return LB3E_ERR_FIELD;
@@ -337,7 +416,7 @@ class Sim final : public SimBase {
 
     // snapshot: current pops, current h, then phi..psi_prev fields, then a trailer
     size_t state_bytes() const override {
-        return 45 * N_ * sizeof(S) + 9 * N_ * sizeof(R) + fields_bytes() + 4 * sizeof(int64_t);
+        return 45 * N_ * sizeof(S) + 9 * N_ * sizeof(R) + fields_bytes() + ion_bytes() + 4 * sizeof(int64_t);
     }
     int save(void* dst) override {
         char* o = static_cast<char*>(dst);
@@ -347,6 +426,12 @@ class Sim final : public SimBase {
         o += 9 * N_ * sizeof(R);
         TRY(copy(o, base_ + L_.phi, fields_bytes()));
         o += fields_bytes();
+        if (p_.ions) {  // current ion populations, then n_i and (n_i v_i)^{n-1}
+            TRY(copy(o, ion_[icur_], 18 * N_ * sizeof(R)));
+            o += 18 * N_ * sizeof(R);
+            TRY(copy(o, nion_, 6 * N_ * sizeof(R)));
+            o += 6 * N_ * sizeof(R);
+        }
         int64_t trailer[4] = {step_, last_iters_, last_conv_, 0};
         std::memcpy(&trailer[3], &last_res_, sizeof(double));
         TRY(copy(o, trailer, sizeof trailer));
@@ -362,6 +447,13 @@ class Sim final : public SimBase {
         s += 9 * N_ * sizeof(R);
         TRY(copy(base_ + L_.phi, s, fields_bytes()));
         s += fields_bytes();
+        if (p_.ions) {
+            icur_ = 0;
+            TRY(copy(ion_[0], s, 18 * N_ * sizeof(R)));
+            s += 18 * N_ * sizeof(R);
+            TRY(copy(nion_, s, 6 * N_ * sizeof(R)));
+            s += 6 * N_ * sizeof(R);
+        }
         int64_t trailer[4];
         TRY(copy(trailer, s, sizeof trailer));
         TRY(sync());
@@ -405,6 +497,7 @@ class Sim final : public SimBase {
 
   private:
     size_t fields_bytes() const { return L_.psi_prev + align256(3 * N_ * sizeof(R)) - L_.phi; }
+    size_t ion_bytes() const { return p_.ions ? 24 * N_ * sizeof(R) : 0; }
     static unsigned blocks1(size_t n) { return (unsigned)((n + 255) / 256); }
     int launched() {
         ++launches;
@@ -667,6 +760,11 @@ class Sim final : public SimBase {
     int chunk_ = 4;  // pseudo-iterations per potential launch (4: fastest measured on a 4096^2 lattice)
     std::vector<MGLevel> mg_;
     std::vector<MGLevelF> mgf_;
+    R* ion_[2] = {nullptr, nullptr};  // Nernst-Planck populations (ions = 1)
+    R* nion_ = nullptr;               // n_i of the step (2 planes), then (n_i v_i)^{n-1} (4 planes)
+    R* ionprev_ = nullptr;
+    int icur_ = 0;
+    IonParams ip_{};
 
   public:
     int64_t poisson_iters_run_ = 0;  // pseudo-iterations executed (all solves)

@@ -58,7 +58,9 @@ def test_struct_layouts_match_the_header(tmp_path):
 
 @pytest.mark.parametrize("bad", [dict(tau_f=0.5), dict(nx=1), dict(bc_y=3), dict(precision=7),
                                  dict(gamma23=3e-3), dict(eps=(1.0, 0.0, 2.0)), dict(sigma=(-1, 0, 0)),
-                                 dict(inner_phase=0), dict(V_top=float("nan")), dict(nx=2, ny=65535 * 8 + 1)])
+                                 dict(inner_phase=0), dict(V_top=float("nan")), dict(nx=2, ny=65535 * 8 + 1),
+                                 dict(ions=2), dict(ions=1, ion_D=(0.0, 0.1)), dict(ions=1, precision=3),
+                                 dict(ions=1, ion_beta=float("inf"))])
 def test_invalid_parameters_rejected(bad):
     with pytest.raises(L.LB3EError) as e:
         L.workspace_bytes(W.params(**bad))
@@ -71,3 +73,22 @@ def test_workspace_scales_with_precision():
     b32 = L.workspace_bytes(dict(p, precision=1))
     b16 = L.workspace_bytes(dict(p, precision=2))
     assert b64 > b32 > b16 > 256 * 128 * 45 * 2 * 2
+
+
+def test_ion_transport_adds_its_planes_to_the_workspace():
+    """ions = 1 adds 2 x 18 population planes and 6 state planes (n_i, (n_i v_i)^{n-1})."""
+    p = W.params(nx=256, ny=128)
+    for prec, size in ((0, 8), (1, 4), (2, 4)):
+        base = L.workspace_bytes(dict(p, precision=prec))
+        ions = L.workspace_bytes(dict(p, precision=prec, ions=1))
+        assert ions - base >= 42 * 256 * 128 * size
+        assert ions - base < 42 * 256 * 128 * size + 3 * 256
+
+
+def test_batches_refuse_ion_transport():
+    p = W.params(nx=32, ny=32, poisson_fixed_iter=4, ions=1, ion_D=(0.1, 0.1))
+    ps = (L.Params * 2)(L.Params.from_dict(p), L.Params.from_dict(p))
+    nb = C.c_size_t(0)
+    assert L.lib().lb3e_batch_workspace_bytes(ps, 2, C.byref(nb)) == -1
+    ps[0].ions = ps[1].ions = 0
+    assert L.lib().lb3e_batch_workspace_bytes(ps, 2, C.byref(nb)) == 0 and nb.value > 0

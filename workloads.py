@@ -118,6 +118,25 @@ def noise(nx: int, ny: int, amp: float, seed: int = SEED) -> np.ndarray:
     return rng.uniform(-amp, amp, size=(5, 9, ny, nx))
 
 
+def ion_concentrations(nx: int, ny: int, n0: float = 1.0, amp: float = 0.0, seed: int = SEED) -> np.ndarray:
+    """Concentrations [2, ny, nx] of two ion species: n0 (1 + U(-amp, amp)), drawn in
+    order species, y, x."""
+    rng = np.random.default_rng(seed)
+    return n0 * (1.0 + rng.uniform(-amp, amp, size=(2, ny, nx)))
+
+
+def debye_layers(nx: int, ny: int, zeta: float, kappa: float, beta: float, n0: float = 1.0,
+                 z=(1.0, -1.0)) -> np.ndarray:
+    """Concentrations [2, ny, nx] of a symmetric electrolyte in the Debye-Hueckel double
+    layers of a channel whose walls (y = -1/2, ny - 1/2) sit at the zeta potential:
+    n_i = n0 exp(-z_i beta psi(y)) with psi = zeta cosh(kappa y') / cosh(kappa h), y'
+    measured from the mid-plane, h = ny / 2 (Eq. 53)."""
+    h = ny / 2
+    yc = np.arange(ny) + 0.5 - h
+    psi = zeta * np.cosh(kappa * yc) / np.cosh(kappa * h)
+    return np.stack([np.repeat(n0 * np.exp(-zi * beta * psi)[:, None], nx, axis=1) for zi in z])
+
+
 # ---------------------------------------------------------------------------
 # The five workloads.  Sizes and parameters are the stated ones; where a value is
 # left open, the reading used is the one listed in the design notes.
@@ -283,3 +302,23 @@ def config_shear_regimes(ca_e=(0.2, 0.4, 0.6, 0.8, 1.0), wc=(0.3, 0.5, 0.6, 0.75
             out.append(dict(params=p, phi=compound_droplet(nx, ny, r_in, r_out, 4.0), ca_e=c, wc=w,
                             shear_rate=gdot, capillary_time=mu * r_out / gamma))
     return out
+
+
+def config_eof_channel(nx: int = 10240, ny: int = 2048, kappa_h: float = 20.0, zeta: float = 1e-3,
+                       E: float = 1e-3, beta: float = 1.0, D: float = 0.1, precision: int = 1, **kw):
+    """The electro-osmotic channel of Section 5.1 in lattice units (length 5 H, as in
+    the paper's 5 um x 1 um channel): one phase between electrodes at the zeta
+    potential, two Nernst-Planck species (z = +-1, n0 = 1) started in their Debye-
+    Hueckel double layers, a uniform axial field E.  The charge per concentration
+    gives kappa^2 = 2 beta e_q n0 / eps.  The potential is the multigrid solve of its
+    finite-difference form."""
+    kappa = kappa_h / (ny / 2)
+    base = dict(nx=nx, ny=ny, bc_y=2, electric=1, precision=precision, eps=(1.0, 1.0, 1.0),
+                sigma=(0.0, 0.0, 0.0), eps_ref=1.0, V_bottom=zeta, V_top=zeta, E_ext=(E, 0.0),
+                tau_g=0.5 + math.sqrt(3.0 / 16.0), ions=1, ion_D=(D, D), ion_z=(1.0, -1.0), ion_beta=beta,
+                ion_charge=kappa * kappa / (2.0 * beta), potential_solver=1, poisson_tol=1e-8,
+                poisson_max_iter=50)
+    base.update(kw)
+    p = params(**base)
+    return dict(name=f"eof_channel_{nx}x{ny}", params=p, phi=single_phase(nx, ny, 1),
+                ions=debye_layers(nx, ny, zeta, kappa, beta), kappa=kappa, steps=1000)
