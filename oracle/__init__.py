@@ -15,6 +15,7 @@ import numpy as np
 
 _HERE = Path(__file__).resolve().parent
 _SRC = _HERE / "lb3e_oracle.c"
+_SRC3 = _HERE / "lb3e_oracle3d.c"
 _LIB = _HERE / "liblb3e_oracle.so"
 
 FIELDS = dict(phi1=0, phi2=1, phi3=2, ux=3, uy=4, p=5, q=6, psi=7, ex=8, ey=9,
@@ -45,13 +46,35 @@ class _Params(C.Structure):
     ]
 
 
+FIELDS3 = dict(phi1=0, phi2=1, phi3=2, ux=3, uy=4, uz=5, p=6, q=7, psi=8, ex=9, ey=10, ez=11,
+               mu1=12, mu2=13, mu3=14, phinow1=15, phinow2=16, phinow3=17, qtilde=18)
+OBS3_KEYS = ("mass1", "mass2", "mass3", "charge", "max_sum_dev", "D_inner", "D_outer", "nonfinite", "step",
+             "poisson_iters", "poisson_residual")
+
+
+class _Params3(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("bc", C.c_int32), ("electric", C.c_int32),
+        ("rho", C.c_double * 3), ("visc", C.c_double * 3), ("tau_g", C.c_double),
+        ("gamma12", C.c_double), ("gamma13", C.c_double), ("gamma23", C.c_double),
+        ("width_D", C.c_double), ("tau_f", C.c_double),
+        ("eps", C.c_double * 3), ("sigma", C.c_double * 3), ("eps_ref", C.c_double), ("alpha", C.c_double),
+        ("V_bottom", C.c_double), ("V_top", C.c_double), ("E_ext", C.c_double * 2),
+        ("u_wall_bottom", C.c_double), ("u_wall_top", C.c_double),
+        ("charge_convection", C.c_int32), ("inner_phase", C.c_int32), ("matrix_phase", C.c_int32),
+        ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int32),
+        ("poisson_check_every", C.c_int32), ("poisson_fixed_iter", C.c_int32),
+    ]
+
+
 def build(force: bool = False) -> Path:
     """Compile the oracle with gcc (-O2, no FMA contraction, OpenMP over cells)."""
-    if _LIB.exists() and not force and _LIB.stat().st_mtime >= _SRC.stat().st_mtime:
+    newest = max(_SRC.stat().st_mtime, _SRC3.stat().st_mtime)
+    if _LIB.exists() and not force and _LIB.stat().st_mtime >= newest:
         return _LIB
     tmp = _LIB.with_suffix(f".{os.getpid()}.tmp")
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
-           "-shared", "-o", str(tmp), str(_SRC), "-lm"]
+           "-shared", "-o", str(tmp), str(_SRC), str(_SRC3), "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -77,6 +100,16 @@ def lib():
         L.orc_stencil.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, dp]
         L.orc_lattice.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), dp, C.POINTER(C.c_int)]
         L.orc_set_ions.argtypes = [C.c_void_p, dp]
+        L.orc3_create.restype = C.c_void_p
+        L.orc3_create.argtypes = [C.POINTER(_Params3), dp, dp, dp, C.POINTER(C.c_int)]
+        L.orc3_step.argtypes = [C.c_void_p, C.c_int]
+        L.orc3_get_field.argtypes = [C.c_void_p, C.c_int, dp]
+        L.orc3_observables.argtypes = [C.c_void_p, dp]
+        L.orc3_destroy.argtypes = [C.c_void_p]
+        L.orc3_stencil.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp]
+        L.orc3_lattice.argtypes = [C.POINTER(C.c_int)] * 3 + [dp, C.POINTER(C.c_int)]
+        L.orc3_step_count.restype = C.c_int64
+        L.orc3_step_count.argtypes = [C.c_void_p]
         L.orc_step_count.restype = C.c_int64
         L.orc_step_count.argtypes = [C.c_void_p]
         _lib = L
@@ -178,3 +211,72 @@ def lattice():
     w = (C.c_double * 9)()
     lib().orc_lattice(cx, cy, w, opp)
     return np.array(cx[:]), np.array(cy[:]), np.array(w[:]), np.array(opp[:])
+
+
+class Oracle3D:
+    """FP64 reference of the D3Q15 step.  ``params`` uses the two-dimensional keys
+    plus ``nz``; ``bc_y`` gives the boundary of the z walls (the wall normal is z in
+    three dimensions, x and y periodic), ``E_ext`` = (along x, along z).  Arrays are
+    [.., nz, ny, nx]."""
+
+    def __init__(self, params: dict, phi, u=None, q=None):
+        self.params = dict(params)
+        self.nx, self.ny, self.nz = int(params["nx"]), int(params["ny"]), int(params["nz"])
+        self._keep = [_c64(phi), _c64(u), _c64(q)]
+        pr = _Params3()
+        for name, ctype in _Params3._fields_:
+            v = params["bc_y"] if name == "bc" else params[name]
+            if hasattr(ctype, "_length_"):
+                getattr(pr, name)[:] = list(v)
+            else:
+                setattr(pr, name, v)
+        self._p = pr
+        st = C.c_int(0)
+        h = lib().orc3_create(C.byref(pr), *(_ptr(a) for a in self._keep), C.byref(st))
+        if not h:
+            raise ValueError(f"oracle rejected parameters (status {st.value})")
+        self._h = C.c_void_p(h)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().orc3_destroy(self._h)
+            self._h = None
+
+    def step(self, n: int = 1):
+        lib().orc3_step(self._h, int(n))
+        return self
+
+    @property
+    def steps_done(self) -> int:
+        return int(lib().orc3_step_count(self._h))
+
+    def field(self, name: str) -> np.ndarray:
+        out = np.empty((self.nz, self.ny, self.nx))
+        if lib().orc3_get_field(self._h, FIELDS3[name], _ptr(out)) != 0:
+            raise KeyError(name)
+        return out
+
+    def pop(self, set_name: str, j: int) -> np.ndarray:
+        out = np.empty((self.nz, self.ny, self.nx))
+        lib().orc3_get_field(self._h, POP_BASE + 15 * SETS[set_name] + j, _ptr(out))
+        return out
+
+    def observables(self) -> dict:
+        out = np.zeros(11)
+        lib().orc3_observables(self._h, _ptr(out))
+        return dict(zip(OBS3_KEYS, out.tolist()))
+
+
+def stencil3(chi: np.ndarray, bc: int):
+    chi = _c64(chi)
+    nz, ny, nx = chi.shape
+    g, lap = np.empty((3,) + chi.shape), np.empty_like(chi)
+    lib().orc3_stencil(nx, ny, nz, bc, _ptr(chi), _ptr(g), _ptr(lap))
+    return g, lap
+
+
+def lattice3():
+    cx, cy, cz, opp = (C.c_int * 15)(), (C.c_int * 15)(), (C.c_int * 15)(), (C.c_int * 15)()
+    w = (C.c_double * 15)()
+    lib().orc3_lattice(cx, cy, cz, w, opp)
+    return np.array(cx[:]), np.array(cy[:]), np.array(cz[:]), np.array(w[:]), np.array(opp[:])
