@@ -49,6 +49,12 @@ MG_VCYCLE_BYTES = 48 + round(170 * 4 / 3)
 ION_WORDS = {"k_ion_moments": 21, "k_ions": 50}
 # with ions on, k_fused also writes u, p and mu (6 planes) every step
 FUSED_DIAG_WORDS = 6
+# three-dimensional (D3Q15) kernels per cell, in words of the compute type:
+# k3_collide reads 75 populations, phi (3), q, E (3), mu (3), rho, sigma, eps and the
+# d/dt history (12) and writes 75 populations and the history (100 + 87); one
+# potential iteration reads 15 h, eps, q and writes 15 h (32); k3_moments reads 60
+# populations and writes phi (3), q~, rho, sigma, eps (67)
+WORDS_3D = {"fused": 187, "poisson": 32, "moments": 67}
 
 
 def parse():
@@ -58,7 +64,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lb3e", choices=["lb3e", "reference"])
     ap.add_argument("--workload", default="deformation",
-                    choices=["deformation", "sweep", "adjoint", "regimes", "eof"],
+                    choices=["deformation", "sweep", "adjoint", "regimes", "eof", "deformation3d"],
                     help="deformation: the 4096^2 lattice (default); sweep: 256 lattices in one batch; "
                          "adjoint: cost of the three parameter derivatives relative to a forward step")
     ap.add_argument("--precision", type=int, default=1, help="0 fp64, 1 fp32, 2 fp32 + fp16-stored populations")
@@ -673,6 +679,104 @@ def run_eof(args):
     print(json.dumps(line), flush=True)
 
 
+def run_deformation3d(args):
+    """The compound drop under field on a 256^3 D3Q15 lattice (the paper's deformation
+    runs are three-dimensional): MLUPS over the timed steps, 16 warm-started potential
+    iterations a step, the roofline of the dominant kernel class, an end-to-end run
+    from pinned host fields, and the oracle on a bounded sample."""
+    import torch
+    import paper_2608_05787_b300 as L
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    prec = min(args.precision, 1)
+    cfg = W.config_deformation_3d(precision=prec)
+    params = cfg["params"]
+    n = params["nx"]
+    N = n ** 3
+    word = 8 if prec == 0 else 4
+    iters = params["poisson_fixed_iter"]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = L.Sim(params, torch.from_numpy(cfg["phi"]).cuda(), stream=stream)
+        sim.step(args.warmup)
+        torch.cuda.synchronize()
+        sim.set_timing(True)
+        l0 = sim.launches
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(0) as clk:
+            ev0.record(stream)
+            sim.step(args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        launches = sim.launches - l0
+        kt = sim.kernel_times()
+        sim.set_timing(False)
+        obs = sim.observables()
+    t = ms / 1e3
+    total = N * args.steps
+    hbm, peak_kind = peaks()
+    units = {"fused": args.steps, "poisson": args.steps * iters, "moments": args.steps}
+    gbs = {k: WORDS_3D[k] * word * N * units[k] / (kt[k][0] / 1e3) / 1e9 for k in WORDS_3D if kt[k][1]}
+    dominant = max(WORDS_3D, key=lambda k: kt[k][0])
+    kname = {"fused": "k3_collide", "poisson": "k3_poisson", "moments": "k3_moments"}[dominant]
+    roofline = {"bound": "hbm", "achieved": gbs.get(dominant), "peak": hbm, "unit": "GB/s",
+                "frac": gbs.get(dominant, 0) / hbm, "traffic": None, "kernel": kname,
+                "peak_kind": f"{peak_kind} copy bandwidth",
+                "algorithmic_bytes_per_cell": WORDS_3D[dominant] * word,
+                "units": "cells x pseudo-iterations" if dominant == "poisson" else "cells x steps",
+                "other_kernel_gbs": {k: v for k, v in gbs.items() if k != dominant}}
+    kernels = {k: {"launches": kn, "ms_total": kms, "share": kms / max(1e-12, sum(v[0] for v in kt.values()))}
+               for k, (kms, kn) in kt.items() if kn}
+    e2e = None
+    if not args.no_e2e:
+        del sim
+        torch.cuda.empty_cache()
+        host_phi = torch.from_numpy(cfg["phi"]).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            s2 = L.Sim(params, host_phi, stream=stream)
+            for _ in range(args.steps):
+                s2.step(1)
+                s2.observables()
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": total / t_e2e / 1e6, "unit": METRIC, "h2d_bytes_per_step": int(3 * N * 8 / args.steps),
+               "d2h_bytes_per_step": 16 * 8, "includes": "init from pinned host phases (with its potential solve) "
+               "+ per-step observables read-back", "seconds": t_e2e}
+        del s2
+    cpu = None
+    if not args.no_cpu:
+        try:
+            import oracle
+            cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+            m = 48
+            c = W.config_deformation_3d(n=m, r_out=40.0 * m / 256, r_in=20.0 * m / 256, precision=0)
+            o = oracle.Oracle3D(c["params"], c["phi"])
+            t0 = time.perf_counter()
+            o.step(3)
+            dt = (time.perf_counter() - t0) / 3
+            cpu = {"value": m ** 3 / dt / 1e6, "unit": METRIC, "cores": cores, "kind": "oracle",
+                   "sample": f"3 steps of the same drop at {m}^3 (radii scaled), 16 potential iterations a step; "
+                             "init untimed", "seconds_per_step": dt}
+        except Exception as exc:
+            cpu = {"value": None, "error": repr(exc)}
+    line = {"metric": METRIC, "value": total / t / 1e6, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {0: "f64", 1: "f32"}[prec],
+            "data": "synthetic (a compound sphere between electrodes)",
+            "config": {"workload": f"compound drop deformation under field, D3Q15, {n}^3",
+                       "potential_iters_per_step": iters,
+                       "l2": "working set (%.1f GB) exceeds the 126 MB L2; no flush needed" % (
+                           L.workspace_bytes(params) / 1e9)},
+            "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "observables": {k: obs[k] for k in ("D_inner", "D_outer", "max_sum_dev", "nonfinite")}}
+    print(json.dumps(line), flush=True)
+
+
 def run_adjoint(args):
     """Derivative cost on the 256^2 drop under field plus shear: time per step of
     the FP32 tangent build (three parameter directions: E0, eps3, gamma23) over the
@@ -729,6 +833,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "eof":
         run_eof(args)
+    elif args.workload == "deformation3d":
+        run_deformation3d(args)
     else:
         run_lb3e(args)
 

@@ -70,12 +70,15 @@ enum {
     LB3E_FIELD_QTILDE = 16,  /* sum_j l_j of the current populations */
     LB3E_FIELD_N1 = 17,      /* ion concentrations n_i = sum_j n^i_j of the current */
     LB3E_FIELD_N2 = 18,      /* ion populations (ions = 1 only) */
+    LB3E_FIELD_UZ = 19,      /* three-dimensional lattices: velocity and field along z */
+    LB3E_FIELD_EZ = 20,
     LB3E_FIELD_POP = 100     /* + 9*set + j; sets 0 g, 1-3 f^1..f^3, 4 l, 5 h,
-                                6-7 the ion species (ions = 1 only) */
+                                6-7 the ion species (ions = 1 only); on
+                                three-dimensional lattices + 15*set + j, sets 0-5 */
 };
 
-/* Largest lattice lb3e_init accepts (45 population planes are addressed with
- * 32-bit offsets). */
+/* Largest lattice lb3e_init accepts (cells, nx * ny * nz on three-dimensional
+ * lattices; 45 population planes are addressed with 32-bit offsets). */
 #define LB3E_MAX_CELLS 40000000
 #define LB3E_MAX_NY (65535 * 8)   /* tiles of 8 rows, at most 65535 of them along y */
 
@@ -135,6 +138,15 @@ typedef struct lb3e_params {
     double ion_z[2];              /* valences */
     double ion_beta;              /* e / (k_B T): inverse thermal voltage, lattice units */
     double ion_charge;            /* charge per unit concentration */
+    /* >= 2: the three-dimensional step on the D3Q15 lattice (Eq. 32) over nx x ny x nz
+     * cells, arrays [..][nz][ny][nx].  x and y are periodic; bc_y then gives the
+     * boundary of the walls normal to z (at z = -1/2 and nz - 1/2; electrodes V_bottom,
+     * V_top; wall speeds along x), E_ext = (along x, along z).  The potential source
+     * is split evenly over the 14 moving directions.  Precisions 0 and 1, the LB
+     * potential solve, no ions, no population noise, no snapshots, single lattices.
+     * 0 or 1: the two-dimensional D2Q9 step. */
+    int32_t nz;
+    int32_t _pad4;
 } lb3e_params;
 
 /* Field id offset of tangent k (1..3) of a field in the tangent builds: field

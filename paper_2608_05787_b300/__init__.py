@@ -18,7 +18,8 @@ _HERE = Path(__file__).resolve().parent
 LIB_PATH = Path(os.environ.get("LB3E_LIBRARY", _HERE / "liblb3e.so"))
 
 FIELDS = dict(phi1=0, phi2=1, phi3=2, ux=3, uy=4, p=5, q=6, psi=7, ex=8, ey=9,
-              mu1=10, mu2=11, mu3=12, phinow1=13, phinow2=14, phinow3=15, qtilde=16, n1=17, n2=18)
+              mu1=10, mu2=11, mu3=12, phinow1=13, phinow2=14, phinow3=15, qtilde=16, n1=17, n2=18,
+              uz=19, ez=20)
 SETS = dict(g=0, f1=1, f2=2, f3=3, l=4, h=5, n1=6, n2=7)
 POP_BASE = 100
 PRECISIONS = {0: "f64", 1: "f32", 2: "f32-compute/f16-store", 3: "f32 + 3 tangents", 4: "f64 + 1 tangent"}
@@ -45,10 +46,11 @@ class Params(C.Structure):
         ("poisson_check_every", C.c_int32), ("poisson_fixed_iter", C.c_int32), ("_pad2", C.c_int32),
         ("tangent_param", C.c_int32 * 3), ("potential_solver", C.c_int32),
         ("ions", C.c_int32), ("_pad3", C.c_int32), ("ion_D", C.c_double * 2), ("ion_z", C.c_double * 2),
-        ("ion_beta", C.c_double), ("ion_charge", C.c_double),
+        ("ion_beta", C.c_double), ("ion_charge", C.c_double), ("nz", C.c_int32), ("_pad4", C.c_int32),
     ]
-    # Nernst-Planck ion transport is off unless the dict asks for it
-    _ION_DEFAULTS = dict(ions=0, ion_D=(0.0, 0.0), ion_z=(1.0, -1.0), ion_beta=1.0, ion_charge=0.0)
+    # Nernst-Planck ion transport and the three-dimensional lattice are off unless
+    # the dict asks for them
+    _DEFAULTS = dict(ions=0, ion_D=(0.0, 0.0), ion_z=(1.0, -1.0), ion_beta=1.0, ion_charge=0.0, nz=0)
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
@@ -60,7 +62,7 @@ class Params(C.Structure):
         for name, ctype in cls._fields_:
             if name.startswith("_pad"):
                 continue
-            v = d[name] if name in d or name not in cls._ION_DEFAULTS else cls._ION_DEFAULTS[name]
+            v = d[name] if name in d or name not in cls._DEFAULTS else cls._DEFAULTS[name]
             if hasattr(ctype, "_length_"):
                 conv = int if ctype._type_ is C.c_int32 else float
                 getattr(s, name)[:] = [conv(a) for a in v]
@@ -204,6 +206,10 @@ class Sim:
             raise RuntimeError("lb3e needs a CUDA device (there is no CPU fallback)")
         self.params = dict(params)
         self.nx, self.ny = int(params["nx"]), int(params["ny"])
+        self.nz = int(params.get("nz", 0))
+        # arrays are [.., ny, nx], or [.., nz, ny, nx] on three-dimensional (D3Q15) lattices
+        self.shape = (self.nz, self.ny, self.nx) if self.nz >= 2 else (self.ny, self.nx)
+        self.q_dirs = 15 if self.nz >= 2 else 9
         self.device = torch.device(device or "cuda")
         self._p = Params.from_dict(self.params)
         nbytes = workspace_bytes(self.params)
@@ -246,11 +252,11 @@ class Sim:
         return self._get(fid, out)
 
     def pop(self, set_name: str, j: int, out=None):
-        return self._get(POP_BASE + 9 * SETS[set_name] + j, out)
+        return self._get(POP_BASE + self.q_dirs * SETS[set_name] + j, out)
 
     def _get(self, fid: int, out):
         if out is None:
-            arr = np.empty((self.ny, self.nx))
+            arr = np.empty(self.shape)
             _check("lb3e_get_field", lib().lb3e_get_field(self._h, fid, arr.ctypes.data))
             return arr
         _check("lb3e_get_field", lib().lb3e_get_field(self._h, fid, out.data_ptr()))

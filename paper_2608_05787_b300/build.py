@@ -21,6 +21,9 @@ UNITS = {
     # FP64: no contraction into FMA, so the arithmetic rounds like plain C
     "lb3e_f64.cu": ["--fmad=false"],
     "lb3e_f32.cu": [],
+    # the three-dimensional (D3Q15) step, FP64 without contraction and FP32
+    "lb3e_3d_f64.cu": ["--fmad=false"],
+    "lb3e_3d_f32.cu": [],
     # dual-number (tangent) builds
     "lb3e_tangent.cu": [],
     # fixed-scratch observables for callers that cannot allocate (FP64 like lb3e_f64.cu)

@@ -1,0 +1,900 @@
+// lb3e_3d.cuh -- the three-dimensional step on the D3Q15 lattice (Eq. 32): the
+// schemes of Section 3 with 15 directions, the isotropic stencils of Eq. 33 with
+// the D3Q15 weights, x and y periodic, walls (and electrodes) normal to z.
+//
+// One thread per cell, blocks of 32 x 8 cells in an x-y plane, one grid layer per
+// z plane.  Populations are structure-of-arrays planes (15 set + j) * N + cell,
+// cell = (z ny + y) nx + x, sets g, f1, f2, f3, l; the potential populations h
+// have their own 15 planes.  Push streaming between two buffers.
+//
+// Readings beyond the two-dimensional ones: the potential source is split evenly
+// over the 14 moving directions (varpi_j = 1/14; the paper gives 1/8 on D2Q9's 8);
+// the external field is (E_ext[0], 0, E_ext[1]) -- its second component along the
+// wall normal; moving walls slide along x.
+//
+// The FP64 build evaluates each formula in the order a plain C evaluation takes
+// it (compiled without FMA contraction), so it reproduces a plain FP64 CPU
+// evaluation to rounding of reductions; the FP32 build uses the same expressions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "lb3e_internal.h"
+#include "lb3e_kernels.cuh"
+
+namespace lb3e {
+
+// ---------------------------------------------------------------- D3Q15 (Eq. 32)
+__host__ __device__ constexpr int c3x(int j) {
+    return (j == 1 || j == 7 || j == 9 || j == 11 || j == 14) ? 1 : (j == 2 || j == 8 || j == 10 || j == 12 || j == 13) ? -1 : 0;
+}
+__host__ __device__ constexpr int c3y(int j) {
+    return (j == 3 || j == 7 || j == 9 || j == 12 || j == 13) ? 1 : (j == 4 || j == 8 || j == 10 || j == 11 || j == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int c3z(int j) {
+    return (j == 5 || j == 7 || j == 10 || j == 11 || j == 13) ? 1 : (j == 6 || j == 8 || j == 9 || j == 12 || j == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp3(int j) { return j == 0 ? 0 : ((j & 1) ? j + 1 : j - 1); }
+template <class R>
+__host__ __device__ constexpr R w3(int j) { return j == 0 ? R(2.0 / 9.0) : (j <= 6 ? R(1.0 / 9.0) : R(1.0 / 72.0)); }
+constexpr int Q3 = 15;
+
+// c_j . (a, b, c) in the order x, y, z, zero components left out (the same value as
+// cx*a + cy*b + cz*c: a product with a zero component only adds a signed zero)
+template <class R>
+__device__ __forceinline__ R cdot3(int j, R a, R b, R c) {
+    R s = R(0);
+    bool any = false;
+    if (c3x(j) != 0) { s = c3x(j) > 0 ? a : -a; any = true; }
+    if (c3y(j) != 0) { s = any ? (c3y(j) > 0 ? s + b : s - b) : (c3y(j) > 0 ? b : -b); any = true; }
+    if (c3z(j) != 0) { s = any ? (c3z(j) > 0 ? s + c : s - c) : (c3z(j) > 0 ? c : -c); }
+    return s;
+}
+template <class R>
+__device__ __forceinline__ R ocs2(R a) { return exact_arith<R>() ? a / (R(1) / R(3)) : a * R(3); }
+
+// launch-wide parameters (formed on the host in double precision)
+struct P3 {
+    int nx, ny, nz, bc, cc, use_visc;
+    size_t N;
+    double rho[3], visc[3], tau_g, lam[3], D, tau_f, m0, eps[3], sigma[3], eps_ref, tau_h, tau_l;
+    double V_bottom, V_top, E0, E1, uwb, uwt;
+    int inner, matrix;
+};
+
+inline P3 make_p3(const lb3e_params& p) {
+    P3 q{};
+    q.nx = p.nx; q.ny = p.ny; q.nz = p.nz; q.bc = p.bc_y; q.cc = p.charge_convection;
+    q.use_visc = p.visc[0] > 0 && p.visc[1] > 0 && p.visc[2] > 0;
+    q.N = (size_t)p.nx * p.ny * p.nz;
+    for (int i = 0; i < 3; ++i) {
+        q.rho[i] = p.rho[i]; q.visc[i] = p.visc[i]; q.eps[i] = p.eps[i]; q.sigma[i] = p.sigma[i];
+    }
+    q.lam[0] = p.gamma12 + p.gamma13 - p.gamma23;   // Eq. 9
+    q.lam[1] = p.gamma12 + p.gamma23 - p.gamma13;
+    q.lam[2] = p.gamma13 + p.gamma23 - p.gamma12;
+    const double c2 = 1.0 / 3.0;
+    q.tau_g = p.tau_g; q.D = p.width_D; q.tau_f = p.tau_f; q.m0 = c2 * (p.tau_f - 0.5);
+    q.eps_ref = p.eps_ref; q.tau_h = 0.5 + p.eps_ref / c2; q.tau_l = 0.5 + p.alpha / c2;
+    q.V_bottom = p.V_bottom; q.V_top = p.V_top; q.E0 = p.E_ext[0]; q.E1 = p.E_ext[1];
+    q.uwb = p.u_wall_bottom; q.uwt = p.u_wall_top;
+    q.inner = p.inner_phase; q.matrix = p.matrix_phase;
+    return q;
+}
+
+// cell coordinates of this thread; false outside the lattice
+__device__ __forceinline__ bool cell3(const P3& P, int& x, int& y, int& z, size_t& c) {
+    x = blockIdx.x * blockDim.x + threadIdx.x;
+    y = blockIdx.y * blockDim.y + threadIdx.y;
+    z = blockIdx.z;
+    c = ((size_t)z * P.ny + y) * P.nx + x;
+    return x < P.nx && y < P.ny;
+}
+// neighbour cell for the stencils: periodic x, y; z periodic or mirrored at the walls
+__device__ __forceinline__ size_t nb3(const P3& P, int x, int y, int z, int j) {
+    int zz = z + c3z(j);
+    if (P.bc == 0) zz = zz < 0 ? zz + P.nz : (zz >= P.nz ? zz - P.nz : zz);
+    else zz = zz < 0 ? -zz - 1 : (zz >= P.nz ? 2 * P.nz - zz - 1 : zz);
+    const int yy = wrapi(y + c3y(j), P.ny), xx = wrapi(x + c3x(j), P.nx);
+    return ((size_t)zz * P.ny + yy) * P.nx + xx;
+}
+// Eq. 33 gradient of a field at a cell
+template <class R>
+__device__ __forceinline__ void grad3(const P3& P, const R* __restrict__ f, int x, int y, int z, R g[3]) {
+    R a0 = R(0), a1 = R(0), a2 = R(0);
+#pragma unroll
+    for (int j = 0; j < Q3; ++j) {
+        const R v = w3<R>(j) * f[nb3(P, x, y, z, j)];
+        cacc(a0, c3x(j), v);
+        cacc(a1, c3y(j), v);
+        cacc(a2, c3z(j), v);
+    }
+    g[0] = ocs2(a0); g[1] = ocs2(a1); g[2] = ocs2(a2);
+}
+template <class R>
+__device__ __forceinline__ R lap3(const P3& P, const R* __restrict__ f, int x, int y, int z, size_t c) {
+    const R c0 = f[c];
+    R a = R(0);
+#pragma unroll
+    for (int j = 0; j < Q3; ++j) a += R(2) * w3<R>(j) * (f[nb3(P, x, y, z, j)] - c0);
+    return ocs2(a);
+}
+// streaming target: false when the link leaves through a wall (bounce-back)
+__device__ __forceinline__ bool target3(const P3& P, int x, int y, int z, int j, size_t& t) {
+    int zt = z + c3z(j);
+    if (P.bc != 0 && (zt < 0 || zt >= P.nz)) return false;
+    zt = zt < 0 ? zt + P.nz : (zt >= P.nz ? zt - P.nz : zt);
+    t = ((size_t)zt * P.ny + wrapi(y + c3y(j), P.ny)) * P.nx + wrapi(x + c3x(j), P.nx);
+    return true;
+}
+
+template <class R>
+__device__ __forceinline__ R s3(int j, R u0, R u1, R u2) {   // s_j(u), Eq. 40
+    const R cu = cdot3<R>(j, u0, u1, u2);
+    const R uu = u0 * u0 + u1 * u1 + u2 * u2;
+    const R c2 = R(1) / R(3);
+    return w3<R>(j) * (cu / c2 + cu * cu / (R(2) * c2 * c2) - uu / (R(2) * c2));
+}
+
+// ---------------------------------------------------------------- S1, S2
+// phi_i, q~ of the current populations; rho, sigma, eps of those phi
+template <class R>
+__global__ void __launch_bounds__(256) k3_moments(P3 P, const R* __restrict__ pop, R* __restrict__ phi,
+                                                  R* __restrict__ qt, R* __restrict__ rho, R* __restrict__ sig,
+                                                  R* __restrict__ eps) {
+    int x, y, z;
+    size_t c;
+    if (!cell3(P, x, y, z, c)) return;
+    const size_t N = P.N;
+    R ph[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        R a = R(0);
+#pragma unroll
+        for (int j = 0; j < Q3; ++j) a += pop[(Q3 * (i + 1) + j) * N + c];
+        ph[i] = a;
+        phi[i * N + c] = a;
+    }
+    R a = R(0);
+#pragma unroll
+    for (int j = 0; j < Q3; ++j) a += pop[(Q3 * 4 + j) * N + c];
+    qt[c] = a;
+    rho[c] = ph[0] * R(P.rho[0]) + ph[1] * R(P.rho[1]) + ph[2] * R(P.rho[2]);   // Eq. 29
+    sig[c] = ph[0] * R(P.sigma[0]) + ph[1] * R(P.sigma[1]) + ph[2] * R(P.sigma[2]);
+    R e = R(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) e += R(P.eps[i]) * ph[i] * ph[i] * (R(3) - R(2) * ph[i]);   // Eq. 30
+    eps[c] = e;
+}
+// properties only (initial state)
+template <class R>
+__global__ void __launch_bounds__(256) k3_props(P3 P, const R* __restrict__ phi, R* __restrict__ rho,
+                                                R* __restrict__ sig, R* __restrict__ eps) {
+    int x, y, z;
+    size_t c;
+    if (!cell3(P, x, y, z, c)) return;
+    const size_t N = P.N;
+    const R ph[3] = {phi[c], phi[N + c], phi[2 * N + c]};
+    rho[c] = ph[0] * R(P.rho[0]) + ph[1] * R(P.rho[1]) + ph[2] * R(P.rho[2]);
+    sig[c] = ph[0] * R(P.sigma[0]) + ph[1] * R(P.sigma[1]) + ph[2] * R(P.sigma[2]);
+    R e = R(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) e += R(P.eps[i]) * ph[i] * ph[i] * (R(3) - R(2) * ph[i]);
+    eps[c] = e;
+}
+
+// ---------------------------------------------------------------- S4
+// q = (q~ + (r grad eps . E - grad sigma . E)/2) / (1 + r/2), r = sigma/eps, with the
+// previous step's field
+template <class R>
+__global__ void __launch_bounds__(256) k3_closure(P3 P, const R* __restrict__ qt, const R* __restrict__ sig,
+                                                  const R* __restrict__ eps, const R* __restrict__ E,
+                                                  R* __restrict__ q) {
+    int x, y, z;
+    size_t c;
+    if (!cell3(P, x, y, z, c)) return;
+    const size_t N = P.N;
+    R ge3[3], gs3[3];
+    grad3<R>(P, eps, x, y, z, ge3);
+    grad3<R>(P, sig, x, y, z, gs3);
+    const R r = sig[c] / eps[c];
+    R ge = R(0), gs = R(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ge += ge3[a] * E[a * N + c];
+        gs += gs3[a] * E[a * N + c];
+    }
+    q[c] = (qt[c] + R(0.5) * (r * ge - gs)) / (R(1) + R(0.5) * r);
+}
+
+// ---------------------------------------------------------------- S5: Eq. 43-45
+template <class R>
+__device__ __forceinline__ void hmoments3(const R* __restrict__ h, size_t N, size_t c, R& psi, R J[3]) {
+    R a = R(0);
+#pragma unroll
+    for (int j = 1; j < Q3; ++j) a += h[j * N + c];
+    psi = a / (R(1) - w3<R>(0));
+    R j0 = R(0), j1 = R(0), j2 = R(0);
+#pragma unroll
+    for (int j = 0; j < Q3; ++j) {
+        const R v = h[j * N + c];
+        cacc(j0, c3x(j), v);
+        cacc(j1, c3y(j), v);
+        cacc(j2, c3z(j), v);
+    }
+    J[0] = j0; J[1] = j1; J[2] = j2;
+}
+
+// One pseudo-iteration: collide and push-stream h.  save: store psi, J (the state
+// a later check compares with); check: accumulate |d psi|^2, |psi|^2, |dJ|^2, |J|^2
+// per block (FP64 partials).
+template <class R>
+__global__ void __launch_bounds__(256) k3_poisson(P3 P, const R* __restrict__ hin, R* __restrict__ hout,
+                                                  const R* __restrict__ eps, const R* __restrict__ q,
+                                                  R* __restrict__ prev, double* __restrict__ partial, int save,
+                                                  int check) {
+    int x, y, z;
+    size_t c;
+    const bool in = cell3(P, x, y, z, c);
+    const size_t N = P.N;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (in) {
+        R psi, J[3];
+        hmoments3<R>(hin, N, c, psi, J);
+        if (check) {
+            const double d = (double)psi - (double)prev[c];
+            acc[0] = d * d;
+            acc[1] = (double)psi * (double)psi;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double e = (double)J[a] - (double)prev[(1 + a) * N + c];
+                acc[2] += e * e;
+                acc[3] += (double)J[a] * (double)J[a];
+            }
+        }
+        if (save) {
+            prev[c] = psi;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) prev[(1 + a) * N + c] = J[a];
+        }
+        const R th = R(P.tau_h), epshat = eps[c] - R(P.eps_ref);
+        const R den = epshat + (R(1) / R(3)) * th;
+        const R g0 = -J[0] / den, g1 = -J[1] / den, g2 = -J[2] / den;
+        const R qc = q[c];
+#pragma unroll
+        for (int j = 0; j < Q3; ++j) {
+            const R heq = j == 0 ? (w3<R>(0) - R(1)) * psi : w3<R>(j) * psi;     // Eq. 44
+            const R varpi = j == 0 ? R(0) : R(1.0 / 14.0);
+            const R hj = hin[j * N + c];
+            const R cg = cdot3<R>(j, g0, g1, g2);
+            const R v = hj - (hj - heq) / th - (epshat / (R(1) / R(3))) * w3<R>(j) * cg / th + varpi * qc;
+            size_t t;
+            if (target3(P, x, y, z, j, t)) {
+                hout[j * N + t] = v;
+            } else {
+                R out = v;
+                if (P.bc == 2) out = -v + R(2) * w3<R>(j) * R(c3z(j) > 0 ? P.V_top : P.V_bottom);
+                hout[opp3(j) * N + c] = out;
+            }
+        }
+    }
+    if (check) {
+        const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+        block_reduce_store<4>(acc, partial + 4 * (size_t)b);
+    }
+}
+
+// psi and E = -grad psi (+ the external field) from the potential populations (Eq. 45)
+template <class R>
+__global__ void __launch_bounds__(256) k3_fields(P3 P, const R* __restrict__ h, const R* __restrict__ eps,
+                                                 R* __restrict__ E, R* __restrict__ psi_out) {
+    int x, y, z;
+    size_t c;
+    if (!cell3(P, x, y, z, c)) return;
+    const size_t N = P.N;
+    R psi, J[3];
+    hmoments3<R>(h, N, c, psi, J);
+    const R den = (eps[c] - R(P.eps_ref)) + (R(1) / R(3)) * R(P.tau_h);
+    E[c] = -(-J[0] / den) + R(P.E0);
+    E[N + c] = -(-J[1] / den);
+    E[2 * N + c] = -(-J[2] / den) + R(P.E1);
+    if (psi_out) psi_out[c] = psi;
+}
+template <class R>
+__global__ void k3_fill_E(P3 P, R* __restrict__ E) {
+    const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (c >= P.N) return;
+    E[c] = R(P.E0);
+    E[P.N + c] = R(0);
+    E[2 * P.N + c] = R(P.E1);
+}
+// potential populations at equilibrium with the linear electrode profile
+template <class R>
+__global__ void __launch_bounds__(256) k3_init_h(P3 P, R* __restrict__ h) {
+    int x, y, z;
+    size_t c;
+    if (!cell3(P, x, y, z, c)) return;
+    const R psi0 = P.bc == 2 ? R(P.V_bottom + (P.V_top - P.V_bottom) * (z + 0.5) / P.nz) : R(0);
+#pragma unroll
+    for (int j = 0; j < Q3; ++j) h[j * P.N + c] = j == 0 ? (w3<R>(0) - R(1)) * psi0 : w3<R>(j) * psi0;
+}
+
+// ---------------------------------------------------------------- S6: Eq. 20
+template <class R>
+__global__ void __launch_bounds__(256) k3_chem(P3 P, const R* __restrict__ phi, const R* __restrict__ E,
+                                               R* __restrict__ mu) {
+    int x, y, z;
+    size_t c;
+    if (!cell3(P, x, y, z, c)) return;
+    const size_t N = P.N;
+    const R e2 = E[c] * E[c] + E[N + c] * E[N + c] + E[2 * N + c] * E[2 * N + c];
+    const R D = R(P.D);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const R ph = phi[i * N + c], lam = R(P.lam[i]);
+        const R lap = lap3<R>(P, phi + i * N, x, y, z, c);
+        const R bulk = R(24) / D * lam * ph * (ph - R(0.5)) * (ph - R(1));
+        const R grad = R(0.75) * D * lam * lap;
+        const R deps = R(6) * R(P.eps[i]) * ph * (R(1) - ph);
+        mu[i * N + c] = bulk - grad - R(0.5) * deps * e2;
+    }
+}
+
+// ---------------------------------------------------------------- S7-S14
+// Force, flow moments, d/dt terms, collision of the phase (Eq. 34-36), flow (Eq.
+// 37-40) and charge (Eq. 46-50) populations, push-streaming with bounce-back at the
+// z walls (moving walls along x for the flow set).
+template <class R>
+__global__ void __launch_bounds__(256) k3_collide(P3 P, const R* __restrict__ pin, R* __restrict__ pout,
+                                                  const R* __restrict__ phi, const R* __restrict__ q,
+                                                  const R* __restrict__ E, const R* __restrict__ mu,
+                                                  const R* __restrict__ rho_f, const R* __restrict__ sig_f,
+                                                  const R* __restrict__ eps_f, R* __restrict__ prev,
+                                                  R* __restrict__ diag, int first, int write_diag) {
+    int x, y, z;
+    size_t c;
+    if (!cell3(P, x, y, z, c)) return;
+    const size_t N = P.N;
+    const R c2 = R(1) / R(3);
+    R ph[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ph[i] = phi[i * N + c];
+    const R qc = q[c], rho = rho_f[c];
+    const R Ev[3] = {E[c], E[N + c], E[2 * N + c]};
+    // S7, S8: grad mu_i, F = -sum phi_i grad mu_i + q E
+    R gmu[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) grad3<R>(P, mu + i * N, x, y, z, gmu[i]);
+    R F[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R Fa = R(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) Fa -= ph[i] * gmu[i][a];
+        F[a] = Fa + qc * Ev[a];
+    }
+    // R^n of Eq. 47
+    R ge3[3], gs3[3], gr[3];
+    grad3<R>(P, eps_f, x, y, z, ge3);
+    grad3<R>(P, sig_f, x, y, z, gs3);
+    grad3<R>(P, rho_f, x, y, z, gr);
+    R Rc;
+    {
+        const R r = sig_f[c] / eps_f[c];
+        R ge = R(0), gs = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            ge += ge3[a] * Ev[a];
+            gs += gs3[a] * Ev[a];
+        }
+        Rc = -r * qc + r * ge - gs;
+    }
+    // S9: Eq. 41
+    R g[Q3];
+#pragma unroll
+    for (int j = 0; j < Q3; ++j) g[j] = pin[j * N + c];
+    R u[3], p;
+    {
+        R m0 = R(0), m1 = R(0), m2 = R(0), g1 = R(0);
+#pragma unroll
+        for (int j = 0; j < Q3; ++j) {
+            cacc(m0, c3x(j), g[j]);
+            cacc(m1, c3y(j), g[j]);
+            cacc(m2, c3z(j), g[j]);
+            if (j) g1 += g[j];
+        }
+        u[0] = (m0 + R(0.5) * F[0]) / rho;
+        u[1] = (m1 + R(0.5) * F[1]) / rho;
+        u[2] = (m2 + R(0.5) * F[2]) / rho;
+        const R ugr = u[0] * gr[0] + u[1] * gr[1] + u[2] * gr[2];
+        p = c2 / (R(1) - w3<R>(0)) * (g1 + R(0.5) * ugr + rho * s3<R>(0, u[0], u[1], u[2]));
+    }
+    // S10
+    R dpu[3][3], dqu[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dpu[i][a] = first ? R(0) : ph[i] * u[a] - prev[(3 * i + a) * N + c];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dqu[a] = first ? R(0) : qc * u[a] - prev[(9 + a) * N + c];
+
+    // S11: phase populations with the mobility of Eq. 28
+    const R tf = R(P.tau_f), m0 = R(P.m0), pf = R(1) - R(1) / (R(2) * tf);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        R Mii = R(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (k != i) Mii += m0 * ph[i] * ph[k];
+        R Y[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const R Mik = (k == i) ? (Mii - m0) : -m0 * ph[i] * ph[k];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Y[a] += Mik * gmu[k][a];
+        }
+        R A[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) A[a] = dpu[i][a] / c2 - Y[a] / m0;
+        const R mui = mu[i * N + c];
+        const R pu0 = ph[i] * u[0], pu1 = ph[i] * u[1], pu2 = ph[i] * u[2];
+#pragma unroll
+        for (int j = 0; j < Q3; ++j) {
+            const R feq = (j == 0) ? ph[i] - (R(1) - w3<R>(0)) * mui
+                                   : w3<R>(j) * mui + w3<R>(j) * cdot3<R>(j, pu0, pu1, pu2) / c2;
+            const R Fj = w3<R>(j) * cdot3<R>(j, A[0], A[1], A[2]);
+            const R fj = pin[(Q3 * (i + 1) + j) * N + c];
+            const R v = fj - (fj - feq) / tf + pf * Fj;
+            size_t t;
+            if (target3(P, x, y, z, j, t)) pout[(Q3 * (i + 1) + j) * N + t] = v;
+            else pout[(Q3 * (i + 1) + opp3(j)) * N + c] = v;
+        }
+    }
+    // S12: flow populations
+    {
+        R tg = R(P.tau_g);
+        if (P.use_visc) {
+            R eta = R(0);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) eta += ph[i] * R(P.visc[i]);
+            tg = R(0.5) + eta / (rho * c2);
+        }
+        const R pg = R(1) - R(1) / (R(2) * tg);
+        const R ugr = u[0] * gr[0] + u[1] * gr[1] + u[2] * gr[2];
+#pragma unroll
+        for (int j = 0; j < Q3; ++j) {
+            const R geq = (j == 0) ? (w3<R>(0) - R(1)) * p / c2 + rho * s3<R>(0, u[0], u[1], u[2])
+                                   : w3<R>(j) * p / c2 + rho * s3<R>(j, u[0], u[1], u[2]);
+            const R cu = cdot3<R>(j, u[0], u[1], u[2]);
+            const R cgr = cdot3<R>(j, gr[0], gr[1], gr[2]);
+            const R cF = cdot3<R>(j, F[0], F[1], F[2]);
+            const R G = w3<R>(j) * (ugr + cF / c2 + (cu * cgr - c2 * ugr) / c2);
+            const R v = g[j] - (g[j] - geq) / tg + pg * G;
+            size_t t;
+            if (target3(P, x, y, z, j, t)) {
+                pout[j * N + t] = v;
+            } else {
+                const R uw = R(c3z(j) > 0 ? P.uwt : P.uwb);
+                pout[opp3(j) * N + c] = v - R(2) * w3<R>(j) * rho * (R(c3x(j)) * uw) / c2;
+            }
+        }
+    }
+    // S13: charge populations
+    {
+        const R tl = R(P.tau_l), pl = R(1) - R(1) / (R(2) * tl);
+#pragma unroll
+        for (int j = 0; j < Q3; ++j) {
+            const R cu = cdot3<R>(j, u[0], u[1], u[2]);
+            const R leq = P.cc ? w3<R>(j) * qc * (R(1) + cu / c2) : w3<R>(j) * qc;
+            const R Sj = pl * w3<R>(j) * Rc;
+            const R Tj = P.cc ? pl * w3<R>(j) * cdot3<R>(j, dqu[0], dqu[1], dqu[2]) / c2 : R(0);
+            const R lj = pin[(Q3 * 4 + j) * N + c];
+            const R v = lj - (lj - leq) / tl + Sj + Tj;
+            size_t t;
+            if (target3(P, x, y, z, j, t)) pout[(Q3 * 4 + j) * N + t] = v;
+            else pout[(Q3 * 4 + opp3(j)) * N + c] = v;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) prev[(3 * i + a) * N + c] = ph[i] * u[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) prev[(9 + a) * N + c] = qc * u[a];
+    if (write_diag) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) diag[a * N + c] = u[a];
+        diag[3 * N + c] = p;
+    }
+}
+
+// initial populations: phases at equilibrium with mu (Eq. 20), flow at g_eq(p = 0, u),
+// charge at l_eq(q, u)
+template <class R>
+__global__ void __launch_bounds__(256) k3_init_pops(P3 P, R* __restrict__ pop, const R* __restrict__ phi,
+                                                    const R* __restrict__ q, const R* __restrict__ uin,
+                                                    const R* __restrict__ mu, const R* __restrict__ rho_f) {
+    int x, y, z;
+    size_t c;
+    if (!cell3(P, x, y, z, c)) return;
+    const size_t N = P.N;
+    const R c2 = R(1) / R(3);
+    const R u0 = uin[c], u1 = uin[N + c], u2 = uin[2 * N + c];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const R ph = phi[i * N + c], mui = mu[i * N + c];
+        const R pu0 = ph * u0, pu1 = ph * u1, pu2 = ph * u2;
+#pragma unroll
+        for (int j = 0; j < Q3; ++j)
+            pop[(Q3 * (i + 1) + j) * N + c] = (j == 0) ? ph - (R(1) - w3<R>(0)) * mui
+                                                       : w3<R>(j) * mui + w3<R>(j) * cdot3<R>(j, pu0, pu1, pu2) / c2;
+    }
+    const R rho = rho_f[c], qc = q[c];
+#pragma unroll
+    for (int j = 0; j < Q3; ++j) {
+        pop[j * N + c] = rho * s3<R>(j, u0, u1, u2);
+        const R cu = cdot3<R>(j, u0, u1, u2);
+        pop[(Q3 * 4 + j) * N + c] = P.cc ? w3<R>(j) * qc * (R(1) + cu / c2) : w3<R>(j) * qc;
+    }
+}
+
+// observables: per-block FP64 sums of mass (3), charge, nonfinite count and the
+// second moments of the two indicators (x and z), plus a block max of |sum phi - 1|
+constexpr int NOBS3 = 15;
+template <class R>
+__global__ void __launch_bounds__(256) k3_observables(P3 P, const R* __restrict__ phi, const R* __restrict__ q,
+                                                      const R* __restrict__ u, double* __restrict__ partial,
+                                                      double* __restrict__ maxpart) {
+    int x, y, z;
+    size_t c;
+    const bool in = cell3(P, x, y, z, c);
+    const size_t N = P.N;
+    double v[NOBS3];
+#pragma unroll
+    for (int k = 0; k < NOBS3; ++k) v[k] = 0.0;
+    double dev = 0.0;
+    if (in) {
+        double ph[3], s = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { ph[i] = (double)phi[i * N + c]; v[i] = ph[i]; s += ph[i]; }
+        dev = fabs(s - 1.0);
+        v[3] = (double)q[c];
+        const double vals[7] = {ph[0], ph[1], ph[2], (double)u[c], (double)u[N + c], (double)u[2 * N + c], v[3]};
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+            if (!isfinite(vals[k])) v[4] += 1.0;
+        const double chis[2] = {ph[P.inner - 1], 1.0 - ph[P.matrix - 1]};
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            v[5 + 5 * k] = chis[k];
+            v[6 + 5 * k] = chis[k] * x;
+            v[7 + 5 * k] = chis[k] * z;
+            v[8 + 5 * k] = chis[k] * x * x;
+            v[9 + 5 * k] = chis[k] * z * z;
+        }
+    }
+    const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    block_reduce_store<NOBS3>(v, partial + (size_t)NOBS3 * b);
+    // block max of the deviation
+    __shared__ double red[8];
+    double m = dev;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if ((tid & 31) == 0) red[tid >> 5] = m;
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0;
+        for (int k = 0; k < 8; ++k) a = fmax(a, red[k]);
+        maxpart[b] = a;
+    }
+}
+
+template <class R>
+__global__ void k3_pop_to_f64(double* __restrict__ dst, const R* __restrict__ src, size_t n) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (double)src[i];
+}
+
+// ---------------------------------------------------------------- host sequencing
+template <class R>
+class Sim3 final : public SimBase {
+  public:
+    struct Layout {
+        size_t pop[2], h[2], phi, qt, q, rho, sig, eps, E, mu, prev, diag, psi_prev, partial, result, stage, total;
+    };
+    static size_t nblocks(const lb3e_params& p) { return (size_t)((p.nx + 31) / 32) * ((p.ny + 7) / 8) * p.nz; }
+    static Layout layout(const lb3e_params& p) {
+        const size_t N = (size_t)p.nx * p.ny * p.nz;
+        Layout L{};
+        size_t o = 0;
+        auto take = [&](size_t b) { size_t a = o; o += (b + 255) & ~size_t(255); return a; };
+        L.pop[0] = take(5 * Q3 * N * sizeof(R));
+        L.pop[1] = take(5 * Q3 * N * sizeof(R));
+        L.h[0] = take(Q3 * N * sizeof(R));
+        L.h[1] = take(Q3 * N * sizeof(R));
+        L.phi = take(3 * N * sizeof(R));
+        L.qt = take(N * sizeof(R));
+        L.q = take(N * sizeof(R));
+        L.rho = take(N * sizeof(R));
+        L.sig = take(N * sizeof(R));
+        L.eps = take(N * sizeof(R));
+        L.E = take(3 * N * sizeof(R));
+        L.mu = take(3 * N * sizeof(R));
+        L.prev = take(12 * N * sizeof(R));
+        L.diag = take(4 * N * sizeof(R));
+        L.psi_prev = take(4 * N * sizeof(R));
+        L.partial = take(nblocks(p) * (NOBS3 + 1) * sizeof(double));
+        L.result = take(64 * sizeof(double));
+        L.stage = take(N * sizeof(double) + 4 * N * sizeof(R));
+        L.total = o;
+        return L;
+    }
+
+    Sim3(const lb3e_params& prm, void* ws, cudaStream_t st) : p_(prm), stream_(st) {
+        L_ = layout(prm);
+        char* b = static_cast<char*>(ws);
+        auto at = [&](size_t off) { return reinterpret_cast<R*>(b + off); };
+        pop_[0] = at(L_.pop[0]); pop_[1] = at(L_.pop[1]); h_[0] = at(L_.h[0]); h_[1] = at(L_.h[1]);
+        phi_ = at(L_.phi); qt_ = at(L_.qt); q_ = at(L_.q); rho_ = at(L_.rho); sig_ = at(L_.sig); eps_ = at(L_.eps);
+        E_ = at(L_.E); mu_ = at(L_.mu); prev_ = at(L_.prev); diag_ = at(L_.diag); psi_prev_ = at(L_.psi_prev);
+        partial_ = reinterpret_cast<double*>(b + L_.partial);
+        result_ = reinterpret_cast<double*>(b + L_.result);
+        stage_ = reinterpret_cast<double*>(b + L_.stage);
+        P_ = make_p3(prm);
+        N_ = P_.N;
+        grid_ = dim3((prm.nx + 31) / 32, (prm.ny + 7) / 8, prm.nz);
+        nblk_ = (int)nblocks(prm);
+    }
+    ~Sim3() override {
+        if (pinned_) cudaFreeHost(pinned_);
+    }
+
+    int init(const double* phi, const double* u, const double* q, const double* noise) override {
+        if (noise) return LB3E_ERR_PARAM;  // the 3-D path takes no population noise
+        if (cudaHostAlloc(reinterpret_cast<void**>(&pinned_), 64 * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
+            return LB3E_ERR_CUDA;
+        TRY(upload(phi, 3 * N_, phi_));
+        if (u) TRY(upload(u, 3 * N_, diag_));
+        else TRY(zero(diag_, 3 * N_ * sizeof(R)));
+        if (q) TRY(upload(q, N_, q_));
+        else TRY(zero(q_, N_ * sizeof(R)));
+        TRY(zero(prev_, 12 * N_ * sizeof(R)));
+        TRY(zero(psi_prev_, 4 * N_ * sizeof(R)));
+        cur_ = hcur_ = 0;
+        k3_props<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, phi_, rho_, sig_, eps_);
+        TRY(launched());
+        k3_init_h<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, h_[0]);
+        TRY(launched());
+        TRY(solve_now());
+        k3_chem<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, phi_, E_, mu_);
+        TRY(launched());
+        k3_init_pops<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, pop_[0], phi_, q_, diag_, mu_, rho_);
+        TRY(launched());
+        step_ = 0;
+        return sync();
+    }
+
+    int step(int nsteps) override {
+        for (int s = 0; s < nsteps; ++s) {
+            const int last = s == nsteps - 1;
+            timer.begin(stream_, KC_MOMENTS);
+            k3_moments<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, pop_[cur_], phi_, qt_, rho_, sig_, eps_);
+            TRY(launched());
+            timer.begin(stream_, KC_PROLOGUE);
+            k3_closure<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, qt_, sig_, eps_, E_, q_);
+            TRY(launched());
+            TRY(solve_now());
+            timer.begin(stream_, KC_OTHER);
+            k3_chem<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, phi_, E_, mu_);
+            TRY(launched());
+            timer.begin(stream_, KC_FUSED);
+            k3_collide<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, pop_[cur_], pop_[cur_ ^ 1], phi_, q_, E_, mu_, rho_,
+                                                              sig_, eps_, prev_, diag_, step_ == 0 ? 1 : 0, last);
+            TRY(launched());
+            cur_ ^= 1;
+            ++step_;
+        }
+        return LB3E_OK;
+    }
+
+    int solve_potential(const double* q, double tol, int max_iter, int check, int* iters, double* res) override {
+        if (q) TRY(upload(q, N_, q_));
+        TRY(poisson(tol, max_iter, 0, check));
+        if (iters) *iters = last_iters_;
+        if (res) *res = last_res_;
+        TRY(sync());
+        return last_conv_ ? LB3E_OK : LB3E_ERR_NOT_CONVERGED;
+    }
+
+    int observables(lb3e_observables_t* o) override {
+        timer.begin(stream_, KC_REDUCE);
+        k3_observables<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, phi_, q_, diag_, partial_,
+                                                              partial_ + (size_t)nblk_ * NOBS3);
+        TRY(launched());
+        k_reduce_partials<NOBS3><<<1, 256, 0, stream_>>>(partial_, nblk_, result_);
+        TRY(launched());
+        k_max_partials<<<1, 256, 0, stream_>>>(partial_ + (size_t)nblk_ * NOBS3, nblk_, result_ + NOBS3);
+        TRY(launched());
+        if (cudaMemcpyAsync(pinned_, result_, (NOBS3 + 1) * sizeof(double), cudaMemcpyDeviceToHost, stream_) !=
+            cudaSuccess)
+            return LB3E_ERR_CUDA;
+        TRY(sync());
+        const double* v = pinned_;
+        std::memset(o, 0, sizeof(*o));
+        for (int i = 0; i < 3; ++i) o->mass[i] = v[i];
+        o->charge = v[3];
+        o->nonfinite = (int64_t)v[4];
+        double Dk[2];
+        for (int k = 0; k < 2; ++k) {
+            const double* m = v + 5 + 5 * k;
+            const double A = m[0];
+            if (!(A > 0)) { Dk[k] = 0.0; continue; }
+            const double xc = m[1] / A, zc = m[2] / A;
+            const double Ixx = m[3] / A - xc * xc, Izz = m[4] / A - zc * zc;
+            const double a = 2.0 * std::sqrt(Izz > 0 ? Izz : 0.0), bb = 2.0 * std::sqrt(Ixx > 0 ? Ixx : 0.0);
+            Dk[k] = (a + bb) > 0 ? (a - bb) / (a + bb) : 0.0;
+        }
+        o->D_inner = Dk[0];
+        o->D_outer = Dk[1];
+        o->max_sum_dev = v[NOBS3];
+        o->poisson_residual = last_res_;
+        o->poisson_iters = last_iters_;
+        o->poisson_converged = last_conv_;
+        o->step = step_;
+        return LB3E_OK;
+    }
+
+    int get_field(int id, double* dst) override {
+        const R* src = nullptr;
+        switch (id) {
+            case LB3E_FIELD_PHI1: case LB3E_FIELD_PHI2: case LB3E_FIELD_PHI3: src = phi_ + (id - LB3E_FIELD_PHI1) * N_; break;
+            case LB3E_FIELD_UX: src = diag_; break;
+            case LB3E_FIELD_UY: src = diag_ + N_; break;
+            case LB3E_FIELD_UZ: src = diag_ + 2 * N_; break;
+            case LB3E_FIELD_P: src = diag_ + 3 * N_; break;
+            case LB3E_FIELD_Q: src = q_; break;
+            case LB3E_FIELD_EX: src = E_; break;
+            case LB3E_FIELD_EY: src = E_ + N_; break;
+            case LB3E_FIELD_EZ: src = E_ + 2 * N_; break;
+            case LB3E_FIELD_MU1: case LB3E_FIELD_MU2: case LB3E_FIELD_MU3: src = mu_ + (id - LB3E_FIELD_MU1) * N_; break;
+            case LB3E_FIELD_PSI: {
+                R* tmp = reinterpret_cast<R*>(stage_ + N_);
+                R* Etmp = tmp + N_;
+                k3_fields<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, h_[hcur_], eps_, Etmp, tmp);
+                TRY(launched());
+                src = tmp;
+                break;
+            }
+            case LB3E_FIELD_PHINOW1: case LB3E_FIELD_PHINOW2: case LB3E_FIELD_PHINOW3: case LB3E_FIELD_QTILDE: {
+                R* tmp = reinterpret_cast<R*>(stage_ + N_);   // 4 planes: phi (3), q~
+                R* scratch = reinterpret_cast<R*>(base_scratch());
+                k3_moments<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, pop_[cur_], tmp, tmp + 3 * N_, scratch,
+                                                                  scratch + N_, scratch + 2 * N_);
+                TRY(launched());
+                src = id == LB3E_FIELD_QTILDE ? tmp + 3 * N_ : tmp + (id - LB3E_FIELD_PHINOW1) * N_;
+                break;
+            }
+            default: break;
+        }
+        if (!src && id >= LB3E_FIELD_POP && id < LB3E_FIELD_POP + 6 * Q3) {
+            const int set = (id - LB3E_FIELD_POP) / Q3, j = (id - LB3E_FIELD_POP) % Q3;
+            src = set < 5 ? pop_[cur_] + (size_t)(Q3 * set + j) * N_ : h_[hcur_] + (size_t)j * N_;
+        }
+        if (!src) return LB3E_ERR_FIELD;
+        k3_pop_to_f64<R><<<(unsigned)((N_ + 255) / 256), 256, 0, stream_>>>(stage_, src, N_);
+        TRY(launched());
+        if (cudaMemcpyAsync(dst, stage_, N_ * sizeof(double), cudaMemcpyDefault, stream_) != cudaSuccess)
+            return LB3E_ERR_CUDA;
+        return sync();
+    }
+
+    size_t state_bytes() const override { return 0; }
+    int save(void*) override { return LB3E_ERR_PARAM; }
+    int load(const void*) override { return LB3E_ERR_PARAM; }
+    int kernel_times(double* ms, int64_t* counts) override {
+        TRY(sync());
+        timer.collect();
+        for (int k = 0; k < KC_COUNT; ++k) {
+            if (ms) ms[k] = timer.ms[k];
+            if (counts) counts[k] = timer.n[k];
+            timer.ms[k] = 0.0;
+            timer.n[k] = 0;
+        }
+        return LB3E_OK;
+    }
+    int64_t potential_iterations() const override { return iters_run_; }
+    int set_chunk(int k) override { return k == 1 ? LB3E_OK : LB3E_ERR_PARAM; }
+    int set_ions(const double*) override { return LB3E_ERR_PARAM; }
+
+  private:
+    // the q~, rho, sigma outputs of a field-readback moments pass go to the
+    // closure-free scratch: the multigrid-free 3-D layout reuses psi_prev's planes
+    // only when no solve is in progress (field readback is between steps)
+    R* base_scratch() { return psi_prev_; }
+    int launched() {
+        ++launches;
+        timer.end(stream_);
+        return cudaGetLastError() == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
+    }
+    int sync() { return cudaStreamSynchronize(stream_) == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA; }
+    int zero(void* p, size_t b) { return cudaMemsetAsync(p, 0, b, stream_) == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA; }
+    int upload(const double* src, size_t n, R* dst) {
+        for (size_t off = 0; off < n; off += N_) {
+            const size_t m = (n - off) < N_ ? (n - off) : N_;
+            if (cudaMemcpyAsync(stage_, src + off, m * sizeof(double), cudaMemcpyDefault, stream_) != cudaSuccess)
+                return LB3E_ERR_CUDA;
+            k_from_f64<R><<<(unsigned)((m + 255) / 256), 256, 0, stream_>>>(dst + off, stage_, m);
+            TRY(launched());
+        }
+        return LB3E_OK;
+    }
+    int solve_now() {
+        if (p_.electric) return poisson(p_.poisson_tol, p_.poisson_max_iter, p_.poisson_fixed_iter, p_.poisson_check_every);
+        k3_fill_E<R><<<(unsigned)((N_ + 255) / 256), 256, 0, stream_>>>(P_, E_);
+        return launched();
+    }
+    // Iterate Eq. 43 until the relative increments of psi and J are <= tol (checked
+    // every `check` iterations before that iteration's collision, against the state
+    // saved one iteration earlier), or exactly `fixed` iterations.
+    int poisson(double tol, int max_iter, int fixed, int check) {
+        const int n = fixed > 0 ? fixed : max_iter;
+        if (check < 1) check = 1;
+        last_res_ = -1.0;
+        last_conv_ = fixed > 0;
+        last_iters_ = n;
+        for (int k = 1; k <= n; ++k) {
+            const int do_check = fixed <= 0 && k >= 2 && k % check == 0;
+            const int save = fixed <= 0 && (k + 1) % check == 0;
+            timer.begin(stream_, KC_POISSON);
+            k3_poisson<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, h_[hcur_], h_[hcur_ ^ 1], eps_, q_, psi_prev_,
+                                                              partial_, save, do_check);
+            TRY(launched());
+            if (do_check) {
+                // the residual of the state before this launch's collision
+                k_reduce_partials<4><<<1, 256, 0, stream_>>>(partial_, nblk_, result_);
+                TRY(launched());
+                if (cudaMemcpyAsync(pinned_, result_, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream_) != cudaSuccess)
+                    return LB3E_ERR_CUDA;
+                TRY(sync());
+                const double dp = pinned_[0], pp = pinned_[1], dj = pinned_[2], jj = pinned_[3];
+                const double r1 = pp > 0.0 ? std::sqrt(dp) / std::sqrt(pp) : (dp > 0.0 ? INFINITY : 0.0);
+                const double r2 = jj > 0.0 ? std::sqrt(dj) / std::sqrt(jj) : (dj > 0.0 ? INFINITY : 0.0);
+                last_res_ = r1 > r2 ? r1 : r2;
+                if (last_res_ <= tol) {
+                    // the launch also collided and streamed: its output is discarded
+                    last_conv_ = 1;
+                    last_iters_ = k - 1;
+                    ++iters_run_;
+                    break;
+                }
+            }
+            hcur_ ^= 1;
+            ++iters_run_;
+        }
+        timer.begin(stream_, KC_FIELDS);
+        k3_fields<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, h_[hcur_], eps_, E_, nullptr);
+        return launched();
+    }
+
+    lb3e_params p_;
+    cudaStream_t stream_;
+    Layout L_;
+    P3 P_{};
+    size_t N_ = 0;
+    dim3 grid_;
+    int nblk_ = 0;
+    R *pop_[2]{}, *h_[2]{}, *phi_{}, *qt_{}, *q_{}, *rho_{}, *sig_{}, *eps_{}, *E_{}, *mu_{}, *prev_{}, *diag_{},
+        *psi_prev_{};
+    double *partial_{}, *result_{}, *stage_{};
+    double* pinned_ = nullptr;
+    int cur_ = 0, hcur_ = 0;
+    int64_t step_ = 0;
+    int last_iters_ = 0, last_conv_ = 0;
+    double last_res_ = -1.0;
+    int64_t iters_run_ = 0;
+};
+
+}  // namespace lb3e

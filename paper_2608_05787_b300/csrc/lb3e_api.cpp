@@ -42,6 +42,11 @@ int validate(const lb3e_params* p) {
     for (double v : vals)
         if (!std::isfinite(v)) return LB3E_ERR_PARAM;
     if (p->ions < 0 || p->ions > 1) return LB3E_ERR_PARAM;
+    if (p->nz < 0 || p->nz > 65535) return LB3E_ERR_PARAM;
+    if (p->nz >= 2) {  // the three-dimensional D3Q15 step
+        if ((int64_t)p->nx * p->ny * p->nz > LB3E_MAX_CELLS || p->ny > LB3E_MAX_NY) return LB3E_ERR_PARAM;
+        if (p->precision > 1 || p->potential_solver != 0 || p->ions) return LB3E_ERR_PARAM;
+    }
     if (p->ions) {  // Nernst-Planck ions: plain precisions, positive diffusivities
         if (p->precision > 2 || !(p->ion_D[0] > 0) || !(p->ion_D[1] > 0)) return LB3E_ERR_PARAM;
         const double iv[] = {p->ion_z[0], p->ion_z[1], p->ion_beta, p->ion_charge};
@@ -52,6 +57,7 @@ int validate(const lb3e_params* p) {
 }
 
 size_t ws_bytes(const lb3e_params& p) {
+    if (p.nz >= 2) return p.precision == 0 ? lb3e::workspace_bytes_3d_f64(p) : lb3e::workspace_bytes_3d_f32(p);
     switch (p.precision) {
         case 0: return lb3e::workspace_bytes_f64(p);
         case 1: return lb3e::workspace_bytes_f32(p);
@@ -68,7 +74,8 @@ int validate_batch(const lb3e_params* ps, int32_t n) {
     int iters = -1;
     for (int i = 0; i < n; ++i) {
         TRY(validate(ps + i));
-        if (ps[i].precision != ps[0].precision || ps[i].precision > 2 || ps[i].potential_solver != 0 || ps[i].ions)
+        if (ps[i].precision != ps[0].precision || ps[i].precision > 2 || ps[i].potential_solver != 0 || ps[i].ions ||
+            ps[i].nz >= 2)
             return LB3E_ERR_PARAM;
         if (ps[i].electric) {
             if (ps[i].poisson_fixed_iter <= 0) return LB3E_ERR_PARAM;
@@ -111,7 +118,10 @@ int lb3e_init(const lb3e_params* params, void* workspace, size_t workspace_bytes
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0 || workspace_bytes < ws_bytes(*params))
         return LB3E_ERR_WORKSPACE;
     lb3e::SimBase* sim = nullptr;
-    switch (params->precision) {
+    if (params->nz >= 2) {
+        sim = params->precision == 0 ? lb3e::make_sim_3d_f64(*params, workspace, stream)
+                                     : lb3e::make_sim_3d_f32(*params, workspace, stream);
+    } else switch (params->precision) {
         case 0: sim = lb3e::make_sim_f64(*params, workspace, stream); break;
         case 1: sim = lb3e::make_sim_f32(*params, workspace, stream); break;
         case 2: sim = lb3e::make_sim_f16s(*params, workspace, stream); break;

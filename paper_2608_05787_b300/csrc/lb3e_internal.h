@@ -107,6 +107,10 @@ size_t workspace_bytes_t32(const lb3e_params& p);
 SimBase* make_sim_t32(const lb3e_params& p, void* ws, void* stream);
 size_t workspace_bytes_t64(const lb3e_params& p);
 SimBase* make_sim_t64(const lb3e_params& p, void* ws, void* stream);
+size_t workspace_bytes_3d_f64(const lb3e_params& p);
+SimBase* make_sim_3d_f64(const lb3e_params& p, void* ws, void* stream);
+size_t workspace_bytes_3d_f32(const lb3e_params& p);
+SimBase* make_sim_3d_f32(const lb3e_params& p, void* ws, void* stream);
 size_t batch_bytes_f64(const lb3e_params* ps, int n);
 BatchBase* new_batch_f64(const lb3e_params* ps, int n, void* ws, void* stream);
 int init_batch_f64(BatchBase* b, const double* const* phis);

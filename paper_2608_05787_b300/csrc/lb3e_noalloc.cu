@@ -80,7 +80,7 @@ extern "C" int lb3e_observables_noalloc(const lb3e_params* params, const double*
     using namespace lb3e;
     if (!params || !phi || !q || !E || !u || !out) return LB3E_ERR_NULL;
     if (params->nx < 2 || params->ny < 2 || params->inner_phase < 1 || params->inner_phase > 3 ||
-        params->matrix_phase < 1 || params->matrix_phase > 3 || !(params->width_D > 0))
+        params->matrix_phase < 1 || params->matrix_phase > 3 || !(params->width_D > 0) || params->nz >= 2)
         return LB3E_ERR_PARAM;
     if ((int64_t)params->nx * params->ny > LB3E_NOALLOC_MAX_CELLS) return LB3E_ERR_TOO_LARGE;
     const dim3 grid = obs_grid(params->nx, params->ny);

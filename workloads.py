@@ -322,3 +322,30 @@ def config_eof_channel(nx: int = 10240, ny: int = 2048, kappa_h: float = 20.0, z
     p = params(**base)
     return dict(name=f"eof_channel_{nx}x{ny}", params=p, phi=single_phase(nx, ny, 1),
                 ions=debye_layers(nx, ny, zeta, kappa, beta), kappa=kappa, steps=1000)
+
+
+def compound_sphere(n: int, r_in: float, r_out: float, W: float) -> np.ndarray:
+    """[3, n, n, n] phases of a compound sphere centred in an n^3 box: core (phase 3)
+    of radius r_in, shell (phase 2) out to r_out, matrix (phase 1); tanh profiles of
+    width W (the three-dimensional counterpart of compound_droplet)."""
+    c = (n - 1) / 2.0
+    z, y, x = np.meshgrid(*(np.arange(n, dtype=float),) * 3, indexing="ij")
+    r = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    core = 0.5 - 0.5 * np.tanh(2.0 * (r - r_in) / W)
+    drop = 0.5 - 0.5 * np.tanh(2.0 * (r - r_out) / W)
+    return np.stack([1.0 - drop, drop - core, core])
+
+
+def config_deformation_3d(n: int = 256, r_out: float = 40.0, r_in: float = 20.0, ca_e: float = 0.5,
+                          precision: int = 1, iters: int = 16, **kw):
+    """Compound drop deforming in a uniform field between electrodes on a D3Q15
+    lattice (the paper's compound-drop deformation runs are three-dimensional):
+    n^3 cells, walls and electrodes normal to z, permittivity 1:2:4, conductivity
+    1:0.5:0.25, Ca_E from Eq. 51.  The potential is iterated a fixed `iters` times a
+    step, warm-started."""
+    eps = (1.0, 2.0, 4.0)
+    E0 = field_for_capillary(ca_e, 1e-3, eps[0], r_out)
+    p = params(nx=n, ny=n, bc_y=2, electric=1, precision=precision, eps=eps, sigma=(1.0, 0.5, 0.25),
+               eps_ref=eps[2], V_bottom=0.0, V_top=E0 * n, charge_convection=1, poisson_fixed_iter=iters, **kw)
+    p["nz"] = n
+    return dict(name=f"deformation3d_{n}^3", params=p, phi=compound_sphere(n, r_in, r_out, 4.0), E0=E0)
