@@ -114,6 +114,31 @@ __device__ __forceinline__ void grad3(const P3& P, const R* __restrict__ f, int 
     }
     g[0] = ocs2(a0); g[1] = ocs2(a1); g[2] = ocs2(a2);
 }
+// Eq. 33 gradients of M fields (planes of one array set) at a cell, one pass over
+// the neighbours: the same sums, in the same order, as M calls of grad3
+template <class R, int M>
+__device__ __forceinline__ void grad3_multi(const P3& P, const R* const (&f)[M], int x, int y, int z, R g[M][3]) {
+    R a[M][3];
+#pragma unroll
+    for (int m = 0; m < M; ++m) a[m][0] = a[m][1] = a[m][2] = R(0);
+#pragma unroll
+    for (int j = 0; j < Q3; ++j) {
+        const size_t n = nb3(P, x, y, z, j);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const R v = w3<R>(j) * f[m][n];
+            cacc(a[m][0], c3x(j), v);
+            cacc(a[m][1], c3y(j), v);
+            cacc(a[m][2], c3z(j), v);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        g[m][0] = ocs2(a[m][0]);
+        g[m][1] = ocs2(a[m][1]);
+        g[m][2] = ocs2(a[m][2]);
+    }
+}
 template <class R>
 __device__ __forceinline__ R lap3(const P3& P, const R* __restrict__ f, int x, int y, int z, size_t c) {
     const R c0 = f[c];
@@ -136,7 +161,8 @@ __device__ __forceinline__ R s3(int j, R u0, R u1, R u2) {   // s_j(u), Eq. 40
     const R cu = cdot3<R>(j, u0, u1, u2);
     const R uu = u0 * u0 + u1 * u1 + u2 * u2;
     const R c2 = R(1) / R(3);
-    return w3<R>(j) * (cu / c2 + cu * cu / (R(2) * c2 * c2) - uu / (R(2) * c2));
+    if constexpr (exact_arith<R>()) return w3<R>(j) * (cu / c2 + cu * cu / (R(2) * c2 * c2) - uu / (R(2) * c2));
+    else return w3<R>(j) * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
 }
 
 // ---------------------------------------------------------------- S1, S2
@@ -260,17 +286,18 @@ __global__ void __launch_bounds__(256) k3_poisson(P3 P, const R* __restrict__ hi
 #pragma unroll
             for (int a = 0; a < 3; ++a) prev[(1 + a) * N + c] = J[a];
         }
-        const R th = R(P.tau_h), epshat = eps[c] - R(P.eps_ref);
-        const R den = epshat + (R(1) / R(3)) * th;
-        const R g0 = -J[0] / den, g1 = -J[1] / den, g2 = -J[2] / den;
-        const R qc = q[c];
+        // divisions: exact in the FP64 build, by a reciprocal formed once in FP32
+        const R th = R(P.tau_h), ith = R(1.0 / P.tau_h), epshat = eps[c] - R(P.eps_ref);
+        const R den = epshat + (R(1) / R(3)) * th, iden = rcp(den);
+        const R g0 = dv(-J[0], den, iden), g1 = dv(-J[1], den, iden), g2 = dv(-J[2], den, iden);
+        const R qc = q[c], e3 = ocs2(epshat);
 #pragma unroll
         for (int j = 0; j < Q3; ++j) {
             const R heq = j == 0 ? (w3<R>(0) - R(1)) * psi : w3<R>(j) * psi;     // Eq. 44
             const R varpi = j == 0 ? R(0) : R(1.0 / 14.0);
             const R hj = hin[j * N + c];
             const R cg = cdot3<R>(j, g0, g1, g2);
-            const R v = hj - (hj - heq) / th - (epshat / (R(1) / R(3))) * w3<R>(j) * cg / th + varpi * qc;
+            const R v = hj - dv(hj - heq, th, ith) - dv(e3 * w3<R>(j) * cg, th, ith) + varpi * qc;
             size_t t;
             if (target3(P, x, y, z, j, t)) {
                 hout[j * N + t] = v;
@@ -362,12 +389,16 @@ __global__ void __launch_bounds__(256) k3_collide(P3 P, const R* __restrict__ pi
     R ph[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) ph[i] = phi[i * N + c];
-    const R qc = q[c], rho = rho_f[c];
+    const R qc = q[c], rho = rho_f[c], irho = rcp(rho);
     const R Ev[3] = {E[c], E[N + c], E[2 * N + c]};
-    // S7, S8: grad mu_i, F = -sum phi_i grad mu_i + q E
-    R gmu[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) grad3<R>(P, mu + i * N, x, y, z, gmu[i]);
+    // S7, S8: grad mu_i (and, in the same neighbour pass, grad eps, grad sigma,
+    // grad rho), F = -sum phi_i grad mu_i + q E
+    R gg[6][3];
+    {
+        const R* const fl[6] = {mu, mu + N, mu + 2 * N, eps_f, sig_f, rho_f};
+        grad3_multi<R, 6>(P, fl, x, y, z, gg);
+    }
+    R (&gmu)[6][3] = gg;
     R F[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -377,10 +408,9 @@ __global__ void __launch_bounds__(256) k3_collide(P3 P, const R* __restrict__ pi
         F[a] = Fa + qc * Ev[a];
     }
     // R^n of Eq. 47
-    R ge3[3], gs3[3], gr[3];
-    grad3<R>(P, eps_f, x, y, z, ge3);
-    grad3<R>(P, sig_f, x, y, z, gs3);
-    grad3<R>(P, rho_f, x, y, z, gr);
+    const R* ge3 = gg[3];
+    const R* gs3 = gg[4];
+    const R* gr = gg[5];
     R Rc;
     {
         const R r = sig_f[c] / eps_f[c];
@@ -406,9 +436,9 @@ __global__ void __launch_bounds__(256) k3_collide(P3 P, const R* __restrict__ pi
             cacc(m2, c3z(j), g[j]);
             if (j) g1 += g[j];
         }
-        u[0] = (m0 + R(0.5) * F[0]) / rho;
-        u[1] = (m1 + R(0.5) * F[1]) / rho;
-        u[2] = (m2 + R(0.5) * F[2]) / rho;
+        u[0] = dv(m0 + R(0.5) * F[0], rho, irho);
+        u[1] = dv(m1 + R(0.5) * F[1], rho, irho);
+        u[2] = dv(m2 + R(0.5) * F[2], rho, irho);
         const R ugr = u[0] * gr[0] + u[1] * gr[1] + u[2] * gr[2];
         p = c2 / (R(1) - w3<R>(0)) * (g1 + R(0.5) * ugr + rho * s3<R>(0, u[0], u[1], u[2]));
     }
@@ -422,7 +452,8 @@ __global__ void __launch_bounds__(256) k3_collide(P3 P, const R* __restrict__ pi
     for (int a = 0; a < 3; ++a) dqu[a] = first ? R(0) : qc * u[a] - prev[(9 + a) * N + c];
 
     // S11: phase populations with the mobility of Eq. 28
-    const R tf = R(P.tau_f), m0 = R(P.m0), pf = R(1) - R(1) / (R(2) * tf);
+    const R tf = R(P.tau_f), itf = R(1.0 / P.tau_f), m0 = R(P.m0), im0 = R(1.0 / P.m0);
+    const R pf = R(1) - R(1) / (R(2) * tf);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         R Mii = R(0);
@@ -438,16 +469,16 @@ __global__ void __launch_bounds__(256) k3_collide(P3 P, const R* __restrict__ pi
         }
         R A[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) A[a] = dpu[i][a] / c2 - Y[a] / m0;
+        for (int a = 0; a < 3; ++a) A[a] = ocs2(dpu[i][a]) - dv(Y[a], m0, im0);
         const R mui = mu[i * N + c];
         const R pu0 = ph[i] * u[0], pu1 = ph[i] * u[1], pu2 = ph[i] * u[2];
 #pragma unroll
         for (int j = 0; j < Q3; ++j) {
             const R feq = (j == 0) ? ph[i] - (R(1) - w3<R>(0)) * mui
-                                   : w3<R>(j) * mui + w3<R>(j) * cdot3<R>(j, pu0, pu1, pu2) / c2;
+                                   : w3<R>(j) * mui + ocs2(w3<R>(j) * cdot3<R>(j, pu0, pu1, pu2));
             const R Fj = w3<R>(j) * cdot3<R>(j, A[0], A[1], A[2]);
             const R fj = pin[(Q3 * (i + 1) + j) * N + c];
-            const R v = fj - (fj - feq) / tf + pf * Fj;
+            const R v = fj - dv(fj - feq, tf, itf) + pf * Fj;
             size_t t;
             if (target3(P, x, y, z, j, t)) pout[(Q3 * (i + 1) + j) * N + t] = v;
             else pout[(Q3 * (i + 1) + opp3(j)) * N + c] = v;
@@ -460,39 +491,39 @@ __global__ void __launch_bounds__(256) k3_collide(P3 P, const R* __restrict__ pi
             R eta = R(0);
 #pragma unroll
             for (int i = 0; i < 3; ++i) eta += ph[i] * R(P.visc[i]);
-            tg = R(0.5) + eta / (rho * c2);
+            tg = R(0.5) + dv(eta, rho * c2, irho * R(3));
         }
-        const R pg = R(1) - R(1) / (R(2) * tg);
+        const R itg = rcp(tg), pg = R(1) - R(1) / (R(2) * tg);
         const R ugr = u[0] * gr[0] + u[1] * gr[1] + u[2] * gr[2];
 #pragma unroll
         for (int j = 0; j < Q3; ++j) {
-            const R geq = (j == 0) ? (w3<R>(0) - R(1)) * p / c2 + rho * s3<R>(0, u[0], u[1], u[2])
-                                   : w3<R>(j) * p / c2 + rho * s3<R>(j, u[0], u[1], u[2]);
+            const R geq = (j == 0) ? ocs2((w3<R>(0) - R(1)) * p) + rho * s3<R>(0, u[0], u[1], u[2])
+                                   : ocs2(w3<R>(j) * p) + rho * s3<R>(j, u[0], u[1], u[2]);
             const R cu = cdot3<R>(j, u[0], u[1], u[2]);
             const R cgr = cdot3<R>(j, gr[0], gr[1], gr[2]);
             const R cF = cdot3<R>(j, F[0], F[1], F[2]);
-            const R G = w3<R>(j) * (ugr + cF / c2 + (cu * cgr - c2 * ugr) / c2);
-            const R v = g[j] - (g[j] - geq) / tg + pg * G;
+            const R G = w3<R>(j) * (ugr + ocs2(cF) + ocs2(cu * cgr - c2 * ugr));
+            const R v = g[j] - dv(g[j] - geq, tg, itg) + pg * G;
             size_t t;
             if (target3(P, x, y, z, j, t)) {
                 pout[j * N + t] = v;
             } else {
                 const R uw = R(c3z(j) > 0 ? P.uwt : P.uwb);
-                pout[opp3(j) * N + c] = v - R(2) * w3<R>(j) * rho * (R(c3x(j)) * uw) / c2;
+                pout[opp3(j) * N + c] = v - ocs2(R(2) * w3<R>(j) * rho * (R(c3x(j)) * uw));
             }
         }
     }
     // S13: charge populations
     {
-        const R tl = R(P.tau_l), pl = R(1) - R(1) / (R(2) * tl);
+        const R tl = R(P.tau_l), itl = R(1.0 / P.tau_l), pl = R(1) - R(1) / (R(2) * tl);
 #pragma unroll
         for (int j = 0; j < Q3; ++j) {
             const R cu = cdot3<R>(j, u[0], u[1], u[2]);
-            const R leq = P.cc ? w3<R>(j) * qc * (R(1) + cu / c2) : w3<R>(j) * qc;
+            const R leq = P.cc ? w3<R>(j) * qc * (R(1) + ocs2(cu)) : w3<R>(j) * qc;
             const R Sj = pl * w3<R>(j) * Rc;
-            const R Tj = P.cc ? pl * w3<R>(j) * cdot3<R>(j, dqu[0], dqu[1], dqu[2]) / c2 : R(0);
+            const R Tj = P.cc ? ocs2(pl * w3<R>(j) * cdot3<R>(j, dqu[0], dqu[1], dqu[2])) : R(0);
             const R lj = pin[(Q3 * 4 + j) * N + c];
-            const R v = lj - (lj - leq) / tl + Sj + Tj;
+            const R v = lj - dv(lj - leq, tl, itl) + Sj + Tj;
             size_t t;
             if (target3(P, x, y, z, j, t)) pout[(Q3 * 4 + j) * N + t] = v;
             else pout[(Q3 * 4 + opp3(j)) * N + c] = v;
