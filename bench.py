@@ -10,6 +10,11 @@ the residual test passes, and the fused chemical-potential/force/collide/stream
 pass.  Metric: MLUPS = cells x steps / second (all population sets updated per
 cell per step).  Inputs are synthetic (the stated initial condition, no dataset).
 
+Other workloads (`--workload`): sweep (the batched parameter sweep), regimes (drop
+pairs and confined shear as one batch), adjoint (tangent-mode derivatives), eof (the
+electro-osmotic channel with Nernst-Planck ions), deformation3d (the D3Q15 step on a
+256^3 compound drop).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lb3e|reference]
 Under torchrun (N > 1) every rank steps its own replica (no data exchange: a
 single lattice does not shard without a halo exchange); value = all ranks' cell
@@ -104,7 +109,8 @@ def kernel_source_hash() -> str:
     for name in KERNEL_SOURCES:
         h.update((ROOT / "paper_2608_05787_b300" / "csrc" / name).read_bytes())
     common = [a for i, a in enumerate(B.COMMON) if a != "-I" and (i == 0 or B.COMMON[i - 1] != "-I")]
-    h.update(repr((B.ARCH, common, sorted(B.UNITS.items()))).encode())
+    units = [(u, B.UNITS[u]) for u in KERNEL_SOURCES if u in B.UNITS]
+    h.update(repr((B.ARCH, common, units)).encode())
     return h.hexdigest()[:16]
 
 
