@@ -841,9 +841,9 @@ class Sim3 final : public SimBase {
     int set_ions(const double*) override { return LB3E_ERR_PARAM; }
 
   private:
-    // the q~, rho, sigma outputs of a field-readback moments pass go to the
-    // closure-free scratch: the multigrid-free 3-D layout reuses psi_prev's planes
-    // only when no solve is in progress (field readback is between steps)
+    // Scratch for the rho, sigma, eps outputs of a field-readback moments pass: the
+    // residual-check planes.  Field readback happens between steps, and every solve
+    // saves those planes before its first check reads them.
     R* base_scratch() { return psi_prev_; }
     int launched() {
         ++launches;

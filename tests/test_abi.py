@@ -92,3 +92,32 @@ def test_batches_refuse_ion_transport():
     assert L.lib().lb3e_batch_workspace_bytes(ps, 2, C.byref(nb)) == -1
     ps[0].ions = ps[1].ions = 0
     assert L.lib().lb3e_batch_workspace_bytes(ps, 2, C.byref(nb)) == 0 and nb.value > 0
+
+
+def test_three_dimensional_lattices_validated_and_sized():
+    """nz >= 2 selects the D3Q15 step: FP64/FP32 and the LB potential only, no ions;
+    the workspace holds 2 x 75 population planes, 2 x 15 potential planes and the
+    fields (about 220 words a cell in FP32)."""
+    p = dict(W.params(nx=64, ny=48), nz=40)
+    n = 64 * 48 * 40
+    b64 = L.workspace_bytes(dict(p, precision=0))
+    b32 = L.workspace_bytes(dict(p, precision=1))
+    assert 200 * 4 * n < b32 < 240 * 4 * n and b64 > 1.9 * b32
+    for bad in (dict(precision=2), dict(precision=3), dict(potential_solver=1), dict(ions=1, ion_D=(0.1, 0.1)),
+                dict(nz=70000)):
+        with pytest.raises(L.LB3EError) as e:
+            L.workspace_bytes(dict(p, **bad))
+        assert e.value.code == -1
+    # nz 0 or 1 is the two-dimensional step, and a dict without the key means 0
+    assert L.workspace_bytes(dict(p, nz=1)) == L.workspace_bytes(W.params(nx=64, ny=48))
+    ps = (L.Params * 2)(L.Params.from_dict(p), L.Params.from_dict(p))
+    nb = C.c_size_t(0)
+    assert L.lib().lb3e_batch_workspace_bytes(ps, 2, C.byref(nb)) == -1
+
+
+def test_params_default_the_optional_fields():
+    """Dicts written before the ion and three-dimensional fields existed still map:
+    ions off, nz 0."""
+    d = {k: v for k, v in W.params().items() if k not in ("ions", "ion_D", "ion_z", "ion_beta", "ion_charge")}
+    s = L.Params.from_dict(d)
+    assert s.ions == 0 and s.nz == 0 and s.precision == d["precision"]
