@@ -277,6 +277,40 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_sample(args):
+    """The reference arm for the eof and deformation3d workloads: the oracle, as it
+    stands, stepping a bounded sample of that workload on the host cores (rank 0)."""
+    import oracle
+    import workloads as W
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    if args.workload == "eof":
+        nx, ny = 1280, 256
+        c = W.config_eof_channel(nx=nx, ny=ny, precision=0)
+        o = oracle.Oracle(c["params"], c["phi"], ions=c["ions"])
+        cells, name = nx * ny, f"electro-osmotic channel with Nernst-Planck ions, {nx}x{ny} sample of 10240x2048"
+    else:
+        m = 48
+        c = W.config_deformation_3d(n=m, r_out=40.0 * m / 256, r_in=20.0 * m / 256, precision=0)
+        o = oracle.Oracle3D(c["params"], c["phi"])
+        cells, name = m ** 3, f"compound drop deformation under field, D3Q15, {m}^3 sample of 256^3"
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    per_step = (time.perf_counter() - t0) / max(1, args.steps)
+    value = cells / per_step / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (as the lb3e arm)",
+            "config": {"workload": name},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} timed steps of the {name} (radii scaled alike)"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_lb3e(args):
     import torch
     import paper_2608_05787_b300 as L
@@ -829,7 +863,9 @@ def run_adjoint(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.impl == "reference" and args.workload in ("eof", "deformation3d"):
+        run_reference_sample(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "sweep":
         run_sweep(args)
