@@ -215,3 +215,24 @@ def test_couette_between_moving_walls_normal_to_z():
     exact = Ub + (Ut - Ub) * (z + 0.5) / nz
     assert np.abs(o.field("ux") - exact[:, None, None]).max() < 1e-7 * Ut
     assert np.abs(o.field("uz")).max() < 1e-9 * Ut and np.abs(o.field("uy")).max() < 1e-18
+
+
+def test_charge_transport_with_walls_reduces_exactly_to_two_dimensions():
+    """With the flow exactly at rest (one phase, no field: mu = 0 and qE = 0), the
+    charge populations (Eq. 46-50) of a y-invariant state between walls normal to z
+    evolve as the D2Q9 ones: the D3Q15 equilibrium, source and bounce-back project
+    exactly onto the x-z plane.  A charge blob diffusing and relaxing (sigma/eps)
+    beside a wall agrees with the two-dimensional oracle to rounding over 200 steps."""
+    nx, nz = 24, 16
+    base = dict(bc_y=1, electric=0, sigma=(0.02, 0.02, 0.02), eps=(1.0, 1.0, 1.0), alpha=0.1, E_ext=(0.0, 0.0))
+    x = np.arange(nx)[None, :]
+    z = np.arange(nz)[:, None]
+    q2 = 1e-3 * np.exp(-((x - 9.3) ** 2 + (z - 2.2) ** 2) / 8.0)
+    phi2 = W.single_phase(nx, nz, 1)
+    o2 = oracle.Oracle(W.params(nx=nx, ny=nz, **base), phi2, q=q2).step(200)
+    o3 = oracle.Oracle3D(params3(nz, nx=nx, ny=2, **base), np.repeat(phi2[:, :, None, :], 2, axis=2),
+                         q=np.repeat(q2[:, None, :], 2, axis=1)).step(200)
+    a, b = o2.field("q"), o3.field("q")[:, 0]
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+    assert np.abs(a).max() < 0.5 * 1e-3          # it did relax
+    assert np.abs(o3.field("ux")).max() == 0.0 and np.abs(o3.field("uz")).max() == 0.0
