@@ -6,7 +6,10 @@ Whole-lattice array operations replace the oracle's per-cell loops: neighbours
 come from index arrays (x periodic; y periodic, or mirrored about the half-way
 walls for stencils), streaming shifts whole planes and reflects what crosses a wall.
 Only the fixed-iteration potential solve is implemented (the residual-controlled
-stop is a host decision, covered elsewhere).
+stop is a host decision, covered elsewhere).  Optionally the two Nernst-Planck ion
+species of Eq. 52 (the reading in the design notes: per species a D2Q9 set with
+equilibrium w_j n (1 + c_j . v / cs2), v = u + z beta D E, the backward-difference
+source of d/dt(n v), bounce-back walls; the charge they carry replaces the closure).
 """
 from __future__ import annotations
 
@@ -20,7 +23,7 @@ CS2 = 1.0 / 3.0
 
 
 class Twin:
-    def __init__(self, p: dict, phi, u=None, q=None, noise=None):
+    def __init__(self, p: dict, phi, u=None, q=None, noise=None, ions=None):
         self.p = dict(p)
         self.ny, self.nx = int(p["ny"]), int(p["nx"])
         ny, nx = self.ny, self.nx
@@ -54,6 +57,23 @@ class Twin:
             self.l = self.l + nz[4]
         self.prev_phiu = np.zeros((3, 2, ny, nx))
         self.prev_qu = np.zeros((2, ny, nx))
+        self.ion = None
+        if ions is not None:
+            # start the species: their charge, a potential solve, each set at equilibrium
+            n = np.asarray(ions, dtype=float)
+            self.q = p["ion_charge"] * (p["ion_z"][0] * n[0] + p["ion_z"][1] * n[1])
+            self._solve_potential()
+            self.ion = np.array([self._neq(k, n[k]) for k in range(2)])
+            self.prev_nv = np.zeros((2, 2, ny, nx))
+
+    def _drift(self, k):                        # v_k = u + z_k beta D_k E
+        p = self.p
+        m = p["ion_z"][k] * p["ion_beta"] * p["ion_D"][k]
+        return self.u[0] + m * self.E[0], self.u[1] + m * self.E[1]
+
+    def _neq(self, k, n):
+        vx, vy = self._drift(k)
+        return np.array([W[j] * n * (1 + (CX[j] * vx + CY[j] * vy) / CS2) for j in range(9)])
 
     # ---------------------------------------------------------------- lattice helpers
     def _rows(self, dy):
@@ -194,7 +214,11 @@ class Twin:
         r = self.sig / self.eps
         Ex, Ey = self.E                                                             # E of the last step
         src = r * (self.geps[0] * Ex + self.geps[1] * Ey) - (self.gsig[0] * Ex + self.gsig[1] * Ey)
-        self.q = (qt + 0.5 * src) / (1 + 0.5 * r)                                   # S4 (reading R9)
+        if self.ion is None:
+            self.q = (qt + 0.5 * src) / (1 + 0.5 * r)                               # S4 (reading R9)
+        else:                                                                       # the ions' charge
+            nion = self.ion.sum(1)
+            self.q = p["ion_charge"] * (p["ion_z"][0] * nion[0] + p["ion_z"][1] * nion[1])
         self._solve_potential()                                                     # S5
         Ex, Ey = self.E
         R = -r * self.q + r * (self.geps[0] * Ex + self.geps[1] * Ey) - (self.gsig[0] * Ex + self.gsig[1] * Ey)
@@ -258,6 +282,22 @@ class Twin:
         self.f = np.array([self._stream(fpost[i], "bb") for i in range(3)])
         self.g = self._stream(gpost, "flow")
         self.l = self._stream(lpost, "bb")
+        if self.ion is not None:                                                    # Eq. 52 (ions)
+            new = np.empty_like(self.ion)
+            for k in range(2):
+                tk = 0.5 + p["ion_D"][k] / CS2
+                vx, vy = self._drift(k)
+                nk = nion[k]
+                nv = np.array([nk * vx, nk * vy])
+                dnv = np.zeros_like(nv) if first else nv - self.prev_nv[k]
+                neq = self._neq(k, nk)
+                post = np.empty_like(self.ion[k])
+                for j in range(9):
+                    Tj = (1 - 1 / (2 * tk)) * W[j] * (CX[j] * dnv[0] + CY[j] * dnv[1]) / CS2
+                    post[j] = self.ion[k, j] - (self.ion[k, j] - neq[j]) / tk + Tj
+                new[k] = self._stream(post, "bb")
+                self.prev_nv[k] = nv
+            self.ion = new
         self.prev_phiu = phiu
         self.prev_qu = qu
         self.step_count += 1

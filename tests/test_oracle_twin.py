@@ -56,3 +56,27 @@ def test_oracle_and_numpy_twin_agree(bc_y):
         ref = o.field(f)
         scale = max(np.abs(ref).max(), 1e-300)
         assert np.abs(fields[f] - ref).max() <= 1e-13 * scale, (f, np.abs(fields[f] - ref).max(), scale)
+
+
+@pytest.mark.parametrize("bc_y", [0, 2])
+def test_oracle_and_numpy_twin_agree_with_ion_transport(bc_y):
+    """The same check with the Nernst-Planck species on (valences +1 and -2, unequal
+    D, concentrations 1 and 1/2 +- 20%): ion populations and every field."""
+    p, phi, u, q, noise = _case(bc_y)
+    p = dict(p, ions=1, ion_D=(0.05, 0.12), ion_z=(1.0, -2.0), ion_beta=4.0, ion_charge=1e-3)
+    n = W.ion_concentrations(8, 8, 1.0, 0.2, seed=5)
+    n[1] *= 0.5
+    o = oracle.Oracle(p, phi, u=u, q=q, noise=noise, ions=n)
+    t = Twin(p, phi, u=u, q=q, noise=noise, ions=n)
+    for step in (0, 5):
+        if step:
+            o.step(step)
+            t.step(step)
+        for k, name in enumerate(("n1", "n2")):
+            ref = np.array([o.pop(name, j) for j in range(9)])
+            assert np.abs(t.ion[k] - ref).max() <= 1e-13 * np.abs(ref).max(), (step, name)
+        _compare(o, t)
+    fields = {"q": t.q, "psi": t.psi, "ex": t.E[0], "ey": t.E[1], "ux": t.u[0], "uy": t.u[1]}
+    for f, a in fields.items():
+        ref = o.field(f)
+        assert np.abs(a - ref).max() <= 1e-13 * max(np.abs(ref).max(), 1e-300), f
