@@ -38,7 +38,8 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 METRIC = "MLUPS"
-# algorithmic bytes per cell (compulsory traffic, see the design notes)
+# algorithmic bytes per cell: the compulsory traffic of each kernel (every array it must
+# read or write once per cell), not counting halo re-reads
 FUSED_BYTES = {0: 8 * 112, 1: 4 * 112, 2: 2 * 90 + 4 * 22}   # k_fused: 45 pops r+w, phi, q, E, d/dt state
 POISSON_BYTES = {0: 8 * 20, 1: 4 * 20, 2: 4 * 20}           # one pseudo-iteration: h 9 r + 9 w, eps, q
 STEP_BYTES = {0: 960, 1: 480, 2: 300}                        # whole step without the potential loop

@@ -317,7 +317,10 @@ void lb3e_batch_destroy(lb3e_batch* b);
  * any stream capture.  All calls share the one array, so calls that overlap on
  * the GPU (different streams or threads, same device) race; serialise them.
  * Each call overwrites what the previous one left there.
- * Errors: NULL, PARAM, TOO_LARGE (nx * ny > LB3E_NOALLOC_MAX_CELLS), CUDA.
+ * params is checked as lb3e_init checks it; the arrays are not checked: each must
+ * hold the stated number of doubles for params' nx and ny, on the current device.
+ * Errors: NULL, PARAM (a field lb3e_init rejects, or nz >= 2), TOO_LARGE (nx * ny >
+ * LB3E_NOALLOC_MAX_CELLS), CUDA.
  * Synchronises `stream`. */
 int lb3e_observables_noalloc(const lb3e_params* params, const double* phi, const double* q,
                              const double* E, const double* u, void* stream,

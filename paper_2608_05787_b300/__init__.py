@@ -178,16 +178,28 @@ def observables_noalloc(params: dict, phi, q, E, u, stream=None) -> dict:
     """The observables reductions on caller-provided FP64 CUDA tensors, for callers
     that cannot allocate device memory: the scratch is a fixed array inside the
     library (lattices up to 2048 x 2048).  phi [3,ny,nx], q [ny,nx], E and u
-    [2,ny,nx], all contiguous float64 on the current device."""
+    [2,ny,nx], all contiguous float64 CUDA tensors on one device, with nx and ny
+    those of ``params`` (checked here: the C entry point cannot see the sizes)."""
     import torch
-    for t in (phi, q, E, u):
+    ny, nx = int(params["ny"]), int(params["nx"])
+    shapes = ((phi, (3, ny, nx)), (q, (ny, nx)), (E, (2, ny, nx)), (u, (2, ny, nx)))
+    for t, shape in shapes:
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
             raise TypeError("lb3e_observables_noalloc takes contiguous float64 CUDA tensors")
-    st = stream if stream is not None else torch.cuda.current_stream()
-    o = Observables()
-    _check("lb3e_observables_noalloc",
-           lib().lb3e_observables_noalloc(C.byref(Params.from_dict(params)), phi.data_ptr(), q.data_ptr(),
-                                          E.data_ptr(), u.data_ptr(), st.cuda_stream, C.byref(o)))
+        if tuple(t.shape) != shape:
+            raise ValueError(f"lb3e_observables_noalloc: a field of shape {tuple(t.shape)}, expected {shape}")
+        if t.device != phi.device:
+            raise ValueError("lb3e_observables_noalloc: all fields must be on one device")
+    # the library launches on the current device: make it the fields' device, and
+    # take that device's current stream unless one is given
+    with torch.cuda.device(phi.device):
+        st = stream if stream is not None else torch.cuda.current_stream(phi.device)
+        if st.device != phi.device:
+            raise ValueError("lb3e_observables_noalloc: the stream is on another device than the fields")
+        o = Observables()
+        _check("lb3e_observables_noalloc",
+               lib().lb3e_observables_noalloc(C.byref(Params.from_dict(params)), phi.data_ptr(), q.data_ptr(),
+                                              E.data_ptr(), u.data_ptr(), st.cuda_stream, C.byref(o)))
     return o.as_dict()
 
 

@@ -54,15 +54,23 @@ def build(force: bool = False, verbose: bool = False) -> Path:
         return LIB
     BUILD.mkdir(exist_ok=True)
     nvcc = _nvcc()
-    objs = []
+    cmds, objs = [], []
     for unit, extra in UNITS.items():
         obj = BUILD / (unit + ".o")
         lang = ["-x", "cu"] if unit.endswith(".cu") else []
-        cmd = [nvcc, *ARCH, *COMMON, *extra, *lang, "-c", str(CSRC / unit), "-o", str(obj)]
+        cmds.append([nvcc, *ARCH, *COMMON, *extra, *lang, "-c", str(CSRC / unit), "-o", str(obj)])
+        objs.append(str(obj))
+    # the translation units are independent: compile them concurrently
+    from concurrent.futures import ThreadPoolExecutor
+
+    def run(cmd):
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)
-        objs.append(str(obj))
+
+    with ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as ex:
+        for f in [ex.submit(run, c) for c in cmds]:
+            f.result()
     tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
     subprocess.run([nvcc, *ARCH, "-shared", "-o", str(tmp), *objs], check=True)
     os.replace(tmp, LIB)

@@ -13,9 +13,10 @@ struct lb3e_handle {
     lb3e_params params;
 };
 
-namespace {
+namespace lb3e {
 
-int validate(const lb3e_params* p) {
+// every parameter of the model and the run checked for range and finiteness
+int validate_params(const lb3e_params* p) {
     if (!p) return LB3E_ERR_NULL;
     if (p->nx < 2 || p->ny < 2) return LB3E_ERR_PARAM;
     if ((int64_t)p->nx * p->ny > LB3E_MAX_CELLS) return LB3E_ERR_PARAM;  // 32-bit plane offsets
@@ -55,6 +56,12 @@ int validate(const lb3e_params* p) {
     }
     return LB3E_OK;
 }
+
+}  // namespace lb3e
+
+namespace {
+
+int validate(const lb3e_params* p) { return lb3e::validate_params(p); }
 
 size_t ws_bytes(const lb3e_params& p) {
     if (p.nz >= 2) return p.precision == 0 ? lb3e::workspace_bytes_3d_f64(p) : lb3e::workspace_bytes_3d_f32(p);

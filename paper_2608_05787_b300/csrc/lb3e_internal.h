@@ -21,6 +21,9 @@ namespace lb3e {
 
 struct DevParams;
 
+// range and finiteness checks of every lb3e_params field (LB3E_OK or LB3E_ERR_*)
+int validate_params(const lb3e_params* p);
+
 // kernel classes for the timing facility (lb3e_kernel_times)
 enum KernelClass { KC_MOMENTS = 0, KC_PROLOGUE, KC_POISSON, KC_REDUCE, KC_FIELDS, KC_FUSED, KC_OTHER, KC_IONS,
                    KC_COUNT };

@@ -79,10 +79,12 @@ extern "C" int lb3e_observables_noalloc(const lb3e_params* params, const double*
                                         lb3e_observables_t* out) {
     using namespace lb3e;
     if (!params || !phi || !q || !E || !u || !out) return LB3E_ERR_NULL;
-    if (params->nx < 2 || params->ny < 2 || params->inner_phase < 1 || params->inner_phase > 3 ||
-        params->matrix_phase < 1 || params->matrix_phase > 3 || !(params->width_D > 0) || params->nz >= 2)
-        return LB3E_ERR_PARAM;
+    // the same checks as lb3e_init (ranges, positivity, finiteness), then the
+    // limits of this entry point: two-dimensional lattices within the fixed scratch
+    if (params->nx < 2 || params->ny < 2) return LB3E_ERR_PARAM;
     if ((int64_t)params->nx * params->ny > LB3E_NOALLOC_MAX_CELLS) return LB3E_ERR_TOO_LARGE;
+    TRY(validate_params(params));
+    if (params->nz >= 2) return LB3E_ERR_PARAM;
     const dim3 grid = obs_grid(params->nx, params->ny);
     const int64_t nblk64 = (int64_t)grid.x * grid.y;
     // NOBS sums and one max per block must fit before the result slots

@@ -1,5 +1,7 @@
 """A second, independent implementation of the method's step in vectorised NumPy,
-written from the paper's equations and the readings listed in the design notes
+written from the paper's equations (where the paper leaves a step open, the same
+reading as the oracle: the source of Eq. 36 with c_j on the mobility part, the
+closed-form charge of Eq. 50 with the previous field, half-way walls)
 (test infrastructure: it checks the C oracle's transcription on tiny lattices).
 
 Whole-lattice array operations replace the oracle's per-cell loops: neighbours
@@ -7,7 +9,7 @@ come from index arrays (x periodic; y periodic, or mirrored about the half-way
 walls for stencils), streaming shifts whole planes and reflects what crosses a wall.
 Only the fixed-iteration potential solve is implemented (the residual-controlled
 stop is a host decision, covered elsewhere).  Optionally the two Nernst-Planck ion
-species of Eq. 52 (the reading in the design notes: per species a D2Q9 set with
+species of Eq. 52 (the paper prints no lattice scheme for them; read as, per species, a D2Q9 set with
 equilibrium w_j n (1 + c_j . v / cs2), v = u + z beta D E, the backward-difference
 source of d/dt(n v), bounce-back walls; the charge they carry replaces the closure).
 """

@@ -138,8 +138,10 @@ def debye_layers(nx: int, ny: int, zeta: float, kappa: float, beta: float, n0: f
 
 
 # ---------------------------------------------------------------------------
-# The five workloads.  Sizes and parameters are the stated ones; where a value is
-# left open, the reading used is the one listed in the design notes.
+# The five workloads.  Sizes and parameters are the stated ones.  Where a value is
+# left open: gamma = 1e-3, D = 4, rho = 1 and tau_g = 0.8 everywhere; permittivity
+# and conductivity taken literally in lattice units; E0 from Eq. 51 with the
+# matrix permittivity and the outer radius.
 # ---------------------------------------------------------------------------
 
 def config_static_compound(precision: int = 0, n: int = 64, field: bool = True, **kw):
