@@ -139,6 +139,45 @@ class Twin:
         self.gsig = np.array(self._grad(self.sig))
         self.grho = np.array(self._grad(self.rho))
 
+    def observables(self) -> dict:
+        """The reductions over the last step's fields: phase masses, total charge, the
+        parts of the free energy of Eq. 18 summed over cells (phase: bulk
+        6 lambda_i phi_i^2 (1 - phi_i)^2 / D plus gradient 3 D lambda_i |grad phi_i|^2 / 8
+        with the Eq. 33 gradient; electric eps |E|^2 / 2; kinetic rho |u|^2 / 2; charge
+        alpha q^2 / (2 sigma) where sigma > 0), max |sum phi - 1|, and the deformation
+        factors (a - b)/(a + b) of the indicators phi_inner and 1 - phi_matrix, with a
+        and b twice the standard deviations of the indicator along y and x."""
+        p, ph = self.p, self.phi
+        D = p["width_D"]
+        ny, nx = self.ny, self.nx
+        out = {f"mass{i + 1}": float(ph[i].sum()) for i in range(3)}
+        out["charge"] = float(self.q.sum())
+        fphi = 0.0
+        for i in range(3):
+            gx, gy = self._grad(ph[i])
+            fphi += float((6.0 * self.lam[i] / D * ph[i] ** 2 * (1 - ph[i]) ** 2
+                           + 3.0 * D * self.lam[i] / 8.0 * (gx ** 2 + gy ** 2)).sum())
+        out["F_phi"] = fphi
+        eps = sum(p["eps"][i] * ph[i] ** 2 * (3 - 2 * ph[i]) for i in range(3))
+        out["F_E"] = float((0.5 * eps * (self.E[0] ** 2 + self.E[1] ** 2)).sum())
+        rho = sum(ph[i] * p["rho"][i] for i in range(3))
+        out["F_u"] = float((0.5 * rho * (self.u[0] ** 2 + self.u[1] ** 2)).sum())
+        sig = sum(ph[i] * p["sigma"][i] for i in range(3))
+        safe = np.where(sig > 0, sig, 1.0)
+        out["F_q"] = float(np.where(sig > 0, 0.5 * p["alpha"] / safe * self.q ** 2, 0.0).sum())
+        out["max_sum_dev"] = float(np.abs(ph.sum(axis=0) - 1.0).max())
+        y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+        for key, chi in (("D_inner", ph[p["inner_phase"] - 1]), ("D_outer", 1.0 - ph[p["matrix_phase"] - 1])):
+            A = chi.sum()
+            if not A > 0:
+                out[key] = 0.0
+                continue
+            xm, ym = (chi * x).sum() / A, (chi * y).sum() / A
+            a = 2.0 * np.sqrt(max(((chi * (y - ym) ** 2).sum() / A), 0.0))
+            b = 2.0 * np.sqrt(max(((chi * (x - xm) ** 2).sum() / A), 0.0))
+            out[key] = float((a - b) / (a + b)) if a + b > 0 else 0.0
+        return out
+
     def _heq(self, psi):
         h = np.empty((9,) + psi.shape)
         h[0] = (W[0] - 1.0) * psi                                                   # Eq. 44

@@ -593,3 +593,78 @@ def test_lb_potential_converges_to_the_fd_solution_with_variable_permittivity():
         diffs.append(np.abs(psi[0] - psi[1]).max() / np.abs(psi[1]).max())
     rates = [math.log2(diffs[k] / diffs[k + 1]) for k in range(2)]
     assert diffs[-1] < 5e-4 and min(rates) > 1.3, (diffs, rates)
+
+
+# --------------------------------------------------------------------------- observables (Eq. 18, Section 5.3)
+def _ellipse(nx, ny, a, b, xc, yc, W=4.0):
+    """Smooth indicator of an ellipse with semi-axis a along y and b along x: a tanh
+    of the elliptic radius, so its second moments scale exactly as a^2 and b^2."""
+    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    r = np.sqrt(((x - xc) / b) ** 2 + ((y - yc) / a) ** 2)
+    return 0.5 + 0.5 * np.tanh(2.0 * (1.0 - r) * np.sqrt(a * b) / W)
+
+
+def test_deformation_factors_of_ellipses():
+    """Section 5.3's D = (a - b)/(a + b), a along the field (y), b across it, from the
+    indicator's second moments: the inner indicator phi_inner and the outer one
+    1 - phi_matrix, on two off-centre ellipses of different shape and orientation."""
+    n = 256
+    inner = _ellipse(n, n, 30.0, 20.0, 127.3, 129.6)          # elongated along y: D = +0.2
+    outer = _ellipse(n, n, 50.0, 70.0, 127.3, 129.6)          # elongated along x: D = -1/6
+    phi3 = inner
+    phi2 = outer * (1.0 - inner)
+    phi = np.stack([1.0 - phi2 - phi3, phi2, phi3])
+    p = W.params(nx=n, ny=n, bc_y=1, electric=0, inner_phase=3, matrix_phase=1)
+    obs = oracle.Oracle(p, phi).observables()
+    assert abs(obs["D_inner"] - 0.2) < 1e-6, obs["D_inner"]
+    assert abs(obs["D_outer"] - (-20.0 / 120.0)) < 1e-6, obs["D_outer"]
+    # a sharp ellipse: the same value up to the lattice quadrature of its edge
+    y, x = np.meshgrid(np.arange(n, dtype=float), np.arange(n, dtype=float), indexing="ij")
+    sharp = ((((x - 120.4) / 40.0) ** 2 + ((y - 131.1) / 60.0) ** 2) <= 1.0).astype(float)
+    phi = np.stack([1.0 - sharp, np.zeros_like(sharp), sharp])
+    obs = oracle.Oracle(p, phi).observables()
+    assert abs(obs["D_inner"] / 0.2 - 1.0) < 5e-3, obs["D_inner"]
+    assert abs(obs["D_outer"] / 0.2 - 1.0) < 5e-3, obs["D_outer"]
+
+
+def test_electric_energy_of_a_uniform_and_a_layered_dielectric():
+    """Eq. 18's electric part |D|^2/(2 eps) = eps |E|^2 / 2 summed over cells.
+    Uniform permittivity 2.5 between electrodes: E = dV/ny exactly, so F_E =
+    eps (dV/ny)^2 N / 2.  Sharp layers of permittivity 1 and 4 (series
+    capacitor): E_k = dV / (L_1/eps_1 + L_3/eps_3) / eps_k in each layer, F_E =
+    sum_k eps_k E_k^2 L_k nx / 2 (the LB potential is exact on cell-wise layers)."""
+    nx, ny, V = 8, 64, 0.3
+    p = W.params(nx=nx, ny=ny, bc_y=2, electric=1, V_top=V, eps=(2.5, 2.5, 2.5), eps_ref=2.5,
+                 poisson_tol=1e-13, poisson_max_iter=400000)
+    o = oracle.Oracle(p, W.single_phase(nx, ny, 1))
+    assert abs(o.observables()["F_E"] / (0.5 * 2.5 * (V / ny) ** 2 * nx * ny) - 1.0) < 1e-9
+    phi = np.zeros((3, ny, nx))
+    phi[0, : ny // 2] = 1.0
+    phi[2, ny // 2:] = 1.0
+    p = dict(p, eps=(1.0, 2.0, 4.0), eps_ref=4.0)
+    o = oracle.Oracle(p, phi)
+    L = ny / 2
+    D = V / (L / 1.0 + L / 4.0)
+    want = 0.5 * nx * L * (D ** 2 / 1.0 + D ** 2 / 4.0)
+    assert abs(o.observables()["F_E"] / want - 1.0) < 1e-9, (o.observables()["F_E"], want)
+
+
+def test_charge_and_kinetic_energy_of_uniform_states():
+    """Eq. 18's charge part alpha q^2 / (2 sigma) and the kinetic part rho |u|^2 / 2,
+    summed over cells, on the initial state: uniform q and u over two half-lattices
+    of phases with different conductivity and density."""
+    nx, ny = 16, 12
+    q0, u0, v0, alpha = 2e-3, 3e-3, -1e-3, 0.1
+    phi = np.zeros((3, ny, nx))
+    phi[0, : ny // 2] = 1.0
+    phi[1, ny // 2:] = 1.0
+    p = W.params(nx=nx, ny=ny, bc_y=1, electric=0, alpha=alpha, sigma=(0.4, 0.1, 0.2), rho=(1.0, 3.0, 1.0))
+    u = np.stack([np.full((ny, nx), u0), np.full((ny, nx), v0)])
+    o = oracle.Oracle(p, phi, u=u, q=np.full((ny, nx), q0))
+    obs = o.observables()
+    half = nx * ny / 2
+    want_q = 0.5 * alpha * q0 ** 2 * half * (1 / 0.4 + 1 / 0.1)
+    want_u = 0.5 * (u0 ** 2 + v0 ** 2) * half * (1.0 + 3.0)
+    assert abs(obs["F_q"] / want_q - 1.0) < 1e-12, (obs["F_q"], want_q)
+    assert abs(obs["F_u"] / want_u - 1.0) < 1e-12, (obs["F_u"], want_u)
+    assert abs(obs["charge"] / (q0 * nx * ny) - 1.0) < 1e-12

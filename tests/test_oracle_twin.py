@@ -58,6 +58,35 @@ def test_oracle_and_numpy_twin_agree(bc_y):
         assert np.abs(fields[f] - ref).max() <= 1e-13 * scale, (f, np.abs(fields[f] - ref).max(), scale)
 
 
+OBS = ("mass1", "mass2", "mass3", "charge", "F_phi", "F_E", "F_u", "F_q", "max_sum_dev", "D_inner", "D_outer")
+
+
+@pytest.mark.parametrize("bc_y", [0, 1, 2])
+def test_oracle_and_numpy_twin_observables_agree(bc_y):
+    """The reductions of the oracle (masses, charge, the Eq. 18 energy parts, the sum
+    deviation, the deformation factors) against the twin's own, after init and after
+    5 steps of the all-terms case on a 16 x 12 lattice (off-centre compound drop)."""
+    p, _, _, _, _ = _case(bc_y)
+    nx, ny = 16, 12
+    p = dict(p, nx=nx, ny=ny)
+    phi = W.compound_droplet(nx, ny, 2.5, 4.5, 2.0, xc=7.3, yc=5.6)
+    rng = np.random.default_rng(9)
+    u = 1e-3 * rng.standard_normal((2, ny, nx))
+    q = 1e-3 * rng.standard_normal((ny, nx))
+    o = oracle.Oracle(p, phi, u=u, q=q)
+    t = Twin(p, phi, u=u, q=q)
+    for n in (0, 5):
+        if n:
+            o.step(n)
+            t.step(n)
+        ref, got = o.observables(), t.observables()
+        for k in OBS:
+            # D is a small difference of two radii: compared on its own O(1) scale
+            scale = 1.0 if k.startswith("D_") else max(abs(ref[k]), 1e-300)
+            assert abs(got[k] - ref[k]) <= 1e-12 * scale, (n, k, got[k], ref[k])
+        assert got["D_inner"] != 0.0 and got["F_E"] > 0 and got["F_q"] > 0
+
+
 @pytest.mark.parametrize("bc_y", [0, 2])
 def test_oracle_and_numpy_twin_agree_with_ion_transport(bc_y):
     """The same check with the Nernst-Planck species on (valences +1 and -2, unequal
