@@ -4,11 +4,17 @@
 Workload: compound drop deforming under a uniform field on a 4096 x 4096
 lattice (outer radius 600, inner 300, electric capillary number 0.5,
 permittivity 1:2:4, conductivity 1:0.5:0.25, surface-charge convection on), the
-potential solved to a relative residual of 1e-8 every step.  A "step" is one full
-time step: moments, stencils and charge closure, the potential iterations until
-the residual test passes, and the fused chemical-potential/force/collide/stream
-pass.  Metric: MLUPS = cells x steps / second (all population sets updated per
-cell per step).  Inputs are synthetic (the stated initial condition, no dataset).
+potential solved every step until the relative increments of psi and J of the
+pseudo-time LB iteration (Eq. 42-45) are <= 1e-8.  By default the LB iteration
+runs on an FP64 anchor with a multigrid coarse correction (the same discrete
+fixed point as the plain iteration, reached in a few hundred iterations instead of
+~1e5; `--potential lb` runs the plain iteration, which stalls on its FP32 rounding
+floor at this size).  The line reports, over the timed steps, how many solves
+reached the tolerance and the largest final residual.  A "step" is one full time
+step: moments, stencils and charge closure, the potential solve, and the fused
+chemical-potential/force/collide/stream pass.  Metric: MLUPS = cells x steps /
+second (all population sets updated per cell per step).  Inputs are synthetic (the
+stated initial condition, no dataset).
 
 Other workloads (`--workload`): sweep (the batched parameter sweep), regimes (drop
 pairs and confined shear as one batch), adjoint (tangent-mode derivatives), eof (the
@@ -38,10 +44,24 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 METRIC = "MLUPS"
+SOLVER_NAMES = {
+    0: "LB pseudo-time iterations of Eq. 42-45, h in the build's precision",
+    1: "multigrid V-cycles on the finite-difference form of Eq. 27d",
+    2: "LB pseudo-time iterations of Eq. 42-45 on an FP64 anchor, multigrid coarse correction every check "
+       "(fixed point of Eq. 43; stop on its increments)",
+    3: "LB pseudo-time iterations of Eq. 42-45 on an FP64 anchor",
+}
 # algorithmic bytes per cell: the compulsory traffic of each kernel (every array it must
 # read or write once per cell), not counting halo re-reads
 FUSED_BYTES = {0: 8 * 112, 1: 4 * 112, 2: 2 * 90 + 4 * 22}   # k_fused: 45 pops r+w, phi, q, E, d/dt state
 POISSON_BYTES = {0: 8 * 20, 1: 4 * 20, 2: 4 * 20}           # one pseudo-iteration: h 9 r + 9 w, eps, q
+# one pseudo-iteration on the correction to the FP64 anchor: delta 9 r + 9 w, eps,
+# and the anchor's increment (9 planes) instead of q
+POISSON_RS_BYTES = {0: 8 * 28, 1: 4 * 28, 2: 4 * 28}
+# one anchor refresh (two launches): fold and FP64 collision (anchor 9 r + 9 w,
+# delta 9 r + 9 w, eps, q, 9 FP64 staging planes written) and increment (anchor and
+# staging read, 9 increment planes written)
+ANCHOR_BYTES = {0: 72 * 4 + 8 * 20 + 72 + 8 * 9, 1: 72 * 4 + 4 * 20 + 72 + 4 * 9, 2: 72 * 4 + 4 * 20 + 72 + 4 * 9}
 STEP_BYTES = {0: 960, 1: 480, 2: 300}                        # whole step without the potential loop
 # multigrid cycle per fine cell (defect correction): the FP64 fine residual (psi,
 # rhs, 3 coefficients read, residual written: 48 B), then the FP32 V-cycle on the
@@ -77,10 +97,10 @@ def parse():
     ap.add_argument("--n", type=int, default=4096, help="lattice side (the stated workload is 4096)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
-    ap.add_argument("--cpu-sample", type=int, default=1024, help="side of the oracle's CPU sample lattice")
-    ap.add_argument("--cpu-iters", type=int, default=0, help="potential iterations per step in the CPU sample")
-    ap.add_argument("--potential", default="lb", choices=["lb", "mg"],
-                    help="lb: the paper's pseudo-time LB solve (default); mg: multigrid on its FD form")
+    ap.add_argument("--potential", default="lbmg", choices=["lb", "mg", "lbmg", "lba"],
+                    help="lb: the paper's pseudo-time LB solve, h in the build's precision; mg: multigrid on its "
+                         "FD form; lbmg: the LB solve on an FP64 anchor with a multigrid coarse correction; "
+                         "lba: the LB solve on an FP64 anchor")
     ap.add_argument("--max-iter", type=int, default=0,
                     help="cap on LB potential iterations per step (default: the workload's 20000); profiling "
                          "runs use a small cap to keep ncu captures short, and config records it")
@@ -176,104 +196,95 @@ def dist_env():
     return ws, rank, local
 
 
-def _oracle_sample(n: int, iters: int, solver: int = 0):
+def _oracle_sample(n: int, iters: int = 0, solver: int = 0, tol: float = 1e-8):
+    """The oracle on an n^2 lattice of the deformation workload (radii scaled), with
+    the LB potential iterated to `tol` each step (or a fixed count when iters > 0),
+    or with its FD solve (solver 1)."""
     import oracle
     import workloads as W
     scale = n / 4096.0
     cfg = W.config_deformation(n=n, r_out=600.0 * scale, r_in=300.0 * scale)
-    return oracle.Oracle(dict(cfg["params"], poisson_fixed_iter=iters, potential_solver=solver), cfg["phi"])
+    p = dict(cfg["params"], poisson_fixed_iter=iters, potential_solver=solver, poisson_tol=tol,
+             poisson_max_iter=10 ** 7)
+    return oracle.Oracle(p, cfg["phi"])
+
+
+# side of the oracle's sample lattice: the plain LB iteration needs O(n^2) iterations
+# a step, so the sample stays small enough for a bounded run
+CPU_SAMPLE_LB = 128
+CPU_SAMPLE_MG = 256
+# the workload's potential tolerance (relative increment, every step)
+WORKLOAD_TOL = 1e-8
+
+
+def _time_oracle_steps(o, warmup: int, steps: int):
+    o.step(warmup)
+    iters, t = [], 0.0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        o.step(1)
+        t += time.perf_counter() - t0
+        iters.append(o.last_poisson()[0])
+    return t / steps, iters
 
 
 def cpu_baseline(args, iters_per_step: float):
     """The oracle, as it stands, on the host cores, on a bounded sample of the
-    workload: a cpu_sample^2 lattice with the geometry scaled.  Timed (init
-    excluded): one time step with a single potential iteration, and 40 potential
-    iterations on their own; the step time is projected to the potential
-    iterations per step that the GPU needed."""
-    n = args.cpu_sample
+    workload: a small lattice with the geometry scaled and the same potential
+    tolerance.  Measured step times (no projection), init untimed."""
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    if getattr(args, "potential", "lb") == "mg":
-        # the oracle's own FD solve (conjugate gradients to 1e-13, O(n) iterations),
-        # one full step on a 256^2 sample to stay within the baseline's time budget
-        n = min(n, 256)
-        o = _oracle_sample(n, 1, solver=1)
-        t0 = time.perf_counter()
-        o.step(1)
-        dt = time.perf_counter() - t0
-        return {"value": n * n / dt / 1e6, "unit": METRIC, "cores": cores, "kind": "oracle",
-                "sample": f"one step of a {n}x{n} lattice of the same workload (radii scaled) with the oracle's "
-                          "FD potential solve (conjugate gradients to 1e-13); init untimed",
-                "seconds_per_step": dt}
-    o = _oracle_sample(n, 1)
-    t0 = time.perf_counter()
-    o.step(1)
-    t_step1 = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    o.solve_potential(fixed=40, max_iter=40)
-    per_iter = (time.perf_counter() - t0) / 40
-    base = max(1e-9, t_step1 - per_iter)
-    it = args.cpu_iters or iters_per_step
-    dt = base + it * per_iter
-    return {"value": n * n / dt / 1e6, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": f"{n}x{n} lattice of the same workload (radii scaled): one step with 1 potential iteration "
-                      f"and 40 potential iterations timed separately, projected to {it:.1f} iterations per step "
-                      "(the GPU's mean); init untimed",
-            "seconds_per_step": dt, "seconds_per_potential_iteration": per_iter, "seconds_rest_of_step": base}
+    if getattr(args, "potential", "lbmg") == "mg":
+        n = CPU_SAMPLE_MG
+        o = _oracle_sample(n, solver=1)
+        per_step, _ = _time_oracle_steps(o, 0, 1)
+        sample = (f"one step of a {n}x{n} lattice of the same workload (radii scaled) with the oracle's FD "
+                  "potential solve (conjugate gradients to 1e-13); init untimed")
+        iters = None
+    else:
+        n = CPU_SAMPLE_LB
+        o = _oracle_sample(n, tol=WORKLOAD_TOL)
+        per_step, iters = _time_oracle_steps(o, 1, 2)
+        sample = (f"2 steps (after 1 untimed) of a {n}x{n} lattice of the same workload (radii scaled), the "
+                  f"oracle's plain LB potential iteration to the same relative increment {WORKLOAD_TOL:g} "
+                  "every step (the same discrete fixed point as the GPU's solve); init untimed")
+    return {"value": n * n / per_step / 1e6, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample,
+            "projected": False, "seconds_per_step": per_step, "sample_potential_iters": iters}
 
 
 def run_reference(args):
     """The oracle timed on the host cores for the same metric as the lb3e arm; rank 0
-    only.  Each timed step is a bounded sample of the workload: a cpu_sample^2
-    lattice with the geometry scaled.
-    * LB potential: the sample steps with a few potential iterations; the cost of
-      one iteration is timed on its own, and the step time is projected to the
-      iterations per step of the workload, its cap (the FP32 GPU solve runs to the
-      cap every step at 4096^2; --max-iter lowers it for both arms).
-    * multigrid (--potential mg): the oracle's own FD solve (conjugate gradients to
-      1e-13) on a sample of at most 256^2."""
+    only.  Each timed step is a measured step of a bounded sample of the workload: a
+    small lattice with the geometry scaled, the potential solved to the same
+    tolerance by the oracle's plain LB iteration (or, with --potential mg, its FD
+    solve by conjugate gradients)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    n = min(args.cpu_sample, args.n)
-    mg = getattr(args, "potential", "lb") == "mg"
+    mg = getattr(args, "potential", "lbmg") == "mg"
     if mg:
-        n = min(n, 256)
-        o = _oracle_sample(n, 1, solver=1)
-        iters, target, per_iter = None, None, 0.0
-    else:
-        iters = args.cpu_iters or 30
-        target = args.max_iter or 20000
-        o = _oracle_sample(n, iters)
-    o.step(args.warmup)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        o.step(1)
-        times.append(time.perf_counter() - t0)
-    per_step = statistics.mean(times)
-    if not mg:
-        t0 = time.perf_counter()
-        o.solve_potential(fixed=40, max_iter=40)
-        per_iter = (time.perf_counter() - t0) / 40
-        per_step = max(1e-9, per_step - iters * per_iter) + target * per_iter
-        sample = (f"{args.steps} timed steps of a {n}x{n} lattice of the same workload (radii scaled) with "
-                  f"{iters} potential iterations each, plus 40 iterations timed alone; projected to {target} "
-                  f"iterations per step")
-        cfg = {"potential_iters_per_step": target, "potential_solver": "LB pseudo-time iterations (Eq. 43)"}
-    else:
-        sample = (f"{args.steps} timed steps of a {n}x{n} lattice of the same workload (radii scaled), the "
-                  f"oracle's FD potential solve (conjugate gradients to 1e-13)")
+        n = min(CPU_SAMPLE_MG, args.n)
+        o = _oracle_sample(n, solver=1)
         cfg = {"potential_solver": "FD form, conjugate gradients (oracle)"}
+        sample = (f"{args.steps} timed steps of a {n}x{n} lattice of the same workload (radii scaled), the "
+                  "oracle's FD potential solve (conjugate gradients to 1e-13)")
+    else:
+        n = min(CPU_SAMPLE_LB, args.n)
+        o = _oracle_sample(n, tol=WORKLOAD_TOL)
+        cfg = {"potential_solver": "LB pseudo-time iterations of Eq. 42-45, plain (oracle)",
+               "poisson_tol": WORKLOAD_TOL}
+        sample = (f"{args.steps} timed steps of a {n}x{n} lattice of the same workload (radii scaled), the "
+                  f"potential iterated to the relative increment {WORKLOAD_TOL:g} every step")
+    per_step, iters = _time_oracle_steps(o, args.warmup, args.steps)
     value = n * n / per_step / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (stated initial condition of the workload)",
             "config": dict({"workload": f"compound drop deformation under field, {args.n}x{args.n}",
-                            "sample_side": n}, **cfg),
+                            "sample_side": n, "potential_iters_per_step": iters}, **cfg),
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample,
-                             "seconds_per_potential_iteration": per_iter},
+                             "projected": False},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -337,6 +348,11 @@ def run_lb3e(args):
         params = dict(params, poisson_max_iter=args.max_iter)
     if args.potential == "mg":
         params = dict(params, potential_solver=1, poisson_max_iter=50)
+    elif args.potential in ("lbmg", "lba"):
+        # a coarse correction (lbmg) every 32 iterations; the plain anchored iteration
+        # (lba) checks every 16
+        params = dict(params, potential_solver=2 if args.potential == "lbmg" else 3,
+                      poisson_check_every=args.check_every or (32 if args.potential == "lbmg" else 16))
     N = args.n * args.n
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -349,6 +365,7 @@ def run_lb3e(args):
         init_obs = sim.observables()
         sim.step(args.warmup)
         torch.cuda.synchronize()
+        sim.potential_stats()
         sim.set_timing(True)
         l0 = sim.launches
         it0 = sim.potential_iterations
@@ -366,7 +383,9 @@ def run_lb3e(args):
         pot_iters = sim.potential_iterations - it0
         kt = sim.kernel_times()
         sim.set_timing(False)
+        pstats = sim.potential_stats()
         obs = sim.observables()
+        fd_res = sim.fd_residual() if params["electric"] else None
 
     t = ms / 1e3
     if dist:
@@ -377,40 +396,53 @@ def run_lb3e(args):
     value = total_cells / t / 1e6
 
     hbm, peak_kind = peaks()
-    poisson_ms, poisson_n = kt["poisson"]
     fused_ms, fused_n = kt["fused"]
     iters_per_step = pot_iters / args.steps
     kernels = {}
     for name, (kms, kn) in kt.items():
         if kn:
             kernels[name] = {"launches": kn, "ms_total": kms, "share": kms / max(1e-12, sum(v[0] for v in kt.values()))}
-    k_gbs = {}
-    if fused_n:
-        k_gbs["fused"] = FUSED_BYTES[prec] * N / (fused_ms / fused_n / 1e3) / 1e9
-    mg = bool(params.get("potential_solver"))
-    pot_bytes = MG_VCYCLE_BYTES if mg else POISSON_BYTES[prec]
-    if poisson_n:
-        # per pseudo-iteration (the unit of the algorithmic figure); a blocked launch runs several
-        k_gbs["poisson"] = pot_bytes * N * pot_iters / (poisson_ms / 1e3) / 1e9
-    dominant = max(("fused", "poisson"), key=lambda k: kt[k][0])
-    per_cell = FUSED_BYTES[prec] if dominant == "fused" else pot_bytes
+    solver = int(params.get("potential_solver", 0))
+    mg = solver == 1
+    anchored = solver in (2, 3)
     chunk = args.chunk or 4
-    if dominant == "fused":
-        kname = "k_fused"
-    elif mg:
-        kname = "multigrid V-cycle kernels"
-    else:
-        kname = "k_poisson_tb" if chunk > 1 else "k_poisson"
-    traffic = None if mg and dominant == "poisson" else profiled_traffic(
-        f"{kname}:{prec}" + (f":{chunk}" if kname == "k_poisson_tb" else ""))
-    roofline = {"bound": "hbm", "achieved": k_gbs.get(dominant), "peak": hbm, "unit": "GB/s",
-                "frac": (k_gbs.get(dominant) or 0) / hbm, "traffic": traffic * N if traffic else None,
-                "kernel": kname,
-                "peak_kind": f"{peak_kind} copy bandwidth",
-                "algorithmic_bytes_per_launch": per_cell * N * (pot_iters / max(1, poisson_n) if dominant == "poisson" else 1),
-                "units_per_launch": (f"{N} cells x {pot_iters / max(1, poisson_n):.2f} pseudo-iterations"
-                                     if dominant == "poisson" else f"{N} cells"),
+    # per kernel class: algorithmic bytes per launch (units x bytes per unit), the
+    # mean launch time, the kernel that carries the class, and its unit
+    classes = {}
+    if fused_n:
+        classes["fused"] = (FUSED_BYTES[prec] * N, fused_ms / fused_n, "k_fused", f"{N} cells")
+    poisson_ms, poisson_n = kt["poisson"]
+    if poisson_n and not mg:
+        per_it = POISSON_RS_BYTES[prec] if anchored else POISSON_BYTES[prec]
+        ipl = pot_iters / poisson_n
+        kname = ("k_poisson_tb_rs" if chunk > 1 else "k_poisson_rs") if anchored else \
+            ("k_poisson_tb" if chunk > 1 else "k_poisson")
+        classes["poisson"] = (per_it * N * ipl, poisson_ms / poisson_n, kname,
+                              f"{N} cells x {ipl:.2f} pseudo-iterations ({per_it} B per cell-iteration)")
+    elif poisson_n:
+        classes["poisson"] = (MG_VCYCLE_BYTES * N * pot_iters / poisson_n, poisson_ms / poisson_n,
+                              "multigrid V-cycle kernels", f"{N} cells x V-cycles")
+    anchor_ms, anchor_n = kt.get("anchor", (0.0, 0))
+    if anchor_n:
+        classes["anchor"] = (ANCHOR_BYTES[prec] * N, anchor_ms / (anchor_n / 2), "k_anchor_refresh + k_anchor_residual",
+                             f"{N} cells, one refresh (two launches)")
+    k_gbs = {k: b / (t / 1e3) / 1e9 for k, (b, t, _, _) in classes.items()}
+    dominant = max(classes, key=lambda k: kt[k][0])
+    dbytes, dms, kname, units = classes[dominant]
+    key = f"{kname}:{prec}" + (f":{chunk}" if kname in ("k_poisson_tb", "k_poisson_tb_rs") else "")
+    traffic = None if kname.startswith("multigrid") else profiled_traffic(key)
+    roofline = {"bound": "hbm", "achieved": k_gbs[dominant], "peak": hbm, "unit": "GB/s",
+                "frac": k_gbs[dominant] / hbm, "traffic": traffic * N if traffic else None,
+                "dram_frac": (traffic * N / (dms / 1e3) / 1e9 / hbm) if traffic else None,
+                "kernel": kname, "peak_kind": f"{peak_kind} copy bandwidth",
+                "algorithmic_bytes_per_launch": dbytes, "units_per_launch": units, "ms_per_launch": dms,
                 "other_kernel_gbs": {k: v for k, v in k_gbs.items() if k != dominant}}
+    # the whole step: fused step bytes (Section 8 figure) + potential iterations +
+    # anchor refreshes, over the measured step time
+    step_bytes = STEP_BYTES[prec] * N + (classes["poisson"][0] * poisson_n if "poisson" in classes else 0) / \
+        args.steps + ANCHOR_BYTES[prec] * N * (anchor_n / 2) / args.steps
+    step_roofline = {"bytes_per_step": step_bytes, "achieved": step_bytes / (ms / args.steps / 1e3) / 1e9,
+                     "frac": step_bytes / (ms / args.steps / 1e3) / 1e9 / hbm}
 
     # end to end through the public API: pinned host initial fields, init (with its
     # potential solve), K steps each followed by an observables read-back
@@ -458,13 +490,16 @@ def run_lb3e(args):
             "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic (stated initial condition of the workload)",
             "config": {"workload": f"compound drop deformation under field, {args.n}x{args.n}",
-                       "poisson_tol": params["poisson_tol"], "poisson_max_iter": params["poisson_max_iter"], "potential_chunk": args.chunk or 4, "potential_iters_per_step": iters_per_step,
-                       "potential_solver": ("multigrid V-cycles on the FD form" if params.get("potential_solver")
-                                            else "LB pseudo-time iterations (Eq. 43)"),
+                       "poisson_tol": params["poisson_tol"], "poisson_max_iter": params["poisson_max_iter"],
+                       "poisson_check_every": params["poisson_check_every"], "potential_chunk": chunk,
+                       "potential_iters_per_step": iters_per_step,
+                       "anchor_refreshes_per_step": (anchor_n / 2) / args.steps,
+                       "potential_solver": SOLVER_NAMES[solver],
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single lattice",
                        "l2": "working set (%.1f GB) exceeds the 126 MB L2; no flush needed" % (L.workspace_bytes(params) / 1e9),
                        "init_seconds": t_init, "init_potential_iters": init_obs["poisson_iters"]},
             "roofline": roofline,
+            "step_roofline": step_roofline,
             "kernels": kernels,
             "fused_mlups": N / (fused_ms / fused_n / 1e3) / 1e6 if fused_n else None,
             "step_bytes_per_cell_no_potential": STEP_BYTES[prec],
@@ -474,6 +509,7 @@ def run_lb3e(args):
             "clocks": clk.summary(),
             "observables": {k: obs[k] for k in ("D_inner", "D_outer", "max_sum_dev", "poisson_residual",
                                                  "poisson_iters", "nonfinite")},
+            "potential_timed_steps": dict(pstats, fd_residual_after=fd_res),
         }
         print(json.dumps(line), flush=True)
     if dist:

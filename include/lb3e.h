@@ -118,11 +118,25 @@ typedef struct lb3e_params {
      * gamma13, gamma23).  Fields are then available per direction (see
      * LB3E_TANGENT). */
     int32_t tangent_param[3];
-    /* 0: the paper's pseudo-time LB potential solve (Eq. 42-45); 1: geometric
-     * multigrid on the finite-difference form of Eq. 27d (5-point, harmonic-mean
-     * faces, half-cell Dirichlet electrodes; bc_y = 2, even nx, precision <= 2), FP64, V-cycles until
-     * the relative residual is <= poisson_tol (at most poisson_max_iter cycles);
-     * E is then the Eq. 33 gradient of psi */
+    /* 0: the paper's pseudo-time LB potential solve (Eq. 42-45), h in the build's
+     *    precision;
+     * 1: geometric multigrid on the finite-difference form of Eq. 27d (5-point,
+     *    harmonic-mean faces, half-cell Dirichlet electrodes; bc_y = 2, even nx,
+     *    precision <= 2), FP64, V-cycles until the relative residual is <=
+     *    poisson_tol (at most poisson_max_iter cycles); E is then the Eq. 33
+     *    gradient of psi;
+     * 2: the LB solve of Eq. 42-45 (same fixed point as 0) with h held as an FP64
+     *    anchor plus a correction in the build's precision, and a multigrid coarse
+     *    correction at every check (every poisson_check_every iterations): the
+     *    residual of the macroscopic equation, read from the LB increment, drives
+     *    one FP32 V-cycle of the finite-difference operator whose solution enters h
+     *    as its local equilibrium.  The stopping test is the LB increment of 0,
+     *    taken in FP64 (bc_y = 2, even nx, precision <= 2);
+     * 3: as 2 without the coarse correction (the plain pseudo-time iteration on an
+     *    FP64 anchor; precision <= 2).
+     * With poisson_fixed_iter > 0, solvers 2 and 3 run exactly that many plain
+     * pseudo-iterations (no corrections).  Solvers 0, 2 and 3 stop, not converged,
+     * when the residual stalls (no 1% gain over 32 checks; 8 for solver 2). */
     int32_t potential_solver;
     /* 1: two Nernst-Planck ion species (Eq. 52; Section 5.1's electro-osmotic
      * check) carry the charge, q = ion_charge * sum_i ion_z[i] n_i, in place of the
@@ -163,7 +177,8 @@ typedef struct lb3e_observables_t {
     int64_t nonfinite;       /* non-finite phi, u or q values */
     int64_t step;            /* completed time steps */
     int32_t poisson_iters;   /* iterations of the last solve */
-    int32_t poisson_converged;
+    int32_t poisson_converged; /* 1 reached poisson_tol (or a fixed count ran); 0 hit the
+                                  iteration cap; -1 stopped on a stalled residual */
 } lb3e_observables_t;
 
 typedef struct lb3e_handle lb3e_handle;
@@ -211,6 +226,22 @@ int lb3e_state_bytes(const lb3e_handle* h, size_t* bytes);
 int lb3e_save_state(lb3e_handle* h, void* dst);
 int lb3e_load_state(lb3e_handle* h, const void* src);
 
+/* Potential solves since the previous call (or lb3e_init): how many ran, how many
+ * ended above the tolerance (iteration cap or a stalled residual), and the largest
+ * final residual among them (-1: none taken, e.g. fixed counts).  Host counters:
+ * no synchronisation.  The counters are then cleared.  Errors: NULL. */
+int lb3e_potential_stats(lb3e_handle* h, int64_t* solves, int64_t* not_converged, double* max_residual);
+
+/* Diagnostic for the potential of the last solve: ||b - A psi|| / ||b|| (FP64) with
+ * A psi = b the finite-difference form of div(eps grad psi) + q = 0 (5-point
+ * stencil, harmonic-mean faces; electrodes as Dirichlet faces at half a cell, b = q
+ * plus their 2 eps V terms; plain walls carry no flux), for this step's eps and q.
+ * For the LB solvers it measures how close the LB fixed point is to that
+ * discretisation (they differ at second order); for solver 1 it is the solve's own
+ * residual.  Synchronises the stream.  Errors: NULL, PARAM (electric = 0, a tangent
+ * build, or a three-dimensional lattice), CUDA. */
+int lb3e_potential_fd_residual(lb3e_handle* h, double* residual);
+
 /* Start the Nernst-Planck ion species (ions = 1) from the concentrations n_init
  * ([2][ny][nx] doubles, host or device; species-major): their charge replaces q,
  * the potential is solved for it as lb3e_init solves it, and each ion set starts at
@@ -248,7 +279,9 @@ enum {
     LB3E_KC_FUSED = 5,     /* fused chemical potential, force, collide and stream */
     LB3E_KC_OTHER = 6,     /* initialisation and conversions */
     LB3E_KC_IONS = 7,      /* Nernst-Planck ion moments, collision and streaming */
-    LB3E_KC_COUNT = 8
+    LB3E_KC_ANCHOR = 8,    /* potential solvers 2, 3: FP64 anchor refresh (fold, increment) */
+    LB3E_KC_COARSE = 9,    /* potential solver 2: the multigrid coarse correction */
+    LB3E_KC_COUNT = 10
 };
 
 /* Synchronise the stream and return, per kernel class, the summed event time in

@@ -26,7 +26,8 @@ PRECISIONS = {0: "f64", 1: "f32", 2: "f32-compute/f16-store", 3: "f32 + 3 tangen
 TANGENT = 1000
 TANGENT_PARAMS = dict(V_top=0, eps1=1, eps2=2, eps3=3, gamma12=4, gamma13=5, gamma23=6)
 
-KERNEL_CLASSES = ("moments", "prologue", "poisson", "reduce", "fields", "fused", "other", "ions")
+KERNEL_CLASSES = ("moments", "prologue", "poisson", "reduce", "fields", "fused", "other", "ions", "anchor",
+                  "coarse")
 
 
 class Params(C.Structure):
@@ -87,7 +88,8 @@ class Observables(C.Structure):
                     D_inner=self.D_inner, D_outer=self.D_outer, nonfinite=self.nonfinite,
                     step=self.step, poisson_iters=self.poisson_iters,
                     poisson_residual=self.poisson_residual,
-                    poisson_converged=bool(self.poisson_converged))
+                    poisson_converged=self.poisson_converged == 1,
+                    poisson_stalled=self.poisson_converged == -1)
 
 
 class LB3EError(RuntimeError):
@@ -124,6 +126,8 @@ def lib() -> C.CDLL:
         L.lb3e_set_timing.argtypes = [vp, C.c_int32]
         L.lb3e_set_potential_chunk.argtypes = [vp, C.c_int32]
         L.lb3e_set_ions.argtypes = [vp, vp]
+        L.lb3e_potential_fd_residual.argtypes = [vp, dp]
+        L.lb3e_potential_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), dp]
         L.lb3e_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64)]
         L.lb3e_observables_noalloc.argtypes = [C.POINTER(Params), vp, vp, vp, vp, vp, C.POINTER(Observables)]
         L.lb3e_batch_workspace_bytes.argtypes = [C.POINTER(Params), C.c_int32, C.POINTER(C.c_size_t)]
@@ -281,6 +285,20 @@ class Sim:
         if rc not in (0, -4):
             _check("lb3e_solve_potential", rc)
         return it.value, res.value, rc == 0
+
+    def potential_stats(self) -> dict:
+        """Potential solves since the previous call: count, how many ended above the
+        tolerance, the largest final residual (then cleared)."""
+        n, bad, mx = C.c_int64(0), C.c_int64(0), C.c_double(0)
+        _check("lb3e_potential_stats", lib().lb3e_potential_stats(self._h, C.byref(n), C.byref(bad), C.byref(mx)))
+        return dict(solves=n.value, not_converged=bad.value, max_residual=mx.value)
+
+    def fd_residual(self) -> float:
+        """||b - A psi|| / ||b|| of the current potential in the finite-difference form
+        of div(eps grad psi) + q = 0 (a diagnostic; see lb3e_potential_fd_residual)."""
+        r = C.c_double(0)
+        _check("lb3e_potential_fd_residual", lib().lb3e_potential_fd_residual(self._h, C.byref(r)))
+        return r.value
 
     def state_bytes(self) -> int:
         n = C.c_size_t(0)

@@ -839,6 +839,7 @@ class Sim3 final : public SimBase {
     int64_t potential_iterations() const override { return iters_run_; }
     int set_chunk(int k) override { return k == 1 ? LB3E_OK : LB3E_ERR_PARAM; }
     int set_ions(const double*) override { return LB3E_ERR_PARAM; }
+    int fd_residual(double*) override { return LB3E_ERR_PARAM; }
 
   private:
     // Scratch for the rho, sigma, eps outputs of a field-readback moments pass: the

@@ -24,9 +24,13 @@ int validate_params(const lb3e_params* p) {
     if (p->bc_y < 0 || p->bc_y > 2 || p->precision < 0 || p->precision > 4) return LB3E_ERR_PARAM;
     for (int k = 0; k < 3; ++k)
         if (p->tangent_param[k] < -1 || p->tangent_param[k] > 6) return LB3E_ERR_PARAM;
-    if (p->potential_solver < 0 || p->potential_solver > 1) return LB3E_ERR_PARAM;
-    if (p->potential_solver == 1 && p->electric && (p->bc_y != 2 || p->precision > 2 || (p->nx & 1)))
-        return LB3E_ERR_PARAM;  // multigrid: electrodes, plain precisions, even nx (red-black across the seam)
+    if (p->potential_solver < 0 || p->potential_solver > 3) return LB3E_ERR_PARAM;
+    // multigrid (solver 1, and the coarse correction of solver 2): electrodes, plain
+    // precisions, even nx (red-black across the seam); the FP64 anchor (2, 3): plain precisions
+    if ((p->potential_solver == 1 || p->potential_solver == 2) && p->electric &&
+        (p->bc_y != 2 || p->precision > 2 || (p->nx & 1)))
+        return LB3E_ERR_PARAM;
+    if (p->potential_solver == 3 && p->precision > 2) return LB3E_ERR_PARAM;
     if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5) || !(p->width_D > 0) || !(p->eps_ref > 0) || !(p->alpha > 0))
         return LB3E_ERR_PARAM;
     for (int i = 0; i < 3; ++i)
@@ -201,6 +205,23 @@ int64_t lb3e_potential_iterations(const lb3e_handle* h) { return h ? h->sim->pot
 int lb3e_set_potential_chunk(lb3e_handle* h, int32_t iterations_per_launch) {
     if (!h) return LB3E_ERR_NULL;
     return h->sim->set_chunk(iterations_per_launch);
+}
+
+int lb3e_potential_stats(lb3e_handle* h, int64_t* solves, int64_t* not_converged, double* max_residual) {
+    if (!h) return LB3E_ERR_NULL;
+    lb3e::SimBase* s = h->sim;
+    if (solves) *solves = s->solves;
+    if (not_converged) *not_converged = s->unconverged;
+    if (max_residual) *max_residual = s->max_residual;
+    s->solves = 0;
+    s->unconverged = 0;
+    s->max_residual = -1.0;
+    return LB3E_OK;
+}
+
+int lb3e_potential_fd_residual(lb3e_handle* h, double* residual) {
+    if (!h || !residual) return LB3E_ERR_NULL;
+    return h->sim->fd_residual(residual);
 }
 
 int lb3e_set_ions(lb3e_handle* h, const double* n_init) {

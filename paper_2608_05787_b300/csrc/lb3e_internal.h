@@ -26,7 +26,7 @@ int validate_params(const lb3e_params* p);
 
 // kernel classes for the timing facility (lb3e_kernel_times)
 enum KernelClass { KC_MOMENTS = 0, KC_PROLOGUE, KC_POISSON, KC_REDUCE, KC_FIELDS, KC_FUSED, KC_OTHER, KC_IONS,
-                   KC_COUNT };
+                   KC_ANCHOR, KC_COARSE, KC_COUNT };
 
 // CUDA-event timing of kernel launches on the simulation's stream (off by default)
 struct LaunchTimer {
@@ -83,8 +83,18 @@ struct SimBase {
     virtual int64_t potential_iterations() const = 0;
     virtual int set_chunk(int k) = 0;
     virtual int set_ions(const double* n) = 0;
+    virtual int fd_residual(double* out) = 0;
     int64_t launches = 0;
     LaunchTimer timer;
+    // potential solves since the last lb3e_potential_stats call: count, how many
+    // ended above the tolerance (cap or stall), the largest final residual
+    int64_t solves = 0, unconverged = 0;
+    double max_residual = -1.0;
+    void record_solve(int conv, double res) {
+        ++solves;
+        if (conv != 1) ++unconverged;
+        if (res > max_residual) max_residual = res;
+    }
 };
 
 // a batch of lattices of one precision, stepped together

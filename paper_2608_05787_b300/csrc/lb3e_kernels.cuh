@@ -401,11 +401,15 @@ __device__ __forceinline__ R h_collide(int j, R hj, R ps, R gx, R gy, R jx, R jy
 // One pseudo-time collide + push-stream of h.  On iterations before a check it
 // saves psi and J = sum c_j h_j; on a check it accumulates (FP64, per block)
 // |d psi|^2, |psi|^2, |d J|^2, |J|^2.
-template <class R>
+// RS (the correction to an FP64 anchor, lb3e_anchor.cuh): no charge source,
+// electrodes at zero, and the anchor's increment rres (post-streaming layout)
+// added where each population arrives.
+template <class R, bool RS = false>
 __device__ __forceinline__ void body_poisson(const DevParams P, const R* __restrict__ hin, R* __restrict__ hout,
                                                  const R* __restrict__ eps, const R* __restrict__ q,
                                                  R* __restrict__ prev, double* __restrict__ partial,
-                                                 int save_prev, int check, int bx, int by, int gdx) {
+                                                 int save_prev, int check, int bx, int by, int gdx,
+                                                 const R* __restrict__ rres = nullptr) {
     const int x = bx * blockDim.x + threadIdx.x, y = by * blockDim.y + threadIdx.y;
     const bool in = x < P.nx && y < P.ny;
     const unsigned N = P.N, c = in ? (unsigned)y * P.nx + x : 0;
@@ -432,7 +436,7 @@ __device__ __forceinline__ void body_poisson(const DevParams P, const R* __restr
         const R epshat = eps[c] - pv<R>(P.eps_ref, P.feps_ref);
         const R den = epshat + cs2<R>() * th, iden = rcp(den);
         const R gx = dv(-jx, den, iden), gy = dv(-jy, den, iden);
-        const R qc = q[c];
+        const R qc = RS ? R(0) : q[c];
         const R Kc = R(3) * ith * epshat * iden;
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
@@ -440,12 +444,19 @@ __device__ __forceinline__ void body_poisson(const DevParams P, const R* __restr
             const int yt = y + cy(j);
             if (P.bc_y != 0 && (yt < 0 || yt >= P.ny)) {
                 R out = v;
-                if (P.bc_y == 2)
-                    out = -v + R(2) * wgt<R>(j) * (yt >= P.ny ? prm<R>(P.V_top, P.t_Vt, P.fVt)
-                                                              : prm<R>(P.V_bottom, P.t_Vb, P.fVb));
-                hout[opp(j) * N + c] = out;
+                if (P.bc_y == 2) {
+                    if constexpr (RS) out = -v;
+                    else
+                        out = -v + R(2) * wgt<R>(j) * (yt >= P.ny ? prm<R>(P.V_top, P.t_Vt, P.fVt)
+                                                                  : prm<R>(P.V_bottom, P.t_Vb, P.fVb));
+                }
+                const unsigned to = opp(j) * N + c;
+                if constexpr (RS) out = out + rres[to];
+                hout[to] = out;
             } else {
-                hout[j * N + (unsigned)wrapi(yt, P.ny) * P.nx + wrapi(x + cx(j), P.nx)] = v;
+                const unsigned to = j * N + (unsigned)wrapi(yt, P.ny) * P.nx + wrapi(x + cx(j), P.nx);
+                if constexpr (RS) hout[to] = v + rres[to];
+                else hout[to] = v;
             }
         }
     }
@@ -460,6 +471,15 @@ __global__ void __launch_bounds__(256) k_poisson(DevParams P, const R* __restric
                                                  R* __restrict__ prev, double* __restrict__ partial,
                                                  int save_prev, int check) {
     body_poisson<R>(P, hin, hout, eps, q, prev, partial, save_prev, check, blockIdx.x, blockIdx.y, gridDim.x);
+}
+// one iteration on the correction to an FP64 anchor (no residual sums; save_prev:
+// psi and J before the collision into prev)
+template <class R>
+__global__ void __launch_bounds__(256) k_poisson_rs(DevParams P, const R* __restrict__ hin, R* __restrict__ hout,
+                                                    const R* __restrict__ eps, const R* __restrict__ rres,
+                                                    R* __restrict__ prev, int save_prev) {
+    body_poisson<R, true>(P, hin, hout, eps, nullptr, prev, nullptr, save_prev, 0, blockIdx.x, blockIdx.y,
+                          gridDim.x, rres);
 }
 
 // ---------------------------------------------------------------- S5, temporally blocked
@@ -486,17 +506,19 @@ template <class R, int H>
 __host__ __device__ constexpr int pb_min_blocks() {
     return std::is_same<R, float>::value ? (H == 8 ? 2 : 3) : 1;
 }
-template <class R, int H>
-constexpr size_t pb_smem_bytes() { return (size_t)11 * PBGeom<H>::CELLS * sizeof(R); }
+// shared planes: 9 post-collision planes and eps (Kc), then q (q/8), or, on the
+// correction to an FP64 anchor (RS), the anchor's 9 increment planes
+template <class R, int H, bool RS = false>
+constexpr size_t pb_smem_bytes() { return (size_t)(RS ? 19 : 11) * PBGeom<H>::CELLS * sizeof(R); }
 // halo depth of the region that serves a chunk of K iterations
 __host__ __device__ constexpr int pb_halo_for(int K) { return K <= 2 ? 2 : (K <= 4 ? 4 : 8); }
 
-template <class R, int H, int KC = 0>
+template <class R, int H, int KC = 0, bool RS = false>
 __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __restrict__ hin,
                                                 R* __restrict__ hout, const R* __restrict__ eps,
                                                 const R* __restrict__ q, R* __restrict__ prev,
                                                 double* __restrict__ partial, int Kdyn, int save_prev, int check,
-                                                int bx, int by, int gdx) {
+                                                int bx, int by, int gdx, const R* __restrict__ rres = nullptr) {
     using G = PBGeom<H>;
     constexpr int RX = G::RX, CELLS = G::CELLS, CPT = G::CPT, NT = G::THREADS;
     extern __shared__ __align__(16) unsigned char pb_raw[];
@@ -505,7 +527,8 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
     // form, Kc = 3 eps_hat / (tau_h den) and q / 8
     constexpr bool kFact = std::is_same<R, float>::value;
     R* se = hs + 9 * CELLS;  // eps (Kc)
-    R* sq = se + CELLS;      // q (q / 8)
+    R* sq = se + CELLS;      // q (q / 8); RS: unused
+    R* rs = se + CELLS;      // RS: [9][CELLS] the anchor's increment, added after each pull
     const int nx = P.nx, ny = P.ny;
     const unsigned N = P.N;
     const int x0 = bx * PB_TX - H, y0 = by * PB_TY - H;
@@ -535,16 +558,25 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
             if constexpr (kFact) {
                 const R eh = eps[c] - P.feps_ref;
                 se[k] = R(3) * P.fitau_h * eh * rcp(eh + cs2<R>() * P.ftau_h);
-                sq[k] = R(0.125) * q[c];
+                if constexpr (!RS) sq[k] = R(0.125) * q[c];
             } else {
                 se[k] = eps[c];
-                sq[k] = q[c];
+                if constexpr (!RS) sq[k] = q[c];
+            }
+            if constexpr (RS) {
+#pragma unroll
+                for (int j = 0; j < 9; ++j) rs[j * CELLS + k] = rres[j * N + c];
             }
         } else {
 #pragma unroll
             for (int j = 0; j < 9; ++j) h[m][j] = R(0);
             se[k] = kFact ? R(0) : pv<R>(P.eps_ref, P.feps_ref);
-            sq[k] = R(0);
+            if constexpr (RS) {
+#pragma unroll
+                for (int j = 0; j < 9; ++j) rs[j * CELLS + k] = R(0);
+            } else {
+                sq[k] = R(0);
+            }
         }
     }
     __syncthreads();
@@ -590,14 +622,14 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
             }
             R hc[9];
             if constexpr (kFact) {
-                const R Kc = se[k], q8 = sq[k];
+                const R Kc = se[k], q8 = RS ? R(0) : sq[k];
 #pragma unroll
                 for (int j = 0; j < 9; ++j) hc[j] = h_collide<R>(j, h[m][j], ps, R(0), R(0), jx, jy, th, ith, R(0), Kc, R(0), q8);
             } else {
                 const R epshat = se[k] - eref;
                 const R den = epshat + cs2<R>() * th, iden = rcp(den);
                 const R gx = dv(-jx, den, iden), gy2 = dv(-jy, den, iden);
-                const R qc = sq[k];
+                const R qc = RS ? R(0) : sq[k];
 #pragma unroll
                 for (int j = 0; j < 9; ++j)
                     hc[j] = h_collide<R>(j, h[m][j], ps, gx, gy2, jx, jy, th, ith, epshat, R(0), qc, R(0));
@@ -615,7 +647,7 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
                     const bool bottom = cy(j) < 0 && (meta[m] & 256), top = cy(j) > 0 && (meta[m] & 512);
                     if (!bottom && !top) continue;
                     const int jo = opp(j);  // arriving direction
-                    const R v = electrodes ? -hc[j] + R(2) * wgt<R>(j) * (top ? vt : vb) : hc[j];
+                    const R v = electrodes ? (RS ? -hc[j] : -hc[j] + R(2) * wgt<R>(j) * (top ? vt : vb)) : hc[j];
                     hs[jo * CELLS + k - cy(jo) * RX - cx(jo)] = v;
                 }
             }
@@ -627,7 +659,10 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
             if ((meta[m] & 255) > K - 1 - t) continue;
             const int k = tid + m * NT;
 #pragma unroll
-            for (int j = 0; j < 9; ++j) h[m][j] = hs[j * CELLS + k - cy(j) * RX - cx(j)];
+            for (int j = 0; j < 9; ++j) {
+                h[m][j] = hs[j * CELLS + k - cy(j) * RX - cx(j)];
+                if constexpr (RS) h[m][j] += rs[j * CELLS + k];
+            }
         }
         __syncthreads();
     }
@@ -648,6 +683,15 @@ __global__ void __launch_bounds__(PBGeom<H>::THREADS, pb_min_blocks<R, H>())
                  int check) {
     body_poisson_tb<R, H, KC>(P, hin, hout, eps, q, prev, partial, K, save_prev, check, blockIdx.x, blockIdx.y,
                           gridDim.x);
+}
+// K iterations on the correction to an FP64 anchor (no residual sums; save_prev:
+// psi and J before the last collision into prev)
+template <class R, int H, int KC = 0>
+__global__ void __launch_bounds__(PBGeom<H>::THREADS, pb_min_blocks<R, H>())
+    k_poisson_tb_rs(DevParams P, const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ eps,
+                    const R* __restrict__ rres, R* __restrict__ prev, int K, int save_prev) {
+    body_poisson_tb<R, H, KC, true>(P, hin, hout, eps, nullptr, prev, nullptr, K, save_prev, 0, blockIdx.x,
+                                    blockIdx.y, gridDim.x, rres);
 }
 
 // final reduction of nblk x NV partials in a fixed order (one block of 256 threads)

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <vector>
 
+#include "lb3e_anchor.cuh"
 #include "lb3e_internal.h"
 #include "lb3e_ions.cuh"
 #include "lb3e_kernels.cuh"
@@ -27,7 +28,7 @@ class Sim final : public SimBase {
     // workspace layout (byte offsets), computed identically by bytes() and the constructor
     struct Layout {
         size_t pop[2], h[2], phi, qt, q, eps, E, prev, diag, psi_prev, partial, result, stage, mg, ion[2], ionst,
-            total;
+            anchor, rres, total;
     };
     static Layout layout(const lb3e_params& p) {
         const size_t N = (size_t)p.nx * p.ny;
@@ -60,7 +61,7 @@ class Sim final : public SimBase {
         // multigrid levels (finite-difference potential only): FP64 psi, rhs, res, eps
         // and coefficients; FP32 error-equation psi, rhs, res and coefficients
         size_t mg = 0;
-        if (p.potential_solver == 1 && p.electric) {
+        if ((p.potential_solver == 1 || p.potential_solver == 2) && p.electric) {
             const int nl = mg_levels(p.nx, p.ny);
             for (int l = 0; l < nl; ++l) {
                 const size_t n = (size_t)(p.nx >> l) * (p.ny >> l);
@@ -74,6 +75,11 @@ class Sim final : public SimBase {
         L.ion[0] = take(18 * ni * sizeof(R));
         L.ion[1] = take(18 * ni * sizeof(R));
         L.ionst = take(6 * ni * sizeof(R));
+        // LB potential on an FP64 anchor (solvers 2, 3): the anchor's 9 FP64 planes
+        // and its increment's 9 planes in R
+        const size_t na = (p.potential_solver >= 2 && p.electric) ? N : 0;
+        L.anchor = take(9 * na * sizeof(double));
+        L.rres = take(9 * na * sizeof(R));
         L.total = o;
         return L;
     }
@@ -108,7 +114,11 @@ class Sim final : public SimBase {
         dp_ = make_dev_params(prm);
         grid2_ = dim3((prm.nx + TX - 1) / TX, (prm.ny + TY - 1) / TY);
         nblk_ = (int)(grid2_.x * grid2_.y);
-        if (prm.potential_solver == 1 && prm.electric) {
+        if (prm.electric && prm.potential_solver >= 2) {
+            anchor_ = reinterpret_cast<double*>(b + L_.anchor);
+            rres_ = reinterpret_cast<R*>(b + L_.rres);
+        }
+        if ((prm.potential_solver == 1 || prm.potential_solver == 2) && prm.electric) {
             const int nl = mg_levels(prm.nx, prm.ny);
             char* m = b + L_.mg;
             for (int l = 0; l < nl; ++l) {
@@ -178,13 +188,20 @@ class Sim final : public SimBase {
         timer.begin(stream_, KC_OTHER);
         k_init_h<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[0]);
         TRY(launched());
-        if (p_.electric && !mg_.empty()) {
+        if constexpr (!is_dual<R>::value) {
+            if (anchor_) {
+                timer.begin(stream_, KC_OTHER);
+                k_anchor_init<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.h[0]);
+                TRY(launched());
+            }
+        }
+        if (p_.electric && p_.potential_solver == 1) {
             timer.begin(stream_, KC_OTHER);
             k_mg_init<<<mg_grid(0), dim3(TX, TY), 0, stream_>>>(mg_[0], p_.V_bottom, p_.V_top);
             TRY(launched());
-            TRY(mg_solve(p_.poisson_tol, p_.poisson_max_iter));
+            TRY(potential());
         } else if (p_.electric) {
-            TRY(poisson(p_.poisson_tol, p_.poisson_max_iter, p_.poisson_fixed_iter, p_.poisson_check_every));
+            TRY(potential());
         } else {
             timer.begin(stream_, KC_OTHER);
             k_fill_E<R><<<blocks1(N_), 256, 0, stream_>>>(dp_, d_.E);
@@ -224,11 +241,7 @@ class Sim final : public SimBase {
                     TRY(launched());
                 }
             }
-            if (p_.electric && !mg_.empty()) {
-                TRY(mg_solve(p_.poisson_tol, p_.poisson_max_iter));
-            } else if (p_.electric) {
-                TRY(poisson(p_.poisson_tol, p_.poisson_max_iter, p_.poisson_fixed_iter, p_.poisson_check_every));
-            }
+            if (p_.electric) TRY(potential());
             timer.begin(stream_, KC_FUSED);
             k_fused<R, S><<<grid2_, dim3(TX, TY), fused_dyn_smem<R, S>(), stream_>>>(dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q,
                                                                  d_.E, d_.prev, d_.diag, step_ == 0 ? 1 : 0,
@@ -252,14 +265,11 @@ class Sim final : public SimBase {
 
     int solve_potential(const double* q, double tol, int max_iter, int check, int* iters, double* res) override {
         if (q) TRY(upload(q, N_, d_.q));
-        if (!mg_.empty())
-            TRY(mg_solve(tol, max_iter));
-        else
-            TRY(poisson(tol, max_iter, 0, check));
+        TRY(potential(tol, max_iter, 0, check));
         if (iters) *iters = last_iters_;
         if (res) *res = last_res_;
         TRY(sync());
-        return last_conv_ ? LB3E_OK : LB3E_ERR_NOT_CONVERGED;
+        return last_conv_ == 1 ? LB3E_OK : LB3E_ERR_NOT_CONVERGED;
     }
 
     int set_ions(const double* n) override {
@@ -271,11 +281,7 @@ class Sim final : public SimBase {
             timer.begin(stream_, KC_OTHER);
             k_ion_charge<R><<<blocks1(N_), 256, 0, stream_>>>(N_, nion_, d_.q, ip_);
             TRY(launched());
-            if (p_.electric && !mg_.empty()) {
-                TRY(mg_solve(p_.poisson_tol, p_.poisson_max_iter));
-            } else if (p_.electric) {
-                TRY(poisson(p_.poisson_tol, p_.poisson_max_iter, p_.poisson_fixed_iter, p_.poisson_check_every));
-            }
+            if (p_.electric) TRY(potential());
             icur_ = 0;
             timer.begin(stream_, KC_OTHER);
             k_init_ions<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(p_.nx, p_.ny, ion_[0], nion_, d_.diag, d_.E, ip_);
@@ -353,10 +359,8 @@ class Sim final : public SimBase {
             case LB3E_FIELD_MU1: case LB3E_FIELD_MU2: case LB3E_FIELD_MU3: src = d_.diag + (3 + id - LB3E_FIELD_MU1) * N_; break;
             case LB3E_FIELD_PSI:
                 if (comp) return LB3E_ERR_FIELD;
-                if (!mg_.empty()) return copy_out(dst, mg_[0].psi);
-                timer.begin(stream_, KC_FIELDS);
-                k_potential_fields<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[hcur_], d_.eps, d_.E, d_.stage);
-                TRY(launched());
+                if (p_.potential_solver == 1 && !mg_.empty()) return copy_out(dst, mg_[0].psi);
+                TRY(psi_to_stage());
                 return copy_out(dst, d_.stage);
             case LB3E_FIELD_PHINOW1: case LB3E_FIELD_PHINOW2: case LB3E_FIELD_PHINOW3: case LB3E_FIELD_QTILDE: {
                 // moments of the current populations into scratch planes of the other buffer's view
@@ -400,6 +404,11 @@ class Sim final : public SimBase {
             if (set < 5) {
                 timer.begin(stream_, KC_OTHER);
                 k_pop_to_f64<R, S><<<blocks1(N_), 256, 0, stream_>>>(d_.stage, d_.pop[cur_], d_.phi, set, j, N_);
+            } else if (anchor_) {  // h = a + delta
+                if constexpr (!is_dual<R>::value) {
+                    timer.begin(stream_, KC_OTHER);
+                    k_anchor_pop<R><<<blocks1(N_), 256, 0, stream_>>>(d_.stage, anchor_ + j * N_, d_.h[hcur_] + j * N_, N_);
+                }
             } else {
                 timer.begin(stream_, KC_OTHER);
                 k_to_f64<R><<<blocks1(N_), 256, 0, stream_>>>(d_.stage, d_.h[hcur_] + j * N_, N_);
@@ -416,7 +425,8 @@ class Sim final : public SimBase {
 
     // snapshot: current pops, current h, then phi..psi_prev fields, then a trailer
     size_t state_bytes() const override {
-        return 45 * N_ * sizeof(S) + 9 * N_ * sizeof(R) + fields_bytes() + ion_bytes() + 4 * sizeof(int64_t);
+        return 45 * N_ * sizeof(S) + 9 * N_ * sizeof(R) + fields_bytes() + ion_bytes() + anchor_bytes() +
+               4 * sizeof(int64_t);
     }
     int save(void* dst) override {
         char* o = static_cast<char*>(dst);
@@ -431,6 +441,10 @@ class Sim final : public SimBase {
             o += 18 * N_ * sizeof(R);
             TRY(copy(o, nion_, 6 * N_ * sizeof(R)));
             o += 6 * N_ * sizeof(R);
+        }
+        if (anchor_) {  // the FP64 anchor of the potential populations (h = anchor + the planes above)
+            TRY(copy(o, anchor_, anchor_bytes()));
+            o += anchor_bytes();
         }
         int64_t trailer[4] = {step_, last_iters_, last_conv_, 0};
         std::memcpy(&trailer[3], &last_res_, sizeof(double));
@@ -453,6 +467,10 @@ class Sim final : public SimBase {
             s += 18 * N_ * sizeof(R);
             TRY(copy(nion_, s, 6 * N_ * sizeof(R)));
             s += 6 * N_ * sizeof(R);
+        }
+        if (anchor_) {
+            TRY(copy(anchor_, s, anchor_bytes()));
+            s += anchor_bytes();
         }
         int64_t trailer[4];
         TRY(copy(trailer, s, sizeof trailer));
@@ -498,6 +516,7 @@ class Sim final : public SimBase {
   private:
     size_t fields_bytes() const { return L_.psi_prev + align256(3 * N_ * sizeof(R)) - L_.phi; }
     size_t ion_bytes() const { return p_.ions ? 24 * N_ * sizeof(R) : 0; }
+    size_t anchor_bytes() const { return anchor_ ? 9 * N_ * sizeof(double) : 0; }
     static unsigned blocks1(size_t n) { return (unsigned)((n + 255) / 256); }
     int launched() {
         ++launches;
@@ -567,16 +586,6 @@ class Sim final : public SimBase {
             }
             TRY(launched());
         }
-        // smoothing of the FP32 error equation on level l
-        auto smooth = [&](int l, int sweeps) -> int {
-            for (int s = 0; s < sweeps; ++s)
-                for (int color = 0; color < 2; ++color) {
-                    timer.begin(stream_, KC_POISSON);
-                    k_mg_smooth<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], color);
-                    TRY(launched());
-                }
-            return LB3E_OK;
-        };
         last_res_ = -1.0;
         last_conv_ = 0;
         int cycles = 0;
@@ -597,24 +606,7 @@ class Sim final : public SimBase {
             timer.begin(stream_, KC_POISSON);
             k_mg_defect<<<mg_grid(0), blk, 0, stream_>>>(mg_[0], mgf_[0]);
             TRY(launched());
-            for (int l = 0; l + 1 < nl; ++l) {
-                TRY(smooth(l, 2));
-                timer.begin(stream_, KC_POISSON);
-                k_mg_residual<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], nullptr);
-                TRY(launched());
-                timer.begin(stream_, KC_POISSON);
-                k_mg_restrict<float><<<mg_grid(l + 1), blk, 0, stream_>>>(mgf_[l], mgf_[l + 1]);
-                TRY(launched());
-            }
-            timer.begin(stream_, KC_POISSON);
-            k_mg_coarse_solve<float><<<1, 256, 0, stream_>>>(mgf_[nl - 1], nl == 1 ? 2 : 50);
-            TRY(launched());
-            for (int l = nl - 2; l >= 0; --l) {
-                timer.begin(stream_, KC_POISSON);
-                k_mg_prolong<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], mgf_[l + 1]);
-                TRY(launched());
-                TRY(smooth(l, 2));
-            }
+            TRY(vcycle(KC_POISSON));
             timer.begin(stream_, KC_POISSON);
             k_mg_correct<<<mg_grid(0), blk, 0, stream_>>>(mg_[0], mgf_[0]);
             TRY(launched());
@@ -625,6 +617,322 @@ class Sim final : public SimBase {
         timer.begin(stream_, KC_FIELDS);
         k_mg_fields<R><<<mg_grid(0), blk, 0, stream_>>>(mg_[0], vb, vt, p_.E_ext[0], p_.E_ext[1], d_.E);
         return launched();
+    }
+
+    // One FP32 V-cycle on level 0's A e = rhs (rhs and e = 0 set by the caller):
+    // 2 red-black pre- and post-sweeps per level, residual restriction by sums of the
+    // four children, bilinear prolongation, 50 sweeps on the coarsest level.
+    int vcycle(int kc) {
+        const int nl = (int)mgf_.size();
+        const dim3 blk(TX, TY);
+        auto smooth = [&](int l, int sweeps) -> int {
+            for (int s = 0; s < sweeps; ++s)
+                for (int color = 0; color < 2; ++color) {
+                    timer.begin(stream_, kc);
+                    k_mg_smooth<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], color);
+                    TRY(launched());
+                }
+            return LB3E_OK;
+        };
+        for (int l = 0; l + 1 < nl; ++l) {
+            TRY(smooth(l, 2));
+            timer.begin(stream_, kc);
+            k_mg_residual<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], nullptr);
+            TRY(launched());
+            timer.begin(stream_, kc);
+            k_mg_restrict<float><<<mg_grid(l + 1), blk, 0, stream_>>>(mgf_[l], mgf_[l + 1]);
+            TRY(launched());
+        }
+        timer.begin(stream_, kc);
+        k_mg_coarse_solve<float><<<1, 256, 0, stream_>>>(mgf_[nl - 1], nl == 1 ? 2 : 50);
+        TRY(launched());
+        for (int l = nl - 2; l >= 0; --l) {
+            timer.begin(stream_, kc);
+            k_mg_prolong<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], mgf_[l + 1]);
+            TRY(launched());
+            TRY(smooth(l, 2));
+        }
+        return LB3E_OK;
+    }
+
+    // the potential solve of this simulation's solver with the run parameters
+    int potential() {
+        return potential(p_.poisson_tol, p_.poisson_max_iter, p_.poisson_fixed_iter, p_.poisson_check_every);
+    }
+    int potential(double tol, int max_iter, int fixed, int check) {
+        int rc;
+        if (p_.potential_solver == 1) {
+            rc = mg_solve(tol, max_iter);
+        } else {
+            rc = LB3E_ERR_PARAM;
+            if constexpr (!is_dual<R>::value) {
+                if (anchor_) rc = poisson_anchored(tol, max_iter, fixed, check);
+            }
+            if (!anchor_) rc = poisson(tol, max_iter, fixed, check);
+        }
+        if (rc == LB3E_OK) record_solve(last_conv_, last_res_);
+        return rc;
+    }
+    // psi of the current potential state into the FP64 staging plane
+    int psi_to_stage() {
+        timer.begin(stream_, KC_FIELDS);
+        if constexpr (!is_dual<R>::value) {
+            if (anchor_) {
+                k_anchor_fields<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.h[hcur_], d_.eps, d_.E,
+                                                                         d_.stage);
+                return launched();
+            }
+        }
+        if (p_.potential_solver == 1 && !mg_.empty()) {
+            if (cudaMemcpyAsync(d_.stage, mg_[0].psi, N_ * sizeof(double), cudaMemcpyDeviceToDevice, stream_) !=
+                cudaSuccess)
+                return LB3E_ERR_CUDA;
+            return launched();
+        }
+        k_potential_fields<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[hcur_], d_.eps, d_.E, d_.stage);
+        return launched();
+    }
+
+  public:
+    // ||b - A psi|| / ||b|| of the current psi for the finite-difference form of the
+    // potential equation (5-point, harmonic-mean faces, half-cell electrodes), FP64:
+    // a diagnostic of how close the LB fixed point is to that discretisation
+    int fd_residual(double* out) {
+        if (!p_.electric) return LB3E_ERR_PARAM;
+        if constexpr (is_dual<R>::value) {
+            return LB3E_ERR_PARAM;
+        } else {
+            TRY(psi_to_stage());
+            timer.begin(stream_, KC_REDUCE);
+            k_fd_residual<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.stage, d_.eps, d_.q, d_.partial);
+            TRY(launched());
+            TRY(reduce_nv<2>(nblk_));
+            if (cudaMemcpyAsync(pinned_, d_.result, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_) !=
+                cudaSuccess)
+                return LB3E_ERR_CUDA;
+            TRY(sync());
+            *out = pinned_[1] > 0 ? std::sqrt(pinned_[0] / pinned_[1]) : 0.0;
+            return LB3E_OK;
+        }
+    }
+
+  private:
+    // relative residual from the 4 FP64 sums |d psi|^2, |psi|^2, |d J|^2, |J|^2
+    static double rel_residual(const double* v) {
+        const double dp = v[0], pp = v[1], dj = v[2], jj = v[3];
+        const double r1 = pp > 0.0 ? std::sqrt(dp) / std::sqrt(pp) : (dp > 0.0 ? INFINITY : 0.0);
+        const double r2 = jj > 0.0 ? std::sqrt(dj) / std::sqrt(jj) : (dj > 0.0 ? INFINITY : 0.0);
+        return r1 > r2 ? r1 : r2;
+    }
+    // the plateau rule: a residual-controlled solve stops, not converged, once the
+    // best residual has not fallen by 1% over `window` consecutive checks (a
+    // rounding floor, or a rate too slow to reach the tolerance in bounded work)
+    struct Plateau {
+        double best = INFINITY;
+        int since = 0;
+        bool stalled(double r, int window) {
+            if (r < 0.99 * best) {
+                best = r;
+                since = 0;
+                return false;
+            }
+            return ++since >= window;
+        }
+    };
+
+    // Fold delta into the FP64 anchor and form the anchor's increment r = T a + s - a
+    // (rres), delta = 0.  With `residual`: the relative increments of psi and J in
+    // *res, and the anchor's |psi|^2, |J|^2 (the denominators of later checks) in norms.
+    int anchor_refresh(bool residual, double* res, double* norms) {
+        if constexpr (is_dual<R>::value) {
+            return LB3E_ERR_PARAM;
+        } else {
+            timer.begin(stream_, KC_ANCHOR);
+            k_anchor_refresh<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.h[hcur_], d_.eps, d_.q,
+                                                                      d_.stage, 1.0 / dp_.tau_h, dp_.tau_h / 3.0);
+            TRY(launched());
+            timer.begin(stream_, KC_ANCHOR);
+            k_anchor_residual<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.stage, rres_, d_.partial);
+            TRY(launched());
+            if (!residual) return LB3E_OK;
+            TRY(reduce4(nblk_));
+            if (cudaMemcpyAsync(pinned_, d_.result, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream_) !=
+                cudaSuccess)
+                return LB3E_ERR_CUDA;
+            TRY(sync());
+            *res = rel_residual(pinned_);
+            norms[0] = pinned_[1];
+            norms[1] = pinned_[3];
+            return LB3E_OK;
+        }
+    }
+    // the increment of the last pseudo-iteration of delta, relative to the anchor's
+    // norms; with `rhs`, also the coarse correction's right-hand side.  *noisy: the
+    // rounding floor of these increments (the precision's epsilon times the size of
+    // delta) is above a tenth of tol -- time to fold delta into the anchor.
+    int rs_check(const double* norms, bool rhs, double tol, double* res, bool* noisy) {
+        if constexpr (!is_dual<R>::value) {
+            timer.begin(stream_, KC_REDUCE);
+            k_rs_increment<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(
+                dp_, d_.h[hcur_], d_.psi_prev, d_.partial, rhs ? mgf_[0].rhs : nullptr, rhs ? mgf_[0].psi : nullptr);
+            TRY(launched());
+            TRY(reduce_nv<3>(nblk_));
+            if (cudaMemcpyAsync(pinned_, d_.result, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream_) !=
+                cudaSuccess)
+                return LB3E_ERR_CUDA;
+            TRY(sync());
+            const double v[4] = {pinned_[0], norms[0], pinned_[1], norms[1]};
+            *res = rel_residual(v);
+            const double eps = std::is_same<R, float>::value ? 6e-8 : 1.2e-16;
+            const double floor_abs = 2.0 * eps * std::sqrt(pinned_[2]);
+            const double nmin = std::sqrt(norms[0] < norms[1] ? norms[0] : norms[1]);
+            *noisy = floor_abs > 0.1 * tol * nmin;
+        }
+        return LB3E_OK;
+    }
+    // permittivity of every multigrid level and the FP32 coefficients (once per solve:
+    // eps is fixed within it)
+    int lbmg_setup() {
+        if constexpr (!is_dual<R>::value) {
+            const int nl = (int)mg_.size();
+            const dim3 blk(TX, TY);
+            timer.begin(stream_, KC_COARSE);
+            k_lbmg_eps<R><<<mg_grid(0), blk, 0, stream_>>>(mg_[0], d_.eps);
+            TRY(launched());
+            for (int l = 0; l < nl; ++l) {
+                if (l > 0) {
+                    timer.begin(stream_, KC_COARSE);
+                    k_mg_coarsen_eps<<<mg_grid(l), blk, 0, stream_>>>(mg_[l - 1], mg_[l]);
+                    TRY(launched());
+                }
+                timer.begin(stream_, KC_COARSE);
+                k_mg_coeffs_f<<<mg_grid(l), blk, 0, stream_>>>(mg_[l], mgf_[l]);
+                TRY(launched());
+            }
+        }
+        return LB3E_OK;
+    }
+    // One V-cycle on A e = (the macroscopic residual), its solution e entering delta
+    // as its local equilibrium and first-order flux.  Right after a refresh the
+    // residual is sum_{j>0} r_j of the anchor and delta = e; otherwise rs_check left
+    // it in level 0's rhs and delta += e.
+    int lbmg_correct(bool after_refresh) {
+        if constexpr (!is_dual<R>::value) {
+            const dim3 blk(TX, TY);
+            if (after_refresh) {
+                timer.begin(stream_, KC_COARSE);
+                k_lbmg_rhs<R><<<grid2_, blk, 0, stream_>>>(dp_, rres_, mgf_[0]);
+                TRY(launched());
+            }
+            TRY(vcycle(KC_COARSE));
+            timer.begin(stream_, KC_COARSE);
+            k_lbmg_correct<R><<<grid2_, blk, 0, stream_>>>(dp_, mgf_[0], d_.eps, d_.h[hcur_], after_refresh ? 0 : 1);
+            TRY(launched());
+        }
+        return LB3E_OK;
+    }
+    // iterations per launch on delta: the chunk, within the shared memory the
+    // blocked kernel needs (the 8-cell halo does not fit for FP64)
+    int rs_chunk() const {
+        if (pb_smem_bytes<R, 8, true>() > 227 * 1024 && chunk_ > 4) return 4;
+        return chunk_;
+    }
+    // m pseudo-iterations on delta (blocked, rs_chunk() per launch); with save,
+    // psi and J before the last collision go to psi_prev for rs_check
+    int rs_iterations(int m, bool save) {
+        if constexpr (!is_dual<R>::value) {
+            TRY(pb_prepare());
+            const dim3 pgrid((p_.nx + PB_TX - 1) / PB_TX, (p_.ny + PB_TY - 1) / PB_TY);
+            const int kmax = rs_chunk();
+            for (int k = 0; k < m;) {
+                const int c = m - k < kmax ? m - k : kmax;
+                const int sv = save && k + c == m;
+                timer.begin(stream_, KC_POISSON);
+                if (c == 1)
+                    k_poisson_rs<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps,
+                                                                          rres_, d_.psi_prev, sv);
+                else if (pb_halo_for(c) == 2)
+                    k_poisson_tb_rs<R, 2><<<pgrid, PBGeom<2>::THREADS, pb_smem_bytes<R, 2, true>(), stream_>>>(
+                        dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
+                else if (c == 4)
+                    k_poisson_tb_rs<R, 4, 4><<<pgrid, PBGeom<4>::THREADS, pb_smem_bytes<R, 4, true>(), stream_>>>(
+                        dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
+                else if (pb_halo_for(c) == 4)
+                    k_poisson_tb_rs<R, 4><<<pgrid, PBGeom<4>::THREADS, pb_smem_bytes<R, 4, true>(), stream_>>>(
+                        dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
+                else if constexpr (pb_smem_bytes<R, 8, true>() <= 227 * 1024)
+                    k_poisson_tb_rs<R, 8><<<pgrid, PBGeom<8>::THREADS, pb_smem_bytes<R, 8, true>(), stream_>>>(
+                        dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
+                TRY(launched());
+                poisson_iters_run_ += c;
+                hcur_ ^= 1;
+                k += c;
+            }
+        }
+        return LB3E_OK;
+    }
+    // The LB potential solve on an FP64 anchor (solver 3), with a multigrid coarse
+    // correction before every run of check_every iterations (solver 2).  One refresh
+    // at the start gives the exact FP64 increment of the warm start; later checks
+    // take the increment of the last iteration of delta.  A stalled residual leads to
+    // one more refresh (delta folded into the anchor); a stall right after a refresh
+    // ends the solve (-1).  With fixed > 0: exactly that many plain pseudo-iterations.
+    int poisson_anchored(double tol, int max_iter, int fixed, int check) {
+        if (check < 1) check = 1;
+        last_res_ = -1.0;
+        last_conv_ = fixed > 0;
+        last_iters_ = 0;
+        const bool coarse = p_.potential_solver == 2 && fixed <= 0;
+        if (coarse) TRY(lbmg_setup());
+        double norms[2] = {0.0, 0.0}, res = -1.0;
+        TRY(anchor_refresh(fixed <= 0, &res, norms));
+        int it = 0;
+        if (fixed > 0) {
+            // the plain iterates, delta folded into the anchor every check iterations so
+            // that it stays small against h
+            while (it < fixed) {
+                if (it > 0) TRY(anchor_refresh(false, &res, norms));
+                const int m = fixed - it < check ? fixed - it : check;
+                TRY(rs_iterations(m, false));
+                it += m;
+            }
+        } else {
+            Plateau pl;
+            bool after_refresh = true, stall_refreshed = false;
+            for (;;) {
+                last_res_ = res;
+                if (res <= tol) { last_conv_ = 1; break; }
+                if (pl.stalled(res, coarse ? 4 : 32)) {
+                    // a stall again after a stall refresh, with no progress between: a floor
+                    if (stall_refreshed) { last_conv_ = -1; break; }
+                    TRY(anchor_refresh(true, &res, norms));
+                    after_refresh = true;
+                    stall_refreshed = true;
+                    pl = Plateau();
+                    continue;
+                }
+                if (pl.since == 0) stall_refreshed = false;  // progress since the last stall
+                if (it >= max_iter) break;
+                if (coarse) TRY(lbmg_correct(after_refresh));
+                const int m = max_iter - it < check ? max_iter - it : check;
+                TRY(rs_iterations(m, true));
+                it += m;
+                bool noisy = false;
+                TRY(rs_check(norms, coarse, tol, &res, &noisy));
+                after_refresh = false;
+                if (noisy && res > tol) {  // the exact increment at a fresh anchor instead
+                    TRY(anchor_refresh(true, &res, norms));
+                    after_refresh = true;
+                }
+            }
+        }
+        last_iters_ = it;
+        if constexpr (!is_dual<R>::value) {
+            timer.begin(stream_, KC_FIELDS);
+            k_anchor_fields<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.h[hcur_], d_.eps, d_.E, nullptr);
+            TRY(launched());
+        }
+        return LB3E_OK;
     }
 
     // blocked-iteration kernels need more than the default dynamic shared memory
@@ -640,6 +948,19 @@ class Sim final : public SimBase {
                     cudaFuncSetAttribute(k_poisson_tb<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)pb_smem_bytes<R, 8>()) != cudaSuccess)
                     return LB3E_ERR_CUDA;
+                if (anchor_ &&
+                    (cudaFuncSetAttribute(k_poisson_tb_rs<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)pb_smem_bytes<R, 2, true>()) != cudaSuccess ||
+                     cudaFuncSetAttribute(k_poisson_tb_rs<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)pb_smem_bytes<R, 4, true>()) != cudaSuccess ||
+                     cudaFuncSetAttribute(k_poisson_tb_rs<R, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)pb_smem_bytes<R, 4, true>()) != cudaSuccess))
+                    return LB3E_ERR_CUDA;
+                if constexpr (pb_smem_bytes<R, 8, true>() <= 227 * 1024) {
+                    if (anchor_ && cudaFuncSetAttribute(k_poisson_tb_rs<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        (int)pb_smem_bytes<R, 8, true>()) != cudaSuccess)
+                        return LB3E_ERR_CUDA;
+                }
                 pb_ready_ = true;
             }
         }
@@ -689,6 +1010,7 @@ class Sim final : public SimBase {
         TRY(pb_prepare());
         const dim3 pgrid((p_.nx + PB_TX - 1) / PB_TX, (p_.ny + PB_TY - 1) / PB_TY);
         const int pblk = (int)(pgrid.x * pgrid.y);
+        Plateau pl;
         int k = 1;
         while (k <= n) {
             int c = n - k + 1 < chunk_ ? n - k + 1 : chunk_;
@@ -724,12 +1046,14 @@ class Sim final : public SimBase {
                     cudaSuccess)
                     return LB3E_ERR_CUDA;
                 TRY(sync());
-                const double dp = pinned_[0], pp = pinned_[1], dj = pinned_[2], jj = pinned_[3];
-                const double r1 = pp > 0.0 ? std::sqrt(dp) / std::sqrt(pp) : (dp > 0.0 ? INFINITY : 0.0);
-                const double r2 = jj > 0.0 ? std::sqrt(dj) / std::sqrt(jj) : (dj > 0.0 ? INFINITY : 0.0);
-                last_res_ = r1 > r2 ? r1 : r2;
+                last_res_ = rel_residual(pinned_);
                 if (last_res_ <= tol) {  // the state before this chunk's first collision is the answer
                     last_conv_ = 1;
+                    last_iters_ = k - 1;
+                    break;
+                }
+                if (pl.stalled(last_res_, 32)) {  // the state before this chunk, as above
+                    last_conv_ = -1;
                     last_iters_ = k - 1;
                     break;
                 }
@@ -760,6 +1084,8 @@ class Sim final : public SimBase {
     int chunk_ = 4;  // pseudo-iterations per potential launch (4: fastest measured on a 4096^2 lattice)
     std::vector<MGLevel> mg_;
     std::vector<MGLevelF> mgf_;
+    double* anchor_ = nullptr;  // FP64 anchor of the potential populations (solvers 2, 3)
+    R* rres_ = nullptr;         // the anchor's increment over one pseudo-iteration
     R* ion_[2] = {nullptr, nullptr};  // Nernst-Planck populations (ions = 1)
     R* nion_ = nullptr;               // n_i of the step (2 planes), then (n_i v_i)^{n-1} (4 planes)
     R* ionprev_ = nullptr;

@@ -121,3 +121,22 @@ def test_params_default_the_optional_fields():
     d = {k: v for k, v in W.params().items() if k not in ("ions", "ion_D", "ion_z", "ion_beta", "ion_charge")}
     s = L.Params.from_dict(d)
     assert s.ions == 0 and s.nz == 0 and s.precision == d["precision"]
+
+
+@pytest.mark.parametrize("bad", [dict(potential_solver=2, nx=63), dict(potential_solver=2, bc_y=1),
+                                 dict(potential_solver=3, precision=3), dict(potential_solver=2, precision=4),
+                                 dict(potential_solver=4), dict(potential_solver=2, nz=8)])
+def test_potential_solver_limits_are_checked(bad):
+    """The anchored LB solves (2, 3) take the plain precisions; the coarse-corrected
+    one (2) also needs electrodes and an even nx, like the multigrid solver."""
+    p = W.config_deformation(n=64, r_out=16.0, r_in=8.0)["params"]
+    with pytest.raises(L.LB3EError):
+        L.workspace_bytes(dict(p, **bad))
+
+
+def test_anchored_solver_workspace_holds_the_fp64_anchor():
+    p = W.config_deformation(n=64, r_out=16.0, r_in=8.0, precision=1)["params"]
+    plain, anch, coarse = (L.workspace_bytes(dict(p, potential_solver=s)) for s in (0, 3, 2))
+    n = 64 * 64
+    assert anch - plain >= 9 * n * 8 + 9 * n * 4   # the FP64 anchor and its FP32 increment
+    assert coarse > anch                           # plus the multigrid levels
