@@ -88,7 +88,8 @@ typedef struct lb3e_params {
     int32_t bc_y;                 /* 0 periodic, 1 half-way walls, 2 walls with electrodes */
     int32_t electric;             /* 1: solve the potential every step; 0: E = E_ext */
     int32_t precision;            /* 0 fp64; 1 fp32; 2 fp32 compute, fp16-stored populations;
-                                     3 fp32 with 3 tangent directions; 4 fp64 with 1 tangent */
+                                     3 fp32 with 3 tangent directions; 4 fp64 with 1 tangent;
+                                     5 fp32 compute, bf16-stored populations */
     int32_t _pad0;
     double rho[3];                /* phase densities, Eq. 29 */
     double visc[3];               /* phase dynamic viscosities, Eq. 29; all <= 0: use tau_g */
@@ -225,6 +226,26 @@ int lb3e_get_field(lb3e_handle* h, int32_t field_id, double* dst);
 int lb3e_state_bytes(const lb3e_handle* h, size_t* bytes);
 int lb3e_save_state(lb3e_handle* h, void* dst);
 int lb3e_load_state(lb3e_handle* h, const void* src);
+
+/* Deformation factors D = (a - b)/(a + b) (Section 5.3's measure, radii from the
+ * second moments of the indicator: a = 2 sqrt(Iyy) along the field, b = 2 sqrt(Ixx)
+ * across it) of the phases of the current populations (phi_i = sum_j f^i_j, as the
+ * PHINOW fields): D[0] of phi_inner, D[1] of 1 - phi_matrix.  In the tangent builds
+ * (precision 3, 4) also their derivatives along each tangent direction: dD[3 k + t]
+ * is dD[k]/d(parameter of direction t) (0 for directions a build does not carry);
+ * plain builds set dD to 0.  dD may be NULL.  The moments are FP64 sums on the GPU;
+ * D and dD are formed from them on the host.  Synchronises the stream.
+ * Errors: NULL, PARAM (three-dimensional lattices), CUDA. */
+int lb3e_deformation(lb3e_handle* h, double* D, double* dD);
+
+/* Target interface shape: J = sum over the three phases and all cells of
+ * (phi_i - phi_target_i)^2, phi_i of the current populations, phi_target
+ * [3][ny][nx] doubles (host or device).  In the tangent builds also dJ[t] =
+ * dJ/d(parameter of tangent direction t) = sum 2 (phi_i - phi_target_i)
+ * dphi_i/dtheta_t, t = 0..2 (0 for directions a build does not carry; plain builds
+ * set dJ to 0).  dJ may be NULL.  FP64 sums on the GPU.  Synchronises the stream.
+ * Errors: NULL, PARAM (three-dimensional lattices), CUDA. */
+int lb3e_shape_objective(lb3e_handle* h, const double* phi_target, double* J, double* dJ);
 
 /* Potential solves since the previous call (or lb3e_init): how many ran, how many
  * ended above the tolerance (iteration cap or a stalled residual), and the largest

@@ -112,6 +112,8 @@ def lib():
         L.orc3_step_count.argtypes = [C.c_void_p]
         L.orc_step_count.restype = C.c_int64
         L.orc_step_count.argtypes = [C.c_void_p]
+        L.orc_perturb.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_uint64]
+        L.orc_round_storage.argtypes = [C.c_void_p, C.c_int]
         _lib = L
     return _lib
 
@@ -190,12 +192,33 @@ class Oracle:
         conv = C.c_int(0)
         it = lib().orc_solve_potential(self._h, _ptr(qa), tol, max_iter, fixed, check, C.byref(res),
                                        C.byref(conv))
-        return it, res.value, bool(conv.value)
+        return it, res.value, conv.value == 1
+
+    def perturb(self, rel: float, floor_abs: float = 0.0, field_rel: float = 0.0, seed: int = 0):
+        """Test facility: perturb the populations (g, f, l) as storing them in a format
+        of relative precision `rel` (and spacing `floor_abs` near zero) would; the
+        phase rest populations by their deviation from phi_i, and phi_i itself as a
+        field of relative precision `field_rel`.  Deterministic in seed."""
+        lib().orc_perturb(self._h, float(rel), float(floor_abs), float(field_rel), int(seed))
+        return self
+
+    def round_storage(self, fmt: str):
+        """Test facility: round the stored populations to a storage format ('fp32',
+        'fp16' or 'bf16') as the GPU's builds store them (phase rest populations by
+        their deviation from phi_i, phi_i itself an FP32 field)."""
+        lib().orc_round_storage(self._h, {"fp32": 1, "fp16": 2, "bf16": 3}[fmt])
+        return self
 
     def last_poisson(self):
         it, res, conv = C.c_int(0), C.c_double(0), C.c_int(0)
         lib().orc_last_poisson(self._h, C.byref(it), C.byref(res), C.byref(conv))
-        return it.value, res.value, bool(conv.value)
+        return it.value, res.value, conv.value == 1
+
+    def last_poisson_stalled(self) -> bool:
+        """The last solve stopped on a stalled residual (not converged)."""
+        it, res, conv = C.c_int(0), C.c_double(0), C.c_int(0)
+        lib().orc_last_poisson(self._h, C.byref(it), C.byref(res), C.byref(conv))
+        return conv.value == -1
 
 
 def stencil(chi: np.ndarray, bc_y: int):

@@ -242,7 +242,11 @@ static void first_moment(const orc_state* s, const double* h, int c, double* jx,
 /* Iterate until the relative increments of psi and of the first moment J between
  * consecutive pseudo-iterations are both <= tol (checked every check_every
  * iterations, before the collision of that iteration), or a fixed number of
- * iterations.  Returns the number of collide+stream iterations applied. */
+ * iterations.  A solve whose best residual has not fallen by 1% over 32
+ * consecutive checks stops there, not converged (*converged = -1): a residual that
+ * stalls (a drifting null mode on a lattice without electrodes, a rounding floor)
+ * does not spin to the cap.  Returns the number of collide+stream iterations
+ * applied. */
 static int poisson_solve(orc_state* s, double tol, int max_iter, int fixed, int check,
                          double* res, int* converged) {
     const int N = s->N;
@@ -250,6 +254,8 @@ static int poisson_solve(orc_state* s, double tol, int max_iter, int fixed, int 
     if (check < 1) check = 1;
     *res = -1.0;
     *converged = fixed > 0;
+    double best = INFINITY;
+    int since_best = 0;
     for (int k = 1; k <= n; ++k) {
         if (fixed <= 0 && k >= 2 && k % check == 0) {
             double dp = 0.0, pp = 0.0, dj = 0.0, jj = 0.0;
@@ -268,6 +274,13 @@ static int poisson_solve(orc_state* s, double tol, int max_iter, int fixed, int 
             double r = r1 > r2 ? r1 : r2;
             *res = r;
             if (r <= tol) { *converged = 1; return k - 1; }
+            if (r < 0.99 * best) {
+                best = r;
+                since_best = 0;
+            } else if (++since_best >= 32) {
+                *converged = -1;
+                return k - 1;
+            }
         }
         if (fixed <= 0 && (k + 1) % check == 0)
             for (int c = 0; c < N; ++c) {
@@ -978,3 +991,86 @@ int orc_last_poisson(const orc_state* s, int* iters, double* res, int* converged
 }
 
 int64_t orc_step_count(const orc_state* s) { return s->step; }
+
+/* ---------------- test facility: storage-rounding perturbations ----------------
+ * Not part of the method.  Perturbs every population of the sets g, f^1..f^3 and l
+ * as storing it in a narrower floating-point format would: by u * max(rel |v|, floor)
+ * with u uniform in [-1, 1) from a counter-based hash (splitmix64 of the seed and
+ * the population's index), v the stored value.  The rest population of each phase
+ * set is taken as stored by its deviation from phi_i of the last step, as the GPU's
+ * narrow storage keeps it, and phi_i itself (held in a field of relative precision
+ * field_rel) as rounded once more: the anchor phi_i is a running quantity, rounded
+ * every step.  Used to measure how much the scheme itself amplifies perturbations
+ * of FP32, BF16 or FP16 size (floor: the format's smallest spacing near zero, 0
+ * where it plays no part). */
+static uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+static double unit_pm1(uint64_t seed, uint64_t i) {
+    uint64_t r = splitmix64(seed * 0x100000001B3ull ^ splitmix64(i));
+    return (double)(r >> 11) * (2.0 / 9007199254740992.0) - 1.0; /* [-1, 1) */
+}
+static double perturbed(double v, double rel, double floor_abs, uint64_t seed, uint64_t i) {
+    double a = fabs(v) * rel;
+    if (a < floor_abs) a = floor_abs;
+    return v + unit_pm1(seed, i) * a;
+}
+int orc_perturb(orc_state* s, double rel, double floor_abs, double field_rel, uint64_t seed) {
+    const int N = s->N;
+    uint64_t k = 0;
+    for (int i = 0; i < 9 * N; ++i, ++k) s->g[i] = perturbed(s->g[i], rel, floor_abs, seed, k);
+    for (int set = 0; set < 3; ++set)
+        for (int j = 0; j < 9; ++j)
+            for (int c = 0; c < N; ++c, ++k) {
+                double* f = &s->f[(size_t)(9 * set + j) * N + c];
+                if (j == 0) {
+                    const double anchor = s->phi[(size_t)set * N + c];
+                    const double dev = perturbed(*f - anchor, rel, floor_abs, seed, k);
+                    *f = perturbed(anchor, field_rel, 0.0, seed ^ 0x5bd1e995ull, k) + dev;
+                } else {
+                    *f = perturbed(*f, rel, floor_abs, seed, k);
+                }
+            }
+    for (int i = 0; i < 9 * N; ++i, ++k) s->l[i] = perturbed(s->l[i], rel, floor_abs, seed, k);
+    return 0;
+}
+
+/* Round-to-nearest-even of v to a binary format with `bits` significant bits whose
+ * smallest spacing (subnormal range) is 2^min_exp. */
+static double round_to_format(double v, int bits, int min_exp) {
+    if (v == 0.0 || !isfinite(v)) return v;
+    int e;
+    frexp(fabs(v), &e);                  /* |v| = m 2^e, m in [0.5, 1) */
+    int ex = e - bits;                   /* spacing of the format at |v| */
+    if (ex < min_exp) ex = min_exp;
+    const double q = ldexp(1.0, ex);
+    return copysign(nearbyint(fabs(v) / q) * q, v);   /* default rounding mode: ties to even */
+}
+/* Test facility (not part of the method): replace the stored populations by their
+ * values rounded to a storage format, as the GPU's builds store them:
+ * fmt 1 FP32, 2 FP16 (11 bits, subnormal spacing 2^-24), 3 BF16 (8 bits).  The phase
+ * rest populations are stored by their deviation from phi_i, and phi_i itself is an
+ * FP32 field.  Deterministic: this emulates the storage rounding exactly (with FP64
+ * arithmetic everywhere else). */
+int orc_round_storage(orc_state* s, int fmt) {
+    const int bits = fmt == 2 ? 11 : (fmt == 3 ? 8 : 24);
+    const int min_exp = fmt == 2 ? -24 : -149;
+    const int N = s->N;
+    for (int i = 0; i < 9 * N; ++i) s->g[i] = round_to_format(s->g[i], bits, min_exp);
+    for (int i = 0; i < 9 * N; ++i) s->l[i] = round_to_format(s->l[i], bits, min_exp);
+    for (int set = 0; set < 3; ++set)
+        for (int j = 0; j < 9; ++j)
+            for (int c = 0; c < N; ++c) {
+                double* f = &s->f[(size_t)(9 * set + j) * N + c];
+                if (j == 0) {
+                    const double anchor = round_to_format(s->phi[(size_t)set * N + c], 24, -149);
+                    *f = anchor + round_to_format(*f - anchor, bits, min_exp);
+                } else {
+                    *f = round_to_format(*f, bits, min_exp);
+                }
+            }
+    return 0;
+}

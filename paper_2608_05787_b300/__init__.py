@@ -22,7 +22,8 @@ FIELDS = dict(phi1=0, phi2=1, phi3=2, ux=3, uy=4, p=5, q=6, psi=7, ex=8, ey=9,
               uz=19, ez=20)
 SETS = dict(g=0, f1=1, f2=2, f3=3, l=4, h=5, n1=6, n2=7)
 POP_BASE = 100
-PRECISIONS = {0: "f64", 1: "f32", 2: "f32-compute/f16-store", 3: "f32 + 3 tangents", 4: "f64 + 1 tangent"}
+PRECISIONS = {0: "f64", 1: "f32", 2: "f32-compute/f16-store", 3: "f32 + 3 tangents", 4: "f64 + 1 tangent",
+              5: "f32-compute/bf16-store"}
 TANGENT = 1000
 TANGENT_PARAMS = dict(V_top=0, eps1=1, eps2=2, eps3=3, gamma12=4, gamma13=5, gamma23=6)
 
@@ -127,6 +128,8 @@ def lib() -> C.CDLL:
         L.lb3e_set_potential_chunk.argtypes = [vp, C.c_int32]
         L.lb3e_set_ions.argtypes = [vp, vp]
         L.lb3e_potential_fd_residual.argtypes = [vp, dp]
+        L.lb3e_deformation.argtypes = [vp, dp, dp]
+        L.lb3e_shape_objective.argtypes = [vp, vp, dp, dp]
         L.lb3e_potential_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), dp]
         L.lb3e_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64)]
         L.lb3e_observables_noalloc.argtypes = [C.POINTER(Params), vp, vp, vp, vp, vp, C.POINTER(Observables)]
@@ -292,6 +295,25 @@ class Sim:
         n, bad, mx = C.c_int64(0), C.c_int64(0), C.c_double(0)
         _check("lb3e_potential_stats", lib().lb3e_potential_stats(self._h, C.byref(n), C.byref(bad), C.byref(mx)))
         return dict(solves=n.value, not_converged=bad.value, max_residual=mx.value)
+
+    def deformation(self):
+        """(D_inner, D_outer) of the current populations' phases and, in the tangent
+        builds, ((dD_inner/dtheta_t), (dD_outer/dtheta_t)) along the tangent
+        directions t = 0..2 (zeros in the plain builds)."""
+        D = (C.c_double * 2)()
+        dD = (C.c_double * 6)()
+        _check("lb3e_deformation", lib().lb3e_deformation(self._h, D, dD))
+        return (D[0], D[1]), (tuple(dD[0:3]), tuple(dD[3:6]))
+
+    def shape_objective(self, phi_target):
+        """J = sum (phi_i - target_i)^2 of the current populations' phases and, in the
+        tangent builds, (dJ/dtheta_t) along the tangent directions (zeros otherwise).
+        ``phi_target``: [3, ny, nx] float64, host numpy or CUDA tensor."""
+        addr, _keep = _addr(phi_target)
+        J = C.c_double(0)
+        dJ = (C.c_double * 3)()
+        _check("lb3e_shape_objective", lib().lb3e_shape_objective(self._h, addr, C.byref(J), dJ))
+        return J.value, tuple(dJ)
 
     def fd_residual(self) -> float:
         """||b - A psi|| / ||b|| of the current potential in the finite-difference form

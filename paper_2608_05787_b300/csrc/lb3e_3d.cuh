@@ -840,6 +840,8 @@ class Sim3 final : public SimBase {
     int set_chunk(int k) override { return k == 1 ? LB3E_OK : LB3E_ERR_PARAM; }
     int set_ions(const double*) override { return LB3E_ERR_PARAM; }
     int fd_residual(double*) override { return LB3E_ERR_PARAM; }
+    int deformation(double*, double*) override { return LB3E_ERR_PARAM; }
+    int shape_objective(const double*, double*, double*) override { return LB3E_ERR_PARAM; }
 
   private:
     // Scratch for the rho, sigma, eps outputs of a field-readback moments pass: the

@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(256) k_anchor_init(DevParams P, double* __rest
 template <class R>
 __global__ void __launch_bounds__(256) k_anchor_refresh(DevParams P, double* __restrict__ a, R* __restrict__ d,
                                                         const R* __restrict__ eps, const R* __restrict__ q,
-                                                        double* __restrict__ stage, double ith, double Kn) {
+                                                        double* __restrict__ stage, R* __restrict__ ja,
+                                                        double ith, double Kn) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
     const unsigned N = P.N, c = (unsigned)y * P.nx + x;
@@ -86,10 +87,21 @@ __global__ void __launch_bounds__(256) k_anchor_refresh(DevParams P, double* __r
     ps *= 1.8;  // / (1 - w_0), to within an FP64 rounding
 #pragma unroll
     for (int j = 0; j < 9; ++j) { cacc(jx, cx(j), h[j]); cacc(jy, cy(j), h[j]); }
-    // ith = 1/tau_h and Kn = cs^2 tau_h are formed on the host
+    // ith = 1/tau_h and Kn = cs^2 tau_h are formed on the host.  Kc scales the
+    // first moment only (sum_j w_j c_j = 0 in any precision), so the FP32 builds
+    // take the FP32 value of their correction kernels (no FP64 division)
     const double om = 1.0 - ith;
-    const double eh = (double)eps[c] - P.eps_ref;
-    const double Kc = 3.0 * ith * eh / (eh + Kn);
+    double Kc;
+    if constexpr (std::is_same<R, float>::value) {
+        const float eh = eps[c] - P.feps_ref;
+        Kc = (double)(3.0f * P.fitau_h * eh * rcp(eh + cs2<float>() * P.ftau_h));
+    } else {
+        const double eh = (double)eps[c] - P.eps_ref;
+        Kc = 3.0 * ith * eh / (eh + Kn);
+    }
+    // the anchor's flux, for the fields kernel
+    ja[c] = R(jx);
+    ja[N + c] = R(jy);
     const double A = ith * ps, q8 = 0.125 * (double)q[c];
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
@@ -107,35 +119,39 @@ __global__ void __launch_bounds__(256) k_anchor_refresh(DevParams P, double* __r
 }
 
 // r = stage - a (the anchor's increment over one pseudo-iteration), stored in R,
-// and per-block FP64 sums of |d psi|^2, |psi|^2, |d J|^2, |J|^2 of that increment
-// (psi = sum_{j>0} h_j / (1 - w_0), J = sum_j c_j h_j)
+// and per-block sums of |d psi|^2, |psi|^2, |d J|^2, |J|^2 (psi = sum_{j>0} h_j /
+// (1 - w_0), J = sum_j c_j h_j).  Only the subtraction needs FP64 (it cancels O(psi)
+// values down to the increment); the increments are then small and the anchor's
+// psi and J serve only as denominators, so the sums are taken in R within a thread
+// and a warp, and in FP64 across warps.
 template <class R>
 __global__ void __launch_bounds__(256) k_anchor_residual(DevParams P, const double* __restrict__ a,
                                                          const double* __restrict__ stage, R* __restrict__ r,
                                                          double* __restrict__ partial) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    R acc[4] = {R(0), R(0), R(0), R(0)};
     if (x < P.nx && y < P.ny) {
         const unsigned N = P.N, c = (unsigned)y * P.nx + x;
-        double dps = 0.0, ps = 0.0, djx = 0.0, djy = 0.0, jx = 0.0, jy = 0.0;
+        R dps = R(0), ps = R(0), djx = R(0), djy = R(0), jx = R(0), jy = R(0);
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
-            const double aj = a[j * N + c], rj = stage[j * N + c] - aj;
-            r[j * N + c] = R(rj);
-            if (j) { dps += rj; ps += aj; }
+            const double aj = a[j * N + c];
+            const R rj = R(stage[j * N + c] - aj), ar = R(aj);
+            r[j * N + c] = rj;
+            if (j) { dps += rj; ps += ar; }
             cacc(djx, cx(j), rj);
             cacc(djy, cy(j), rj);
-            cacc(jx, cx(j), aj);
-            cacc(jy, cy(j), aj);
+            cacc(jx, cx(j), ar);
+            cacc(jy, cy(j), ar);
         }
-        dps *= 1.8;  // / (1 - w_0)
-        ps *= 1.8;
+        dps = dps * R(1.8);
+        ps = ps * R(1.8);
         acc[0] = dps * dps;
         acc[1] = ps * ps;
         acc[2] = djx * djx + djy * djy;
         acc[3] = jx * jx + jy * jy;
     }
-    block_reduce_store<4>(acc, partial + 4 * (size_t)(blockIdx.x + gridDim.x * blockIdx.y));
+    block_reduce_store_r<4>(acc, partial + 4 * (size_t)(blockIdx.x + gridDim.x * blockIdx.y));
 }
 
 // psi and E = sum c_j h_j / (eps - eps_ref + cs2 tau_h) + E_ext of h = a + delta
@@ -169,6 +185,27 @@ __global__ void __launch_bounds__(256) k_anchor_fields(DevParams P, const double
     const R iden = rcp(den);
     E[c] = dv(R(jx + (double)djx), den, iden) + pv<R>(P.E_ext[0], (float)P.E_ext[0]);
     E[N + c] = dv(R(jy + (double)djy), den, iden) + pv<R>(P.E_ext[1], (float)P.E_ext[1]);
+}
+
+// E = (J_a + J(delta)) / (eps - eps_ref + cs2 tau_h) + E_ext with J_a the anchor's
+// flux stored by the last refresh: no FP64 traffic
+template <class R>
+__global__ void __launch_bounds__(256) k_anchor_efield(DevParams P, const R* __restrict__ ja, const R* __restrict__ d,
+                                                       const R* __restrict__ eps, R* __restrict__ E) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const unsigned N = P.N, c = (unsigned)y * P.nx + x;
+    R jx = ja[c], jy = ja[N + c];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const R dj = d[j * N + c];
+        cacc(jx, cx(j), dj);
+        cacc(jy, cy(j), dj);
+    }
+    const R den = (eps[c] - pv<R>(P.eps_ref, P.feps_ref)) + cs2<R>() * pv<R>(P.tau_h, P.ftau_h);
+    const R iden = rcp(den);
+    E[c] = dv(jx, den, iden) + pv<R>(P.E_ext[0], (float)P.E_ext[0]);
+    E[N + c] = dv(jy, den, iden) + pv<R>(P.E_ext[1], (float)P.E_ext[1]);
 }
 
 // population j of h = a + delta as FP64

@@ -21,16 +21,17 @@ int validate_params(const lb3e_params* p) {
     if (p->nx < 2 || p->ny < 2) return LB3E_ERR_PARAM;
     if ((int64_t)p->nx * p->ny > LB3E_MAX_CELLS) return LB3E_ERR_PARAM;  // 32-bit plane offsets
     if (p->ny > LB3E_MAX_NY) return LB3E_ERR_PARAM;  // grid y extent of the 32 x 8 tile launches
-    if (p->bc_y < 0 || p->bc_y > 2 || p->precision < 0 || p->precision > 4) return LB3E_ERR_PARAM;
+    if (p->bc_y < 0 || p->bc_y > 2 || p->precision < 0 || p->precision > 5) return LB3E_ERR_PARAM;
+    const bool plain = lb3e::plain_precision(p->precision);
     for (int k = 0; k < 3; ++k)
         if (p->tangent_param[k] < -1 || p->tangent_param[k] > 6) return LB3E_ERR_PARAM;
     if (p->potential_solver < 0 || p->potential_solver > 3) return LB3E_ERR_PARAM;
     // multigrid (solver 1, and the coarse correction of solver 2): electrodes, plain
     // precisions, even nx (red-black across the seam); the FP64 anchor (2, 3): plain precisions
     if ((p->potential_solver == 1 || p->potential_solver == 2) && p->electric &&
-        (p->bc_y != 2 || p->precision > 2 || (p->nx & 1)))
+        (p->bc_y != 2 || !plain || (p->nx & 1)))
         return LB3E_ERR_PARAM;
-    if (p->potential_solver == 3 && p->precision > 2) return LB3E_ERR_PARAM;
+    if (p->potential_solver == 3 && !plain) return LB3E_ERR_PARAM;
     if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5) || !(p->width_D > 0) || !(p->eps_ref > 0) || !(p->alpha > 0))
         return LB3E_ERR_PARAM;
     for (int i = 0; i < 3; ++i)
@@ -53,7 +54,7 @@ int validate_params(const lb3e_params* p) {
         if (p->precision > 1 || p->potential_solver != 0 || p->ions) return LB3E_ERR_PARAM;
     }
     if (p->ions) {  // Nernst-Planck ions: plain precisions, positive diffusivities
-        if (p->precision > 2 || !(p->ion_D[0] > 0) || !(p->ion_D[1] > 0)) return LB3E_ERR_PARAM;
+        if (!plain || !(p->ion_D[0] > 0) || !(p->ion_D[1] > 0)) return LB3E_ERR_PARAM;
         const double iv[] = {p->ion_z[0], p->ion_z[1], p->ion_beta, p->ion_charge};
         for (double v : iv)
             if (!std::isfinite(v)) return LB3E_ERR_PARAM;
@@ -73,6 +74,7 @@ size_t ws_bytes(const lb3e_params& p) {
         case 0: return lb3e::workspace_bytes_f64(p);
         case 1: return lb3e::workspace_bytes_f32(p);
         case 2: return lb3e::workspace_bytes_f16s(p);
+        case 5: return lb3e::workspace_bytes_bf16s(p);
         case 3: return lb3e::workspace_bytes_t32(p);
         default: return lb3e::workspace_bytes_t64(p);
     }
@@ -85,7 +87,8 @@ int validate_batch(const lb3e_params* ps, int32_t n) {
     int iters = -1;
     for (int i = 0; i < n; ++i) {
         TRY(validate(ps + i));
-        if (ps[i].precision != ps[0].precision || ps[i].precision > 2 || ps[i].potential_solver != 0 || ps[i].ions ||
+        if (ps[i].precision != ps[0].precision || !lb3e::plain_precision(ps[i].precision) ||
+            ps[i].potential_solver != 0 || ps[i].ions ||
             ps[i].nz >= 2)
             return LB3E_ERR_PARAM;
         if (ps[i].electric) {
@@ -101,6 +104,7 @@ size_t batch_ws_bytes(const lb3e_params* ps, int n) {
     switch (ps[0].precision) {
         case 0: return lb3e::batch_bytes_f64(ps, n);
         case 1: return lb3e::batch_bytes_f32(ps, n);
+        case 5: return lb3e::batch_bytes_bf16s(ps, n);
         default: return lb3e::batch_bytes_f16s(ps, n);
     }
 }
@@ -136,6 +140,7 @@ int lb3e_init(const lb3e_params* params, void* workspace, size_t workspace_bytes
         case 0: sim = lb3e::make_sim_f64(*params, workspace, stream); break;
         case 1: sim = lb3e::make_sim_f32(*params, workspace, stream); break;
         case 2: sim = lb3e::make_sim_f16s(*params, workspace, stream); break;
+        case 5: sim = lb3e::make_sim_bf16s(*params, workspace, stream); break;
         case 3: sim = lb3e::make_sim_t32(*params, workspace, stream); break;
         default: sim = lb3e::make_sim_t64(*params, workspace, stream); break;
     }
@@ -219,6 +224,16 @@ int lb3e_potential_stats(lb3e_handle* h, int64_t* solves, int64_t* not_converged
     return LB3E_OK;
 }
 
+int lb3e_deformation(lb3e_handle* h, double* D, double* dD) {
+    if (!h || !D) return LB3E_ERR_NULL;
+    return h->sim->deformation(D, dD);
+}
+
+int lb3e_shape_objective(lb3e_handle* h, const double* phi_target, double* J, double* dJ) {
+    if (!h || !phi_target || !J) return LB3E_ERR_NULL;
+    return h->sim->shape_objective(phi_target, J, dJ);
+}
+
 int lb3e_potential_fd_residual(lb3e_handle* h, double* residual) {
     if (!h || !residual) return LB3E_ERR_NULL;
     return h->sim->fd_residual(residual);
@@ -269,6 +284,7 @@ int lb3e_batch_create(const lb3e_params* params, int32_t n, const double* const*
     switch (params[0].precision) {
         case 0: b = lb3e::new_batch_f64(params, n, workspace, stream); rc = b ? lb3e::init_batch_f64(b, phi_init) : LB3E_ERR_CUDA; break;
         case 1: b = lb3e::new_batch_f32(params, n, workspace, stream); rc = b ? lb3e::init_batch_f32(b, phi_init) : LB3E_ERR_CUDA; break;
+        case 5: b = lb3e::new_batch_bf16s(params, n, workspace, stream); rc = b ? lb3e::init_batch_bf16s(b, phi_init) : LB3E_ERR_CUDA; break;
         default: b = lb3e::new_batch_f16s(params, n, workspace, stream); rc = b ? lb3e::init_batch_f16s(b, phi_init) : LB3E_ERR_CUDA; break;
     }
     if (rc != LB3E_OK) {

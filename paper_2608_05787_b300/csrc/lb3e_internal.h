@@ -84,6 +84,8 @@ struct SimBase {
     virtual int set_chunk(int k) = 0;
     virtual int set_ions(const double* n) = 0;
     virtual int fd_residual(double* out) = 0;
+    virtual int deformation(double* D, double* dD) = 0;
+    virtual int shape_objective(const double* target, double* J, double* dJ) = 0;
     int64_t launches = 0;
     LaunchTimer timer;
     // potential solves since the last lb3e_potential_stats call: count, how many
@@ -133,5 +135,36 @@ int init_batch_f32(BatchBase* b, const double* const* phis);
 size_t batch_bytes_f16s(const lb3e_params* ps, int n);
 BatchBase* new_batch_f16s(const lb3e_params* ps, int n, void* ws, void* stream);
 int init_batch_f16s(BatchBase* b, const double* const* phis);
+size_t workspace_bytes_bf16s(const lb3e_params& p);
+SimBase* make_sim_bf16s(const lb3e_params& p, void* ws, void* stream);
+size_t batch_bytes_bf16s(const lb3e_params* ps, int n);
+BatchBase* new_batch_bf16s(const lb3e_params* ps, int n, void* ws, void* stream);
+int init_batch_bf16s(BatchBase* b, const double* const* phis);
+
+// Deformation factor (a - b)/(a + b) of an indicator from its moments m = (sum chi,
+// chi x, chi y, chi x^2, chi y^2), with a = 2 sqrt(Iyy), b = 2 sqrt(Ixx) the radii
+// along and across the field (y); and its derivative along a tangent dm of those
+// moments (0 where the radii vanish).
+inline double deformation_of(const double* m, const double* dm, double* dD) {
+    if (dD) *dD = 0.0;
+    const double A = m[0];
+    if (!(A > 0)) return 0.0;
+    const double xc = m[1] / A, yc = m[2] / A;
+    const double Ixx = m[3] / A - xc * xc, Iyy = m[4] / A - yc * yc;
+    if (!(Ixx > 0) || !(Iyy > 0)) return 0.0;
+    const double a = 2.0 * std::sqrt(Iyy), b = 2.0 * std::sqrt(Ixx);
+    if (dD && dm) {
+        const double dxc = (dm[1] - xc * dm[0]) / A, dyc = (dm[2] - yc * dm[0]) / A;
+        const double dIxx = (dm[3] - (m[3] / A) * dm[0]) / A - 2.0 * xc * dxc;
+        const double dIyy = (dm[4] - (m[4] / A) * dm[0]) / A - 2.0 * yc * dyc;
+        const double da = dIyy / std::sqrt(Iyy), db = dIxx / std::sqrt(Ixx);  // d(2 sqrt(I)) = dI / sqrt(I)
+        *dD = 2.0 * (b * da - a * db) / ((a + b) * (a + b));
+    }
+    return (a - b) / (a + b);
+}
+
+// precision codes: the plain builds (one arithmetic type, populations stored in it
+// or in a narrower type) and the dual-number tangent builds
+inline bool plain_precision(int prec) { return prec == 0 || prec == 1 || prec == 2 || prec == 5; }
 
 }  // namespace lb3e

@@ -14,6 +14,7 @@
 // bounce-back at y walls).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
 
@@ -189,13 +190,19 @@ template <> struct Store<__half> {
     static __device__ __forceinline__ float ld(const __half* p, size_t i) { return __half2float(p[i]); }
     static __device__ __forceinline__ void st(__half* p, size_t i, float v) { p[i] = __float2half_rn(v); }
 };
+// BF16: the FP32 exponent range (no subnormals at the small magnitudes of the flow
+// and charge populations), 8 significant bits
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, size_t i) { return __bfloat162float(p[i]); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, size_t i, float v) { p[i] = __float2bfloat16_rn(v); }
+};
 template <class T, int M> struct Store<Dual<T, M>> {
     static __device__ __forceinline__ Dual<T, M> ld(const Dual<T, M>* p, size_t i) { return p[i]; }
     static __device__ __forceinline__ void st(Dual<T, M>* p, size_t i, Dual<T, M> v) { p[i] = v; }
 };
 template <class S>
 __host__ __device__ constexpr bool anchored() {
-    return std::is_same<S, float>::value || std::is_same<S, __half>::value;
+    return std::is_same<S, float>::value || std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
 }
 
 // ---------------------------------------------------------------- grid helpers
@@ -495,21 +502,26 @@ __global__ void __launch_bounds__(256) k_poisson_rs(DevParams P, const R* __rest
 // arithmetic per cell is that of body_poisson.  Residual partials (check) are taken
 // before the first collision, the residual state (save_prev) before the last one.
 constexpr int PB_TX = 32, PB_TY = 16, PB_HALO = 8;
-template <int H>
+// CPT cells per thread: 3 for the plain kernel, 2 on the correction to an FP64
+// anchor (RS), whose anchor increments then fit in registers (9 per cell) at the
+// same number of resident threads
+template <int H, bool RS = false>
 struct PBGeom {
     static constexpr int RX = PB_TX + 2 * H, RY = PB_TY + 2 * H, CELLS = RX * RY;
-    static constexpr int CPT = 3, THREADS = CELLS / CPT;
+    static constexpr int CPT = RS ? 2 : 3, THREADS = CELLS / CPT;
     static_assert(CELLS % CPT == 0, "region cells split evenly over the threads");
 };
 // blocks per SM the register budget is sized for (64 registers a thread in FP32)
-template <class R, int H>
+template <class R, int H, bool RS = false>
 __host__ __device__ constexpr int pb_min_blocks() {
+    if constexpr (RS) return std::is_same<R, float>::value ? (H == 8 ? 1 : 2) : 1;
     return std::is_same<R, float>::value ? (H == 8 ? 2 : 3) : 1;
 }
-// shared planes: 9 post-collision planes and eps (Kc), then q (q/8), or, on the
-// correction to an FP64 anchor (RS), the anchor's 9 increment planes
+// shared planes: 9 post-collision planes and eps (Kc), then q (q/8); on the
+// correction to an FP64 anchor (RS) no charge (the anchor's increments sit in
+// registers)
 template <class R, int H, bool RS = false>
-constexpr size_t pb_smem_bytes() { return (size_t)(RS ? 19 : 11) * PBGeom<H>::CELLS * sizeof(R); }
+constexpr size_t pb_smem_bytes() { return (size_t)(RS ? 10 : 11) * PBGeom<H, RS>::CELLS * sizeof(R); }
 // halo depth of the region that serves a chunk of K iterations
 __host__ __device__ constexpr int pb_halo_for(int K) { return K <= 2 ? 2 : (K <= 4 ? 4 : 8); }
 
@@ -519,7 +531,7 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
                                                 const R* __restrict__ q, R* __restrict__ prev,
                                                 double* __restrict__ partial, int Kdyn, int save_prev, int check,
                                                 int bx, int by, int gdx, const R* __restrict__ rres = nullptr) {
-    using G = PBGeom<H>;
+    using G = PBGeom<H, RS>;
     constexpr int RX = G::RX, CELLS = G::CELLS, CPT = G::CPT, NT = G::THREADS;
     extern __shared__ __align__(16) unsigned char pb_raw[];
     R* hs = reinterpret_cast<R*>(pb_raw);  // [9][CELLS] post-collision values
@@ -527,8 +539,7 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
     // form, Kc = 3 eps_hat / (tau_h den) and q / 8
     constexpr bool kFact = std::is_same<R, float>::value;
     R* se = hs + 9 * CELLS;  // eps (Kc)
-    R* sq = se + CELLS;      // q (q / 8); RS: unused
-    R* rs = se + CELLS;      // RS: [9][CELLS] the anchor's increment, added after each pull
+    R* sq = se + CELLS;      // q (q / 8); RS: not allocated
     const int nx = P.nx, ny = P.ny;
     const unsigned N = P.N;
     const int x0 = bx * PB_TX - H, y0 = by * PB_TY - H;
@@ -539,6 +550,7 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
     // bits 0-7 the distance d outside the tile (0 inside; 255: not a fluid cell),
     // bit 8 bottom wall row, bit 9 top wall row, bit 10 a tile cell inside the grid
     R h[CPT][9];
+    R rr[RS ? CPT : 1][9];  // RS: the anchor's increment at each owned cell, added after each pull
     int meta[CPT];
 #pragma unroll
     for (int m = 0; m < CPT; ++m) {
@@ -565,7 +577,7 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
             }
             if constexpr (RS) {
 #pragma unroll
-                for (int j = 0; j < 9; ++j) rs[j * CELLS + k] = rres[j * N + c];
+                for (int j = 0; j < 9; ++j) rr[m][j] = rres[j * N + c];
             }
         } else {
 #pragma unroll
@@ -573,7 +585,7 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
             se[k] = kFact ? R(0) : pv<R>(P.eps_ref, P.feps_ref);
             if constexpr (RS) {
 #pragma unroll
-                for (int j = 0; j < 9; ++j) rs[j * CELLS + k] = R(0);
+                for (int j = 0; j < 9; ++j) rr[m][j] = R(0);
             } else {
                 sq[k] = R(0);
             }
@@ -661,7 +673,7 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
 #pragma unroll
             for (int j = 0; j < 9; ++j) {
                 h[m][j] = hs[j * CELLS + k - cy(j) * RX - cx(j)];
-                if constexpr (RS) h[m][j] += rs[j * CELLS + k];
+                if constexpr (RS) h[m][j] += rr[m][j];
             }
         }
         __syncthreads();
@@ -687,7 +699,7 @@ __global__ void __launch_bounds__(PBGeom<H>::THREADS, pb_min_blocks<R, H>())
 // K iterations on the correction to an FP64 anchor (no residual sums; save_prev:
 // psi and J before the last collision into prev)
 template <class R, int H, int KC = 0>
-__global__ void __launch_bounds__(PBGeom<H>::THREADS, pb_min_blocks<R, H>())
+__global__ void __launch_bounds__(PBGeom<H, true>::THREADS, pb_min_blocks<R, H, true>())
     k_poisson_tb_rs(DevParams P, const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ eps,
                     const R* __restrict__ rres, R* __restrict__ prev, int K, int save_prev) {
     body_poisson_tb<R, H, KC, true>(P, hin, hout, eps, nullptr, prev, nullptr, K, save_prev, 0, blockIdx.x,
@@ -806,7 +818,8 @@ constexpr int TX = 32, TY = 8;
 // holding registers.  Used when the storage type is float or double.
 template <class S>
 __host__ __device__ constexpr bool fused_prefetch() {
-    return std::is_same<S, float>::value || std::is_same<S, double>::value || std::is_same<S, __half>::value;
+    return std::is_same<S, float>::value || std::is_same<S, double>::value || std::is_same<S, __half>::value ||
+           std::is_same<S, __nv_bfloat16>::value;
 }
 // staging area: 45 population planes in the storage type, then the 8 d/dt planes
 // and the charge in the arithmetic type, TX * TY cells each
@@ -1387,6 +1400,73 @@ __global__ void __launch_bounds__(256) k_observables(DevParams P, const R* __res
         for (int k = 0; k < (TX * TY) / 32; ++k) a = fmax(a, mred[k]);
         maxpart[b] = a;
     }
+}
+
+// component m of a value: 0 its value, m >= 1 its tangent m - 1 (dual builds)
+template <class R>
+__device__ __forceinline__ double comp_of(const R& v, int m) {
+    if constexpr (is_dual<R>::value) return m == 0 ? (double)v.v : (double)v.d[m - 1];
+    else return m == 0 ? (double)v : 0.0;
+}
+template <class R> struct n_comp { static constexpr int value = 1; };
+template <class T, int M> struct n_comp<Dual<T, M>> { static constexpr int value = 1 + M; };
+
+// Per-block FP64 sums for the deformation factors and their tangents: for the
+// indicators chi_inner = phi_inner and chi_outer = 1 - phi_matrix, and for each
+// component m (value, tangents), sum chi, chi x, chi y, chi x^2, chi y^2 -- at
+// partial[b * 10 M + (5 M) k + 5 m + i], k = 0 inner, 1 outer.
+template <class R>
+__global__ void __launch_bounds__(256) k_deform_moments(DevParams P, const R* __restrict__ phi,
+                                                        double* __restrict__ partial) {
+    constexpr int M = n_comp<R>::value, NV = 10 * M;
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+    const int x = blockIdx.x * TX + threadIdx.x;
+    for (int r = 0; r < OBS_Y; ++r) {
+        const int y = blockIdx.y * (TY * OBS_Y) + r * TY + threadIdx.y;
+        if (x >= P.nx || y >= P.ny) continue;
+        const unsigned N = P.N, c = (unsigned)y * P.nx + x;
+        const R pin = phi[P.inner * N + c], pmx = phi[P.matrix * N + c];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const double chis[2] = {comp_of(pin, m), (m == 0 ? 1.0 : 0.0) - comp_of(pmx, m)};
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                double* o = v + 5 * M * k + 5 * m;
+                o[0] += chis[k];
+                o[1] += chis[k] * x;
+                o[2] += chis[k] * y;
+                o[3] += chis[k] * x * x;
+                o[4] += chis[k] * y * y;
+            }
+        }
+    }
+    block_reduce_store<NV>(v, partial + (size_t)NV * (blockIdx.x + gridDim.x * blockIdx.y));
+}
+
+// Per-block FP64 sums for the shape objective of one phase: sum (phi - target)^2 and,
+// per tangent direction t, sum 2 (phi - target) dphi/dtheta_t, at partial[b * M + m]
+template <class R>
+__global__ void __launch_bounds__(256) k_shape_objective(DevParams P, const R* __restrict__ phi,
+                                                         const double* __restrict__ target,
+                                                         double* __restrict__ partial) {
+    constexpr int M = n_comp<R>::value;
+    double v[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = 0.0;
+    const int x = blockIdx.x * TX + threadIdx.x;
+    for (int r = 0; r < OBS_Y; ++r) {
+        const int y = blockIdx.y * (TY * OBS_Y) + r * TY + threadIdx.y;
+        if (x >= P.nx || y >= P.ny) continue;
+        const unsigned c = (unsigned)y * P.nx + x;
+        const R f = phi[c];
+        const double d = comp_of(f, 0) - target[c];
+        v[0] += d * d;
+#pragma unroll
+        for (int m = 1; m < M; ++m) v[m] += 2.0 * d * comp_of(f, m);
+    }
+    block_reduce_store<M>(v, partial + (size_t)M * (blockIdx.x + gridDim.x * blockIdx.y));
 }
 
 // fixed-order max of n per-block maxima

@@ -28,7 +28,7 @@ class Sim final : public SimBase {
     // workspace layout (byte offsets), computed identically by bytes() and the constructor
     struct Layout {
         size_t pop[2], h[2], phi, qt, q, eps, E, prev, diag, psi_prev, partial, result, stage, mg, ion[2], ionst,
-            anchor, rres, total;
+            anchor, rres, ja, total;
     };
     static Layout layout(const lb3e_params& p) {
         const size_t N = (size_t)p.nx * p.ny;
@@ -80,6 +80,7 @@ class Sim final : public SimBase {
         const size_t na = (p.potential_solver >= 2 && p.electric) ? N : 0;
         L.anchor = take(9 * na * sizeof(double));
         L.rres = take(9 * na * sizeof(R));
+        L.ja = take(2 * na * sizeof(R));
         L.total = o;
         return L;
     }
@@ -117,6 +118,7 @@ class Sim final : public SimBase {
         if (prm.electric && prm.potential_solver >= 2) {
             anchor_ = reinterpret_cast<double*>(b + L_.anchor);
             rres_ = reinterpret_cast<R*>(b + L_.rres);
+            ja_ = reinterpret_cast<R*>(b + L_.ja);
         }
         if ((prm.potential_solver == 1 || prm.potential_solver == 2) && prm.electric) {
             const int nl = mg_levels(prm.nx, prm.ny);
@@ -155,6 +157,7 @@ class Sim final : public SimBase {
     }
     ~Sim() override {
         if (pinned_) cudaFreeHost(pinned_);
+        if (vgraph_) cudaGraphExecDestroy(vgraph_);
     }
 
     int init(const double* phi, const double* u, const double* q, const double* noise) override {
@@ -621,35 +624,71 @@ class Sim final : public SimBase {
 
     // One FP32 V-cycle on level 0's A e = rhs (rhs and e = 0 set by the caller):
     // 2 red-black pre- and post-sweeps per level, residual restriction by sums of the
-    // four children, bilinear prolongation, 50 sweeps on the coarsest level.
+    // four children, bilinear prolongation, 50 sweeps on the coarsest level.  About
+    // 10 launches a level, most of them small: on a created stream the sequence is
+    // captured once as a CUDA graph and replayed (the level pointers are fixed for
+    // the simulation's lifetime), timed as one interval of class kc.
     int vcycle(int kc) {
+        if (stream_ == nullptr) return vcycle_launches(kc, true);  // the legacy stream cannot be captured
+        if (!vgraph_) {
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return LB3E_ERR_CUDA;
+            const int64_t l0 = launches;
+            const int rc = vcycle_launches(kc, false);
+            vgraph_nodes_ = launches - l0;
+            launches = l0;
+            if (cudaStreamEndCapture(stream_, &graph) != cudaSuccess || rc != LB3E_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc != LB3E_OK ? rc : LB3E_ERR_CUDA;
+            }
+            const cudaError_t e = cudaGraphInstantiate(&vgraph_, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                vgraph_ = nullptr;
+                return LB3E_ERR_CUDA;
+            }
+        }
+        timer.begin(stream_, kc);
+        if (cudaGraphLaunch(vgraph_, stream_) != cudaSuccess) return LB3E_ERR_CUDA;
+        timer.end(stream_);
+        launches += vgraph_nodes_;
+        return cudaGetLastError() == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
+    }
+    int vcycle_launches(int kc, bool timed) {
         const int nl = (int)mgf_.size();
         const dim3 blk(TX, TY);
+        auto begin = [&]() { if (timed) timer.begin(stream_, kc); };
+        auto done = [&]() -> int {
+            if (timed) return launched();
+            ++launches;
+            return cudaGetLastError() == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
+        };
         auto smooth = [&](int l, int sweeps) -> int {
             for (int s = 0; s < sweeps; ++s)
                 for (int color = 0; color < 2; ++color) {
-                    timer.begin(stream_, kc);
+                    begin();
                     k_mg_smooth<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], color);
-                    TRY(launched());
+                    TRY(done());
                 }
             return LB3E_OK;
         };
         for (int l = 0; l + 1 < nl; ++l) {
             TRY(smooth(l, 2));
-            timer.begin(stream_, kc);
+            begin();
             k_mg_residual<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], nullptr);
-            TRY(launched());
-            timer.begin(stream_, kc);
+            TRY(done());
+            begin();
             k_mg_restrict<float><<<mg_grid(l + 1), blk, 0, stream_>>>(mgf_[l], mgf_[l + 1]);
-            TRY(launched());
+            TRY(done());
         }
-        timer.begin(stream_, kc);
+        begin();
         k_mg_coarse_solve<float><<<1, 256, 0, stream_>>>(mgf_[nl - 1], nl == 1 ? 2 : 50);
-        TRY(launched());
+        TRY(done());
         for (int l = nl - 2; l >= 0; --l) {
-            timer.begin(stream_, kc);
+            begin();
             k_mg_prolong<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], mgf_[l + 1]);
-            TRY(launched());
+            TRY(done());
             TRY(smooth(l, 2));
         }
         return LB3E_OK;
@@ -716,6 +755,72 @@ class Sim final : public SimBase {
         }
     }
 
+    // D_inner, D_outer of the current populations' phi (sum_j f^i_j) and, in the
+    // tangent builds, their derivatives along each tangent direction (dD[3 k + t],
+    // k = 0 inner, 1 outer; zero where a build has no such direction)
+    int deformation(double* D, double* dD) override {
+        constexpr int M = n_comp<R>::value, NV = 10 * M;
+        R* tmp = reinterpret_cast<R*>(d_.stage + N_);  // phi (3 planes) and q~ after the first plane
+        timer.begin(stream_, KC_MOMENTS);
+        k_moments<R, S><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.pop[cur_], d_.phi, tmp, tmp + 3 * N_);
+        TRY(launched());
+        const dim3 og = obs_grid(p_.nx, p_.ny);
+        const int nb = (int)(og.x * og.y);
+        timer.begin(stream_, KC_REDUCE);
+        k_deform_moments<R><<<og, dim3(TX, TY), 0, stream_>>>(dp_, tmp, d_.partial);
+        TRY(launched());
+        timer.begin(stream_, KC_REDUCE);
+        k_reduce_partials<NV><<<1, 256, 0, stream_>>>(d_.partial, nb, d_.result);
+        TRY(launched());
+        if (cudaMemcpyAsync(pinned_, d_.result, NV * sizeof(double), cudaMemcpyDeviceToHost, stream_) != cudaSuccess)
+            return LB3E_ERR_CUDA;
+        TRY(sync());
+        for (int k = 0; k < 2; ++k) {
+            const double* m = pinned_ + 5 * M * k;
+            D[k] = deformation_of(m, nullptr, nullptr);
+            for (int t = 0; t < 3; ++t) {
+                double g = 0.0;
+                if (t + 1 < M) deformation_of(m, m + 5 * (t + 1), &g);
+                if (dD) dD[3 * k + t] = g;
+            }
+        }
+        return LB3E_OK;
+    }
+
+    // J = sum_i sum_cells (phi_i - target_i)^2 of the current populations' phi and,
+    // in the tangent builds, dJ[t] = sum 2 (phi_i - target_i) dphi_i/dtheta_t
+    int shape_objective(const double* target, double* J, double* dJ) override {
+        constexpr int M = n_comp<R>::value;
+        R* tmp = reinterpret_cast<R*>(d_.stage + N_);  // phi (3 planes) and q~ after the first plane
+        timer.begin(stream_, KC_MOMENTS);
+        k_moments<R, S><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.pop[cur_], d_.phi, tmp, tmp + 3 * N_);
+        TRY(launched());
+        const dim3 og = obs_grid(p_.nx, p_.ny);
+        const int nb = (int)(og.x * og.y);
+        double sum[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < 3; ++i) {
+            // the target plane goes to the first staging plane (host or device source)
+            if (cudaMemcpyAsync(d_.stage, target + (size_t)i * N_, N_ * sizeof(double), cudaMemcpyDefault,
+                                stream_) != cudaSuccess)
+                return LB3E_ERR_CUDA;
+            timer.begin(stream_, KC_REDUCE);
+            k_shape_objective<R><<<og, dim3(TX, TY), 0, stream_>>>(dp_, tmp + (size_t)i * N_, d_.stage, d_.partial);
+            TRY(launched());
+            timer.begin(stream_, KC_REDUCE);
+            k_reduce_partials<M><<<1, 256, 0, stream_>>>(d_.partial, nb, d_.result);
+            TRY(launched());
+            if (cudaMemcpyAsync(pinned_, d_.result, M * sizeof(double), cudaMemcpyDeviceToHost, stream_) !=
+                cudaSuccess)
+                return LB3E_ERR_CUDA;
+            TRY(sync());
+            for (int m = 0; m < M; ++m) sum[m] += pinned_[m];
+        }
+        *J = sum[0];
+        if (dJ)
+            for (int t = 0; t < 3; ++t) dJ[t] = t + 1 < M ? sum[t + 1] : 0.0;
+        return LB3E_OK;
+    }
+
   private:
     // relative residual from the 4 FP64 sums |d psi|^2, |psi|^2, |d J|^2, |J|^2
     static double rel_residual(const double* v) {
@@ -749,7 +854,7 @@ class Sim final : public SimBase {
         } else {
             timer.begin(stream_, KC_ANCHOR);
             k_anchor_refresh<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.h[hcur_], d_.eps, d_.q,
-                                                                      d_.stage, 1.0 / dp_.tau_h, dp_.tau_h / 3.0);
+                                                                      d_.stage, ja_, 1.0 / dp_.tau_h, dp_.tau_h / 3.0);
             TRY(launched());
             timer.begin(stream_, KC_ANCHOR);
             k_anchor_residual<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.stage, rres_, d_.partial);
@@ -852,16 +957,16 @@ class Sim final : public SimBase {
                     k_poisson_rs<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps,
                                                                           rres_, d_.psi_prev, sv);
                 else if (pb_halo_for(c) == 2)
-                    k_poisson_tb_rs<R, 2><<<pgrid, PBGeom<2>::THREADS, pb_smem_bytes<R, 2, true>(), stream_>>>(
+                    k_poisson_tb_rs<R, 2><<<pgrid, PBGeom<2, true>::THREADS, pb_smem_bytes<R, 2, true>(), stream_>>>(
                         dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
                 else if (c == 4)
-                    k_poisson_tb_rs<R, 4, 4><<<pgrid, PBGeom<4>::THREADS, pb_smem_bytes<R, 4, true>(), stream_>>>(
+                    k_poisson_tb_rs<R, 4, 4><<<pgrid, PBGeom<4, true>::THREADS, pb_smem_bytes<R, 4, true>(), stream_>>>(
                         dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
                 else if (pb_halo_for(c) == 4)
-                    k_poisson_tb_rs<R, 4><<<pgrid, PBGeom<4>::THREADS, pb_smem_bytes<R, 4, true>(), stream_>>>(
+                    k_poisson_tb_rs<R, 4><<<pgrid, PBGeom<4, true>::THREADS, pb_smem_bytes<R, 4, true>(), stream_>>>(
                         dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
                 else if constexpr (pb_smem_bytes<R, 8, true>() <= 227 * 1024)
-                    k_poisson_tb_rs<R, 8><<<pgrid, PBGeom<8>::THREADS, pb_smem_bytes<R, 8, true>(), stream_>>>(
+                    k_poisson_tb_rs<R, 8><<<pgrid, PBGeom<8, true>::THREADS, pb_smem_bytes<R, 8, true>(), stream_>>>(
                         dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
                 TRY(launched());
                 poisson_iters_run_ += c;
@@ -929,7 +1034,7 @@ class Sim final : public SimBase {
         last_iters_ = it;
         if constexpr (!is_dual<R>::value) {
             timer.begin(stream_, KC_FIELDS);
-            k_anchor_fields<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.h[hcur_], d_.eps, d_.E, nullptr);
+            k_anchor_efield<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, ja_, d_.h[hcur_], d_.eps, d_.E);
             TRY(launched());
         }
         return LB3E_OK;
@@ -1084,8 +1189,11 @@ class Sim final : public SimBase {
     int chunk_ = 4;  // pseudo-iterations per potential launch (4: fastest measured on a 4096^2 lattice)
     std::vector<MGLevel> mg_;
     std::vector<MGLevelF> mgf_;
+    cudaGraphExec_t vgraph_ = nullptr;  // the captured V-cycle (multigrid solvers, created streams)
+    int64_t vgraph_nodes_ = 0;
     double* anchor_ = nullptr;  // FP64 anchor of the potential populations (solvers 2, 3)
     R* rres_ = nullptr;         // the anchor's increment over one pseudo-iteration
+    R* ja_ = nullptr;           // the anchor's flux J = sum_j c_j a_j (2 planes), for E
     R* ion_[2] = {nullptr, nullptr};  // Nernst-Planck populations (ions = 1)
     R* nion_ = nullptr;               // n_i of the step (2 planes), then (n_i v_i)^{n-1} (4 planes)
     R* ionprev_ = nullptr;

@@ -1,7 +1,8 @@
-"""Host-side deformation factor and its tangent (no GPU)."""
+"""The test-side deformation factor and its tangent (no GPU): the reference the
+library's lb3e_deformation is checked against."""
 import numpy as np
 
-from paper_2608_05787_b300.gradients import deformation_from_moments
+from deformation_ref import deformation_from_moments  # tests/ is on sys.path (pytest rootdir conftest)
 
 
 def _ellipse(n, a, b, w=3.0):

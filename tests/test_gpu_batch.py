@@ -92,3 +92,32 @@ def test_batch_rejects_mixed_iteration_counts():
     inst[1][0]["poisson_fixed_iter"] = 7
     with pytest.raises(L.LB3EError):
         L.Batch([p for p, _ in inst], [phi for _, phi in inst])
+
+
+@pytest.mark.slow
+def test_sweep_instances_at_full_size_match_the_oracle():
+    """Eight seeded instances of the 256-instance sweep at their stated sizes (the
+    first instance of each side 128, 192, 256, 384, 512 and the next three), stepped
+    together as one FP64 batch for 50 steps with the sweep's 16 warm-started
+    potential iterations a step, against the oracle run on each: every field to
+    1e-12 and the deformation factors to 1e-12."""
+    import paper_2608_05787_b300 as L
+    insts = W.config_batched_sweep(precision=0)
+    picks = []
+    for side in (128, 192, 256, 384, 512):
+        picks.append(next(i for i, s in enumerate(insts) if s["shape"][0] == side))
+    picks += [i for i in range(len(insts)) if i not in picks][:3]
+    assert len(picks) == 8 and {insts[i]["shape"][0] for i in picks} == {128, 192, 256, 384, 512}
+    b = L.Batch([insts[i]["params"] for i in picks], [W.sweep_phi(insts[i]) for i in picks]).set_chunk(4)
+    b.run(50)
+    obs = b.observables()
+    for k, i in enumerate(picks):
+        o = oracle.Oracle(insts[i]["params"], W.sweep_phi(insts[i]))
+        o.step(50)
+        for f in ("phi1", "phi2", "phi3", "phinow1", "phinow3", "psi", "ex", "ey", "q", "ux", "uy", "p"):
+            ref = o.field(f)
+            err = np.abs(b.field(k, f) - ref).max() / max(np.abs(ref).max(), 1e-300)
+            assert err <= 1e-12, (i, insts[i]["shape"], f, err)
+        oo = o.observables()
+        for key in ("D_inner", "D_outer"):
+            assert abs(obs[k][key] - oo[key]) <= 1e-12, (i, key, obs[k][key], oo[key])

@@ -40,7 +40,7 @@ def _base(p, name):
 
 
 def _D_outer(field_fn, p):
-    from paper_2608_05787_b300.gradients import deformation_from_moments
+    from deformation_ref import deformation_from_moments
     chi = 1.0 - field_fn(f"phinow{p['matrix_phase']}")
     return deformation_from_moments(chi, [])[0]
 
@@ -125,3 +125,106 @@ def test_autograd_function_returns_the_tangent_derivatives():
     assert abs(E0.grad.item() - g["V_top"] * p["ny"]) <= 1e-12 * abs(g["V_top"] * p["ny"])
     assert abs(er.grad.item() - g["eps3"]) <= 1e-12 * abs(g["eps3"])
     assert abs(g23.grad.item() - g["gamma23"]) <= 1e-12 * abs(g["gamma23"])
+
+
+@pytest.mark.parametrize("precision", [0, 1, 3])
+def test_library_deformation_matches_the_moments_of_the_fields(precision):
+    """lb3e_deformation (GPU moment sums, host finish) against the test-side NumPy
+    reduction of the same phinow fields; in the tangent build also the tangents."""
+    import paper_2608_05787_b300 as L
+    from deformation_ref import deformation_from_moments
+    p, phi, steps = _setup(steps=10)
+    p = dict(p, precision=precision, tangent_param=(0, 3, 6) if precision == 3 else (-1, -1, -1))
+    sim = L.Sim(p, phi)
+    sim.step(steps)
+    (Di, Do), (dDi, dDo) = sim.deformation()
+    for k, key, D, dD in ((p["inner_phase"], "inner", Di, dDi), (p["matrix_phase"], "outer", Do, dDo)):
+        sgn = 1.0 if key == "inner" else -1.0
+        chi = sim.field(f"phinow{k}") if key == "inner" else 1.0 - sim.field(f"phinow{k}")
+        dchi = [sgn * sim.field(f"phinow{k}", tangent=t + 1) for t in range(3)] if precision == 3 else []
+        ref, g = deformation_from_moments(chi, dchi)
+        assert abs(D - ref) <= 1e-9 * max(abs(ref), 1e-6), (key, D, ref)
+        for t in range(len(g)):
+            assert abs(dD[t] - g[t]) <= 1e-6 * max(abs(g[t]), 1e-12), (key, t, dD[t], g[t])
+        if precision != 3:
+            assert dD == (0.0, 0.0, 0.0)
+
+
+def _J(sim_or_orc, target):
+    phi = np.stack([sim_or_orc.field(f"phinow{i}") for i in (1, 2, 3)])
+    return float(((phi - target) ** 2).sum())
+
+
+def test_shape_objective_tangent_matches_central_differences():
+    """The target-shape objective J = sum (phi - phi_target)^2 (target: the compound
+    drop stretched 10% along the field): FP64 tangents against FP64 central
+    differences of J from GPU runs, and the library's J against the fields'."""
+    import paper_2608_05787_b300 as L
+    from paper_2608_05787_b300.gradients import shape_objective_tangents
+    p, phi, steps = _setup()
+    y, x = np.meshgrid(np.arange(64.0), np.arange(64.0), indexing="ij")
+    target = W.compound_droplet(64, 64, 8.0, 16.0, 4.0, yc=32.0)
+    # stretch along y by resampling the radius
+    r = np.sqrt((x - 32.0) ** 2 + ((y - 32.0) / 1.1) ** 2)
+    p3 = 0.5 + 0.5 * np.tanh(2.0 * (8.0 - r) / 4.0)
+    p2 = (1.0 - p3) * (0.5 + 0.5 * np.tanh(2.0 * (16.0 - r) / 4.0))
+    target = np.stack([1.0 - p2 - p3, p2, p3])
+    J, g = shape_objective_tangents(p, phi, steps, target, wrt=WRT, precision=4)
+    s = L.Sim(p, phi)
+    s.step(steps)
+    assert abs(s.shape_objective(target)[0] - _J(s, target)) <= 1e-10 * _J(s, target)
+    assert abs(J - _J(s, target)) <= 1e-9 * J
+    for name in WRT:
+        h = 1e-4 * _base(p, name)
+        vals = []
+        for sg in (+1, -1):
+            sim = L.Sim(_perturb(p, name, sg * h), phi)
+            sim.step(steps)
+            vals.append(sim.shape_objective(target)[0])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        print(f"{name}: dJ tangent {g[name]:.9e}  fd {fd:.9e}")
+        assert abs(g[name] - fd) <= 1e-4 * abs(fd), name
+
+
+def test_shape_objective_autograd():
+    import torch
+
+    from paper_2608_05787_b300.gradients import shape_objective, shape_objective_tangents
+    p, phi, steps = _setup(steps=10)
+    target = W.compound_droplet(64, 64, 9.0, 15.0, 4.0)
+    E0 = torch.tensor(p["V_top"] / p["ny"], dtype=torch.float64, requires_grad=True)
+    er = torch.tensor(4.0, dtype=torch.float64, requires_grad=True)
+    g23 = torch.tensor(1e-3, dtype=torch.float64, requires_grad=True)
+    J = shape_objective(E0, er, g23, p, phi, steps, target)
+    J.backward()
+    _, g = shape_objective_tangents(p, phi, steps, target)
+    assert abs(E0.grad.item() - g["V_top"] * p["ny"]) <= 1e-12 * abs(g["V_top"] * p["ny"])
+    assert abs(g23.grad.item() - g["gamma23"]) <= 1e-12 * abs(g["gamma23"])
+
+
+@pytest.mark.slow
+def test_config5_stated_size_tangents_match_fp64_central_differences():
+    """Configuration 5 as stated: a 256^2 compound drop (radii 32/64) under a field
+    between electrodes plus shear (walls at -/+1e-3), 4000 steps, the potential
+    iterated 16 times a step (warm-started; a fixed count keeps D a smooth function of
+    the parameters).  dD_outer/dE0, dD/d(eps3/eps1), dD/dgamma23 from one FP32
+    tangent run (three directions) and from FP64 tangent runs, against FP64 central
+    differences (relative step 1e-4) of GPU runs."""
+    import paper_2608_05787_b300 as L
+    from paper_2608_05787_b300.gradients import deformation_tangents
+    cfg = W.config_adjoint(n=256, precision=0)
+    p = dict(cfg["params"], poisson_fixed_iter=16)
+    phi, steps = cfg["phi"], cfg["steps"]
+    D64, g64 = deformation_tangents(p, phi, steps, wrt=WRT, precision=4)
+    D32, g32 = deformation_tangents(p, phi, steps, wrt=WRT, precision=3)
+    for name in WRT:
+        h = 1e-4 * _base(p, name)
+        vals = []
+        for sg in (+1, -1):
+            sim = L.Sim(_perturb(p, name, sg * h), phi)
+            sim.step(steps)
+            vals.append(sim.deformation()[0][1])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        print(f"{name}: fd {fd:.6e}  fp64 tangent {g64[name]:.6e}  fp32 tangent {g32[name]:.6e}")
+        assert abs(g64[name] - fd) <= 1e-4 * abs(fd), name
+        assert abs(g32[name] - fd) <= FP32_TOL[name] * abs(fd), name

@@ -126,10 +126,10 @@ def test_fp64_static_compound_full_run():
 
 
 # ------------------------------------------------------------------ reduced precision
-@pytest.mark.parametrize("precision,tol", [(1, 1e-5), (2, 1e-3)])
+@pytest.mark.parametrize("precision,tol", [(1, 1e-5), (2, 1e-3), (5, 1e-3)])
 def test_reduced_precision_static_compound(precision, tol):
-    """FP32 and FP16-stored populations against the FP64 oracle, 200 steps of the
-    64x64 compound drop (fixed iteration counts so both do the same work)."""
+    """FP32, FP16- and BF16-stored populations against the FP64 oracle, 200 steps of
+    the 64x64 compound drop (fixed iteration counts so both do the same work)."""
     cfg = W.config_static_compound(precision=precision)
     p = dict(cfg["params"], poisson_fixed_iter=60)
     sim, orc = run_pair(p, cfg["phi"], 200, noise=cfg["noise"])
@@ -137,27 +137,50 @@ def test_reduced_precision_static_compound(precision, tol):
     assert max(errs.values()) <= tol, errs
 
 
+# The bound per field after the stated 2000 steps: the stated tolerance (FP32 1e-5,
+# narrow storage 1e-3), or twice what the FP64 oracle itself does under the rounding
+# the build adds, whichever is larger (tests/golden/precision_sensitivity.json,
+# written from the oracle alone by make_precision_sensitivity.py).  FP16 and BF16
+# storage: the oracle with its stored populations rounded to the format every step
+# (the GPU's errors are that rounding's effect, within a factor 1.3 on every field).
+# FP32: the oracle with every stored value perturbed at the FP32 unit roundoff every
+# step (the rounding of the FP32 arithmetic; the GPU's errors are 0.4-0.8 of it).
+# The velocity of this near-static drop is a small residual of balanced forces, so
+# the scheme amplifies rounding most there: no implementation in these formats can
+# hold u_x to the stated tolerance.
+MODEL_FACTOR = 2.0
+FORMAT = {1: ("fp32", 1e-5, "perturbation"), 2: ("fp16", 1e-3, "rounding"), 5: ("bf16", 1e-3, "rounding")}
+
+
+def sensitivity_bounds(precision):
+    import json
+    from pathlib import Path
+    d = json.loads((Path(__file__).parent / "golden" / "precision_sensitivity.json").read_text())
+    name, tol, model = FORMAT[precision]
+    ref = d["formats"][name][model]
+    return {f: max(tol, MODEL_FACTOR * ref[f]) for f in FIELDS}
+
+
 @pytest.mark.slow
-@pytest.mark.parametrize("precision,tol", [(1, 1e-5), (2, 1e-3)])
-def test_reduced_precision_static_compound_full_run(precision, tol):
-    """The stated 64x64 run (2000 steps) in FP32 and with FP16-stored populations,
-    against the FP64 oracle, phase fields.  The potential is solved to 1e-6 here:
-    the FP32 potential populations cannot resolve relative increments of 1e-8 (the
-    iteration would run to its cap every step), so both sides use the tolerance
-    FP32 can meet."""
+@pytest.mark.parametrize("precision", [1, 2, 5])
+def test_reduced_precision_static_compound_full_run(precision):
+    """The stated 64x64 run: 2000 steps, the potential to a relative increment of
+    1e-8 every step (on the GPU the LB iteration on an FP64 anchor, solver 3, the
+    same iteration and stopping test as the oracle's), every field gated."""
+    L = _lb()
     cfg = W.config_static_compound(precision=precision)
-    p = dict(cfg["params"], poisson_tol=1e-6)
-    sim, orc = run_pair(p, cfg["phi"], cfg["steps"], noise=cfg["noise"])
-    # gated: the phase fields and the potential (FP32 also charge and field); the
-    # velocity and pressure are reported only: u is a small residual of balanced
-    # capillary, Coulomb and pressure terms (max |u| ~ 1e-5 against p ~ 1e-4), so
-    # FP32 rounding of those terms leaves ~1e-9 absolute, ~1e-4 of max |u|
-    gated = ["phi1", "phi2", "phi3", "phinow1", "phinow2", "phinow3", "psi"]
-    if precision == 1:
-        gated += ["q", "ex", "ey"]
-    errs = field_errors(sim, orc, gated)
-    print(f"precision {precision}: 2000-step errors per field", field_errors(sim, orc))
-    assert max(errs.values()) <= tol, errs
+    sim = L.Sim(dict(cfg["params"], potential_solver=3), cfg["phi"], noise=cfg["noise"])
+    orc = oracle.Oracle(cfg["params"], cfg["phi"], noise=cfg["noise"])
+    sim.step(cfg["steps"])
+    orc.step(cfg["steps"])
+    errs = field_errors(sim, orc)
+    bounds = sensitivity_bounds(precision)
+    print(f"precision {precision}: 2000-step errors and bounds per field",
+          {f: (f"{errs[f]:.2e}", f"{bounds[f]:.1e}") for f in FIELDS})
+    bad = {f: (errs[f], bounds[f]) for f in FIELDS if not errs[f] <= bounds[f]}
+    assert not bad, bad
+    st = sim.potential_stats()
+    assert st["not_converged"] == 0 and st["max_residual"] <= 1e-8, st
 
 
 def test_state_save_load_roundtrip():
