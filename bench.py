@@ -121,7 +121,8 @@ def peaks():
 
 # the files the profiled kernels' device code is compiled from (host sequencing and
 # the ABI layer do not enter it), hashed with the build's flags
-KERNEL_SOURCES = ("lb3e_kernels.cuh", "lb3e_params.cuh", "lb3e_dual.cuh", "lb3e_f32.cu", "lb3e_f64.cu")
+KERNEL_SOURCES = ("lb3e_kernels.cuh", "lb3e_anchor.cuh", "lb3e_mg.cuh", "lb3e_params.cuh", "lb3e_dual.cuh",
+                  "lb3e_f32.cu", "lb3e_f64.cu")
 
 
 def kernel_source_hash() -> str:
