@@ -536,12 +536,13 @@ def run_sweep(args):
     insts = W.config_batched_sweep(precision=args.precision)
     cells = [i["shape"][0] * i["shape"][1] for i in insts]
     mine = shard(cells, ws)[rank]
-    from paper_2608_05787_b300.autotune import tune_batch_chunk
-    chunk = tune_batch_chunk([insts[i]["params"] for i in mine])
+    from paper_2608_05787_b300.autotune import tune_batch
+    tuned = tune_batch([insts[i]["params"] for i in mine])
+    chunk = tuned["chunk"]
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         b = L.Batch([insts[i]["params"] for i in mine], [W.sweep_phi(insts[i]) for i in mine], stream=stream)
-        b.set_chunk(chunk)
+        b.set_chunk(chunk).set_tile(tuned["tile"])
         b.run(args.warmup)
         torch.cuda.synchronize()
         if dist:
@@ -571,6 +572,7 @@ def run_sweep(args):
                 "data": "synthetic (seeded sweep of the stated parameter ranges)",
                 "config": {"workload": "batched sweep: 256 compound drops, sides {128,192,256,384,512}",
                            "cells": sum(cells), "potential_iters_per_step": 16, "autotuned_chunk": chunk,
+                           "autotuned_fused_tile": f"32x{tuned['tile']}",
                            "parallelism": f"instances sharded over {ws} ranks" if ws > 1 else "one batch"},
                 "roofline": {"bound": "hbm", "achieved": per_cell * total / t / 1e9, "peak": hbm, "unit": "GB/s",
                              "frac": per_cell * total / t / 1e9 / hbm, "traffic": None,
@@ -768,7 +770,9 @@ def run_deformation3d(args):
 
     torch.cuda.set_device(0)
     prec = min(args.precision, 1)
-    cfg = W.config_deformation_3d(precision=prec)
+    # --n other than the 2-D default scales the 256^3 drop (profiling runs)
+    n3 = 256 if args.n == 4096 else args.n
+    cfg = W.config_deformation_3d(n=n3, r_out=40.0 * n3 / 256, r_in=20.0 * n3 / 256, precision=prec)
     params = cfg["params"]
     n = params["nx"]
     N = n ** 3

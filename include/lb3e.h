@@ -345,6 +345,13 @@ int lb3e_batch_get_field(lb3e_batch* b, int32_t instance, int32_t field_id, doub
  * Errors: NULL, PARAM (out of range), CUDA. */
 int lb3e_batch_set_potential_chunk(lb3e_batch* b, int32_t iterations_per_launch);
 
+/* Tile of the batch's fused chemical-potential/force/collide/stream pass: blocks of
+ * 32 x rows cells, rows 4, 8 (the default) or 16 (FP32-compute precisions only).  The
+ * result does not depend on it (the per-cell arithmetic is the same); the speed does
+ * -- shared memory per block, blocks per SM and the halo overhead change with it.
+ * Errors: NULL, PARAM (another height), CUDA. */
+int lb3e_batch_set_fused_tile(lb3e_batch* b, int32_t rows);
+
 /* Kernel launches issued for this batch (graph nodes counted per replay). */
 int64_t lb3e_batch_launch_count(const lb3e_batch* b);
 

@@ -140,6 +140,7 @@ def lib() -> C.CDLL:
         L.lb3e_batch_observables.argtypes = [vp, C.POINTER(Observables)]
         L.lb3e_batch_get_field.argtypes = [vp, C.c_int32, C.c_int32, vp]
         L.lb3e_batch_set_potential_chunk.argtypes = [vp, C.c_int32]
+        L.lb3e_batch_set_fused_tile.argtypes = [vp, C.c_int32]
         L.lb3e_batch_launch_count.restype = C.c_int64
         L.lb3e_batch_launch_count.argtypes = [vp]
         L.lb3e_batch_destroy.argtypes = [vp]
@@ -409,6 +410,12 @@ class Batch:
         """Potential pseudo-iterations per launch (1..8); see autotune.py."""
         _check("lb3e_batch_set_potential_chunk", lib().lb3e_batch_set_potential_chunk(self._h, int(k)))
         self.chunk = int(k)
+        return self
+
+    def set_tile(self, rows: int) -> "Batch":
+        """Rows of the fused pass's 32 x rows tiles (4, 8, 16; speed only); see autotune.py."""
+        _check("lb3e_batch_set_fused_tile", lib().lb3e_batch_set_fused_tile(self._h, int(rows)))
+        self.tile = int(rows)
         return self
 
     def observables(self) -> list:

@@ -300,6 +300,11 @@ int lb3e_batch_create(const lb3e_params* params, int32_t n, const double* const*
     return LB3E_OK;
 }
 
+int lb3e_batch_set_fused_tile(lb3e_batch* b, int32_t rows) {
+    if (!b) return LB3E_ERR_NULL;
+    return b->b->set_fused_tile(rows);
+}
+
 int lb3e_batch_run(lb3e_batch* b, int32_t nsteps) {
     if (!b) return LB3E_ERR_NULL;
     if (nsteps < 0) return LB3E_ERR_PARAM;

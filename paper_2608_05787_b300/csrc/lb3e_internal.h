@@ -108,6 +108,7 @@ struct BatchBase {
     virtual int count() const = 0;
     virtual int64_t total_launches() const = 0;
     virtual int set_chunk(int k) = 0;
+    virtual int set_fused_tile(int rows) = 0;
     int64_t launches = 0;
 };
 

@@ -114,9 +114,12 @@ template <class R>
 __host__ __device__ constexpr bool exact_arith() { return std::is_same<R, double>::value; }
 // blocks per SM the register budget is sized for: FP32 80 registers a thread, FP32
 // duals 128 (at 255 they held one block, 8 warps, per SM), FP64 unconstrained
-template <class R>
+template <class R, int BY = 8>
 __host__ __device__ constexpr int fused_min_blocks() {
-    return std::is_same<R, float>::value ? 3 : (f32_family<R>::value ? 2 : 1);
+    // tiles of other heights (batches only): the same ~80 registers a thread for 32 x 4
+    // (six blocks); 32 x 16 holds one block by its shared memory
+    if constexpr (std::is_same<R, float>::value) return BY == 4 ? 6 : (BY == 16 ? 1 : 3);
+    return f32_family<R>::value ? 2 : 1;
 }
 
 // A parameter as an R: the FP32 build reads its single-precision copy.
@@ -344,22 +347,36 @@ __global__ void __launch_bounds__(256) k_moments(DevParams P, const S* __restric
 }
 
 // ---------------------------------------------------------------- S2-S4: properties, stencils, charge
-// Reads phi on the 1-ring (L1-cached), writes eps and the closed-form charge
-// q = [q~ + (sigma/eps grad eps . E - grad sigma . E)/2] / (1 + sigma/(2 eps)),
-// with E of the previous step.
+// eps and sigma (Eq. 29-30) of the block's 32 x 8 tile and its one-cell ring are
+// formed once per cell into shared memory (ghost rows mirrored at walls, as the
+// stencil expects); each thread then takes the Eq. 33 gradients from there (the
+// same sums, in the same order, as a per-neighbour evaluation) and writes eps and
+// the closed-form charge q = [q~ + (sigma/eps grad eps . E - grad sigma . E)/2] /
+// (1 + sigma/(2 eps)), with E of the previous step.
 template <class R>
 __device__ __forceinline__ void body_prologue(const DevParams P, const R* __restrict__ phi, const R* __restrict__ qt,
                                                   const R* __restrict__ E, R* __restrict__ q, R* __restrict__ eps_out,
                                                   int use_qt, int bx, int by, int gdx) {
-    const int x = bx * blockDim.x + threadIdx.x, y = by * blockDim.y + threadIdx.y;
+    constexpr int SX = 34, SY = 10;  // blockDim (32, 8) and a one-cell ring
+    __shared__ R se_[SY * SX], ss_[SY * SX];
+    const int x0 = bx * blockDim.x, y0 = by * blockDim.y;
+    const unsigned N = P.N;
+    for (int k = threadIdx.x + blockDim.x * threadIdx.y; k < SX * SY; k += blockDim.x * blockDim.y) {
+        const int ly = k / SX, lx = k - ly * SX;
+        const unsigned n = (unsigned)tile_row(y0 + ly - 1, P.ny, P.bc_y) * P.nx + wrapi(x0 + lx - 1, P.nx);
+        const R p0 = phi[n], p1 = phi[N + n], p2 = phi[2 * N + n];
+        se_[k] = perm<R>(P, p0, p1, p2);
+        ss_[k] = cond<R>(P, p0, p1, p2);
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
-    const unsigned N = P.N, c = (unsigned)y * P.nx + x;
+    const unsigned c = (unsigned)y * P.nx + x;
+    const int sc = (threadIdx.y + 1) * SX + threadIdx.x + 1;
     R gex = R(0), gey = R(0), gsx = R(0), gsy = R(0), e0 = R(0), s0 = R(0);
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
-        const unsigned n = (unsigned)ghost_row(y + cy(j), P.ny, P.bc_y) * P.nx + wrapi(x + cx(j), P.nx);
-        const R p0 = phi[n], p1 = phi[N + n], p2 = phi[2 * N + n];
-        const R e = perm<R>(P, p0, p1, p2), s = cond<R>(P, p0, p1, p2);
+        const R e = se_[sc + cy(j) * SX + cx(j)], s = ss_[sc + cy(j) * SX + cx(j)];
         gex += wgt<R>(j) * R(cx(j)) * e;
         gey += wgt<R>(j) * R(cy(j)) * e;
         gsx += wgt<R>(j) * R(cx(j)) * s;
@@ -823,9 +840,9 @@ __host__ __device__ constexpr bool fused_prefetch() {
 }
 // staging area: 45 population planes in the storage type, then the 8 d/dt planes
 // and the charge in the arithmetic type, TX * TY cells each
-template <class R, class S>
+template <class R, class S, int BY = 8>
 __host__ __device__ constexpr size_t fused_dyn_smem() {
-    return fused_prefetch<S>() ? (size_t)45 * TX * TY * sizeof(S) + (size_t)9 * TX * TY * sizeof(R) : 0;
+    return fused_prefetch<S>() ? (size_t)45 * TX * BY * sizeof(S) + (size_t)9 * TX * BY * sizeof(R) : 0;
 }
 template <class T>
 __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
@@ -844,13 +861,13 @@ __device__ __forceinline__ void cp_async16(T* smem, const T* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <class R, class S>
+template <class R, class S, int BY = 8>
 __device__ __forceinline__ void body_fused(const DevParams P, const S* __restrict__ pin, S* __restrict__ pout,
                                                    const R* __restrict__ phi, const R* __restrict__ qf,
                                                    const R* __restrict__ E, R* __restrict__ prev,
                                                    R* __restrict__ diag, int first, int write_diag, int bx, int by, int gdx) {
-    constexpr int PX = TX + 4, PY = TY + 4;  // phi tile, 2-ring
-    constexpr int MX = TX + 2, MY = TY + 2;  // mu / E tile, 1-ring
+    constexpr int PX = TX + 4, PY = BY + 4;  // phi tile, 2-ring
+    constexpr int MX = TX + 2, MY = BY + 2;  // mu / E tile, 1-ring
     __shared__ R sphi[3][PY * PX];
     __shared__ R sE[2][MY * MX];
     __shared__ R smu[3][MY * MX];
@@ -863,7 +880,7 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     __shared__ R sprop[kProps ? 3 : 1][kProps ? MY * MX : 1];
     const int nx = P.nx, ny = P.ny;
     const unsigned N = P.N;
-    const int x0 = bx * TX, y0 = by * TY;
+    const int x0 = bx * TX, y0 = by * BY;
     const int tid = threadIdx.x + TX * threadIdx.y;
 
     // request the tile's populations, d/dt state and charge first: 16-byte copies
@@ -872,8 +889,8 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     // storage, plain loads later; slot layout [plane][ty * TX + tx]
     constexpr bool kStage = fused_prefetch<S>();
     extern __shared__ __align__(16) unsigned char fz_raw[];
-    S* sp = reinterpret_cast<S*>(fz_raw);                                      // [45][TX * TY]
-    R* sr = reinterpret_cast<R*>(fz_raw + (size_t)45 * TX * TY * sizeof(S));  // [9][TX * TY]
+    S* sp = reinterpret_cast<S*>(fz_raw);                                      // [45][TX * BY]
+    R* sr = reinterpret_cast<R*>(fz_raw + (size_t)45 * TX * BY * sizeof(S));  // [9][TX * BY]
     bool staged = false;  // the same for the whole block (depends on nx only)
     if constexpr (kStage) {
         constexpr int VS = 16 / (int)sizeof(S), VR = 16 / (int)sizeof(R);  // cells per 16-byte segment
@@ -881,18 +898,18 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
         auto rplane = [&](int k) -> const R* { return k < 8 ? prev + (size_t)k * N : qf; };
         if (nx % (VS > VR ? VS : VR) == 0) {
             staged = true;
-            for (int t = tid; t < 45 * TY * SGS; t += TX * TY) {
-                const int k = t / (TY * SGS), r = (t / SGS) % TY, m = t % SGS;
+            for (int t = tid; t < 45 * BY * SGS; t += TX * BY) {
+                const int k = t / (BY * SGS), r = (t / SGS) % BY, m = t % SGS;
                 if (anchored<S>() && (k == 9 || k == 18 || k == 27)) continue;  // rest populations rebuilt
                 const int ys = y0 + r, xs = x0 + m * VS;
                 if (ys >= ny || xs >= nx) continue;  // nx % VS == 0: a segment is all in or all out
-                cp_async16(sp + k * (TX * TY) + r * TX + m * VS, pin + (size_t)k * N + (unsigned)ys * nx + xs);
+                cp_async16(sp + k * (TX * BY) + r * TX + m * VS, pin + (size_t)k * N + (unsigned)ys * nx + xs);
             }
-            for (int t = tid; t < 9 * TY * SGR; t += TX * TY) {
-                const int k = t / (TY * SGR), r = (t / SGR) % TY, m = t % SGR;
+            for (int t = tid; t < 9 * BY * SGR; t += TX * BY) {
+                const int k = t / (BY * SGR), r = (t / SGR) % BY, m = t % SGR;
                 const int ys = y0 + r, xs = x0 + m * VR;
                 if (ys >= ny || xs >= nx) continue;
-                cp_async16(sr + k * (TX * TY) + r * TX + m * VR, rplane(k) + (unsigned)ys * nx + xs);
+                cp_async16(sr + k * (TX * BY) + r * TX + m * VR, rplane(k) + (unsigned)ys * nx + xs);
             }
         } else if constexpr (sizeof(S) >= 4) {
             staged = true;
@@ -901,27 +918,27 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
                 const unsigned cs = (unsigned)ys * nx + xs;
                 for (int k = 0; k < 45; ++k) {
                     if (anchored<S>() && (k == 9 || k == 18 || k == 27)) continue;
-                    cp_async(sp + k * (TX * TY) + tid, pin + (size_t)k * N + cs);
+                    cp_async(sp + k * (TX * BY) + tid, pin + (size_t)k * N + cs);
                 }
-                for (int k = 0; k < 9; ++k) cp_async(sr + k * (TX * TY) + tid, rplane(k) + cs);
+                for (int k = 0; k < 9; ++k) cp_async(sr + k * (TX * BY) + tid, rplane(k) + cs);
             }
         }
         cp_async_commit();
     }
     // population k (plane k of the set-major layout) of this cell
     auto popk = [&](int k, unsigned cc) -> R {
-        if (kStage && staged) return (R)sp[k * (TX * TY) + tid];
+        if (kStage && staged) return (R)sp[k * (TX * BY) + tid];
         return Store<S>::ld(pin, k * N + cc);
     };
 
-    for (int k = tid; k < PY * PX; k += TX * TY) {
+    for (int k = tid; k < PY * PX; k += TX * BY) {
         const int ly = k / PX, lx = k % PX;
         const unsigned n = (unsigned)tile_row(y0 + ly - 2, ny, P.bc_y) * nx + wrapi(x0 + lx - 2, nx);
         sphi[0][k] = phi[n];
         sphi[1][k] = phi[N + n];
         sphi[2][k] = phi[2 * N + n];
     }
-    for (int k = tid; k < MY * MX; k += TX * TY) {
+    for (int k = tid; k < MY * MX; k += TX * BY) {
         const int ly = k / MX, lx = k % MX;
         const unsigned n = (unsigned)tile_row(y0 + ly - 1, ny, P.bc_y) * nx + wrapi(x0 + lx - 1, nx);
         sE[0][k] = E[n];
@@ -930,7 +947,7 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     __syncthreads();
     // mu on the 1-ring at in-domain rows
     const R c24 = kconst<R>(P.fc24, [&] { return R(24) / pv<R>(P.D, P.fD); });
-    for (int k = tid; k < MY * MX; k += TX * TY) {
+    for (int k = tid; k < MY * MX; k += TX * BY) {
         const int ly = k / MX, lx = k % MX;
         const int gy = y0 + ly - 1;
         if constexpr (kProps) {
@@ -954,7 +971,7 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     __syncthreads();
     // ghost rows of mu mirror the in-domain row they face
     if (P.bc_y != 0) {
-        for (int k = tid; k < MY * MX; k += TX * TY) {
+        for (int k = tid; k < MY * MX; k += TX * BY) {
             const int ly = k / MX, lx = k % MX;
             const int gy = y0 + ly - 1;
             if (gy >= 0 && gy < ny) continue;
@@ -1018,7 +1035,7 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     gsx = oc2(gsx); gsy = oc2(gsy);
 
     const R Ex = sE[0][my * MX + mx], Ey = sE[1][my * MX + mx];
-    const R qc = (kStage && staged) ? sr[8 * (TX * TY) + tid] : qf[c];
+    const R qc = (kStage && staged) ? sr[8 * (TX * BY) + tid] : qf[c];
     // R of Eq. 47 with q^n and E^n
     const R rr = dv(sg, ep, rcp(ep));
     const R Rc = -rr * qc + rr * (gex * Ex + gey * Ey) - (gsx * Ex + gsy * Ey);
@@ -1048,7 +1065,7 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
 
     // d/dt terms (first-order backward differences)
     auto prevk = [&](int k) -> R {
-        if (kStage && staged) return sr[k * (TX * TY) + tid];
+        if (kStage && staged) return sr[k * (TX * BY) + tid];
         return prev[k * N + c];
     };
     R dpu[3][2], dqu[2];
@@ -1538,12 +1555,14 @@ __global__ void __launch_bounds__(256) kb_potential_fields(const InstState<R, S>
     if (!e.P.electric) return;
     body_potential_fields<R>(e.P, e.h[hcur], e.eps, e.E, nullptr, t.y, t.z, 0);
 }
-template <class R, class S>
-__global__ void __launch_bounds__(TX * TY, fused_min_blocks<R>())
+// the fused pass over tiles of 32 x BY cells (BY 4, 8 or 16, picked by the autotuner)
+template <class R, class S, int BY = 8>
+__global__ void __launch_bounds__(TX * BY, fused_min_blocks<R, BY>())
     kb_fused(const InstState<R, S>* __restrict__ st, const int4* __restrict__ tiles, int cur, int first, int write_diag) {
     const int4 t = tiles[blockIdx.x];
     const InstState<R, S>& e = st[t.x];
-    body_fused<R, S>(e.P, e.pop[cur], e.pop[cur ^ 1], e.phi, e.q, e.E, e.prev, e.diag, first, write_diag, t.y, t.z, 0);
+    body_fused<R, S, BY>(e.P, e.pop[cur], e.pop[cur ^ 1], e.phi, e.q, e.E, e.prev, e.diag, first, write_diag, t.y, t.z,
+                         0);
 }
 
 }  // namespace lb3e

@@ -1219,15 +1219,20 @@ class Batch final : public BatchBase {
     static size_t ptiles_of(const lb3e_params& p) {
         return (size_t)((p.nx + PB_TX - 1) / PB_TX) * ((p.ny + PB_TY - 1) / PB_TY);
     }
+    // tiles of 32 x rows cells for the fused pass
+    static size_t ftiles_of(const lb3e_params& p, int rows) {
+        return (size_t)((p.nx + TX - 1) / TX) * ((p.ny + rows - 1) / rows);
+    }
     static size_t bytes(const lb3e_params* ps, int n) {
-        size_t ntiles = 0, nptiles = 0, b = 0;
+        size_t ntiles = 0, nptiles = 0, nft = 0, b = 0;
         for (int i = 0; i < n; ++i) {
             ntiles += tiles_of(ps[i]);
             nptiles += ptiles_of(ps[i]);
+            nft += ftiles_of(ps[i], 4);  // the smallest tile height needs the longest list
             b += align256(Sim<R, S>::layout(ps[i]).total);
         }
         return b + align256(n * sizeof(InstState<R, S>)) + align256(ntiles * sizeof(int4)) +
-               align256(nptiles * sizeof(int4));
+               align256(nptiles * sizeof(int4)) + align256(nft * sizeof(int4));
     }
 
     Batch(const lb3e_params* ps, int n, void* ws, cudaStream_t st) : stream_(st), n_(n) {
@@ -1243,6 +1248,10 @@ class Batch final : public BatchBase {
         b += align256(ntiles * sizeof(int4));
         ptiles_ = reinterpret_cast<int4*>(b);
         b += align256(nptiles * sizeof(int4));
+        size_t nft = 0;
+        for (int i = 0; i < n; ++i) nft += ftiles_of(ps[i], 4);
+        ftiles_ = reinterpret_cast<int4*>(b);
+        b += align256(nft * sizeof(int4));
         ntiles_ = (int)ntiles;
         nptiles_ = (int)nptiles;
         iters_ = 0;
@@ -1260,9 +1269,16 @@ class Batch final : public BatchBase {
 
     int init(const double* const* phis) {
         if constexpr (fused_dyn_smem<R, S>() > 0) {
-            if (cudaFuncSetAttribute(kb_fused<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)fused_dyn_smem<R, S>()) != cudaSuccess)
+            if (cudaFuncSetAttribute(kb_fused<R, S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)fused_dyn_smem<R, S, 4>()) != cudaSuccess ||
+                cudaFuncSetAttribute(kb_fused<R, S, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)fused_dyn_smem<R, S, 8>()) != cudaSuccess)
                 return LB3E_ERR_CUDA;
+            if constexpr (std::is_same<R, float>::value) {
+                if (cudaFuncSetAttribute(kb_fused<R, S, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fused_dyn_smem<R, S, 16>()) != cudaSuccess)
+                    return LB3E_ERR_CUDA;
+            }
         }
         for (int i = 0; i < n_; ++i) TRY(sims_[i]->init(phis[i], nullptr, nullptr, nullptr));
         std::vector<InstState<R, S>> tab(n_);
@@ -1306,6 +1322,26 @@ class Batch final : public BatchBase {
                 cudaSuccess ||
             cudaStreamSynchronize(stream_) != cudaSuccess)
             return LB3E_ERR_CUDA;
+        return set_fused_tile(8);
+    }
+
+    // tile height of the fused pass (32 x rows cells a block): 4, 8, or 16 in the FP32
+    // compute builds; the result does not depend on it, the speed does
+    int set_fused_tile(int rows) override {
+        if (rows != 4 && rows != 8 && !(rows == 16 && std::is_same<R, float>::value)) return LB3E_ERR_PARAM;
+        std::vector<int4> ft;
+        for (int i = 0; i < n_; ++i) {
+            const DevParams& P = sims_[i]->dev_params();
+            const int gx = (P.nx + TX - 1) / TX, gy = (P.ny + rows - 1) / rows;
+            for (int by = 0; by < gy; ++by)
+                for (int bx = 0; bx < gx; ++bx) ft.push_back(make_int4(i, bx, by, 0));
+        }
+        if (cudaMemcpyAsync(ftiles_, ft.data(), ft.size() * sizeof(int4), cudaMemcpyHostToDevice, stream_) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(stream_) != cudaSuccess)
+            return LB3E_ERR_CUDA;
+        nftiles_ = (int)ft.size();
+        ftile_ = rows;
         return LB3E_OK;
     }
 
@@ -1373,7 +1409,7 @@ class Batch final : public BatchBase {
 
   private:
     struct Graph {
-        int cur, hcur, chunk;
+        int cur, hcur, chunk, ftile;
         cudaGraphExec_t exec;
     };
     // potential launches per step (each swaps the h buffers once)
@@ -1403,13 +1439,21 @@ class Batch final : public BatchBase {
             }
         }
         if (iters_ > 0) kb_potential_fields<R, S><<<ntiles_, blk, 0, stream_>>>(table_, tiles_, h);
-        kb_fused<R, S><<<ntiles_, blk, fused_dyn_smem<R, S>(), stream_>>>(table_, tiles_, cur, first ? 1 : 0, diag ? 1 : 0);
+        if (ftile_ == 4)
+            kb_fused<R, S, 4><<<nftiles_, dim3(TX, 4), fused_dyn_smem<R, S, 4>(), stream_>>>(table_, ftiles_, cur,
+                                                                                           first ? 1 : 0, diag ? 1 : 0);
+        else if (ftile_ == 8)
+            kb_fused<R, S, 8><<<nftiles_, dim3(TX, 8), fused_dyn_smem<R, S, 8>(), stream_>>>(table_, ftiles_, cur,
+                                                                                           first ? 1 : 0, diag ? 1 : 0);
+        else if constexpr (std::is_same<R, float>::value)
+            kb_fused<R, S, 16><<<nftiles_, dim3(TX, 16), fused_dyn_smem<R, S, 16>(), stream_>>>(
+                table_, ftiles_, cur, first ? 1 : 0, diag ? 1 : 0);
         launches += 3 + swaps() + (iters_ > 0);
         return cudaGetLastError() == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
     }
     int graph_for(int cur, int hcur, cudaGraphExec_t* out) {
         for (auto& g : graphs_)
-            if (g.cur == cur && g.hcur == hcur && g.chunk == chunk_) { *out = g.exec; return LB3E_OK; }
+            if (g.cur == cur && g.hcur == hcur && g.chunk == chunk_ && g.ftile == ftile_) { *out = g.exec; return LB3E_OK; }
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LB3E_ERR_CUDA;
         const int64_t l0 = launches;
@@ -1424,19 +1468,20 @@ class Batch final : public BatchBase {
         const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return LB3E_ERR_CUDA;
-        graphs_.push_back({cur, hcur, chunk_, exec});
+        graphs_.push_back({cur, hcur, chunk_, ftile_, exec});
         *out = exec;
         return LB3E_OK;
     }
 
     cudaStream_t stream_;
-    int n_ = 0, ntiles_ = 0, nptiles_ = 0, iters_ = 0, chunk_ = 1;
+    int n_ = 0, ntiles_ = 0, nptiles_ = 0, nftiles_ = 0, ftile_ = 8, iters_ = 0, chunk_ = 1;
     bool pb_ready_ = false;
     int cur_ = 0, hcur_ = 0;
     int64_t steps_ = 0;
     InstState<R, S>* table_ = nullptr;
     int4* tiles_ = nullptr;
     int4* ptiles_ = nullptr;
+    int4* ftiles_ = nullptr;  // the fused pass's tiles of 32 x ftile_ cells
     std::vector<Sim<R, S>*> sims_;
     std::vector<Graph> graphs_;
 };

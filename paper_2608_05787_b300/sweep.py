@@ -40,9 +40,10 @@ def run_shard(instances: Sequence[dict], indices: Sequence[int], steps: int,
 
 def _run_batch(mine: list, steps: int) -> list:
     from . import Batch
-    from .autotune import tune_batch_chunk
+    from .autotune import tune_batch
     params = [m["params"] for m in mine]
-    b = Batch(params, [m["phi"] for m in mine]).set_chunk(tune_batch_chunk(params))
+    tuned = tune_batch(params)
+    b = Batch(params, [m["phi"] for m in mine]).set_chunk(tuned["chunk"]).set_tile(tuned["tile"])
     b.run(steps)
     return b.observables()
 

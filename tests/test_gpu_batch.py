@@ -80,10 +80,37 @@ def test_autotuner_picks_a_candidate_and_caches(tmp_path, monkeypatch):
     from paper_2608_05787_b300 import autotune
     monkeypatch.setenv("LB3E_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     inst = _instances(1, iters=8)
-    k = autotune.tune_batch_chunk([p for p, _ in inst], steps=2)
-    assert k in autotune.CANDIDATES
-    assert autotune.tune_batch_chunk([p for p, _ in inst]) == k     # served from the cache
+    t = autotune.tune_batch([p for p, _ in inst], steps=2)
+    assert t["chunk"] in autotune.CHUNKS and t["tile"] in autotune.TILES
+    assert autotune.tune_batch([p for p, _ in inst]) == t     # served from the cache
     assert (tmp_path / "tune.json").exists()
+
+
+@pytest.mark.parametrize("precision,rows,tol", [(0, 4, 0.0), (1, 4, 1e-5), (1, 16, 1e-5), (2, 16, 1e-4),
+                                               (5, 4, 1e-4)])
+def test_fused_tile_shapes_give_the_same_state(precision, rows, tol):
+    """The fused pass over tiles of 32 x 4 or 32 x 16 cells against the default 32 x 8:
+    bitwise in FP64 (no contraction; the per-cell arithmetic does not depend on the
+    tile), within the batch-vs-single bounds otherwise (each instantiation may fuse
+    different multiply-adds)."""
+    import paper_2608_05787_b300 as L
+    inst = _instances(precision, iters=5)
+    a = L.Batch([p for p, _ in inst], [phi for _, phi in inst])
+    b = L.Batch([p for p, _ in inst], [phi for _, phi in inst]).set_tile(rows)
+    a.run(6)
+    b.run(6)
+    for i in range(len(inst)):
+        for f in ("phinow1", "phinow3", "psi", "ex", "ux", "p", "q"):
+            x, r = b.field(i, f), a.field(i, f)
+            assert np.abs(x - r).max() <= tol * np.abs(r).max(), (rows, i, f, np.abs(x - r).max())
+
+
+def test_fused_tile_of_16_rows_is_refused_in_fp64():
+    import paper_2608_05787_b300 as L
+    inst = _instances(0, iters=5)
+    b = L.Batch([p for p, _ in inst], [phi for _, phi in inst])
+    with pytest.raises(L.LB3EError):
+        b.set_tile(16)
 
 
 def test_batch_rejects_mixed_iteration_counts():
