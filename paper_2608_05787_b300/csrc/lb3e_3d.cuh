@@ -383,12 +383,16 @@ __global__ void __launch_bounds__(256) k3_chem(P3 P, const R* __restrict__ phi, 
 // arithmetic.  Blocks of consecutive planes run close together in time, so the
 // neighbour planes come from L2.
 constexpr int K3X = 34, K3Y = 10, K3P = K3X * K3Y, K3F = 3 * K3P;  // staged tile: 3 planes of 34 x 10
+// Shared memory: the six staged stencil fields, then the cell's 75 populations and
+// 12 d/dt history planes, requested as cp.async copies at entry so that all of them
+// are in flight together (the kernel was bound by the latency of these loads).
+constexpr int K3T = 256;  // cells (threads) a block
 template <class R>
-constexpr size_t k3_collide_smem() { return (size_t)6 * K3F * sizeof(R); }
-// blocks per SM the register budget is sized for (FP32: 3 blocks, 85 registers a
-// thread; FP64 unconstrained)
+constexpr size_t k3_collide_smem() { return (size_t)(6 * K3F + (5 * Q3 + 12) * K3T) * sizeof(R); }
+// blocks per SM: FP32 two (its shared memory), so up to 128 registers a thread;
+// FP64 one
 template <class R>
-constexpr int k3_collide_min_blocks() { return std::is_same<R, float>::value ? 3 : 1; }
+constexpr int k3_collide_min_blocks() { return std::is_same<R, float>::value ? 2 : 1; }
 template <class R>
 __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3 P, const R* __restrict__ pin, R* __restrict__ pout,
                                                   const R* __restrict__ phi, const R* __restrict__ q,
@@ -398,7 +402,28 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
                                                   R* __restrict__ diag, int first, int write_diag) {
     extern __shared__ __align__(16) unsigned char k3_raw[];
     R* st = reinterpret_cast<R*>(k3_raw);  // [6 fields][3 planes][10][34]
+    R* sp = st + 6 * K3F;                  // [75 population planes][256 cells], then [12 history planes][256]
     const size_t N = P.N;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    {
+        // this cell's populations and history: 4- or 8-byte copies (one per plane), or
+        // 16-byte copies of row segments when the tile's rows are whole and aligned
+        const int xa = blockIdx.x * 32, ya = blockIdx.y * 8, za = blockIdx.z;
+        constexpr int V = 16 / (int)sizeof(R), SEG = 32 / V;  // cells per 16 bytes, segments per row
+        const bool whole = xa + 32 <= P.nx && ya + 8 <= P.ny && (P.nx % V) == 0 && (N % V) == 0;
+        auto plane = [&](int k) -> const R* { return k < 5 * Q3 ? pin + (size_t)k * N : prev + (size_t)(k - 5 * Q3) * N; };
+        if (whole) {
+            for (int t = tid; t < (5 * Q3 + 12) * 8 * SEG; t += K3T) {
+                const int k = t / (8 * SEG), r = (t / SEG) % 8, m = t % SEG;
+                const size_t g = ((size_t)za * P.ny + ya + r) * P.nx + xa + m * V;
+                cp_async16(sp + k * K3T + r * 32 + m * V, plane(k) + g);
+            }
+        } else if (xa + (int)threadIdx.x < P.nx && ya + (int)threadIdx.y < P.ny) {
+            const size_t g = ((size_t)za * P.ny + ya + threadIdx.y) * P.nx + xa + threadIdx.x;
+            for (int k = 0; k < 5 * Q3 + 12; ++k) cp_async(sp + k * K3T + tid, plane(k) + g);
+        }
+        cp_async_commit();
+    }
     {
         const int x0 = blockIdx.x * 32 - 1, y0 = blockIdx.y * 8 - 1, zc = blockIdx.z;
         int zs[3];
@@ -410,7 +435,6 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
             zs[d] = zz;
         }
         const R* const fl[6] = {mu, mu + N, mu + 2 * N, eps_f, sig_f, rho_f};
-        const int tid = threadIdx.x + 32 * threadIdx.y;
         for (int k = tid; k < K3F; k += 256) {
             const int pz = k / K3P, r = k - pz * K3P, ly = r / K3X, lx = r - ly * K3X;
             const size_t n = ((size_t)zs[pz] * P.ny + wrapi(y0 + ly, P.ny)) * P.nx + wrapi(x0 + lx, P.nx);
@@ -418,6 +442,7 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
             for (int f = 0; f < 6; ++f) st[f * K3F + k] = fl[f][n];
         }
     }
+    cp_async_wait_all();  // the copies are published by the barrier
     __syncthreads();
     int x, y, z;
     size_t c;
@@ -481,7 +506,7 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
     // S9: Eq. 41
     R g[Q3];
 #pragma unroll
-    for (int j = 0; j < Q3; ++j) g[j] = pin[j * N + c];
+    for (int j = 0; j < Q3; ++j) g[j] = sp[j * K3T + tid];
     R u[3], p;
     {
         R m0 = R(0), m1 = R(0), m2 = R(0), g1 = R(0);
@@ -503,9 +528,9 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) dpu[i][a] = first ? R(0) : ph[i] * u[a] - prev[(3 * i + a) * N + c];
+        for (int a = 0; a < 3; ++a) dpu[i][a] = first ? R(0) : ph[i] * u[a] - sp[(5 * Q3 + 3 * i + a) * K3T + tid];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) dqu[a] = first ? R(0) : qc * u[a] - prev[(9 + a) * N + c];
+    for (int a = 0; a < 3; ++a) dqu[a] = first ? R(0) : qc * u[a] - sp[(5 * Q3 + 9 + a) * K3T + tid];
 
     // S11: phase populations with the mobility of Eq. 28
     const R tf = R(P.tau_f), itf = R(1.0 / P.tau_f), m0 = R(P.m0), im0 = R(1.0 / P.m0);
@@ -533,7 +558,7 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
             const R feq = (j == 0) ? ph[i] - (R(1) - w3<R>(0)) * mui
                                    : w3<R>(j) * mui + ocs2(w3<R>(j) * cdot3<R>(j, pu0, pu1, pu2));
             const R Fj = w3<R>(j) * cdot3<R>(j, A[0], A[1], A[2]);
-            const R fj = pin[(Q3 * (i + 1) + j) * N + c];
+            const R fj = sp[(Q3 * (i + 1) + j) * K3T + tid];
             const R v = fj - dv(fj - feq, tf, itf) + pf * Fj;
             size_t t;
             if (target3(P, x, y, z, j, t)) pout[(Q3 * (i + 1) + j) * N + t] = v;
@@ -578,7 +603,7 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
             const R leq = P.cc ? w3<R>(j) * qc * (R(1) + ocs2(cu)) : w3<R>(j) * qc;
             const R Sj = pl * w3<R>(j) * Rc;
             const R Tj = P.cc ? ocs2(pl * w3<R>(j) * cdot3<R>(j, dqu[0], dqu[1], dqu[2])) : R(0);
-            const R lj = pin[(Q3 * 4 + j) * N + c];
+            const R lj = sp[(Q3 * 4 + j) * K3T + tid];
             const R v = lj - dv(lj - leq, tl, itl) + Sj + Tj;
             size_t t;
             if (target3(P, x, y, z, j, t)) pout[(Q3 * 4 + j) * N + t] = v;
