@@ -532,6 +532,27 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
 #pragma unroll
     for (int a = 0; a < 3; ++a) dqu[a] = first ? R(0) : qc * u[a] - sp[(5 * Q3 + 9 + a) * K3T + tid];
 
+    // streaming targets, the same for the five sets: the neighbour's index within a
+    // plane, or this cell (bit j of wall set) when link j leaves through a z wall
+    unsigned tgt[Q3];
+    unsigned wall = 0u;
+#pragma unroll
+    for (int j = 0; j < Q3; ++j) {
+        size_t t;
+        if (target3(P, x, y, z, j, t)) {
+            tgt[j] = (unsigned)t;
+        } else {
+            tgt[j] = (unsigned)c;
+            wall |= 1u << j;
+        }
+    }
+    // post-collision value v of population j of `set`: to the neighbour, or back to
+    // this cell in the opposite direction at a wall
+    auto push = [&](int set, int j, R v) {
+        const int jj = ((wall >> j) & 1u) ? opp3(j) : j;
+        pout[(size_t)(Q3 * set + jj) * N + tgt[j]] = v;
+    };
+
     // S11: phase populations with the mobility of Eq. 28
     const R tf = R(P.tau_f), itf = R(1.0 / P.tau_f), m0 = R(P.m0), im0 = R(1.0 / P.m0);
     const R pf = R(1) - R(1) / (R(2) * tf);
@@ -559,10 +580,7 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
                                    : w3<R>(j) * mui + ocs2(w3<R>(j) * cdot3<R>(j, pu0, pu1, pu2));
             const R Fj = w3<R>(j) * cdot3<R>(j, A[0], A[1], A[2]);
             const R fj = sp[(Q3 * (i + 1) + j) * K3T + tid];
-            const R v = fj - dv(fj - feq, tf, itf) + pf * Fj;
-            size_t t;
-            if (target3(P, x, y, z, j, t)) pout[(Q3 * (i + 1) + j) * N + t] = v;
-            else pout[(Q3 * (i + 1) + opp3(j)) * N + c] = v;
+            push(i + 1, j, fj - dv(fj - feq, tf, itf) + pf * Fj);
         }
     }
     // S12: flow populations
@@ -585,12 +603,11 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
             const R cF = cdot3<R>(j, F[0], F[1], F[2]);
             const R G = w3<R>(j) * (ugr + ocs2(cF) + ocs2(cu * cgr - c2 * ugr));
             const R v = g[j] - dv(g[j] - geq, tg, itg) + pg * G;
-            size_t t;
-            if (target3(P, x, y, z, j, t)) {
-                pout[j * N + t] = v;
-            } else {
+            if ((wall >> j) & 1u) {
                 const R uw = R(c3z(j) > 0 ? P.uwt : P.uwb);
-                pout[opp3(j) * N + c] = v - ocs2(R(2) * w3<R>(j) * rho * (R(c3x(j)) * uw));
+                push(0, j, v - ocs2(R(2) * w3<R>(j) * rho * (R(c3x(j)) * uw)));
+            } else {
+                push(0, j, v);
             }
         }
     }
@@ -604,10 +621,7 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
             const R Sj = pl * w3<R>(j) * Rc;
             const R Tj = P.cc ? ocs2(pl * w3<R>(j) * cdot3<R>(j, dqu[0], dqu[1], dqu[2])) : R(0);
             const R lj = sp[(Q3 * 4 + j) * K3T + tid];
-            const R v = lj - dv(lj - leq, tl, itl) + Sj + Tj;
-            size_t t;
-            if (target3(P, x, y, z, j, t)) pout[(Q3 * 4 + j) * N + t] = v;
-            else pout[(Q3 * 4 + opp3(j)) * N + c] = v;
+            push(4, j, lj - dv(lj - leq, tl, itl) + Sj + Tj);
         }
     }
 #pragma unroll
