@@ -104,6 +104,8 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=0,
                     help="cap on LB potential iterations per step (default: the workload's 20000); profiling "
                          "runs use a small cap to keep ncu captures short, and config records it")
+    ap.add_argument("--fused-tile", type=int, default=0,
+                    help="rows of the fused pass's 32-wide tiles, 4, 8 or 16 (default: the library's, 4 in FP32)")
     ap.add_argument("--chunk", type=int, default=0,
                     help="LB potential iterations per launch, 1..8 (default: the library's)")
     ap.add_argument("--check-every", type=int, default=0,
@@ -362,6 +364,8 @@ def run_lb3e(args):
         sim = L.Sim(params, phi_dev, stream=stream)
         if args.chunk:
             sim.set_chunk(args.chunk)
+        if args.fused_tile:
+            sim.set_tile(args.fused_tile)
         t_init = time.perf_counter() - t_init0
         init_obs = sim.observables()
         sim.step(args.warmup)
@@ -459,6 +463,8 @@ def run_lb3e(args):
             s2 = L.Sim(params, host_phi, stream=stream)
             if args.chunk:
                 s2.set_chunk(args.chunk)
+            if args.fused_tile:
+                s2.set_tile(args.fused_tile)
             for _ in range(args.steps):
                 s2.step(1)
                 s2.observables()

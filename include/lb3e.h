@@ -285,6 +285,13 @@ int64_t lb3e_potential_iterations(const lb3e_handle* h);
  * Errors: NULL, PARAM (out of range). */
 int lb3e_set_potential_chunk(lb3e_handle* h, int32_t iterations_per_launch);
 
+/* Tile of the fused chemical-potential/force/collide/stream pass: blocks of 32 x rows
+ * cells, rows 4 (the default in the FP32-compute precisions), 8 (the default
+ * otherwise) or 16 (FP32-compute precisions only; 8 only in the tangent builds).  The per-cell arithmetic is the same for every tile (FP64
+ * states agree bitwise); the speed differs.  Errors: NULL, PARAM (another height, a
+ * three-dimensional lattice). */
+int lb3e_set_fused_tile(lb3e_handle* h, int32_t rows);
+
 /* Kernel timing with CUDA events recorded on the simulation's stream around each
  * launch (off by default; costs two event records per launch).  Enabling or
  * disabling clears the totals. */

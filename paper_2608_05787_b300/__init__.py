@@ -126,6 +126,7 @@ def lib() -> C.CDLL:
         L.lb3e_potential_iterations.argtypes = [vp]
         L.lb3e_set_timing.argtypes = [vp, C.c_int32]
         L.lb3e_set_potential_chunk.argtypes = [vp, C.c_int32]
+        L.lb3e_set_fused_tile.argtypes = [vp, C.c_int32]
         L.lb3e_set_ions.argtypes = [vp, vp]
         L.lb3e_potential_fd_residual.argtypes = [vp, dp]
         L.lb3e_deformation.argtypes = [vp, dp, dp]
@@ -344,6 +345,11 @@ class Sim:
     def set_chunk(self, k: int) -> "Sim":
         """LB potential iterations per kernel launch (1..8; speed only)."""
         _check("lb3e_set_potential_chunk", lib().lb3e_set_potential_chunk(self._h, int(k)))
+        return self
+
+    def set_tile(self, rows: int) -> "Sim":
+        """Rows of the fused pass's 32 x rows tiles (4, 8, 16; speed only)."""
+        _check("lb3e_set_fused_tile", lib().lb3e_set_fused_tile(self._h, int(rows)))
         return self
 
     def kernel_times(self) -> dict:

@@ -941,6 +941,7 @@ class Sim3 final : public SimBase {
     int fd_residual(double*) override { return LB3E_ERR_PARAM; }
     int deformation(double*, double*) override { return LB3E_ERR_PARAM; }
     int shape_objective(const double*, double*, double*) override { return LB3E_ERR_PARAM; }
+    int set_fused_tile(int) override { return LB3E_ERR_PARAM; }
 
   private:
     // Scratch for the rho, sigma, eps outputs of a field-readback moments pass: the

@@ -224,6 +224,11 @@ int lb3e_potential_stats(lb3e_handle* h, int64_t* solves, int64_t* not_converged
     return LB3E_OK;
 }
 
+int lb3e_set_fused_tile(lb3e_handle* h, int32_t rows) {
+    if (!h) return LB3E_ERR_NULL;
+    return h->sim->set_fused_tile(rows);
+}
+
 int lb3e_deformation(lb3e_handle* h, double* D, double* dD) {
     if (!h || !D) return LB3E_ERR_NULL;
     return h->sim->deformation(D, dD);

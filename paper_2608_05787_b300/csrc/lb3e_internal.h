@@ -86,6 +86,7 @@ struct SimBase {
     virtual int fd_residual(double* out) = 0;
     virtual int deformation(double* D, double* dD) = 0;
     virtual int shape_objective(const double* target, double* J, double* dJ) = 0;
+    virtual int set_fused_tile(int rows) = 0;
     int64_t launches = 0;
     LaunchTimer timer;
     // potential solves since the last lb3e_potential_stats call: count, how many

@@ -1230,12 +1230,13 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
         }
     }
 }
-template <class R, class S>
-__global__ void __launch_bounds__(TX * TY, fused_min_blocks<R>()) k_fused(DevParams P, const S* __restrict__ pin, S* __restrict__ pout,
+// the fused pass on one lattice, tiles of 32 x BY cells (lb3e_set_fused_tile)
+template <class R, class S, int BY = 8>
+__global__ void __launch_bounds__(TX * BY, fused_min_blocks<R, BY>()) k_fused(DevParams P, const S* __restrict__ pin, S* __restrict__ pout,
                                                    const R* __restrict__ phi, const R* __restrict__ qf,
                                                    const R* __restrict__ E, R* __restrict__ prev,
                                                    R* __restrict__ diag, int first, int write_diag) {
-    body_fused<R, S>(P, pin, pout, phi, qf, E, prev, diag, first, write_diag, blockIdx.x, blockIdx.y, gridDim.x);
+    body_fused<R, S, BY>(P, pin, pout, phi, qf, E, prev, diag, first, write_diag, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 // ---------------------------------------------------------------- initial populations

@@ -165,6 +165,16 @@ class Sim final : public SimBase {
             if (cudaFuncSetAttribute(k_fused<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)fused_dyn_smem<R, S>()) != cudaSuccess)
                 return LB3E_ERR_CUDA;
+            if constexpr (!is_dual<R>::value) {
+                if (cudaFuncSetAttribute(k_fused<R, S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fused_dyn_smem<R, S, 4>()) != cudaSuccess)
+                    return LB3E_ERR_CUDA;
+            }
+            if constexpr (std::is_same<R, float>::value) {
+                if (cudaFuncSetAttribute(k_fused<R, S, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fused_dyn_smem<R, S, 16>()) != cudaSuccess)
+                    return LB3E_ERR_CUDA;
+            }
         }
         if (cudaHostAlloc(reinterpret_cast<void**>(&pinned_), 64 * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
             return LB3E_ERR_CUDA;
@@ -246,9 +256,7 @@ class Sim final : public SimBase {
             }
             if (p_.electric) TRY(potential());
             timer.begin(stream_, KC_FUSED);
-            k_fused<R, S><<<grid2_, dim3(TX, TY), fused_dyn_smem<R, S>(), stream_>>>(dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q,
-                                                                 d_.E, d_.prev, d_.diag, step_ == 0 ? 1 : 0,
-                                                                 (last || p_.ions) ? 1 : 0);
+            fused_launch(step_ == 0 ? 1 : 0, (last || p_.ions) ? 1 : 0);
             TRY(launched());
             if constexpr (!is_dual<R>::value) {
                 if (p_.ions) {  // with the u^n (diag) and E^n of this step
@@ -486,6 +494,15 @@ class Sim final : public SimBase {
     }
 
     int64_t potential_iterations() const override { return poisson_iters_run_; }
+
+    // tile height of the fused pass (4, 8 or 16 rows of 32 cells; 16 in the FP32
+    // compute builds, 8 only in the tangent builds)
+    int set_fused_tile(int rows) override {
+        if (rows == 8) { ftile_ = 8; return LB3E_OK; }
+        if constexpr (is_dual<R>::value) return LB3E_ERR_PARAM;
+        if (rows == 4 || (rows == 16 && std::is_same<R, float>::value)) { ftile_ = rows; return LB3E_OK; }
+        return LB3E_ERR_PARAM;
+    }
     int kernel_times(double* ms, int64_t* counts) override {
         TRY(sync());
         timer.collect();
@@ -496,6 +513,26 @@ class Sim final : public SimBase {
             timer.n[k] = 0;
         }
         return LB3E_OK;
+    }
+
+    void fused_launch(int first, int write_diag) {
+        auto grid = [&](int rows) { return dim3((p_.nx + TX - 1) / TX, (p_.ny + rows - 1) / rows); };
+        if constexpr (!is_dual<R>::value) {
+            if (ftile_ == 4) {
+                k_fused<R, S, 4><<<grid(4), dim3(TX, 4), fused_dyn_smem<R, S, 4>(), stream_>>>(
+                    dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q, d_.E, d_.prev, d_.diag, first, write_diag);
+                return;
+            }
+        }
+        if constexpr (std::is_same<R, float>::value) {
+            if (ftile_ == 16) {
+                k_fused<R, S, 16><<<grid(16), dim3(TX, 16), fused_dyn_smem<R, S, 16>(), stream_>>>(
+                    dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q, d_.E, d_.prev, d_.diag, first, write_diag);
+                return;
+            }
+        }
+        k_fused<R, S><<<grid2_, dim3(TX, TY), fused_dyn_smem<R, S>(), stream_>>>(
+            dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q, d_.E, d_.prev, d_.diag, first, write_diag);
     }
 
     // --- used by Batch: device buffers, and bookkeeping after steps run elsewhere
@@ -1187,6 +1224,9 @@ class Sim final : public SimBase {
     double* pinned_ = nullptr;
     bool pb_ready_ = false;
     int chunk_ = 4;  // pseudo-iterations per potential launch (4: fastest measured on a 4096^2 lattice)
+    // rows of the fused pass's 32-wide tiles: 4 in FP32 compute (3% faster than 8 on a
+    // 4096^2 lattice, six blocks a SM), 8 otherwise
+    int ftile_ = std::is_same<R, float>::value ? 4 : 8;
     std::vector<MGLevel> mg_;
     std::vector<MGLevelF> mgf_;
     cudaGraphExec_t vgraph_ = nullptr;  // the captured V-cycle (multigrid solvers, created streams)

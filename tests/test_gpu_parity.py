@@ -196,3 +196,21 @@ def test_state_save_load_roundtrip():
     sim.step(7)
     assert np.array_equal(a, sim.field("phinow1"))
     assert sim.observables()["step"] == 12
+
+
+@pytest.mark.parametrize("precision,rows,tol", [(0, 4, 0.0), (1, 4, 1e-5), (1, 16, 1e-5)])
+def test_fused_tile_shapes_agree(precision, rows, tol):
+    """The fused pass on tiles of 32 x 4 or 32 x 16 cells against the default 32 x 8,
+    on a ragged 53 x 37 lattice with electrodes: FP64 bitwise (the per-cell
+    arithmetic does not depend on the tile), FP32 within 1e-5 (each instantiation may
+    fuse different multiply-adds)."""
+    L = _lb()
+    nx, ny = 53, 37
+    p = W.params(nx=nx, ny=ny, bc_y=2, electric=1, precision=precision, V_top=0.02, poisson_fixed_iter=6)
+    phi = W.compound_droplet(nx, ny, 6.0, 12.0, 4.0, xc=25.3, yc=17.6)
+    a = L.Sim(p, phi, noise=W.noise(nx, ny, 1e-7, seed=5))
+    b = L.Sim(p, phi, noise=W.noise(nx, ny, 1e-7, seed=5)).set_tile(rows)
+    a.step(12)
+    b.step(12)
+    for f in FIELDS:
+        assert rel_linf(b.field(f), a.field(f)) <= tol, f
