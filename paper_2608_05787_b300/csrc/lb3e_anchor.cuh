@@ -38,19 +38,181 @@
 
 namespace lb3e {
 
+// ---------------------------------------------------------------- double-float numbers
+// The FP32 builds hold the anchor as an unevaluated sum hi + lo of two FP32 numbers
+// (|lo| <= ulp(hi)/2, about 48 significant bits) and do the refresh's state
+// arithmetic on them with error-free transformations: Knuth's TwoSum and Dekker's
+// FastTwoSum for sums, the FMA-based exact product for products.  That keeps the
+// refresh on the FP32 pipe (FP64 runs at about 1/64 of its rate on this part) at
+// far more precision than the tolerance needs.  The __f*_rn intrinsics keep the
+// compiler from contracting or reordering these steps.
+struct df32 {
+    float hi, lo;
+};
+// a + b exactly as hi + lo (Knuth)
+__device__ __forceinline__ df32 df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// a + b exactly as hi + lo when |a| >= |b| (Dekker)
+__device__ __forceinline__ df32 df_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df32 df_neg(df32 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df32 df_add(df32 a, df32 b) {
+    df32 s = df_two_sum(a.hi, b.hi);
+    const df32 t = df_two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = df_fast_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return df_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df32 df_add_f(df32 a, float b) {
+    df32 s = df_two_sum(a.hi, b);
+    s.lo = __fadd_rn(s.lo, a.lo);
+    return df_fast_two_sum(s.hi, s.lo);
+}
+// products: hi*hi exactly through one FMA, the cross terms added to its error
+__device__ __forceinline__ df32 df_mul(df32 a, df32 b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df32 df_mul_f(df32 a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return df_fast_two_sum(p, e);
+}
+__host__ __device__ inline df32 df_of(double x) {
+    const float hi = (float)x;
+    return {hi, (float)(x - (double)hi)};
+}
+__device__ __forceinline__ double df_value(df32 a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ float df_round(df32 a) { return __fadd_rn(a.hi, a.lo); }
+
+// the anchor's number type: FP64 in the FP64 build, double-float in the FP32 builds
+template <class R> struct AnchorOf { using type = double; };
+template <> struct AnchorOf<float> { using type = df32; };
+template <class A> __device__ __forceinline__ double anchor_value(const A& a);
+template <> __device__ __forceinline__ double anchor_value<double>(const double& a) { return a; }
+template <> __device__ __forceinline__ double anchor_value<df32>(const df32& a) { return df_value(a); }
+
+// the refresh's coefficients as double-float numbers (formed on the host from FP64):
+// 1 - 1/tau_h, 1/tau_h, w_0 - 1, w_1..4, w_5..8, 1/(1 - w_0), and 2 w V at the two
+// electrodes for the two classes of moving directions
+struct AnchorCoef {
+    df32 om, ith, w0m1, w1, w5, c18, wv[2][2];  // wv[top][class 0: |c| = 1, 1: diagonal]
+};
+
 // a and delta at the start of a solve: the equilibrium of the linear electrode
 // profile (or zero) in the anchor, delta = 0
 template <class R>
-__global__ void __launch_bounds__(256) k_anchor_init(DevParams P, double* __restrict__ a, R* __restrict__ d) {
+__global__ void __launch_bounds__(256) k_anchor_init(DevParams P, typename AnchorOf<R>::type* __restrict__ a,
+                                                     R* __restrict__ d) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
     const unsigned N = P.N, c = (unsigned)y * P.nx + x;
     const double ps = P.bc_y == 2 ? P.V_bottom + (P.V_top - P.V_bottom) * (y + 0.5) / P.ny : 0.0;
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
-        a[j * N + c] = (j == 0) ? (wgt<double>(0) - 1.0) * ps : wgt<double>(j) * ps;
+        const double v = (j == 0) ? (wgt<double>(0) - 1.0) * ps : wgt<double>(j) * ps;
+        if constexpr (std::is_same<R, float>::value) a[j * N + c] = df_of(v);
+        else a[j * N + c] = v;
         d[j * N + c] = R(0);
     }
+}
+
+// The refresh of the FP32 builds in double-float arithmetic: fold delta into the
+// anchor, then the collision of Eq. 43 (factored form, as k_anchor_refresh) pushed to
+// the staging planes (double-float), with the charge source and the electrode walls.
+// Kc is the FP32 value of the correction kernels (it scales the first moment only).
+static __global__ void __launch_bounds__(256) k_anchor_refresh_df(DevParams P, df32* __restrict__ a, float* __restrict__ d,
+                                                           const float* __restrict__ eps, const float* __restrict__ q,
+                                                           df32* __restrict__ stage, float* __restrict__ ja,
+                                                           AnchorCoef K) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const unsigned N = P.N, c = (unsigned)y * P.nx + x;
+    df32 h[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        h[j] = df_add_f(a[j * N + c], d[j * N + c]);
+        a[j * N + c] = h[j];
+        d[j * N + c] = 0.f;
+    }
+    df32 sum = h[1], jx = {0.f, 0.f}, jy = {0.f, 0.f};
+#pragma unroll
+    for (int j = 2; j < 9; ++j) sum = df_add(sum, h[j]);
+    const df32 ps = df_mul(sum, K.c18);
+    // J = sum_j c_j h_j (the lattice components are 0 or +-1)
+#pragma unroll
+    for (int j = 1; j < 9; ++j) {
+        if (cx(j)) jx = df_add(jx, cx(j) > 0 ? h[j] : df_neg(h[j]));
+        if (cy(j)) jy = df_add(jy, cy(j) > 0 ? h[j] : df_neg(h[j]));
+    }
+    ja[c] = df_round(jx);
+    ja[N + c] = df_round(jy);
+    const float eh = eps[c] - P.feps_ref;
+    const float Kc = 3.0f * P.fitau_h * eh * rcp(eh + cs2<float>() * P.ftau_h);
+    const df32 A = df_mul(K.ith, ps);
+    const float q8 = 0.125f * q[c];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        df32 v;
+        if (j == 0) {
+            v = df_add(df_mul(K.om, h[0]), df_mul(K.w0m1, A));
+        } else {
+            df32 cj = cx(j) > 0 ? jx : (cx(j) < 0 ? df_neg(jx) : df32{0.f, 0.f});
+            if (cy(j) > 0) cj = df_add(cj, jy);
+            else if (cy(j) < 0) cj = df_add(cj, df_neg(jy));
+            const df32 t = df_add(A, df_mul_f(cj, Kc));
+            v = df_add_f(df_add(df_mul(K.om, h[j]), df_mul(j <= 4 ? K.w1 : K.w5, t)), q8);
+        }
+        const int yt = y + cy(j);
+        if (P.bc_y != 0 && (yt < 0 || yt >= P.ny)) {
+            df32 out = v;
+            if (P.bc_y == 2) out = df_add(df_neg(v), K.wv[yt >= P.ny ? 1 : 0][j <= 4 ? 0 : 1]);
+            stage[opp(j) * N + c] = out;
+        } else {
+            stage[j * N + (unsigned)wrapi(yt, P.ny) * P.nx + wrapi(x + cx(j), P.nx)] = v;
+        }
+    }
+}
+
+// r = stage - a in double-float, rounded to FP32, and the per-block sums of
+// k_anchor_residual
+static __global__ void __launch_bounds__(256) k_anchor_residual_df(DevParams P, const df32* __restrict__ a,
+                                                            const df32* __restrict__ stage, float* __restrict__ r,
+                                                            double* __restrict__ partial) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    if (x < P.nx && y < P.ny) {
+        const unsigned N = P.N, c = (unsigned)y * P.nx + x;
+        float dps = 0.f, ps = 0.f, djx = 0.f, djy = 0.f, jx = 0.f, jy = 0.f;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const df32 aj = a[j * N + c];
+            const float rj = df_round(df_add(stage[j * N + c], df_neg(aj))), ar = df_round(aj);
+            r[j * N + c] = rj;
+            if (j) { dps += rj; ps += ar; }
+            cacc(djx, cx(j), rj);
+            cacc(djy, cy(j), rj);
+            cacc(jx, cx(j), ar);
+            cacc(jy, cy(j), ar);
+        }
+        dps *= 1.8f;
+        ps *= 1.8f;
+        acc[0] = dps * dps;
+        acc[1] = ps * ps;
+        acc[2] = djx * djx + djy * djy;
+        acc[3] = jx * jx + jy * jy;
+    }
+    block_reduce_store_r<4>(acc, partial + 4 * (size_t)(blockIdx.x + gridDim.x * blockIdx.y));
 }
 
 // Fold delta into the anchor (a += delta, delta = 0) and push the FP64 collision
@@ -158,7 +320,7 @@ __global__ void __launch_bounds__(256) k_anchor_residual(DevParams P, const doub
 // (moments of a in FP64, of delta in R, added in FP64); psi_out != nullptr: write
 // psi (FP64) instead of E
 template <class R>
-__global__ void __launch_bounds__(256) k_anchor_fields(DevParams P, const double* __restrict__ a,
+__global__ void __launch_bounds__(256) k_anchor_fields(DevParams P, const typename AnchorOf<R>::type* __restrict__ a,
                                                        const R* __restrict__ d, const R* __restrict__ eps,
                                                        R* __restrict__ E, double* __restrict__ psi_out) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -168,7 +330,7 @@ __global__ void __launch_bounds__(256) k_anchor_fields(DevParams P, const double
     R dps = R(0), djx = R(0), djy = R(0);
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
-        const double aj = a[j * N + c];
+        const double aj = anchor_value(a[j * N + c]);
         const R dj = d[j * N + c];
         if (j) { ps += aj; dps += dj; }
         cacc(jx, cx(j), aj);
@@ -210,10 +372,10 @@ __global__ void __launch_bounds__(256) k_anchor_efield(DevParams P, const R* __r
 
 // population j of h = a + delta as FP64
 template <class R>
-__global__ void k_anchor_pop(double* __restrict__ dst, const double* __restrict__ a, const R* __restrict__ d,
-                             size_t n) {
+__global__ void k_anchor_pop(double* __restrict__ dst, const typename AnchorOf<R>::type* __restrict__ a,
+                             const R* __restrict__ d, size_t n) {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = a[i] + (double)d[i];
+    if (i < n) dst[i] = anchor_value(a[i]) + (double)d[i];
 }
 
 // coarse correction, level-0 input: rhs = sum_{j>0} r_j (the macroscopic residual
@@ -279,13 +441,23 @@ __global__ void __launch_bounds__(256) k_rs_increment(DevParams P, const R* __re
     if (x < P.nx && y < P.ny) {
         const unsigned N = P.N, c = (unsigned)y * P.nx + x;
         R ps = R(0), jx = R(0), jy = R(0);
+        if constexpr (std::is_same<R, float>::value) {  // the moments as the FP32 iteration forms them
+            float v[9];
 #pragma unroll
-        for (int j = 0; j < 9; ++j) {
-            const R v = d[j * N + c];
-            if (j) ps += v;
-            cacc(jx, cx(j), v);
-            cacc(jy, cy(j), v);
-            acc[2] += v * v;
+            for (int j = 0; j < 9; ++j) {
+                v[j] = d[j * N + c];
+                acc[2] += v[j] * v[j];
+            }
+            moments_f32<float>(v, ps, jx, jy);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const R v = d[j * N + c];
+                if (j) ps += v;
+                cacc(jx, cx(j), v);
+                cacc(jy, cy(j), v);
+                acc[2] += v * v;
+            }
         }
         const R s = ps;  // (1 - w_0) psi
         ps = dv(ps, R(1) - wgt<R>(0), R(1.8));

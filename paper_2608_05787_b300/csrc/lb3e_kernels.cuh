@@ -422,6 +422,67 @@ __device__ __forceinline__ R h_collide(int j, R hj, R ps, R gx, R gy, R jx, R jy
     }
 }
 
+// The FP32 build's collision of Eq. 43, one sequence of explicitly rounded
+// operations shared by the per-iteration and blocked kernels, so that the two
+// produce bitwise-equal iterates.  The factored form
+//   h_j* = (1 - 1/tau_h) h_j + w_j (psi/tau_h + Kc c_j.J) + q/8
+// (h_0* without the source and Kc term) is evaluated from S = sum_{j>0} h_j (psi =
+// 1.8 S) as  h_j* = om h_j + (cw_j S + q/8) + (w_j Kc) c_j.J, with the direction
+// sums paired so that J costs 8 operations and each population 2.
+template <class V> struct F32Ops;
+template <> struct F32Ops<float> {
+    static __device__ __forceinline__ float splat(float a) { return a; }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float neg(float a) { return -a; }
+};
+// launch-wide constants of the FP32 collision: 1 - 1/tau_h and the equilibrium
+// weights times 1.8/tau_h (w_0 - 1, w_1, w_5)
+struct PoissonF32 {
+    float om, cw0, cw1, cw5;
+};
+__device__ __forceinline__ PoissonF32 poisson_f32(const DevParams& P) {
+    const float a = P.fitau_h * 1.8f;
+    return {1.0f - P.fitau_h, (wgt<float>(0) - 1.0f) * a, wgt<float>(1) * a, wgt<float>(5) * a};
+}
+// w_1 Kc = w_1 3 eps_hat / (tau_h den) of a cell (w_5 Kc = w_1 Kc / 4 exactly)
+__device__ __forceinline__ float poisson_k1(const DevParams& P, float eps_c) {
+    const float eh = eps_c - P.feps_ref;
+    return wgt<float>(1) * (3.0f * P.fitau_h * eh * rcp(eh + cs2<float>() * P.ftau_h));
+}
+// S = sum_{j>0} h_j and J = sum_j c_j h_j
+template <class V>
+__device__ __forceinline__ void moments_f32(const V (&h)[9], V& S, V& jx, V& jy) {
+    using O = F32Ops<V>;
+    const V a = O::sub(h[1], h[3]), b = O::sub(h[5], h[7]), c = O::sub(h[8], h[6]), d = O::sub(h[2], h[4]);
+    S = O::add(O::add(O::add(h[1], h[3]), O::add(h[2], h[4])), O::add(O::add(h[5], h[7]), O::add(h[6], h[8])));
+    jx = O::add(O::add(a, b), c);
+    jy = O::sub(O::add(d, b), c);
+}
+// post-collision values v[0..8] from h, S, J, w_1 Kc and (with Q) q/8
+template <class V, bool Q>
+__device__ __forceinline__ void collide_f32(const V (&h)[9], V S, V jx, V jy, V K1, V q8, const PoissonF32& C,
+                                            V (&v)[9]) {
+    using O = F32Ops<V>;
+    const V om = O::splat(C.om);
+    const V W0 = O::mul(O::splat(C.cw0), S);
+    const V W1 = Q ? O::fma(O::splat(C.cw1), S, q8) : O::mul(O::splat(C.cw1), S);
+    const V W5 = Q ? O::fma(O::splat(C.cw5), S, q8) : O::mul(O::splat(C.cw5), S);
+    const V K5 = O::mul(K1, O::splat(0.25f));
+    const V sp = O::add(jx, jy), sm = O::sub(jx, jy);  // c.J of directions 5 (+) and 8 (-)
+    v[0] = O::fma(om, h[0], W0);
+    v[1] = O::fma(om, h[1], O::fma(K1, jx, W1));
+    v[3] = O::fma(om, h[3], O::fma(O::neg(K1), jx, W1));
+    v[2] = O::fma(om, h[2], O::fma(K1, jy, W1));
+    v[4] = O::fma(om, h[4], O::fma(O::neg(K1), jy, W1));
+    v[5] = O::fma(om, h[5], O::fma(K5, sp, W5));
+    v[7] = O::fma(om, h[7], O::fma(O::neg(K5), sp, W5));
+    v[8] = O::fma(om, h[8], O::fma(K5, sm, W5));
+    v[6] = O::fma(om, h[6], O::fma(O::neg(K5), sm, W5));
+}
+
 // One pseudo-time collide + push-stream of h.  On iterations before a check it
 // saves psi and J = sum c_j h_j; on a check it accumulates (FP64, per block)
 // |d psi|^2, |psi|^2, |d J|^2, |J|^2.
@@ -438,7 +499,38 @@ __device__ __forceinline__ void body_poisson(const DevParams P, const R* __restr
     const bool in = x < P.nx && y < P.ny;
     const unsigned N = P.N, c = in ? (unsigned)y * P.nx + x : 0;
     R acc[4] = {R(0), R(0), R(0), R(0)};
-    if (in) {
+    if constexpr (std::is_same<R, float>::value) {
+        if (in) {
+            float hj[9], S, jx, jy, v[9];
+#pragma unroll
+            for (int j = 0; j < 9; ++j) hj[j] = hin[j * N + c];
+            moments_f32<float>(hj, S, jx, jy);
+            const float ps = S * 1.8f;
+            if (check) {
+                const float d = ps - prev[c], ex = jx - prev[N + c], ey = jy - prev[2 * N + c];
+                acc[0] = d * d;
+                acc[1] = ps * ps;
+                acc[2] = ex * ex + ey * ey;
+                acc[3] = jx * jx + jy * jy;
+            }
+            if (save_prev) { prev[c] = ps; prev[N + c] = jx; prev[2 * N + c] = jy; }
+            const PoissonF32 C = poisson_f32(P);
+            collide_f32<float, !RS>(hj, S, jx, jy, poisson_k1(P, eps[c]), RS ? 0.f : 0.125f * q[c], C, v);
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const int yt = y + cy(j);
+                if (P.bc_y != 0 && (yt < 0 || yt >= P.ny)) {
+                    float out = v[j];
+                    if (P.bc_y == 2) out = RS ? -v[j] : __fmaf_rn(2.0f * wgt<float>(j), yt >= P.ny ? P.fVt : P.fVb, -v[j]);
+                    const unsigned to = opp(j) * N + c;
+                    hout[to] = RS ? __fadd_rn(out, rres[to]) : out;
+                } else {
+                    const unsigned to = j * N + (unsigned)wrapi(yt, P.ny) * P.nx + wrapi(x + cx(j), P.nx);
+                    hout[to] = RS ? __fadd_rn(v[j], rres[to]) : v[j];
+                }
+            }
+        }
+    } else if (in) {
         R hj[9];
 #pragma unroll
         for (int j = 0; j < 9; ++j) hj[j] = hin[j * N + c];
@@ -520,27 +612,188 @@ __global__ void __launch_bounds__(256) k_poisson_rs(DevParams P, const R* __rest
 // before the first collision, the residual state (save_prev) before the last one.
 constexpr int PB_TX = 32, PB_TY = 16, PB_HALO = 8;
 // CPT cells per thread: 3 for the plain kernel, 2 on the correction to an FP64
-// anchor (RS), whose anchor increments then fit in registers (9 per cell) at the
-// same number of resident threads
-template <int H, bool RS = false>
+// anchor (RS), whose anchor increments then fit in registers (9 per cell) at about
+// the same number of resident threads.
+template <int H, int CPT_>
 struct PBGeom {
     static constexpr int RX = PB_TX + 2 * H, RY = PB_TY + 2 * H, CELLS = RX * RY;
-    static constexpr int CPT = RS ? 2 : 3, THREADS = CELLS / CPT;
+    static constexpr int CPT = CPT_, THREADS = CELLS / CPT;
     static_assert(CELLS % CPT == 0, "region cells split evenly over the threads");
 };
+template <class R, bool RS = false>
+__host__ __device__ constexpr int pb_cpt() { return RS ? 2 : 3; }
+// FP32 post-collision plane sets (two: double-buffered, one barrier an iteration)
+template <class R, bool RS = false>
+__host__ __device__ constexpr int pb_sets() { return RS ? 2 : 1; }
+template <class R, int H, bool RS = false>
+__host__ __device__ constexpr int pb_threads() { return PBGeom<H, pb_cpt<R, RS>()>::THREADS; }
 // blocks per SM the register budget is sized for (64 registers a thread in FP32)
 template <class R, int H, bool RS = false>
 __host__ __device__ constexpr int pb_min_blocks() {
     if constexpr (RS) return std::is_same<R, float>::value ? (H == 8 ? 1 : 2) : 1;
     return std::is_same<R, float>::value ? (H == 8 ? 2 : 3) : 1;
 }
-// shared planes: 9 post-collision planes and eps (Kc), then q (q/8); on the
-// correction to an FP64 anchor (RS) no charge (the anchor's increments sit in
-// registers)
+// shared planes.  FP32: one or two sets of 8 post-collision planes (directions
+// 1-8), w_1 Kc and, unless RS, q/8.  FP64: 9 planes, eps and q
+// (RS: no charge; the anchor's increments sit in registers).
 template <class R, int H, bool RS = false>
-constexpr size_t pb_smem_bytes() { return (size_t)(RS ? 10 : 11) * PBGeom<H, RS>::CELLS * sizeof(R); }
+constexpr size_t pb_smem_bytes() {
+    constexpr int planes = std::is_same<R, float>::value ? 8 * pb_sets<R, RS>() + (RS ? 1 : 2) : (RS ? 10 : 11);
+    return (size_t)planes * PBGeom<H, pb_cpt<R, RS>()>::CELLS * sizeof(R);
+}
 // halo depth of the region that serves a chunk of K iterations
 __host__ __device__ constexpr int pb_halo_for(int K) { return K <= 2 ? 2 : (K <= 4 ? 4 : 8); }
+
+// The FP32 blocked kernel.  Thread i owns the region cells i + m NT (m < CPT, NT =
+// the region over CPT), so a warp's cells are consecutive in a region row and the
+// thread's cells are independent instruction streams.  The collision is collide_f32, the
+// per-iteration kernel's sequence of operations, so the two kernels produce
+// bitwise-equal iterates.  Streaming moves only directions 1-8 through shared
+// memory (the rest population stays in registers).  On the correction to the
+// anchor (2 blocks an SM) two sets of planes alternate between iterations: an
+// iteration's pulls read the set its collisions wrote, the next collisions write
+// the other, so one barrier an iteration suffices.  The plain kernel (3 blocks an
+// SM) keeps one set and two barriers: a second set would leave the SM's unified
+// L1 too little room for the tile loads (measured slower).
+// A cell collides while it is inside the dependency cone (d <= K - t) and pulls
+// while its pull is still needed (d <= K - 1 - t); non-fluid rows (beyond a wall)
+// neither collide nor store: their slots are the ghost slots the wall rows write.
+template <int H, int KC, bool RS>
+__device__ __forceinline__ void body_poisson_tb_f32(const DevParams P, const float* __restrict__ hin,
+                                                    float* __restrict__ hout, const float* __restrict__ eps,
+                                                    const float* __restrict__ q, float* __restrict__ prev,
+                                                    double* __restrict__ partial, int Kdyn, int save_prev,
+                                                    int check, int bx, int by, int gdx,
+                                                    const float* __restrict__ rres) {
+    using G = PBGeom<H, pb_cpt<float, RS>()>;
+    constexpr int RX = G::RX, CELLS = G::CELLS, CPT = G::CPT, NT = G::THREADS, SET = 8 * CELLS;
+    constexpr int SETS = pb_sets<float, RS>();
+    extern __shared__ __align__(16) unsigned char pb_raw[];
+    float* hs = reinterpret_cast<float*>(pb_raw);  // [SETS][directions 1..8][CELLS]
+    float* sk = hs + SETS * SET;                   // [CELLS] w_1 Kc
+    float* sq = sk + CELLS;                        // [CELLS] q/8 (not RS)
+    const int nx = P.nx, ny = P.ny;
+    const unsigned N = P.N;
+    const int x0 = bx * PB_TX - H, y0 = by * PB_TY - H;
+    const int tid = threadIdx.x;
+    const bool walls = P.bc_y != 0;
+
+    // per owned cell k = tid + m NT, packed in one word: bits 0-7 the distance d
+    // outside the tile (0 inside; 255: not a fluid cell), bit 8 bottom wall row, bit
+    // 9 top wall row, bit 10 a tile cell inside the grid
+    float h[CPT][9];
+    float rr[RS ? CPT : 1][9];
+    int meta[CPT];
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+        const int k = tid + m * NT;
+        const int ly = k / RX, lx = k % RX;
+        const int gy = y0 + ly, gx = x0 + lx;
+        const bool real = !walls || (gy >= 0 && gy < ny);
+        const int dx = lx < H ? H - lx : (lx >= H + PB_TX ? lx - (H + PB_TX - 1) : 0);
+        const int dy = ly < H ? H - ly : (ly >= H + PB_TY ? ly - (H + PB_TY - 1) : 0);
+        const int d = dx > dy ? dx : dy;
+        meta[m] = (real ? d : 255) | (walls && gy == 0 ? 256 : 0) | (walls && gy == ny - 1 ? 512 : 0) |
+                  (real && d == 0 && gx < nx && gy < ny ? 1024 : 0);
+        if (real) {
+            const unsigned c = (unsigned)wrapi(gy, ny) * nx + wrapi(gx, nx);
+#pragma unroll
+            for (int j = 0; j < 9; ++j) h[m][j] = hin[j * N + c];
+            sk[k] = poisson_k1(P, eps[c]);
+            if constexpr (RS) {
+#pragma unroll
+                for (int j = 0; j < 9; ++j) rr[m][j] = rres[j * N + c];
+            } else {
+                sq[k] = 0.125f * q[c];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) h[m][j] = 0.f;
+            if constexpr (RS) {
+#pragma unroll
+                for (int j = 0; j < 9; ++j) rr[m][j] = 0.f;
+            }
+            sk[k] = 0.f;
+            if constexpr (!RS) sq[k] = 0.f;
+        }
+    }
+    auto cell = [&](int m) {
+        const int k = tid + m * NT;
+        return (unsigned)(y0 + k / RX) * nx + (unsigned)(x0 + k % RX);
+    };
+    const PoissonF32 C = poisson_f32(P);
+    const bool electrodes = P.bc_y == 2;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int K = KC > 0 ? KC : Kdyn;
+    constexpr int kUnroll = KC > 0 ? KC : 1;
+    __syncthreads();  // sk, sq
+#pragma unroll kUnroll
+    for (int t = 0; t < K; ++t) {
+        float* const hp = hs + (SETS == 2 ? (t & 1) * SET : 0) - CELLS;  // hp + j * CELLS: direction j
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) {
+            if ((meta[m] & 255) > K - t) continue;  // no longer feeds the tile (or not a fluid cell)
+            const int k = tid + m * NT;
+            float S, jx, jy, v[9];
+            moments_f32<float>(h[m], S, jx, jy);
+            if ((meta[m] & 1024) && ((check && t == 0) || (save_prev && t == K - 1))) {
+                const unsigned c = cell(m);
+                const float ps = S * 1.8f;
+                if (check && t == 0) {
+                    const float d = ps - prev[c], ex = jx - prev[N + c], ey = jy - prev[2 * N + c];
+                    acc[0] += d * d;
+                    acc[1] += ps * ps;
+                    acc[2] += ex * ex + ey * ey;
+                    acc[3] += jx * jx + jy * jy;
+                }
+                if (save_prev && t == K - 1) { prev[c] = ps; prev[N + c] = jx; prev[2 * N + c] = jy; }
+            }
+            collide_f32<float, !RS>(h[m], S, jx, jy, sk[k], RS ? 0.f : sq[k], C, v);
+            h[m][0] = RS ? __fadd_rn(v[0], rr[m][0]) : v[0];  // the rest population stays
+#pragma unroll
+            for (int j = 1; j < 9; ++j) hp[j * CELLS + k] = v[j];
+            // a wall cell whose own pull is still needed (so it is not on the region
+            // border, and its ghost slots lie inside the region): the populations
+            // leaving toward the wall come back in the opposite direction, through
+            // the ghost cell they would be pulled from (anti-bounce-back to the
+            // electrode potential, or plain bounce-back)
+            if ((meta[m] & 768) && (meta[m] & 255) <= K - 1 - t) {
+                const bool top = meta[m] & 512;
+                const float V = top ? P.fVt : P.fVb;
+#pragma unroll
+                for (int j = 1; j < 9; ++j) {
+                    if (!((cy(j) < 0 && !top) || (cy(j) > 0 && top))) continue;
+                    const int jo = opp(j);  // arriving direction
+                    hp[jo * CELLS + k - cy(jo) * RX - cx(jo)] =
+                        electrodes ? (RS ? -v[j] : __fmaf_rn(2.0f * wgt<float>(j), V, -v[j])) : v[j];
+                }
+            }
+        }
+        __syncthreads();
+        // pull streaming inside the region (cells whose sources were all updated):
+        // cell k takes direction j from k - cy RX - cx
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) {
+            if ((meta[m] & 255) > K - 1 - t) continue;
+            const int k = tid + m * NT;
+#pragma unroll
+            for (int j = 1; j < 9; ++j) {
+                const float g = hp[j * CELLS + k - cy(j) * RX - cx(j)];
+                h[m][j] = RS ? __fadd_rn(g, rr[m][j]) : g;
+            }
+        }
+        if (SETS == 1 && t + 1 < K) __syncthreads();  // one set: the pulls end before the next stores
+    }
+    // write the tile
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+        if (!(meta[m] & 1024)) continue;
+        const unsigned c = cell(m);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) hout[j * N + c] = h[m][j];
+    }
+    if (check) block_reduce_store_r<4>(acc, partial + 4 * (size_t)(bx + gdx * by));
+}
 
 template <class R, int H, int KC = 0, bool RS = false>
 __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __restrict__ hin,
@@ -548,7 +801,12 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
                                                 const R* __restrict__ q, R* __restrict__ prev,
                                                 double* __restrict__ partial, int Kdyn, int save_prev, int check,
                                                 int bx, int by, int gdx, const R* __restrict__ rres = nullptr) {
-    using G = PBGeom<H, RS>;
+    if constexpr (std::is_same<R, float>::value) {
+        body_poisson_tb_f32<H, KC, RS>(P, hin, hout, eps, q, prev, partial, Kdyn, save_prev, check, bx, by, gdx,
+                                       rres);
+        return;
+    }
+    using G = PBGeom<H, pb_cpt<R, RS>()>;
     constexpr int RX = G::RX, CELLS = G::CELLS, CPT = G::CPT, NT = G::THREADS;
     extern __shared__ __align__(16) unsigned char pb_raw[];
     R* hs = reinterpret_cast<R*>(pb_raw);  // [9][CELLS] post-collision values
@@ -706,7 +964,7 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
     if (check) block_reduce_store_r<4>(acc, partial + 4 * (size_t)(bx + gdx * by));
 }
 template <class R, int H, int KC = 0>
-__global__ void __launch_bounds__(PBGeom<H>::THREADS, pb_min_blocks<R, H>())
+__global__ void __launch_bounds__(pb_threads<R, H>(), pb_min_blocks<R, H>())
     k_poisson_tb(DevParams P, const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ eps,
                  const R* __restrict__ q, R* __restrict__ prev, double* __restrict__ partial, int K, int save_prev,
                  int check) {
@@ -716,7 +974,7 @@ __global__ void __launch_bounds__(PBGeom<H>::THREADS, pb_min_blocks<R, H>())
 // K iterations on the correction to an FP64 anchor (no residual sums; save_prev:
 // psi and J before the last collision into prev)
 template <class R, int H, int KC = 0>
-__global__ void __launch_bounds__(PBGeom<H, true>::THREADS, pb_min_blocks<R, H, true>())
+__global__ void __launch_bounds__(pb_threads<R, H, true>(), pb_min_blocks<R, H, true>())
     k_poisson_tb_rs(DevParams P, const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ eps,
                     const R* __restrict__ rres, R* __restrict__ prev, int K, int save_prev) {
     body_poisson_tb<R, H, KC, true>(P, hin, hout, eps, nullptr, prev, nullptr, K, save_prev, 0, blockIdx.x,
@@ -1541,7 +1799,7 @@ __global__ void __launch_bounds__(256) kb_poisson(const InstState<R, S>* __restr
 }
 // K pseudo-iterations per launch over the 32 x 16 tiles of all instances
 template <class R, class S, int H, int KC = 0>
-__global__ void __launch_bounds__(PBGeom<H>::THREADS, pb_min_blocks<R, H>())
+__global__ void __launch_bounds__(pb_threads<R, H>(), pb_min_blocks<R, H>())
     kb_poisson_tb(const InstState<R, S>* __restrict__ st, const int4* __restrict__ tiles, int hcur, int K) {
     const int4 t = tiles[blockIdx.x];
     const InstState<R, S>& e = st[t.x];

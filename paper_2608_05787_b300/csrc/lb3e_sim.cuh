@@ -116,9 +116,13 @@ class Sim final : public SimBase {
         grid2_ = dim3((prm.nx + TX - 1) / TX, (prm.ny + TY - 1) / TY);
         nblk_ = (int)(grid2_.x * grid2_.y);
         if (prm.electric && prm.potential_solver >= 2) {
-            anchor_ = reinterpret_cast<double*>(b + L_.anchor);
+            anchor_ = reinterpret_cast<AT*>(b + L_.anchor);
             rres_ = reinterpret_cast<R*>(b + L_.rres);
             ja_ = reinterpret_cast<R*>(b + L_.ja);
+            const double ith = 1.0 / dp_.tau_h, w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w5 = 1.0 / 36.0;
+            acoef_ = {df_of(1.0 - ith), df_of(ith), df_of(w0 - 1.0), df_of(w1), df_of(w5), df_of(1.0 / (1.0 - w0)),
+                      {{df_of(2 * w1 * dp_.V_bottom), df_of(2 * w5 * dp_.V_bottom)},
+                       {df_of(2 * w1 * dp_.V_top), df_of(2 * w5 * dp_.V_top)}}};
         }
         if ((prm.potential_solver == 1 || prm.potential_solver == 2) && prm.electric) {
             const int nl = mg_levels(prm.nx, prm.ny);
@@ -556,7 +560,7 @@ class Sim final : public SimBase {
   private:
     size_t fields_bytes() const { return L_.psi_prev + align256(3 * N_ * sizeof(R)) - L_.phi; }
     size_t ion_bytes() const { return p_.ions ? 24 * N_ * sizeof(R) : 0; }
-    size_t anchor_bytes() const { return anchor_ ? 9 * N_ * sizeof(double) : 0; }
+    size_t anchor_bytes() const { return anchor_ ? 9 * N_ * sizeof(AT) : 0; }
     static unsigned blocks1(size_t n) { return (unsigned)((n + 255) / 256); }
     int launched() {
         ++launches;
@@ -890,11 +894,21 @@ class Sim final : public SimBase {
             return LB3E_ERR_PARAM;
         } else {
             timer.begin(stream_, KC_ANCHOR);
-            k_anchor_refresh<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.h[hcur_], d_.eps, d_.q,
-                                                                      d_.stage, ja_, 1.0 / dp_.tau_h, dp_.tau_h / 3.0);
-            TRY(launched());
-            timer.begin(stream_, KC_ANCHOR);
-            k_anchor_residual<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.stage, rres_, d_.partial);
+            if constexpr (std::is_same<R, float>::value) {  // double-float anchor
+                df32* st = reinterpret_cast<df32*>(d_.stage);
+                k_anchor_refresh_df<<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.h[hcur_], d_.eps, d_.q, st,
+                                                                          ja_, acoef_);
+                TRY(launched());
+                timer.begin(stream_, KC_ANCHOR);
+                k_anchor_residual_df<<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, st, rres_, d_.partial);
+            } else {
+                k_anchor_refresh<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.h[hcur_], d_.eps, d_.q,
+                                                                          d_.stage, ja_, 1.0 / dp_.tau_h,
+                                                                          dp_.tau_h / 3.0);
+                TRY(launched());
+                timer.begin(stream_, KC_ANCHOR);
+                k_anchor_residual<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.stage, rres_, d_.partial);
+            }
             TRY(launched());
             if (!residual) return LB3E_OK;
             TRY(reduce4(nblk_));
@@ -994,16 +1008,16 @@ class Sim final : public SimBase {
                     k_poisson_rs<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps,
                                                                           rres_, d_.psi_prev, sv);
                 else if (pb_halo_for(c) == 2)
-                    k_poisson_tb_rs<R, 2><<<pgrid, PBGeom<2, true>::THREADS, pb_smem_bytes<R, 2, true>(), stream_>>>(
+                    k_poisson_tb_rs<R, 2><<<pgrid, pb_threads<R, 2, true>(), pb_smem_bytes<R, 2, true>(), stream_>>>(
                         dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
                 else if (c == 4)
-                    k_poisson_tb_rs<R, 4, 4><<<pgrid, PBGeom<4, true>::THREADS, pb_smem_bytes<R, 4, true>(), stream_>>>(
+                    k_poisson_tb_rs<R, 4, 4><<<pgrid, pb_threads<R, 4, true>(), pb_smem_bytes<R, 4, true>(), stream_>>>(
                         dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
                 else if (pb_halo_for(c) == 4)
-                    k_poisson_tb_rs<R, 4><<<pgrid, PBGeom<4, true>::THREADS, pb_smem_bytes<R, 4, true>(), stream_>>>(
+                    k_poisson_tb_rs<R, 4><<<pgrid, pb_threads<R, 4, true>(), pb_smem_bytes<R, 4, true>(), stream_>>>(
                         dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
                 else if constexpr (pb_smem_bytes<R, 8, true>() <= 227 * 1024)
-                    k_poisson_tb_rs<R, 8><<<pgrid, PBGeom<8, true>::THREADS, pb_smem_bytes<R, 8, true>(), stream_>>>(
+                    k_poisson_tb_rs<R, 8><<<pgrid, pb_threads<R, 8, true>(), pb_smem_bytes<R, 8, true>(), stream_>>>(
                         dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
                 TRY(launched());
                 poisson_iters_run_ += c;
@@ -1112,16 +1126,16 @@ class Sim final : public SimBase {
     void pb_launch(dim3 pgrid, int c, int save, int check) {
         if constexpr (!is_dual<R>::value) {
             if (pb_halo_for(c) == 2)
-                k_poisson_tb<R, 2><<<pgrid, PBGeom<2>::THREADS, pb_smem_bytes<R, 2>(), stream_>>>(
+                k_poisson_tb<R, 2><<<pgrid, pb_threads<R, 2>(), pb_smem_bytes<R, 2>(), stream_>>>(
                     dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q, d_.psi_prev, d_.partial, c, save, check);
             else if (c == 4)
-                k_poisson_tb<R, 4, 4><<<pgrid, PBGeom<4>::THREADS, pb_smem_bytes<R, 4>(), stream_>>>(
+                k_poisson_tb<R, 4, 4><<<pgrid, pb_threads<R, 4>(), pb_smem_bytes<R, 4>(), stream_>>>(
                     dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q, d_.psi_prev, d_.partial, c, save, check);
             else if (pb_halo_for(c) == 4)
-                k_poisson_tb<R, 4><<<pgrid, PBGeom<4>::THREADS, pb_smem_bytes<R, 4>(), stream_>>>(
+                k_poisson_tb<R, 4><<<pgrid, pb_threads<R, 4>(), pb_smem_bytes<R, 4>(), stream_>>>(
                     dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q, d_.psi_prev, d_.partial, c, save, check);
             else
-                k_poisson_tb<R, 8><<<pgrid, PBGeom<8>::THREADS, pb_smem_bytes<R, 8>(), stream_>>>(
+                k_poisson_tb<R, 8><<<pgrid, pb_threads<R, 8>(), pb_smem_bytes<R, 8>(), stream_>>>(
                     dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q, d_.psi_prev, d_.partial, c, save, check);
         }
     }
@@ -1231,7 +1245,11 @@ class Sim final : public SimBase {
     std::vector<MGLevelF> mgf_;
     cudaGraphExec_t vgraph_ = nullptr;  // the captured V-cycle (multigrid solvers, created streams)
     int64_t vgraph_nodes_ = 0;
-    double* anchor_ = nullptr;  // FP64 anchor of the potential populations (solvers 2, 3)
+    // the anchor of the potential populations (solvers 2, 3): FP64 in the FP64 build,
+    // double-float in the FP32 builds, with the refresh's coefficients in that form
+    using AT = typename AnchorOf<R>::type;
+    AT* anchor_ = nullptr;
+    AnchorCoef acoef_{};
     R* rres_ = nullptr;         // the anchor's increment over one pseudo-iteration
     R* ja_ = nullptr;           // the anchor's flux J = sum_j c_j a_j (2 planes), for E
     R* ion_[2] = {nullptr, nullptr};  // Nernst-Planck populations (ions = 1)
@@ -1465,16 +1483,16 @@ class Batch final : public BatchBase {
             for (int k = 0; k < iters_; k += chunk_, h ^= 1) {
                 const int c = iters_ - k < chunk_ ? iters_ - k : chunk_;
                 if (pb_halo_for(c) == 2)
-                    kb_poisson_tb<R, S, 2><<<nptiles_, PBGeom<2>::THREADS, pb_smem_bytes<R, 2>(), stream_>>>(
+                    kb_poisson_tb<R, S, 2><<<nptiles_, pb_threads<R, 2>(), pb_smem_bytes<R, 2>(), stream_>>>(
                         table_, ptiles_, h, c);
                 else if (c == 4)
-                    kb_poisson_tb<R, S, 4, 4><<<nptiles_, PBGeom<4>::THREADS, pb_smem_bytes<R, 4>(), stream_>>>(
+                    kb_poisson_tb<R, S, 4, 4><<<nptiles_, pb_threads<R, 4>(), pb_smem_bytes<R, 4>(), stream_>>>(
                         table_, ptiles_, h, c);
                 else if (pb_halo_for(c) == 4)
-                    kb_poisson_tb<R, S, 4><<<nptiles_, PBGeom<4>::THREADS, pb_smem_bytes<R, 4>(), stream_>>>(
+                    kb_poisson_tb<R, S, 4><<<nptiles_, pb_threads<R, 4>(), pb_smem_bytes<R, 4>(), stream_>>>(
                         table_, ptiles_, h, c);
                 else
-                    kb_poisson_tb<R, S, 8><<<nptiles_, PBGeom<8>::THREADS, pb_smem_bytes<R, 8>(), stream_>>>(
+                    kb_poisson_tb<R, S, 8><<<nptiles_, pb_threads<R, 8>(), pb_smem_bytes<R, 8>(), stream_>>>(
                         table_, ptiles_, h, c);
             }
         }
