@@ -963,6 +963,24 @@ __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __re
     }
     if (check) block_reduce_store_r<4>(acc, partial + 4 * (size_t)(bx + gdx * by));
 }
+// Asynchronous global->shared copies (cp.async) of 4, 8 or 16 bytes
+template <class T>
+__device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async of 4 or 8 bytes");
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+template <class T>
+__device__ __forceinline__ void cp_async16(T* smem, const T* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <class R, int H, int KC = 0>
 __global__ void __launch_bounds__(pb_threads<R, H>(), pb_min_blocks<R, H>())
     k_poisson_tb(DevParams P, const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ eps,
@@ -1087,10 +1105,10 @@ __device__ __forceinline__ R chem_pot(const DevParams& P, int i, R ph, R lap, R 
 // 45 populations.  write_diag stores u, p, mu for field output.
 constexpr int TX = 32, TY = 8;
 
-// Asynchronous global->shared copies (cp.async): a thread's populations, d/dt
-// state and charge are requested at kernel entry and stream in while the phi/E
-// tiles load and mu is evaluated, so many loads are in flight per warp without
-// holding registers.  Used when the storage type is float or double.
+// The fused pass stages through cp.async: a thread's populations, d/dt state and
+// charge are requested at kernel entry and stream in while the phi/E tiles load
+// and mu is evaluated, so many loads are in flight per warp without holding
+// registers.
 template <class S>
 __host__ __device__ constexpr bool fused_prefetch() {
     return std::is_same<S, float>::value || std::is_same<S, double>::value || std::is_same<S, __half>::value ||
@@ -1102,22 +1120,6 @@ template <class R, class S, int BY = 8>
 __host__ __device__ constexpr size_t fused_dyn_smem() {
     return fused_prefetch<S>() ? (size_t)45 * TX * BY * sizeof(S) + (size_t)9 * TX * BY * sizeof(R) : 0;
 }
-template <class T>
-__device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
-    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async of 4 or 8 bytes");
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    if constexpr (sizeof(T) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-template <class T>
-__device__ __forceinline__ void cp_async16(T* smem, const T* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 template <class R, class S, int BY = 8>
 __device__ __forceinline__ void body_fused(const DevParams P, const S* __restrict__ pin, S* __restrict__ pout,

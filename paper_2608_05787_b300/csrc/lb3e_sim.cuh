@@ -665,18 +665,22 @@ class Sim final : public SimBase {
 
     // One FP32 V-cycle on level 0's A e = rhs (rhs and e = 0 set by the caller):
     // 2 red-black pre- and post-sweeps per level, residual restriction by sums of the
-    // four children, bilinear prolongation, 50 sweeps on the coarsest level.  About
-    // 10 launches a level, most of them small: on a created stream the sequence is
-    // captured once as a CUDA graph and replayed (the level pointers are fixed for
-    // the simulation's lifetime), timed as one interval of class kc.
-    int vcycle(int kc) {
-        if (stream_ == nullptr) return vcycle_launches(kc, true);  // the legacy stream cannot be captured
+    // four children, bilinear prolongation, 50 sweeps on the coarsest level.  With
+    // first > 0 the cycle starts on level 1 from the restricted level-0 rhs and ends
+    // with the prolongation of its solution to level 0: no level-0 sweeps (the
+    // coarse correction of the LB solve, whose own iterations smooth the fine
+    // level).  About 10 launches a level, most of them small: on a created stream
+    // the sequence is captured once as a CUDA graph and replayed (the level pointers
+    // are fixed for the simulation's lifetime; a simulation uses one first level),
+    // timed as one interval of class kc.
+    int vcycle(int kc, int first = 0) {
+        if (stream_ == nullptr) return vcycle_launches(kc, true, first);  // the legacy stream cannot be captured
         if (!vgraph_) {
             cudaGraph_t graph = nullptr;
             if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
                 return LB3E_ERR_CUDA;
             const int64_t l0 = launches;
-            const int rc = vcycle_launches(kc, false);
+            const int rc = vcycle_launches(kc, false, first);
             vgraph_nodes_ = launches - l0;
             launches = l0;
             if (cudaStreamEndCapture(stream_, &graph) != cudaSuccess || rc != LB3E_OK) {
@@ -696,8 +700,9 @@ class Sim final : public SimBase {
         launches += vgraph_nodes_;
         return cudaGetLastError() == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
     }
-    int vcycle_launches(int kc, bool timed) {
+    int vcycle_launches(int kc, bool timed, int first = 0) {
         const int nl = (int)mgf_.size();
+        if (first >= nl) first = 0;
         const dim3 blk(TX, TY);
         auto begin = [&]() { if (timed) timer.begin(stream_, kc); };
         auto done = [&]() -> int {
@@ -714,7 +719,15 @@ class Sim final : public SimBase {
                 }
             return LB3E_OK;
         };
-        for (int l = 0; l + 1 < nl; ++l) {
+        if (first > 0) {  // level 0's residual is its rhs (e = 0): restricted to level 1
+            first = 1;
+            MGLevelF f0 = mgf_[0];
+            f0.res = f0.rhs;
+            begin();
+            k_mg_restrict<float><<<mg_grid(1), blk, 0, stream_>>>(f0, mgf_[1]);
+            TRY(done());
+        }
+        for (int l = first; l + 1 < nl; ++l) {
             TRY(smooth(l, 2));
             begin();
             k_mg_residual<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], nullptr);
@@ -730,7 +743,7 @@ class Sim final : public SimBase {
             begin();
             k_mg_prolong<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], mgf_[l + 1]);
             TRY(done());
-            TRY(smooth(l, 2));
+            if (l >= first) TRY(smooth(l, 2));
         }
         return LB3E_OK;
     }
@@ -980,7 +993,7 @@ class Sim final : public SimBase {
                 k_lbmg_rhs<R><<<grid2_, blk, 0, stream_>>>(dp_, rres_, mgf_[0]);
                 TRY(launched());
             }
-            TRY(vcycle(KC_COARSE));
+            TRY(vcycle(KC_COARSE, lbmg_first_));
             timer.begin(stream_, KC_COARSE);
             k_lbmg_correct<R><<<grid2_, blk, 0, stream_>>>(dp_, mgf_[0], d_.eps, d_.h[hcur_], after_refresh ? 0 : 1);
             TRY(launched());
@@ -1122,8 +1135,9 @@ class Sim final : public SimBase {
         }
         return LB3E_OK;
     }
-    // one blocked launch of c iterations, on the region sized for c
-    void pb_launch(dim3 pgrid, int c, int save, int check) {
+    // one blocked launch of c iterations, on the region sized for c; returns the
+    // number of blocks (residual partial sums) it launched
+    int pb_launch(dim3 pgrid, int c, int save, int check) {
         if constexpr (!is_dual<R>::value) {
             if (pb_halo_for(c) == 2)
                 k_poisson_tb<R, 2><<<pgrid, pb_threads<R, 2>(), pb_smem_bytes<R, 2>(), stream_>>>(
@@ -1138,6 +1152,7 @@ class Sim final : public SimBase {
                 k_poisson_tb<R, 8><<<pgrid, pb_threads<R, 8>(), pb_smem_bytes<R, 8>(), stream_>>>(
                     dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q, d_.psi_prev, d_.partial, c, save, check);
         }
+        return (int)(pgrid.x * pgrid.y);
     }
 
   public:
@@ -1165,7 +1180,7 @@ class Sim final : public SimBase {
         last_iters_ = n;
         TRY(pb_prepare());
         const dim3 pgrid((p_.nx + PB_TX - 1) / PB_TX, (p_.ny + PB_TY - 1) / PB_TY);
-        const int pblk = (int)(pgrid.x * pgrid.y);
+        int pblk = (int)(pgrid.x * pgrid.y);
         Plateau pl;
         int k = 1;
         while (k <= n) {
@@ -1181,7 +1196,7 @@ class Sim final : public SimBase {
             if constexpr (!is_dual<R>::value) {  // dual tiles would not fit in shared memory
                 if (c >= 2) {
                     timer.begin(stream_, KC_POISSON);
-                    pb_launch(pgrid, c, save, do_check);
+                    pblk = pb_launch(pgrid, c, save, do_check);
                     TRY(launched());
                     poisson_iters_run_ += c;
                     blocked = true;
@@ -1244,6 +1259,7 @@ class Sim final : public SimBase {
     std::vector<MGLevel> mg_;
     std::vector<MGLevelF> mgf_;
     cudaGraphExec_t vgraph_ = nullptr;  // the captured V-cycle (multigrid solvers, created streams)
+    int lbmg_first_ = 1;                // first V-cycle level of the LB solve's coarse correction
     int64_t vgraph_nodes_ = 0;
     // the anchor of the potential populations (solvers 2, 3): FP64 in the FP64 build,
     // double-float in the FP32 builds, with the refresh's coefficients in that form
