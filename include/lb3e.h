@@ -299,8 +299,9 @@ int lb3e_set_timing(lb3e_handle* h, int32_t enable);
 
 /* Kernel classes reported by lb3e_kernel_times. */
 enum {
-    LB3E_KC_MOMENTS = 0,   /* zeroth moments of the phase and charge populations */
-    LB3E_KC_PROLOGUE = 1,  /* properties, stencils, closed-form charge */
+    LB3E_KC_MOMENTS = 0,   /* zeroth moments of the phase and charge populations, with the
+                              properties, stencils and closed-form charge in the same pass */
+    LB3E_KC_PROLOGUE = 1,  /* properties and stencils alone (initialisation, batches) */
     LB3E_KC_POISSON = 2,   /* potential solve: LB pseudo-iterations (one or several per launch) or multigrid */
     LB3E_KC_REDUCE = 3,    /* FP64 reductions (residual, observables) */
     LB3E_KC_FIELDS = 4,    /* psi and E from the potential populations */

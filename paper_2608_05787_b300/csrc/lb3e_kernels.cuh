@@ -118,7 +118,7 @@ template <class R, int BY = 8>
 __host__ __device__ constexpr int fused_min_blocks() {
     // tiles of other heights (batches only): the same ~80 registers a thread for 32 x 4
     // (six blocks); 32 x 16 holds one block by its shared memory
-    if constexpr (std::is_same<R, float>::value) return BY == 4 ? 6 : (BY == 16 ? 1 : 3);
+    if constexpr (std::is_same<R, float>::value) return BY == 4 ? 7 : (BY == 16 ? 1 : 3);
     return f32_family<R>::value ? 2 : 1;
 }
 
@@ -347,6 +347,34 @@ __global__ void __launch_bounds__(256) k_moments(DevParams P, const S* __restric
 }
 
 // ---------------------------------------------------------------- S2-S4: properties, stencils, charge
+// the Eq. 33 gradients of eps and sigma at this thread's cell from a staged tile of
+// pitch SX (the cell at row srow, column threadIdx.x + 1 of the tile), then eps and,
+// with use_qt, the closed-form charge from q~ = qt and E of the previous step
+template <class R, int SX>
+__device__ __forceinline__ void prologue_cell(const DevParams& P, const R* se_, const R* ss_, R qt,
+                                              const R* __restrict__ E, R* __restrict__ q, R* __restrict__ eps_out,
+                                              int use_qt, unsigned c, int srow) {
+    const unsigned N = P.N;
+    const int sc = srow * SX + threadIdx.x + 1;
+    R gex = R(0), gey = R(0), gsx = R(0), gsy = R(0), e0 = R(0), s0 = R(0);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const R e = se_[sc + cy(j) * SX + cx(j)], s = ss_[sc + cy(j) * SX + cx(j)];
+        gex += wgt<R>(j) * R(cx(j)) * e;
+        gey += wgt<R>(j) * R(cy(j)) * e;
+        gsx += wgt<R>(j) * R(cx(j)) * s;
+        gsy += wgt<R>(j) * R(cy(j)) * s;
+        if (j == 0) { e0 = e; s0 = s; }
+    }
+    gex = oc2(gex); gey = oc2(gey); gsx = oc2(gsx); gsy = oc2(gsy);
+    eps_out[c] = e0;
+    if (!use_qt) return;
+    const R r = dv(s0, e0, rcp(e0));
+    const R Ex = E[c], Ey = E[N + c];
+    const R src = r * (gex * Ex + gey * Ey) - (gsx * Ex + gsy * Ey);
+    const R den = R(1) + R(0.5) * r;
+    q[c] = dv(qt + R(0.5) * src, den, rcp(den));
+}
 // eps and sigma (Eq. 29-30) of the block's 32 x 8 tile and its one-cell ring are
 // formed once per cell into shared memory (ghost rows mirrored at walls, as the
 // stencil expects); each thread then takes the Eq. 33 gradients from there (the
@@ -372,31 +400,77 @@ __device__ __forceinline__ void body_prologue(const DevParams P, const R* __rest
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
     const unsigned c = (unsigned)y * P.nx + x;
-    const int sc = (threadIdx.y + 1) * SX + threadIdx.x + 1;
-    R gex = R(0), gey = R(0), gsx = R(0), gsy = R(0), e0 = R(0), s0 = R(0);
-#pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        const R e = se_[sc + cy(j) * SX + cx(j)], s = ss_[sc + cy(j) * SX + cx(j)];
-        gex += wgt<R>(j) * R(cx(j)) * e;
-        gey += wgt<R>(j) * R(cy(j)) * e;
-        gsx += wgt<R>(j) * R(cx(j)) * s;
-        gsy += wgt<R>(j) * R(cy(j)) * s;
-        if (j == 0) { e0 = e; s0 = s; }
-    }
-    gex = oc2(gex); gey = oc2(gey); gsx = oc2(gsx); gsy = oc2(gsy);
-    eps_out[c] = e0;
-    if (!use_qt) return;
-    const R r = dv(s0, e0, rcp(e0));
-    const R Ex = E[c], Ey = E[N + c];
-    const R src = r * (gex * Ex + gey * Ey) - (gsx * Ex + gsy * Ey);
-    const R den = R(1) + R(0.5) * r;
-    q[c] = dv(qt[c] + R(0.5) * src, den, rcp(den));
+    prologue_cell<R, SX>(P, se_, ss_, use_qt ? qt[c] : R(0), E, q, eps_out, use_qt, c, threadIdx.y + 1);
 }
 template <class R>
 __global__ void __launch_bounds__(256) k_prologue(DevParams P, const R* __restrict__ phi, const R* __restrict__ qt,
                                                   const R* __restrict__ E, R* __restrict__ q, R* __restrict__ eps_out,
                                                   int use_qt) {
     body_prologue<R>(P, phi, qt, E, q, eps_out, use_qt, blockIdx.x, blockIdx.y, gridDim.x);
+}
+
+// S1-S4 in one pass: the block forms phi of its 32 x 8 tile and one-cell ring from
+// the phase populations (ring rows mirrored at walls, as the stencil expects; the
+// ring's moments are formed again by the neighbouring blocks), writes phi of its own
+// cells, stages eps and sigma, sums q~ from the charge populations and closes the
+// charge as the prologue does.  With the rest population stored as a deviation
+// (anchored storage) phi = the previous phi (phi_old) + the sum; phi_old and phi
+// are different sets of planes, since neighbouring blocks read phi_old on their
+// rings.  The sums run in the order of the separate passes, so the results are the
+// same bit for bit; what is saved is the q~ plane and the prologue's re-read of phi.
+template <class R, class S>
+__device__ __forceinline__ void body_moments_closure(const DevParams P, const S* __restrict__ pop,
+                                                     const R* __restrict__ phi_old, R* __restrict__ phi,
+                                                     const R* __restrict__ E, R* __restrict__ q,
+                                                     R* __restrict__ eps_out, int use_qt, int bx, int by) {
+    constexpr int MC_Y = 8, SX = 34, SY = MC_Y + 2;  // blockDim (32, 8), one-cell ring
+    __shared__ R se_[SY * SX], ss_[SY * SX];
+    const int x0 = bx * blockDim.x, y0 = by * MC_Y;
+    const int nx = P.nx, ny = P.ny;
+    const unsigned N = P.N;
+    for (int k = threadIdx.x + blockDim.x * threadIdx.y; k < SX * SY; k += blockDim.x * blockDim.y) {
+        const int ly = k / SX, lx = k - ly * SX;
+        const unsigned n = (unsigned)tile_row(y0 + ly - 1, ny, P.bc_y) * nx + wrapi(x0 + lx - 1, nx);
+        R p[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            R a = R(0);
+#pragma unroll
+            for (int j = 0; j < 9; ++j) a += Store<S>::ld(pop, (9 * (i + 1) + j) * N + n);
+            if (anchored<S>()) a = phi_old[i * N + n] + a;  // anchor + (deviation + moving populations)
+            p[i] = a;
+        }
+        se_[k] = perm<R>(P, p[0], p[1], p[2]);
+        ss_[k] = cond<R>(P, p[0], p[1], p[2]);
+        if (lx >= 1 && lx <= 32 && ly >= 1 && ly <= MC_Y && x0 + lx - 1 < nx && y0 + ly - 1 < ny) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) phi[i * N + n] = p[i];  // an own cell (row in the domain)
+        }
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x;
+    if (x >= nx) return;
+#pragma unroll
+    for (int r = 0; r < MC_Y; r += 8) {
+        const int y = y0 + threadIdx.y + r;
+        if (y >= ny) return;
+        const unsigned c = (unsigned)y * nx + x;
+        R qt = R(0);
+        if (use_qt) {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) qt += Store<S>::ld(pop, (36 + j) * N + c);
+        }
+        prologue_cell<R, SX>(P, se_, ss_, qt, E, q, eps_out, use_qt, c, threadIdx.y + r + 1);
+    }
+}
+// the merged pass covers 32 x 8 cells a block (32 x 16 measured no faster)
+__host__ __device__ constexpr int moments_closure_rows() { return 8; }
+template <class R, class S>
+__global__ void __launch_bounds__(256) k_moments_closure(DevParams P, const S* __restrict__ pop,
+                                                         const R* __restrict__ phi_old, R* __restrict__ phi,
+                                                         const R* __restrict__ E, R* __restrict__ q,
+                                                         R* __restrict__ eps_out, int use_qt) {
+    body_moments_closure<R, S>(P, pop, phi_old, phi, E, q, eps_out, use_qt, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------- S5: potential iteration (Eq. 43-45)
@@ -1355,14 +1429,18 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     const bool walls = P.bc_y != 0;
     // link j of this cell crosses a wall (half-way bounce-back) instead of reaching a neighbour
     auto to_wall = [&](int j) { return cy(j) != 0 && walls && (y + cy(j) < 0 || y + cy(j) >= ny); };
-    // push helper: post-collision value v of plane (set, j) leaving cell (x, y); a
-    // link into a wall returns to this cell in the opposite direction.  Selects, not
-    // branches: the target is an index computed for every cell.
-    auto push = [&](int set, int j, R v) {
-        const unsigned to = to_wall(j) ? (unsigned)opp(j) * N + c
-                                       : (unsigned)j * N + (unsigned)wrap1(y + cy(j), ny) * nx + wrap1(x + cx(j), nx);
-        Store<S>::st(pout, (size_t)(9 * set) * N + to, v);
-    };
+    // push targets within a set, formed once for the five sets: post-collision value
+    // v of plane (set, j) leaving cell (x, y) goes to the neighbour's plane j, or, on
+    // a link into a wall, back to this cell in the opposite direction
+    unsigned tgt[9];
+    {
+        const unsigned rows[3] = {(unsigned)wrap1(y - 1, ny) * nx, (unsigned)y * nx, (unsigned)wrap1(y + 1, ny) * nx};
+        const unsigned cols[3] = {(unsigned)wrap1(x - 1, nx), (unsigned)x, (unsigned)wrap1(x + 1, nx)};
+#pragma unroll
+        for (int j = 0; j < 9; ++j)
+            tgt[j] = to_wall(j) ? (unsigned)opp(j) * N + c : (unsigned)j * N + rows[cy(j) + 1] + cols[cx(j) + 1];
+    }
+    auto push = [&](int set, int j, R v) { Store<S>::st(pout, (size_t)(9 * set) * N + tgt[j], v); };
 
     // phase populations, Eq. 34-36 with the mobility of Eq. 28
     const R tf = pv<R>(P.tau_f, P.ftau_f), m0 = pv<R>(P.m0, P.fm0);

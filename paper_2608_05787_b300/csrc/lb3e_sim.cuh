@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "lb3e_anchor.cuh"
@@ -28,7 +29,7 @@ class Sim final : public SimBase {
     // workspace layout (byte offsets), computed identically by bytes() and the constructor
     struct Layout {
         size_t pop[2], h[2], phi, qt, q, eps, E, prev, diag, psi_prev, partial, result, stage, mg, ion[2], ionst,
-            anchor, rres, ja, total;
+            anchor, rres, ja, phi2, total;
     };
     static Layout layout(const lb3e_params& p) {
         const size_t N = (size_t)p.nx * p.ny;
@@ -48,6 +49,9 @@ class Sim final : public SimBase {
         L.prev = take(8 * N * sizeof(R));
         L.diag = take(6 * N * sizeof(R));
         L.psi_prev = take(3 * N * sizeof(R));
+        // the other set of phi planes: the moments pass reads the previous step's phi
+        // (the rest populations' anchor) from one set and writes the new phi to the other
+        L.phi2 = take(3 * N * sizeof(R));
         // per-block partials: NOBS per 32 x 8 tile, or the observables' NOBS sums
         // and one max per 32 x 64 block, whichever is larger
         const dim3 og = obs_grid(p.nx, p.ny);
@@ -93,6 +97,7 @@ class Sim final : public SimBase {
         d_.h[0] = reinterpret_cast<R*>(b + L_.h[0]);
         d_.h[1] = reinterpret_cast<R*>(b + L_.h[1]);
         d_.phi = reinterpret_cast<R*>(b + L_.phi);
+        phi_alt_ = reinterpret_cast<R*>(b + L_.phi2);
         d_.qt = reinterpret_cast<R*>(b + L_.qt);
         d_.q = reinterpret_cast<R*>(b + L_.q);
         d_.eps = reinterpret_cast<R*>(b + L_.eps);
@@ -244,13 +249,14 @@ class Sim final : public SimBase {
     int step(int nsteps) override {
         for (int s = 0; s < nsteps; ++s) {
             const int last = (s == nsteps - 1);
+            // moments, properties and the closed-form charge in one pass: the new phi
+            // goes to the other set of planes (the current set is the anchor of the
+            // rest populations, read by the neighbouring blocks for their rings)
             timer.begin(stream_, KC_MOMENTS);
-            k_moments<R, S><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.pop[cur_], d_.phi, d_.phi, d_.qt);
+            k_moments_closure<R, S><<<mc_grid(), dim3(TX, TY), 0, stream_>>>(dp_, d_.pop[cur_], d_.phi, phi_alt_, d_.E,
+                                                                           d_.q, d_.eps, p_.ions ? 0 : 1);
             TRY(launched());
-            timer.begin(stream_, KC_PROLOGUE);
-            k_prologue<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.phi, d_.qt, d_.E, d_.q, d_.eps,
-                                                                p_.ions ? 0 : 1);
-            TRY(launched());
+            std::swap(d_.phi, phi_alt_);
             if constexpr (!is_dual<R>::value) {
                 if (p_.ions) {  // the charge the ions carry replaces the closure charge
                     timer.begin(stream_, KC_IONS);
@@ -449,7 +455,8 @@ class Sim final : public SimBase {
         o += 45 * N_ * sizeof(S);
         TRY(copy(o, d_.h[hcur_], 9 * N_ * sizeof(R)));
         o += 9 * N_ * sizeof(R);
-        TRY(copy(o, base_ + L_.phi, fields_bytes()));
+        TRY(copy(o, d_.phi, phi_bytes()));  // the current of the two phi sets
+        TRY(copy(o + phi_bytes(), base_ + L_.phi + phi_bytes(), fields_bytes() - phi_bytes()));
         o += fields_bytes();
         if (p_.ions) {  // current ion populations, then n_i and (n_i v_i)^{n-1}
             TRY(copy(o, ion_[icur_], 18 * N_ * sizeof(R)));
@@ -474,7 +481,8 @@ class Sim final : public SimBase {
         s += 45 * N_ * sizeof(S);
         TRY(copy(d_.h[0], s, 9 * N_ * sizeof(R)));
         s += 9 * N_ * sizeof(R);
-        TRY(copy(base_ + L_.phi, s, fields_bytes()));
+        TRY(copy(d_.phi, s, phi_bytes()));
+        TRY(copy(base_ + L_.phi + phi_bytes(), s + phi_bytes(), fields_bytes() - phi_bytes()));
         s += fields_bytes();
         if (p_.ions) {
             icur_ = 0;
@@ -559,6 +567,10 @@ class Sim final : public SimBase {
 
   private:
     size_t fields_bytes() const { return L_.psi_prev + align256(3 * N_ * sizeof(R)) - L_.phi; }
+    size_t phi_bytes() const { return align256(3 * N_ * sizeof(R)); }
+    dim3 mc_grid() const {
+        return dim3((p_.nx + TX - 1) / TX, (p_.ny + moments_closure_rows() - 1) / moments_closure_rows());
+    }
     size_t ion_bytes() const { return p_.ions ? 24 * N_ * sizeof(R) : 0; }
     size_t anchor_bytes() const { return anchor_ ? 9 * N_ * sizeof(AT) : 0; }
     static unsigned blocks1(size_t n) { return (unsigned)((n + 255) / 256); }
@@ -1265,6 +1277,7 @@ class Sim final : public SimBase {
     // double-float in the FP32 builds, with the refresh's coefficients in that form
     using AT = typename AnchorOf<R>::type;
     AT* anchor_ = nullptr;
+    R* phi_alt_ = nullptr;  // the set of phi planes the next moments pass writes
     AnchorCoef acoef_{};
     R* rres_ = nullptr;         // the anchor's increment over one pseudo-iteration
     R* ja_ = nullptr;           // the anchor's flux J = sum_j c_j a_j (2 planes), for E
