@@ -53,16 +53,23 @@ SOLVER_NAMES = {
 }
 # algorithmic bytes per cell: the compulsory traffic of each kernel (every array it must
 # read or write once per cell), not counting halo re-reads
-FUSED_BYTES = {0: 8 * 112, 1: 4 * 112, 2: 2 * 90 + 4 * 22}   # k_fused: 45 pops r+w, phi, q, E, d/dt state
-POISSON_BYTES = {0: 8 * 20, 1: 4 * 20, 2: 4 * 20}           # one pseudo-iteration: h 9 r + 9 w, eps, q
+FUSED_BYTES = {0: 8 * 112, 1: 4 * 112, 2: 2 * 90 + 4 * 22, 5: 2 * 90 + 4 * 22}  # k_fused: 45 pops r+w, phi, q, E, d/dt state
+POISSON_BYTES = {0: 8 * 20, 1: 4 * 20, 2: 4 * 20, 5: 4 * 20}  # one pseudo-iteration: h 9 r + 9 w, eps, q
 # one pseudo-iteration on the correction to the FP64 anchor: delta 9 r + 9 w, eps,
 # and the anchor's increment (9 planes) instead of q
-POISSON_RS_BYTES = {0: 8 * 28, 1: 4 * 28, 2: 4 * 28}
-# one anchor refresh (two launches): fold and FP64 collision (anchor 9 r + 9 w,
-# delta 9 r + 9 w, eps, q, 9 FP64 staging planes written) and increment (anchor and
-# staging read, 9 increment planes written)
-ANCHOR_BYTES = {0: 72 * 4 + 8 * 20 + 72 + 8 * 9, 1: 72 * 4 + 4 * 20 + 72 + 4 * 9, 2: 72 * 4 + 4 * 20 + 72 + 4 * 9}
-STEP_BYTES = {0: 960, 1: 480, 2: 300}                        # whole step without the potential loop
+POISSON_RS_BYTES = {0: 8 * 28, 1: 4 * 28, 2: 4 * 28, 5: 4 * 28}
+# one anchor refresh.  FP64 build (two launches): fold and FP64 collision (anchor 9 r +
+# 9 w, delta 9 r + 9 w, eps, q, 9 FP64 staging planes written) and increment (anchor
+# and staging read, 9 increment planes written).  FP32 builds (one launch, the
+# double-float anchor in 8-byte words): anchor 9 r + 9 w, delta 9 r, eps, q, 9
+# increment planes and the anchor's flux (2) written; delta is left for the coarse
+# correction to overwrite
+ANCHOR_BYTES = {0: 72 * 4 + 8 * 20 + 72 + 8 * 9, 1: 72 * 2 + 4 * (9 + 2 + 9 + 2)}
+ANCHOR_LAUNCHES = {0: 2, 1: 1}
+for _p in (2, 5):  # 16-bit population storage: FP32 arithmetic, FP32 potential
+    ANCHOR_BYTES[_p], ANCHOR_LAUNCHES[_p] = ANCHOR_BYTES[1], ANCHOR_LAUNCHES[1]
+STEP_BYTES = {0: 960, 1: 480, 2: 300, 5: 300}               # whole step without the potential loop
+DTYPE_NAMES = {0: "f64", 1: "f32", 2: "f32 (f16-stored populations)", 5: "f32 (bf16-stored populations)"}
 # multigrid cycle per fine cell (defect correction): the FP64 fine residual (psi,
 # rhs, 3 coefficients read, residual written: 48 B), then the FP32 V-cycle on the
 # error equation -- defect load (16 B), 4 red-black sweeps (e r/w, rhs, 3
@@ -93,7 +100,8 @@ def parse():
                     choices=["deformation", "sweep", "adjoint", "regimes", "eof", "deformation3d"],
                     help="deformation: the 4096^2 lattice (default); sweep: 256 lattices in one batch; "
                          "adjoint: cost of the three parameter derivatives relative to a forward step")
-    ap.add_argument("--precision", type=int, default=1, help="0 fp64, 1 fp32, 2 fp32 + fp16-stored populations")
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2, 5],
+                    help="0 fp64, 1 fp32, 2 fp32 + fp16-stored populations, 5 fp32 + bf16-stored populations")
     ap.add_argument("--n", type=int, default=4096, help="lattice side (the stated workload is 4096)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
@@ -428,9 +436,11 @@ def run_lb3e(args):
         classes["poisson"] = (MG_VCYCLE_BYTES * N * pot_iters / poisson_n, poisson_ms / poisson_n,
                               "multigrid V-cycle kernels", f"{N} cells x V-cycles")
     anchor_ms, anchor_n = kt.get("anchor", (0.0, 0))
+    refreshes = anchor_n / ANCHOR_LAUNCHES[prec]
     if anchor_n:
-        classes["anchor"] = (ANCHOR_BYTES[prec] * N, anchor_ms / (anchor_n / 2), "k_anchor_refresh + k_anchor_residual",
-                             f"{N} cells, one refresh (two launches)")
+        classes["anchor"] = (ANCHOR_BYTES[prec] * N, anchor_ms / refreshes,
+                             "k_anchor_refresh + k_anchor_residual" if ANCHOR_LAUNCHES[prec] == 2
+                             else "k_anchor_refresh_pull_df", f"{N} cells, one refresh")
     k_gbs = {k: b / (t / 1e3) / 1e9 for k, (b, t, _, _) in classes.items()}
     dominant = max(classes, key=lambda k: kt[k][0])
     dbytes, dms, kname, units = classes[dominant]
@@ -445,7 +455,7 @@ def run_lb3e(args):
     # the whole step: fused step bytes (Section 8 figure) + potential iterations +
     # anchor refreshes, over the measured step time
     step_bytes = STEP_BYTES[prec] * N + (classes["poisson"][0] * poisson_n if "poisson" in classes else 0) / \
-        args.steps + ANCHOR_BYTES[prec] * N * (anchor_n / 2) / args.steps
+        args.steps + ANCHOR_BYTES[prec] * N * refreshes / args.steps
     step_roofline = {"bytes_per_step": step_bytes, "achieved": step_bytes / (ms / args.steps / 1e3) / 1e9,
                      "frac": step_bytes / (ms / args.steps / 1e3) / 1e9 / hbm}
 
@@ -490,7 +500,7 @@ def run_lb3e(args):
             cpu = {"value": None, "error": repr(exc)}
 
     if rank == 0:
-        dtype = {0: "f64", 1: "f32", 2: "f32 (f16-stored populations)"}[prec]
+        dtype = DTYPE_NAMES[prec]
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -500,7 +510,7 @@ def run_lb3e(args):
                        "poisson_tol": params["poisson_tol"], "poisson_max_iter": params["poisson_max_iter"],
                        "poisson_check_every": params["poisson_check_every"], "potential_chunk": chunk,
                        "potential_iters_per_step": iters_per_step,
-                       "anchor_refreshes_per_step": (anchor_n / 2) / args.steps,
+                       "anchor_refreshes_per_step": refreshes / args.steps,
                        "potential_solver": SOLVER_NAMES[solver],
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single lattice",
                        "l2": "working set (%.1f GB) exceeds the 126 MB L2; no flush needed" % (L.workspace_bytes(params) / 1e9),
@@ -574,7 +584,7 @@ def run_sweep(args):
         line = {"metric": METRIC, "value": total / t / 1e6, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "strong", "vs_baseline": None,
-                "dtype": {0: "f64", 1: "f32", 2: "f32 (f16-stored populations)"}[args.precision],
+                "dtype": DTYPE_NAMES[args.precision],
                 "data": "synthetic (seeded sweep of the stated parameter ranges)",
                 "config": {"workload": "batched sweep: 256 compound drops, sides {128,192,256,384,512}",
                            "cells": sum(cells), "potential_iters_per_step": 16, "autotuned_chunk": chunk,
@@ -633,7 +643,7 @@ def run_regimes(args):
     per_cell = FUSED_BYTES[args.precision] + 16 * POISSON_BYTES[args.precision]
     line = {"metric": METRIC, "value": total / t / 1e6, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {0: "f64", 1: "f32", 2: "f32 (f16-stored populations)"}[args.precision],
+            "vs_baseline": None, "dtype": DTYPE_NAMES[args.precision],
             "data": "synthetic (the paper's drop-pair and confined-shear set-ups)",
             "config": {"workload": "second workload: 20 confined-shear channels + 2 drop pairs, one batch",
                        "cells": cells, "potential_iters_per_step": 16, "chunk": 4,
@@ -751,7 +761,7 @@ def run_eof(args):
 
     line = {"metric": METRIC, "value": total / t / 1e6, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {0: "f64", 1: "f32", 2: "f32 (f16-stored populations)"}[prec],
+            "vs_baseline": None, "dtype": DTYPE_NAMES[prec],
             "data": "synthetic (the paper's electro-osmotic channel in lattice units, ions in their double layers)",
             "config": {"workload": f"electro-osmotic channel with Nernst-Planck ions, {params['nx']}x{params['ny']}",
                        "kappa_h": 20.0, "potential_solver": "multigrid V-cycles on the FD form",

@@ -127,77 +127,98 @@ __global__ void __launch_bounds__(256) k_anchor_init(DevParams P, typename Ancho
     }
 }
 
-// The refresh of the FP32 builds in double-float arithmetic: fold delta into the
-// anchor, then the collision of Eq. 43 (factored form, as k_anchor_refresh) pushed to
-// the staging planes (double-float), with the charge source and the electrode walls.
-// Kc is the FP32 value of the correction kernels (it scales the first moment only).
-static __global__ void __launch_bounds__(256) k_anchor_refresh_df(DevParams P, df32* __restrict__ a, float* __restrict__ d,
-                                                           const float* __restrict__ eps, const float* __restrict__ q,
-                                                           df32* __restrict__ stage, float* __restrict__ ja,
-                                                           AnchorCoef K) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
-    const unsigned N = P.N, c = (unsigned)y * P.nx + x;
-    df32 h[9];
+// The refresh and the anchor's increment in one pass (FP32 builds): a block of
+// 32 x 8 cells folds delta into the anchor and collides (Eq. 43, double-float, the
+// factored form of k_anchor_refresh) on its tile and one-cell ring, keeps the
+// post-collision values in shared memory, and each of its cells pulls what streams
+// into it (across a wall: the reflected value of its own opposite direction, as the
+// push form writes it) and forms r = pulled - a, with the per-block sums of
+// k_anchor_residual over the same 32 x 8 blocks.  The folded anchor goes to a_out
+// and, with d_out, delta = 0 to d_out: neighbouring blocks read a_in and d on their
+// rings.  d = nullptr: delta is zero (already folded).
+static __global__ void __launch_bounds__(256) k_anchor_refresh_pull_df(DevParams P, const df32* __restrict__ a_in,
+                                                                       df32* __restrict__ a_out,
+                                                                       const float* __restrict__ d,
+                                                                       float* __restrict__ d_out,
+                                                                       const float* __restrict__ eps,
+                                                                       const float* __restrict__ q,
+                                                                       float* __restrict__ r, float* __restrict__ ja,
+                                                                       double* __restrict__ partial, AnchorCoef K) {
+    constexpr int SX = 34, SY = 10, NC = SX * SY, TC = 32 * 8;
+    __shared__ df32 sv[9 * NC];  // post-collision values of the tile and its ring
+    __shared__ df32 sh[9 * TC];  // the folded anchor of the tile's cells
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8, tid = threadIdx.x + 32 * threadIdx.y;
+    const int nx = P.nx, ny = P.ny;
+    const unsigned N = P.N;
+    const bool walls = P.bc_y != 0;
+    for (int k = tid; k < NC; k += TC) {
+        const int ly = k / SX, lx = k - ly * SX;
+        const int gy = y0 + ly - 1, gx = x0 + lx - 1;
+        if (walls && (gy < 0 || gy >= ny)) continue;  // beyond a wall: no cell, never a source
+        const unsigned c = (unsigned)wrapi(gy, ny) * nx + wrapi(gx, nx);
+        const bool own = lx >= 1 && lx <= 32 && ly >= 1 && ly <= 8 && gx < nx && gy < ny;
+        df32 h[9];
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        h[j] = df_add_f(a[j * N + c], d[j * N + c]);
-        a[j * N + c] = h[j];
-        d[j * N + c] = 0.f;
-    }
-    df32 sum = h[1], jx = {0.f, 0.f}, jy = {0.f, 0.f};
+        for (int j = 0; j < 9; ++j) h[j] = d ? df_add_f(a_in[j * N + c], d[j * N + c]) : a_in[j * N + c];
+        df32 sum = h[1], jx = {0.f, 0.f}, jy = {0.f, 0.f};
 #pragma unroll
-    for (int j = 2; j < 9; ++j) sum = df_add(sum, h[j]);
-    const df32 ps = df_mul(sum, K.c18);
-    // J = sum_j c_j h_j (the lattice components are 0 or +-1)
+        for (int j = 2; j < 9; ++j) sum = df_add(sum, h[j]);
+        const df32 ps = df_mul(sum, K.c18);
 #pragma unroll
-    for (int j = 1; j < 9; ++j) {
-        if (cx(j)) jx = df_add(jx, cx(j) > 0 ? h[j] : df_neg(h[j]));
-        if (cy(j)) jy = df_add(jy, cy(j) > 0 ? h[j] : df_neg(h[j]));
-    }
-    ja[c] = df_round(jx);
-    ja[N + c] = df_round(jy);
-    const float eh = eps[c] - P.feps_ref;
-    const float Kc = 3.0f * P.fitau_h * eh * rcp(eh + cs2<float>() * P.ftau_h);
-    const df32 A = df_mul(K.ith, ps);
-    const float q8 = 0.125f * q[c];
-#pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        df32 v;
-        if (j == 0) {
-            v = df_add(df_mul(K.om, h[0]), df_mul(K.w0m1, A));
-        } else {
-            df32 cj = cx(j) > 0 ? jx : (cx(j) < 0 ? df_neg(jx) : df32{0.f, 0.f});
-            if (cy(j) > 0) cj = df_add(cj, jy);
-            else if (cy(j) < 0) cj = df_add(cj, df_neg(jy));
-            const df32 t = df_add(A, df_mul_f(cj, Kc));
-            v = df_add_f(df_add(df_mul(K.om, h[j]), df_mul(j <= 4 ? K.w1 : K.w5, t)), q8);
+        for (int j = 1; j < 9; ++j) {
+            if (cx(j)) jx = df_add(jx, cx(j) > 0 ? h[j] : df_neg(h[j]));
+            if (cy(j)) jy = df_add(jy, cy(j) > 0 ? h[j] : df_neg(h[j]));
         }
-        const int yt = y + cy(j);
-        if (P.bc_y != 0 && (yt < 0 || yt >= P.ny)) {
-            df32 out = v;
-            if (P.bc_y == 2) out = df_add(df_neg(v), K.wv[yt >= P.ny ? 1 : 0][j <= 4 ? 0 : 1]);
-            stage[opp(j) * N + c] = out;
-        } else {
-            stage[j * N + (unsigned)wrapi(yt, P.ny) * P.nx + wrapi(x + cx(j), P.nx)] = v;
+        if (own) {
+            const int t = (ly - 1) * 32 + lx - 1;
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                a_out[j * N + c] = h[j];
+                sh[j * TC + t] = h[j];
+                if (d_out) d_out[j * N + c] = 0.f;
+            }
+            ja[c] = df_round(jx);
+            ja[N + c] = df_round(jy);
+        }
+        const float eh = eps[c] - P.feps_ref;
+        const float Kc = 3.0f * P.fitau_h * eh * rcp(eh + cs2<float>() * P.ftau_h);
+        const df32 A = df_mul(K.ith, ps);
+        const float q8 = 0.125f * q[c];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            df32 v;
+            if (j == 0) {
+                v = df_add(df_mul(K.om, h[0]), df_mul(K.w0m1, A));
+            } else {
+                df32 cj = cx(j) > 0 ? jx : (cx(j) < 0 ? df_neg(jx) : df32{0.f, 0.f});
+                if (cy(j) > 0) cj = df_add(cj, jy);
+                else if (cy(j) < 0) cj = df_add(cj, df_neg(jy));
+                const df32 t = df_add(A, df_mul_f(cj, Kc));
+                v = df_add_f(df_add(df_mul(K.om, h[j]), df_mul(j <= 4 ? K.w1 : K.w5, t)), q8);
+            }
+            sv[j * NC + k] = v;
         }
     }
-}
-
-// r = stage - a in double-float, rounded to FP32, and the per-block sums of
-// k_anchor_residual
-static __global__ void __launch_bounds__(256) k_anchor_residual_df(DevParams P, const df32* __restrict__ a,
-                                                            const df32* __restrict__ stage, float* __restrict__ r,
-                                                            double* __restrict__ partial) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    __syncthreads();
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    if (x < P.nx && y < P.ny) {
-        const unsigned N = P.N, c = (unsigned)y * P.nx + x;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x < nx && y < ny) {
+        const unsigned c = (unsigned)y * nx + x;
+        const int k = (threadIdx.y + 1) * SX + threadIdx.x + 1;
         float dps = 0.f, ps = 0.f, djx = 0.f, djy = 0.f, jx = 0.f, jy = 0.f;
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
-            const df32 aj = a[j * N + c];
-            const float rj = df_round(df_add(stage[j * N + c], df_neg(aj))), ar = df_round(aj);
+            const int ys = y - cy(j);  // the source row
+            df32 g;
+            if (walls && (ys < 0 || ys >= ny)) {
+                const int jl = opp(j);  // the direction that left this cell toward the wall
+                g = sv[jl * NC + k];
+                if (P.bc_y == 2) g = df_add(df_neg(g), K.wv[ys >= ny ? 1 : 0][jl <= 4 ? 0 : 1]);
+            } else {
+                g = sv[j * NC + k - cy(j) * SX - cx(j)];
+            }
+            const df32 aj = sh[j * TC + tid];
+            const float rj = df_round(df_add(g, df_neg(aj))), ar = df_round(aj);
             r[j * N + c] = rj;
             if (j) { dps += rj; ps += ar; }
             cacc(djx, cx(j), rj);
@@ -214,6 +235,7 @@ static __global__ void __launch_bounds__(256) k_anchor_residual_df(DevParams P, 
     }
     block_reduce_store_r<4>(acc, partial + 4 * (size_t)(blockIdx.x + gridDim.x * blockIdx.y));
 }
+
 
 // Fold delta into the anchor (a += delta, delta = 0) and push the FP64 collision
 // of the folded anchor (Eq. 43 with the charge source and the electrode walls) to

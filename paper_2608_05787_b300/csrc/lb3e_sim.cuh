@@ -29,7 +29,7 @@ class Sim final : public SimBase {
     // workspace layout (byte offsets), computed identically by bytes() and the constructor
     struct Layout {
         size_t pop[2], h[2], phi, qt, q, eps, E, prev, diag, psi_prev, partial, result, stage, mg, ion[2], ionst,
-            anchor, rres, ja, phi2, total;
+            anchor, rres, ja, phi2, anchor2, total;
     };
     static Layout layout(const lb3e_params& p) {
         const size_t N = (size_t)p.nx * p.ny;
@@ -85,6 +85,9 @@ class Sim final : public SimBase {
         L.anchor = take(9 * na * sizeof(double));
         L.rres = take(9 * na * sizeof(R));
         L.ja = take(2 * na * sizeof(R));
+        // FP32 builds: a second set of anchor planes (the one-pass refresh writes the
+        // folded anchor there while neighbouring blocks read the current one)
+        L.anchor2 = take(9 * (std::is_same<R, float>::value ? na : 0) * sizeof(double));
         L.total = o;
         return L;
     }
@@ -122,6 +125,7 @@ class Sim final : public SimBase {
         nblk_ = (int)(grid2_.x * grid2_.y);
         if (prm.electric && prm.potential_solver >= 2) {
             anchor_ = reinterpret_cast<AT*>(b + L_.anchor);
+            if (std::is_same<R, float>::value) anchor_alt_ = reinterpret_cast<AT*>(b + L_.anchor2);
             rres_ = reinterpret_cast<R*>(b + L_.rres);
             ja_ = reinterpret_cast<R*>(b + L_.ja);
             const double ith = 1.0 / dp_.tau_h, w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w5 = 1.0 / 36.0;
@@ -914,18 +918,21 @@ class Sim final : public SimBase {
     // Fold delta into the FP64 anchor and form the anchor's increment r = T a + s - a
     // (rres), delta = 0.  With `residual`: the relative increments of psi and J in
     // *res, and the anchor's |psi|^2, |J|^2 (the denominators of later checks) in norms.
-    int anchor_refresh(bool residual, double* res, double* norms) {
+    // zero_delta = false (a coarse correction that overwrites delta follows): the FP32
+    // builds leave delta as it is and mark it stale (cleared if the solve ends first)
+    int anchor_refresh(bool residual, double* res, double* norms, bool zero_delta = true) {
         if constexpr (is_dual<R>::value) {
             return LB3E_ERR_PARAM;
         } else {
             timer.begin(stream_, KC_ANCHOR);
-            if constexpr (std::is_same<R, float>::value) {  // double-float anchor
-                df32* st = reinterpret_cast<df32*>(d_.stage);
-                k_anchor_refresh_df<<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.h[hcur_], d_.eps, d_.q, st,
-                                                                          ja_, acoef_);
-                TRY(launched());
-                timer.begin(stream_, KC_ANCHOR);
-                k_anchor_residual_df<<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, st, rres_, d_.partial);
+            if constexpr (std::is_same<R, float>::value) {  // double-float anchor, one pass
+                k_anchor_refresh_pull_df<<<grid2_, dim3(TX, TY), 0, stream_>>>(
+                    dp_, anchor_, anchor_alt_, delta_stale_ ? nullptr : d_.h[hcur_], zero_delta ? d_.h[hcur_ ^ 1] : nullptr,
+                    d_.eps, d_.q,
+                    rres_, ja_, d_.partial, acoef_);
+                std::swap(anchor_, anchor_alt_);
+                if (zero_delta) hcur_ ^= 1;
+                delta_stale_ = !zero_delta;
             } else {
                 k_anchor_refresh<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, anchor_, d_.h[hcur_], d_.eps, d_.q,
                                                                           d_.stage, ja_, 1.0 / dp_.tau_h,
@@ -1009,6 +1016,7 @@ class Sim final : public SimBase {
             timer.begin(stream_, KC_COARSE);
             k_lbmg_correct<R><<<grid2_, blk, 0, stream_>>>(dp_, mgf_[0], d_.eps, d_.h[hcur_], after_refresh ? 0 : 1);
             TRY(launched());
+            if (after_refresh) delta_stale_ = false;  // delta = the correction
         }
         return LB3E_OK;
     }
@@ -1066,7 +1074,7 @@ class Sim final : public SimBase {
         const bool coarse = p_.potential_solver == 2 && fixed <= 0;
         if (coarse) TRY(lbmg_setup());
         double norms[2] = {0.0, 0.0}, res = -1.0;
-        TRY(anchor_refresh(fixed <= 0, &res, norms));
+        TRY(anchor_refresh(fixed <= 0, &res, norms, !coarse));
         int it = 0;
         if (fixed > 0) {
             // the plain iterates, delta folded into the anchor every check iterations so
@@ -1086,7 +1094,7 @@ class Sim final : public SimBase {
                 if (pl.stalled(res, coarse ? 4 : 32)) {
                     // a stall again after a stall refresh, with no progress between: a floor
                     if (stall_refreshed) { last_conv_ = -1; break; }
-                    TRY(anchor_refresh(true, &res, norms));
+                    TRY(anchor_refresh(true, &res, norms, !coarse));
                     after_refresh = true;
                     stall_refreshed = true;
                     pl = Plateau();
@@ -1102,12 +1110,16 @@ class Sim final : public SimBase {
                 TRY(rs_check(norms, coarse, tol, &res, &noisy));
                 after_refresh = false;
                 if (noisy && res > tol) {  // the exact increment at a fresh anchor instead
-                    TRY(anchor_refresh(true, &res, norms));
+                    TRY(anchor_refresh(true, &res, norms, !coarse));
                     after_refresh = true;
                 }
             }
         }
         last_iters_ = it;
+        if (delta_stale_) {  // the solve ended at a refresh: h = the anchor
+            if (cudaMemsetAsync(d_.h[hcur_], 0, 9 * N_ * sizeof(R), stream_) != cudaSuccess) return LB3E_ERR_CUDA;
+            delta_stale_ = false;
+        }
         if constexpr (!is_dual<R>::value) {
             timer.begin(stream_, KC_FIELDS);
             k_anchor_efield<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, ja_, d_.h[hcur_], d_.eps, d_.E);
@@ -1277,6 +1289,8 @@ class Sim final : public SimBase {
     // double-float in the FP32 builds, with the refresh's coefficients in that form
     using AT = typename AnchorOf<R>::type;
     AT* anchor_ = nullptr;
+    AT* anchor_alt_ = nullptr;   // FP32 builds: the anchor planes the next refresh writes
+    bool delta_stale_ = false;   // delta was folded into the anchor but not yet cleared
     R* phi_alt_ = nullptr;  // the set of phi planes the next moments pass writes
     AnchorCoef acoef_{};
     R* rres_ = nullptr;         // the anchor's increment over one pseudo-iteration
