@@ -61,12 +61,14 @@ __device__ __forceinline__ df32 df_fast_two_sum(float a, float b) {
     return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
 __device__ __forceinline__ df32 df_neg(df32 a) { return {-a.hi, -a.lo}; }
+// a + b with an error of a few units of 2^-48 of the larger operand (Dekker's add:
+// one TwoSum on the leading parts, the trailing parts added plainly).  The refresh
+// needs its results to that accuracy in absolute terms, relative to the anchor's
+// size, not relative to a cancelled difference; the full TwoSum add costs twice the
+// instructions on a pass bound by them.
 __device__ __forceinline__ df32 df_add(df32 a, df32 b) {
     df32 s = df_two_sum(a.hi, b.hi);
-    const df32 t = df_two_sum(a.lo, b.lo);
-    s.lo = __fadd_rn(s.lo, t.hi);
-    s = df_fast_two_sum(s.hi, s.lo);
-    s.lo = __fadd_rn(s.lo, t.lo);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
     return df_fast_two_sum(s.hi, s.lo);
 }
 __device__ __forceinline__ df32 df_add_f(df32 a, float b) {
