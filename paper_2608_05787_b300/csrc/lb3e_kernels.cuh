@@ -732,13 +732,14 @@ __host__ __device__ constexpr int pb_halo_for(int K) { return K <= 2 ? 2 : (K <=
 // A cell collides while it is inside the dependency cone (d <= K - t) and pulls
 // while its pull is still needed (d <= K - 1 - t); non-fluid rows (beyond a wall)
 // neither collide nor store: their slots are the ghost slots the wall rows write.
-template <int H, int KC, bool RS>
+template <int H, int KC, bool RS, bool INC = false>
 __device__ __forceinline__ void body_poisson_tb_f32(const DevParams P, const float* __restrict__ hin,
                                                     float* __restrict__ hout, const float* __restrict__ eps,
                                                     const float* __restrict__ q, float* __restrict__ prev,
                                                     double* __restrict__ partial, int Kdyn, int save_prev,
                                                     int check, int bx, int by, int gdx,
-                                                    const float* __restrict__ rres) {
+                                                    const float* __restrict__ rres, float* __restrict__ rhs,
+                                                    float* __restrict__ e0) {
     using G = PBGeom<H, pb_cpt<float, RS>()>;
     constexpr int RX = G::RX, CELLS = G::CELLS, CPT = G::CPT, NT = G::THREADS, SET = 8 * CELLS;
     constexpr int SETS = pb_sets<float, RS>();
@@ -757,6 +758,7 @@ __device__ __forceinline__ void body_poisson_tb_f32(const DevParams P, const flo
     // 9 top wall row, bit 10 a tile cell inside the grid
     float h[CPT][9];
     float rr[RS ? CPT : 1][9];
+    float pv[RS && INC ? CPT : 1][3];  // RS with INC: psi, J before the last collision
     int meta[CPT];
 #pragma unroll
     for (int m = 0; m < CPT; ++m) {
@@ -820,7 +822,17 @@ __device__ __forceinline__ void body_poisson_tb_f32(const DevParams P, const flo
                     acc[2] += ex * ex + ey * ey;
                     acc[3] += jx * jx + jy * jy;
                 }
-                if (save_prev && t == K - 1) { prev[c] = ps; prev[N + c] = jx; prev[2 * N + c] = jy; }
+                if (save_prev && t == K - 1) {
+                    if constexpr (RS && INC) {  // kept for the check below
+                        pv[m][0] = ps;
+                        pv[m][1] = jx;
+                        pv[m][2] = jy;
+                    } else {
+                        prev[c] = ps;
+                        prev[N + c] = jx;
+                        prev[2 * N + c] = jy;
+                    }
+                }
             }
             collide_f32<float, !RS>(h[m], S, jx, jy, sk[k], RS ? 0.f : sq[k], C, v);
             h[m][0] = RS ? __fadd_rn(v[0], rr[m][0]) : v[0];  // the rest population stays
@@ -867,17 +879,45 @@ __device__ __forceinline__ void body_poisson_tb_f32(const DevParams P, const flo
         for (int j = 0; j < 9; ++j) hout[j * N + c] = h[m][j];
     }
     if (check) block_reduce_store_r<4>(acc, partial + 4 * (size_t)(bx + gdx * by));
+    // RS, INC (with save_prev): the check of k_rs_increment on the tile, from
+    // the final delta and psi, J before the last collision, all in registers (prev
+    // is not written): per-block sums of |d psi|^2, |d J|^2, sum_j delta_j^2 and,
+    // with rhs, the coarse correction's right-hand side and zero initial guess
+    if constexpr (RS && INC) {
+        {
+            float ai[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int m = 0; m < CPT; ++m) {
+                if (!(meta[m] & 1024)) continue;
+                const unsigned c = cell(m);
+                float S, jx, jy;
+                moments_f32<float>(h[m], S, jx, jy);
+#pragma unroll
+                for (int j = 0; j < 9; ++j) ai[2] += h[m][j] * h[m][j];
+                const float pp = pv[m][0];
+                const float dp = S * 1.8f - pp, ex = jx - pv[m][1], ey = jy - pv[m][2];
+                ai[0] += dp * dp;
+                ai[1] += ex * ex + ey * ey;
+                if (rhs) {
+                    rhs[c] = S - (1.0f - wgt<float>(0)) * pp;
+                    e0[c] = 0.f;
+                }
+            }
+            block_reduce_store_r<3>(ai, partial + 3 * (size_t)(bx + gdx * by));
+        }
+    }
 }
 
-template <class R, int H, int KC = 0, bool RS = false>
+template <class R, int H, int KC = 0, bool RS = false, bool INC = false>
 __device__ __forceinline__ void body_poisson_tb(const DevParams P, const R* __restrict__ hin,
                                                 R* __restrict__ hout, const R* __restrict__ eps,
                                                 const R* __restrict__ q, R* __restrict__ prev,
                                                 double* __restrict__ partial, int Kdyn, int save_prev, int check,
-                                                int bx, int by, int gdx, const R* __restrict__ rres = nullptr) {
+                                                int bx, int by, int gdx, const R* __restrict__ rres = nullptr,
+                                                float* __restrict__ rhs = nullptr, float* __restrict__ e0 = nullptr) {
     if constexpr (std::is_same<R, float>::value) {
-        body_poisson_tb_f32<H, KC, RS>(P, hin, hout, eps, q, prev, partial, Kdyn, save_prev, check, bx, by, gdx,
-                                       rres);
+        body_poisson_tb_f32<H, KC, RS, INC>(P, hin, hout, eps, q, prev, partial, Kdyn, save_prev, check, bx, by, gdx,
+                                            rres, rhs, e0);
         return;
     }
     using G = PBGeom<H, pb_cpt<R, RS>()>;
@@ -1063,14 +1103,16 @@ __global__ void __launch_bounds__(pb_threads<R, H>(), pb_min_blocks<R, H>())
     body_poisson_tb<R, H, KC>(P, hin, hout, eps, q, prev, partial, K, save_prev, check, blockIdx.x, blockIdx.y,
                           gridDim.x);
 }
-// K iterations on the correction to an FP64 anchor (no residual sums; save_prev:
-// psi and J before the last collision into prev)
-template <class R, int H, int KC = 0>
+// K iterations on the correction to the anchor (save_prev: psi and J before the
+// last collision into prev; FP32 with INC, the last launch before a check: the
+// check's block sums instead, see body_poisson_tb_f32)
+template <class R, int H, int KC = 0, bool INC = false>
 __global__ void __launch_bounds__(pb_threads<R, H, true>(), pb_min_blocks<R, H, true>())
     k_poisson_tb_rs(DevParams P, const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ eps,
-                    const R* __restrict__ rres, R* __restrict__ prev, int K, int save_prev) {
-    body_poisson_tb<R, H, KC, true>(P, hin, hout, eps, nullptr, prev, nullptr, K, save_prev, 0, blockIdx.x,
-                                    blockIdx.y, gridDim.x, rres);
+                    const R* __restrict__ rres, R* __restrict__ prev, int K, int save_prev,
+                    double* __restrict__ partial, float* __restrict__ rhs, float* __restrict__ e0) {
+    body_poisson_tb<R, H, KC, true, INC>(P, hin, hout, eps, nullptr, prev, partial, K, save_prev, 0, blockIdx.x,
+                                         blockIdx.y, gridDim.x, rres, rhs, e0);
 }
 
 // final reduction of nblk x NV partials in a fixed order (one block of 256 threads)

@@ -958,13 +958,17 @@ class Sim final : public SimBase {
     // norms; with `rhs`, also the coarse correction's right-hand side.  *noisy: the
     // rounding floor of these increments (the precision's epsilon times the size of
     // delta) is above a tenth of tol -- time to fold delta into the anchor.
-    int rs_check(const double* norms, bool rhs, double tol, double* res, bool* noisy) {
+    int rs_check(const double* norms, bool rhs, double tol, double* res, bool* noisy, int inc_blocks = 0) {
         if constexpr (!is_dual<R>::value) {
-            timer.begin(stream_, KC_REDUCE);
-            k_rs_increment<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(
-                dp_, d_.h[hcur_], d_.psi_prev, d_.partial, rhs ? mgf_[0].rhs : nullptr, rhs ? mgf_[0].psi : nullptr);
-            TRY(launched());
-            TRY(reduce_nv<3>(nblk_));
+            if (inc_blocks > 0) {  // the last iteration launch formed the block sums
+                TRY(reduce_nv<3>(inc_blocks));
+            } else {
+                timer.begin(stream_, KC_REDUCE);
+                k_rs_increment<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(
+                    dp_, d_.h[hcur_], d_.psi_prev, d_.partial, rhs ? mgf_[0].rhs : nullptr, rhs ? mgf_[0].psi : nullptr);
+                TRY(launched());
+                TRY(reduce_nv<3>(nblk_));
+            }
             if (cudaMemcpyAsync(pinned_, d_.result, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream_) !=
                 cudaSuccess)
                 return LB3E_ERR_CUDA;
@@ -1027,8 +1031,11 @@ class Sim final : public SimBase {
         return chunk_;
     }
     // m pseudo-iterations on delta (blocked, rs_chunk() per launch); with save,
-    // psi and J before the last collision go to psi_prev for rs_check
-    int rs_iterations(int m, bool save) {
+    // psi and J before the last collision go to psi_prev for rs_check.  FP32 builds:
+    // a blocked last launch also forms the check's block sums (and, with rhs, the
+    // coarse right-hand side); *inc_blocks is their number (0: rs_check forms them)
+    int rs_iterations(int m, bool save, bool rhs = false, int* inc_blocks = nullptr) {
+        if (inc_blocks) *inc_blocks = 0;
         if constexpr (!is_dual<R>::value) {
             TRY(pb_prepare());
             const dim3 pgrid((p_.nx + PB_TX - 1) / PB_TX, (p_.ny + PB_TY - 1) / PB_TY);
@@ -1036,23 +1043,31 @@ class Sim final : public SimBase {
             for (int k = 0; k < m;) {
                 const int c = m - k < kmax ? m - k : kmax;
                 const int sv = save && k + c == m;
+                const bool inc = sv && c > 1 && std::is_same<R, float>::value && inc_blocks;
+                float* rp = inc && rhs ? mgf_[0].rhs : nullptr;
+                float* ep = inc && rhs ? mgf_[0].psi : nullptr;
+                auto launch = [&](auto kern, int threads, size_t smem) {
+                    kern<<<pgrid, threads, smem, stream_>>>(dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_,
+                                                            d_.psi_prev, c, sv, d_.partial, rp, ep);
+                };
                 timer.begin(stream_, KC_POISSON);
                 if (c == 1)
                     k_poisson_rs<R><<<grid2_, dim3(TX, TY), 0, stream_>>>(dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps,
                                                                           rres_, d_.psi_prev, sv);
                 else if (pb_halo_for(c) == 2)
-                    k_poisson_tb_rs<R, 2><<<pgrid, pb_threads<R, 2, true>(), pb_smem_bytes<R, 2, true>(), stream_>>>(
-                        dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
+                    launch(inc ? k_poisson_tb_rs<R, 2, 0, true> : k_poisson_tb_rs<R, 2>, pb_threads<R, 2, true>(),
+                           pb_smem_bytes<R, 2, true>());
                 else if (c == 4)
-                    k_poisson_tb_rs<R, 4, 4><<<pgrid, pb_threads<R, 4, true>(), pb_smem_bytes<R, 4, true>(), stream_>>>(
-                        dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
+                    launch(inc ? k_poisson_tb_rs<R, 4, 4, true> : k_poisson_tb_rs<R, 4, 4>, pb_threads<R, 4, true>(),
+                           pb_smem_bytes<R, 4, true>());
                 else if (pb_halo_for(c) == 4)
-                    k_poisson_tb_rs<R, 4><<<pgrid, pb_threads<R, 4, true>(), pb_smem_bytes<R, 4, true>(), stream_>>>(
-                        dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
+                    launch(inc ? k_poisson_tb_rs<R, 4, 0, true> : k_poisson_tb_rs<R, 4>, pb_threads<R, 4, true>(),
+                           pb_smem_bytes<R, 4, true>());
                 else if constexpr (pb_smem_bytes<R, 8, true>() <= 227 * 1024)
-                    k_poisson_tb_rs<R, 8><<<pgrid, pb_threads<R, 8, true>(), pb_smem_bytes<R, 8, true>(), stream_>>>(
-                        dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, rres_, d_.psi_prev, c, sv);
+                    launch(inc ? k_poisson_tb_rs<R, 8, 0, true> : k_poisson_tb_rs<R, 8>, pb_threads<R, 8, true>(),
+                           pb_smem_bytes<R, 8, true>());
                 TRY(launched());
+                if (inc) *inc_blocks = (int)(pgrid.x * pgrid.y);
                 poisson_iters_run_ += c;
                 hcur_ ^= 1;
                 k += c;
@@ -1104,10 +1119,11 @@ class Sim final : public SimBase {
                 if (it >= max_iter) break;
                 if (coarse) TRY(lbmg_correct(after_refresh));
                 const int m = max_iter - it < check ? max_iter - it : check;
-                TRY(rs_iterations(m, true));
+                int inc_blocks = 0;
+                TRY(rs_iterations(m, true, coarse, &inc_blocks));
                 it += m;
                 bool noisy = false;
-                TRY(rs_check(norms, coarse, tol, &res, &noisy));
+                TRY(rs_check(norms, coarse, tol, &res, &noisy, inc_blocks));
                 after_refresh = false;
                 if (noisy && res > tol) {  // the exact increment at a fresh anchor instead
                     TRY(anchor_refresh(true, &res, norms, !coarse));
@@ -1141,17 +1157,25 @@ class Sim final : public SimBase {
                     cudaFuncSetAttribute(k_poisson_tb<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)pb_smem_bytes<R, 8>()) != cudaSuccess)
                     return LB3E_ERR_CUDA;
-                if (anchor_ &&
-                    (cudaFuncSetAttribute(k_poisson_tb_rs<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)pb_smem_bytes<R, 2, true>()) != cudaSuccess ||
-                     cudaFuncSetAttribute(k_poisson_tb_rs<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)pb_smem_bytes<R, 4, true>()) != cudaSuccess ||
-                     cudaFuncSetAttribute(k_poisson_tb_rs<R, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)pb_smem_bytes<R, 4, true>()) != cudaSuccess))
-                    return LB3E_ERR_CUDA;
+                if (anchor_) {
+                    auto attr = [](auto kern, size_t bytes) {
+                        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+                               cudaSuccess;
+                    };
+                    if (!attr(k_poisson_tb_rs<R, 2>, pb_smem_bytes<R, 2, true>()) ||
+                        !attr(k_poisson_tb_rs<R, 2, 0, true>, pb_smem_bytes<R, 2, true>()) ||
+                        !attr(k_poisson_tb_rs<R, 4>, pb_smem_bytes<R, 4, true>()) ||
+                        !attr(k_poisson_tb_rs<R, 4, 0, true>, pb_smem_bytes<R, 4, true>()) ||
+                        !attr(k_poisson_tb_rs<R, 4, 4>, pb_smem_bytes<R, 4, true>()) ||
+                        !attr(k_poisson_tb_rs<R, 4, 4, true>, pb_smem_bytes<R, 4, true>()))
+                        return LB3E_ERR_CUDA;
+                }
                 if constexpr (pb_smem_bytes<R, 8, true>() <= 227 * 1024) {
-                    if (anchor_ && cudaFuncSetAttribute(k_poisson_tb_rs<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                        (int)pb_smem_bytes<R, 8, true>()) != cudaSuccess)
+                    if (anchor_ &&
+                        (cudaFuncSetAttribute(k_poisson_tb_rs<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)pb_smem_bytes<R, 8, true>()) != cudaSuccess ||
+                         cudaFuncSetAttribute(k_poisson_tb_rs<R, 8, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)pb_smem_bytes<R, 8, true>()) != cudaSuccess))
                         return LB3E_ERR_CUDA;
                 }
                 pb_ready_ = true;
