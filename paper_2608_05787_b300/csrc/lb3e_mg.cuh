@@ -197,6 +197,69 @@ __global__ void __launch_bounds__(256) k_mg_coarse_solve(MGLevelT<T> L, int swee
         }
 }
 
+// The small levels of a V-cycle in one block: from level lv[0] (its rhs restricted,
+// psi = 0) down to the coarsest and back, each pass a block-strided loop closed by a
+// barrier, with the per-cell arithmetic of k_mg_smooth, k_mg_residual,
+// k_mg_restrict, k_mg_coarse_solve and k_mg_prolong.  These levels hold a few
+// thousand cells or fewer, so one block does them in less time than their ~10
+// launches a level take to issue.
+constexpr int MG_SMALL_MAX = 12, MG_SMALL_CELLS = 4096, MG_SMALL_THREADS = 1024;
+template <class T>
+struct MGSmall {
+    MGLevelT<T> lv[MG_SMALL_MAX];
+    int n;  // levels lv[0 .. n-1], lv[n-1] the coarsest
+};
+template <class T>
+__device__ __forceinline__ void mgb_smooth(const MGLevelT<T>& L, int sweeps) {
+    const int n = L.nx * L.ny;
+    for (int s = 0; s < sweeps; ++s)
+        for (int color = 0; color < 2; ++color) {
+            for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                const int y = c / L.nx, x = c - y * L.nx;
+                if (((x + y) & 1) != color) continue;
+                L.psi[c] = (L.rhs[c] + mg_offdiag(L, x, y, c)) * L.idg[c];
+            }
+            __syncthreads();
+        }
+}
+template <class T>
+__global__ void __launch_bounds__(MG_SMALL_THREADS) k_mg_small_cycle(MGSmall<T> S) {
+    for (int l = 0; l + 1 < S.n; ++l) {
+        const MGLevelT<T>& F = S.lv[l];
+        const MGLevelT<T>& C = S.lv[l + 1];
+        mgb_smooth(F, 2);
+        const int nf = F.nx * F.ny;
+        for (int c = threadIdx.x; c < nf; c += blockDim.x) {
+            const int y = c / F.nx, x = c - y * F.nx;
+            F.res[c] = F.rhs[c] - (F.dg[c] * F.psi[c] - mg_offdiag(F, x, y, c));
+        }
+        __syncthreads();
+        const int nc = C.nx * C.ny;
+        for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+            const int y = c / C.nx, x = c - y * C.nx;
+            const int f = 2 * y * F.nx + 2 * x;
+            C.rhs[c] = F.res[f] + F.res[f + 1] + F.res[f + F.nx] + F.res[f + F.nx + 1];
+            C.psi[c] = T(0);
+        }
+        __syncthreads();
+    }
+    mgb_smooth(S.lv[S.n - 1], 50);  // the coarsest level (the sweeps of k_mg_coarse_solve)
+    for (int l = S.n - 2; l >= 0; --l) {
+        const MGLevelT<T>& F = S.lv[l];
+        const MGLevelT<T>& C = S.lv[l + 1];
+        const int nf = F.nx * F.ny;
+        for (int c = threadIdx.x; c < nf; c += blockDim.x) {
+            const int y = c / F.nx, x = c - y * F.nx;
+            const int cx0 = x >> 1, cy0 = y >> 1;
+            const int sx = (x & 1) ? 1 : -1, sy = (y & 1) ? 1 : -1;
+            F.psi[c] += T(0.5625) * mg_coarse_at(C, cx0, cy0) + T(0.1875) * mg_coarse_at(C, cx0 + sx, cy0) +
+                        T(0.1875) * mg_coarse_at(C, cx0, cy0 + sy) + T(0.0625) * mg_coarse_at(C, cx0 + sx, cy0 + sy);
+        }
+        __syncthreads();
+        mgb_smooth(F, 2);
+    }
+}
+
 // level-0 inputs: eps (R) -> FP64; rhs = q plus the electrode terms 2 eps_C V of
 // the wall rows (the coarse error equations are homogeneous)
 template <class R>

@@ -743,7 +743,15 @@ class Sim final : public SimBase {
             k_mg_restrict<float><<<mg_grid(1), blk, 0, stream_>>>(f0, mgf_[1]);
             TRY(done());
         }
-        for (int l = first; l + 1 < nl; ++l) {
+        if (nl == 1) {
+            begin();
+            k_mg_coarse_solve<float><<<1, 256, 0, stream_>>>(mgf_[0], 2);
+            return done();
+        }
+        // the small levels (from ls on, at most MG_SMALL_CELLS cells) in one block
+        int ls = first;
+        while (ls + 1 < nl && (size_t)mgf_[ls].nx * mgf_[ls].ny > (size_t)MG_SMALL_CELLS) ++ls;
+        for (int l = first; l < ls; ++l) {
             TRY(smooth(l, 2));
             begin();
             k_mg_residual<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], nullptr);
@@ -752,10 +760,13 @@ class Sim final : public SimBase {
             k_mg_restrict<float><<<mg_grid(l + 1), blk, 0, stream_>>>(mgf_[l], mgf_[l + 1]);
             TRY(done());
         }
+        MGSmall<float> small{};
+        small.n = nl - ls;
+        for (int l = ls; l < nl; ++l) small.lv[l - ls] = mgf_[l];
         begin();
-        k_mg_coarse_solve<float><<<1, 256, 0, stream_>>>(mgf_[nl - 1], nl == 1 ? 2 : 50);
+        k_mg_small_cycle<float><<<1, MG_SMALL_THREADS, 0, stream_>>>(small);
         TRY(done());
-        for (int l = nl - 2; l >= 0; --l) {
+        for (int l = ls - 1; l >= 0; --l) {
             begin();
             k_mg_prolong<float><<<mg_grid(l), blk, 0, stream_>>>(mgf_[l], mgf_[l + 1]);
             TRY(done());
