@@ -277,6 +277,7 @@ static __global__ void __launch_bounds__(256) k_mg_load(MGLevel L, const R* __re
 }
 
 // E = -grad psi with the isotropic stencil of Eq. 33; ghosts 2V - psi at electrodes
+// (FP64 output: all in FP64)
 __device__ __forceinline__ double mg_psi_ghost(const MGLevel& L, int x, int y, double vb, double vt) {
     x = x < 0 ? x + L.nx : (x >= L.nx ? x - L.nx : x);
     if (y < 0) return 2.0 * vb - L.psi[x];
@@ -290,30 +291,53 @@ static __global__ void __launch_bounds__(256) k_mg_fields(MGLevel L, double vb, 
     if (x >= L.nx || y >= L.ny) return;
     const int c = y * L.nx + x;
     const size_t N = (size_t)L.nx * L.ny;
-    if constexpr (std::is_same<R, double>::value) {
-        double ax = 0.0, ay = 0.0;
+    double ax = 0.0, ay = 0.0;
 #pragma unroll
-        for (int j = 0; j < 9; ++j) {
-            const double v = mg_psi_ghost(L, x + cx(j), y + cy(j), vb, vt);
-            ax += wgt<double>(j) * cx(j) * v;
-            ay += wgt<double>(j) * cy(j) * v;
-        }
-        E[c] = R(-(ax * 3.0) + ex);  // / cs^2 (a multiply: FP64 division is slow here)
-        E[N + c] = R(-(ay * 3.0) + ey);
-    } else {
-        // FP32 output: differences from the centre in FP64 (the electrode profile
-        // makes psi large against its neighbour differences), weighted sums in FP32
-        const double pc = L.psi[c];
-        float ax = 0.f, ay = 0.f;
-#pragma unroll
-        for (int j = 1; j < 9; ++j) {
-            const float d = (float)(mg_psi_ghost(L, x + cx(j), y + cy(j), vb, vt) - pc);
-            cacc(ax, cx(j), wgt<float>(j), d);
-            cacc(ay, cy(j), wgt<float>(j), d);
-        }
-        E[c] = R(-(double)(ax * 3.0f) + ex);  // / cs^2
-        E[N + c] = R(-(double)(ay * 3.0f) + ey);
+    for (int j = 0; j < 9; ++j) {
+        const double v = mg_psi_ghost(L, x + cx(j), y + cy(j), vb, vt);
+        ax += wgt<double>(j) * cx(j) * v;
+        ay += wgt<double>(j) * cy(j) * v;
     }
+    E[c] = R(-(ax * 3.0) + ex);  // / cs^2 (a multiply: FP64 division is slow here)
+    E[N + c] = R(-(ay * 3.0) + ey);
+}
+// FP32 output.  The electrode profile makes psi large against its neighbour
+// differences, so the differences need more than FP32: the block stages psi (ghosts
+// included) of its tile and one-cell ring as hi + lo FP32 pairs, one FP64 split a
+// cell (FP64 runs at a small fraction of the FP32 rate), and forms each difference
+// as (hi_n - hi_c) + (lo_n - lo_c) in FP32; weighted sums in FP32
+template <class R>
+static __global__ void __launch_bounds__(256) k_mg_fields_f32(MGLevel L, double vb, double vt, double ex, double ey,
+                                                              R* __restrict__ E) {
+    constexpr int SX = 34, SY = 10;  // blockDim (32, 8) and a one-cell ring
+    __shared__ float shi[SY * SX], slo[SY * SX];
+    const int x0 = blockIdx.x * blockDim.x, y0 = blockIdx.y * blockDim.y;
+    for (int k = threadIdx.x + blockDim.x * threadIdx.y; k < SX * SY; k += blockDim.x * blockDim.y) {
+        const int ly = k / SX, lx = k - ly * SX;
+        const int gy = y0 + ly - 1, gx = x0 + lx - 1;
+        double v = 0.0;
+        if (gy >= -1 && gy <= L.ny) v = mg_psi_ghost(L, gx, gy, vb, vt);  // rows beyond the ring row: unused
+        const float hi = (float)v;
+        shi[k] = hi;
+        slo[k] = (float)(v - (double)hi);
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= L.nx || y >= L.ny) return;
+    const int c = y * L.nx + x;
+    const size_t N = (size_t)L.nx * L.ny;
+    const int sc = (threadIdx.y + 1) * SX + threadIdx.x + 1;
+    const float hc = shi[sc], lc = slo[sc];
+    float ax = 0.f, ay = 0.f;
+#pragma unroll
+    for (int j = 1; j < 9; ++j) {
+        const int sn = sc + cy(j) * SX + cx(j);
+        const float d = (shi[sn] - hc) + (slo[sn] - lc);
+        cacc(ax, cx(j), wgt<float>(j), d);
+        cacc(ay, cy(j), wgt<float>(j), d);
+    }
+    E[c] = R(-(ax * 3.0f) + (float)ex);  // / cs^2
+    E[N + c] = R(-(ay * 3.0f) + (float)ey);
 }
 
 // initial guess: the linear electrode profile

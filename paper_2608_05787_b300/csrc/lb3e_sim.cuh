@@ -675,7 +675,10 @@ class Sim final : public SimBase {
         }
         last_iters_ = cycles;
         timer.begin(stream_, KC_FIELDS);
-        k_mg_fields<R><<<mg_grid(0), blk, 0, stream_>>>(mg_[0], vb, vt, p_.E_ext[0], p_.E_ext[1], d_.E);
+        if constexpr (std::is_same<R, double>::value)
+            k_mg_fields<R><<<mg_grid(0), blk, 0, stream_>>>(mg_[0], vb, vt, p_.E_ext[0], p_.E_ext[1], d_.E);
+        else
+            k_mg_fields_f32<R><<<mg_grid(0), blk, 0, stream_>>>(mg_[0], vb, vt, p_.E_ext[0], p_.E_ext[1], d_.E);
         return launched();
     }
 
