@@ -14,6 +14,7 @@
 // bounce-back at y walls).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the tensor-map descriptor type of the TMA copies)
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -1095,6 +1096,51 @@ __device__ __forceinline__ void cp_async16(T* smem, const T* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Tensor-memory-accelerator (TMA) copies of boxes of a 2-D or 3-D array into shared
+// memory, completing on an mbarrier with transaction counting (sm_90 and later)
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"((unsigned)__cvta_generic_to_shared(bar)),
+                 "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"((unsigned)__cvta_generic_to_shared(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+        "[%2];\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"((unsigned)__cvta_generic_to_shared(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+// wait for phase `parity` of the barrier, at most `limit` polls; false on giving up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int limit) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    for (int i = 0; i < limit; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// polls of a TMA wait before a block gives up, sets the error flag and returns
+constexpr int TMA_WAIT_LIMIT = 1 << 22;
+
 template <class R, int H, int KC = 0>
 __global__ void __launch_bounds__(pb_threads<R, H>(), pb_min_blocks<R, H>())
     k_poisson_tb(DevParams P, const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ eps,
@@ -1241,7 +1287,10 @@ template <class R, class S, int BY = 8>
 __device__ __forceinline__ void body_fused(const DevParams P, const S* __restrict__ pin, S* __restrict__ pout,
                                                    const R* __restrict__ phi, const R* __restrict__ qf,
                                                    const R* __restrict__ E, R* __restrict__ prev,
-                                                   R* __restrict__ diag, int first, int write_diag, int bx, int by, int gdx) {
+                                                   R* __restrict__ diag, int first, int write_diag, int bx, int by, int gdx,
+                                                   const CUtensorMap* tm_pop = nullptr,
+                                                   const CUtensorMap* tm_prev = nullptr,
+                                                   const CUtensorMap* tm_q = nullptr, int* err = nullptr) {
     constexpr int PX = TX + 4, PY = BY + 4;  // phi tile, 2-ring
     constexpr int MX = TX + 2, MY = BY + 2;  // mu / E tile, 1-ring
     __shared__ R sphi[3][PY * PX];
@@ -1264,11 +1313,30 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
     // both types), else one element per copy (4- or 8-byte types) or, for 2-byte
     // storage, plain loads later; slot layout [plane][ty * TX + tx]
     constexpr bool kStage = fused_prefetch<S>();
-    extern __shared__ __align__(16) unsigned char fz_raw[];
+    extern __shared__ __align__(128) unsigned char fz_raw[];
+    __shared__ __align__(8) uint64_t fz_bar;  // the TMA staging's barrier
     S* sp = reinterpret_cast<S*>(fz_raw);                                      // [45][TX * BY]
     R* sr = reinterpret_cast<R*>(fz_raw + (size_t)45 * TX * BY * sizeof(S));  // [9][TX * BY]
     bool staged = false;  // the same for the whole block (depends on nx only)
-    if constexpr (kStage) {
+    const bool tma = kStage && tm_pop != nullptr;
+    if (tma) {
+        // one thread copies the tile of every needed population plane, of the 8 d/dt
+        // planes and of the charge with the tensor memory accelerator (boxes of 32 x
+        // BY cells; parts beyond the lattice arrive as zeros and are never used)
+        staged = true;
+        if (tid == 0) {
+            constexpr unsigned PB = TX * BY * sizeof(S), RB = TX * BY * sizeof(R);
+            constexpr int NP = anchored<S>() ? 42 : 45;
+            mbar_init(&fz_bar, 1);
+            mbar_arrive_expect_tx(&fz_bar, NP * PB + 9 * RB);
+            for (int k = 0; k < 45; ++k) {
+                if (anchored<S>() && (k == 9 || k == 18 || k == 27)) continue;  // rest populations rebuilt
+                tma_load_3d(sp + k * (TX * BY), tm_pop, x0, y0, k, &fz_bar);
+            }
+            tma_load_3d(sr, tm_prev, x0, y0, 0, &fz_bar);
+            tma_load_2d(sr + 8 * (TX * BY), tm_q, x0, y0, &fz_bar);
+        }
+    } else if constexpr (kStage) {
         constexpr int VS = 16 / (int)sizeof(S), VR = 16 / (int)sizeof(R);  // cells per 16-byte segment
         constexpr int SGS = TX / VS, SGR = TX / VR;                        // segments per tile row
         auto rplane = [&](int k) -> const R* { return k < 8 ? prev + (size_t)k * N : qf; };
@@ -1299,8 +1367,8 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
                 for (int k = 0; k < 9; ++k) cp_async(sr + k * (TX * BY) + tid, rplane(k) + cs);
             }
         }
-        cp_async_commit();
     }
+    if (kStage && !tma) cp_async_commit();
     // population k (plane k of the set-major layout) of this cell
     auto popk = [&](int k, unsigned cc) -> R {
         if (kStage && staged) return (R)sp[k * (TX * BY) + tid];
@@ -1343,7 +1411,14 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
             smu[i][k] = chem_pot<R>(P, i, ph, lap_tile<R>(sphi[i], PX, ly + 1, lx + 1), e2, c24);
         }
     }
-    if constexpr (kStage) cp_async_wait_all();  // slots are published by the barrier
+    if (tma) {  // every thread sees the copies complete (the barrier's phase 0)
+        if (!mbar_wait(&fz_bar, 0, TMA_WAIT_LIMIT)) {
+            if (err) atomicExch(err, 1);
+            return;
+        }
+    } else if constexpr (kStage) {
+        cp_async_wait_all();  // slots are published by the barrier
+    }
     __syncthreads();
     // ghost rows of mu mirror the in-domain row they face
     if (P.bc_y != 0) {
@@ -1615,8 +1690,12 @@ template <class R, class S, int BY = 8>
 __global__ void __launch_bounds__(TX * BY, fused_min_blocks<R, BY>()) k_fused(DevParams P, const S* __restrict__ pin, S* __restrict__ pout,
                                                    const R* __restrict__ phi, const R* __restrict__ qf,
                                                    const R* __restrict__ E, R* __restrict__ prev,
-                                                   R* __restrict__ diag, int first, int write_diag) {
-    body_fused<R, S, BY>(P, pin, pout, phi, qf, E, prev, diag, first, write_diag, blockIdx.x, blockIdx.y, gridDim.x);
+                                                   R* __restrict__ diag, int first, int write_diag,
+                                                   const __grid_constant__ CUtensorMap tm_pop,
+                                                   const __grid_constant__ CUtensorMap tm_prev,
+                                                   const __grid_constant__ CUtensorMap tm_q, int use_tma, int* err) {
+    body_fused<R, S, BY>(P, pin, pout, phi, qf, E, prev, diag, first, write_diag, blockIdx.x, blockIdx.y, gridDim.x,
+                         use_tma ? &tm_pop : nullptr, &tm_prev, &tm_q, err);
 }
 
 // ---------------------------------------------------------------- initial populations

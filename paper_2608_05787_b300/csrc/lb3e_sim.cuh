@@ -191,6 +191,8 @@ class Sim final : public SimBase {
         }
         if (cudaHostAlloc(reinterpret_cast<void**>(&pinned_), 64 * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
             return LB3E_ERR_CUDA;
+        pinned_[63] = 0.0;
+        TRY(memset_async(err_flag(), sizeof(int)));
         // phi, u, q -> device fields (through the FP64 staging area)
         TRY(upload(phi, 3 * N_, d_.phi));
         if (u) {
@@ -533,23 +535,82 @@ class Sim final : public SimBase {
 
     void fused_launch(int first, int write_diag) {
         auto grid = [&](int rows) { return dim3((p_.nx + TX - 1) / TX, (p_.ny + rows - 1) / rows); };
+        const int by = ftile_ == 4 && !is_dual<R>::value ? 4 : (ftile_ == 16 && std::is_same<R, float>::value ? 16 : 8);
+        const int tma = tma_prepare(by) ? 1 : 0;
         if constexpr (!is_dual<R>::value) {
-            if (ftile_ == 4) {
+            if (by == 4) {
                 k_fused<R, S, 4><<<grid(4), dim3(TX, 4), fused_dyn_smem<R, S, 4>(), stream_>>>(
-                    dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q, d_.E, d_.prev, d_.diag, first, write_diag);
+                    dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q, d_.E, d_.prev, d_.diag, first, write_diag,
+                    tm_pop_[cur_], tm_prev_, tm_q_, tma, err_flag());
                 return;
             }
         }
         if constexpr (std::is_same<R, float>::value) {
-            if (ftile_ == 16) {
+            if (by == 16) {
                 k_fused<R, S, 16><<<grid(16), dim3(TX, 16), fused_dyn_smem<R, S, 16>(), stream_>>>(
-                    dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q, d_.E, d_.prev, d_.diag, first, write_diag);
+                    dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q, d_.E, d_.prev, d_.diag, first, write_diag,
+                    tm_pop_[cur_], tm_prev_, tm_q_, tma, err_flag());
                 return;
             }
         }
         k_fused<R, S><<<grid2_, dim3(TX, TY), fused_dyn_smem<R, S>(), stream_>>>(
-            dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q, d_.E, d_.prev, d_.diag, first, write_diag);
+            dp_, d_.pop[cur_], d_.pop[cur_ ^ 1], d_.phi, d_.q, d_.E, d_.prev, d_.diag, first, write_diag,
+            tm_pop_[cur_], tm_prev_, tm_q_, tma, err_flag());
     }
+
+    // TMA descriptors of the fused pass's staging, made once for the tile height in
+    // use: the two population buffers ([45][ny][nx] in the storage type), the 8 d/dt
+    // planes and the charge, in boxes of 32 x BY cells.  Needs rows of a multiple of
+    // 16 bytes (tensor-map strides); otherwise, or if the driver offers no encoder,
+    // the pass stages with per-thread cp.async copies.  True when the descriptors for
+    // BY are ready.
+    bool tma_prepare(int BY) {
+        if constexpr (is_dual<R>::value || !fused_prefetch<S>()) {
+            return false;
+        } else {
+            if (tma_by_ == BY) return true;
+            tma_by_ = 0;
+            if (p_.nx % (16 / (int)sizeof(S)) != 0 || p_.nx % (16 / (int)sizeof(R)) != 0) return false;
+            using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                        const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                        CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+            static Encode encode = [] {
+                void* f = nullptr;
+                cudaDriverEntryPointQueryResult q{};
+                if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                        cudaSuccess ||
+                    q != cudaDriverEntryPointSuccess)
+                    f = nullptr;
+                return reinterpret_cast<Encode>(f);
+            }();
+            if (!encode) return false;
+            auto type_of = [](size_t bytes, bool bf16) {
+                return bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                  : (bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                : (bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16));
+            };
+            const cuuint64_t nx = (cuuint64_t)p_.nx, ny = (cuuint64_t)p_.ny;
+            const cuuint32_t one[3] = {1, 1, 1};
+            auto make = [&](CUtensorMap* m, void* base, size_t es, bool bf16, cuuint32_t rank, cuuint64_t planes,
+                            cuuint32_t zbox) {
+                const cuuint64_t dims[3] = {nx, ny, planes};
+                const cuuint64_t strides[2] = {nx * es, nx * ny * es};
+                const cuuint32_t box[3] = {(cuuint32_t)TX, (cuuint32_t)BY, zbox};
+                return encode(m, type_of(es, bf16), rank, base, dims, strides, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            };
+            constexpr bool bf = std::is_same<S, __nv_bfloat16>::value;
+            if (!make(&tm_pop_[0], d_.pop[0], sizeof(S), bf, 3, 45, 1) ||
+                !make(&tm_pop_[1], d_.pop[1], sizeof(S), bf, 3, 45, 1) ||
+                !make(&tm_prev_, d_.prev, sizeof(R), false, 3, 8, 8) || !make(&tm_q_, d_.q, sizeof(R), false, 2, 1, 1))
+                return false;
+            tma_by_ = BY;
+            return true;
+        }
+    }
+    // a kernel's error flag (a timed-out wait), read back by sync()
+    int* err_flag() { return reinterpret_cast<int*>(d_.result + 63); }
 
     // --- used by Batch: device buffers, and bookkeeping after steps run elsewhere
     const DevState<R, S>& dev() const { return d_; }
@@ -583,7 +644,22 @@ class Sim final : public SimBase {
         timer.end(stream_);
         return cudaGetLastError() == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
     }
-    int sync() { return cudaStreamSynchronize(stream_) == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA; }
+    // wait for the stream; a kernel that gave up a bounded wait (error flag) fails it
+    int sync() {
+        if (pinned_) {
+            int* fl = reinterpret_cast<int*>(pinned_ + 63);
+            if (cudaMemcpyAsync(fl, err_flag(), sizeof(int), cudaMemcpyDeviceToHost, stream_) != cudaSuccess)
+                return LB3E_ERR_CUDA;
+            if (cudaStreamSynchronize(stream_) != cudaSuccess) return LB3E_ERR_CUDA;
+            if (*fl) {
+                *fl = 0;
+                cudaMemsetAsync(err_flag(), 0, sizeof(int), stream_);
+                return LB3E_ERR_CUDA;
+            }
+            return LB3E_OK;
+        }
+        return cudaStreamSynchronize(stream_) == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
+    }
     int memset_async(void* p, size_t b) { return cudaMemsetAsync(p, 0, b, stream_) == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA; }
     int copy(void* d, const void* s, size_t b) {
         return cudaMemcpyAsync(d, s, b, cudaMemcpyDefault, stream_) == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
@@ -1327,6 +1403,8 @@ class Sim final : public SimBase {
     // double-float in the FP32 builds, with the refresh's coefficients in that form
     using AT = typename AnchorOf<R>::type;
     AT* anchor_ = nullptr;
+    CUtensorMap tm_pop_[2]{}, tm_prev_{}, tm_q_{};  // TMA descriptors of the fused pass (tma_prepare)
+    int tma_by_ = 0;                                // the tile height they were made for (0: none)
     AT* anchor_alt_ = nullptr;   // FP32 builds: the anchor planes the next refresh writes
     bool delta_stale_ = false;   // delta was folded into the anchor but not yet cleared
     R* phi_alt_ = nullptr;  // the set of phi planes the next moments pass writes
