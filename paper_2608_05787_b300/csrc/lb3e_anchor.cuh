@@ -395,6 +395,23 @@ __global__ void __launch_bounds__(256) k_anchor_efield(DevParams P, const R* __r
 }
 
 // population j of h = a + delta as FP64
+// The starting state of a time step's solve, extrapolated linearly in time: with h =
+// a + delta the state the last step's solve ended at and hs the one the step before
+// ended at, delta += h - hs (the solve starts from 2h - hs); then hs = h.  With
+// extrap = 0 only hs = h (the first step after initialisation).  h and hs in R: the
+// extrapolation is a starting guess, so its rounding does not matter.
+template <class R>
+__global__ void k_anchor_extrapolate(const typename AnchorOf<R>::type* __restrict__ a, R* __restrict__ d,
+                                     R* __restrict__ hs, size_t n, int extrap) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    R h;
+    if constexpr (std::is_same<R, float>::value) h = __fadd_rn(a[i].hi, __fadd_rn(a[i].lo, d[i]));
+    else h = R(anchor_value(a[i]) + (double)d[i]);
+    if (extrap) d[i] += h - hs[i];
+    hs[i] = h;
+}
+
 template <class R>
 __global__ void k_anchor_pop(double* __restrict__ dst, const typename AnchorOf<R>::type* __restrict__ a,
                              const R* __restrict__ d, size_t n) {

@@ -29,7 +29,7 @@ class Sim final : public SimBase {
     // workspace layout (byte offsets), computed identically by bytes() and the constructor
     struct Layout {
         size_t pop[2], h[2], phi, qt, q, eps, E, prev, diag, psi_prev, partial, result, stage, mg, ion[2], ionst,
-            anchor, rres, ja, phi2, anchor2, total;
+            anchor, rres, ja, phi2, anchor2, hprev, total;
     };
     static Layout layout(const lb3e_params& p) {
         const size_t N = (size_t)p.nx * p.ny;
@@ -88,6 +88,9 @@ class Sim final : public SimBase {
         // FP32 builds: a second set of anchor planes (the one-pass refresh writes the
         // folded anchor there while neighbouring blocks read the current one)
         L.anchor2 = take(9 * (std::is_same<R, float>::value ? na : 0) * sizeof(double));
+        // the state the step before last ended at (the time extrapolation of the
+        // solve's starting state)
+        L.hprev = take(9 * na * sizeof(R));
         L.total = o;
         return L;
     }
@@ -126,6 +129,7 @@ class Sim final : public SimBase {
         if (prm.electric && prm.potential_solver >= 2) {
             anchor_ = reinterpret_cast<AT*>(b + L_.anchor);
             if (std::is_same<R, float>::value) anchor_alt_ = reinterpret_cast<AT*>(b + L_.anchor2);
+            hprev_ = reinterpret_cast<R*>(b + L_.hprev);
             rres_ = reinterpret_cast<R*>(b + L_.rres);
             ja_ = reinterpret_cast<R*>(b + L_.ja);
             const double ith = 1.0 / dp_.tau_h, w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w5 = 1.0 / 36.0;
@@ -193,6 +197,7 @@ class Sim final : public SimBase {
             return LB3E_ERR_CUDA;
         pinned_[63] = 0.0;
         TRY(memset_async(err_flag(), sizeof(int)));
+        hprev_valid_ = 0;  // the first step's solve starts from the initial solution
         // phi, u, q -> device fields (through the FP64 staging area)
         TRY(upload(phi, 3 * N_, d_.phi));
         if (u) {
@@ -270,7 +275,12 @@ class Sim final : public SimBase {
                     TRY(launched());
                 }
             }
-            if (p_.electric) TRY(potential());
+            if (p_.electric) {
+                in_step_ = true;
+                const int rc = potential();
+                in_step_ = false;
+                TRY(rc);
+            }
             timer.begin(stream_, KC_FUSED);
             fused_launch(step_ == 0 ? 1 : 0, (last || p_.ions) ? 1 : 0);
             TRY(launched());
@@ -453,7 +463,7 @@ class Sim final : public SimBase {
     // snapshot: current pops, current h, then phi..psi_prev fields, then a trailer
     size_t state_bytes() const override {
         return 45 * N_ * sizeof(S) + 9 * N_ * sizeof(R) + fields_bytes() + ion_bytes() + anchor_bytes() +
-               4 * sizeof(int64_t);
+               hprev_bytes() + 5 * sizeof(int64_t);
     }
     int save(void* dst) override {
         char* o = static_cast<char*>(dst);
@@ -470,11 +480,13 @@ class Sim final : public SimBase {
             TRY(copy(o, nion_, 6 * N_ * sizeof(R)));
             o += 6 * N_ * sizeof(R);
         }
-        if (anchor_) {  // the FP64 anchor of the potential populations (h = anchor + the planes above)
+        if (anchor_) {  // the anchor of the potential populations (h = anchor + the planes above)
             TRY(copy(o, anchor_, anchor_bytes()));
             o += anchor_bytes();
+            TRY(copy(o, hprev_, hprev_bytes()));  // the time extrapolation's previous state
+            o += hprev_bytes();
         }
-        int64_t trailer[4] = {step_, last_iters_, last_conv_, 0};
+        int64_t trailer[5] = {step_, last_iters_, last_conv_, 0, hprev_valid_};
         std::memcpy(&trailer[3], &last_res_, sizeof(double));
         TRY(copy(o, trailer, sizeof trailer));
         return sync();
@@ -500,14 +512,17 @@ class Sim final : public SimBase {
         if (anchor_) {
             TRY(copy(anchor_, s, anchor_bytes()));
             s += anchor_bytes();
+            TRY(copy(hprev_, s, hprev_bytes()));
+            s += hprev_bytes();
         }
-        int64_t trailer[4];
+        int64_t trailer[5];
         TRY(copy(trailer, s, sizeof trailer));
         TRY(sync());
         step_ = trailer[0];
         last_iters_ = (int)trailer[1];
         last_conv_ = (int)trailer[2];
         std::memcpy(&last_res_, &trailer[3], sizeof(double));
+        hprev_valid_ = (int)trailer[4];
         return LB3E_OK;
     }
 
@@ -638,6 +653,7 @@ class Sim final : public SimBase {
     }
     size_t ion_bytes() const { return p_.ions ? 24 * N_ * sizeof(R) : 0; }
     size_t anchor_bytes() const { return anchor_ ? 9 * N_ * sizeof(AT) : 0; }
+    size_t hprev_bytes() const { return anchor_ ? 9 * N_ * sizeof(R) : 0; }
     static unsigned blocks1(size_t n) { return (unsigned)((n + 255) / 256); }
     int launched() {
         ++launches;
@@ -1179,6 +1195,15 @@ class Sim final : public SimBase {
         const bool coarse = p_.potential_solver == 2 && fixed <= 0;
         if (coarse) TRY(lbmg_setup());
         double norms[2] = {0.0, 0.0}, res = -1.0;
+        if constexpr (!is_dual<R>::value) {
+            if (fixed <= 0 && in_step_) {  // start from 2 h_n - h_{n-1} (fixed point and test unchanged)
+                timer.begin(stream_, KC_OTHER);
+                k_anchor_extrapolate<R><<<blocks1(9 * N_), 256, 0, stream_>>>(anchor_, d_.h[hcur_], hprev_, 9 * N_,
+                                                                                hprev_valid_);
+                TRY(launched());
+                hprev_valid_ = 1;
+            }
+        }
         TRY(anchor_refresh(fixed <= 0, &res, norms, !coarse));
         int it = 0;
         if (fixed > 0) {
@@ -1407,6 +1432,9 @@ class Sim final : public SimBase {
     int tma_by_ = 0;                                // the tile height they were made for (0: none)
     AT* anchor_alt_ = nullptr;   // FP32 builds: the anchor planes the next refresh writes
     bool delta_stale_ = false;   // delta was folded into the anchor but not yet cleared
+    R* hprev_ = nullptr;         // the state the last step's solve started from (see k_anchor_extrapolate)
+    int hprev_valid_ = 0;        // hprev_ holds the state after the previous step's solve
+    bool in_step_ = false;       // a time step's solve (extrapolated from the two before)
     R* phi_alt_ = nullptr;  // the set of phi planes the next moments pass writes
     AnchorCoef acoef_{};
     R* rres_ = nullptr;         // the anchor's increment over one pseudo-iteration
