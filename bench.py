@@ -93,7 +93,7 @@ WORDS_3D = {"fused": 187, "poisson": 32, "moments": 67}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lb3e", choices=["lb3e", "reference"])
     ap.add_argument("--workload", default="deformation",
