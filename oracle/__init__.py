@@ -114,6 +114,12 @@ def lib():
         L.orc_step_count.argtypes = [C.c_void_p]
         L.orc_perturb.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_uint64]
         L.orc_round_storage.argtypes = [C.c_void_p, C.c_int]
+        L.orc_clone.restype = C.c_void_p
+        L.orc_clone.argtypes = [C.c_void_p]
+        L.orc_get_state_vector.argtypes = [C.c_void_p, dp]
+        L.orc_set_state_vector.argtypes = [C.c_void_p, dp]
+        L.orc_adjoint_step.argtypes = [C.c_void_p, dp, dp, dp]
+        L.orc_adjoint_init.argtypes = [C.POINTER(_Params), dp, dp, dp, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -124,6 +130,15 @@ def _ptr(a):
 
 def _c64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+# reverse mode: planes of the state vector X = (g, f, l, h, E, (phi_i u)^{n-1}, (q u)^{n-1})
+# and the parameter slots of dJ/dtheta
+STATE_PLANES = dict(g=(0, 9), f=(9, 36), l=(36, 45), h=(45, 54), E=(54, 56), prev_phiu=(56, 62),
+                    prev_qu=(62, 64))
+N_STATE = 64
+ADJ_PARAMS = ("V_bottom", "V_top", "eps1", "eps2", "eps3", "sigma1", "sigma2", "sigma3",
+              "gamma12", "gamma13", "gamma23")
 
 
 def make_params(p: dict) -> _Params:
@@ -209,6 +224,37 @@ class Oracle:
         lib().orc_round_storage(self._h, {"fp32": 1, "fp16": 2, "bf16": 3}[fmt])
         return self
 
+    def clone(self) -> "Oracle":
+        """An independent copy of the current state."""
+        o = Oracle.__new__(Oracle)
+        o.params, o.nx, o.ny, o._keep, o._p = dict(self.params), self.nx, self.ny, self._keep, self._p
+        o._h = C.c_void_p(lib().orc_clone(self._h))
+        return o
+
+    def state_vector(self) -> np.ndarray:
+        """The state X as (64, ny, nx) planes (STATE_PLANES)."""
+        out = np.empty((N_STATE, self.ny, self.nx))
+        lib().orc_get_state_vector(self._h, _ptr(out))
+        return out
+
+    def set_state_vector(self, x) -> "Oracle":
+        xa = _c64(x)
+        assert xa.shape == (N_STATE, self.ny, self.nx)
+        lib().orc_set_state_vector(self._h, _ptr(xa))
+        return self
+
+    def adjoint_step(self, a_in) -> tuple[np.ndarray, np.ndarray]:
+        """For the step from this state: (dX'/dX)^T a_in and (dX'/dtheta)^T a_in (the
+        ADJ_PARAMS slots).  The state is left unchanged."""
+        a = _c64(a_in)
+        assert a.shape == (N_STATE, self.ny, self.nx)
+        out = np.empty_like(a)
+        dpar = np.zeros(len(ADJ_PARAMS))
+        if lib().orc_adjoint_step(self._h, _ptr(a), _ptr(out), _ptr(dpar)) != 0:
+            raise ValueError("no reverse mode for this configuration (ions, Debye-Hueckel closure, FD "
+                             "potential or a residual-controlled potential)")
+        return out, dpar
+
     def last_poisson(self):
         it, res, conv = C.c_int(0), C.c_double(0), C.c_int(0)
         lib().orc_last_poisson(self._h, C.byref(it), C.byref(res), C.byref(conv))
@@ -219,6 +265,78 @@ class Oracle:
         it, res, conv = C.c_int(0), C.c_double(0), C.c_int(0)
         lib().orc_last_poisson(self._h, C.byref(it), C.byref(res), C.byref(conv))
         return conv.value == -1
+
+
+def adjoint_init(params: dict, phi, a_in, u=None, q=None) -> tuple[np.ndarray, np.ndarray]:
+    """Transpose of the state's creation from phi (u, q held fixed, noise additive):
+    (dX0/dtheta)^T a_in over ADJ_PARAMS and (dX0/dphi)^T a_in as (3, ny, nx)."""
+    ph, ua, qa, a = _c64(phi), _c64(u), _c64(q), _c64(a_in)
+    pr = make_params(params)
+    dpar = np.zeros(len(ADJ_PARAMS))
+    dphi = np.zeros_like(ph)
+    if lib().orc_adjoint_init(C.byref(pr), _ptr(ph), _ptr(ua), _ptr(qa), _ptr(a), _ptr(dpar), _ptr(dphi)) != 0:
+        raise ValueError("no reverse mode for this configuration")
+    return dpar, dphi
+
+
+def deformation_seed(phi_of_state: np.ndarray, inner: int, matrix: int, which: str = "outer"):
+    """D of the second moments of chi (chi = phi_inner, or 1 - phi_matrix for the
+    outer drop) and dD/dphi as (3, ny, nx)."""
+    ny, nx = phi_of_state.shape[1:]
+    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    chi = phi_of_state[inner] if which == "inner" else 1.0 - phi_of_state[matrix]
+    A = chi.sum()
+    xc, yc = (chi * x).sum() / A, (chi * y).sum() / A
+    Ixx, Iyy = (chi * x * x).sum() / A - xc ** 2, (chi * y * y).sum() / A - yc ** 2
+    a, b = 2.0 * np.sqrt(Iyy), 2.0 * np.sqrt(Ixx)
+    D = (a - b) / (a + b)
+    # chain rule through the moments: dI_xx/dchi = (x^2 - m3/A)/A - 2 xc (x - xc)/A
+    dIxx = (x * x - (chi * x * x).sum() / A) / A - 2.0 * xc * (x - xc) / A
+    dIyy = (y * y - (chi * y * y).sum() / A) / A - 2.0 * yc * (y - yc) / A
+    dchi = 2.0 * (b * dIyy / np.sqrt(Iyy) - a * dIxx / np.sqrt(Ixx)) / (a + b) ** 2
+    dphi = np.zeros_like(phi_of_state)
+    if which == "inner":
+        dphi[inner] = dchi
+    else:
+        dphi[matrix] = -dchi
+    return D, dphi
+
+
+def phi_of_state(x: np.ndarray) -> np.ndarray:
+    """phi_i = sum_j f^i_j of a state vector."""
+    f0, f1 = STATE_PLANES["f"]
+    return x[f0:f1].reshape(3, 9, *x.shape[1:]).sum(axis=1)
+
+
+def seed_from_phi(dphi: np.ndarray) -> np.ndarray:
+    """The state-vector adjoint of an objective of phi = sum_j f^i_j."""
+    ny, nx = dphi.shape[1:]
+    a = np.zeros((N_STATE, ny, nx))
+    f0 = STATE_PLANES["f"][0]
+    for i in range(3):
+        a[f0 + 9 * i:f0 + 9 * i + 9] = dphi[i]
+    return a
+
+
+def gradient(params: dict, phi, steps: int, objective, u=None, q=None):
+    """Reverse-mode gradient of objective(phi of the final populations) after `steps`
+    steps from the state created from phi.  `objective(phi) -> (J, dJ/dphi)`.
+    Returns J, {parameter: dJ/dparameter}, dJ/dphi_init.  Every state is kept (small
+    lattices only)."""
+    o = Oracle(params, phi, u=u, q=q)
+    states = []
+    for _ in range(steps):
+        states.append(o.clone())
+        o.step(1)
+    J, dphi = objective(phi_of_state(o.state_vector()))
+    a = seed_from_phi(dphi)
+    dpar = np.zeros(len(ADJ_PARAMS))
+    for st in reversed(states):
+        a, dp = st.adjoint_step(a)
+        dpar += dp
+    dp0, dphi0 = adjoint_init(params, phi, a, u=u, q=q)
+    dpar += dp0
+    return J, dict(zip(ADJ_PARAMS, dpar.tolist())), dphi0
 
 
 def stencil(chi: np.ndarray, bc_y: int):

@@ -605,9 +605,12 @@ static void ions_collide_and_stream(orc_state* s, int first) {
     }
 }
 
-static void one_step(orc_state* s) {
-    const int nx = s->p.nx, ny = s->p.ny, N = s->N;
-    const int first = s->step == 0;
+/* The step in four phases (one_step runs them in order; the reverse mode below
+ * re-runs the first three to recover the intermediates of a step). */
+
+/* S1-S4: zeroth moments, properties and stencils, the charge of the step */
+static void step_moments_closure(orc_state* s) {
+    const int N = s->N;
     /* S1: zeroth moments of the current populations */
     for (int c = 0; c < N; ++c) {
         for (int i = 0; i < 3; ++i) {
@@ -629,7 +632,11 @@ static void one_step(orc_state* s) {
         double src = r * (s->geps[c] * Ex + s->geps[N + c] * Ey) - (s->gsig[c] * Ex + s->gsig[N + c] * Ey);
         s->q[c] = (s->qt[c] + 0.5 * src) / (1.0 + 0.5 * r);
     }
-    /* S5: potential solve (warm-started from the current h, or the FD form) */
+}
+
+/* S5: potential solve (warm-started from the current h, or the FD form) */
+static void step_potential(orc_state* s) {
+    const int N = s->N;
     if (s->p.electric && s->p.potential_solver == 1) {
         s->last_iters = fd_solve(s, &s->last_res);
         s->last_converged = 1;
@@ -647,6 +654,11 @@ static void one_step(orc_state* s) {
             s->psi[c] = 0.0;
         }
     }
+}
+
+/* R^n, S6-S9: charge source, chemical potential and its gradient, force, flow moments */
+static void step_forces(orc_state* s) {
+    const int nx = s->p.nx, ny = s->p.ny, N = s->N;
     /* the Debye-Hueckel closure: charge from the solved potential */
     if (s->p.debye_kappa2 > 0.0)
         for (int c = 0; c < N; ++c) s->q[c] = -s->eps[c] * s->p.debye_kappa2 * s->psi[c];
@@ -675,7 +687,11 @@ static void one_step(orc_state* s) {
     }
     /* S9 */
     flow_moments(s);
-    /* S10-S14 */
+}
+
+/* S10-S14: collisions and streaming; the d/dt state for the next step */
+static void step_collide(orc_state* s, int first) {
+    const int N = s->N;
     collide_and_stream(s, first);
     if (s->p.ions) ions_collide_and_stream(s, first);
     for (int c = 0; c < N; ++c) {
@@ -687,6 +703,605 @@ static void one_step(orc_state* s) {
         s->prev_qu[N + c] = s->q[c] * s->u[N + c];
     }
     s->step += 1;
+}
+
+static void one_step(orc_state* s) {
+    const int first = s->step == 0;
+    step_moments_closure(s);
+    step_potential(s);
+    step_forces(s);
+    step_collide(s, first);
+}
+
+/* ---------------- reverse mode: the transposed step ----------------
+ *
+ * The step maps the state X^n = (g, f, l, h, E, (phi_i u)^{n-1}, (q u)^{n-1}) and the
+ * parameters theta to X^{n+1}.  Given the adjoint a^{n+1} = dJ/dX^{n+1} of an
+ * objective J, the routines below return a^n = (dX^{n+1}/dX^n)^T a^{n+1} and add
+ * (dX^{n+1}/dtheta)^T a^{n+1} to dJ/dtheta.  Each is the literal transpose of the
+ * forward statements above, taken in reverse order: a statement y = f(x) becomes
+ * xbar += (df/dx)^T ybar, and a stencil or streaming gather becomes the matching
+ * scatter.  The potential is differentiated through its fixed number of pseudo-time
+ * iterations (Eq. 43), each transposed at the iterate it was applied to (a residual-
+ * controlled solve stops on a decision that has no derivative).
+ *
+ * State vector planes (N cells each): g 0-8, f 9-35 (set-major), l 36-44, h 45-53,
+ * E 54-55, (phi_i u)^{n-1} 56-61 (x, y per phase), (q u)^{n-1} 62-63.
+ * Parameter slots: V_bottom, V_top, eps_1..3, sigma_1..3, gamma_12, gamma_13, gamma_23. */
+void orc_destroy(orc_state* s);
+orc_state* orc_create(const orc_params* p, const double* phi_init, const double* u_init,
+                      const double* q_init, const double* noise, int* status);
+
+enum { SV_G = 0, SV_F = 9, SV_L = 36, SV_H = 45, SV_E = 54, SV_PU = 56, SV_QU = 62, SV_N = 64 };
+enum { AP_VB = 0, AP_VT, AP_EPS, AP_SIG = AP_EPS + 3, AP_GAM = AP_SIG + 3, AP_N = AP_GAM + 3 };
+
+#define ORC_BUFFERS(X) X(g, 9) X(f, 27) X(l, 9) X(h, 9) X(gs, 9) X(fs, 27) X(ls, 9) X(hs, 9) \
+    X(phi, 3) X(qt, 1) X(q, 1) X(rho, 1) X(sig, 1) X(eps, 1) X(lap, 3) X(geps, 2) X(gsig, 2) X(grho, 2) \
+    X(E, 2) X(psi, 1) X(mu, 3) X(gmu, 6) X(F, 2) X(u, 2) X(pr, 1) X(R, 1) X(prev_phiu, 6) X(prev_qu, 2) \
+    X(psi_prev, 1) X(J_prev, 2) X(ion, 18) X(ions_s, 18) X(nion, 2) X(prev_nv, 4)
+
+/* deep copy of a state */
+orc_state* orc_clone(const orc_state* s) {
+    orc_state* t = (orc_state*)malloc(sizeof(orc_state));
+    if (!t) return NULL;
+    *t = *s;
+    const size_t N = (size_t)s->N;
+#define ORC_COPY(name, k) t->name = alloc0((k) * N); memcpy(t->name, s->name, (k) * N * sizeof(double));
+    ORC_BUFFERS(ORC_COPY)
+#undef ORC_COPY
+    return t;
+}
+
+/* the state vector of the layout above: read (out) or write (in) */
+static double* sv_plane(orc_state* s, int k) {
+    const size_t N = (size_t)s->N;
+    if (k < SV_F) return s->g + k * N;
+    if (k < SV_L) return s->f + (k - SV_F) * N;
+    if (k < SV_H) return s->l + (k - SV_L) * N;
+    if (k < SV_E) return s->h + (k - SV_H) * N;
+    if (k < SV_PU) return s->E + (k - SV_E) * N;
+    if (k < SV_QU) return s->prev_phiu + (k - SV_PU) * N;
+    return s->prev_qu + (k - SV_QU) * N;
+}
+void orc_get_state_vector(orc_state* s, double* out) {
+    for (int k = 0; k < SV_N; ++k) memcpy(out + (size_t)k * s->N, sv_plane(s, k), s->N * sizeof(double));
+}
+void orc_set_state_vector(orc_state* s, const double* in) {
+    for (int k = 0; k < SV_N; ++k) memcpy(sv_plane(s, k), in + (size_t)k * s->N, s->N * sizeof(double));
+}
+
+/* transpose of grad_at over the lattice: out(d) += sum over (c, j) with ghost(c + c_j)
+ * = d of w_j c_j . gbar(c) / cs2;  gbar = (x plane, y plane) */
+static void grad_T(const orc_state* s, const double* gbar, double* out) {
+    const int nx = s->p.nx, ny = s->p.ny, N = s->N;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            int c = y * nx + x;
+            for (int j = 0; j < 9; ++j) {
+                int d = ghost_y(s, y + CY[j]) * nx + wrap(x + CX[j], nx);
+                out[d] += W[j] * (CX[j] * gbar[c] + CY[j] * gbar[N + c]) / CS2;
+            }
+        }
+}
+/* transpose of lap_at */
+static void lap_T(const orc_state* s, const double* lbar, double* out) {
+    const int nx = s->p.nx, ny = s->p.ny;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            int c = y * nx + x;
+            for (int j = 0; j < 9; ++j) {
+                int d = ghost_y(s, y + CY[j]) * nx + wrap(x + CX[j], nx);
+                out[d] += 2.0 * W[j] * lbar[c] / CS2;
+                out[c] -= 2.0 * W[j] * lbar[c] / CS2;
+            }
+        }
+}
+/* transpose of stream(): srcbar = (dst <- src)^T dstbar; the moving-wall term adds
+ * to rhobar (kind 1), the electrode term to the V slots (kind 2) */
+static void stream_T(const orc_state* s, const double* dstbar, double* srcbar, int kind, double* rhobar,
+                     double* dpar) {
+    const int nx = s->p.nx, ny = s->p.ny, N = s->N;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            int c = y * nx + x;
+            for (int j = 0; j < 9; ++j) {
+                int yt = y + CY[j];
+                if (s->p.bc_y != 0 && (yt < 0 || yt >= ny)) {
+                    int top = yt >= ny;
+                    double b = dstbar[OPP[j] * N + c];
+                    if (kind == 1) {
+                        double uw = top ? s->p.u_wall_top : s->p.u_wall_bottom;
+                        srcbar[j * N + c] = b;
+                        rhobar[c] += -2.0 * W[j] * (CX[j] * uw) / CS2 * b;
+                    } else if (kind == 2 && s->p.bc_y == 2) {
+                        srcbar[j * N + c] = -b;
+                        dpar[top ? AP_VT : AP_VB] += 2.0 * W[j] * b;
+                    } else {
+                        srcbar[j * N + c] = b;
+                    }
+                } else {
+                    srcbar[j * N + c] = dstbar[j * N + wrap(yt, ny) * nx + wrap(x + CX[j], nx)];
+                }
+            }
+        }
+}
+
+/* transpose of one pseudo-time iteration (collide at the iterate hk, then stream):
+ * hbar <- (iteration)^T hbar, adding to epsbar, qbar and the V slots */
+static void poisson_iteration_T(const orc_state* s, const double* hk, double* hbar, double* tmp,
+                                double* epsbar, double* qbar, double* dpar) {
+    const int N = s->N;
+    const double th = s->tau_h;
+    stream_T(s, hbar, tmp, 2, NULL, dpar);
+    for (int c = 0; c < N; ++c) {
+        double epshat = s->eps[c] - s->p.eps_ref;
+        double den = epshat + CS2 * th;
+        double ax = 0.0, ay = 0.0;
+        for (int j = 0; j < 9; ++j) {
+            ax += CX[j] * hk[j * N + c];
+            ay += CY[j] * hk[j * N + c];
+        }
+        double gx = -ax / den, gy = -ay / den;
+        double apsi = 0.0, agx = 0.0, agy = 0.0, aeh = 0.0, aq = 0.0;
+        for (int j = 0; j < 9; ++j) {
+            double b = tmp[j * N + c];
+            double coef = (j == 0) ? (W[0] - 1.0) : W[j];   /* h_eq = coef psi, Eq. 44 */
+            double cg = CX[j] * gx + CY[j] * gy;
+            hbar[j * N + c] = (1.0 - 1.0 / th) * b;
+            apsi += coef * b / th;
+            agx += -(epshat / CS2) * W[j] * CX[j] * b / th;
+            agy += -(epshat / CS2) * W[j] * CY[j] * b / th;
+            aeh += -(1.0 / CS2) * W[j] * cg * b / th;
+            if (j) aq += b / 8.0;
+        }
+        /* g = -a / den, den = epshat + cs2 tau_h */
+        double aax = -agx / den, aay = -agy / den;
+        aeh += (agx * ax + agy * ay) / (den * den);
+        for (int j = 0; j < 9; ++j)
+            hbar[j * N + c] += CX[j] * aax + CY[j] * aay + (j ? apsi / (1.0 - W[0]) : 0.0);
+        epsbar[c] += aeh;
+        qbar[c] += aq;
+    }
+}
+
+/* transpose of E = J(h) / (epshat + cs2 tau_h) + E_ext (potential_fields) into hbar
+ * and epsbar */
+static void fields_T(const orc_state* s, const double* h, const double* Ebar, double* hbar, double* epsbar) {
+    const int N = s->N;
+    for (int c = 0; c < N; ++c) {
+        double den = s->eps[c] - s->p.eps_ref + CS2 * s->tau_h;
+        double ax = 0.0, ay = 0.0;
+        for (int j = 0; j < 9; ++j) {
+            ax += CX[j] * h[j * N + c];
+            ay += CY[j] * h[j * N + c];
+        }
+        for (int j = 0; j < 9; ++j) hbar[j * N + c] += (CX[j] * Ebar[c] + CY[j] * Ebar[N + c]) / den;
+        epsbar[c] += -(ax * Ebar[c] + ay * Ebar[N + c]) / (den * den);
+    }
+}
+
+/* transpose of the chemical potential (Eq. 20) into phibar, lapbar, Ebar, lambar and
+ * the eps slots */
+static void chemical_potential_T(const orc_state* s, const double* mubar, double* phibar, double* lapbar,
+                                 double* Ebar, double* lambar, double* dpar) {
+    const int N = s->N;
+    const double D = s->p.width_D;
+    for (int c = 0; c < N; ++c) {
+        double Ex = s->E[c], Ey = s->E[N + c];
+        double e2 = Ex * Ex + Ey * Ey;
+        for (int i = 0; i < 3; ++i) {
+            double ph = s->phi[i * N + c], mb = mubar[i * N + c];
+            double deps = 6.0 * s->p.eps[i] * ph * (1.0 - ph);
+            phibar[i * N + c] += mb * (24.0 / D * s->lam[i] * (3.0 * ph * ph - 3.0 * ph + 0.5)
+                                       - 3.0 * s->p.eps[i] * (1.0 - 2.0 * ph) * e2);
+            lapbar[i * N + c] += -0.75 * D * s->lam[i] * mb;
+            Ebar[c] += -deps * Ex * mb;
+            Ebar[N + c] += -deps * Ey * mb;
+            lambar[i] += mb * (24.0 / D * ph * (ph - 0.5) * (ph - 1.0) - 0.75 * D * s->lap[i * N + c]);
+            dpar[AP_EPS + i] += -3.0 * ph * (1.0 - ph) * e2 * mb;
+        }
+    }
+}
+
+/* transpose of the properties (Eq. 29-30) into phibar and the eps, sigma slots */
+static void properties_T(const orc_state* s, const double* rhobar, const double* sigbar, const double* epsbar,
+                         double* phibar, double* dpar) {
+    const int N = s->N;
+    for (int c = 0; c < N; ++c)
+        for (int i = 0; i < 3; ++i) {
+            double ph = s->phi[i * N + c];
+            phibar[i * N + c] += s->p.rho[i] * rhobar[c] + s->p.sigma[i] * sigbar[c]
+                               + s->p.eps[i] * 6.0 * ph * (1.0 - ph) * epsbar[c];
+            dpar[AP_SIG + i] += ph * sigbar[c];
+            dpar[AP_EPS + i] += ph * ph * (3.0 - 2.0 * ph) * epsbar[c];
+        }
+}
+
+/* lambda_i of Eq. 9 are sums of the gamma_jk: their adjoints map back */
+static void lambda_T(const double* lambar, double* dpar) {
+    dpar[AP_GAM + 0] += lambar[0] + lambar[1] - lambar[2];
+    dpar[AP_GAM + 1] += lambar[0] - lambar[1] + lambar[2];
+    dpar[AP_GAM + 2] += -lambar[0] + lambar[1] + lambar[2];
+}
+
+static int adjoint_supported(const orc_params* p) {
+    if (p->ions || p->debye_kappa2 > 0.0) return 0;
+    if (p->electric && (p->potential_solver != 0 || p->poisson_fixed_iter <= 0)) return 0;
+    return 1;
+}
+
+/* a_out = (dX^{n+1}/dX^n)^T a_in for the step that starts from the state s (left
+ * unchanged); dpar[AP_N] += (dX^{n+1}/dtheta)^T a_in.  Returns -1 for a configuration
+ * without a derivative here (ions, the Debye-Hueckel closure, the FD potential, a
+ * residual-controlled potential). */
+int orc_adjoint_step(const orc_state* s0, const double* a_in, double* a_out, double* dpar) {
+    if (!adjoint_supported(&s0->p)) return -1;
+    const int N = s0->N;
+    const size_t n = (size_t)N;
+    const int K = s0->p.electric ? s0->p.poisson_fixed_iter : 0;
+    const int first = s0->step == 0;
+    /* forward again on a copy, keeping the intermediates and the potential iterates */
+    orc_state* t = orc_clone(s0);
+    double* Eprev = alloc0(2 * n);
+    memcpy(Eprev, t->E, 2 * n * sizeof(double));
+    double* hk = alloc0((size_t)(K + 1) * 9 * n);
+    step_moments_closure(t);
+    if (t->p.electric) {
+        for (int k = 0; k < K; ++k) {
+            memcpy(hk + (size_t)k * 9 * n, t->h, 9 * n * sizeof(double));
+            poisson_iteration(t);
+        }
+        memcpy(hk + (size_t)K * 9 * n, t->h, 9 * n * sizeof(double));
+        potential_fields(t);
+    } else {
+        step_potential(t);
+    }
+    step_forces(t);
+
+    const double tf = t->p.tau_f, tl = t->tau_l, m0 = t->m0;
+    const int cc = t->p.charge_convection;
+    double *a_fs = alloc0(27 * n), *a_gs = alloc0(9 * n), *a_ls = alloc0(9 * n);
+    double *a_phi = alloc0(3 * n), *a_u = alloc0(2 * n), *a_q = alloc0(n), *a_mu = alloc0(3 * n);
+    double *a_gmu = alloc0(6 * n), *a_rho = alloc0(n), *a_p = alloc0(n), *a_F = alloc0(2 * n);
+    double *a_grho = alloc0(2 * n), *a_R = alloc0(n), *a_E = alloc0(2 * n), *a_sig = alloc0(n);
+    double *a_eps = alloc0(n), *a_geps = alloc0(2 * n), *a_gsig = alloc0(2 * n), *a_lap = alloc0(3 * n);
+    double *a_h = alloc0(9 * n), *tmp = alloc0(9 * n);
+    double lambar[3] = {0.0, 0.0, 0.0};
+    memset(a_out, 0, SV_N * n * sizeof(double));
+    /* the field of this step is part of the state it leaves */
+    memcpy(a_E, a_in + SV_E * n, 2 * n * sizeof(double));
+
+    /* the d/dt state written at the end of the step: (phi_i u), (q u) */
+    for (int c = 0; c < N; ++c) {
+        double ux = t->u[c], uy = t->u[N + c];
+        for (int i = 0; i < 3; ++i) {
+            double bx = a_in[(SV_PU + 2 * i) * n + c], by = a_in[(SV_PU + 2 * i + 1) * n + c];
+            a_phi[i * N + c] += ux * bx + uy * by;
+            a_u[c] += t->phi[i * N + c] * bx;
+            a_u[N + c] += t->phi[i * N + c] * by;
+        }
+        double bx = a_in[SV_QU * n + c], by = a_in[(SV_QU + 1) * n + c];
+        a_q[c] += ux * bx + uy * by;
+        a_u[c] += t->q[c] * bx;
+        a_u[N + c] += t->q[c] * by;
+    }
+    /* streaming (S14) */
+    for (int i = 0; i < 3; ++i) stream_T(t, a_in + (SV_F + 9 * i) * n, a_fs + 9 * i * n, 0, NULL, NULL);
+    stream_T(t, a_in + SV_G * n, a_gs, 1, a_rho, NULL);
+    stream_T(t, a_in + SV_L * n, a_ls, 0, NULL, NULL);
+
+    /* collisions (S10-S13) */
+    for (int c = 0; c < N; ++c) {
+        double ph[3];
+        phis(t, c, ph);
+        double ux = t->u[c], uy = t->u[N + c], qc = t->q[c];
+        double aux = 0.0, auy = 0.0, aqc = 0.0;
+        /* phase populations, Eq. 34-36 */
+        for (int i = 0; i < 3; ++i) {
+            double aAx = 0.0, aAy = 0.0;
+            for (int j = 0; j < 9; ++j) {
+                double fb = a_fs[(9 * i + j) * n + c];
+                a_out[(SV_F + 9 * i + j) * n + c] += (1.0 - 1.0 / tf) * fb;
+                double feqb = fb / tf, Fjb = (1.0 - 1.0 / (2.0 * tf)) * fb;
+                aAx += W[j] * CX[j] * Fjb;
+                aAy += W[j] * CY[j] * Fjb;
+                if (j == 0) {
+                    a_phi[i * N + c] += feqb;
+                    a_mu[i * N + c] += -(1.0 - W[0]) * feqb;
+                } else {
+                    a_mu[i * N + c] += W[j] * feqb;
+                    double tq = W[j] * feqb / CS2;   /* d feq_j / d(phi_i u) = w_j c_j / cs2 */
+                    a_phi[i * N + c] += tq * (CX[j] * ux + CY[j] * uy);
+                    aux += tq * CX[j] * ph[i];
+                    auy += tq * CY[j] * ph[i];
+                }
+            }
+            /* A = d/dt(phi_i u) / cs2 - Y / m0,  Y = sum_k M_ik grad mu_k */
+            double aYx = -aAx / m0, aYy = -aAy / m0;
+            for (int k = 0; k < 3; ++k) {
+                double Mii = 0.0;
+                for (int kk = 0; kk < 3; ++kk)
+                    if (kk != i) Mii += m0 * ph[i] * ph[kk];
+                double Mik = (k == i) ? (Mii - m0) : -m0 * ph[i] * ph[k];
+                a_gmu[(2 * k) * n + c] += Mik * aYx;
+                a_gmu[(2 * k + 1) * n + c] += Mik * aYy;
+                double aM = aYx * t->gmu[(2 * k) * n + c] + aYy * t->gmu[(2 * k + 1) * n + c];
+                if (k != i) {
+                    a_phi[i * N + c] += -m0 * ph[k] * aM;
+                    a_phi[k * N + c] += -m0 * ph[i] * aM;
+                } else {
+                    for (int kk = 0; kk < 3; ++kk)
+                        if (kk != i) {
+                            a_phi[i * N + c] += m0 * ph[kk] * aM;
+                            a_phi[kk * N + c] += m0 * ph[i] * aM;
+                        }
+                }
+            }
+            if (!first) {
+                double adx = aAx / CS2, ady = aAy / CS2;
+                a_phi[i * N + c] += ux * adx + uy * ady;
+                aux += ph[i] * adx;
+                auy += ph[i] * ady;
+                a_out[(SV_PU + 2 * i) * n + c] -= adx;
+                a_out[(SV_PU + 2 * i + 1) * n + c] -= ady;
+            }
+        }
+        /* flow populations, Eq. 37-40 */
+        {
+            double tg = tau_g_at(t, c);
+            double rho = t->rho[c], p = t->pr[c];
+            double Fx = t->F[c], Fy = t->F[N + c];
+            double grx = t->grho[c], gry = t->grho[N + c];
+            double ugr = ux * grx + uy * gry;
+            double atg = 0.0;
+            for (int j = 0; j < 9; ++j) {
+                double gb = a_gs[j * n + c];
+                a_out[(SV_G + j) * n + c] += (1.0 - 1.0 / tg) * gb;
+                double geqb = gb / tg, Gb = (1.0 - 1.0 / (2.0 * tg)) * gb;
+                double sj = s_j(j, ux, uy);
+                double cu = CX[j] * ux + CY[j] * uy;
+                double cgr = CX[j] * grx + CY[j] * gry;
+                if (use_visc(&t->p)) {
+                    double geq = (j == 0) ? (W[0] - 1.0) * p / CS2 + rho * sj : W[j] * p / CS2 + rho * sj;
+                    double cF = CX[j] * Fx + CY[j] * Fy;
+                    double G = W[j] * (ugr + cF / CS2 + (cu * cgr - CS2 * ugr) / CS2);
+                    atg += gb * ((t->g[j * n + c] - geq) + 0.5 * G) / (tg * tg);
+                }
+                a_p[c] += ((j == 0) ? (W[0] - 1.0) : W[j]) / CS2 * geqb;
+                a_rho[c] += sj * geqb;
+                /* d s_j / du = w_j (c_j / cs2 + (c_j.u) c_j / cs2^2 - u / cs2) */
+                aux += rho * geqb * W[j] * (CX[j] / CS2 + cu * CX[j] / (CS2 * CS2) - ux / CS2);
+                auy += rho * geqb * W[j] * (CY[j] / CS2 + cu * CY[j] / (CS2 * CS2) - uy / CS2);
+                /* G_j: the u.grad rho terms cancel (coefficient w_j (1 - cs2/cs2) = 0) */
+                a_F[c] += W[j] * CX[j] * Gb / CS2;
+                a_F[N + c] += W[j] * CY[j] * Gb / CS2;
+                aux += W[j] * CX[j] * cgr * Gb / CS2;
+                auy += W[j] * CY[j] * cgr * Gb / CS2;
+                a_grho[c] += W[j] * CX[j] * cu * Gb / CS2;
+                a_grho[N + c] += W[j] * CY[j] * cu * Gb / CS2;
+            }
+            if (use_visc(&t->p)) {
+                double eta = 0.0;
+                for (int i = 0; i < 3; ++i) eta += ph[i] * t->p.visc[i];
+                double aeta = atg / (rho * CS2);
+                a_rho[c] += -atg * eta / (rho * rho * CS2);
+                for (int i = 0; i < 3; ++i) a_phi[i * N + c] += t->p.visc[i] * aeta;
+            }
+        }
+        /* charge populations, Eq. 48-50 */
+        {
+            double adqx = 0.0, adqy = 0.0;
+            for (int j = 0; j < 9; ++j) {
+                double lb = a_ls[j * n + c];
+                a_out[(SV_L + j) * n + c] += (1.0 - 1.0 / tl) * lb;
+                double leqb = lb / tl;
+                a_R[c] += (1.0 - 1.0 / (2.0 * tl)) * W[j] * lb;
+                if (cc) {
+                    double cu = CX[j] * ux + CY[j] * uy;
+                    aqc += W[j] * (1.0 + cu / CS2) * leqb;
+                    aux += W[j] * qc * CX[j] / CS2 * leqb;
+                    auy += W[j] * qc * CY[j] / CS2 * leqb;
+                    adqx += (1.0 - 1.0 / (2.0 * tl)) * W[j] * CX[j] * lb / CS2;
+                    adqy += (1.0 - 1.0 / (2.0 * tl)) * W[j] * CY[j] * lb / CS2;
+                } else {
+                    aqc += W[j] * leqb;
+                }
+            }
+            if (cc && !first) {
+                aqc += ux * adqx + uy * adqy;
+                aux += qc * adqx;
+                auy += qc * adqy;
+                a_out[SV_QU * n + c] -= adqx;
+                a_out[(SV_QU + 1) * n + c] -= adqy;
+            }
+        }
+        a_u[c] += aux;
+        a_u[N + c] += auy;
+        a_q[c] += aqc;
+    }
+
+    /* S9: u = (m + F/2) / rho, p = cs2/(1 - w0) (g1 + ugr/2 + rho s_0(u)) */
+    for (int c = 0; c < N; ++c) {
+        double rho = t->rho[c], ux = t->u[c], uy = t->u[N + c];
+        double grx = t->grho[c], gry = t->grho[N + c];
+        double kp = CS2 / (1.0 - W[0]), ap = a_p[c];
+        double ag1 = kp * ap, augr = 0.5 * kp * ap;
+        a_rho[c] += kp * s_j(0, ux, uy) * ap;
+        double aux = a_u[c] + kp * rho * ap * W[0] * (-ux / CS2);  /* d s_0 / du = -w0 u / cs2 */
+        double auy = a_u[N + c] + kp * rho * ap * W[0] * (-uy / CS2);
+        aux += grx * augr;
+        auy += gry * augr;
+        a_grho[c] += ux * augr;
+        a_grho[N + c] += uy * augr;
+        double amx = aux / rho, amy = auy / rho;
+        a_F[c] += 0.5 * aux / rho;
+        a_F[N + c] += 0.5 * auy / rho;
+        a_rho[c] += -(ux * aux + uy * auy) / rho;
+        for (int j = 0; j < 9; ++j) a_out[(SV_G + j) * n + c] += CX[j] * amx + CY[j] * amy + (j ? ag1 : 0.0);
+    }
+    /* S8: F = -sum phi_i grad mu_i + q E;  R = -r q + r geps.E - gsig.E, r = sig/eps */
+    for (int c = 0; c < N; ++c) {
+        double aFx = a_F[c], aFy = a_F[N + c];
+        for (int i = 0; i < 3; ++i) {
+            a_phi[i * N + c] += -(t->gmu[(2 * i) * n + c] * aFx + t->gmu[(2 * i + 1) * n + c] * aFy);
+            a_gmu[(2 * i) * n + c] += -t->phi[i * N + c] * aFx;
+            a_gmu[(2 * i + 1) * n + c] += -t->phi[i * N + c] * aFy;
+        }
+        double Ex = t->E[c], Ey = t->E[N + c], qc = t->q[c];
+        a_q[c] += Ex * aFx + Ey * aFy;
+        a_E[c] += qc * aFx;
+        a_E[N + c] += qc * aFy;
+        double r = t->sig[c] / t->eps[c], aR = a_R[c];
+        double gex = t->geps[c], gey = t->geps[N + c], gsx = t->gsig[c], gsy = t->gsig[N + c];
+        a_q[c] += -r * aR;
+        double ar = (-qc + gex * Ex + gey * Ey) * aR;
+        a_geps[c] += r * Ex * aR;
+        a_geps[N + c] += r * Ey * aR;
+        a_E[c] += (r * gex - gsx) * aR;
+        a_E[N + c] += (r * gey - gsy) * aR;
+        a_gsig[c] += -Ex * aR;
+        a_gsig[N + c] += -Ey * aR;
+        a_sig[c] += ar / t->eps[c];
+        a_eps[c] += -ar * t->sig[c] / (t->eps[c] * t->eps[c]);
+    }
+    /* S7, S6 */
+    for (int i = 0; i < 3; ++i) grad_T(t, a_gmu + 2 * i * n, a_mu + i * n);
+    chemical_potential_T(t, a_mu, a_phi, a_lap, a_E, lambar, dpar);
+    /* S5: E from the last iterate, then the iterations in reverse */
+    for (size_t k = 0; k < 9 * n; ++k) a_h[k] = a_in[SV_H * n + k];
+    if (t->p.electric) {
+        fields_T(t, hk + (size_t)K * 9 * n, a_E, a_h, a_eps);
+        for (int k = K - 1; k >= 0; --k) poisson_iteration_T(t, hk + (size_t)k * 9 * n, a_h, tmp, a_eps, a_q, dpar);
+    }
+    for (size_t k = 0; k < 9 * n; ++k) a_out[SV_H * n + k] = a_h[k];
+    /* S4: q = (qt + src/2) / (1 + r/2), src = r geps.E' - gsig.E' with the previous E' */
+    double* a_qt = tmp;
+    for (int c = 0; c < N; ++c) {
+        double r = t->sig[c] / t->eps[c], d = 1.0 + 0.5 * r, aq = a_q[c];
+        double Ex = Eprev[c], Ey = Eprev[N + c];
+        double gex = t->geps[c], gey = t->geps[N + c], gsx = t->gsig[c], gsy = t->gsig[N + c];
+        a_qt[c] = aq / d;
+        double asrc = 0.5 * aq / d;
+        double ar = 0.5 * (-t->q[c] * aq / d) + (gex * Ex + gey * Ey) * asrc;
+        a_geps[c] += r * Ex * asrc;
+        a_geps[N + c] += r * Ey * asrc;
+        a_gsig[c] += -Ex * asrc;
+        a_gsig[N + c] += -Ey * asrc;
+        a_out[SV_E * n + c] += (r * gex - gsx) * asrc;
+        a_out[(SV_E + 1) * n + c] += (r * gey - gsy) * asrc;
+        a_sig[c] += ar / t->eps[c];
+        a_eps[c] += -ar * t->sig[c] / (t->eps[c] * t->eps[c]);
+    }
+    /* S3, S2 */
+    for (int i = 0; i < 3; ++i) lap_T(t, a_lap + i * n, a_phi + i * n);
+    grad_T(t, a_geps, a_eps);
+    grad_T(t, a_gsig, a_sig);
+    grad_T(t, a_grho, a_rho);
+    properties_T(t, a_rho, a_sig, a_eps, a_phi, dpar);
+    lambda_T(lambar, dpar);
+    /* S1 */
+    for (int c = 0; c < N; ++c) {
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 9; ++j) a_out[(SV_F + 9 * i + j) * n + c] += a_phi[i * N + c];
+        for (int j = 0; j < 9; ++j) a_out[(SV_L + j) * n + c] += a_qt[c];
+    }
+    double* bufs[] = {Eprev, hk, a_fs, a_gs, a_ls, a_phi, a_u, a_q, a_mu, a_gmu, a_rho, a_p, a_F, a_grho,
+                      a_R, a_E, a_sig, a_eps, a_geps, a_gsig, a_lap, a_h, tmp};
+    for (size_t k = 0; k < sizeof(bufs) / sizeof(bufs[0]); ++k) free(bufs[k]);
+    orc_destroy(t);
+    return 0;
+}
+
+/* Transpose of orc_create: dpar[AP_N] += (dX^0/dtheta)^T a_in and, if dphi is not
+ * NULL, dphi[3N] += (dX^0/dphi_init)^T a_in (the noise is additive and u_init, q_init
+ * are held fixed).  Returns -1 as orc_adjoint_step does, or on bad parameters. */
+int orc_adjoint_init(const orc_params* p, const double* phi_init, const double* u_init, const double* q_init,
+                     const double* a_in, double* dpar, double* dphi) {
+    if (!adjoint_supported(p)) return -1;
+    int st;
+    orc_state* t = orc_create(p, phi_init, u_init, q_init, NULL, &st);
+    if (!t) return -1;
+    const int N = t->N, nx = p->nx, ny = p->ny;
+    const size_t n = (size_t)N;
+    const int K = p->electric ? p->poisson_fixed_iter : 0;
+    /* the intermediates of the creation: properties from phi_init, the iterates of the
+     * potential from the linear electrode profile */
+    memcpy(t->phi, phi_init, 3 * n * sizeof(double));
+    memset(t->q, 0, n * sizeof(double));
+    if (q_init) memcpy(t->q, q_init, n * sizeof(double));
+    properties_and_stencils(t);
+    double* hk = alloc0((size_t)(K + 1) * 9 * n);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            int c = y * nx + x;
+            double psi0 = p->bc_y == 2 ? p->V_bottom + (p->V_top - p->V_bottom) * (y + 0.5) / ny : 0.0;
+            for (int j = 0; j < 9; ++j) t->h[j * N + c] = (j == 0) ? (W[0] - 1.0) * psi0 : W[j] * psi0;
+        }
+    if (p->electric) {
+        for (int k = 0; k < K; ++k) {
+            memcpy(hk + (size_t)k * 9 * n, t->h, 9 * n * sizeof(double));
+            poisson_iteration(t);
+        }
+        memcpy(hk + (size_t)K * 9 * n, t->h, 9 * n * sizeof(double));
+        potential_fields(t);
+    } else {
+        for (int c = 0; c < N; ++c) {
+            t->E[c] = p->E_ext[0];
+            t->E[N + c] = p->E_ext[1];
+        }
+    }
+    chemical_potential(t);
+
+    double *a_phi = alloc0(3 * n), *a_mu = alloc0(3 * n), *a_lap = alloc0(3 * n), *a_E = alloc0(2 * n);
+    double *a_rho = alloc0(n), *a_sig = alloc0(n), *a_eps = alloc0(n), *a_q = alloc0(n);
+    double *a_h = alloc0(9 * n), *tmp = alloc0(9 * n);
+    double lambar[3] = {0.0, 0.0, 0.0};
+    const int cc = p->charge_convection;
+    for (int c = 0; c < N; ++c) {
+        double ux = t->u[c], uy = t->u[N + c];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 9; ++j) {
+                double fb = a_in[(SV_F + 9 * i + j) * n + c];
+                if (j == 0) {
+                    a_phi[i * N + c] += fb;
+                    a_mu[i * N + c] += -(1.0 - W[0]) * fb;
+                } else {
+                    a_mu[i * N + c] += W[j] * fb;
+                    a_phi[i * N + c] += W[j] * (CX[j] * ux + CY[j] * uy) / CS2 * fb;
+                }
+            }
+        for (int j = 0; j < 9; ++j) {
+            a_rho[c] += s_j(j, ux, uy) * a_in[(SV_G + j) * n + c];
+            double cu = CX[j] * ux + CY[j] * uy;
+            a_q[c] += (cc ? W[j] * (1.0 + cu / CS2) : W[j]) * a_in[(SV_L + j) * n + c];
+        }
+        a_E[c] += a_in[SV_E * n + c];
+        a_E[N + c] += a_in[(SV_E + 1) * n + c];
+    }
+    chemical_potential_T(t, a_mu, a_phi, a_lap, a_E, lambar, dpar);
+    for (size_t k = 0; k < 9 * n; ++k) a_h[k] = a_in[SV_H * n + k];
+    if (p->electric) {
+        fields_T(t, hk + (size_t)K * 9 * n, a_E, a_h, a_eps);
+        for (int k = K - 1; k >= 0; --k) poisson_iteration_T(t, hk + (size_t)k * 9 * n, a_h, tmp, a_eps, a_q, dpar);
+        if (p->bc_y == 2)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    int c = y * nx + x;
+                    double apsi = 0.0, s = (y + 0.5) / ny;
+                    for (int j = 0; j < 9; ++j) apsi += ((j == 0) ? (W[0] - 1.0) : W[j]) * a_h[j * N + c];
+                    dpar[AP_VT] += apsi * s;
+                    dpar[AP_VB] += apsi * (1.0 - s);
+                }
+    }
+    for (int i = 0; i < 3; ++i) lap_T(t, a_lap + i * n, a_phi + i * n);
+    properties_T(t, a_rho, a_sig, a_eps, a_phi, dpar);
+    lambda_T(lambar, dpar);
+    if (dphi)
+        for (size_t k = 0; k < 3 * n; ++k) dphi[k] += a_phi[k];
+    double* bufs[] = {hk, a_phi, a_mu, a_lap, a_E, a_rho, a_sig, a_eps, a_q, a_h, tmp};
+    for (size_t k = 0; k < sizeof(bufs) / sizeof(bufs[0]); ++k) free(bufs[k]);
+    orc_destroy(t);
+    return 0;
 }
 
 /* ---------------- public (test-only) API ---------------- */
