@@ -45,7 +45,8 @@ enum {
     LB3E_ERR_NOT_CONVERGED = -4,  /* potential solve hit max_iter above tol */
     LB3E_ERR_FIELD = -5,          /* unknown field id */
     LB3E_ERR_NULL = -6,           /* NULL handle or output pointer */
-    LB3E_ERR_TOO_LARGE = -7       /* lattice larger than lb3e_observables_noalloc's fixed scratch */
+    LB3E_ERR_TOO_LARGE = -7,      /* lattice larger than lb3e_observables_noalloc's fixed scratch */
+    LB3E_ERR_UNSUPPORTED = -8     /* no reverse mode for this configuration (see lb3e_adjoint_step) */
 };
 
 /* Field ids for lb3e_get_field.  "Last step" fields hold the values computed
@@ -246,6 +247,72 @@ int lb3e_deformation(lb3e_handle* h, double* D, double* dD);
  * set dJ to 0).  dJ may be NULL.  FP64 sums on the GPU.  Synchronises the stream.
  * Errors: NULL, PARAM (three-dimensional lattices), CUDA. */
 int lb3e_shape_objective(lb3e_handle* h, const double* phi_target, double* J, double* dJ);
+
+/* ---------------------------------------------------------------- reverse mode
+ * The adjoint of the step: for an objective J of a later state, the derivative of J
+ * with respect to the state before a step and to the model parameters, one step at a
+ * time backwards (the chain rule through the step of Section 3 and the state's
+ * creation).  Two-dimensional plain builds (precision 0 FP64, 1 FP32, 2 and 5 with
+ * FP32 arithmetic) without ion transport, and, with electric = 1, the LB potential
+ * (potential_solver 0) run for a fixed count of pseudo-time iterations
+ * (poisson_fixed_iter > 0, Eq. 43): the count is part of the discrete step, while a
+ * residual-controlled solve stops on a decision with no derivative.  Anything else
+ * returns LB3E_ERR_UNSUPPORTED.
+ *
+ * The state vector X (device memory, 64 planes of N values in the build's
+ * arithmetic type: double for precision 0, float otherwise; plane k is the [ny][nx]
+ * array at offset k N):  g_j 0-8, f^i_j 9-35 (phase-major), l_j 36-44, h_j 45-53
+ * (the potential populations the next solve starts from), E 54-55 (x, y; the field
+ * the next step's charge closure reads), (phi_i u)^{n-1} 56-61 (x, y per phase),
+ * (q u)^{n-1} 62-63.  The phase rest populations are the full f^i_0 (the storage's
+ * deviation form rebuilt).  An adjoint a has the same layout: a = dJ/dX.
+ *
+ * Parameter slots of dparams (11 doubles, host, added to):  V_bottom, V_top,
+ * eps_1, eps_2, eps_3, sigma_1, sigma_2, sigma_3, gamma_12, gamma_13, gamma_23.  The
+ * electric field strength E0 enters through V_top = V_bottom + E0 ny.
+ *
+ * The adjoint needs a caller-owned device workspace (lb3e_adjoint_workspace_bytes,
+ * 256-byte aligned): the re-computed intermediates of one step, every potential
+ * iterate included, and the adjoint's scratch planes.  All calls run on the
+ * handle's stream and synchronise it before returning. */
+
+/* Bytes of the adjoint workspace of this handle's configuration.
+ * Errors: NULL, UNSUPPORTED. */
+int lb3e_adjoint_workspace_bytes(const lb3e_handle* h, size_t* bytes);
+
+/* Write the current state vector X (layout above) to dst (device, 64 N values).
+ * Errors: NULL, UNSUPPORTED, CUDA. */
+int lb3e_state_vector(lb3e_handle* h, void* dst);
+
+/* One step backwards.  saved_state: a snapshot of the state X^n before the step, as
+ * lb3e_save_state wrote it (host or device), which replaces the handle's state; NULL
+ * takes the handle's current state as X^n.  adj_in = dJ/dX^{n+1} and adj_out =
+ * dJ/dX^n (device, 64 N values each, distinct buffers); dparams[11] += dJ/dtheta
+ * through this step.  The step is re-run from X^n to recover its intermediates (the
+ * moments, properties, stencils, charge, each potential iterate, the field, the
+ * chemical potential, force and flow moments), then every statement of the step is
+ * transposed in reverse order.
+ * Errors: NULL, UNSUPPORTED, WORKSPACE, CUDA. */
+int lb3e_adjoint_step(lb3e_handle* h, const void* saved_state, const void* adj_in, void* adj_out,
+                      double* dparams, void* adj_workspace, size_t adj_bytes);
+
+/* The state's creation backwards: with adj_in = dJ/dX^0, dparams[11] += dJ/dtheta
+ * through the creation from phi_init (the initial populations at equilibrium with
+ * phi, zero velocity and charge, the potential iterated poisson_fixed_iter times
+ * from the linear electrode profile), and, if dphi_init is not NULL, dphi_init
+ * [3][ny][nx] doubles (host or device) += dJ/dphi_init.  phi_init [3][ny][nx]
+ * doubles, host or device, as given to lb3e_init.  The handle's state is left as it
+ * was.  Errors: NULL, UNSUPPORTED, WORKSPACE, CUDA. */
+int lb3e_adjoint_init(lb3e_handle* h, const double* phi_init, const void* adj_in, double* dparams,
+                      double* dphi_init, void* adj_workspace, size_t adj_bytes);
+
+/* Seeds of the two objectives of the current populations' phases: D of
+ * lb3e_deformation (which = 0 inner, 1 outer) and the shape objective J of
+ * lb3e_shape_objective; *D or *J gets the value and adj_out (device, 64 N values) the
+ * state-vector adjoint dD/dX or dJ/dX (nonzero on the f planes only, since phi_i =
+ * sum_j f^i_j).  Errors: NULL, PARAM (which), UNSUPPORTED, CUDA. */
+int lb3e_deformation_seed(lb3e_handle* h, int32_t which, double* D, void* adj_out);
+int lb3e_shape_seed(lb3e_handle* h, const double* phi_target, double* J, void* adj_out);
 
 /* Potential solves since the previous call (or lb3e_init): how many ran, how many
  * ended above the tolerance (iteration cap or a stalled residual), and the largest

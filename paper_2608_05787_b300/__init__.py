@@ -26,6 +26,12 @@ PRECISIONS = {0: "f64", 1: "f32", 2: "f32-compute/f16-store", 3: "f32 + 3 tangen
               5: "f32-compute/bf16-store"}
 TANGENT = 1000
 TANGENT_PARAMS = dict(V_top=0, eps1=1, eps2=2, eps3=3, gamma12=4, gamma13=5, gamma23=6)
+# reverse mode: the parameter slots of dJ/dtheta and the planes of the state vector
+ADJ_PARAMS = ("V_bottom", "V_top", "eps1", "eps2", "eps3", "sigma1", "sigma2", "sigma3",
+              "gamma12", "gamma13", "gamma23")
+N_STATE = 64
+STATE_PLANES = dict(g=(0, 9), f=(9, 36), l=(36, 45), h=(45, 54), E=(54, 56), prev_phiu=(56, 62),
+                    prev_qu=(62, 64))
 
 KERNEL_CLASSES = ("moments", "prologue", "poisson", "reduce", "fields", "fused", "other", "ions", "anchor",
                   "coarse")
@@ -131,6 +137,12 @@ def lib() -> C.CDLL:
         L.lb3e_potential_fd_residual.argtypes = [vp, dp]
         L.lb3e_deformation.argtypes = [vp, dp, dp]
         L.lb3e_shape_objective.argtypes = [vp, vp, dp, dp]
+        L.lb3e_adjoint_workspace_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.lb3e_state_vector.argtypes = [vp, vp]
+        L.lb3e_adjoint_step.argtypes = [vp, vp, vp, vp, dp, vp, C.c_size_t]
+        L.lb3e_adjoint_init.argtypes = [vp, vp, vp, dp, vp, vp, C.c_size_t]
+        L.lb3e_deformation_seed.argtypes = [vp, C.c_int32, dp, vp]
+        L.lb3e_shape_seed.argtypes = [vp, vp, dp, vp]
         L.lb3e_potential_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), dp]
         L.lb3e_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64)]
         L.lb3e_observables_noalloc.argtypes = [C.POINTER(Params), vp, vp, vp, vp, vp, C.POINTER(Observables)]
@@ -316,6 +328,74 @@ class Sim:
         dJ = (C.c_double * 3)()
         _check("lb3e_shape_objective", lib().lb3e_shape_objective(self._h, addr, C.byref(J), dJ))
         return J.value, tuple(dJ)
+
+    # ---------------------------------------------------------------- reverse mode
+    @property
+    def compute_dtype(self):
+        import torch
+        return torch.float64 if int(self.params.get("precision", 0)) == 0 else torch.float32
+
+    def _adj_ws(self):
+        ws = getattr(self, "_adj_workspace", None)
+        if ws is None:
+            n = C.c_size_t(0)
+            _check("lb3e_adjoint_workspace_bytes", lib().lb3e_adjoint_workspace_bytes(self._h, C.byref(n)))
+            import torch
+            ws = self._adj_workspace = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+        return ws
+
+    def _state_tensor(self):
+        import torch
+        return torch.empty((N_STATE,) + self.shape, dtype=self.compute_dtype, device=self.device)
+
+    def state_vector(self, out=None):
+        """The state X as a (64, ny, nx) CUDA tensor in the build's arithmetic type
+        (planes: STATE_PLANES)."""
+        out = self._state_tensor() if out is None else out
+        _check("lb3e_state_vector", lib().lb3e_state_vector(self._h, out.data_ptr()))
+        return out
+
+    def adjoint_step(self, a_in, state=None, out=None) -> np.ndarray:
+        """One step backwards (lb3e_adjoint_step): writes dJ/dX^n into ``out`` (a
+        (64, ny, nx) CUDA tensor, allocated if None) from a_in = dJ/dX^{n+1}, for the
+        step from ``state`` (a snapshot from save_state; None: the current state).
+        Returns (out, dJ/dtheta over ADJ_PARAMS through this step)."""
+        out = self._state_tensor() if out is None else out
+        ws = self._adj_ws()
+        dpar = np.zeros(len(ADJ_PARAMS))
+        _check("lb3e_adjoint_step",
+               lib().lb3e_adjoint_step(self._h, None if state is None else state.data_ptr(), a_in.data_ptr(),
+                                       out.data_ptr(), dpar.ctypes.data_as(C.POINTER(C.c_double)),
+                                       ws.data_ptr(), ws.numel()))
+        return out, dpar
+
+    def adjoint_init(self, phi, a_in, want_dphi: bool = True):
+        """The creation backwards (lb3e_adjoint_init): (dJ/dtheta over ADJ_PARAMS,
+        dJ/dphi_init as a host (3, ny, nx) array or None)."""
+        addr, _keep = _addr(phi)
+        ws = self._adj_ws()
+        dpar = np.zeros(len(ADJ_PARAMS))
+        dphi = np.zeros((3,) + self.shape) if want_dphi else None
+        _check("lb3e_adjoint_init",
+               lib().lb3e_adjoint_init(self._h, addr, a_in.data_ptr(), dpar.ctypes.data_as(C.POINTER(C.c_double)),
+                                       None if dphi is None else dphi.ctypes.data, ws.data_ptr(), ws.numel()))
+        return dpar, dphi
+
+    def deformation_seed(self, which: str = "outer"):
+        """(D, dD/dX) of the current populations (lb3e_deformation_seed)."""
+        a = self._state_tensor()
+        D = C.c_double(0)
+        _check("lb3e_deformation_seed",
+               lib().lb3e_deformation_seed(self._h, 0 if which == "inner" else 1, C.byref(D), a.data_ptr()))
+        return D.value, a
+
+    def shape_seed(self, phi_target):
+        """(J, dJ/dX) of the shape objective of the current populations (lb3e_shape_seed)."""
+        addr, _keep = _addr(phi_target)
+        a = self._state_tensor()
+        J = C.c_double(0)
+        _check("lb3e_shape_seed", lib().lb3e_shape_seed(self._h, addr, C.byref(J), a.data_ptr()))
+        return J.value, a
 
     def fd_residual(self) -> float:
         """||b - A psi|| / ||b|| of the current potential in the finite-difference form

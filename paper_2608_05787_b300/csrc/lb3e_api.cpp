@@ -239,6 +239,39 @@ int lb3e_shape_objective(lb3e_handle* h, const double* phi_target, double* J, do
     return h->sim->shape_objective(phi_target, J, dJ);
 }
 
+int lb3e_adjoint_workspace_bytes(const lb3e_handle* h, size_t* bytes) {
+    if (!h || !bytes) return LB3E_ERR_NULL;
+    return h->sim->adjoint_workspace_bytes(bytes);
+}
+
+int lb3e_state_vector(lb3e_handle* h, void* dst) {
+    if (!h || !dst) return LB3E_ERR_NULL;
+    return h->sim->state_vector(dst);
+}
+
+int lb3e_adjoint_step(lb3e_handle* h, const void* saved_state, const void* adj_in, void* adj_out,
+                      double* dparams, void* adj_workspace, size_t adj_bytes) {
+    if (!h || !adj_in || !adj_out || !dparams) return LB3E_ERR_NULL;
+    return h->sim->adjoint_step(saved_state, adj_in, adj_out, dparams, adj_workspace, adj_bytes);
+}
+
+int lb3e_adjoint_init(lb3e_handle* h, const double* phi_init, const void* adj_in, double* dparams,
+                      double* dphi_init, void* adj_workspace, size_t adj_bytes) {
+    if (!h || !phi_init || !adj_in || !dparams) return LB3E_ERR_NULL;
+    return h->sim->adjoint_init(phi_init, adj_in, dparams, dphi_init, adj_workspace, adj_bytes);
+}
+
+int lb3e_deformation_seed(lb3e_handle* h, int32_t which, double* D, void* adj_out) {
+    if (!h || !D || !adj_out) return LB3E_ERR_NULL;
+    if (which != 0 && which != 1) return LB3E_ERR_PARAM;
+    return h->sim->deformation_seed(which, D, adj_out);
+}
+
+int lb3e_shape_seed(lb3e_handle* h, const double* phi_target, double* J, void* adj_out) {
+    if (!h || !phi_target || !J || !adj_out) return LB3E_ERR_NULL;
+    return h->sim->shape_seed(phi_target, J, adj_out);
+}
+
 int lb3e_potential_fd_residual(lb3e_handle* h, double* residual) {
     if (!h || !residual) return LB3E_ERR_NULL;
     return h->sim->fd_residual(residual);
@@ -349,6 +382,7 @@ const char* lb3e_status_string(int status) {
         case LB3E_ERR_FIELD: return "unknown field id";
         case LB3E_ERR_NULL: return "NULL handle or pointer";
         case LB3E_ERR_TOO_LARGE: return "lattice larger than the fixed scratch of lb3e_observables_noalloc";
+        case LB3E_ERR_UNSUPPORTED: return "no reverse mode for this configuration";
         default: return "unknown status";
     }
 }

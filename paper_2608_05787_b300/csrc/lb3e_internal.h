@@ -87,6 +87,27 @@ struct SimBase {
     virtual int deformation(double* D, double* dD) = 0;
     virtual int shape_objective(const double* target, double* J, double* dJ) = 0;
     virtual int set_fused_tile(int rows) = 0;
+    // reverse mode (two-dimensional plain builds with a fixed potential count)
+    virtual int adjoint_workspace_bytes(size_t* bytes) { (void)bytes; return LB3E_ERR_UNSUPPORTED; }
+    virtual int state_vector(void* dst) { (void)dst; return LB3E_ERR_UNSUPPORTED; }
+    virtual int adjoint_step(const void* state, const void* a_in, void* a_out, double* dparams, void* ws,
+                             size_t bytes) {
+        (void)state; (void)a_in; (void)a_out; (void)dparams; (void)ws; (void)bytes;
+        return LB3E_ERR_UNSUPPORTED;
+    }
+    virtual int adjoint_init(const double* phi, const void* a_in, double* dparams, double* dphi, void* ws,
+                             size_t bytes) {
+        (void)phi; (void)a_in; (void)dparams; (void)dphi; (void)ws; (void)bytes;
+        return LB3E_ERR_UNSUPPORTED;
+    }
+    virtual int deformation_seed(int which, double* D, void* a_out) {
+        (void)which; (void)D; (void)a_out;
+        return LB3E_ERR_UNSUPPORTED;
+    }
+    virtual int shape_seed(const double* target, double* J, void* a_out) {
+        (void)target; (void)J; (void)a_out;
+        return LB3E_ERR_UNSUPPORTED;
+    }
     int64_t launches = 0;
     LaunchTimer timer;
     // potential solves since the last lb3e_potential_stats call: count, how many

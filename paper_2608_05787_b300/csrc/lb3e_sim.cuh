@@ -13,6 +13,7 @@
 #include <utility>
 #include <vector>
 
+#include "lb3e_adjoint.cuh"
 #include "lb3e_anchor.cuh"
 #include "lb3e_internal.h"
 #include "lb3e_ions.cuh"
@@ -997,7 +998,129 @@ class Sim final : public SimBase {
         return LB3E_OK;
     }
 
+    // ---------------------------------------------------------------- reverse mode
+    // (lb3e_adjoint.cuh): plain builds, no ions, the LB potential at a fixed count
+    int adjoint_K() const { return p_.electric ? p_.poisson_fixed_iter : 0; }
+    int adjoint_supported() const {
+        if constexpr (is_dual<R>::value) {
+            return LB3E_ERR_UNSUPPORTED;
+        } else {
+            if (p_.ions) return LB3E_ERR_UNSUPPORTED;
+            if (p_.electric && (p_.potential_solver != 0 || p_.poisson_fixed_iter <= 0)) return LB3E_ERR_UNSUPPORTED;
+            return LB3E_OK;
+        }
+    }
+    int adjoint_workspace_bytes(size_t* bytes) override {
+        TRY(adjoint_supported());
+        if constexpr (!is_dual<R>::value) *bytes = AdjointWS<R>::make(dp_, adjoint_K(), nullptr).total;
+        return LB3E_OK;
+    }
+    int state_vector(void* dst) override {
+        TRY(adjoint_supported());
+        if constexpr (!is_dual<R>::value) {
+            timer.begin(stream_, KC_OTHER);
+            k_adj_export<R, S><<<blocks1(N_), 256, 0, stream_>>>(dp_, d_.pop[cur_], d_.phi, d_.h[hcur_], d_.E,
+                                                                 d_.prev, static_cast<R*>(dst));
+            TRY(launched());
+            return sync();
+        }
+        return LB3E_OK;
+    }
+    int adjoint_step(const void* state, const void* a_in, void* a_out, double* dparams, void* ws,
+                     size_t bytes) override {
+        TRY(adjoint_supported());
+        if constexpr (!is_dual<R>::value) {
+            AdjointWS<R> w;
+            TRY(adjoint_ws(ws, bytes, &w));
+            if (state) TRY(load(state));
+            k_adj_export<R, S><<<blocks1(N_), 256, 0, stream_>>>(dp_, d_.pop[cur_], d_.phi, d_.h[hcur_], d_.E,
+                                                                 d_.prev, w.X);
+            TRY(launched());
+            AdjointRunner<R> run{dp_, adjoint_K(), stream_, w};
+            TRY(run.step_T(step_ == 0, static_cast<const R*>(a_in), static_cast<R*>(a_out)));
+            launches += run.launches;
+            return adjoint_params_out(w, dparams);
+        }
+        return LB3E_OK;
+    }
+    int adjoint_init(const double* phi, const void* a_in, double* dparams, double* dphi, void* ws,
+                     size_t bytes) override {
+        TRY(adjoint_supported());
+        if constexpr (!is_dual<R>::value) {
+            AdjointWS<R> w;
+            TRY(adjoint_ws(ws, bytes, &w));
+            TRY(upload(phi, 3 * N_, w.X));  // phi_init in the first state-vector planes
+            if (cudaMemsetAsync(d_.stage, 0, 3 * N_ * sizeof(double), stream_) != cudaSuccess) return LB3E_ERR_CUDA;
+            AdjointRunner<R> run{dp_, adjoint_K(), stream_, w};
+            TRY(run.init_T(w.X, static_cast<const R*>(a_in), d_.stage));
+            launches += run.launches;
+            if (dphi) {
+                // add the FP64 planes to the caller's (host or device) dphi through the staging area
+                TRY(copy(d_.stage + 3 * N_, dphi, 3 * N_ * sizeof(double)));
+                timer.begin(stream_, KC_OTHER);
+                k_add_f64<<<blocks1(3 * N_), 256, 0, stream_>>>(d_.stage + 3 * N_, d_.stage, 3 * N_);
+                TRY(launched());
+                TRY(copy(dphi, d_.stage + 3 * N_, 3 * N_ * sizeof(double)));
+            }
+            return adjoint_params_out(w, dparams);
+        }
+        return LB3E_OK;
+    }
+    int deformation_seed(int which, double* D, void* a_out) override {
+        TRY(adjoint_supported());
+        if constexpr (!is_dual<R>::value) {
+            double Ds[2];
+            TRY(deformation(Ds, nullptr));  // leaves the moment sums in pinned_
+            const double* m = pinned_ + 5 * which;
+            double g[5];
+            for (int k = 0; k < 5; ++k) {
+                double e[5] = {0, 0, 0, 0, 0};
+                e[k] = 1.0;
+                deformation_of(m, e, &g[k]);
+            }
+            *D = Ds[which];
+            timer.begin(stream_, KC_OTHER);
+            k_adj_seed_deformation<R><<<blocks1(N_), 256, 0, stream_>>>(
+                dp_, which == 0 ? dp_.inner : dp_.matrix, which == 0 ? 1.0 : -1.0, g[0], g[1], g[2], g[3], g[4],
+                static_cast<R*>(a_out));
+            TRY(launched());
+            return sync();
+        }
+        return LB3E_OK;
+    }
+    int shape_seed(const double* target, double* J, void* a_out) override {
+        TRY(adjoint_supported());
+        if constexpr (!is_dual<R>::value) {
+            TRY(shape_objective(target, J, nullptr));  // leaves phi of the current populations after the first plane
+            const R* tmp = reinterpret_cast<const R*>(d_.stage + N_);
+            TRY(copy(d_.stage + 5 * N_, target, 3 * N_ * sizeof(double)));
+            timer.begin(stream_, KC_OTHER);
+            k_adj_seed_shape<R><<<blocks1(N_), 256, 0, stream_>>>(dp_, tmp, d_.stage + 5 * N_,
+                                                                  static_cast<R*>(a_out));
+            TRY(launched());
+            return sync();
+        }
+        return LB3E_OK;
+    }
+
   private:
+    template <class W>
+    int adjoint_ws(void* ws, size_t bytes, W* w) {
+        if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0) return LB3E_ERR_WORKSPACE;
+        *w = W::make(dp_, adjoint_K(), static_cast<char*>(ws));
+        if (bytes < w->total) return LB3E_ERR_WORKSPACE;
+        if (cudaMemsetAsync(w->dpar, 0, AJ_N * sizeof(double), stream_) != cudaSuccess) return LB3E_ERR_CUDA;
+        return LB3E_OK;
+    }
+    template <class W>
+    int adjoint_params_out(const W& w, double* dparams) {
+        if (cudaMemcpyAsync(pinned_, w.dpar, AJ_N * sizeof(double), cudaMemcpyDeviceToHost, stream_) != cudaSuccess)
+            return LB3E_ERR_CUDA;
+        TRY(sync());
+        for (int k = 0; k < AJ_N; ++k) dparams[k] += pinned_[k];
+        return LB3E_OK;
+    }
+
     // relative residual from the 4 FP64 sums |d psi|^2, |psi|^2, |d J|^2, |J|^2
     static double rel_residual(const double* v) {
         const double dp = v[0], pp = v[1], dj = v[2], jj = v[3];

@@ -1,16 +1,58 @@
 """Derivatives of droplet deformation with respect to model parameters.
 
-The step kernels are instantiated on dual numbers (the tangent builds, precision 3
-and 4), so one run carries the exact derivative of the discrete state with respect
-to up to three parameters alongside the state itself.  The library's
-lb3e_deformation reduces the phase indicator's moments and their tangents on the GPU
-and forms the deformation factor D = (r_par - r_perp) / (r_par + r_perp) of the
-paper's Section 5.3 (radii from second moments) and its derivatives; this module
-sequences the runs and wraps them in a torch.autograd.Function.
+Two modes, both exact derivatives of the discrete step:
+* tangent (forward) mode: the step kernels instantiated on dual numbers (precision 3
+  and 4) carry d(state)/d(theta) for up to three parameters alongside the state;
+* reverse mode: the library's adjoint of the step (lb3e_adjoint_step), run backwards
+  from the objective's seed with checkpoint-and-recompute, gives dJ/dtheta for all
+  eleven parameter slots and dJ/dphi_init in one backward sweep.
+The library reduces the phase indicator's moments on the GPU and forms the
+deformation factor D = (r_par - r_perp) / (r_par + r_perp) of the paper's Section
+5.3 (radii from second moments) and its seeds; this module sequences the runs and
+wraps them in torch.autograd.Functions.
 """
 from __future__ import annotations
 
-from . import TANGENT_PARAMS, Sim
+import numpy as np
+
+from . import ADJ_PARAMS, TANGENT_PARAMS, Sim
+
+
+def reverse_gradient(params: dict, phi, steps: int, objective: str = "deformation", which: str = "outer",
+                     target=None, checkpoint_every: int = 200, want_dphi: bool = False):
+    """J after `steps` steps and its gradient by reverse mode: returns (J, {slot:
+    dJ/dslot} over ADJ_PARAMS, dJ/dphi_init or None).  The forward run keeps a
+    snapshot every `checkpoint_every` steps (device memory); the backward sweep
+    re-runs each segment from its snapshot, keeping that segment's states, and steps
+    back through them with lb3e_adjoint_step.  `objective`: "deformation" (D of
+    lb3e_deformation, `which` inner or outer) or "shape" (lb3e_shape_objective
+    against `target`).  The parameters must give a fixed potential count
+    (poisson_fixed_iter > 0, potential_solver 0)."""
+    sim = Sim(params, phi)
+    C = max(1, int(checkpoint_every))
+    ckpt = {}
+    for n in range(steps):
+        if n % C == 0:
+            ckpt[n] = sim.save_state()
+        sim.step(1)
+    J, a = sim.deformation_seed(which) if objective == "deformation" else sim.shape_seed(target)
+    b = a.clone()
+    dpar = np.zeros(len(ADJ_PARAMS))
+    for start in sorted(ckpt, reverse=True):
+        snaps = [ckpt[start]]
+        sim.load_state(ckpt[start])
+        for _ in range(start + 1, min(start + C, steps)):
+            sim.step(1)
+            snaps.append(sim.save_state())
+        for snap in reversed(snaps):
+            _, dp = sim.adjoint_step(a, state=snap, out=b)
+            a, b = b, a
+            dpar += dp
+        del snaps
+    dp0, dphi0 = sim.adjoint_init(phi, a, want_dphi=want_dphi)
+    dpar += dp0
+    sim.close()
+    return J, dict(zip(ADJ_PARAMS, dpar.tolist())), dphi0
 
 
 def deformation_tangents(params: dict, phi, steps: int, wrt=("V_top", "eps3", "gamma23"),
@@ -90,6 +132,35 @@ def _shape_fn():
 def shape_objective(E0, eps_ratio, gamma23, params: dict, phi, steps: int, target):
     """Differentiable target-shape objective (see ShapeObjectiveFn)."""
     return _shape_fn().apply(E0, eps_ratio, gamma23, params, phi, steps, target)
+
+
+def _deformation_reverse_fn():
+    import torch
+
+    class DeformationReverseFn(torch.autograd.Function):
+        """D_outer after `steps` steps as a differentiable function of E0, eps3/eps1
+        and gamma23 (forward: the run and one reverse sweep with checkpoints every
+        `checkpoint_every` steps; backward: the stored gradient)."""
+
+        @staticmethod
+        def forward(ctx, E0, eps_ratio, gamma23, params, phi, steps, checkpoint_every):
+            p, e1 = _scaled_inputs(params, E0, eps_ratio, gamma23)
+            D, g, _ = reverse_gradient(p, phi, steps, checkpoint_every=checkpoint_every)
+            ctx.save_for_backward(torch.tensor([g["V_top"] * p["ny"], g["eps3"] * e1, g["gamma23"]],
+                                               dtype=torch.float64))
+            return torch.tensor(D, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad):
+            (d,) = ctx.saved_tensors
+            return grad * d[0], grad * d[1], grad * d[2], None, None, None, None
+
+    return DeformationReverseFn
+
+
+def deformation_reverse(E0, eps_ratio, gamma23, params: dict, phi, steps: int, checkpoint_every: int = 200):
+    """Differentiable D_outer by reverse mode (see DeformationReverseFn)."""
+    return _deformation_reverse_fn().apply(E0, eps_ratio, gamma23, params, phi, steps, checkpoint_every)
 
 
 def _deformation_fn():
