@@ -907,6 +907,30 @@ def run_adjoint(args):
             res[name + "_kernels"] = {k: {"launches": n, "ms_per_step": ms / args.steps}
                                       for k, (ms, n) in kt.items() if n}
             sim.close()
+    # reverse mode: one sweep (forward run with a snapshot every 200 steps, the
+    # segment re-run keeping each step's snapshot, lb3e_adjoint_step back through it,
+    # the creation's adjoint) over S steps, all eleven parameter slots at once
+    from paper_2608_05787_b300.gradients import reverse_gradient
+    S = max(args.steps, 200)
+    for prec in (1, 0):
+        pr = dict(p, precision=prec)
+        reverse_gradient(pr, cfg["phi"], 8, checkpoint_every=200)  # warm-up (workspace, module load)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        D, g, _ = reverse_gradient(pr, cfg["phi"], S, checkpoint_every=200)
+        torch.cuda.synchronize()
+        res[f"reverse{prec}"] = (time.perf_counter() - t0) * 1e3 / S
+        res[f"reverse{prec}_grad"] = {k: g[k] for k in ("V_top", "eps3", "gamma23")}
+        if prec == 0:
+            # the FP64 forward step for the FP64 sweep's ratio
+            sim = L.Sim(pr, cfg["phi"])
+            sim.step(args.warmup)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.step(S)
+            torch.cuda.synchronize()
+            res["forward0"] = (time.perf_counter() - t0) * 1e3 / S
+            sim.close()
     N = p["nx"] * p["ny"]
     line = {"metric": "derivative/forward time per step", "value": res["tangent3"] / res["forward"],
             "unit": "ratio", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -915,7 +939,14 @@ def run_adjoint(args):
             "config": {"workload": "compound drop under field + shear, 256x256", "potential_iters_per_step": 16,
                        "forward_ms_per_step": res["forward"], "forward_mlups": N / res["forward"] / 1e3,
                        "forward_kernels": res["forward_kernels"], "tangent_kernels": res["tangent3_kernels"],
-                       "derivatives": ["dD/dE0", "dD/d(eps3/eps1)", "dD/dgamma23"], "mode": "tangent (forward)"}}
+                       "derivatives": ["dD/dE0", "dD/d(eps3/eps1)", "dD/dgamma23"], "mode": "tangent (forward)"},
+            "reverse": {"steps": S, "checkpoint_every": 200, "slots": 11,
+                        "fp32_ms_per_step": res["reverse1"], "fp32_over_forward": res["reverse1"] / res["forward"],
+                        "fp64_ms_per_step": res["reverse0"], "fp64_forward_ms_per_step": res["forward0"],
+                        "fp64_over_forward": res["reverse0"] / res["forward0"],
+                        "timing": "host clock around the whole sweep (forward run, re-runs, adjoint steps, the "
+                                  "creation's adjoint), divided by the steps",
+                        "fp32_gradient": res["reverse1_grad"], "fp64_gradient": res["reverse0_grad"]}}
     print(json.dumps(line), flush=True)
 
 

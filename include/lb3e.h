@@ -280,9 +280,12 @@ int lb3e_shape_objective(lb3e_handle* h, const double* phi_target, double* J, do
  * Errors: NULL, UNSUPPORTED. */
 int lb3e_adjoint_workspace_bytes(const lb3e_handle* h, size_t* bytes);
 
-/* Write the current state vector X (layout above) to dst (device, 64 N values).
+/* Write the current state vector X (layout above) to dst (device, 64 N values), in
+ * stream order (no synchronisation).  *first = 1 while the handle's state is the
+ * created one (its step has no d/dt terms), else 0.
  * Errors: NULL, UNSUPPORTED, CUDA. */
 int lb3e_state_vector(lb3e_handle* h, void* dst);
+int lb3e_is_first_step(const lb3e_handle* h, int32_t* first);
 
 /* One step backwards.  saved_state: a snapshot of the state X^n before the step, as
  * lb3e_save_state wrote it (host or device), which replaces the handle's state; NULL
@@ -295,6 +298,18 @@ int lb3e_state_vector(lb3e_handle* h, void* dst);
  * Errors: NULL, UNSUPPORTED, WORKSPACE, CUDA. */
 int lb3e_adjoint_step(lb3e_handle* h, const void* saved_state, const void* adj_in, void* adj_out,
                       double* dparams, void* adj_workspace, size_t adj_bytes);
+
+/* The same step backwards from a state vector X^n (device, as lb3e_state_vector
+ * wrote it before the step) instead of a snapshot; first = 1 for the step from the
+ * created state.  The handle's state is not touched.  dparams may be device memory
+ * (11 doubles): it is then accumulated in stream order and the call returns without
+ * synchronising, so a backward sweep needs no host round trip; a host dparams
+ * synchronises as in lb3e_adjoint_step.  On a stream other than the legacy default
+ * stream the step's kernels are captured once per (workspace, adj_in, adj_out,
+ * first, dparams) as a CUDA graph (the last 8 are kept) and replayed.
+ * Errors: NULL, UNSUPPORTED, WORKSPACE, CUDA. */
+int lb3e_adjoint_step_x(lb3e_handle* h, const void* X, int32_t first, const void* adj_in, void* adj_out,
+                        double* dparams, void* adj_workspace, size_t adj_bytes);
 
 /* The state's creation backwards: with adj_in = dJ/dX^0, dparams[11] += dJ/dtheta
  * through the creation from phi_init (the initial populations at equilibrium with

@@ -141,6 +141,8 @@ def lib() -> C.CDLL:
         L.lb3e_state_vector.argtypes = [vp, vp]
         L.lb3e_adjoint_step.argtypes = [vp, vp, vp, vp, dp, vp, C.c_size_t]
         L.lb3e_adjoint_init.argtypes = [vp, vp, vp, dp, vp, vp, C.c_size_t]
+        L.lb3e_adjoint_step_x.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp, C.c_size_t]
+        L.lb3e_is_first_step.argtypes = [vp, C.POINTER(C.c_int32)]
         L.lb3e_deformation_seed.argtypes = [vp, C.c_int32, dp, vp]
         L.lb3e_shape_seed.argtypes = [vp, vp, dp, vp]
         L.lb3e_potential_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), dp]
@@ -368,6 +370,22 @@ class Sim:
                                        out.data_ptr(), dpar.ctypes.data_as(C.POINTER(C.c_double)),
                                        ws.data_ptr(), ws.numel()))
         return out, dpar
+
+    @property
+    def is_first_step(self) -> bool:
+        f = C.c_int32(0)
+        _check("lb3e_is_first_step", lib().lb3e_is_first_step(self._h, C.byref(f)))
+        return bool(f.value)
+
+    def adjoint_step_x(self, X, first: bool, a_in, out, dparams):
+        """One step backwards from a state vector X (lb3e_adjoint_step_x) into
+        ``out``; ``dparams`` a float64 CUDA tensor of 11 slots, accumulated in stream
+        order (no synchronisation)."""
+        ws = self._adj_ws()
+        _check("lb3e_adjoint_step_x",
+               lib().lb3e_adjoint_step_x(self._h, X.data_ptr(), int(bool(first)), a_in.data_ptr(), out.data_ptr(),
+                                         dparams.data_ptr(), ws.data_ptr(), ws.numel()))
+        return out
 
     def adjoint_init(self, phi, a_in, want_dphi: bool = True):
         """The creation backwards (lb3e_adjoint_init): (dJ/dtheta over ADJ_PARAMS,

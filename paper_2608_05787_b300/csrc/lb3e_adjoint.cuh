@@ -38,6 +38,14 @@ __device__ __forceinline__ R acs2() { return R(1.0 / 3.0); }
 template <class R>
 __device__ __forceinline__ R aw(int j) { return j == 0 ? R(4.0 / 9.0) : (j <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0)); }
 
+// a / b in FP64 (the tape re-runs the FP64 step in its own rounding), a * (1/b) in
+// FP32 (a division is a long instruction sequence there)
+template <class R>
+__device__ __forceinline__ R adiv(R a, R b, R ib) {
+    if constexpr (std::is_same<R, double>::value) return a / b;
+    else return a * ib;
+}
+
 // stencil ghost row: periodic, or mirrored about a half-way wall (Eq. 33 at walls)
 __device__ __forceinline__ int adj_ghost_y(const DevParams& P, int y) {
     if (P.bc_y == 0) return y < 0 ? y + P.ny : (y >= P.ny ? y - P.ny : y);
@@ -98,6 +106,17 @@ __device__ __forceinline__ R lap_T_at(const DevParams& P, const R* __restrict__ 
         acc -= w2 * lb[c];
     }
     return acc;
+}
+
+// the post-collision adjoint of link j of a plain bounce-back set (phase or charge
+// populations): the streaming transposed, gathered from where the population went
+template <class R>
+__device__ __forceinline__ R post_T(const DevParams& P, const R* __restrict__ ain, int base, int j, int x, int y,
+                                    int c) {
+    const int yt = y + cy(j);
+    if (P.bc_y != 0 && (yt < 0 || yt >= P.ny)) return ain[(size_t)(base + opp(j)) * P.N + c];
+    const int t = (yt < 0 ? yt + P.ny : (yt >= P.ny ? yt - P.ny : yt)) * P.nx + adj_wx(x + cx(j), P.nx);
+    return ain[(size_t)(base + j) * P.N + t];
 }
 
 // ============================================================ tape (forward re-run)
@@ -205,49 +224,11 @@ __global__ void k_adj_h_linear(DevParams P, R* __restrict__ h) {
     for (int j = 0; j < 9; ++j) h[(size_t)j * N + c] = j == 0 ? (aw<R>(0) - R(1)) * psi0 : aw<R>(j) * psi0;
 }
 
-// one pseudo-time iteration of Eq. 43 (collide, then push along the links; the
-// electrodes by anti-bounce-back, insulating walls by bounce-back)
+// E = J(h) / (eps - eps_ref + cs2 tau_h) + E_ext (Eq. 45), or E_ext without a
+// potential; J of the last iterate goes to Jout
 template <class R>
-__global__ void k_adj_pot_iter(DevParams P, const R* __restrict__ eps, const R* __restrict__ q,
-                               const R* __restrict__ hin, R* __restrict__ hout) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int N = P.N, nx = P.nx, ny = P.ny;
-    if (c >= N) return;
-    const int x = c % nx, y = c / nx;
-    const R th = R(P.tau_h);
-    const R epshat = eps[c] - R(P.eps_ref);
-    R hv[9];
-    for (int j = 0; j < 9; ++j) hv[j] = hin[(size_t)j * N + c];
-    R a = R(0);
-    for (int j = 1; j < 9; ++j) a += hv[j];
-    const R psi = a / (R(1) - aw<R>(0));
-    R ax = R(0), ay = R(0);
-    for (int j = 0; j < 9; ++j) {
-        ax += R(cx(j)) * hv[j];
-        ay += R(cy(j)) * hv[j];
-    }
-    const R den = epshat + acs2<R>() * th;
-    const R gx = -ax / den, gy = -ay / den;
-    const R qc = q[c];
-    for (int j = 0; j < 9; ++j) {
-        const R heq = j == 0 ? (aw<R>(0) - R(1)) * psi : aw<R>(j) * psi;
-        const R varpi = j == 0 ? R(0) : R(1.0 / 8.0);
-        const R cg = R(cx(j)) * gx + R(cy(j)) * gy;
-        const R v = hv[j] - (hv[j] - heq) / th - (epshat / acs2<R>()) * aw<R>(j) * cg / th + varpi * qc;
-        const int yt = y + cy(j);
-        if (P.bc_y != 0 && (yt < 0 || yt >= ny)) {
-            const R vw = yt >= ny ? R(P.V_top) : R(P.V_bottom);
-            hout[(size_t)opp(j) * N + c] = P.bc_y == 2 ? -v + R(2) * aw<R>(j) * vw : v;
-        } else {
-            const int t = (yt < 0 ? yt + ny : (yt >= ny ? yt - ny : yt)) * nx + adj_wx(x + cx(j), nx);
-            hout[(size_t)j * N + t] = v;
-        }
-    }
-}
-
-// E = J(h) / (eps - eps_ref + cs2 tau_h) + E_ext (Eq. 45), or E_ext without a potential
-template <class R>
-__global__ void k_adj_field(DevParams P, const R* __restrict__ h, const R* __restrict__ eps, R* __restrict__ E) {
+__global__ void k_adj_field(DevParams P, const R* __restrict__ h, const R* __restrict__ eps, R* __restrict__ E,
+                            R* __restrict__ Jout) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = P.N;
     if (c >= N) return;
@@ -261,6 +242,8 @@ __global__ void k_adj_field(DevParams P, const R* __restrict__ h, const R* __res
         ax += R(cx(j)) * h[(size_t)j * N + c];
         ay += R(cy(j)) * h[(size_t)j * N + c];
     }
+    Jout[c] = ax;
+    Jout[N + c] = ay;
     const R den = eps[c] - R(P.eps_ref) + acs2<R>() * R(P.tau_h);
     const R gx = -ax / den, gy = -ay / den;
     E[c] = -gx + R(P.E_ext[0]);
@@ -354,7 +337,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_collide_T(
     const int N = P.N, nx = P.nx, ny = P.ny;
     if (c >= N) return;
     const int x = c % nx, y = c / nx;
-    const R cs = acs2<R>();
+    const R cs = acs2<R>(), ics = R(3), ics2 = R(9);
     // post-collision adjoint of (plane base, link j): S14 transposed
     R arho = R(0);
     auto post = [&](int base, int j, int kind) -> R {
@@ -363,7 +346,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_collide_T(
             const R b = ain[(size_t)(base + opp(j)) * N + c];
             if (kind == 1) {
                 const R uw = yt >= ny ? R(P.u_wall_top) : R(P.u_wall_bottom);
-                arho += -R(2) * aw<R>(j) * (R(cx(j)) * uw) / cs * b;
+                arho += -R(2) * aw<R>(j) * (R(cx(j)) * uw) * ics * b;
             }
             return b;
         }
@@ -390,14 +373,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_collide_T(
         auy += qc * by;
     }
     // phase populations, Eq. 34-36, with the mobility of Eq. 28
-    const R tf = R(P.tau_f), m0 = R(P.m0);
+    const R tf = R(P.tau_f), m0 = R(P.m0), itf = R(1) / tf, im0 = R(1) / m0;
     R aprev[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
     for (int i = 0; i < 3; ++i) {
         R aAx = R(0), aAy = R(0);
         for (int j = 0; j < 9; ++j) {
-            const R fb = post(AV_F + 9 * i, j, 0);
-            aout[(size_t)(AV_F + 9 * i + j) * N + c] = (R(1) - R(1) / tf) * fb;
-            const R feqb = fb / tf, Fjb = (R(1) - R(1) / (R(2) * tf)) * fb;
+            const R fb = post(AV_F + 9 * i, j, 0);  // its direct part (1 - 1/tau_f) fb is added by k_adj_props_T
+            const R feqb = fb * itf, Fjb = (R(1) - R(0.5) * itf) * fb;
             aAx += aw<R>(j) * R(cx(j)) * Fjb;
             aAy += aw<R>(j) * R(cy(j)) * Fjb;
             if (j == 0) {
@@ -405,13 +387,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_collide_T(
                 amu[i] += -(R(1) - aw<R>(0)) * feqb;
             } else {
                 amu[i] += aw<R>(j) * feqb;
-                const R tq = aw<R>(j) * feqb / cs;
+                const R tq = aw<R>(j) * feqb * ics;
                 aph[i] += tq * (R(cx(j)) * ux + R(cy(j)) * uy);
                 aux += tq * R(cx(j)) * ph[i];
                 auy += tq * R(cy(j)) * ph[i];
             }
         }
-        const R aYx = -aAx / m0, aYy = -aAy / m0;
+        const R aYx = -aAx * im0, aYy = -aAy * im0;
         for (int k = 0; k < 3; ++k) {
             R Mii = R(0);
             for (int kk = 0; kk < 3; ++kk)
@@ -432,7 +414,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_collide_T(
             }
         }
         if (!first) {
-            const R adx = aAx / cs, ady = aAy / cs;
+            const R adx = aAx * ics, ady = aAy * ics;
             aph[i] += ux * adx + uy * ady;
             aux += ph[i] * adx;
             auy += ph[i] * ady;
@@ -448,57 +430,58 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_collide_T(
         for (int i = 0; i < 3; ++i) eta += ph[i] * R(P.visc[i]);
         tg = R(0.5) + eta / (rh * cs);
     }
+    const R itg = R(1) / tg, irh = R(1) / rh;
     R ag[9], ap = R(0), agrx = R(0), agry = R(0), aFx = R(0), aFy = R(0), atg = R(0);
     {
         const R ugr = ux * grx + uy * gry;
         for (int j = 0; j < 9; ++j) {
             const R gb = post(AV_G, j, 1);
-            ag[j] = (R(1) - R(1) / tg) * gb;
-            const R geqb = gb / tg, Gb = (R(1) - R(1) / (R(2) * tg)) * gb;
+            ag[j] = (R(1) - itg) * gb;
+            const R geqb = gb * itg, Gb = (R(1) - R(0.5) * itg) * gb;
             const R sj = adj_sj<R>(j, ux, uy);
             const R cu = R(cx(j)) * ux + R(cy(j)) * uy;
             const R cgr = R(cx(j)) * grx + R(cy(j)) * gry;
             if (P.use_visc) {
-                const R geq = j == 0 ? (aw<R>(0) - R(1)) * p / cs + rh * sj : aw<R>(j) * p / cs + rh * sj;
+                const R geq = j == 0 ? (aw<R>(0) - R(1)) * p * ics + rh * sj : aw<R>(j) * p * ics + rh * sj;
                 const R cF = R(cx(j)) * Fx + R(cy(j)) * Fy;
-                const R G = aw<R>(j) * (ugr + cF / cs + (cu * cgr - cs * ugr) / cs);
-                atg += gb * ((X[(size_t)(AV_G + j) * N + c] - geq) + R(0.5) * G) / (tg * tg);
+                const R G = aw<R>(j) * (ugr + cF * ics + (cu * cgr - cs * ugr) * ics);
+                atg += gb * ((X[(size_t)(AV_G + j) * N + c] - geq) + R(0.5) * G) * (itg * itg);
             }
-            ap += (j == 0 ? aw<R>(0) - R(1) : aw<R>(j)) / cs * geqb;
+            ap += (j == 0 ? aw<R>(0) - R(1) : aw<R>(j)) * ics * geqb;
             arho += sj * geqb;
-            aux += rh * geqb * aw<R>(j) * (R(cx(j)) / cs + cu * R(cx(j)) / (cs * cs) - ux / cs);
-            auy += rh * geqb * aw<R>(j) * (R(cy(j)) / cs + cu * R(cy(j)) / (cs * cs) - uy / cs);
+            aux += rh * geqb * aw<R>(j) * (R(cx(j)) * ics + cu * R(cx(j)) * ics2 - ux * ics);
+            auy += rh * geqb * aw<R>(j) * (R(cy(j)) * ics + cu * R(cy(j)) * ics2 - uy * ics);
             // G_j: the u.grad rho terms cancel (their coefficient is w_j (1 - cs2/cs2) = 0)
-            aFx += aw<R>(j) * R(cx(j)) * Gb / cs;
-            aFy += aw<R>(j) * R(cy(j)) * Gb / cs;
-            aux += aw<R>(j) * R(cx(j)) * cgr * Gb / cs;
-            auy += aw<R>(j) * R(cy(j)) * cgr * Gb / cs;
-            agrx += aw<R>(j) * R(cx(j)) * cu * Gb / cs;
-            agry += aw<R>(j) * R(cy(j)) * cu * Gb / cs;
+            aFx += aw<R>(j) * R(cx(j)) * Gb * ics;
+            aFy += aw<R>(j) * R(cy(j)) * Gb * ics;
+            aux += aw<R>(j) * R(cx(j)) * cgr * Gb * ics;
+            auy += aw<R>(j) * R(cy(j)) * cgr * Gb * ics;
+            agrx += aw<R>(j) * R(cx(j)) * cu * Gb * ics;
+            agry += aw<R>(j) * R(cy(j)) * cu * Gb * ics;
         }
         if (P.use_visc) {
-            const R aeta = atg / (rh * cs);
-            arho += -atg * eta / (rh * rh * cs);
+            const R aeta = atg * irh * ics;
+            arho += -atg * eta * irh * irh * ics;
             for (int i = 0; i < 3; ++i) aph[i] += R(P.visc[i]) * aeta;
         }
     }
     // charge populations, Eq. 48-50
     R aR = R(0);
     {
-        const R tl = R(P.tau_l), pl = R(1) - R(1) / (R(2) * tl);
+        const R itl = R(1) / R(P.tau_l), pl = R(1) - R(0.5) * itl;
         R adqx = R(0), adqy = R(0);
         for (int j = 0; j < 9; ++j) {
             const R lb = post(AV_L, j, 0);
-            aout[(size_t)(AV_L + j) * N + c] = (R(1) - R(1) / tl) * lb;
-            const R leqb = lb / tl;
+            aout[(size_t)(AV_L + j) * N + c] = (R(1) - itl) * lb;
+            const R leqb = lb * itl;
             aR += pl * aw<R>(j) * lb;
             if (P.charge_convection) {
                 const R cu = R(cx(j)) * ux + R(cy(j)) * uy;
-                aqc += aw<R>(j) * (R(1) + cu / cs) * leqb;
-                aux += aw<R>(j) * qc * R(cx(j)) / cs * leqb;
-                auy += aw<R>(j) * qc * R(cy(j)) / cs * leqb;
-                adqx += pl * aw<R>(j) * R(cx(j)) * lb / cs;
-                adqy += pl * aw<R>(j) * R(cy(j)) * lb / cs;
+                aqc += aw<R>(j) * (R(1) + cu * ics) * leqb;
+                aux += aw<R>(j) * qc * R(cx(j)) * ics * leqb;
+                auy += aw<R>(j) * qc * R(cy(j)) * ics * leqb;
+                adqx += pl * aw<R>(j) * R(cx(j)) * lb * ics;
+                adqy += pl * aw<R>(j) * R(cy(j)) * lb * ics;
             } else {
                 aqc += aw<R>(j) * leqb;
             }
@@ -514,19 +497,19 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_collide_T(
     for (int k = 0; k < 8; ++k) aout[(size_t)(AV_PREV + k) * N + c] = aprev[k];
     // S9: u = (m + F/2) / rho, p = cs2/(1 - w0) (g1 + ugr/2 + rho s_0(u))
     {
-        const R kp = cs / (R(1) - aw<R>(0));
+        const R kp = cs * (R(1) / (R(1) - aw<R>(0)));
         const R ag1 = kp * ap, augr = R(0.5) * kp * ap;
         arho += kp * adj_sj<R>(0, ux, uy) * ap;
-        aux += kp * rh * ap * aw<R>(0) * (-ux / cs);
-        auy += kp * rh * ap * aw<R>(0) * (-uy / cs);
+        aux += kp * rh * ap * aw<R>(0) * (-ux * ics);
+        auy += kp * rh * ap * aw<R>(0) * (-uy * ics);
         aux += grx * augr;
         auy += gry * augr;
         agrx += ux * augr;
         agry += uy * augr;
-        const R amx = aux / rh, amy = auy / rh;
-        aFx += R(0.5) * aux / rh;
-        aFy += R(0.5) * auy / rh;
-        arho += -(ux * aux + uy * auy) / rh;
+        const R amx = aux * irh, amy = auy * irh;
+        aFx += R(0.5) * amx;
+        aFy += R(0.5) * amy;
+        arho += -(ux * aux + uy * auy) * irh;
         for (int j = 0; j < 9; ++j)
             aout[(size_t)(AV_G + j) * N + c] = ag[j] + R(cx(j)) * amx + R(cy(j)) * amy + (j ? ag1 : R(0));
     }
@@ -541,7 +524,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_collide_T(
     aqc += Ex * aFx + Ey * aFy;
     aEx += qc * aFx;
     aEy += qc * aFy;
-    const R r = sig[c] / eps[c];
+    const R ieps = R(1) / eps[c], r = sig[c] * ieps;
     const R gex = geps[c], gey = geps[N + c], gsx = gsig[c], gsy = gsig[N + c];
     aqc += -r * aR;
     const R ar = (-qc + gex * Ex + gey * Ey) * aR;
@@ -551,8 +534,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_collide_T(
     a_geps[N + c] = r * Ey * aR;
     a_gsig[c] = -Ex * aR;
     a_gsig[N + c] = -Ey * aR;
-    a_sig[c] = ar / eps[c];
-    a_eps[c] = -ar * sig[c] / (eps[c] * eps[c]);
+    a_sig[c] = ar * ieps;
+    a_eps[c] = -ar * r * ieps;
     for (int i = 0; i < 3; ++i) {
         a_phi[(size_t)i * N + c] = aph[i];
         a_mu[(size_t)i * N + c] = amu[i];
@@ -605,81 +588,19 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_mu_T(
 }
 
 // E = J(h_K)/den + E_ext transposed into the last iterate's adjoint (hbar = the
-// state's h adjoint plus this) and eps
+// state's h adjoint plus this) and eps; J_K = sum_j c_j h_j of that iterate
 template <class R>
-__global__ void k_adj_field_T(DevParams P, const R* __restrict__ h, const R* __restrict__ eps,
+__global__ void k_adj_field_T(DevParams P, const R* __restrict__ J, const R* __restrict__ eps,
                               const R* __restrict__ a_E, const R* __restrict__ ah_in, R* __restrict__ ah,
                               R* __restrict__ a_eps) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = P.N;
     if (c >= N) return;
-    const R den = eps[c] - R(P.eps_ref) + acs2<R>() * R(P.tau_h);
-    R ax = R(0), ay = R(0);
-    for (int j = 0; j < 9; ++j) {
-        ax += R(cx(j)) * h[(size_t)j * N + c];
-        ay += R(cy(j)) * h[(size_t)j * N + c];
-    }
-    const R bx = a_E[c], by = a_E[N + c];
-    for (int j = 0; j < 9; ++j)
-        ah[(size_t)j * N + c] = ah_in[(size_t)j * N + c] + (R(cx(j)) * bx + R(cy(j)) * by) / den;
-    a_eps[c] += -(ax * bx + ay * by) / (den * den);
-}
-
-// One pseudo-time iteration transposed at the iterate hk: the streaming (with the
-// electrodes' anti-bounce-back) gathered, then the collision of Eq. 43-45.  The
-// electrode terms accumulate per column in vbar[x] (bottom) and vbar[nx + x] (top).
-template <class R>
-__global__ void __launch_bounds__(ADJ_THREADS) k_adj_pot_iter_T(
-    DevParams P, const R* __restrict__ hk, const R* __restrict__ eps, const R* __restrict__ ah_in,
-    R* __restrict__ ah_out, R* __restrict__ a_eps, R* __restrict__ a_q, R* __restrict__ vbar) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int N = P.N, nx = P.nx, ny = P.ny;
-    if (c >= N) return;
-    const int x = c % nx, y = c / nx;
-    const R th = R(P.tau_h), cs = acs2<R>();
-    R b[9], av = R(0);
-    for (int j = 0; j < 9; ++j) {
-        const int yt = y + cy(j);
-        if (P.bc_y != 0 && (yt < 0 || yt >= ny)) {
-            const R t = ah_in[(size_t)opp(j) * N + c];
-            if (P.bc_y == 2) {
-                b[j] = -t;
-                av += R(2) * aw<R>(j) * t;
-            } else {
-                b[j] = t;
-            }
-        } else {
-            const int s = (yt < 0 ? yt + ny : (yt >= ny ? yt - ny : yt)) * nx + adj_wx(x + cx(j), nx);
-            b[j] = ah_in[(size_t)j * N + s];
-        }
-    }
-    if (P.bc_y == 2 && (y == 0 || y == ny - 1)) vbar[(y == 0 ? 0 : nx) + x] += av;
-    const R epshat = eps[c] - R(P.eps_ref);
-    const R den = epshat + cs * th;
-    R ax = R(0), ay = R(0);
-    for (int j = 0; j < 9; ++j) {
-        ax += R(cx(j)) * hk[(size_t)j * N + c];
-        ay += R(cy(j)) * hk[(size_t)j * N + c];
-    }
-    const R gx = -ax / den, gy = -ay / den;
-    R apsi = R(0), agx = R(0), agy = R(0), aeh = R(0), aq = R(0);
-    R out[9];
-    for (int j = 0; j < 9; ++j) {
-        const R coef = j == 0 ? aw<R>(0) - R(1) : aw<R>(j);
-        const R cg = R(cx(j)) * gx + R(cy(j)) * gy;
-        out[j] = (R(1) - R(1) / th) * b[j];
-        apsi += coef * b[j] / th;
-        agx += -(epshat / cs) * aw<R>(j) * R(cx(j)) * b[j] / th;
-        agy += -(epshat / cs) * aw<R>(j) * R(cy(j)) * b[j] / th;
-        aeh += -(R(1) / cs) * aw<R>(j) * cg * b[j] / th;
-        if (j) aq += b[j] / R(8);
-    }
-    const R aax = -agx / den, aay = -agy / den;
-    aeh += (agx * ax + agy * ay) / (den * den);
-    for (int j = 0; j < 9; ++j)
-        ah_out[(size_t)j * N + c] = out[j] + R(cx(j)) * aax + R(cy(j)) * aay + (j ? apsi / (R(1) - aw<R>(0)) : R(0));
-    a_eps[c] += aeh;
-    a_q[c] += aq;
+    const R iden = R(1) / (eps[c] - R(P.eps_ref) + acs2<R>() * R(P.tau_h));
+    const R ax = J[c], ay = J[N + c];
+    const R bx = a_E[c] * iden, by = a_E[N + c] * iden;
+    for (int j = 0; j < 9; ++j) ah[(size_t)j * N + c] = ah_in[(size_t)j * N + c] + (R(cx(j)) * bx + R(cy(j)) * by);
+    a_eps[c] += -(ax * bx + ay * by) * iden;
 }
 
 // S4 transposed: q = (q~ + src/2) / (1 + r/2), src = r geps.E' - gsig.E' with the
@@ -709,16 +630,62 @@ __global__ void k_adj_closure_T(DevParams P, const R* __restrict__ X, const R* _
     for (int j = 0; j < 9; ++j) aout[(size_t)(AV_L + j) * N + c] += aqt;
 }
 
+// Fixed-order sum of the partials into the FP64 parameter adjoint (added), by one
+// block: the mu-part (eps, lambda) and props-part (eps, sigma) partials of nb blocks
+// each, the electrode columns (2 nx values of R) or nbv V partials, lambda mapped to
+// gamma by Eq. 9.  Partials of the running kernel's other blocks are read past L1.
+template <class R>
+__device__ void params_reduce_block(const double* __restrict__ pmu, const double* pprops, int nb,
+                                    const R* __restrict__ vbar, int nx, const double* __restrict__ pv, int nbv,
+                                    double* __restrict__ dpar) {
+    double v[14];
+    for (int k = 0; k < 14; ++k) v[k] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        for (int k = 0; k < 6; ++k) v[k] += __ldcg(pmu + (size_t)6 * b + k);
+        for (int k = 0; k < 6; ++k) v[6 + k] += __ldcg(pprops + (size_t)6 * b + k);
+    }
+    if (vbar)
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            v[12] += (double)vbar[x];
+            v[13] += (double)vbar[nx + x];
+        }
+    if (pv)
+        for (int b = threadIdx.x; b < nbv; b += blockDim.x) {
+            v[12] += __ldcg(pv + (size_t)2 * b);
+            v[13] += __ldcg(pv + (size_t)2 * b + 1);
+        }
+    __shared__ double out[14];
+    block_reduce_store<14>(v, out);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // v: eps(mu) 0-2, lambda 3-5, eps(props) 6-8, sigma 9-11, V_bottom 12, V_top 13
+        dpar[AJ_VB] += out[12];
+        dpar[AJ_VT] += out[13];
+        for (int i = 0; i < 3; ++i) {
+            dpar[AJ_EPS + i] += out[i] + out[6 + i];
+            dpar[AJ_SIG + i] += out[9 + i];
+        }
+        dpar[AJ_GAM + 0] += out[3] + out[4] - out[5];
+        dpar[AJ_GAM + 1] += out[3] - out[4] + out[5];
+        dpar[AJ_GAM + 2] += -out[3] + out[4] + out[5];
+    }
+}
+
 // S3 and S2 transposed (Laplacians, gradients of eps and sigma, the properties of
-// Eq. 29-30), then S1: phi_i = sum_j f^i_j adds phibar to every f^i plane.  The h
-// adjoint of the state is copied out here.  With dphi (the creation), phibar goes
-// there in FP64 instead.  Block partials: eps_1..3, sigma_1..3.
+// Eq. 29-30), then S1: phi_i = sum_j f^i_j adds phibar to every f^i plane, which here
+// also gets its collision's direct part (1 - 1/tau_f) times the post-collision
+// adjoint gathered from ain.  The h adjoint of the state is copied out here.  With
+// dphi (the creation), phibar goes there in FP64 instead.  Block partials: eps_1..3,
+// sigma_1..3; the last block to finish sums every partial of the step into dpar
+// (the mu-part, these, the electrode columns or partials) and re-arms the counter.
 template <class R>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_props_T(
     DevParams P, const R* __restrict__ phi, const R* __restrict__ a_lap, const R* __restrict__ a_geps,
     const R* __restrict__ a_gsig, const R* __restrict__ a_rho, const R* __restrict__ a_sig,
-    const R* __restrict__ a_eps, const R* __restrict__ a_phi, const R* __restrict__ ah, R* __restrict__ aout,
-    double* __restrict__ dphi, double* __restrict__ partial) {
+    const R* __restrict__ a_eps, const R* __restrict__ a_phi, const R* __restrict__ ah, const R* __restrict__ ain,
+    R* __restrict__ aout, double* __restrict__ dphi, double* partial, const double* __restrict__ pmu,
+    const R* __restrict__ vbar, const double* __restrict__ pv, unsigned* __restrict__ count,
+    double* __restrict__ dpar) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = P.N, nx = P.nx;
     double v[6] = {0, 0, 0, 0, 0, 0};
@@ -727,6 +694,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_props_T(
         const R ae = a_eps[c] + (a_geps ? grad_T_at<R>(P, a_geps, a_geps + N, x, y) : R(0));
         const R as = (a_sig ? a_sig[c] : R(0)) + (a_gsig ? grad_T_at<R>(P, a_gsig, a_gsig + N, x, y) : R(0));
         const R ar = a_rho ? a_rho[c] : R(0);
+        const R dk = R(1) - R(1) / R(P.tau_f);
         for (int i = 0; i < 3; ++i) {
             const R ph = phi[(size_t)i * N + c];
             const R tot = a_phi[(size_t)i * N + c] + lap_T_at<R>(P, a_lap + (size_t)i * N, x, y) +
@@ -736,13 +704,25 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_props_T(
             if (dphi) {
                 dphi[(size_t)i * N + c] += (double)tot;
             } else {
-                for (int j = 0; j < 9; ++j) aout[(size_t)(AV_F + 9 * i + j) * N + c] += tot;
+                for (int j = 0; j < 9; ++j)
+                    aout[(size_t)(AV_F + 9 * i + j) * N + c] = dk * post_T<R>(P, ain, AV_F + 9 * i, j, x, y, c) + tot;
             }
         }
         if (ah)
             for (int j = 0; j < 9; ++j) aout[(size_t)(AV_H + j) * N + c] = ah[(size_t)j * N + c];
     }
     block_reduce_store<6>(v, partial + (size_t)6 * blockIdx.x);
+    __shared__ int is_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        is_last = atomicAdd(count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        params_reduce_block<R>(pmu, partial, (int)gridDim.x, vbar, nx, pv, pv ? (int)gridDim.x : 0, dpar);
+        if (threadIdx.x == 0) *count = 0u;
+    }
 }
 
 // The creation's state transposed into its inputs: f = f_eq(phi, mu) with u held at
@@ -796,49 +776,6 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_h_linear_T(DevParams P, con
     block_reduce_store<2>(v, partial + (size_t)2 * blockIdx.x);
 }
 
-// Fixed-order sum of the partials into the FP64 parameter adjoint (added): the
-// mu-part (eps, lambda) and props-part (eps, sigma) partials of nb blocks each, the
-// electrode columns (2 nx values of R) or nbv V partials, lambda mapped to gamma
-// by Eq. 9.
-template <class R>
-__global__ void __launch_bounds__(256) k_adj_params_reduce(const double* __restrict__ pmu,
-                                                           const double* __restrict__ pprops, int nb,
-                                                           const R* __restrict__ vbar, int nx,
-                                                           const double* __restrict__ pv, int nbv,
-                                                           double* __restrict__ dpar) {
-    double v[14];
-    for (int k = 0; k < 14; ++k) v[k] = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        for (int k = 0; k < 6; ++k) v[k] += pmu[(size_t)6 * b + k];
-        for (int k = 0; k < 6; ++k) v[6 + k] += pprops[(size_t)6 * b + k];
-    }
-    if (vbar)
-        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-            v[12] += (double)vbar[x];
-            v[13] += (double)vbar[nx + x];
-        }
-    if (pv)
-        for (int b = threadIdx.x; b < nbv; b += blockDim.x) {
-            v[12] += pv[(size_t)2 * b];
-            v[13] += pv[(size_t)2 * b + 1];
-        }
-    __shared__ double out[14];
-    block_reduce_store<14>(v, out);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        // v: eps(mu) 0-2, lambda 3-5, eps(props) 6-8, sigma 9-11, V_bottom 12, V_top 13
-        dpar[AJ_VB] += out[12];
-        dpar[AJ_VT] += out[13];
-        for (int i = 0; i < 3; ++i) {
-            dpar[AJ_EPS + i] += out[i] + out[6 + i];
-            dpar[AJ_SIG + i] += out[9 + i];
-        }
-        dpar[AJ_GAM + 0] += out[3] + out[4] - out[5];
-        dpar[AJ_GAM + 1] += out[3] - out[4] + out[5];
-        dpar[AJ_GAM + 2] += -out[3] + out[4] + out[5];
-    }
-}
-
 // dst += src (FP64)
 static __global__ void k_add_f64(double* __restrict__ dst, const double* __restrict__ src, size_t n) {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -873,16 +810,211 @@ __global__ void k_adj_seed_shape(DevParams P, const R* __restrict__ phi, const d
     }
 }
 
+// ============================================================ potential iterations in tiles
+// Both the re-run of the potential iterations and their transpose advance PT_H
+// iterations per launch on a tile of PT_TX x PT_TY cells held in shared memory with
+// a halo of PT_H cells (one thread per tile cell): after t iterations the values
+// within t cells of the tile's edge are stale, so the interior is exact after PT_H.
+constexpr int PT_TX = 32, PT_TY = 8, PT_H = 4, PT_W = PT_TX + 2 * PT_H, PT_HT = PT_TY + 2 * PT_H;
+constexpr int PT_NT = PT_W * PT_HT;  // 640 threads
+template <class R>
+constexpr size_t pt_smem_bytes() { return 2 * 9 * PT_NT * sizeof(R); }
+
+struct TileCell {
+    int t, c;          // tile index, lattice index (0 where absent)
+    bool present;      // the lattice has this cell (not beyond a wall)
+    bool interior;     // this launch's tile owns it (writes it back)
+    int gy;            // lattice row
+};
+__device__ __forceinline__ TileCell tile_cell(const DevParams& P) {
+    TileCell r;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    r.t = ty * PT_W + tx;
+    const int x0 = blockIdx.x * PT_TX, y0 = blockIdx.y * PT_TY;
+    int gx = x0 - PT_H + tx, gy = y0 - PT_H + ty;
+    gx = ((gx % P.nx) + P.nx) % P.nx;
+    r.present = true;
+    if (P.bc_y == 0) gy = ((gy % P.ny) + P.ny) % P.ny;
+    else r.present = gy >= 0 && gy < P.ny;
+    r.gy = gy;
+    r.c = r.present ? gy * P.nx + gx : 0;
+    r.interior = r.present && tx >= PT_H && tx < PT_H + PT_TX && ty >= PT_H && ty < PT_H + PT_TY &&
+                 x0 + tx - PT_H < P.nx && y0 + ty - PT_H < P.ny;
+    return r;
+}
+// tile index of the neighbour at (dx, dy), clamped into the tile (a clamped read only
+// happens in the stale rim)
+__device__ __forceinline__ int tile_nb(int dx, int dy) {
+    const int tx = min(max((int)threadIdx.x + dx, 0), PT_W - 1);
+    const int ty = min(max((int)threadIdx.y + dy, 0), PT_HT - 1);
+    return ty * PT_W + tx;
+}
+
+// nit (<= PT_H) pseudo-time iterations of Eq. 43 from hin to hout, the first moment
+// J of each input iterate to J + 2 N t (t = 0 .. nit - 1)
+template <class R>
+__global__ void __launch_bounds__(PT_NT) k_adj_pot_tape(DevParams P, const R* __restrict__ eps,
+                                                        const R* __restrict__ q, const R* __restrict__ hin,
+                                                        R* __restrict__ hout, R* __restrict__ J, int nit) {
+    extern __shared__ __align__(16) unsigned char pt_raw[];
+    R* cur = reinterpret_cast<R*>(pt_raw);
+    R* post = cur + 9 * PT_NT;
+    const TileCell tc = tile_cell(P);
+    const int N = P.N, ny = P.ny;
+    const R th = R(P.tau_h), ith = R(1) / th;
+    R epshat = R(0), qc = R(0), den = R(1), iden = R(1);
+    if (tc.present) {
+        epshat = eps[tc.c] - R(P.eps_ref);
+        qc = q[tc.c];
+        den = epshat + acs2<R>() * th;
+        iden = R(1) / den;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) cur[j * PT_NT + tc.t] = hin[(size_t)j * N + tc.c];
+    }
+    const R ehc = adiv(epshat, acs2<R>(), R(3));
+    for (int it = 0; it < nit; ++it) {
+        __syncthreads();
+        if (tc.present) {
+            R hv[9];
+#pragma unroll
+            for (int j = 0; j < 9; ++j) hv[j] = cur[j * PT_NT + tc.t];
+            R a = R(0);
+#pragma unroll
+            for (int j = 1; j < 9; ++j) a += hv[j];
+            const R psi = adiv(a, R(1) - aw<R>(0), R(9.0 / 5.0));
+            R ax = R(0), ay = R(0);
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                ax += R(cx(j)) * hv[j];
+                ay += R(cy(j)) * hv[j];
+            }
+            if (tc.interior) {
+                J[(size_t)(2 * it) * N + tc.c] = ax;
+                J[(size_t)(2 * it + 1) * N + tc.c] = ay;
+            }
+            const R gx = -adiv(ax, den, iden), gy = -adiv(ay, den, iden);
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const R heq = j == 0 ? (aw<R>(0) - R(1)) * psi : aw<R>(j) * psi;
+                const R varpi = j == 0 ? R(0) : R(1.0 / 8.0);
+                const R cg = R(cx(j)) * gx + R(cy(j)) * gy;
+                post[j * PT_NT + tc.t] =
+                    hv[j] - adiv(hv[j] - heq, th, ith) - adiv(ehc * aw<R>(j) * cg, th, ith) + varpi * qc;
+            }
+        }
+        __syncthreads();
+        if (tc.present) {
+            // pull: link j arrives from the cell at -c_j, or, where that is beyond a
+            // wall, is this cell's own opp(j) population reflected there
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const int ys = tc.gy - cy(j);
+                R v;
+                if (P.bc_y != 0 && (ys < 0 || ys >= ny)) {
+                    const R o = post[opp(j) * PT_NT + tc.t];
+                    const R vw = ys >= ny ? R(P.V_top) : R(P.V_bottom);
+                    v = P.bc_y == 2 ? -o + R(2) * aw<R>(j) * vw : o;
+                } else {
+                    v = post[j * PT_NT + tile_nb(-cx(j), -cy(j))];
+                }
+                cur[j * PT_NT + tc.t] = v;
+            }
+        }
+    }
+    if (tc.interior)
+#pragma unroll
+        for (int j = 0; j < 9; ++j) hout[(size_t)j * N + tc.c] = cur[j * PT_NT + tc.t];
+}
+
+// nit (<= PT_H) transposed iterations, k = k0, k0 - 1, ..: J_k at J + 2 N k; the
+// adjoint from ah_in to ah_out; eps, q and electrode adjoints accumulated by the
+// interior cells
+template <class R>
+__global__ void __launch_bounds__(PT_NT) k_adj_pot_T(DevParams P, const R* __restrict__ J,
+                                                     const R* __restrict__ eps, const R* __restrict__ ah_in,
+                                                     R* __restrict__ ah_out, R* __restrict__ a_eps,
+                                                     R* __restrict__ a_q, R* __restrict__ vbar, int k0, int nit) {
+    extern __shared__ __align__(16) unsigned char pt_raw[];
+    R* buf[2] = {reinterpret_cast<R*>(pt_raw), reinterpret_cast<R*>(pt_raw) + 9 * PT_NT};
+    const TileCell tc = tile_cell(P);
+    const int N = P.N, ny = P.ny;
+    const R ith = R(1) / R(P.tau_h), ics = R(3);
+    R epshat = R(0), iden = R(1);
+    if (tc.present) {
+        epshat = eps[tc.c] - R(P.eps_ref);
+        iden = R(1) / (epshat + acs2<R>() * R(P.tau_h));
+#pragma unroll
+        for (int j = 0; j < 9; ++j) buf[0][j * PT_NT + tc.t] = ah_in[(size_t)j * N + tc.c];
+    }
+    const R kg = -(epshat * ics) * ith;
+    const R apsi_c = ith * (R(1) / (R(1) - aw<R>(0)));
+    R s_eh = R(0), s_q = R(0), s_v = R(0);
+    for (int it = 0; it < nit; ++it) {
+        const R* cur = buf[it & 1];
+        R* nxt = buf[(it + 1) & 1];
+        __syncthreads();
+        if (tc.present) {
+            const int k = k0 - it;
+            R b[9], av = R(0);
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const int yt = tc.gy + cy(j);
+                if (P.bc_y != 0 && (yt < 0 || yt >= ny)) {
+                    const R t = cur[opp(j) * PT_NT + tc.t];
+                    if (P.bc_y == 2) {
+                        b[j] = -t;
+                        av += R(2) * aw<R>(j) * t;
+                    } else {
+                        b[j] = t;
+                    }
+                } else {
+                    b[j] = cur[j * PT_NT + tile_nb(cx(j), cy(j))];
+                }
+            }
+            const R ax = J[(size_t)(2 * k) * N + tc.c], ay = J[(size_t)(2 * k + 1) * N + tc.c];
+            const R gx = -ax * iden, gy = -ay * iden;
+            R spsi = R(0), sgx = R(0), sgy = R(0), scg = R(0), sq = R(0);
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                spsi += (j == 0 ? aw<R>(0) - R(1) : aw<R>(j)) * b[j];
+                sgx += aw<R>(j) * R(cx(j)) * b[j];
+                sgy += aw<R>(j) * R(cy(j)) * b[j];
+                scg += aw<R>(j) * (R(cx(j)) * gx + R(cy(j)) * gy) * b[j];
+                if (j) sq += b[j];
+            }
+            const R agx = kg * sgx, agy = kg * sgy;
+            const R aax = -agx * iden, aay = -agy * iden;
+            const R apsi_j = spsi * apsi_c;
+#pragma unroll
+            for (int j = 0; j < 9; ++j)
+                nxt[j * PT_NT + tc.t] = (R(1) - ith) * b[j] + R(cx(j)) * aax + R(cy(j)) * aay + (j ? apsi_j : R(0));
+            s_eh += -ics * ith * scg + (agx * ax + agy * ay) * iden * iden;
+            s_q += sq * R(0.125);
+            s_v += av;
+        }
+    }
+    __syncthreads();
+    if (tc.interior) {
+        const R* fin = buf[nit & 1];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) ah_out[(size_t)j * N + tc.c] = fin[j * PT_NT + tc.t];
+        a_eps[tc.c] += s_eh;
+        a_q[tc.c] += s_q;
+        if (P.bc_y == 2 && (tc.gy == 0 || tc.gy == ny - 1)) vbar[(tc.gy == 0 ? 0 : P.nx) + tc.c % P.nx] += s_v;
+    }
+}
+
 // ============================================================ host sequencing
 
-// The adjoint workspace (caller-owned device memory): the tape of one step (with
-// every potential iterate) and the adjoint scratch planes.
+// The adjoint workspace (caller-owned device memory): the tape of one step (the
+// first moment of every potential iterate) and the adjoint scratch planes.
 template <class R>
 struct AdjointWS {
-    R *X, *phi, *qt, *rho, *sig, *eps, *lap, *geps, *gsig, *grho, *q, *hk, *E, *Rq, *mu, *gmu, *F, *u, *pr;
+    R *X, *phi, *qt, *rho, *sig, *eps, *lap, *geps, *gsig, *grho, *q, *hb[2], *Jk, *E, *Rq, *mu, *gmu, *F, *u, *pr;
     R *a_phi, *a_mu, *a_gmu, *a_q, *a_E, *a_rho, *a_grho, *a_geps, *a_gsig, *a_sig, *a_eps, *a_lap, *a_h[2];
     R* vbar;
     double *pmu, *pprops, *pv, *dpar;
+    unsigned* count;
     size_t total;
 
     static size_t align(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -905,7 +1037,7 @@ struct AdjointWS {
         w.X = R_(AV_N);
         w.phi = R_(3); w.qt = R_(1); w.rho = R_(1); w.sig = R_(1); w.eps = R_(1); w.lap = R_(3);
         w.geps = R_(2); w.gsig = R_(2); w.grho = R_(2); w.q = R_(1);
-        w.hk = R_((size_t)9 * (K + 1));
+        w.hb[0] = R_(9); w.hb[1] = R_(9); w.Jk = R_((size_t)2 * (K + 1));
         w.E = R_(2); w.Rq = R_(1); w.mu = R_(3); w.gmu = R_(6); w.F = R_(2); w.u = R_(2); w.pr = R_(1);
         w.a_phi = R_(3); w.a_mu = R_(3); w.a_gmu = R_(6); w.a_q = R_(1); w.a_E = R_(2); w.a_rho = R_(1);
         w.a_grho = R_(2); w.a_geps = R_(2); w.a_gsig = R_(2); w.a_sig = R_(1); w.a_eps = R_(1); w.a_lap = R_(3);
@@ -913,6 +1045,7 @@ struct AdjointWS {
         w.vbar = base ? reinterpret_cast<R*>(base + o) : nullptr;
         o += align(2 * (size_t)P.nx * sizeof(R));
         w.pmu = D_(6 * nb); w.pprops = D_(6 * nb); w.pv = D_(2 * nb); w.dpar = D_(AJ_N);
+        w.count = reinterpret_cast<unsigned*>(D_(1));
         w.total = o;
         return w;
     }
@@ -928,6 +1061,20 @@ struct AdjointRunner {
     AdjointWS<R> w;
     int64_t launches = 0;
     unsigned nb() const { return (unsigned)((P.N + ADJ_THREADS - 1) / ADJ_THREADS); }
+    dim3 pt_grid() const { return dim3((P.nx + PT_TX - 1) / PT_TX, (P.ny + PT_TY - 1) / PT_TY); }
+    // the tiled potential kernels take more than the default 48 KB of shared memory
+    // in FP64 (call before any launch, outside a stream capture)
+    static int prepare() {
+        static int done = 0;
+        if (done) return LB3E_OK;
+        if (cudaFuncSetAttribute(k_adj_pot_tape<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pt_smem_bytes<R>()) != cudaSuccess ||
+            cudaFuncSetAttribute(k_adj_pot_T<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pt_smem_bytes<R>()) != cudaSuccess)
+            return LB3E_ERR_CUDA;
+        done = 1;
+        return LB3E_OK;
+    }
 
     int ok() {
         ++launches;
@@ -942,13 +1089,17 @@ struct AdjointRunner {
         k_adj_stencils<R><<<g, t, 0, s>>>(P, w.phi, w.eps, w.sig, w.rho, w.X + (size_t)AV_E * N, w.qt, closure,
                                           w.lap, w.geps, w.gsig, w.grho, w.q);
         TRY(ok());
+        int hc = 0;
         if (P.electric) {
-            for (int k = 0; k < K; ++k) {
-                k_adj_pot_iter<R><<<g, t, 0, s>>>(P, w.eps, w.q, w.hk + (size_t)9 * k * N, w.hk + (size_t)9 * (k + 1) * N);
+            for (int k = 0; k < K; k += PT_H) {
+                const int nit = K - k < PT_H ? K - k : PT_H;
+                k_adj_pot_tape<R><<<pt_grid(), dim3(PT_W, PT_HT), pt_smem_bytes<R>(), s>>>(
+                    P, w.eps, w.q, w.hb[hc], w.hb[hc ^ 1], w.Jk + (size_t)2 * k * N, nit);
                 TRY(ok());
+                hc ^= 1;
             }
         }
-        k_adj_field<R><<<g, t, 0, s>>>(P, w.hk + (size_t)9 * K * N, w.eps, w.E);
+        k_adj_field<R><<<g, t, 0, s>>>(P, w.hb[hc], w.eps, w.E, w.Jk + (size_t)2 * K * N);
         TRY(ok());
         k_adj_source_mu<R><<<g, t, 0, s>>>(P, w.phi, w.lap, w.E, w.q, w.sig, w.eps, w.geps, w.gsig, w.Rq, w.mu);
         return ok();
@@ -964,12 +1115,13 @@ struct AdjointRunner {
             *result = 0;
             return LB3E_OK;
         }
-        k_adj_field_T<R><<<g, t, 0, s>>>(P, w.hk + (size_t)9 * K * N, w.eps, w.a_E, ah_state, w.a_h[0], w.a_eps);
+        k_adj_field_T<R><<<g, t, 0, s>>>(P, w.Jk + (size_t)2 * K * N, w.eps, w.a_E, ah_state, w.a_h[0], w.a_eps);
         TRY(ok());
         int cur = 0;
-        for (int k = K - 1; k >= 0; --k) {
-            k_adj_pot_iter_T<R><<<g, t, 0, s>>>(P, w.hk + (size_t)9 * k * N, w.eps, w.a_h[cur], w.a_h[cur ^ 1],
-                                                w.a_eps, w.a_q, w.vbar);
+        for (int k = K - 1; k >= 0; k -= PT_H) {
+            const int nit = k + 1 < PT_H ? k + 1 : PT_H;
+            k_adj_pot_T<R><<<pt_grid(), dim3(PT_W, PT_HT), pt_smem_bytes<R>(), s>>>(
+                P, w.Jk, w.eps, w.a_h[cur], w.a_h[cur ^ 1], w.a_eps, w.a_q, w.vbar, k, nit);
             TRY(ok());
             cur ^= 1;
         }
@@ -980,9 +1132,10 @@ struct AdjointRunner {
     int step_T(int first, const R* ain, R* aout) {
         const unsigned g = nb(), t = ADJ_THREADS;
         const size_t N = (size_t)P.N;
-        if (cudaMemcpyAsync(w.hk, w.X + (size_t)AV_H * N, 9 * N * sizeof(R), cudaMemcpyDeviceToDevice, s) !=
+        if (cudaMemcpyAsync(w.hb[0], w.X + (size_t)AV_H * N, 9 * N * sizeof(R), cudaMemcpyDeviceToDevice, s) !=
                 cudaSuccess ||
-            cudaMemsetAsync(w.vbar, 0, 2 * (size_t)P.nx * sizeof(R), s) != cudaSuccess)
+            cudaMemsetAsync(w.vbar, 0, 2 * (size_t)P.nx * sizeof(R), s) != cudaSuccess ||
+            cudaMemsetAsync(w.count, 0, sizeof(unsigned), s) != cudaSuccess)
             return LB3E_ERR_CUDA;
         TRY(tape(nullptr, 1));
         k_adj_force_flow<R><<<g, t, 0, s>>>(P, w.phi, w.mu, w.q, w.E, w.X, w.rho, w.grho, w.gmu, w.F, w.u, w.pr);
@@ -1000,9 +1153,8 @@ struct AdjointRunner {
                                            w.a_gsig, w.a_sig, w.a_eps);
         TRY(ok());
         k_adj_props_T<R><<<g, t, 0, s>>>(P, w.phi, w.a_lap, w.a_geps, w.a_gsig, w.a_rho, w.a_sig, w.a_eps, w.a_phi,
-                                         w.a_h[hres], aout, nullptr, w.pprops);
-        TRY(ok());
-        k_adj_params_reduce<R><<<1, 256, 0, s>>>(w.pmu, w.pprops, (int)g, w.vbar, P.nx, nullptr, 0, w.dpar);
+                                         w.a_h[hres], ain, aout, nullptr, w.pprops, w.pmu, w.vbar, nullptr, w.count,
+                                         w.dpar);
         return ok();
     }
     // the transpose of the creation from phi_init (R planes, u held at zero)
@@ -1012,9 +1164,10 @@ struct AdjointRunner {
         if (cudaMemsetAsync(w.q, 0, N * sizeof(R), s) != cudaSuccess ||
             cudaMemsetAsync(w.vbar, 0, 2 * (size_t)P.nx * sizeof(R), s) != cudaSuccess ||
             cudaMemsetAsync(w.a_eps, 0, N * sizeof(R), s) != cudaSuccess ||
-            cudaMemsetAsync(w.a_q, 0, N * sizeof(R), s) != cudaSuccess)
+            cudaMemsetAsync(w.a_q, 0, N * sizeof(R), s) != cudaSuccess ||
+            cudaMemsetAsync(w.count, 0, sizeof(unsigned), s) != cudaSuccess)
             return LB3E_ERR_CUDA;
-        k_adj_h_linear<R><<<g, t, 0, s>>>(P, w.hk);
+        k_adj_h_linear<R><<<g, t, 0, s>>>(P, w.hb[0]);
         TRY(ok());
         TRY(tape(phi_init, 0));
         k_adj_init_seed_T<R><<<g, t, 0, s>>>(P, nullptr, ain, w.a_phi, w.a_mu, w.a_rho, w.a_E);
@@ -1027,9 +1180,8 @@ struct AdjointRunner {
         k_adj_h_linear_T<R><<<g, t, 0, s>>>(P, w.a_h[hres], w.pv);
         TRY(ok());
         k_adj_props_T<R><<<g, t, 0, s>>>(P, w.phi, w.a_lap, nullptr, nullptr, w.a_rho, nullptr, w.a_eps, w.a_phi,
-                                         nullptr, nullptr, dphi, w.pprops);
-        TRY(ok());
-        k_adj_params_reduce<R><<<1, 256, 0, s>>>(w.pmu, w.pprops, (int)g, w.vbar, P.nx, w.pv, (int)g, w.dpar);
+                                         nullptr, nullptr, nullptr, dphi, w.pprops, w.pmu, w.vbar, w.pv, w.count,
+                                         w.dpar);
         return ok();
     }
 };

@@ -255,6 +255,18 @@ int lb3e_adjoint_step(lb3e_handle* h, const void* saved_state, const void* adj_i
     return h->sim->adjoint_step(saved_state, adj_in, adj_out, dparams, adj_workspace, adj_bytes);
 }
 
+int lb3e_adjoint_step_x(lb3e_handle* h, const void* X, int32_t first, const void* adj_in, void* adj_out,
+                        double* dparams, void* adj_workspace, size_t adj_bytes) {
+    if (!h || !X || !adj_in || !adj_out || !dparams) return LB3E_ERR_NULL;
+    return h->sim->adjoint_step_x(X, first, adj_in, adj_out, dparams, adj_workspace, adj_bytes);
+}
+
+int lb3e_is_first_step(const lb3e_handle* h, int32_t* first) {
+    if (!h || !first) return LB3E_ERR_NULL;
+    *first = h->sim->first_step();
+    return LB3E_OK;
+}
+
 int lb3e_adjoint_init(lb3e_handle* h, const double* phi_init, const void* adj_in, double* dparams,
                       double* dphi_init, void* adj_workspace, size_t adj_bytes) {
     if (!h || !phi_init || !adj_in || !dparams) return LB3E_ERR_NULL;

@@ -100,6 +100,12 @@ struct SimBase {
         (void)phi; (void)a_in; (void)dparams; (void)dphi; (void)ws; (void)bytes;
         return LB3E_ERR_UNSUPPORTED;
     }
+    virtual int first_step() const { return 0; }
+    virtual int adjoint_step_x(const void* X, int first, const void* a_in, void* a_out, double* dparams, void* ws,
+                               size_t bytes) {
+        (void)X; (void)first; (void)a_in; (void)a_out; (void)dparams; (void)ws; (void)bytes;
+        return LB3E_ERR_UNSUPPORTED;
+    }
     virtual int deformation_seed(int which, double* D, void* a_out) {
         (void)which; (void)D; (void)a_out;
         return LB3E_ERR_UNSUPPORTED;

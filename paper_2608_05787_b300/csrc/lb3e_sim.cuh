@@ -176,6 +176,7 @@ class Sim final : public SimBase {
     ~Sim() override {
         if (pinned_) cudaFreeHost(pinned_);
         if (vgraph_) cudaGraphExecDestroy(vgraph_);
+        for (auto& g : adj_graphs_) cudaGraphExecDestroy(g.exec);
     }
 
     int init(const double* phi, const double* u, const double* q, const double* noise) override {
@@ -1021,8 +1022,65 @@ class Sim final : public SimBase {
             timer.begin(stream_, KC_OTHER);
             k_adj_export<R, S><<<blocks1(N_), 256, 0, stream_>>>(dp_, d_.pop[cur_], d_.phi, d_.h[hcur_], d_.E,
                                                                  d_.prev, static_cast<R*>(dst));
-            TRY(launched());
-            return sync();
+            return launched();
+        }
+        return LB3E_OK;
+    }
+    int first_step() const override { return step_ == 0; }
+    // one step backwards from a state vector: no snapshot, and with device dparams no
+    // host round trip; on a created stream the step's launches replay as a graph
+    int adjoint_step_x(const void* X, int first, const void* a_in, void* a_out, double* dparams, void* ws,
+                       size_t bytes) override {
+        TRY(adjoint_supported());
+        if constexpr (!is_dual<R>::value) {
+            if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0) return LB3E_ERR_WORKSPACE;
+            AdjointWS<R> w = AdjointWS<R>::make(dp_, adjoint_K(), static_cast<char*>(ws));
+            if (bytes < w.total) return LB3E_ERR_WORKSPACE;
+            cudaPointerAttributes at{};
+            const bool dev = cudaPointerGetAttributes(&at, dparams) == cudaSuccess &&
+                             (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+            cudaGetLastError();  // a host pointer may leave an error code behind on older drivers
+            if (dev) w.dpar = dparams;
+            else if (cudaMemsetAsync(w.dpar, 0, AJ_N * sizeof(double), stream_) != cudaSuccess) return LB3E_ERR_CUDA;
+            if (cudaMemcpyAsync(w.X, X, (size_t)AV_N * N_ * sizeof(R), cudaMemcpyDeviceToDevice, stream_) !=
+                cudaSuccess)
+                return LB3E_ERR_CUDA;
+            TRY(AdjointRunner<R>::prepare());
+            AdjointRunner<R> run{dp_, adjoint_K(), stream_, w};
+            const R* ain = static_cast<const R*>(a_in);
+            R* aout = static_cast<R*>(a_out);
+            if (stream_ == nullptr) {  // the legacy stream cannot be captured
+                TRY(run.step_T(first != 0, ain, aout));
+                launches += run.launches;
+            } else {
+                cudaGraphExec_t exec = nullptr;
+                for (auto& g : adj_graphs_)
+                    if (g.ws == ws && g.ain == a_in && g.aout == a_out && g.first == (first != 0) && g.dpar == w.dpar)
+                        exec = g.exec;
+                if (!exec) {
+                    if (adj_graphs_.size() >= 8) {
+                        cudaGraphExecDestroy(adj_graphs_.front().exec);
+                        adj_graphs_.erase(adj_graphs_.begin());
+                    }
+                    cudaGraph_t graph = nullptr;
+                    if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                        return LB3E_ERR_CUDA;
+                    const int rc = run.step_T(first != 0, ain, aout);
+                    if (cudaStreamEndCapture(stream_, &graph) != cudaSuccess || rc != LB3E_OK) {
+                        if (graph) cudaGraphDestroy(graph);
+                        return rc != LB3E_OK ? rc : LB3E_ERR_CUDA;
+                    }
+                    const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+                    cudaGraphDestroy(graph);
+                    if (e != cudaSuccess) return LB3E_ERR_CUDA;
+                    adj_graphs_.push_back({ws, a_in, a_out, first != 0, w.dpar, exec, run.launches});
+                }
+                if (cudaGraphLaunch(exec, stream_) != cudaSuccess) return LB3E_ERR_CUDA;
+                for (auto& g : adj_graphs_)
+                    if (g.exec == exec) launches += g.nodes;
+            }
+            if (!dev) return adjoint_params_out(w, dparams);
+            return cudaGetLastError() == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
         }
         return LB3E_OK;
     }
@@ -1036,6 +1094,7 @@ class Sim final : public SimBase {
             k_adj_export<R, S><<<blocks1(N_), 256, 0, stream_>>>(dp_, d_.pop[cur_], d_.phi, d_.h[hcur_], d_.E,
                                                                  d_.prev, w.X);
             TRY(launched());
+            TRY(AdjointRunner<R>::prepare());
             AdjointRunner<R> run{dp_, adjoint_K(), stream_, w};
             TRY(run.step_T(step_ == 0, static_cast<const R*>(a_in), static_cast<R*>(a_out)));
             launches += run.launches;
@@ -1051,6 +1110,7 @@ class Sim final : public SimBase {
             TRY(adjoint_ws(ws, bytes, &w));
             TRY(upload(phi, 3 * N_, w.X));  // phi_init in the first state-vector planes
             if (cudaMemsetAsync(d_.stage, 0, 3 * N_ * sizeof(double), stream_) != cudaSuccess) return LB3E_ERR_CUDA;
+            TRY(AdjointRunner<R>::prepare());
             AdjointRunner<R> run{dp_, adjoint_K(), stream_, w};
             TRY(run.init_T(w.X, static_cast<const R*>(a_in), d_.stage));
             launches += run.launches;
@@ -1104,6 +1164,16 @@ class Sim final : public SimBase {
     }
 
   private:
+    struct AdjGraph {
+        const void* ws;
+        const void* ain;
+        const void* aout;
+        bool first;
+        const double* dpar;
+        cudaGraphExec_t exec;
+        int64_t nodes;
+    };
+    std::vector<AdjGraph> adj_graphs_;  // captured backward steps (at most 8)
     template <class W>
     int adjoint_ws(void* ws, size_t bytes, W* w) {
         if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0) return LB3E_ERR_WORKSPACE;

@@ -23,36 +23,45 @@ def reverse_gradient(params: dict, phi, steps: int, objective: str = "deformatio
     """J after `steps` steps and its gradient by reverse mode: returns (J, {slot:
     dJ/dslot} over ADJ_PARAMS, dJ/dphi_init or None).  The forward run keeps a
     snapshot every `checkpoint_every` steps (device memory); the backward sweep
-    re-runs each segment from its snapshot, keeping that segment's states, and steps
-    back through them with lb3e_adjoint_step.  `objective`: "deformation" (D of
+    re-runs each segment from its snapshot, keeping each step's state vector
+    (lb3e_state_vector), and steps back through them with lb3e_adjoint_step_x on a
+    stream of its own (each backward step a replayed CUDA graph, the parameter
+    gradient accumulated on the device).  `objective`: "deformation" (D of
     lb3e_deformation, `which` inner or outer) or "shape" (lb3e_shape_objective
     against `target`).  The parameters must give a fixed potential count
     (poisson_fixed_iter > 0, potential_solver 0)."""
-    sim = Sim(params, phi)
+    import torch
+    stream = torch.cuda.Stream()
     C = max(1, int(checkpoint_every))
-    ckpt = {}
-    for n in range(steps):
-        if n % C == 0:
-            ckpt[n] = sim.save_state()
-        sim.step(1)
-    J, a = sim.deformation_seed(which) if objective == "deformation" else sim.shape_seed(target)
-    b = a.clone()
-    dpar = np.zeros(len(ADJ_PARAMS))
-    for start in sorted(ckpt, reverse=True):
-        snaps = [ckpt[start]]
-        sim.load_state(ckpt[start])
-        for _ in range(start + 1, min(start + C, steps)):
+    with torch.cuda.stream(stream):
+        sim = Sim(params, phi, stream=stream)
+        ckpt = {}
+        for n in range(steps):
+            if n % C == 0:
+                ckpt[n] = sim.save_state()
             sim.step(1)
-            snaps.append(sim.save_state())
-        for snap in reversed(snaps):
-            _, dp = sim.adjoint_step(a, state=snap, out=b)
-            a, b = b, a
-            dpar += dp
-        del snaps
-    dp0, dphi0 = sim.adjoint_init(phi, a, want_dphi=want_dphi)
-    dpar += dp0
+        J, a = sim.deformation_seed(which) if objective == "deformation" else sim.shape_seed(target)
+        b = torch.empty_like(a)
+        dpar = torch.zeros(len(ADJ_PARAMS), dtype=torch.float64, device=a.device)
+        for start in sorted(ckpt, reverse=True):
+            sim.load_state(ckpt[start])
+            n_seg = min(start + C, steps) - start
+            X = torch.empty((n_seg,) + tuple(a.shape), dtype=a.dtype, device=a.device)
+            first = []
+            for k in range(n_seg):
+                first.append(sim.is_first_step)
+                sim.state_vector(out=X[k])
+                if k + 1 < n_seg:
+                    sim.step(1)
+            for k in reversed(range(n_seg)):
+                sim.adjoint_step_x(X[k], first[k], a, b, dpar)
+                a, b = b, a
+            del X
+        dp0, dphi0 = sim.adjoint_init(phi, a, want_dphi=want_dphi)
+        stream.synchronize()
+        total = dpar.cpu().numpy() + dp0
     sim.close()
-    return J, dict(zip(ADJ_PARAMS, dpar.tolist())), dphi0
+    return J, dict(zip(ADJ_PARAMS, total.tolist())), dphi0
 
 
 def deformation_tangents(params: dict, phi, steps: int, wrt=("V_top", "eps3", "gamma23"),

@@ -168,6 +168,33 @@ def test_reverse_autograd_function():
     assert abs(g23.grad.item() - g["gamma23"]) <= 1e-12 * abs(g["gamma23"])
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_state_vector_form_equals_the_snapshot_form(precision):
+    """lb3e_adjoint_step_x from a state vector (graph-replayed on a created stream,
+    device dparams) gives the bits of lb3e_adjoint_step from the snapshot."""
+    import torch
+    import paper_2608_05787_b300 as L
+    p, phi = _case(precision=precision)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = L.Sim(p, phi, stream=stream).step(2)
+        snap = sim.save_state()
+        X = sim.state_vector()
+        first = sim.is_first_step
+        dt = sim.compute_dtype
+        a = torch.randn((64, p["ny"], p["nx"]), dtype=torch.float64, device="cuda", generator=torch.Generator(
+            "cuda").manual_seed(3)).to(dt)
+        out1, d1 = sim.adjoint_step(a, state=snap)
+        dp = torch.zeros(11, dtype=torch.float64, device="cuda")
+        out2 = torch.empty_like(a)
+        for _ in range(2):  # the second call replays the captured graph
+            dp.zero_()
+            sim.adjoint_step_x(X, first, a, out2, dp)
+        stream.synchronize()
+    assert torch.equal(out1, out2)
+    assert np.array_equal(d1, dp.cpu().numpy())
+
+
 def test_unsupported_configurations_are_refused():
     import torch
     import paper_2608_05787_b300 as L
