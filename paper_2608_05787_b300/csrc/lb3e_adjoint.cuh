@@ -811,44 +811,7 @@ __global__ void k_adj_seed_shape(DevParams P, const R* __restrict__ phi, const d
 }
 
 // ============================================================ potential iterations in tiles
-// Both the re-run of the potential iterations and their transpose advance PT_H
-// iterations per launch on a tile of PT_TX x PT_TY cells held in shared memory with
-// a halo of PT_H cells (one thread per tile cell): after t iterations the values
-// within t cells of the tile's edge are stale, so the interior is exact after PT_H.
-constexpr int PT_TX = 32, PT_TY = 8, PT_H = 4, PT_W = PT_TX + 2 * PT_H, PT_HT = PT_TY + 2 * PT_H;
-constexpr int PT_NT = PT_W * PT_HT;  // 640 threads
-template <class R>
-constexpr size_t pt_smem_bytes() { return 2 * 9 * PT_NT * sizeof(R); }
-
-struct TileCell {
-    int t, c;          // tile index, lattice index (0 where absent)
-    bool present;      // the lattice has this cell (not beyond a wall)
-    bool interior;     // this launch's tile owns it (writes it back)
-    int gy;            // lattice row
-};
-__device__ __forceinline__ TileCell tile_cell(const DevParams& P) {
-    TileCell r;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    r.t = ty * PT_W + tx;
-    const int x0 = blockIdx.x * PT_TX, y0 = blockIdx.y * PT_TY;
-    int gx = x0 - PT_H + tx, gy = y0 - PT_H + ty;
-    gx = ((gx % P.nx) + P.nx) % P.nx;
-    r.present = true;
-    if (P.bc_y == 0) gy = ((gy % P.ny) + P.ny) % P.ny;
-    else r.present = gy >= 0 && gy < P.ny;
-    r.gy = gy;
-    r.c = r.present ? gy * P.nx + gx : 0;
-    r.interior = r.present && tx >= PT_H && tx < PT_H + PT_TX && ty >= PT_H && ty < PT_H + PT_TY &&
-                 x0 + tx - PT_H < P.nx && y0 + ty - PT_H < P.ny;
-    return r;
-}
-// tile index of the neighbour at (dx, dy), clamped into the tile (a clamped read only
-// happens in the stale rim)
-__device__ __forceinline__ int tile_nb(int dx, int dy) {
-    const int tx = min(max((int)threadIdx.x + dx, 0), PT_W - 1);
-    const int ty = min(max((int)threadIdx.y + dy, 0), PT_HT - 1);
-    return ty * PT_W + tx;
-}
+// (the tile geometry PT_* and tile_cell / tile_nb are those of k_poisson_tile)
 
 // nit (<= PT_H) pseudo-time iterations of Eq. 43 from hin to hout, the first moment
 // J of each input iterate to J + 2 N t (t = 0 .. nit - 1)

@@ -673,6 +673,129 @@ __global__ void __launch_bounds__(256) k_poisson_rs(DevParams P, const R* __rest
                           gridDim.x, rres);
 }
 
+// ---------------------------------------------------------------- S5 on tiles, one thread a cell
+// Up to PT_H pseudo-iterations per launch on a tile of PT_TX x PT_TY cells held in
+// shared memory with a halo of PT_H cells, one thread per tile cell: each iteration
+// collides every cell into a post-collision buffer, then each cell pulls its
+// incoming populations (at a wall, its own reflected ones).  After t iterations the
+// values within t cells of the tile's edge are stale, so the interior is exact after
+// PT_H.  Used where a value is too wide for the register tiles of k_poisson_tb (the
+// dual numbers of the tangent builds) and by the reverse mode.
+// The tile geometry: TY rows of PT_TX cells with an H-cell halo.
+template <int TY, int H>
+struct PTGeom {
+    static constexpr int TX = 32, W = TX + 2 * H, HT = TY + 2 * H, NT = W * HT;
+};
+// the reverse mode's tiles: 32 x 8 with a 4-cell halo (640 threads)
+constexpr int PT_TX = 32, PT_TY = 8, PT_H = 4, PT_W = PT_TX + 2 * PT_H, PT_HT = PT_TY + 2 * PT_H;
+constexpr int PT_NT = PT_W * PT_HT;
+template <class R>
+constexpr size_t pt_smem_bytes() { return 2 * 9 * PT_NT * sizeof(R); }
+// the tangent builds' tiles: the same 32 x 8 with a 4-cell halo (dual numbers take 16
+// bytes a value: two sets of 9 planes fill 184 KB; a 2-cell halo on 32 x 16 tiles,
+// 8 launches a step instead of 4, measured slower)
+using PTTangent = PTGeom<8, 4>;
+
+struct TileCell {
+    int t, c;          // tile index, lattice index (0 where absent)
+    bool present;      // the lattice has this cell (not beyond a wall)
+    bool interior;     // this launch's tile owns it (writes it back)
+    int gy;            // lattice row
+};
+template <class G>
+__device__ __forceinline__ TileCell tile_cell_g(const DevParams& P, int H) {
+    TileCell r;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    r.t = ty * G::W + tx;
+    const int x0 = blockIdx.x * G::TX, y0 = blockIdx.y * (G::HT - 2 * H);
+    int gx = x0 - H + tx, gy = y0 - H + ty;
+    gx = ((gx % P.nx) + P.nx) % P.nx;
+    r.present = true;
+    if (P.bc_y == 0) gy = ((gy % P.ny) + P.ny) % P.ny;
+    else r.present = gy >= 0 && gy < P.ny;
+    r.gy = gy;
+    r.c = r.present ? gy * P.nx + gx : 0;
+    r.interior = r.present && tx >= H && tx < H + G::TX && ty >= H && ty < G::HT - H && x0 + tx - H < P.nx &&
+                 y0 + ty - H < P.ny;
+    return r;
+}
+__device__ __forceinline__ TileCell tile_cell(const DevParams& P) { return tile_cell_g<PTGeom<PT_TY, PT_H>>(P, PT_H); }
+// tile index of the neighbour at (dx, dy), clamped into the tile (a clamped read only
+// happens in the stale rim)
+template <class G>
+__device__ __forceinline__ int tile_nb_g(int dx, int dy) {
+    const int tx = min(max((int)threadIdx.x + dx, 0), G::W - 1);
+    const int ty = min(max((int)threadIdx.y + dy, 0), G::HT - 1);
+    return ty * G::W + tx;
+}
+__device__ __forceinline__ int tile_nb(int dx, int dy) { return tile_nb_g<PTGeom<PT_TY, PT_H>>(dx, dy); }
+
+// nit (<= 4) iterations of Eq. 43 with the arithmetic of body_poisson (fixed counts:
+// no residual sums), on the tangent builds' tiles
+template <class R>
+__global__ void __launch_bounds__(PTTangent::NT) k_poisson_tile(DevParams P, const R* __restrict__ hin,
+                                                                R* __restrict__ hout, const R* __restrict__ eps,
+                                                                const R* __restrict__ q, int nit) {
+    using G = PTTangent;
+    extern __shared__ __align__(16) unsigned char ptl_raw[];
+    R* cur = reinterpret_cast<R*>(ptl_raw);
+    R* post = cur + 9 * G::NT;
+    const TileCell tc = tile_cell_g<G>(P, 4);
+    const int N = P.N, ny = P.ny;
+    const R th = pv<R>(P.tau_h, P.ftau_h), ith = kconst<R>(P.fitau_h, [&] { return rcp(th); });
+    R epshat = R(0), den = R(1), iden = R(1), qc = R(0);
+    if (tc.present) {
+        epshat = eps[tc.c] - pv<R>(P.eps_ref, P.feps_ref);
+        den = epshat + cs2<R>() * th;
+        iden = rcp(den);
+        qc = q[tc.c];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) cur[j * G::NT + tc.t] = hin[(size_t)j * N + tc.c];
+    }
+    const R Kc = R(3) * ith * epshat * iden;
+    for (int it = 0; it < nit; ++it) {
+        __syncthreads();
+        if (tc.present) {
+            R hj[9];
+#pragma unroll
+            for (int j = 0; j < 9; ++j) hj[j] = cur[j * G::NT + tc.t];
+            R ps = R(0), jx = R(0), jy = R(0);
+#pragma unroll
+            for (int j = 1; j < 9; ++j) ps += hj[j];
+            ps = dv(ps, R(1) - wgt<R>(0), R(1.8));
+#pragma unroll
+            for (int j = 0; j < 9; ++j) { cacc(jx, cx(j), hj[j]); cacc(jy, cy(j), hj[j]); }
+            const R gx = dv(-jx, den, iden), gy = dv(-jy, den, iden);
+#pragma unroll
+            for (int j = 0; j < 9; ++j)
+                post[j * G::NT + tc.t] = h_collide<R>(j, hj[j], ps, gx, gy, jx, jy, th, ith, epshat, Kc, qc,
+                                                      R(0.125) * qc);
+        }
+        __syncthreads();
+        if (tc.present) {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const int ys = tc.gy - cy(j);
+                R v;
+                if (P.bc_y != 0 && (ys < 0 || ys >= ny)) {
+                    const R o = post[opp(j) * G::NT + tc.t];
+                    if (P.bc_y == 2)
+                        v = -o + R(2) * wgt<R>(j) * (ys >= ny ? prm<R>(P.V_top, P.t_Vt, P.fVt)
+                                                              : prm<R>(P.V_bottom, P.t_Vb, P.fVb));
+                    else
+                        v = o;
+                } else {
+                    v = post[j * G::NT + tile_nb_g<G>(-cx(j), -cy(j))];
+                }
+                cur[j * G::NT + tc.t] = v;
+            }
+        }
+    }
+    if (tc.interior)
+#pragma unroll
+        for (int j = 0; j < 9; ++j) hout[(size_t)j * N + tc.c] = cur[j * G::NT + tc.t];
+}
+
 // ---------------------------------------------------------------- S5, temporally blocked
 // K (<= H) pseudo-iterations of Eq. 43 per launch.  A block loads the h
 // populations of its PB_TX x PB_TY tile plus an H-cell halo into registers (three

@@ -1454,6 +1454,14 @@ class Sim final : public SimBase {
 
     // blocked-iteration kernels need more than the default dynamic shared memory
     int pb_prepare() {
+        if constexpr (is_dual<R>::value) {
+            if (!pb_ready_) {
+                if (cudaFuncSetAttribute(k_poisson_tile<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * 9 * PTTangent::NT * sizeof(R))) != cudaSuccess)
+                    return LB3E_ERR_CUDA;
+                pb_ready_ = true;
+            }
+        }
         if constexpr (!is_dual<R>::value) {
             if (!pb_ready_) {
                 if (cudaFuncSetAttribute(k_poisson_tb<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1517,7 +1525,7 @@ class Sim final : public SimBase {
     int set_chunk(int k) override {
         if (k < 1 || k > PB_HALO) return LB3E_ERR_PARAM;
         if constexpr (is_dual<R>::value) {
-            if (k != 1) return LB3E_ERR_PARAM;
+            if (k > 4) return LB3E_ERR_PARAM;
         }
         chunk_ = k;
         return LB3E_OK;
@@ -1549,7 +1557,19 @@ class Sim final : public SimBase {
             const int do_check = fixed <= 0 && k >= 2 && k % check == 0;
             const int save = fixed <= 0 && (k + c) % check == 0;
             bool blocked = false;
-            if constexpr (!is_dual<R>::value) {  // dual tiles would not fit in shared memory
+            if constexpr (is_dual<R>::value) {  // dual numbers: tiles of one cell a thread
+                if (fixed > 0 && c >= 2) {
+                    using G = PTTangent;
+                    c = c < 4 ? c : 4;
+                    timer.begin(stream_, KC_POISSON);
+                    k_poisson_tile<R><<<dim3((p_.nx + G::TX - 1) / G::TX, (p_.ny + G::HT - 9) / (G::HT - 8)),
+                                        dim3(G::W, G::HT), 2 * 9 * G::NT * sizeof(R), stream_>>>(
+                        dp_, d_.h[hcur_], d_.h[hcur_ ^ 1], d_.eps, d_.q, c);
+                    TRY(launched());
+                    poisson_iters_run_ += c;
+                    blocked = true;
+                }
+            } else {
                 if (c >= 2) {
                     timer.begin(stream_, KC_POISSON);
                     pblk = pb_launch(pgrid, c, save, do_check);
