@@ -84,8 +84,8 @@ def test_fp64_tangent_matches_gpu_and_oracle_central_differences():
 # to a few 1e-3 (measured 4.8e-3); the field and permittivity derivatives agree to
 # a few 1e-6.
 FP32_TOL = {"V_top": 1e-4, "eps3": 1e-4, "gamma23": 1e-2}
-# the same over the stated 4000 steps at 256^2
-FP32_TOL_4000 = {"V_top": 2e-3, "eps3": 2e-3, "gamma23": 3e-2}
+# the same over the stated 4000 steps at 256^2 (measured 4.7e-4, 4.7e-4, 5.5e-4)
+FP32_TOL_4000 = {"V_top": 2e-3, "eps3": 2e-3, "gamma23": 2e-3}
 
 
 def test_fp32_tangent_matches_fp64_tangent():
