@@ -779,10 +779,10 @@ class Sim final : public SimBase {
     // One FP32 V-cycle on level 0's A e = rhs (rhs and e = 0 set by the caller):
     // 2 red-black pre- and post-sweeps per level, residual restriction by sums of the
     // four children, bilinear prolongation, 50 sweeps on the coarsest level.  With
-    // first > 0 the cycle starts on level 1 from the restricted level-0 rhs and ends
-    // with the prolongation of its solution to level 0: no level-0 sweeps (the
-    // coarse correction of the LB solve, whose own iterations smooth the fine
-    // level).  About 10 launches a level, most of them small: on a created stream
+    // first > 0 the cycle starts on level `first` from the level-0 rhs restricted down
+    // to it and ends with the prolongations of its solution back to level 0: no sweeps
+    // on the levels above it (the coarse correction of the LB solve, whose own
+    // iterations smooth the fine scales).  About 10 launches a level, most of them small: on a created stream
     // the sequence is captured once as a CUDA graph and replayed (the level pointers
     // are fixed for the simulation's lifetime; a simulation uses one first level),
     // timed as one interval of class kc.
@@ -815,7 +815,7 @@ class Sim final : public SimBase {
     }
     int vcycle_launches(int kc, bool timed, int first = 0) {
         const int nl = (int)mgf_.size();
-        if (first >= nl) first = 0;
+        if (first > nl - 1) first = nl - 1;  // a small lattice: start on its coarsest level
         const dim3 blk(TX, TY);
         auto begin = [&]() { if (timed) timer.begin(stream_, kc); };
         auto done = [&]() -> int {
@@ -832,13 +832,14 @@ class Sim final : public SimBase {
                 }
             return LB3E_OK;
         };
-        if (first > 0) {  // level 0's residual is its rhs (e = 0): restricted to level 1
-            first = 1;
-            MGLevelF f0 = mgf_[0];
-            f0.res = f0.rhs;
-            begin();
-            k_mg_restrict<float><<<mg_grid(1), blk, 0, stream_>>>(f0, mgf_[1]);
-            TRY(done());
+        if (first > 0) {  // with e = 0 each level's residual is its rhs: restricted down to level first
+            for (int l = 0; l < first; ++l) {
+                MGLevelF fl = mgf_[l];
+                fl.res = fl.rhs;
+                begin();
+                k_mg_restrict<float><<<mg_grid(l + 1), blk, 0, stream_>>>(fl, mgf_[l + 1]);
+                TRY(done());
+            }
         }
         if (nl == 1) {
             begin();
@@ -1635,7 +1636,7 @@ class Sim final : public SimBase {
     std::vector<MGLevel> mg_;
     std::vector<MGLevelF> mgf_;
     cudaGraphExec_t vgraph_ = nullptr;  // the captured V-cycle (multigrid solvers, created streams)
-    int lbmg_first_ = 1;                // first V-cycle level of the LB solve's coarse correction
+    int lbmg_first_ = 3;                // first V-cycle level of the LB solve's coarse correction
     int64_t vgraph_nodes_ = 0;
     // the anchor of the potential populations (solvers 2, 3): FP64 in the FP64 build,
     // double-float in the FP32 builds, with the refresh's coefficients in that form
