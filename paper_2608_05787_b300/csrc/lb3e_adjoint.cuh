@@ -1026,16 +1026,13 @@ struct AdjointRunner {
     unsigned nb() const { return (unsigned)((P.N + ADJ_THREADS - 1) / ADJ_THREADS); }
     dim3 pt_grid() const { return dim3((P.nx + PT_TX - 1) / PT_TX, (P.ny + PT_TY - 1) / PT_TY); }
     // the tiled potential kernels take more than the default 48 KB of shared memory
-    // in FP64 (call before any launch, outside a stream capture)
+    // in FP64: set on the current device (before any launch, outside a stream capture)
     static int prepare() {
-        static int done = 0;
-        if (done) return LB3E_OK;
         if (cudaFuncSetAttribute(k_adj_pot_tape<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)pt_smem_bytes<R>()) != cudaSuccess ||
             cudaFuncSetAttribute(k_adj_pot_T<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)pt_smem_bytes<R>()) != cudaSuccess)
             return LB3E_ERR_CUDA;
-        done = 1;
         return LB3E_OK;
     }
 

@@ -1046,7 +1046,10 @@ class Sim final : public SimBase {
             if (cudaMemcpyAsync(w.X, X, (size_t)AV_N * N_ * sizeof(R), cudaMemcpyDeviceToDevice, stream_) !=
                 cudaSuccess)
                 return LB3E_ERR_CUDA;
-            TRY(AdjointRunner<R>::prepare());
+            if (!adj_ready_) {
+                TRY(AdjointRunner<R>::prepare());
+                adj_ready_ = true;
+            }
             AdjointRunner<R> run{dp_, adjoint_K(), stream_, w};
             const R* ain = static_cast<const R*>(a_in);
             R* aout = static_cast<R*>(a_out);
@@ -1095,7 +1098,10 @@ class Sim final : public SimBase {
             k_adj_export<R, S><<<blocks1(N_), 256, 0, stream_>>>(dp_, d_.pop[cur_], d_.phi, d_.h[hcur_], d_.E,
                                                                  d_.prev, w.X);
             TRY(launched());
-            TRY(AdjointRunner<R>::prepare());
+            if (!adj_ready_) {
+                TRY(AdjointRunner<R>::prepare());
+                adj_ready_ = true;
+            }
             AdjointRunner<R> run{dp_, adjoint_K(), stream_, w};
             TRY(run.step_T(step_ == 0, static_cast<const R*>(a_in), static_cast<R*>(a_out)));
             launches += run.launches;
@@ -1111,7 +1117,10 @@ class Sim final : public SimBase {
             TRY(adjoint_ws(ws, bytes, &w));
             TRY(upload(phi, 3 * N_, w.X));  // phi_init in the first state-vector planes
             if (cudaMemsetAsync(d_.stage, 0, 3 * N_ * sizeof(double), stream_) != cudaSuccess) return LB3E_ERR_CUDA;
-            TRY(AdjointRunner<R>::prepare());
+            if (!adj_ready_) {
+                TRY(AdjointRunner<R>::prepare());
+                adj_ready_ = true;
+            }
             AdjointRunner<R> run{dp_, adjoint_K(), stream_, w};
             TRY(run.init_T(w.X, static_cast<const R*>(a_in), d_.stage));
             launches += run.launches;
@@ -1175,6 +1184,7 @@ class Sim final : public SimBase {
         int64_t nodes;
     };
     std::vector<AdjGraph> adj_graphs_;  // captured backward steps (at most 8)
+    bool adj_ready_ = false;             // the reverse mode's kernel attributes are set
     template <class W>
     int adjoint_ws(void* ws, size_t bytes, W* w) {
         if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0) return LB3E_ERR_WORKSPACE;
