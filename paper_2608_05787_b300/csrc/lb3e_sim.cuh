@@ -1437,16 +1437,26 @@ class Sim final : public SimBase {
                 if (pl.since == 0) stall_refreshed = false;  // progress since the last stall
                 if (it >= max_iter) break;
                 if (coarse) TRY(lbmg_correct(after_refresh));
-                const int m = max_iter - it < check ? max_iter - it : check;
-                int inc_blocks = 0;
-                TRY(rs_iterations(m, true, coarse, &inc_blocks));
-                it += m;
-                bool noisy = false;
-                TRY(rs_check(norms, coarse, tol, &res, &noisy, inc_blocks));
                 after_refresh = false;
-                if (noisy && res > tol) {  // the exact increment at a fresh anchor instead
-                    TRY(anchor_refresh(true, &res, norms, !coarse));
-                    after_refresh = true;
+                // with the coarse correction, the increment is also checked half-way
+                // through the cycle (a check costs a fraction of a correction)
+                const int nsub = coarse && check >= 16 ? 2 : 1;
+                for (int sub = 0; sub < nsub && it < max_iter; ++sub) {
+                    const int want = check / nsub + (sub < check % nsub ? 1 : 0);
+                    const int m = max_iter - it < want ? max_iter - it : want;
+                    // the coarse right-hand side only from the cycle's last check
+                    const bool rhs = coarse && (sub == nsub - 1 || it + m >= max_iter);
+                    int inc_blocks = 0;
+                    TRY(rs_iterations(m, true, rhs, &inc_blocks));
+                    it += m;
+                    bool noisy = false;
+                    TRY(rs_check(norms, rhs, tol, &res, &noisy, inc_blocks));
+                    if (noisy && res > tol) {  // the exact increment at a fresh anchor instead
+                        TRY(anchor_refresh(true, &res, norms, !coarse));
+                        after_refresh = true;
+                        break;
+                    }
+                    if (res <= tol) break;
                 }
             }
         }
