@@ -112,7 +112,9 @@ typedef struct lb3e_params {
     double poisson_tol;           /* stop when the relative increments of psi and of
                                      sum_j c_j h_j between pseudo-iterations are <= tol */
     int32_t poisson_max_iter;     /* iteration cap per solve */
-    int32_t poisson_check_every;  /* residual evaluated every this many iterations */
+    int32_t poisson_check_every;  /* residual evaluated every this many iterations (solver 2:
+                                     a coarse correction every this many, the residual
+                                     max(2, this / 16) times in between) */
     int32_t poisson_fixed_iter;   /* > 0: exactly this many iterations, no residual */
     int32_t _pad2;
     /* precision 3 and 4 only: the parameter each tangent direction (3, or the
@@ -129,7 +131,8 @@ typedef struct lb3e_params {
      *    gradient of psi;
      * 2: the LB solve of Eq. 42-45 (same fixed point as 0) with h held as an FP64
      *    anchor plus a correction in the build's precision, and a multigrid coarse
-     *    correction at every check (every poisson_check_every iterations): the
+     *    correction every poisson_check_every iterations (the increment is checked
+     *    max(2, poisson_check_every / 16) times a cycle, the last check feeding it): the
      *    residual of the macroscopic equation, read from the LB increment, drives
      *    one FP32 V-cycle of the finite-difference operator whose solution enters h
      *    as its local equilibrium.  The stopping test is the LB increment of 0,

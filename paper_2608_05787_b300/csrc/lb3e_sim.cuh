@@ -1438,9 +1438,9 @@ class Sim final : public SimBase {
                 if (it >= max_iter) break;
                 if (coarse) TRY(lbmg_correct(after_refresh));
                 after_refresh = false;
-                // with the coarse correction, the increment is also checked half-way
-                // through the cycle (a check costs a fraction of a correction)
-                const int nsub = coarse && check >= 16 ? 2 : 1;
+                // with the coarse correction, the increment is checked max(2, check/16)
+                // times a cycle (a check costs a fraction of a correction)
+                const int nsub = coarse && check >= 16 ? (check / 16 > 2 ? check / 16 : 2) : 1;
                 for (int sub = 0; sub < nsub && it < max_iter; ++sub) {
                     const int want = check / nsub + (sub < check % nsub ? 1 : 0);
                     const int m = max_iter - it < want ? max_iter - it : want;
