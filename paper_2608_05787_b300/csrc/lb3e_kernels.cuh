@@ -1917,19 +1917,69 @@ constexpr int NOBS = 19;
 // block reduction of the NOBS sums is shared by eight cells per thread.
 constexpr int OBS_Y = 8;
 inline dim3 obs_grid(int nx, int ny) { return dim3((nx + TX - 1) / TX, (ny + TY * OBS_Y - 1) / (TY * OBS_Y)); }
+// A thread's sums of its OBS_Y cells.  FP64: plain FP64 sums.  FP32 terms: an FP32
+// sum and the exact rounding error of each of its additions (Knuth's TwoSum),
+// accumulated beside it, so that s + c carries the sum to about the square of the
+// FP32 precision; converted to FP64 once per thread, where the block and grid
+// reductions continue.  (FP64 adds and conversions run at a small fraction of the
+// FP32 rate on this part, and the per-cell FP64 accumulation was most of the
+// kernel's time.)
+template <class T, int NV>
+struct ObsAcc {
+    double v[NV];
+    __device__ __forceinline__ ObsAcc() {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = 0.0;
+    }
+    __device__ __forceinline__ void add(int k, T x) { v[k] += (double)x; }
+    __device__ __forceinline__ void out(double (&o)[NV]) const {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) o[k] = v[k];
+    }
+};
+template <int NV>
+struct ObsAcc<float, NV> {
+    float s[NV], c[NV];
+    __device__ __forceinline__ ObsAcc() {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] = c[k] = 0.f;
+    }
+    __device__ __forceinline__ void add(int k, float x) {
+        const float t = __fadd_rn(s[k], x);
+        const float bp = __fsub_rn(t, s[k]);
+        const float e = __fadd_rn(__fsub_rn(s[k], __fsub_rn(t, bp)), __fsub_rn(x, bp));
+        s[k] = t;
+        c[k] = __fadd_rn(c[k], e);
+    }
+    __device__ __forceinline__ void out(double (&o)[NV]) const {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) o[k] = (double)s[k] + (double)c[k];
+    }
+};
+// |a + b + c - 1| for phase fractions near 1: FP64 in the FP64 build; in FP32 the two
+// additions are error-free transformed and 1 is subtracted exactly (Sterbenz)
+__device__ __forceinline__ double sum_dev3(double a, double b, double c) { return fabs(a + b + c - 1.0); }
+__device__ __forceinline__ float sum_dev3(float a, float b, float c) {
+    float s1 = __fadd_rn(a, b), bp = __fsub_rn(s1, a);
+    const float e1 = __fadd_rn(__fsub_rn(a, __fsub_rn(s1, bp)), __fsub_rn(b, bp));
+    const float s2 = __fadd_rn(s1, c);
+    bp = __fsub_rn(s2, s1);
+    const float e2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, bp)), __fsub_rn(c, bp));
+    return fabsf(__fadd_rn(__fsub_rn(s2, 1.0f), __fadd_rn(e1, e2)));
+}
+
 // Per-block FP64 sums of the NOBS observables (partial[b * NOBS + k]) and the
 // per-block max |sum phi - 1| (maxpart[b]).  The per-cell terms are evaluated in
 // FP32 in the FP32 builds and in FP64 otherwise (FP64 arithmetic runs at a small
-// fraction of the FP32 rate on this part); every sum and the max are FP64.
+// fraction of the FP32 rate on this part); a thread's sums are ObsAcc pairs, the
+// block and grid sums and the max FP64.
 template <class R>
 __global__ void __launch_bounds__(256) k_observables(DevParams P, const R* __restrict__ phi, const R* __restrict__ q,
                                                      const R* __restrict__ E, const R* __restrict__ diag,
                                                      double* __restrict__ partial, double* __restrict__ maxpart) {
     using T = typename std::conditional<std::is_same<R, float>::value, float, double>::type;
-    double v[NOBS];
-#pragma unroll
-    for (int k = 0; k < NOBS; ++k) v[k] = 0.0;
-    double mdev = 0.0;
+    ObsAcc<T, NOBS> acc;
+    T mdev = T(0);
     const int x = blockIdx.x * TX + threadIdx.x;
     for (int r = 0; r < OBS_Y; ++r) {
         const int y = blockIdx.y * (TY * OBS_Y) + r * TY + threadIdx.y;
@@ -1951,49 +2001,53 @@ __global__ void __launch_bounds__(256) k_observables(DevParams P, const R* __res
             ax = oc2(ax);
             ay = oc2(ay);
             ph[i] = (T)f[c];
-            v[i] += (double)ph[i];
+            acc.add(i, ph[i]);
             const T lam = pv<T>(P.lam[i], P.flam[i]);
             fphi += T(6) / D * lam * ph[i] * ph[i] * (T(1) - ph[i]) * (T(1) - ph[i]) +
                     T(0.375) * D * lam * (ax * ax + ay * ay);
         }
-        v[4] += (double)fphi;
+        acc.add(4, fphi);
         T eps = T(0);
 #pragma unroll
         for (int i = 0; i < 3; ++i) eps += pv<T>(P.eps[i], P.feps[i]) * ph[i] * ph[i] * (T(3) - T(2) * ph[i]);
         const T Ex = (T)E[c], Ey = (T)E[N + c];
-        v[5] += (double)(T(0.5) * eps * (Ex * Ex + Ey * Ey));
+        acc.add(5, T(0.5) * eps * (Ex * Ex + Ey * Ey));
         const T rho = ph[0] * pv<T>(P.rho[0], P.frho[0]) + ph[1] * pv<T>(P.rho[1], P.frho[1]) +
                       ph[2] * pv<T>(P.rho[2], P.frho[2]);
         const T ux = (T)diag[c], uy = (T)diag[N + c];
-        v[6] += (double)(T(0.5) * rho * (ux * ux + uy * uy));
+        acc.add(6, T(0.5) * rho * (ux * ux + uy * uy));
         const T sg = ph[0] * pv<T>(P.sigma[0], P.fsig[0]) + ph[1] * pv<T>(P.sigma[1], P.fsig[1]) +
                      ph[2] * pv<T>(P.sigma[2], P.fsig[2]);
         const T qc = (T)q[c];
-        if (sg > T(0)) v[7] += (double)(T(0.5) * (T(P.alpha) / sg) * qc * qc);
-        v[3] += (double)qc;
+        if (sg > T(0)) acc.add(7, T(0.5) * (T(P.alpha) / sg) * qc * qc);
+        acc.add(3, qc);
         const T vals[6] = {ph[0], ph[1], ph[2], ux, uy, qc};
 #pragma unroll
         for (int k = 0; k < 6; ++k)
-            if (!isfinite(vals[k])) v[8] += 1.0;
+            if (!isfinite(vals[k])) acc.add(8, T(1));
         const T chis[2] = {ph[P.inner], T(1) - ph[P.matrix]};
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            v[9 + 5 * k] += (double)chis[k];
-            v[10 + 5 * k] += (double)(chis[k] * T(x));
-            v[11 + 5 * k] += (double)(chis[k] * T(y));
-            v[12 + 5 * k] += (double)(chis[k] * T(x) * T(x));
-            v[13 + 5 * k] += (double)(chis[k] * T(y) * T(y));
+            acc.add(9 + 5 * k, chis[k]);
+            acc.add(10 + 5 * k, chis[k] * T(x));
+            acc.add(11 + 5 * k, chis[k] * T(y));
+            acc.add(12 + 5 * k, chis[k] * T(x) * T(x));
+            acc.add(13 + 5 * k, chis[k] * T(y) * T(y));
         }
-        mdev = fmax(mdev, fabs((double)ph[0] + (double)ph[1] + (double)ph[2] - 1.0));
+        const T dv = sum_dev3(ph[0], ph[1], ph[2]);
+        mdev = dv > mdev ? dv : mdev;  // as fmax: a NaN is left to the nonfinite count
     }
     const int b = blockIdx.x + gridDim.x * blockIdx.y;
+    double v[NOBS];
+    acc.out(v);
     block_reduce_store<NOBS>(v, partial + (size_t)NOBS * b);
     // block max of the sum deviation (the reduction above ends with a barrier-free
     // warp-0 stage, so this uses its own shared array)
-    for (int o = 16; o > 0; o >>= 1) mdev = fmax(mdev, __shfl_down_sync(0xffffffffu, mdev, o));
+    double md = (double)mdev;
+    for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_down_sync(0xffffffffu, md, o));
     __shared__ double mred[8];
     const int tid = threadIdx.x + TX * threadIdx.y;
-    if ((tid & 31) == 0) mred[tid >> 5] = mdev;
+    if ((tid & 31) == 0) mred[tid >> 5] = md;
     __syncthreads();
     if (tid == 0) {
         double a = 0.0;
