@@ -98,6 +98,43 @@ def test_fp32_step_backwards_is_close_to_the_oracle(kw):
     assert np.abs(d_gpu - d_orc).max() <= 1e-4 * np.abs(d_orc).max(), (d_gpu, d_orc)
 
 
+@pytest.mark.parametrize("precision", [2, 5])
+def test_narrow_storage_step_backwards_is_close_to_the_oracle(precision):
+    """FP16- and BF16-stored populations: the state vector rebuilds the full rest
+    populations from their stored deviations, and the transposed step runs in FP32 on
+    it; against the oracle's at the storage's own precision (1e-2 of each group's
+    norm for FP16's 11 bits, BF16's 8)."""
+    import torch
+    import paper_2608_05787_b300 as L
+    p, phi = _case(precision=precision)
+    sim = L.Sim(p, phi).step(3)
+    o = oracle.Oracle(dict(p, precision=0), phi).step(3)
+    scale = np.maximum(np.abs(o.clone().step(1).state_vector()).max(axis=(1, 2), keepdims=True), 1e-8)
+    a = _seed((p["ny"], p["nx"]), scale, seed=6)
+    a_orc, d_orc = o.adjoint_step(a)
+    a_gpu, d_gpu = sim.adjoint_step(torch.from_numpy(a).float().cuda())
+    a_gpu = a_gpu.double().cpu().numpy()
+    for k, (i0, i1) in GROUPS.items():
+        num = np.linalg.norm(a_gpu[i0:i1] - a_orc[i0:i1])
+        den = np.linalg.norm(a_orc[i0:i1])
+        assert num <= 1e-2 * den + 1e-30, (k, num / den)
+    assert np.abs(d_gpu - d_orc).max() <= 1e-2 * np.abs(d_orc).max(), (d_gpu, d_orc)
+
+
+def test_fp32_creation_backwards_is_close_to_the_oracle():
+    import torch
+    import paper_2608_05787_b300 as L
+    p, phi = _case(precision=1)
+    sim = L.Sim(p, phi)
+    o = oracle.Oracle(dict(p, precision=0), phi)
+    scale = np.maximum(np.abs(o.state_vector()).max(axis=(1, 2), keepdims=True), 1e-8)
+    a = _seed((p["ny"], p["nx"]), scale, seed=10)
+    d_orc, dphi_orc = oracle.adjoint_init(p, phi, a)
+    d_gpu, dphi_gpu = sim.adjoint_init(phi, torch.from_numpy(a).float().cuda())
+    assert np.abs(d_gpu - d_orc).max() <= 1e-4 * np.abs(d_orc).max(), (d_gpu, d_orc)
+    assert np.linalg.norm(dphi_gpu - dphi_orc) <= 1e-4 * np.linalg.norm(dphi_orc)
+
+
 @pytest.mark.parametrize("kw", [dict(), dict(bc_y=0)])
 def test_fp64_creation_backwards_matches_the_oracle(kw):
     import torch
