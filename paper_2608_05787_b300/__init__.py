@@ -233,9 +233,12 @@ class Sim:
     may be host numpy arrays or CUDA tensors (float64, ``[.., ny, nx]``).
     """
 
-    def __init__(self, params: dict, phi, u=None, q=None, noise=None, stream=None, device=None, ions=None):
+    def __init__(self, params: dict, phi, u=None, q=None, noise=None, stream=None, device=None, ions=None,
+                 workspace=None):
         """``ions``: initial concentrations [2, ny, nx] of the Nernst-Planck species
-        (parameters with ``ions`` = 1), set through ``lb3e_set_ions``."""
+        (parameters with ``ions`` = 1), set through ``lb3e_set_ions``.  ``workspace``:
+        a caller-allocated uint8 CUDA tensor of at least ``workspace_bytes(params)``
+        bytes to run in (allocated here if None)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("lb3e needs a CUDA device (there is no CPU fallback)")
@@ -248,7 +251,12 @@ class Sim:
         self.device = torch.device(device or "cuda")
         self._p = Params.from_dict(self.params)
         nbytes = workspace_bytes(self.params)
-        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        elif not (isinstance(workspace, torch.Tensor) and workspace.is_cuda and workspace.dtype == torch.uint8
+                  and workspace.numel() >= nbytes):
+            raise ValueError(f"workspace: a uint8 CUDA tensor of at least {nbytes} bytes")
+        self.workspace = workspace
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         keep = [_addr(a) for a in (phi, u, q, noise)]
         h = C.c_void_p(None)
