@@ -63,6 +63,12 @@ struct P3 {
     double rho[3], visc[3], tau_g, lam[3], D, tau_f, m0, eps[3], sigma[3], eps_ref, tau_h, tau_l;
     double V_bottom, V_top, E0, E1, uwb, uwt;
     int inner, matrix;
+    // FP32 roundings of the above and of the reciprocals the collisions take, formed on
+    // the host (a double parameter converted or divided in device code costs FP64
+    // instructions, a small fraction of the FP32 rate on this part)
+    float frho[3], fvisc[3], flam[3], feps[3], fsig[3];
+    float fD, ftau_f, fitau_f, fm0, fim0, ftau_g, ftau_l, fitau_l, feps_ref, ftau_h, fitau_h;
+    float fVb, fVt, fE0, fE1, fuwb, fuwt;
 };
 
 inline P3 make_p3(const lb3e_params& p) {
@@ -82,6 +88,16 @@ inline P3 make_p3(const lb3e_params& p) {
     q.V_bottom = p.V_bottom; q.V_top = p.V_top; q.E0 = p.E_ext[0]; q.E1 = p.E_ext[1];
     q.uwb = p.u_wall_bottom; q.uwt = p.u_wall_top;
     q.inner = p.inner_phase; q.matrix = p.matrix_phase;
+    for (int i = 0; i < 3; ++i) {
+        q.frho[i] = (float)q.rho[i]; q.fvisc[i] = (float)q.visc[i]; q.flam[i] = (float)q.lam[i];
+        q.feps[i] = (float)q.eps[i]; q.fsig[i] = (float)q.sigma[i];
+    }
+    q.fD = (float)q.D; q.ftau_f = (float)q.tau_f; q.fitau_f = (float)(1.0 / q.tau_f);
+    q.fm0 = (float)q.m0; q.fim0 = (float)(1.0 / q.m0); q.ftau_g = (float)q.tau_g;
+    q.ftau_l = (float)q.tau_l; q.fitau_l = (float)(1.0 / q.tau_l); q.feps_ref = (float)q.eps_ref;
+    q.ftau_h = (float)q.tau_h; q.fitau_h = (float)(1.0 / q.tau_h);
+    q.fVb = (float)q.V_bottom; q.fVt = (float)q.V_top; q.fE0 = (float)q.E0; q.fE1 = (float)q.E1;
+    q.fuwb = (float)q.uwb; q.fuwt = (float)q.uwt;
     return q;
 }
 
@@ -188,11 +204,11 @@ __global__ void __launch_bounds__(256) k3_moments(P3 P, const R* __restrict__ po
 #pragma unroll
     for (int j = 0; j < Q3; ++j) a += pop[(Q3 * 4 + j) * N + c];
     qt[c] = a;
-    rho[c] = ph[0] * R(P.rho[0]) + ph[1] * R(P.rho[1]) + ph[2] * R(P.rho[2]);   // Eq. 29
-    sig[c] = ph[0] * R(P.sigma[0]) + ph[1] * R(P.sigma[1]) + ph[2] * R(P.sigma[2]);
+    rho[c] = ph[0] * pv<R>(P.rho[0], P.frho[0]) + ph[1] * pv<R>(P.rho[1], P.frho[1]) + ph[2] * pv<R>(P.rho[2], P.frho[2]);   // Eq. 29
+    sig[c] = ph[0] * pv<R>(P.sigma[0], P.fsig[0]) + ph[1] * pv<R>(P.sigma[1], P.fsig[1]) + ph[2] * pv<R>(P.sigma[2], P.fsig[2]);
     R e = R(0);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) e += R(P.eps[i]) * ph[i] * ph[i] * (R(3) - R(2) * ph[i]);   // Eq. 30
+    for (int i = 0; i < 3; ++i) e += pv<R>(P.eps[i], P.feps[i]) * ph[i] * ph[i] * (R(3) - R(2) * ph[i]);   // Eq. 30
     eps[c] = e;
 }
 // properties only (initial state)
@@ -204,11 +220,11 @@ __global__ void __launch_bounds__(256) k3_props(P3 P, const R* __restrict__ phi,
     if (!cell3(P, x, y, z, c)) return;
     const size_t N = P.N;
     const R ph[3] = {phi[c], phi[N + c], phi[2 * N + c]};
-    rho[c] = ph[0] * R(P.rho[0]) + ph[1] * R(P.rho[1]) + ph[2] * R(P.rho[2]);
-    sig[c] = ph[0] * R(P.sigma[0]) + ph[1] * R(P.sigma[1]) + ph[2] * R(P.sigma[2]);
+    rho[c] = ph[0] * pv<R>(P.rho[0], P.frho[0]) + ph[1] * pv<R>(P.rho[1], P.frho[1]) + ph[2] * pv<R>(P.rho[2], P.frho[2]);
+    sig[c] = ph[0] * pv<R>(P.sigma[0], P.fsig[0]) + ph[1] * pv<R>(P.sigma[1], P.fsig[1]) + ph[2] * pv<R>(P.sigma[2], P.fsig[2]);
     R e = R(0);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) e += R(P.eps[i]) * ph[i] * ph[i] * (R(3) - R(2) * ph[i]);
+    for (int i = 0; i < 3; ++i) e += pv<R>(P.eps[i], P.feps[i]) * ph[i] * ph[i] * (R(3) - R(2) * ph[i]);
     eps[c] = e;
 }
 
@@ -256,12 +272,13 @@ __device__ __forceinline__ void hmoments3(const R* __restrict__ h, size_t N, siz
 
 // One pseudo-iteration: collide and push-stream h.  save: store psi, J (the state
 // a later check compares with); check: accumulate |d psi|^2, |psi|^2, |dJ|^2, |J|^2
-// per block (FP64 partials).
+// per block (FP64 partials).  FP32: held to 64 registers (four blocks an SM); the
+// scheduler otherwise keeps all 15 populations live across the moments (79
+// registers, three blocks an SM, measured 10% slower).
 template <class R>
-__global__ void __launch_bounds__(256) k3_poisson(P3 P, const R* __restrict__ hin, R* __restrict__ hout,
-                                                  const R* __restrict__ eps, const R* __restrict__ q,
-                                                  R* __restrict__ prev, double* __restrict__ partial, int save,
-                                                  int check) {
+__global__ void __launch_bounds__(256, std::is_same<R, float>::value ? 4 : 1)
+    k3_poisson(P3 P, const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ eps,
+               const R* __restrict__ q, R* __restrict__ prev, double* __restrict__ partial, int save, int check) {
     int x, y, z;
     size_t c;
     const bool in = cell3(P, x, y, z, c);
@@ -287,7 +304,7 @@ __global__ void __launch_bounds__(256) k3_poisson(P3 P, const R* __restrict__ hi
             for (int a = 0; a < 3; ++a) prev[(1 + a) * N + c] = J[a];
         }
         // divisions: exact in the FP64 build, by a reciprocal formed once in FP32
-        const R th = R(P.tau_h), ith = R(1.0 / P.tau_h), epshat = eps[c] - R(P.eps_ref);
+        const R th = pv<R>(P.tau_h, P.ftau_h), ith = pv<R>(1.0 / P.tau_h, P.fitau_h), epshat = eps[c] - pv<R>(P.eps_ref, P.feps_ref);
         const R den = epshat + (R(1) / R(3)) * th, iden = rcp(den);
         const R g0 = dv(-J[0], den, iden), g1 = dv(-J[1], den, iden), g2 = dv(-J[2], den, iden);
         const R qc = q[c], e3 = ocs2(epshat);
@@ -303,7 +320,7 @@ __global__ void __launch_bounds__(256) k3_poisson(P3 P, const R* __restrict__ hi
                 hout[j * N + t] = v;
             } else {
                 R out = v;
-                if (P.bc == 2) out = -v + R(2) * w3<R>(j) * R(c3z(j) > 0 ? P.V_top : P.V_bottom);
+                if (P.bc == 2) out = -v + R(2) * w3<R>(j) * pv<R>(c3z(j) > 0 ? P.V_top : P.V_bottom, c3z(j) > 0 ? P.fVt : P.fVb);
                 hout[opp3(j) * N + c] = out;
             }
         }
@@ -324,19 +341,19 @@ __global__ void __launch_bounds__(256) k3_fields(P3 P, const R* __restrict__ h, 
     const size_t N = P.N;
     R psi, J[3];
     hmoments3<R>(h, N, c, psi, J);
-    const R den = (eps[c] - R(P.eps_ref)) + (R(1) / R(3)) * R(P.tau_h);
-    E[c] = -(-J[0] / den) + R(P.E0);
+    const R den = (eps[c] - pv<R>(P.eps_ref, P.feps_ref)) + (R(1) / R(3)) * pv<R>(P.tau_h, P.ftau_h);
+    E[c] = -(-J[0] / den) + pv<R>(P.E0, P.fE0);
     E[N + c] = -(-J[1] / den);
-    E[2 * N + c] = -(-J[2] / den) + R(P.E1);
+    E[2 * N + c] = -(-J[2] / den) + pv<R>(P.E1, P.fE1);
     if (psi_out) psi_out[c] = psi;
 }
 template <class R>
 __global__ void k3_fill_E(P3 P, R* __restrict__ E) {
     const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (c >= P.N) return;
-    E[c] = R(P.E0);
+    E[c] = pv<R>(P.E0, P.fE0);
     E[P.N + c] = R(0);
-    E[2 * P.N + c] = R(P.E1);
+    E[2 * P.N + c] = pv<R>(P.E1, P.fE1);
 }
 // potential populations at equilibrium with the linear electrode profile
 template <class R>
@@ -358,14 +375,14 @@ __global__ void __launch_bounds__(256) k3_chem(P3 P, const R* __restrict__ phi, 
     if (!cell3(P, x, y, z, c)) return;
     const size_t N = P.N;
     const R e2 = E[c] * E[c] + E[N + c] * E[N + c] + E[2 * N + c] * E[2 * N + c];
-    const R D = R(P.D);
+    const R D = pv<R>(P.D, P.fD);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const R ph = phi[i * N + c], lam = R(P.lam[i]);
+        const R ph = phi[i * N + c], lam = pv<R>(P.lam[i], P.flam[i]);
         const R lap = lap3<R>(P, phi + i * N, x, y, z, c);
         const R bulk = R(24) / D * lam * ph * (ph - R(0.5)) * (ph - R(1));
         const R grad = R(0.75) * D * lam * lap;
-        const R deps = R(6) * R(P.eps[i]) * ph * (R(1) - ph);
+        const R deps = R(6) * pv<R>(P.eps[i], P.feps[i]) * ph * (R(1) - ph);
         mu[i * N + c] = bulk - grad - R(0.5) * deps * e2;
     }
 }
@@ -554,7 +571,7 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
     };
 
     // S11: phase populations with the mobility of Eq. 28
-    const R tf = R(P.tau_f), itf = R(1.0 / P.tau_f), m0 = R(P.m0), im0 = R(1.0 / P.m0);
+    const R tf = pv<R>(P.tau_f, P.ftau_f), itf = pv<R>(1.0 / P.tau_f, P.fitau_f), m0 = pv<R>(P.m0, P.fm0), im0 = pv<R>(1.0 / P.m0, P.fim0);
     const R pf = R(1) - R(1) / (R(2) * tf);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -585,11 +602,11 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
     }
     // S12: flow populations
     {
-        R tg = R(P.tau_g);
+        R tg = pv<R>(P.tau_g, P.ftau_g);
         if (P.use_visc) {
             R eta = R(0);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) eta += ph[i] * R(P.visc[i]);
+            for (int i = 0; i < 3; ++i) eta += ph[i] * pv<R>(P.visc[i], P.fvisc[i]);
             tg = R(0.5) + dv(eta, rho * c2, irho * R(3));
         }
         const R itg = rcp(tg), pg = R(1) - R(1) / (R(2) * tg);
@@ -604,7 +621,7 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
             const R G = w3<R>(j) * (ugr + ocs2(cF) + ocs2(cu * cgr - c2 * ugr));
             const R v = g[j] - dv(g[j] - geq, tg, itg) + pg * G;
             if ((wall >> j) & 1u) {
-                const R uw = R(c3z(j) > 0 ? P.uwt : P.uwb);
+                const R uw = pv<R>(c3z(j) > 0 ? P.uwt : P.uwb, c3z(j) > 0 ? P.fuwt : P.fuwb);
                 push(0, j, v - ocs2(R(2) * w3<R>(j) * rho * (R(c3x(j)) * uw)));
             } else {
                 push(0, j, v);
@@ -613,7 +630,7 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
     }
     // S13: charge populations
     {
-        const R tl = R(P.tau_l), itl = R(1.0 / P.tau_l), pl = R(1) - R(1) / (R(2) * tl);
+        const R tl = pv<R>(P.tau_l, P.ftau_l), itl = pv<R>(1.0 / P.tau_l, P.fitau_l), pl = R(1) - R(1) / (R(2) * tl);
 #pragma unroll
         for (int j = 0; j < Q3; ++j) {
             const R cu = cdot3<R>(j, u[0], u[1], u[2]);
