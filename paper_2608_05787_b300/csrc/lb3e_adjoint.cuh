@@ -164,10 +164,10 @@ __global__ void k_adj_props(DevParams P, const R* __restrict__ X, const R* __res
         for (int j = 0; j < 9; ++j) a += X[(size_t)(AV_L + j) * N + c];
         qt[c] = a;
     }
-    rho[c] = ph[0] * R(P.rho[0]) + ph[1] * R(P.rho[1]) + ph[2] * R(P.rho[2]);
-    sig[c] = ph[0] * R(P.sigma[0]) + ph[1] * R(P.sigma[1]) + ph[2] * R(P.sigma[2]);
+    rho[c] = ph[0] * pv<R>(P.rho[0], P.frho[0]) + ph[1] * pv<R>(P.rho[1], P.frho[1]) + ph[2] * pv<R>(P.rho[2], P.frho[2]);
+    sig[c] = ph[0] * pv<R>(P.sigma[0], P.fsig[0]) + ph[1] * pv<R>(P.sigma[1], P.fsig[1]) + ph[2] * pv<R>(P.sigma[2], P.fsig[2]);
     R e = R(0);
-    for (int i = 0; i < 3; ++i) e += R(P.eps[i]) * ph[i] * ph[i] * (R(3) - R(2) * ph[i]);
+    for (int i = 0; i < 3; ++i) e += pv<R>(P.eps[i], P.feps[i]) * ph[i] * ph[i] * (R(3) - R(2) * ph[i]);
     eps[c] = e;
 }
 
@@ -220,7 +220,7 @@ __global__ void k_adj_h_linear(DevParams P, R* __restrict__ h) {
     const int N = P.N;
     if (c >= N) return;
     const int y = c / P.nx;
-    const R psi0 = P.bc_y == 2 ? R(P.V_bottom) + (R(P.V_top) - R(P.V_bottom)) * (R(y) + R(0.5)) / R(P.ny) : R(0);
+    const R psi0 = P.bc_y == 2 ? pv<R>(P.V_bottom, P.fVb) + (pv<R>(P.V_top, P.fVt) - pv<R>(P.V_bottom, P.fVb)) * (R(y) + R(0.5)) / R(P.ny) : R(0);
     for (int j = 0; j < 9; ++j) h[(size_t)j * N + c] = j == 0 ? (aw<R>(0) - R(1)) * psi0 : aw<R>(j) * psi0;
 }
 
@@ -244,7 +244,7 @@ __global__ void k_adj_field(DevParams P, const R* __restrict__ h, const R* __res
     }
     Jout[c] = ax;
     Jout[N + c] = ay;
-    const R den = eps[c] - R(P.eps_ref) + acs2<R>() * R(P.tau_h);
+    const R den = eps[c] - pv<R>(P.eps_ref, P.feps_ref) + acs2<R>() * pv<R>(P.tau_h, P.ftau_h);
     const R gx = -ax / den, gy = -ay / den;
     E[c] = -gx + R(P.E_ext[0]);
     E[N + c] = -gy + R(P.E_ext[1]);
@@ -263,12 +263,12 @@ __global__ void k_adj_source_mu(DevParams P, const R* __restrict__ phi, const R*
     const R r = sig[c] / eps[c];
     Rq[c] = -r * q[c] + r * (geps[c] * Ex + geps[N + c] * Ey) - (gsig[c] * Ex + gsig[N + c] * Ey);
     const R e2 = Ex * Ex + Ey * Ey;
-    const R D = R(P.D);
+    const R D = pv<R>(P.D, P.fD);
     for (int i = 0; i < 3; ++i) {
-        const R ph = phi[(size_t)i * N + c], lam = R(P.lam[i]);
+        const R ph = phi[(size_t)i * N + c], lam = pv<R>(P.lam[i], P.flam[i]);
         const R bulk = R(24) / D * lam * ph * (ph - R(0.5)) * (ph - R(1));
         const R grad = R(0.75) * D * lam * lap[(size_t)i * N + c];
-        const R deps = R(6) * R(P.eps[i]) * ph * (R(1) - ph);
+        const R deps = R(6) * pv<R>(P.eps[i], P.feps[i]) * ph * (R(1) - ph);
         mu[(size_t)i * N + c] = bulk - grad - R(0.5) * deps * e2;
     }
 }
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_collide_T(
         if (P.bc_y != 0 && (yt < 0 || yt >= ny)) {
             const R b = ain[(size_t)(base + opp(j)) * N + c];
             if (kind == 1) {
-                const R uw = yt >= ny ? R(P.u_wall_top) : R(P.u_wall_bottom);
+                const R uw = yt >= ny ? pv<R>(P.u_wall_top, P.fuwt) : pv<R>(P.u_wall_bottom, P.fuwb);
                 arho += -R(2) * aw<R>(j) * (R(cx(j)) * uw) * ics * b;
             }
             return b;
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_collide_T(
         auy += qc * by;
     }
     // phase populations, Eq. 34-36, with the mobility of Eq. 28
-    const R tf = R(P.tau_f), m0 = R(P.m0), itf = R(1) / tf, im0 = R(1) / m0;
+    const R m0 = pv<R>(P.m0, P.fm0), itf = pv<R>(1.0 / P.tau_f, P.fitau_f), im0 = pv<R>(1.0 / P.m0, P.fim0);
     R aprev[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
     for (int i = 0; i < 3; ++i) {
         R aAx = R(0), aAy = R(0);
@@ -425,9 +425,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_collide_T(
     // flow populations, Eq. 37-40
     const R rh = rho[c], p = pr[c];
     const R Fx = F[c], Fy = F[N + c], grx = grho[c], gry = grho[N + c];
-    R tg = R(P.tau_g), eta = R(0);
+    R tg = pv<R>(P.tau_g, P.ftau_g), eta = R(0);
     if (P.use_visc) {
-        for (int i = 0; i < 3; ++i) eta += ph[i] * R(P.visc[i]);
+        for (int i = 0; i < 3; ++i) eta += ph[i] * pv<R>(P.visc[i], P.fvisc[i]);
         tg = R(0.5) + eta / (rh * cs);
     }
     const R itg = R(1) / tg, irh = R(1) / rh;
@@ -462,13 +462,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_collide_T(
         if (P.use_visc) {
             const R aeta = atg * irh * ics;
             arho += -atg * eta * irh * irh * ics;
-            for (int i = 0; i < 3; ++i) aph[i] += R(P.visc[i]) * aeta;
+            for (int i = 0; i < 3; ++i) aph[i] += pv<R>(P.visc[i], P.fvisc[i]) * aeta;
         }
     }
     // charge populations, Eq. 48-50
     R aR = R(0);
     {
-        const R itl = R(1) / R(P.tau_l), pl = R(1) - R(0.5) * itl;
+        const R itl = pv<R>(1.0 / P.tau_l, P.fitau_l), pl = R(1) - R(0.5) * itl;
         R adqx = R(0), adqy = R(0);
         for (int j = 0; j < 9; ++j) {
             const R lb = post(AV_L, j, 0);
@@ -563,13 +563,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_mu_T(
     if (c < N) {
         const int x = c % nx, y = c / nx;
         const R Ex = E[c], Ey = E[N + c];
-        const R e2 = Ex * Ex + Ey * Ey, D = R(P.D);
+        const R e2 = Ex * Ex + Ey * Ey, D = pv<R>(P.D, P.fD);
         R aEx = R(0), aEy = R(0);
         for (int i = 0; i < 3; ++i) {
             const R mb = (a_mu_in ? a_mu_in[(size_t)i * N + c] : R(0)) +
                          (a_gmu ? grad_T_at<R>(P, a_gmu + (size_t)(2 * i) * N, a_gmu + (size_t)(2 * i + 1) * N, x, y)
                                 : R(0));
-            const R ph = phi[(size_t)i * N + c], lam = R(P.lam[i]), ei = R(P.eps[i]);
+            const R ph = phi[(size_t)i * N + c], lam = pv<R>(P.lam[i], P.flam[i]), ei = pv<R>(P.eps[i], P.feps[i]);
             const R deps = R(6) * ei * ph * (R(1) - ph);
             a_phi[(size_t)i * N + c] += mb * (R(24) / D * lam * (R(3) * ph * ph - R(3) * ph + R(0.5)) -
                                               R(3) * ei * (R(1) - R(2) * ph) * e2);
@@ -596,7 +596,7 @@ __global__ void k_adj_field_T(DevParams P, const R* __restrict__ J, const R* __r
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = P.N;
     if (c >= N) return;
-    const R iden = R(1) / (eps[c] - R(P.eps_ref) + acs2<R>() * R(P.tau_h));
+    const R iden = R(1) / (eps[c] - pv<R>(P.eps_ref, P.feps_ref) + acs2<R>() * pv<R>(P.tau_h, P.ftau_h));
     const R ax = J[c], ay = J[N + c];
     const R bx = a_E[c] * iden, by = a_E[N + c] * iden;
     for (int j = 0; j < 9; ++j) ah[(size_t)j * N + c] = ah_in[(size_t)j * N + c] + (R(cx(j)) * bx + R(cy(j)) * by);
@@ -677,14 +677,15 @@ __device__ void params_reduce_block(const double* __restrict__ pmu, const double
 // adjoint gathered from ain.  The h adjoint of the state is copied out here.  With
 // dphi (the creation), phibar goes there in FP64 instead.  Block partials: eps_1..3,
 // sigma_1..3; the last block to finish sums every partial of the step into dpar
-// (the mu-part, these, the electrode columns or partials) and re-arms the counter.
+// (the mu-part, these, the electrode columns or vpart's partials) and re-arms the
+// counter.
 template <class R>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_props_T(
     DevParams P, const R* __restrict__ phi, const R* __restrict__ a_lap, const R* __restrict__ a_geps,
     const R* __restrict__ a_gsig, const R* __restrict__ a_rho, const R* __restrict__ a_sig,
     const R* __restrict__ a_eps, const R* __restrict__ a_phi, const R* __restrict__ ah, const R* __restrict__ ain,
     R* __restrict__ aout, double* __restrict__ dphi, double* partial, const double* __restrict__ pmu,
-    const R* __restrict__ vbar, const double* __restrict__ pv, unsigned* __restrict__ count,
+    const R* __restrict__ vbar, const double* __restrict__ vpart, unsigned* __restrict__ count,
     double* __restrict__ dpar) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = P.N, nx = P.nx;
@@ -694,11 +695,11 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_props_T(
         const R ae = a_eps[c] + (a_geps ? grad_T_at<R>(P, a_geps, a_geps + N, x, y) : R(0));
         const R as = (a_sig ? a_sig[c] : R(0)) + (a_gsig ? grad_T_at<R>(P, a_gsig, a_gsig + N, x, y) : R(0));
         const R ar = a_rho ? a_rho[c] : R(0);
-        const R dk = R(1) - R(1) / R(P.tau_f);
+        const R dk = R(1) - R(1) / pv<R>(P.tau_f, P.ftau_f);
         for (int i = 0; i < 3; ++i) {
             const R ph = phi[(size_t)i * N + c];
             const R tot = a_phi[(size_t)i * N + c] + lap_T_at<R>(P, a_lap + (size_t)i * N, x, y) +
-                          R(P.rho[i]) * ar + R(P.sigma[i]) * as + R(P.eps[i]) * R(6) * ph * (R(1) - ph) * ae;
+                          pv<R>(P.rho[i], P.frho[i]) * ar + pv<R>(P.sigma[i], P.fsig[i]) * as + pv<R>(P.eps[i], P.feps[i]) * R(6) * ph * (R(1) - ph) * ae;
             v[i] = (double)(ph * ph * (R(3) - R(2) * ph) * ae);
             v[3 + i] = (double)(ph * as);
             if (dphi) {
@@ -720,7 +721,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_props_T(
     __syncthreads();
     if (is_last) {
         __threadfence();
-        params_reduce_block<R>(pmu, partial, (int)gridDim.x, vbar, nx, pv, pv ? (int)gridDim.x : 0, dpar);
+        params_reduce_block<R>(pmu, partial, (int)gridDim.x, vbar, nx, vpart, vpart ? (int)gridDim.x : 0, dpar);
         if (threadIdx.x == 0) *count = 0u;
     }
 }
@@ -824,10 +825,10 @@ __global__ void __launch_bounds__(PT_NT) k_adj_pot_tape(DevParams P, const R* __
     R* post = cur + 9 * PT_NT;
     const TileCell tc = tile_cell(P);
     const int N = P.N, ny = P.ny;
-    const R th = R(P.tau_h), ith = R(1) / th;
+    const R th = pv<R>(P.tau_h, P.ftau_h), ith = R(1) / th;
     R epshat = R(0), qc = R(0), den = R(1), iden = R(1);
     if (tc.present) {
-        epshat = eps[tc.c] - R(P.eps_ref);
+        epshat = eps[tc.c] - pv<R>(P.eps_ref, P.feps_ref);
         qc = q[tc.c];
         den = epshat + acs2<R>() * th;
         iden = R(1) / den;
@@ -875,7 +876,7 @@ __global__ void __launch_bounds__(PT_NT) k_adj_pot_tape(DevParams P, const R* __
                 R v;
                 if (P.bc_y != 0 && (ys < 0 || ys >= ny)) {
                     const R o = post[opp(j) * PT_NT + tc.t];
-                    const R vw = ys >= ny ? R(P.V_top) : R(P.V_bottom);
+                    const R vw = ys >= ny ? pv<R>(P.V_top, P.fVt) : pv<R>(P.V_bottom, P.fVb);
                     v = P.bc_y == 2 ? -o + R(2) * aw<R>(j) * vw : o;
                 } else {
                     v = post[j * PT_NT + tile_nb(-cx(j), -cy(j))];
@@ -901,11 +902,11 @@ __global__ void __launch_bounds__(PT_NT) k_adj_pot_T(DevParams P, const R* __res
     R* buf[2] = {reinterpret_cast<R*>(pt_raw), reinterpret_cast<R*>(pt_raw) + 9 * PT_NT};
     const TileCell tc = tile_cell(P);
     const int N = P.N, ny = P.ny;
-    const R ith = R(1) / R(P.tau_h), ics = R(3);
+    const R ith = pv<R>(1.0 / P.tau_h, P.fitau_h), ics = R(3);
     R epshat = R(0), iden = R(1);
     if (tc.present) {
-        epshat = eps[tc.c] - R(P.eps_ref);
-        iden = R(1) / (epshat + acs2<R>() * R(P.tau_h));
+        epshat = eps[tc.c] - pv<R>(P.eps_ref, P.feps_ref);
+        iden = R(1) / (epshat + acs2<R>() * pv<R>(P.tau_h, P.ftau_h));
 #pragma unroll
         for (int j = 0; j < 9; ++j) buf[0][j * PT_NT + tc.t] = ah_in[(size_t)j * N + tc.c];
     }
