@@ -37,7 +37,7 @@ struct DevParams {
     // single-precision copies used by the FP32 kernels (FP64 arithmetic, including
     // conversions, is slow on this part)
     float frho[3], fvisc[3], feps[3], fsig[3], flam[3];
-    float fD, ftau_f, fm0, ftau_g, ftau_l, ftau_h, feps_ref, fVb, fVt, fuwb, fuwt;
+    float fD, ftau_f, fm0, ftau_g, ftau_l, ftau_h, feps_ref, fVb, fVt, fuwb, fuwt, fE[2];
     // launch-wide constants of the FP32 collisions, formed once on the host:
     // 1/tau, the source prefactor 1 - 1/(2 tau), 1/m0 and 24/D
     float fitau_f, fpf, fim0, fitau_g, fpg, fitau_l, fpl, fitau_h, fc24;
@@ -1327,10 +1327,10 @@ __device__ __forceinline__ void body_potential_fields(const DevParams P, const R
 #pragma unroll
     for (int j = 0; j < 9; ++j) { jx += R(cx(j)) * h[j * N + c]; jy += R(cy(j)) * h[j * N + c]; }
     if (psi_out) { psi_out[c] = (double)(ps / (R(1) - wgt<R>(0))); return; }
-    const R den = (eps[c] - R(P.eps_ref)) + cs2<R>() * R(P.tau_h);
+    const R den = (eps[c] - pv<R>(P.eps_ref, P.feps_ref)) + cs2<R>() * pv<R>(P.tau_h, P.ftau_h);
     const R gx = -jx / den, gy = -jy / den;
-    E[c] = -gx + R(P.E_ext[0]);
-    E[N + c] = -gy + R(P.E_ext[1]);
+    E[c] = -gx + pv<R>(P.E_ext[0], P.fE[0]);
+    E[N + c] = -gy + pv<R>(P.E_ext[1], P.fE[1]);
 }
 template <class R>
 __global__ void __launch_bounds__(256) k_potential_fields(DevParams P, const R* __restrict__ h,

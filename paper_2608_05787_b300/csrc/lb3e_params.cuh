@@ -60,6 +60,8 @@ inline DevParams make_dev_params(const lb3e_params& p) {
     d.fVt = (float)d.V_top;
     d.fuwb = (float)d.u_wall_bottom;
     d.fuwt = (float)d.u_wall_top;
+    d.fE[0] = (float)d.E_ext[0];
+    d.fE[1] = (float)d.E_ext[1];
     d.fitau_f = (float)(1.0 / d.tau_f);
     d.fpf = (float)(1.0 - 1.0 / (2.0 * d.tau_f));
     d.fim0 = (float)(1.0 / d.m0);
