@@ -27,6 +27,8 @@ struct IonParams {
     double mig[2];   // z_i beta D_i
     double z[2];
     double e;        // charge per unit concentration
+    // their FP32 roundings (an FP64 conversion in device code costs FP64 instructions)
+    float ftau[2], fitau[2], fpre[2], fmig[2], fz[2], fe;
 };
 
 inline IonParams make_ion_params(const lb3e_params& p) {
@@ -40,6 +42,14 @@ inline IonParams make_ion_params(const lb3e_params& p) {
         ip.z[i] = p.ion_z[i];
     }
     ip.e = p.ion_charge;
+    for (int i = 0; i < 2; ++i) {
+        ip.ftau[i] = (float)ip.tau[i];
+        ip.fitau[i] = (float)ip.itau[i];
+        ip.fpre[i] = (float)ip.pre[i];
+        ip.fmig[i] = (float)ip.mig[i];
+        ip.fz[i] = (float)ip.z[i];
+    }
+    ip.fe = (float)ip.e;
     return ip;
 }
 
@@ -47,9 +57,9 @@ inline IonParams make_ion_params(const lb3e_params& p) {
 template <class R>
 __device__ __forceinline__ R ion_charge_of(const IonParams& ip, R n0, R n1) {
     R a = R(0);
-    a += R(ip.z[0]) * n0;
-    a += R(ip.z[1]) * n1;
-    return R(ip.e) * a;
+    a += pv<R>(ip.z[0], ip.fz[0]) * n0;
+    a += pv<R>(ip.z[1], ip.fz[1]) * n1;
+    return pv<R>(ip.e, ip.fe) * a;
 }
 
 // Moments n_i = sum_j n^i_j of the current ion populations and the charge they carry.
@@ -83,7 +93,7 @@ __global__ void k_ion_charge(size_t N, const R* __restrict__ nion, R* __restrict
 template <class R>
 __device__ __forceinline__ void ion_velocity(const IonParams& ip, int i, size_t N, size_t c, const R* __restrict__ u,
                                              const R* __restrict__ E, R& vx, R& vy) {
-    const R m = R(ip.mig[i]);
+    const R m = pv<R>(ip.mig[i], ip.fmig[i]);
     vx = u[c] + m * E[c];
     vy = u[N + c] + m * E[N + c];
 }
@@ -122,7 +132,8 @@ __global__ void __launch_bounds__(256) k_ions(int nx, int ny, int bc_y, const R*
         const R nvx = n * vx, nvy = n * vy;
         const R dx = first ? R(0) : nvx - prev[(2 * i) * N + c];
         const R dy = first ? R(0) : nvy - prev[(2 * i + 1) * N + c];
-        const R tau = R(ip.tau[i]), itau = R(ip.itau[i]), pre = R(ip.pre[i]);
+        const R tau = pv<R>(ip.tau[i], ip.ftau[i]), itau = pv<R>(ip.itau[i], ip.fitau[i]),
+                pre = pv<R>(ip.pre[i], ip.fpre[i]);
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
             const R neq = wgt<R>(j) * n * (R(1) + oc2(cdot<R>(j, vx, vy)));
