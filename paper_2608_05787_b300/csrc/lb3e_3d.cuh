@@ -280,48 +280,69 @@ __global__ void __launch_bounds__(256, std::is_same<R, float>::value ? 4 : 1)
     k3_poisson(P3 P, const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ eps,
                const R* __restrict__ q, R* __restrict__ prev, double* __restrict__ partial, int save, int check) {
     int x, y, z;
-    size_t c;
-    const bool in = cell3(P, x, y, z, c);
-    const size_t N = P.N;
+    size_t cz;
+    const bool in = cell3(P, x, y, z, cz);
+    // 32-bit indices (at most LB3E_MAX_CELLS cells, so 15 N fits): the populations
+    // loaded once, the neighbours' columns, rows and planes formed once a cell
+    const unsigned N = (unsigned)P.N, c = (unsigned)cz;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     if (in) {
-        R psi, J[3];
-        hmoments3<R>(hin, N, c, psi, J);
+        R hv[Q3];
+#pragma unroll
+        for (int j = 0; j < Q3; ++j) hv[j] = hin[j * N + c];
+        R a = R(0);
+#pragma unroll
+        for (int j = 1; j < Q3; ++j) a += hv[j];
+        const R psi = a / (R(1) - w3<R>(0));
+        R J[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int j = 0; j < Q3; ++j) {
+            cacc(J[0], c3x(j), hv[j]);
+            cacc(J[1], c3y(j), hv[j]);
+            cacc(J[2], c3z(j), hv[j]);
+        }
         if (check) {
             const double d = (double)psi - (double)prev[c];
             acc[0] = d * d;
             acc[1] = (double)psi * (double)psi;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const double e = (double)J[a] - (double)prev[(1 + a) * N + c];
+            for (int k = 0; k < 3; ++k) {
+                const double e = (double)J[k] - (double)prev[(1 + k) * N + c];
                 acc[2] += e * e;
-                acc[3] += (double)J[a] * (double)J[a];
+                acc[3] += (double)J[k] * (double)J[k];
             }
         }
         if (save) {
             prev[c] = psi;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) prev[(1 + a) * N + c] = J[a];
+            for (int k = 0; k < 3; ++k) prev[(1 + k) * N + c] = J[k];
         }
         // divisions: exact in the FP64 build, by a reciprocal formed once in FP32
-        const R th = pv<R>(P.tau_h, P.ftau_h), ith = pv<R>(1.0 / P.tau_h, P.fitau_h), epshat = eps[c] - pv<R>(P.eps_ref, P.feps_ref);
+        const R th = pv<R>(P.tau_h, P.ftau_h), ith = pv<R>(1.0 / P.tau_h, P.fitau_h),
+                epshat = eps[c] - pv<R>(P.eps_ref, P.feps_ref);
         const R den = epshat + (R(1) / R(3)) * th, iden = rcp(den);
         const R g0 = dv(-J[0], den, iden), g1 = dv(-J[1], den, iden), g2 = dv(-J[2], den, iden);
         const R qc = q[c], e3 = ocs2(epshat);
+        const unsigned nx = (unsigned)P.nx, ny = (unsigned)P.ny, nz = (unsigned)P.nz, nxy = nx * ny;
+        const unsigned col[3] = {x == 0 ? nx - 1 : (unsigned)x - 1, (unsigned)x, x == P.nx - 1 ? 0u : (unsigned)x + 1};
+        const unsigned row[3] = {(y == 0 ? ny - 1 : (unsigned)y - 1) * nx, (unsigned)y * nx,
+                                 (y == P.ny - 1 ? 0u : (unsigned)y + 1) * nx};
+        const unsigned pln[3] = {(z == 0 ? nz - 1 : (unsigned)z - 1) * nxy, (unsigned)z * nxy,
+                                 (z == P.nz - 1 ? 0u : (unsigned)z + 1) * nxy};
+        const bool wall_lo = P.bc != 0 && z == 0, wall_hi = P.bc != 0 && z == P.nz - 1;
 #pragma unroll
         for (int j = 0; j < Q3; ++j) {
             const R heq = j == 0 ? (w3<R>(0) - R(1)) * psi : w3<R>(j) * psi;     // Eq. 44
             const R varpi = j == 0 ? R(0) : R(1.0 / 14.0);
-            const R hj = hin[j * N + c];
+            const R hj = hv[j];
             const R cg = cdot3<R>(j, g0, g1, g2);
             const R v = hj - dv(hj - heq, th, ith) - dv(e3 * w3<R>(j) * cg, th, ith) + varpi * qc;
-            size_t t;
-            if (target3(P, x, y, z, j, t)) {
-                hout[j * N + t] = v;
-            } else {
+            if ((c3z(j) < 0 && wall_lo) || (c3z(j) > 0 && wall_hi)) {  // across a z wall: back to this cell
                 R out = v;
                 if (P.bc == 2) out = -v + R(2) * w3<R>(j) * pv<R>(c3z(j) > 0 ? P.V_top : P.V_bottom, c3z(j) > 0 ? P.fVt : P.fVb);
                 hout[opp3(j) * N + c] = out;
+            } else {
+                hout[j * N + pln[c3z(j) + 1] + row[c3y(j) + 1] + col[c3x(j) + 1]] = v;
             }
         }
     }
