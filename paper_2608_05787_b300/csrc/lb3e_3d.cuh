@@ -571,24 +571,36 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
     for (int a = 0; a < 3; ++a) dqu[a] = first ? R(0) : qc * u[a] - sp[(5 * Q3 + 9 + a) * K3T + tid];
 
     // streaming targets, the same for the five sets: the neighbour's index within a
-    // plane, or this cell (bit j of wall set) when link j leaves through a z wall
+    // plane (from its column, row and plane formed once, 32-bit: at most
+    // LB3E_MAX_CELLS cells, so 75 N fits), or this cell (bit j of wall set) when link j
+    // leaves through a z wall
     unsigned tgt[Q3];
     unsigned wall = 0u;
+    {
+        const unsigned nx = (unsigned)P.nx, ny = (unsigned)P.ny, nz = (unsigned)P.nz, nxy = nx * ny;
+        const unsigned col[3] = {x == 0 ? nx - 1 : (unsigned)x - 1, (unsigned)x,
+                                 x == P.nx - 1 ? 0u : (unsigned)x + 1};
+        const unsigned row[3] = {(y == 0 ? ny - 1 : (unsigned)y - 1) * nx, (unsigned)y * nx,
+                                 (y == P.ny - 1 ? 0u : (unsigned)y + 1) * nx};
+        const unsigned pln[3] = {(z == 0 ? nz - 1 : (unsigned)z - 1) * nxy, (unsigned)z * nxy,
+                                 (z == P.nz - 1 ? 0u : (unsigned)z + 1) * nxy};
+        const bool wall_lo = P.bc != 0 && z == 0, wall_hi = P.bc != 0 && z == P.nz - 1;
 #pragma unroll
-    for (int j = 0; j < Q3; ++j) {
-        size_t t;
-        if (target3(P, x, y, z, j, t)) {
-            tgt[j] = (unsigned)t;
-        } else {
-            tgt[j] = (unsigned)c;
-            wall |= 1u << j;
+        for (int j = 0; j < Q3; ++j) {
+            if ((c3z(j) < 0 && wall_lo) || (c3z(j) > 0 && wall_hi)) {
+                tgt[j] = (unsigned)c;
+                wall |= 1u << j;
+            } else {
+                tgt[j] = pln[c3z(j) + 1] + row[c3y(j) + 1] + col[c3x(j) + 1];
+            }
         }
     }
     // post-collision value v of population j of `set`: to the neighbour, or back to
     // this cell in the opposite direction at a wall
+    const unsigned N32 = (unsigned)N;
     auto push = [&](int set, int j, R v) {
         const int jj = ((wall >> j) & 1u) ? opp3(j) : j;
-        pout[(size_t)(Q3 * set + jj) * N + tgt[j]] = v;
+        pout[(unsigned)(Q3 * set + jj) * N32 + tgt[j]] = v;
     };
 
     // S11: phase populations with the mobility of Eq. 28
