@@ -109,67 +109,48 @@ __device__ __forceinline__ bool cell3(const P3& P, int& x, int& y, int& z, size_
     c = ((size_t)z * P.ny + y) * P.nx + x;
     return x < P.nx && y < P.ny;
 }
-// neighbour cell for the stencils: periodic x, y; z periodic or mirrored at the walls
-__device__ __forceinline__ size_t nb3(const P3& P, int x, int y, int z, int j) {
-    int zz = z + c3z(j);
-    if (P.bc == 0) zz = zz < 0 ? zz + P.nz : (zz >= P.nz ? zz - P.nz : zz);
-    else zz = zz < 0 ? -zz - 1 : (zz >= P.nz ? 2 * P.nz - zz - 1 : zz);
-    const int yy = wrapi(y + c3y(j), P.ny), xx = wrapi(x + c3x(j), P.nx);
-    return ((size_t)zz * P.ny + yy) * P.nx + xx;
+// The stencil neighbours of a cell in 32-bit indices (at most LB3E_MAX_CELLS cells):
+// the columns, rows and planes of the offsets -1, 0, +1 formed once a cell; x and y
+// periodic, z periodic or mirrored at the walls (the stencil ghosts)
+struct Nb3 {
+    unsigned col[3], row[3], pln[3];
+    __device__ __forceinline__ unsigned at(int j) const { return pln[c3z(j) + 1] + row[c3y(j) + 1] + col[c3x(j) + 1]; }
+};
+__device__ __forceinline__ Nb3 stencil3(const P3& P, int x, int y, int z) {
+    Nb3 s;
+    const unsigned nx = (unsigned)P.nx, ny = (unsigned)P.ny, nz = (unsigned)P.nz, nxy = nx * ny;
+    const unsigned ux = (unsigned)x, uy = (unsigned)y, uz = (unsigned)z;
+    s.col[0] = x == 0 ? nx - 1 : ux - 1;
+    s.col[1] = ux;
+    s.col[2] = ux + 1 == nx ? 0u : ux + 1;
+    s.row[0] = (y == 0 ? ny - 1 : uy - 1) * nx;
+    s.row[1] = uy * nx;
+    s.row[2] = (uy + 1 == ny ? 0u : uy + 1) * nx;
+    s.pln[0] = (z == 0 ? (P.bc ? 0u : nz - 1) : uz - 1) * nxy;
+    s.pln[1] = uz * nxy;
+    s.pln[2] = (uz + 1 == nz ? (P.bc ? nz - 1 : 0u) : uz + 1) * nxy;
+    return s;
 }
 // Eq. 33 gradient of a field at a cell
 template <class R>
-__device__ __forceinline__ void grad3(const P3& P, const R* __restrict__ f, int x, int y, int z, R g[3]) {
+__device__ __forceinline__ void grad3(const Nb3& nb, const R* __restrict__ f, R g[3]) {
     R a0 = R(0), a1 = R(0), a2 = R(0);
 #pragma unroll
     for (int j = 0; j < Q3; ++j) {
-        const R v = w3<R>(j) * f[nb3(P, x, y, z, j)];
+        const R v = w3<R>(j) * f[nb.at(j)];
         cacc(a0, c3x(j), v);
         cacc(a1, c3y(j), v);
         cacc(a2, c3z(j), v);
     }
     g[0] = ocs2(a0); g[1] = ocs2(a1); g[2] = ocs2(a2);
 }
-// Eq. 33 gradients of M fields (planes of one array set) at a cell, one pass over
-// the neighbours: the same sums, in the same order, as M calls of grad3
-template <class R, int M>
-__device__ __forceinline__ void grad3_multi(const P3& P, const R* const (&f)[M], int x, int y, int z, R g[M][3]) {
-    R a[M][3];
-#pragma unroll
-    for (int m = 0; m < M; ++m) a[m][0] = a[m][1] = a[m][2] = R(0);
-#pragma unroll
-    for (int j = 0; j < Q3; ++j) {
-        const size_t n = nb3(P, x, y, z, j);
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const R v = w3<R>(j) * f[m][n];
-            cacc(a[m][0], c3x(j), v);
-            cacc(a[m][1], c3y(j), v);
-            cacc(a[m][2], c3z(j), v);
-        }
-    }
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-        g[m][0] = ocs2(a[m][0]);
-        g[m][1] = ocs2(a[m][1]);
-        g[m][2] = ocs2(a[m][2]);
-    }
-}
 template <class R>
-__device__ __forceinline__ R lap3(const P3& P, const R* __restrict__ f, int x, int y, int z, size_t c) {
+__device__ __forceinline__ R lap3(const Nb3& nb, const R* __restrict__ f, unsigned c) {
     const R c0 = f[c];
     R a = R(0);
 #pragma unroll
-    for (int j = 0; j < Q3; ++j) a += R(2) * w3<R>(j) * (f[nb3(P, x, y, z, j)] - c0);
+    for (int j = 0; j < Q3; ++j) a += R(2) * w3<R>(j) * (f[nb.at(j)] - c0);
     return ocs2(a);
-}
-// streaming target: false when the link leaves through a wall (bounce-back)
-__device__ __forceinline__ bool target3(const P3& P, int x, int y, int z, int j, size_t& t) {
-    int zt = z + c3z(j);
-    if (P.bc != 0 && (zt < 0 || zt >= P.nz)) return false;
-    zt = zt < 0 ? zt + P.nz : (zt >= P.nz ? zt - P.nz : zt);
-    t = ((size_t)zt * P.ny + wrapi(y + c3y(j), P.ny)) * P.nx + wrapi(x + c3x(j), P.nx);
-    return true;
 }
 
 template <class R>
@@ -236,12 +217,13 @@ __global__ void __launch_bounds__(256) k3_closure(P3 P, const R* __restrict__ qt
                                                   const R* __restrict__ eps, const R* __restrict__ E,
                                                   R* __restrict__ q) {
     int x, y, z;
-    size_t c;
-    if (!cell3(P, x, y, z, c)) return;
-    const size_t N = P.N;
+    size_t cz;
+    if (!cell3(P, x, y, z, cz)) return;
+    const unsigned N = (unsigned)P.N, c = (unsigned)cz;
+    const Nb3 nb = stencil3(P, x, y, z);
     R ge3[3], gs3[3];
-    grad3<R>(P, eps, x, y, z, ge3);
-    grad3<R>(P, sig, x, y, z, gs3);
+    grad3<R>(nb, eps, ge3);
+    grad3<R>(nb, sig, gs3);
     const R r = sig[c] / eps[c];
     R ge = R(0), gs = R(0);
 #pragma unroll
@@ -392,15 +374,16 @@ template <class R>
 __global__ void __launch_bounds__(256) k3_chem(P3 P, const R* __restrict__ phi, const R* __restrict__ E,
                                                R* __restrict__ mu) {
     int x, y, z;
-    size_t c;
-    if (!cell3(P, x, y, z, c)) return;
-    const size_t N = P.N;
+    size_t cz;
+    if (!cell3(P, x, y, z, cz)) return;
+    const unsigned N = (unsigned)P.N, c = (unsigned)cz;
+    const Nb3 nb = stencil3(P, x, y, z);
     const R e2 = E[c] * E[c] + E[N + c] * E[N + c] + E[2 * N + c] * E[2 * N + c];
     const R D = pv<R>(P.D, P.fD);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const R ph = phi[i * N + c], lam = pv<R>(P.lam[i], P.flam[i]);
-        const R lap = lap3<R>(P, phi + i * N, x, y, z, c);
+        const R lap = lap3<R>(nb, phi + i * N, c);
         const R bulk = R(24) / D * lam * ph * (ph - R(0.5)) * (ph - R(1));
         const R grad = R(0.75) * D * lam * lap;
         const R deps = R(6) * pv<R>(P.eps[i], P.feps[i]) * ph * (R(1) - ph);
@@ -417,7 +400,7 @@ __global__ void __launch_bounds__(256) k3_chem(P3 P, const R* __restrict__ phi, 
 // with a one-cell halo, on the planes z - 1, z, z + 1 (periodic or mirrored at the
 // walls, as the stencil ghosts), are staged in shared memory first: each thread
 // then forms the six gradients from shared memory, in the neighbour order of
-// grad3_multi (the same sums), instead of 90 global loads with their index
+// grad3 (the same sums), instead of 90 global loads with their index
 // arithmetic.  Blocks of consecutive planes run close together in time, so the
 // neighbour planes come from L2.
 constexpr int K3X = 34, K3Y = 10, K3P = K3X * K3Y, K3F = 3 * K3P;  // staged tile: 3 planes of 34 x 10
