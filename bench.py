@@ -156,18 +156,38 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(key: str):
-    """DRAM bytes per cell and launch from the committed ncu summary
-    (profiles/traffic.json, keyed "<kernel>:<precision>[:<iterations per launch>]"),
-    if it was taken on the current kernel sources (else None)."""
+def profiled_record(key: str):
+    """The committed ncu record of a kernel (profiles/traffic.json, keyed
+    "<kernel>:<precision>[:<iterations per launch>]"), if it was taken on the current
+    kernel sources (else None)."""
     f = ROOT / "profiles" / "traffic.json"
     if not f.exists():
         return None
-    d = json.loads(f.read_text())
-    e = d.get(key)
+    e = json.loads(f.read_text()).get(key)
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return float(e["bytes_per_cell"])
+    return e
+
+
+def profiled_traffic(key: str):
+    """DRAM bytes per cell and launch from the committed ncu record, or None."""
+    e = profiled_record(key)
+    return float(e["bytes_per_cell"]) if e else None
+
+
+def issue_bound(key: str, cells: int, ms_per_launch: float, sm_mhz):
+    """The on-chip figure of merit of an issue-bound kernel: its warp instructions per
+    launch (the ncu record's per-cell count x cells) over the launch time, against
+    the schedulers' ceiling of one warp instruction a cycle on each of the 148 SMs'
+    four sub-partitions at the sampled SM clock."""
+    e = profiled_record(key)
+    if not e or "warp_instructions_per_cell" not in e or not sm_mhz:
+        return None
+    inst = float(e["warp_instructions_per_cell"]) * cells
+    peak = 148 * 4 * float(sm_mhz) * 1e6
+    rate = inst / (ms_per_launch / 1e3)
+    return {"warp_instructions_per_launch": inst, "achieved_warp_inst_per_s": rate,
+            "peak_warp_inst_per_s": peak, "frac": rate / peak, "sm_mhz": sm_mhz}
 
 
 class Clocks:
@@ -513,6 +533,8 @@ def run_lb3e(args):
 
     if rank == 0:
         dtype = DTYPE_NAMES[prec]
+        clocks = clk.summary()
+        roofline["issue"] = None if kname.startswith("multigrid") else issue_bound(key, N, dms, clocks.get("sm_mhz"))
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -535,7 +557,7 @@ def run_lb3e(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "observables": {k: obs[k] for k in ("D_inner", "D_outer", "max_sum_dev", "poisson_residual",
                                                  "poisson_iters", "nonfinite")},
             "potential_timed_steps": dict(pstats, fd_residual_after=fd_res),
