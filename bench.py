@@ -852,7 +852,9 @@ def run_deformation3d(args):
     units = {"fused": args.steps, "poisson": args.steps * iters, "moments": args.steps}
     gbs = {k: WORDS_3D[k] * word * N * units[k] / (kt[k][0] / 1e3) / 1e9 for k in WORDS_3D if kt[k][1]}
     dominant = max(WORDS_3D, key=lambda k: kt[k][0])
-    kname = {"fused": "k3_collide", "poisson": "k3_poisson", "moments": "k3_moments"}[dominant]
+    # FP32 with nx a multiple of 4: the potential iteration's inputs staged by TMA
+    pot3 = "k3_poisson_tma" if prec == 1 and n % 4 == 0 else "k3_poisson"
+    kname = {"fused": "k3_collide", "poisson": pot3, "moments": "k3_moments"}[dominant]
     roofline = {"bound": "hbm", "achieved": gbs.get(dominant), "peak": hbm, "unit": "GB/s",
                 "frac": gbs.get(dominant, 0) / hbm, "traffic": None, "kernel": kname,
                 "peak_kind": f"{peak_kind} copy bandwidth",

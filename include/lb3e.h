@@ -377,6 +377,16 @@ int lb3e_set_potential_chunk(lb3e_handle* h, int32_t iterations_per_launch);
  * three-dimensional lattice). */
 int lb3e_set_fused_tile(lb3e_handle* h, int32_t rows);
 
+/* Input staging of the three-dimensional (D3Q15) potential iteration (Eq. 43):
+ * planes >= 1 (2 by default) copies each plane's 15 population boxes, eps and q into
+ * shared memory with the tensor memory accelerator, each block walking `planes`
+ * consecutive z planes of its 32 x 8 tile, where the lattice allows it (FP32, nx a
+ * multiple of 4) and the iteration neither checks nor saves its increment; 0 loads
+ * every input per thread.  The per-cell arithmetic is the same; the states agree
+ * bitwise.  Errors: NULL, PARAM (planes outside 0..1024), UNSUPPORTED (a
+ * two-dimensional lattice). */
+int lb3e_set_staging(lb3e_handle* h, int32_t planes);
+
 /* Kernel timing with CUDA events recorded on the simulation's stream around each
  * launch (off by default; costs two event records per launch).  Enabling or
  * disabling clears the totals. */

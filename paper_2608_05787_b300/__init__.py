@@ -133,6 +133,7 @@ def lib() -> C.CDLL:
         L.lb3e_set_timing.argtypes = [vp, C.c_int32]
         L.lb3e_set_potential_chunk.argtypes = [vp, C.c_int32]
         L.lb3e_set_fused_tile.argtypes = [vp, C.c_int32]
+        L.lb3e_set_staging.argtypes = [vp, C.c_int32]
         L.lb3e_set_ions.argtypes = [vp, vp]
         L.lb3e_potential_fd_residual.argtypes = [vp, dp]
         L.lb3e_deformation.argtypes = [vp, dp, dp]
@@ -456,6 +457,12 @@ class Sim:
     def set_tile(self, rows: int) -> "Sim":
         """Rows of the fused pass's 32 x rows tiles (4, 8, 16; speed only)."""
         _check("lb3e_set_fused_tile", lib().lb3e_set_fused_tile(self._h, int(rows)))
+        return self
+
+    def set_staging(self, planes: int) -> "Sim":
+        """TMA staging of the D3Q15 potential iteration's inputs: z planes a block
+        walks (0: per-thread loads; speed only)."""
+        _check("lb3e_set_staging", lib().lb3e_set_staging(self._h, int(planes)))
         return self
 
     def kernel_times(self) -> dict:

@@ -252,6 +252,58 @@ __device__ __forceinline__ void hmoments3(const R* __restrict__ h, size_t N, siz
     J[0] = j0; J[1] = j1; J[2] = j2;
 }
 
+// psi and J of a cell's potential populations (Eq. 45)
+template <class R>
+__device__ __forceinline__ void pot3_moments(const R (&hv)[Q3], R& psi, R J[3]) {
+    R a = R(0);
+#pragma unroll
+    for (int j = 1; j < Q3; ++j) a += hv[j];
+    psi = a / (R(1) - w3<R>(0));
+    J[0] = J[1] = J[2] = R(0);
+#pragma unroll
+    for (int j = 0; j < Q3; ++j) {
+        cacc(J[0], c3x(j), hv[j]);
+        cacc(J[1], c3y(j), hv[j]);
+        cacc(J[2], c3z(j), hv[j]);
+    }
+}
+// Collision of a cell's potential populations (Eq. 43, equilibrium Eq. 44) and
+// push-streaming to its neighbours: columns, rows and planes formed once, 32-bit
+// indices (at most LB3E_MAX_CELLS cells, so 15 N fits); across a z wall the
+// population returns to this cell (electrodes: the Dirichlet rule)
+template <class R>
+__device__ __forceinline__ void pot3_collide_push(const P3& P, const R (&hv)[Q3], R psi, const R J[3], R epsc, R qc,
+                                                  int x, int y, int z, unsigned c, unsigned N, R* __restrict__ hout) {
+    // divisions: exact in the FP64 build, by a reciprocal formed once in FP32
+    const R th = pv<R>(P.tau_h, P.ftau_h), ith = pv<R>(1.0 / P.tau_h, P.fitau_h),
+            epshat = epsc - pv<R>(P.eps_ref, P.feps_ref);
+    const R den = epshat + (R(1) / R(3)) * th, iden = rcp(den);
+    const R g0 = dv(-J[0], den, iden), g1 = dv(-J[1], den, iden), g2 = dv(-J[2], den, iden);
+    const R e3 = ocs2(epshat);
+    const unsigned nx = (unsigned)P.nx, ny = (unsigned)P.ny, nz = (unsigned)P.nz, nxy = nx * ny;
+    const unsigned col[3] = {x == 0 ? nx - 1 : (unsigned)x - 1, (unsigned)x, x == P.nx - 1 ? 0u : (unsigned)x + 1};
+    const unsigned row[3] = {(y == 0 ? ny - 1 : (unsigned)y - 1) * nx, (unsigned)y * nx,
+                             (y == P.ny - 1 ? 0u : (unsigned)y + 1) * nx};
+    const unsigned pln[3] = {(z == 0 ? nz - 1 : (unsigned)z - 1) * nxy, (unsigned)z * nxy,
+                             (z == P.nz - 1 ? 0u : (unsigned)z + 1) * nxy};
+    const bool wall_lo = P.bc != 0 && z == 0, wall_hi = P.bc != 0 && z == P.nz - 1;
+#pragma unroll
+    for (int j = 0; j < Q3; ++j) {
+        const R heq = j == 0 ? (w3<R>(0) - R(1)) * psi : w3<R>(j) * psi;     // Eq. 44
+        const R varpi = j == 0 ? R(0) : R(1.0 / 14.0);
+        const R hj = hv[j];
+        const R cg = cdot3<R>(j, g0, g1, g2);
+        const R v = hj - dv(hj - heq, th, ith) - dv(e3 * w3<R>(j) * cg, th, ith) + varpi * qc;
+        if ((c3z(j) < 0 && wall_lo) || (c3z(j) > 0 && wall_hi)) {  // across a z wall: back to this cell
+            R out = v;
+            if (P.bc == 2) out = -v + R(2) * w3<R>(j) * pv<R>(c3z(j) > 0 ? P.V_top : P.V_bottom, c3z(j) > 0 ? P.fVt : P.fVb);
+            hout[opp3(j) * N + c] = out;
+        } else {
+            hout[j * N + pln[c3z(j) + 1] + row[c3y(j) + 1] + col[c3x(j) + 1]] = v;
+        }
+    }
+}
+
 // One pseudo-iteration: collide and push-stream h.  save: store psi, J (the state
 // a later check compares with); check: accumulate |d psi|^2, |psi|^2, |dJ|^2, |J|^2
 // per block (FP64 partials).  FP32: held to 64 registers (four blocks an SM); the
@@ -264,25 +316,14 @@ __global__ void __launch_bounds__(256, std::is_same<R, float>::value ? 4 : 1)
     int x, y, z;
     size_t cz;
     const bool in = cell3(P, x, y, z, cz);
-    // 32-bit indices (at most LB3E_MAX_CELLS cells, so 15 N fits): the populations
-    // loaded once, the neighbours' columns, rows and planes formed once a cell
     const unsigned N = (unsigned)P.N, c = (unsigned)cz;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     if (in) {
         R hv[Q3];
 #pragma unroll
         for (int j = 0; j < Q3; ++j) hv[j] = hin[j * N + c];
-        R a = R(0);
-#pragma unroll
-        for (int j = 1; j < Q3; ++j) a += hv[j];
-        const R psi = a / (R(1) - w3<R>(0));
-        R J[3] = {R(0), R(0), R(0)};
-#pragma unroll
-        for (int j = 0; j < Q3; ++j) {
-            cacc(J[0], c3x(j), hv[j]);
-            cacc(J[1], c3y(j), hv[j]);
-            cacc(J[2], c3z(j), hv[j]);
-        }
+        R psi, J[3];
+        pot3_moments(hv, psi, J);
         if (check) {
             const double d = (double)psi - (double)prev[c];
             acc[0] = d * d;
@@ -299,38 +340,73 @@ __global__ void __launch_bounds__(256, std::is_same<R, float>::value ? 4 : 1)
 #pragma unroll
             for (int k = 0; k < 3; ++k) prev[(1 + k) * N + c] = J[k];
         }
-        // divisions: exact in the FP64 build, by a reciprocal formed once in FP32
-        const R th = pv<R>(P.tau_h, P.ftau_h), ith = pv<R>(1.0 / P.tau_h, P.fitau_h),
-                epshat = eps[c] - pv<R>(P.eps_ref, P.feps_ref);
-        const R den = epshat + (R(1) / R(3)) * th, iden = rcp(den);
-        const R g0 = dv(-J[0], den, iden), g1 = dv(-J[1], den, iden), g2 = dv(-J[2], den, iden);
-        const R qc = q[c], e3 = ocs2(epshat);
-        const unsigned nx = (unsigned)P.nx, ny = (unsigned)P.ny, nz = (unsigned)P.nz, nxy = nx * ny;
-        const unsigned col[3] = {x == 0 ? nx - 1 : (unsigned)x - 1, (unsigned)x, x == P.nx - 1 ? 0u : (unsigned)x + 1};
-        const unsigned row[3] = {(y == 0 ? ny - 1 : (unsigned)y - 1) * nx, (unsigned)y * nx,
-                                 (y == P.ny - 1 ? 0u : (unsigned)y + 1) * nx};
-        const unsigned pln[3] = {(z == 0 ? nz - 1 : (unsigned)z - 1) * nxy, (unsigned)z * nxy,
-                                 (z == P.nz - 1 ? 0u : (unsigned)z + 1) * nxy};
-        const bool wall_lo = P.bc != 0 && z == 0, wall_hi = P.bc != 0 && z == P.nz - 1;
-#pragma unroll
-        for (int j = 0; j < Q3; ++j) {
-            const R heq = j == 0 ? (w3<R>(0) - R(1)) * psi : w3<R>(j) * psi;     // Eq. 44
-            const R varpi = j == 0 ? R(0) : R(1.0 / 14.0);
-            const R hj = hv[j];
-            const R cg = cdot3<R>(j, g0, g1, g2);
-            const R v = hj - dv(hj - heq, th, ith) - dv(e3 * w3<R>(j) * cg, th, ith) + varpi * qc;
-            if ((c3z(j) < 0 && wall_lo) || (c3z(j) > 0 && wall_hi)) {  // across a z wall: back to this cell
-                R out = v;
-                if (P.bc == 2) out = -v + R(2) * w3<R>(j) * pv<R>(c3z(j) > 0 ? P.V_top : P.V_bottom, c3z(j) > 0 ? P.fVt : P.fVb);
-                hout[opp3(j) * N + c] = out;
-            } else {
-                hout[j * N + pln[c3z(j) + 1] + row[c3y(j) + 1] + col[c3x(j) + 1]] = v;
-            }
-        }
+        pot3_collide_push(P, hv, psi, J, eps[c], q[c], x, y, z, c, N, hout);
     }
     if (check) {
         const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
         block_reduce_store<4>(acc, partial + 4 * (size_t)b);
+    }
+}
+
+// The same iteration (no check, no save) with its inputs staged by the tensor memory
+// accelerator: a block walks up to `walk` consecutive planes of its 32 x 8 tile, and
+// one thread copies each plane's 15 population boxes, eps and q (17 boxes of 32 x 8
+// cells) into one of P3ST shared-memory stages, so that the loads of the next
+// planes are in flight while a plane is collided.  Boxes beyond the lattice arrive
+// as zeros and are not used.  A wait that runs out sets the error flag; the block
+// then waits, bounded, for its copies still in flight and returns.
+constexpr int P3ST = 3, P3BOX = 17;
+template <class R>
+constexpr size_t k3_poisson_tma_smem() { return (size_t)P3ST * P3BOX * 256 * sizeof(R); }
+template <class R>
+__global__ void __launch_bounds__(256, 4)
+    k3_poisson_tma(P3 P, const __grid_constant__ CUtensorMap tm_h, const __grid_constant__ CUtensorMap tm_eps,
+                   const __grid_constant__ CUtensorMap tm_q, R* __restrict__ hout, int walk, int* err) {
+    extern __shared__ __align__(128) unsigned char p3_raw[];
+    R* st = reinterpret_cast<R*>(p3_raw);  // [stage][17 boxes][8 rows][32]
+    __shared__ __align__(8) uint64_t bar[P3ST];
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8, z0 = blockIdx.z * walk;
+    const int nzb = P.nz - z0 < walk ? P.nz - z0 : walk;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const unsigned N = (unsigned)P.N;
+    auto issue = [&](int i) {  // plane z0 + i into stage i % P3ST (one thread)
+        R* d = st + (size_t)(i % P3ST) * P3BOX * 256;
+        uint64_t* b = &bar[i % P3ST];
+        mbar_arrive_expect_tx(b, P3BOX * 256 * (unsigned)sizeof(R));
+#pragma unroll 1
+        for (int j = 0; j < Q3; ++j) tma_load_3d(d + j * 256, &tm_h, x0, y0, j * P.nz + z0 + i, b);
+        tma_load_3d(d + 15 * 256, &tm_eps, x0, y0, z0 + i, b);
+        tma_load_3d(d + 16 * 256, &tm_q, x0, y0, z0 + i, b);
+    };
+    if (tid == 0) {
+        for (int s = 0; s < P3ST; ++s) mbar_init(&bar[s], 1);
+        for (int i = 0; i < P3ST && i < nzb; ++i) issue(i);
+    }
+    __syncthreads();
+    int i = 0;
+    for (; i < nzb; ++i) {
+        const int s = i % P3ST;
+        const bool ok = mbar_wait(&bar[s], (unsigned)((i / P3ST) & 1), TMA_WAIT_LIMIT);
+        if (ok && x < P.nx && y < P.ny) {
+            const R* d = st + (size_t)s * P3BOX * 256 + tid;
+            R hv[Q3];
+#pragma unroll
+            for (int j = 0; j < Q3; ++j) hv[j] = d[j * 256];
+            R psi, J[3];
+            pot3_moments(hv, psi, J);
+            const int z = z0 + i;
+            const unsigned c = ((unsigned)z * (unsigned)P.ny + (unsigned)y) * (unsigned)P.nx + (unsigned)x;
+            pot3_collide_push(P, hv, psi, J, d[15 * 256], d[16 * 256], x, y, z, c, N, hout);
+        }
+        // stage s read by every thread; a failed wait anywhere seen by all
+        if (__syncthreads_or(ok ? 0 : 1)) break;
+        if (tid == 0 && i + P3ST < nzb) issue(i + P3ST);
+    }
+    if (i < nzb && tid == 0) {  // gave up: let the copies in flight land first
+        const int e = i + P3ST < nzb ? i + P3ST : nzb;
+        for (int k = i; k < e; ++k) mbar_wait(&bar[k % P3ST], (unsigned)((k / P3ST) & 1), TMA_WAIT_LIMIT);
+        if (err) atomicExch(err, 1);
     }
 }
 
@@ -819,6 +895,8 @@ class Sim3 final : public SimBase {
             return LB3E_ERR_CUDA;
         if (cudaHostAlloc(reinterpret_cast<void**>(&pinned_), 64 * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
             return LB3E_ERR_CUDA;
+        TRY(zero(err_flag(), sizeof(int)));
+        tma_ready_ = tma_prepare();
         TRY(upload(phi, 3 * N_, phi_));
         if (u) TRY(upload(u, 3 * N_, diag_));
         else TRY(zero(diag_, 3 * N_ * sizeof(R)));
@@ -975,6 +1053,11 @@ class Sim3 final : public SimBase {
     int deformation(double*, double*) override { return LB3E_ERR_PARAM; }
     int shape_objective(const double*, double*, double*) override { return LB3E_ERR_PARAM; }
     int set_fused_tile(int) override { return LB3E_ERR_PARAM; }
+    int set_staging(int planes) override {
+        if (planes < 0 || planes > 1024) return LB3E_ERR_PARAM;
+        staging_ = planes;
+        return LB3E_OK;
+    }
 
   private:
     // Scratch for the rho, sigma, eps outputs of a field-readback moments pass: the
@@ -986,7 +1069,58 @@ class Sim3 final : public SimBase {
         timer.end(stream_);
         return cudaGetLastError() == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
     }
-    int sync() { return cudaStreamSynchronize(stream_) == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA; }
+    // a kernel's error flag (a timed-out wait), read back by sync()
+    int* err_flag() { return reinterpret_cast<int*>(result_ + 63); }
+    int sync() {
+        if (!pinned_) return cudaStreamSynchronize(stream_) == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA;
+        int* fl = reinterpret_cast<int*>(pinned_ + 63);
+        if (cudaMemcpyAsync(fl, err_flag(), sizeof(int), cudaMemcpyDeviceToHost, stream_) != cudaSuccess)
+            return LB3E_ERR_CUDA;
+        if (cudaStreamSynchronize(stream_) != cudaSuccess) return LB3E_ERR_CUDA;
+        if (*fl) {
+            *fl = 0;
+            cudaMemsetAsync(err_flag(), 0, sizeof(int), stream_);
+            return LB3E_ERR_CUDA;
+        }
+        return LB3E_OK;
+    }
+    // Tensor maps of the staged potential iteration: the two h buffers as (nx, ny,
+    // 15 nz) arrays, eps and q as (nx, ny, nz), boxes of 32 x 8 x 1 (FP32 only; the
+    // row pitch must be a multiple of 16 bytes)
+    bool tma_prepare() {
+        if constexpr (!std::is_same<R, float>::value) {
+            return false;
+        } else {
+            if (p_.nx % 4 != 0) return false;
+            using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                        const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                        CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+            static Encode encode = [] {
+                void* f = nullptr;
+                cudaDriverEntryPointQueryResult q{};
+                if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                        cudaSuccess ||
+                    q != cudaDriverEntryPointSuccess)
+                    f = nullptr;
+                return reinterpret_cast<Encode>(f);
+            }();
+            if (!encode) return false;
+            const cuuint64_t nx = (cuuint64_t)p_.nx, ny = (cuuint64_t)p_.ny, nz = (cuuint64_t)p_.nz;
+            const cuuint32_t one[3] = {1, 1, 1}, box[3] = {32, 8, 1};
+            auto make = [&](CUtensorMap* m, void* base, cuuint64_t planes) {
+                const cuuint64_t dims[3] = {nx, ny, planes};
+                const cuuint64_t strides[2] = {nx * sizeof(float), nx * ny * sizeof(float)};
+                return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, one,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            };
+            if (!make(&tm_h_[0], h_[0], Q3 * nz) || !make(&tm_h_[1], h_[1], Q3 * nz) || !make(&tm_eps_, eps_, nz) ||
+                !make(&tm_q_, q_, nz))
+                return false;
+            return cudaFuncSetAttribute(k3_poisson_tma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)k3_poisson_tma_smem<float>()) == cudaSuccess;
+        }
+    }
     int zero(void* p, size_t b) { return cudaMemsetAsync(p, 0, b, stream_) == cudaSuccess ? LB3E_OK : LB3E_ERR_CUDA; }
     int upload(const double* src, size_t n, R* dst) {
         for (size_t off = 0; off < n; off += N_) {
@@ -1016,8 +1150,16 @@ class Sim3 final : public SimBase {
             const int do_check = fixed <= 0 && k >= 2 && k % check == 0;
             const int save = fixed <= 0 && (k + 1) % check == 0;
             timer.begin(stream_, KC_POISSON);
-            k3_poisson<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, h_[hcur_], h_[hcur_ ^ 1], eps_, q_, psi_prev_,
-                                                              partial_, save, do_check);
+            if (tma_ready_ && staging_ && !save && !do_check) {
+                if constexpr (std::is_same<R, float>::value) {
+                    const dim3 g((p_.nx + 31) / 32, (p_.ny + 7) / 8, (p_.nz + staging_ - 1) / staging_);
+                    k3_poisson_tma<float><<<g, dim3(32, 8), k3_poisson_tma_smem<float>(), stream_>>>(
+                        P_, tm_h_[hcur_], tm_eps_, tm_q_, h_[hcur_ ^ 1], staging_, err_flag());
+                }
+            } else {
+                k3_poisson<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, h_[hcur_], h_[hcur_ ^ 1], eps_, q_, psi_prev_,
+                                                                  partial_, save, do_check);
+            }
             TRY(launched());
             if (do_check) {
                 // the residual of the state before this launch's collision
@@ -1057,6 +1199,9 @@ class Sim3 final : public SimBase {
         *psi_prev_{};
     double *partial_{}, *result_{}, *stage_{};
     double* pinned_ = nullptr;
+    CUtensorMap tm_h_[2]{}, tm_eps_{}, tm_q_{};  // the staged potential iteration's tensor maps (tma_prepare)
+    bool tma_ready_ = false;
+    int staging_ = 2;  // planes a block walks in the staged potential iteration (0: per-thread loads)
     int cur_ = 0, hcur_ = 0;
     int64_t step_ = 0;
     int last_iters_ = 0, last_conv_ = 0;

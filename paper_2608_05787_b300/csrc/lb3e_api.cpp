@@ -229,6 +229,12 @@ int lb3e_set_fused_tile(lb3e_handle* h, int32_t rows) {
     return h->sim->set_fused_tile(rows);
 }
 
+int lb3e_set_staging(lb3e_handle* h, int32_t planes) {
+    if (!h) return LB3E_ERR_NULL;
+    if (planes < 0 || planes > 1024) return LB3E_ERR_PARAM;
+    return h->sim->set_staging(planes);
+}
+
 int lb3e_deformation(lb3e_handle* h, double* D, double* dD) {
     if (!h || !D) return LB3E_ERR_NULL;
     return h->sim->deformation(D, dD);

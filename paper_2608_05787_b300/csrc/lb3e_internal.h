@@ -87,6 +87,8 @@ struct SimBase {
     virtual int deformation(double* D, double* dD) = 0;
     virtual int shape_objective(const double* target, double* J, double* dJ) = 0;
     virtual int set_fused_tile(int rows) = 0;
+    // TMA staging of the D3Q15 potential iteration's inputs (three-dimensional only)
+    virtual int set_staging(int planes) { (void)planes; return LB3E_ERR_UNSUPPORTED; }
     // reverse mode (two-dimensional plain builds with a fixed potential count)
     virtual int adjoint_workspace_bytes(size_t* bytes) { (void)bytes; return LB3E_ERR_UNSUPPORTED; }
     virtual int state_vector(void* dst) { (void)dst; return LB3E_ERR_UNSUPPORTED; }

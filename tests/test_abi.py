@@ -140,3 +140,11 @@ def test_anchored_solver_workspace_holds_the_fp64_anchor():
     n = 64 * 64
     assert anch - plain >= 9 * n * 8 + 9 * n * 4   # the FP64 anchor and its FP32 increment
     assert coarse > anch                           # plus the multigrid levels
+
+
+def test_staging_switch_checks_its_handle():
+    """lb3e_set_staging validates on the host: a NULL handle is refused before any
+    device work."""
+    lib = L.lib()
+    assert lib.lb3e_set_staging(None, 1) == -6
+    assert lib.lb3e_set_staging(None, 0) == -6

@@ -24,13 +24,13 @@ def rel_linf(a, b):
     return np.abs(a - b).max() / scale if scale > 1e-300 else np.abs(a - b).max()
 
 
-def _case(bc, precision=0):
+def _case(bc, precision=0, shape=(37, 11, 10)):
     """37 x 11 x 10 cells (ragged against the 32 x 8 tiles), a compound sphere,
     unequal densities and viscosities, permittivity and conductivity contrasts, an
     external field, moving walls and electrodes (bc >= 1), an initial flow and
     charge (seeded).  Without electrodes the net charge leaves the potential
     undetermined, so those cases run a fixed number of potential iterations."""
-    nx, ny, nz = 37, 11, 10
+    nx, ny, nz = shape
     rng = np.random.default_rng(17)
     p = W.params(nx=nx, ny=ny, bc_y=bc, electric=1, precision=precision, rho=(1.0, 1.3, 0.8),
                  visc=(0.1, 0.05, 0.2), gamma12=1e-3, gamma13=8e-4, gamma23=6e-4, eps=(1.0, 3.0, 2.0),
@@ -80,6 +80,30 @@ def test_fp32_3d_matches_oracle():
     assert all(v <= 1e-5 for v in errs.values()), errs
 
 
+@pytest.mark.parametrize("bc", [0, 2])
+def test_fp32_3d_staged_potential(bc):
+    """The potential iteration with its inputs staged by TMA (FP32, nx a multiple of
+    4) on 40 x 12 x 20 cells, ragged against the 32 x 8 tiles and the 16-plane walks:
+    bitwise the states of the per-thread loads (fixed iterations all staged; with the
+    residual test the checking and saving iterations take the per-thread kernel), and
+    the oracle's fields to 1e-5."""
+    L = _lb()
+    p, phi, u, q = _case(bc, precision=1, shape=(40, 12, 20))
+    a = L.Sim(p, phi, u=u, q=q)
+    b = L.Sim(p, phi, u=u, q=q).set_staging(0)
+    c = L.Sim(p, phi, u=u, q=q).set_staging(7)   # walks of 7, 7 and 6 planes
+    for s in (a, b, c):
+        s.step(12)
+    for f in FIELDS:
+        assert np.array_equal(a.field(f), b.field(f)), f
+        assert np.array_equal(c.field(f), b.field(f)), f
+    assert a.observables()["poisson_iters"] == b.observables()["poisson_iters"]
+    orc = oracle.Oracle3D(p, phi, u=u, q=q)
+    orc.step(12)
+    errs = {f: rel_linf(a.field(f), orc.field(f)) for f in ("phinow1", "phinow2", "phinow3", "psi", "ex", "ez", "q")}
+    assert all(v <= 1e-5 for v in errs.values()), errs
+
+
 def test_3d_rejects_unsupported_options():
     L = _lb()
     p, phi, u, q = _case(2)
@@ -89,6 +113,8 @@ def test_3d_rejects_unsupported_options():
     s = L.Sim(p, phi)
     with pytest.raises(L.LB3EError):
         s.save_state()
+    with pytest.raises(L.LB3EError):
+        s.set_staging(-1)
     with pytest.raises(L.LB3EError):
         L.Sim(p, phi, noise=np.zeros((5, 15, 10, 11, 37)))
 
