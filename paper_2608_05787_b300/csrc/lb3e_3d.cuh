@@ -779,43 +779,58 @@ __global__ void __launch_bounds__(256) k3_init_pops(P3 P, R* __restrict__ pop, c
 // observables: per-block FP64 sums of mass (3), charge, nonfinite count and the
 // second moments of the two indicators (x and z), plus a block max of |sum phi - 1|
 constexpr int NOBS3 = 15;
+// OBS3_Z planes a thread: a block of 32 x 8 threads covers 32 x 8 x OBS3_Z cells, so
+// the FP64 block reduction is shared by OBS3_Z cells a thread and the final
+// single-block reduction sees nz / OBS3_Z times fewer partials.  The per-cell terms
+// are evaluated in FP32 in the FP32 build and summed as FP32 sum-and-error pairs
+// (ObsAcc), FP64 otherwise.
+constexpr int OBS3_Z = 16;
+inline dim3 obs3_grid(const lb3e_params& p) { return dim3((p.nx + 31) / 32, (p.ny + 7) / 8, (p.nz + OBS3_Z - 1) / OBS3_Z); }
 template <class R>
 __global__ void __launch_bounds__(256) k3_observables(P3 P, const R* __restrict__ phi, const R* __restrict__ q,
                                                       const R* __restrict__ u, double* __restrict__ partial,
                                                       double* __restrict__ maxpart) {
-    int x, y, z;
-    size_t c;
-    const bool in = cell3(P, x, y, z, c);
-    const size_t N = P.N;
-    double v[NOBS3];
+    using T = typename std::conditional<std::is_same<R, float>::value, float, double>::type;
+    ObsAcc<T, NOBS3> acc;
+    T mdev = T(0);
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x < P.nx && y < P.ny) {
+        const unsigned N = (unsigned)P.N;
+        const int z1 = (int)(blockIdx.z + 1) * OBS3_Z < P.nz ? (int)(blockIdx.z + 1) * OBS3_Z : P.nz;
+        for (int z = blockIdx.z * OBS3_Z; z < z1; ++z) {
+            const unsigned c = ((unsigned)z * (unsigned)P.ny + (unsigned)y) * (unsigned)P.nx + (unsigned)x;
+            T ph[3];
 #pragma unroll
-    for (int k = 0; k < NOBS3; ++k) v[k] = 0.0;
-    double dev = 0.0;
-    if (in) {
-        double ph[3], s = 0.0;
+            for (int i = 0; i < 3; ++i) {
+                ph[i] = (T)phi[i * N + c];
+                acc.add(i, ph[i]);
+            }
+            const T qc = (T)q[c];
+            acc.add(3, qc);
+            const T vals[7] = {ph[0], ph[1], ph[2], (T)u[c], (T)u[N + c], (T)u[2 * N + c], qc};
 #pragma unroll
-        for (int i = 0; i < 3; ++i) { ph[i] = (double)phi[i * N + c]; v[i] = ph[i]; s += ph[i]; }
-        dev = fabs(s - 1.0);
-        v[3] = (double)q[c];
-        const double vals[7] = {ph[0], ph[1], ph[2], (double)u[c], (double)u[N + c], (double)u[2 * N + c], v[3]};
+            for (int k = 0; k < 7; ++k)
+                if (!isfinite(vals[k])) acc.add(4, T(1));
+            const T chis[2] = {ph[P.inner - 1], T(1) - ph[P.matrix - 1]};
 #pragma unroll
-        for (int k = 0; k < 7; ++k)
-            if (!isfinite(vals[k])) v[4] += 1.0;
-        const double chis[2] = {ph[P.inner - 1], 1.0 - ph[P.matrix - 1]};
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            v[5 + 5 * k] = chis[k];
-            v[6 + 5 * k] = chis[k] * x;
-            v[7 + 5 * k] = chis[k] * z;
-            v[8 + 5 * k] = chis[k] * x * x;
-            v[9 + 5 * k] = chis[k] * z * z;
+            for (int k = 0; k < 2; ++k) {
+                acc.add(5 + 5 * k, chis[k]);
+                acc.add(6 + 5 * k, chis[k] * T(x));
+                acc.add(7 + 5 * k, chis[k] * T(z));
+                acc.add(8 + 5 * k, chis[k] * T(x) * T(x));
+                acc.add(9 + 5 * k, chis[k] * T(z) * T(z));
+            }
+            const T dv = sum_dev3(ph[0], ph[1], ph[2]);
+            mdev = dv > mdev ? dv : mdev;  // as fmax: a NaN is left to the nonfinite count
         }
     }
     const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    double v[NOBS3];
+    acc.out(v);
     block_reduce_store<NOBS3>(v, partial + (size_t)NOBS3 * b);
     // block max of the deviation
     __shared__ double red[8];
-    double m = dev;
+    double m = (double)mdev;
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     if ((tid & 31) == 0) red[tid >> 5] = m;
@@ -952,12 +967,14 @@ class Sim3 final : public SimBase {
 
     int observables(lb3e_observables_t* o) override {
         timer.begin(stream_, KC_REDUCE);
-        k3_observables<R><<<grid_, dim3(32, 8), 0, stream_>>>(P_, phi_, q_, diag_, partial_,
-                                                              partial_ + (size_t)nblk_ * NOBS3);
+        const dim3 og = obs3_grid(p_);
+        const int nob = (int)(og.x * og.y * og.z);
+        k3_observables<R><<<og, dim3(32, 8), 0, stream_>>>(P_, phi_, q_, diag_, partial_,
+                                                           partial_ + (size_t)nob * NOBS3);
         TRY(launched());
-        k_reduce_partials<NOBS3><<<1, 256, 0, stream_>>>(partial_, nblk_, result_);
+        k_reduce_partials<NOBS3><<<1, 256, 0, stream_>>>(partial_, nob, result_);
         TRY(launched());
-        k_max_partials<<<1, 256, 0, stream_>>>(partial_ + (size_t)nblk_ * NOBS3, nblk_, result_ + NOBS3);
+        k_max_partials<<<1, 256, 0, stream_>>>(partial_ + (size_t)nob * NOBS3, nob, result_ + NOBS3);
         TRY(launched());
         if (cudaMemcpyAsync(pinned_, result_, (NOBS3 + 1) * sizeof(double), cudaMemcpyDeviceToHost, stream_) !=
             cudaSuccess)

@@ -2,15 +2,16 @@
 rounding of the FP32 size on the stated spreading lens (512 x 256, walls, no field,
 tensions 1e-3 / 8e-4 / 6e-4, 20 000 steps).
 
-Two oracle runs from the same state; before every step the second has every stored
-population (and the FP32 anchor phi_i) perturbed by u * 2^-24 * |v|, u uniform in
-[-1, 1) from a seeded hash (oracle.Oracle.perturb), the model of the FP32 build's
-rounding that the static-compound gates use.  For each of phinow1..3:
-max |perturbed - plain| / max |plain| after the last step.  The lens is still
-spreading at 20 000 steps (its contact lines move), so rounding of this size shifts
-the interfaces by a small fraction of a lattice spacing, and the relative field
-difference is that shift times the interface gradient.  Only the oracle runs here
-(about an hour on 8 cores).
+Three oracle runs in lock step from the same state:
+* plain;
+* "perturbation": before every step every stored population (and the FP32 anchor
+  phi_i) is perturbed by u * 2^-24 * |v|, u uniform in [-1, 1) from a seeded hash
+  (oracle.Oracle.perturb), fresh every step: rounding as a random walk;
+* "rounding": after every step the stored populations are rounded to FP32 exactly
+  as the FP32 build stores them (oracle.Oracle.round_storage): deterministic, so a
+  cell whose values change slowly is rounded the same way step after step.
+For each of phinow1..3: max |modified - plain| / max |plain| after 2000, 5000, 10 000
+and 20 000 steps.  Only the oracle runs here (about 1.5 hours on 8 cores).
 Usage: python tests/golden/make_lens_sensitivity.py
 """
 from __future__ import annotations
@@ -33,20 +34,27 @@ STEPS = 20000
 REPORT = (2000, 5000, 10000, 20000)
 
 
+def _diff(a, b) -> dict:
+    return {f: float(np.abs(a.field(f) - b.field(f)).max() / np.abs(a.field(f)).max()) for f in FIELDS}
+
+
 def main():
     cfg = W.config_lens(tensions=TENSIONS, precision=0)
-    a = oracle.Oracle(cfg["params"], cfg["phi"])
-    b = oracle.Oracle(cfg["params"], cfg["phi"])
+    a, b, c = (oracle.Oracle(cfg["params"], cfg["phi"]) for _ in range(3))
+    c.round_storage("fp32")
     out = {"workload": "spreading lens 512x256, walls, no field, tensions %s" % (TENSIONS,),
-           "model": "every stored value perturbed at the FP32 unit roundoff before every step", "after": {}}
+           "models": {"perturbation": "every stored value perturbed at the FP32 unit roundoff before every step",
+                      "rounding": "the stored populations rounded to FP32 after every step"},
+           "after": {}}
     for k in range(STEPS):
         b.perturb(2.0 ** -24, 0.0, 2.0 ** -24, seed=k + 1)
         a.step(1)
         b.step(1)
+        c.step(1)
+        c.round_storage("fp32")
         if k + 1 in REPORT:
-            d = {f: float(np.abs(a.field(f) - b.field(f)).max() / np.abs(a.field(f)).max()) for f in FIELDS}
-            out["after"][str(k + 1)] = d
-            print(k + 1, d, flush=True)
+            out["after"][str(k + 1)] = {"perturbation": _diff(a, b), "rounding": _diff(a, c)}
+            print(k + 1, out["after"][str(k + 1)], flush=True)
     (Path(__file__).parent / "lens_sensitivity.json").write_text(json.dumps(out, indent=1) + "\n")
 
 
