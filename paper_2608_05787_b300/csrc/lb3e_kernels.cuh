@@ -1913,9 +1913,10 @@ __global__ void k_pop_to_f64(double* __restrict__ dst, const S* __restrict__ pop
 // moments (sum chi, chi x, chi y, chi x^2, chi y^2) for inner and outer; the max
 // deviation |sum phi - 1| is a separate per-block max.
 constexpr int NOBS = 19;
-// OBS_Y cells per thread along y: a 32 x 8 block covers 32 x 64 cells, so the FP64
-// block reduction of the NOBS sums is shared by eight cells per thread.
-constexpr int OBS_Y = 8;
+// OBS_Y cells per thread along y: a 32 x 8 block covers 32 x 256 cells, so the
+// FP64 conversions and block reduction of the NOBS sums (FP64 runs at a small
+// fraction of the FP32 rate) are shared by 32 cells per thread.
+constexpr int OBS_Y = 32;
 inline dim3 obs_grid(int nx, int ny) { return dim3((nx + TX - 1) / TX, (ny + TY * OBS_Y - 1) / (TY * OBS_Y)); }
 // A thread's sums of its OBS_Y cells.  FP64: plain FP64 sums.  FP32 terms: an FP32
 // sum and the exact rounding error of each of its additions (Knuth's TwoSum),
@@ -1981,10 +1982,14 @@ __global__ void __launch_bounds__(256) k_observables(DevParams P, const R* __res
     ObsAcc<T, NOBS> acc;
     T mdev = T(0);
     const int x = blockIdx.x * TX + threadIdx.x;
+    // the stencil's columns, formed once a thread (32-bit: at most LB3E_MAX_CELLS cells)
+    const unsigned col[3] = {(unsigned)wrapi(x - 1, P.nx), (unsigned)x, (unsigned)wrapi(x + 1, P.nx)};
     for (int r = 0; r < OBS_Y; ++r) {
         const int y = blockIdx.y * (TY * OBS_Y) + r * TY + threadIdx.y;
         if (x >= P.nx || y >= P.ny) continue;
         const unsigned N = P.N, c = (unsigned)y * P.nx + x;
+        const unsigned row[3] = {(unsigned)ghost_row(y - 1, P.ny, P.bc_y) * (unsigned)P.nx, (unsigned)y * (unsigned)P.nx,
+                                 (unsigned)ghost_row(y + 1, P.ny, P.bc_y) * (unsigned)P.nx};
         const T D = pv<T>(P.D, P.fD);
         T ph[3];
         T fphi = T(0);
@@ -1994,7 +1999,7 @@ __global__ void __launch_bounds__(256) k_observables(DevParams P, const R* __res
             T ax = T(0), ay = T(0);
 #pragma unroll
             for (int j = 1; j < 9; ++j) {
-                const T w = (T)f[(size_t)ghost_row(y + cy(j), P.ny, P.bc_y) * P.nx + wrapi(x + cx(j), P.nx)];
+                const T w = (T)f[row[cy(j) + 1] + col[cx(j) + 1]];
                 cacc(ax, cx(j), wgt<T>(j), w);
                 cacc(ay, cy(j), wgt<T>(j), w);
             }
