@@ -109,6 +109,60 @@ __device__ __forceinline__ bool cell3(const P3& P, int& x, int& y, int& z, size_
     c = ((size_t)z * P.ny + y) * P.nx + x;
     return x < P.nx && y < P.ny;
 }
+// A block's stencil tile: its 32 x 8 cells with a one-cell ring, on the planes z - 1,
+// z, z + 1 (x and y periodic; z periodic or mirrored at the walls, the stencil
+// ghosts), one 34 x 10 x 3 array a field in shared memory
+constexpr int K3X = 34, K3Y = 10, K3P = K3X * K3Y, K3F = 3 * K3P;
+// stage M fields' tiles (all threads of the 32 x 8 block, also those outside the
+// lattice; 32-bit indices: at most LB3E_MAX_CELLS cells)
+template <class R, int M>
+__device__ __forceinline__ void stage_tile3(const P3& P, const R* const (&fl)[M], R* __restrict__ st) {
+    const int x0 = blockIdx.x * 32 - 1, y0 = blockIdx.y * 8 - 1, zc = blockIdx.z;
+    const unsigned nx = (unsigned)P.nx, nxy = nx * (unsigned)P.ny;
+    unsigned zo[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int zz = zc + d - 1;
+        if (P.bc == 0) zz = zz < 0 ? zz + P.nz : (zz >= P.nz ? zz - P.nz : zz);
+        else zz = zz < 0 ? -zz - 1 : (zz >= P.nz ? 2 * P.nz - zz - 1 : zz);
+        zo[d] = (unsigned)zz * nxy;
+    }
+    // every load of the thread issued before the first store: IT x M loads in flight
+    constexpr int IT = (K3F + 255) / 256;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    R v[IT][M];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int k = tid + 256 * it;
+        if (k < K3F) {
+            const int pz = k / K3P, r = k - pz * K3P, ly = r / K3X, lx = r - ly * K3X;
+            const unsigned n = zo[pz] + (unsigned)wrapi(y0 + ly, P.ny) * nx + (unsigned)wrapi(x0 + lx, P.nx);
+#pragma unroll
+            for (int m = 0; m < M; ++m) v[it][m] = fl[m][n];
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int k = tid + 256 * it;
+        if (k < K3F) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) st[m * K3F + k] = v[it][m];
+        }
+    }
+}
+// Eq. 33 gradient of a staged field at tile position sc
+template <class R>
+__device__ __forceinline__ void grad3_tile(const R* __restrict__ t, int sc, R g[3]) {
+    R a0 = R(0), a1 = R(0), a2 = R(0);
+#pragma unroll
+    for (int j = 0; j < Q3; ++j) {
+        const R v = w3<R>(j) * t[sc + c3z(j) * K3P + c3y(j) * K3X + c3x(j)];
+        cacc(a0, c3x(j), v);
+        cacc(a1, c3y(j), v);
+        cacc(a2, c3z(j), v);
+    }
+    g[0] = ocs2(a0); g[1] = ocs2(a1); g[2] = ocs2(a2);
+}
 // The stencil neighbours of a cell in 32-bit indices (at most LB3E_MAX_CELLS cells):
 // the columns, rows and planes of the offsets -1, 0, +1 formed once a cell; x and y
 // periodic, z periodic or mirrored at the walls (the stencil ghosts)
@@ -131,7 +185,8 @@ __device__ __forceinline__ Nb3 stencil3(const P3& P, int x, int y, int z) {
     s.pln[2] = (uz + 1 == nz ? (P.bc ? nz - 1 : 0u) : uz + 1) * nxy;
     return s;
 }
-// Eq. 33 gradient of a field at a cell
+// Eq. 33 gradient of a field at a cell, its neighbours read through L1 (the closure
+// has two fields: too little work a block to repay staging them behind a barrier)
 template <class R>
 __device__ __forceinline__ void grad3(const Nb3& nb, const R* __restrict__ f, R g[3]) {
     R a0 = R(0), a1 = R(0), a2 = R(0);
@@ -144,12 +199,13 @@ __device__ __forceinline__ void grad3(const Nb3& nb, const R* __restrict__ f, R 
     }
     g[0] = ocs2(a0); g[1] = ocs2(a1); g[2] = ocs2(a2);
 }
+// Eq. 33 Laplacian of a staged field at tile position sc
 template <class R>
-__device__ __forceinline__ R lap3(const Nb3& nb, const R* __restrict__ f, unsigned c) {
-    const R c0 = f[c];
+__device__ __forceinline__ R lap3_tile(const R* __restrict__ t, int sc) {
+    const R c0 = t[sc];
     R a = R(0);
 #pragma unroll
-    for (int j = 0; j < Q3; ++j) a += R(2) * w3<R>(j) * (f[nb.at(j)] - c0);
+    for (int j = 0; j < Q3; ++j) a += R(2) * w3<R>(j) * (t[sc + c3z(j) * K3P + c3y(j) * K3X + c3x(j)] - c0);
     return ocs2(a);
 }
 
@@ -449,17 +505,21 @@ __global__ void __launch_bounds__(256) k3_init_h(P3 P, R* __restrict__ h) {
 template <class R>
 __global__ void __launch_bounds__(256) k3_chem(P3 P, const R* __restrict__ phi, const R* __restrict__ E,
                                                R* __restrict__ mu) {
+    __shared__ R st[3 * K3F];  // phi_1..3 on the staged three-plane tile
+    const R* const fl[3] = {phi, phi + P.N, phi + 2 * P.N};
+    stage_tile3<R, 3>(P, fl, st);
+    __syncthreads();
     int x, y, z;
     size_t cz;
     if (!cell3(P, x, y, z, cz)) return;
     const unsigned N = (unsigned)P.N, c = (unsigned)cz;
-    const Nb3 nb = stencil3(P, x, y, z);
+    const int sc = K3P + (threadIdx.y + 1) * K3X + threadIdx.x + 1;
     const R e2 = E[c] * E[c] + E[N + c] * E[N + c] + E[2 * N + c] * E[2 * N + c];
     const R D = pv<R>(P.D, P.fD);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const R ph = phi[i * N + c], lam = pv<R>(P.lam[i], P.flam[i]);
-        const R lap = lap3<R>(nb, phi + i * N, c);
+        const R ph = st[i * K3F + sc], lam = pv<R>(P.lam[i], P.flam[i]);
+        const R lap = lap3_tile<R>(st + i * K3F, sc);
         const R bulk = R(24) / D * lam * ph * (ph - R(0.5)) * (ph - R(1));
         const R grad = R(0.75) * D * lam * lap;
         const R deps = R(6) * pv<R>(P.eps[i], P.feps[i]) * ph * (R(1) - ph);
@@ -476,10 +536,9 @@ __global__ void __launch_bounds__(256) k3_chem(P3 P, const R* __restrict__ phi, 
 // with a one-cell halo, on the planes z - 1, z, z + 1 (periodic or mirrored at the
 // walls, as the stencil ghosts), are staged in shared memory first: each thread
 // then forms the six gradients from shared memory, in the neighbour order of
-// grad3 (the same sums), instead of 90 global loads with their index
+// grad3_tile (the same sums), instead of 90 global loads with their index
 // arithmetic.  Blocks of consecutive planes run close together in time, so the
 // neighbour planes come from L2.
-constexpr int K3X = 34, K3Y = 10, K3P = K3X * K3Y, K3F = 3 * K3P;  // staged tile: 3 planes of 34 x 10
 // Shared memory: the six staged stencil fields, then the cell's 75 populations and
 // 12 d/dt history planes, requested as cp.async copies at entry so that all of them
 // are in flight together (the kernel was bound by the latency of these loads).
@@ -522,22 +581,8 @@ __global__ void __launch_bounds__(256, k3_collide_min_blocks<R>()) k3_collide(P3
         cp_async_commit();
     }
     {
-        const int x0 = blockIdx.x * 32 - 1, y0 = blockIdx.y * 8 - 1, zc = blockIdx.z;
-        int zs[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            int zz = zc + d - 1;
-            if (P.bc == 0) zz = zz < 0 ? zz + P.nz : (zz >= P.nz ? zz - P.nz : zz);
-            else zz = zz < 0 ? -zz - 1 : (zz >= P.nz ? 2 * P.nz - zz - 1 : zz);
-            zs[d] = zz;
-        }
         const R* const fl[6] = {mu, mu + N, mu + 2 * N, eps_f, sig_f, rho_f};
-        for (int k = tid; k < K3F; k += 256) {
-            const int pz = k / K3P, r = k - pz * K3P, ly = r / K3X, lx = r - ly * K3X;
-            const size_t n = ((size_t)zs[pz] * P.ny + wrapi(y0 + ly, P.ny)) * P.nx + wrapi(x0 + lx, P.nx);
-#pragma unroll
-            for (int f = 0; f < 6; ++f) st[f * K3F + k] = fl[f][n];
-        }
+        stage_tile3<R, 6>(P, fl, st);
     }
     cp_async_wait_all();  // the copies are published by the barrier
     __syncthreads();
