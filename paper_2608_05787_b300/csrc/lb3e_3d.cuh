@@ -2,10 +2,12 @@
 // schemes of Section 3 with 15 directions, the isotropic stencils of Eq. 33 with
 // the D3Q15 weights, x and y periodic, walls (and electrodes) normal to z.
 //
-// One thread per cell, blocks of 32 x 8 cells in an x-y plane, one grid layer per
-// z plane.  Populations are structure-of-arrays planes (15 set + j) * N + cell,
-// cell = (z ny + y) nx + x, sets g, f1, f2, f3, l; the potential populations h
-// have their own 15 planes.  Push streaming between two buffers.
+// Blocks of 32 x 8 cells in an x-y plane: one thread a cell and one grid layer a z
+// plane, except the TMA-staged potential iteration (a block walks two planes) and
+// the observables (a thread sums 16 planes).  Populations are structure-of-arrays
+// planes (15 set + j) * N + cell, cell = (z ny + y) nx + x, sets g, f1, f2, f3, l;
+// the potential populations h have their own 15 planes.  Push streaming between two
+// buffers.
 //
 // Readings beyond the two-dimensional ones: the potential source is split evenly
 // over the 14 moving directions (varpi_j = 1/14; the paper gives 1/8 on D2Q9's 8);
