@@ -1534,15 +1534,22 @@ __device__ __forceinline__ void body_fused(const DevParams P, const S* __restric
             smu[i][k] = chem_pot<R>(P, i, ph, lap_tile<R>(sphi[i], PX, ly + 1, lx + 1), e2, c24);
         }
     }
-    if (tma) {  // every thread sees the copies complete (the barrier's phase 0)
-        if (!mbar_wait(&fz_bar, 0, TMA_WAIT_LIMIT)) {
-            if (err) atomicExch(err, 1);
+    if (tma) {
+        // every thread sees the copies complete (the barrier's phase 0); a failed wait
+        // anywhere makes the whole block give up, after a second bounded wait by the
+        // issuing thread so that no copy still lands in this block's shared memory
+        const bool ok = mbar_wait(&fz_bar, 0, TMA_WAIT_LIMIT);
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            if (tid == 0) {
+                if (!ok) mbar_wait(&fz_bar, 0, TMA_WAIT_LIMIT);
+                if (err) atomicExch(err, 1);
+            }
             return;
         }
-    } else if constexpr (kStage) {
-        cp_async_wait_all();  // slots are published by the barrier
+    } else {
+        if constexpr (kStage) cp_async_wait_all();  // slots are published by the barrier
+        __syncthreads();
     }
-    __syncthreads();
     // ghost rows of mu mirror the in-domain row they face
     if (P.bc_y != 0) {
         for (int k = tid; k < MY * MX; k += TX * BY) {
