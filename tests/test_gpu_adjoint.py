@@ -244,7 +244,7 @@ def test_unsupported_configurations_are_refused():
 
 # FP32 reverse sweeps carry the FP32 rounding of the forward state over 4000 steps:
 # measured 6.5e-5, 6.2e-5, 6.2e-5 (the FP32 tangents: 4.7e-4, 4.7e-4, 5.5e-4)
-FP32_TOL_4000 = {"V_top": 2e-4, "eps3": 2e-4, "gamma23": 2e-4}
+FP32_TOL_4000 = {"V_top": 1e-4, "eps3": 1e-4, "gamma23": 1e-4}  # the stated 1e-4
 
 
 @pytest.mark.slow
